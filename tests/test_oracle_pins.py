@@ -1,0 +1,581 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+rational arithmetic, closed forms, the moment conditions the paper states,
+textbook special cases (the integer-lattice reduction, shear-wave decay),
+the exact characteristic of the map, and invariants (conservation, uniform
+flow preservation).  All run on the CPU.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04353_gb300 import inputs as I
+
+CX, CY = O.CX, O.CY
+RNG = np.random.default_rng(1234)
+CV = 1.0 / (1.4 - 1.0)  # the oracle derives Cv = 1/(gamma - 1) from gamma
+
+
+# ---------------------------------------------------------------------------
+# exact orientation predicate
+# ---------------------------------------------------------------------------
+
+def _orient_frac(a, b, c):
+    ax, ay, bx, by, cx, cy = (Fraction(v) for v in (*a, *b, *c))
+    d = (ax - cx) * (by - cy) - (ay - cy) * (bx - cx)
+    return (d > 0) - (d < 0)
+
+
+def test_orient_exact_against_rationals():
+    n_zero = 0
+    for k in range(4000):
+        a = RNG.uniform(-50, 50, 2)
+        b = RNG.uniform(-50, 50, 2)
+        if k % 2:
+            # nearly or exactly collinear: c on the line a-b, rounded
+            t = RNG.uniform(-2, 3)
+            c = a + t * (b - a)
+            if k % 4 == 1:
+                c = a + (b - a) * 0.5  # midpoint of quantised points: exact
+                a, b = I.quantize(a), I.quantize(b)
+                c = a + (b - a) * 0.5
+        else:
+            c = RNG.uniform(-50, 50, 2)
+        s = O.orient(a[0], a[1], b[0], b[1], c[0], c[1])
+        e = _orient_frac(a, b, c)
+        n_zero += e == 0
+        assert s == e, (a, b, c)
+    assert n_zero > 500  # the degenerate branch was exercised
+
+
+# ---------------------------------------------------------------------------
+# equilibria: the moment conditions of Sec. IV / Table I
+# ---------------------------------------------------------------------------
+
+def _states(n=50):
+    for _ in range(n):
+        rho = RNG.uniform(0.5, 2.0)
+        ux, uy = RNG.uniform(-0.25, 0.25, 2)
+        T = RNG.uniform(0.15, 0.45)
+        yield rho, ux, uy, T
+
+
+def test_feq_moments_and_third_moment_deviation():
+    for rho, ux, uy, T in _states():
+        f = O.feq(rho, ux, uy, T)
+        assert np.isclose(f.sum(), rho, rtol=1e-14)
+        assert np.isclose((CX * f).sum(), rho * ux, rtol=1e-13, atol=1e-15)
+        assert np.isclose((CY * f).sum(), rho * uy, rtol=1e-13, atol=1e-15)
+        assert np.isclose((CX * CX * f).sum(), rho * ux * ux + rho * T, rtol=1e-13)
+        assert np.isclose((CX * CY * f).sum(), rho * ux * uy, rtol=1e-13, atol=1e-15)
+        assert np.isclose((CY * CY * f).sum(), rho * uy * uy + rho * T, rtol=1e-13)
+        # third moment on D2Q9 equals rho u_x; its deviation from the
+        # Maxwellian (rho u^3 + 3 rho u T) is Q'_xxx of Eq. DeviationTerms
+        m3 = (CX ** 3 * f).sum()
+        assert np.isclose(m3 - (rho * ux ** 3 + 3 * rho * ux * T),
+                          rho * ux * (1 - 3 * T) - rho * ux ** 3, rtol=1e-12, atol=1e-15)
+
+
+def _Req(rho, ux, uy, T, E):
+    d = np.eye(2)
+    u = np.array([ux, uy])
+    return 2 * rho * E * (T * d + np.outer(u, u)) + 2 * rho * T * (T * d + 2 * np.outer(u, u))
+
+
+def _mom2(g):
+    return np.array([[(CX * CX * g).sum(), (CX * CY * g).sum()],
+                     [(CY * CX * g).sum(), (CY * CY * g).sum()]])
+
+
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_geq_moments(gamma):
+    Cv = 1.0 / (gamma - 1.0)
+    for rho, ux, uy, T in _states():
+        g = O.geq(rho, ux, uy, T, Cv)
+        E = Cv * T + 0.5 * (ux * ux + uy * uy)
+        assert np.isclose(g.sum(), 2 * rho * E, rtol=1e-13)
+        q = 2 * rho * np.array([ux, uy]) * (E + T)
+        assert np.allclose([(CX * g).sum(), (CY * g).sum()], q, rtol=1e-12, atol=1e-14)
+        assert np.allclose(_mom2(g), _Req(rho, ux, uy, T, E), rtol=1e-12, atol=1e-14)
+
+
+def test_gstar_moments_carry_the_pressure_deviation():
+    Cv = 2.5
+    for rho, ux, uy, T in _states():
+        P = np.array([[rho * ux * ux + rho * T, rho * ux * uy],
+                      [rho * ux * uy, rho * uy * uy + rho * T]])
+        dP = RNG.uniform(-0.02, 0.02, (2, 2))
+        dP = dP + dP.T
+        Pn = P + dP
+        g = O.gqe(rho, ux, uy, T, Cv, Pn[0, 0], Pn[0, 1], Pn[1, 1])
+        E = Cv * T + 0.5 * (ux * ux + uy * uy)
+        u = np.array([ux, uy])
+        qeq = 2 * rho * u * (E + T)
+        assert np.isclose(g.sum(), 2 * rho * E, rtol=1e-13)
+        assert np.allclose([(CX * g).sum(), (CY * g).sum()], qeq + 2 * dP @ u, rtol=1e-12,
+                           atol=1e-14)
+        assert np.allclose(_mom2(g), _Req(rho, ux, uy, T, E), rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# collision (Eqs. feqn, geqn)
+# ---------------------------------------------------------------------------
+
+def _flow(mu=0.02, Pr=0.71, gamma=1.4):
+    return I.Flow(gamma=gamma, Pr=Pr, mu=mu, rho_inf=1.0, T_inf=0.3)
+
+
+def test_collision_conserves_and_adds_correction_momentum():
+    fl = _flow()
+    Cv = 2.5
+    for rho, ux, uy, T in _states(30):
+        f = O.feq(rho, ux, uy, T) * (1 + RNG.uniform(-0.05, 0.05, 9))
+        g = O.geq(rho, ux, uy, T, Cv) * (1 + RNG.uniform(-0.05, 0.05, 9))
+        Xx, Xy = RNG.uniform(-1e-3, 1e-3, 2)
+        fo, go = O.collide(fl, f, g, Xx, Xy)
+        assert np.isclose(fo.sum(), f.sum(), rtol=1e-14)
+        assert np.isclose(go.sum(), g.sum(), rtol=1e-14)
+        assert np.isclose((CX * fo).sum(), (CX * f).sum() + Xx, rtol=0, atol=1e-14)
+        assert np.isclose((CY * fo).sum(), (CY * f).sum() + Xy, rtol=0, atol=1e-14)
+
+
+def test_uniform_equilibrium_is_a_fixed_point():
+    # holds only with q* = q^eq + 2u.(P - P^eq) (reading of Table I's q*)
+    fl = _flow()
+    for rho, ux, uy, T in _states(30):
+        f = O.feq(rho, ux, uy, T)
+        g = O.geq(rho, ux, uy, T, 2.5)
+        fo, go = O.collide(fl, f, g, 0.0, 0.0)
+        assert np.allclose(fo, f, rtol=1e-13, atol=1e-16)
+        assert np.allclose(go, g, rtol=1e-13, atol=1e-16)
+
+
+def test_relaxation_rates_match_viscosity_and_prandtl():
+    # mu = (1/omega - 1/2) rho T dt and Pr = Cp mu / kappa with
+    # kappa = Cp (1/omega1 - 1/2) rho T dt (Sec. IV)
+    for mu, Pr in [(0.02, 0.71), (0.005, 1.3), (0.08, 0.4)]:
+        fl = _flow(mu=mu, Pr=Pr)
+        rho, ux, uy, T = 1.1, 0.05, -0.03, 0.28
+        f0 = O.feq(rho, ux, uy, T)
+        eps = 1e-6
+        df = eps * CX * CY  # pure shear stress: no mass, no momentum
+        fo, _ = O.collide(fl, f0 + df, O.geq(rho, ux, uy, T, 2.5), 0.0, 0.0)
+        ratio = ((CX * CY * fo).sum() - rho * ux * uy) / (4 * eps)
+        omega = 1 - ratio
+        assert np.isclose((1 / omega - 0.5) * rho * T, mu, rtol=1e-6)
+        # heat-flux relaxation with f at equilibrium: g' - g^eq = (1 - omega1)(g - g^eq)
+        g0 = O.geq(rho, ux, uy, T, 2.5)
+        dg = eps * np.array([0, 1, 0, -1, 0, 0, 0, 0, 0], float)  # x-heat flux, no energy
+        _, go = O.collide(fl, f0, g0 + dg, 0.0, 0.0)
+        r1 = ((CX * go).sum() - (CX * g0).sum()) / (2 * eps)
+        omega1 = 1 - r1
+        assert np.isclose((1 / omega - 0.5) / (1 / omega1 - 0.5), Pr, rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Grad-type missing populations (Sec. IV.A, Table II)
+# ---------------------------------------------------------------------------
+
+def test_grad_bc_reduces_to_equilibrium_without_gradients():
+    fl = _flow()
+    for rho, ux, uy, T in _states(20):
+        f, g = O.grad_bc(fl, rho, ux, uy, T, np.zeros(4), np.zeros(2))
+        assert np.allclose(f, O.feq(rho, ux, uy, T), rtol=1e-15, atol=0)
+        assert np.allclose(g, O.geq(rho, ux, uy, T, CV), rtol=1e-15, atol=0)
+
+
+def test_grad_bc_rigid_rotation_has_no_nonequilibrium_part():
+    # S = du + du^T vanishes for a rigid rotation, div u = 0: f^(1) = 0
+    fl = _flow()
+    rho, ux, uy, T = 1.0, 0.04, 0.02, 0.3
+    w = 0.013
+    f, _ = O.grad_bc(fl, rho, ux, uy, T, np.array([0.0, -w, w, 0.0]), np.zeros(2))
+    assert np.allclose(f, O.feq(rho, ux, uy, T), rtol=0, atol=1e-15)
+
+
+def test_grad_bc_nonequilibrium_moments():
+    fl = _flow(mu=0.02)
+    rho, ux, uy, T = 1.05, 0.03, -0.02, 0.3
+    omega = 1 / (fl.mu / (rho * T) + 0.5)
+    omega1 = 1 / ((1 / omega - 0.5) / fl.Pr + 0.5)
+    s = 0.01
+    feq = O.feq(rho, ux, uy, T)
+    f, g = O.grad_bc(fl, rho, ux, uy, T, np.array([0.0, s, 0.0, 0.0]), np.zeros(2))
+    f1 = f - feq
+    assert abs(f1.sum()) < 1e-16 and abs((CX * f1).sum()) < 1e-16 and abs((CY * f1).sum()) < 1e-16
+    assert np.isclose((CX * CY * f1).sum(), -(1 / omega) * rho * T * s, rtol=1e-12)
+    # temperature gradient at u = 0: first moment of g^(1) = -(2/omega1) rho Cp T dT
+    dT = np.array([2e-3, -1e-3])
+    g0 = O.geq(rho, 0, 0, T, CV)
+    _, g = O.grad_bc(fl, rho, 0.0, 0.0, T, np.zeros(4), dT)
+    g1 = g - g0
+    q1 = -(2 / omega1) * rho * (CV + 1) * T * dT
+    assert np.allclose([(CX * g1).sum(), (CY * g1).sum()], q1, rtol=1e-12)
+    assert abs(g1.sum()) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# P2 shape functions (Eq. Propagation for the 6-node triangle)
+# ---------------------------------------------------------------------------
+
+LOCAL = np.array([[0, 0], [1, 0], [0, 1], [0.5, 0], [0.5, 0.5], [0, 0.5]])
+
+
+def test_shape_functions_unity_kronecker_quadratics():
+    for xi, eta in RNG.uniform(0, 0.5, (100, 2)):
+        assert np.isclose(O.shape(xi, eta).sum(), 1.0, rtol=0, atol=1e-15)
+    for k, (xi, eta) in enumerate(LOCAL):
+        N = O.shape(xi, eta)
+        assert np.array_equal(N, np.eye(6)[k])
+    c = RNG.uniform(-1, 1, 6)
+    q = lambda x, y: c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y
+    vals = np.array([q(*p) for p in LOCAL])
+    for xi, eta in RNG.uniform(0, 0.5, (100, 2)):
+        assert np.isclose(O.shape(xi, eta) @ vals, q(xi, eta), rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# point location against brute force with exact rationals
+# ---------------------------------------------------------------------------
+
+def _elem_frames(mesh):
+    X, conn, L = mesh.X, mesh.conn, mesh.period
+    fr = np.empty((mesh.n_elems, 3, 2))
+    for e in range(mesh.n_elems):
+        v0 = X[conn[e, 0]]
+        for k in range(3):
+            d = X[conn[e, k]] - v0
+            for ax in range(2):
+                if L[ax] > 0:
+                    d[ax] -= L[ax] * np.round(d[ax] / L[ax])
+            fr[e, k] = v0 + d
+    return fr
+
+
+def _brute_locate(mesh, fr, p):
+    L = mesh.period
+    rng_ = (-2, -1, 0, 1, 2)
+    shifts = [(sx, sy) for sx in (rng_ if L[0] else (0,)) for sy in (rng_ if L[1] else (0,))]
+    best = None
+    for e in range(mesh.n_elems):
+        for sx, sy in shifts:
+            v = fr[e] + np.array([sx * L[0], sy * L[1]])
+            if all(_orient_frac(v[k], v[(k + 1) % 3], p) >= 0 for k in range(3)):
+                d = fr[e, 1] - fr[e, 0]
+                d2 = fr[e, 2] - fr[e, 0]
+                a2 = d[0] * d2[1] - d2[0] * d[1]
+                key = (-a2, e)
+                if best is None or key < best[0]:
+                    best = (key, e)
+    return -1 if best is None else best[1]
+
+
+@pytest.mark.parametrize("mesh", [I.periodic_box(4, 8.0, 0.2, seed=3), I.lattice_box(3),
+                                  I.naca_omesh(16, 4, chord=10.0, R=60.0, first=0.5)],
+                         ids=["jittered", "lattice", "omesh"])
+def test_point_location_matches_brute_force(mesh):
+    o = O.Oracle(mesh, I.Motion.make(0), _flow())
+    fr = _elem_frames(mesh)
+    pts = [mesh.X[a] for a in range(0, mesh.n_nodes, max(1, mesh.n_nodes // 40))]
+    lo, hi = mesh.X.min(0), mesh.X.max(0)
+    pts += list(RNG.uniform(lo, hi, (60, 2)))
+    # exact points on edges: quarter points of quantised vertices
+    for e in range(0, mesh.n_elems, max(1, mesh.n_elems // 20)):
+        pts.append(fr[e, 0] + 0.25 * (fr[e, 1] - fr[e, 0]))
+    if mesh.period[0] > 0:
+        pts += [mesh.X[0] + np.array([mesh.period[0], 0.0]), mesh.X[1] - np.array([0.0, mesh.period[1]])]
+    K = np.zeros(mesh.n_nodes)
+    for p in pts:
+        e, _ = o.interp(p[0], p[1], K)
+        assert e == _brute_locate(mesh, fr, np.asarray(p)), p
+
+
+def test_owner_element_is_largest_area_then_lowest_id():
+    mesh = I.periodic_box(5, 10.0, 0.2, seed=7)
+    o = O.Oracle(mesh, I.Motion.make(0), _flow())
+    owner, loc = o.owner()
+    fr = _elem_frames(mesh)
+    a2 = np.array([(fr[e, 1, 0] - fr[e, 0, 0]) * (fr[e, 2, 1] - fr[e, 0, 1])
+                   - (fr[e, 2, 0] - fr[e, 0, 0]) * (fr[e, 1, 1] - fr[e, 0, 1])
+                   for e in range(mesh.n_elems)])
+    for a in range(mesh.n_nodes):
+        inc = np.nonzero((mesh.conn == a).any(1))[0]
+        best = min(inc, key=lambda e: (-a2[e], e))
+        assert owner[a] == best
+        assert mesh.conn[owner[a], loc[a]] == a
+
+
+# ---------------------------------------------------------------------------
+# FE derivatives (Eqs. Ph_Derivative, FE_Derivative)
+# ---------------------------------------------------------------------------
+
+def test_fe_gradient_exact_for_quadratics():
+    mesh = I.naca_omesh(24, 5, chord=10.0, R=40.0, first=0.4)
+    o = O.Oracle(mesh, I.Motion.make(0), _flow())
+    X, Y = mesh.X[:, 0], mesh.X[:, 1]
+    c = RNG.uniform(-1, 1, 6)
+    K = c[0] + c[1] * X + c[2] * Y + c[3] * X * X + c[4] * X * Y + c[5] * Y * Y
+    gx, gy = o.fe_grad(0.0, K)
+    ex = c[1] + 2 * c[3] * X + c[4] * Y
+    ey = c[2] + c[4] * X + 2 * c[5] * Y
+    scale = np.abs(K).max() / 10
+    assert np.allclose(gx, ex, rtol=0, atol=1e-10 * scale)
+    assert np.allclose(gy, ey, rtol=0, atol=1e-10 * scale)
+
+
+@pytest.mark.parametrize("kind", [I.MOTION_PITCH, I.MOTION_PITCH_PLUNGE])
+def test_physical_gradient_of_a_physically_linear_field(kind):
+    # K = b . x(X, t) with an affine map is linear in X: d_x K must equal b.
+    mesh = I.naca_omesh(24, 5, chord=10.0, R=40.0, first=0.4)
+    mot = I.Motion.make(kind, 0.3, 0.2, 0.05, 2.5, 0.0, 1.0, 0.05)
+    o = O.Oracle(mesh, mot, _flow())
+    t = 7.0
+    x = np.array([o.map(t, a)[6:8] for a in range(mesh.n_nodes)])
+    b = np.array([0.7, -1.3])
+    gx, gy = o.fe_grad(t, x @ b)
+    assert np.allclose(gx, b[0], atol=1e-11) and np.allclose(gy, b[1], atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# map, transformed velocity and departure point (Sec. II, reading R1)
+# ---------------------------------------------------------------------------
+
+def _G(mot, X, t):
+    p = mot.params
+    if mot.kind == I.MOTION_PITCH:
+        th = p[0] + p[1] * math.sin(p[2] * t)
+        d = X - p[3:5]
+        R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        return p[3:5] + R @ d
+    if mot.kind == I.MOTION_SINE:
+        A, L, Tp = p[0], p[1], p[2]
+        s = math.sin(2 * math.pi * t / Tp)
+        return np.array([X[0] + A * math.sin(2 * math.pi * X[1] / L) * s,
+                         X[1] + A * math.sin(2 * math.pi * X[0] / L) * s])
+    raise ValueError
+
+
+def _Ginv(mot, x, t, X0):
+    Xc = np.array(X0, float)
+    for _ in range(50):  # Newton on G(X) = x with a finite-difference Jacobian
+        r = _G(mot, Xc, t) - x
+        h = 1e-6
+        J = np.stack([(_G(mot, Xc + [h, 0], t) - _G(mot, Xc - [h, 0], t)) / (2 * h),
+                      (_G(mot, Xc + [0, h], t) - _G(mot, Xc - [0, h], t)) / (2 * h)], 1)
+        dX = np.linalg.solve(J, r)
+        Xc = Xc - dX
+        if np.abs(dX).max() < 1e-13:
+            break
+    return Xc
+
+
+@pytest.mark.parametrize("mot", [I.Motion.make(I.MOTION_PITCH, 0.4, 0.3, 0.02, 20.0, 16.0),
+                                 I.Motion.make(I.MOTION_SINE, 2.0, 32.0, 40.0, 0.0)],
+                         ids=["pitch", "sine"])
+def test_transformed_velocity_is_the_characteristic_slope(mot):
+    """c^_i must be the velocity dX/dtau of the exact characteristic
+    X(tau) = G^-1(G(X_a, t1) - c_i (t1 - tau), tau) at tau = t1."""
+    mesh = I.periodic_box(8, 32.0, 0.2, seed=5)
+    o = O.Oracle(mesh, mot, _flow())
+    ol = O.Oracle(mesh, mot, _flow(), flags=O.FLAG_LITERAL_VG)
+    t1 = 13.0
+    px, py = o.departures(t1)
+    lx, ly = ol.departures(t1)
+    worst, worst_lit = 0.0, 0.0
+    for a in range(0, mesh.n_nodes, 7):
+        Xa = mesh.X[a]
+        xa = _G(mot, Xa, t1)
+        for i in range(9):
+            c = np.array([CX[i], CY[i]], float)
+            h = 1e-4
+            Xp = _Ginv(mot, xa + c * h, t1 + h, Xa)   # tau = t1 + h: x = x_a + c h
+            Xm = _Ginv(mot, xa - c * h, t1 - h, Xa)
+            chat_exact = (Xp - Xm) / (2 * h)
+            chat = Xa - np.array([px[i, a], py[i, a]])
+            chat_lit = Xa - np.array([lx[i, a], ly[i, a]])
+            worst = max(worst, np.abs(chat - chat_exact).max())
+            worst_lit = max(worst_lit, np.abs(chat_lit - chat_exact).max())
+    assert worst < 1e-6
+    assert worst_lit > 1e-3  # the printed form differs whenever g != I and V_G != 0
+
+
+def test_mesh_velocity_is_time_derivative_of_the_map():
+    mot = I.Motion.make(I.MOTION_BLENDED_PITCH, 0.1, 0.3, 0.01, 50.0, 0.0, 200.0, 1000.0)
+    mesh = I.naca_omesh(32, 12, chord=200.0, R=4000.0, first=1.0)
+    o = O.Oracle(mesh, mot, _flow())
+    t, h = 11.0, 1e-3
+    for a in range(0, mesh.n_nodes, 97):
+        m = o.map(t, a)
+        dxdt = (o.map(t + h, a)[6:8] - o.map(t - h, a)[6:8]) / (2 * h)
+        assert np.allclose(m[4:6], dxdt, rtol=1e-6, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# whole-step invariants
+# ---------------------------------------------------------------------------
+
+def _eps(st, u):
+    return (np.abs(st["ux"] - u[0]).sum() + np.abs(st["uy"] - u[1]).sum()) / (
+        st["ux"].size * (abs(u[0]) + abs(u[1])))
+
+
+def test_uniform_flow_preserved_on_deforming_mesh():
+    """Sec. V.A / Table GCL_Error: uniform flow stays uniform to round-off
+    (the paper reports eps ~ 4e-16 .. 1.1e-15)."""
+    gold = dict(np.loadtxt(__file__.replace("test_oracle_pins.py", "golden/gcl_table.txt"),
+                           comments="#"))
+    case = I.uniform_flow_case(n=12, L=24.0, period_steps=40.0, steps=60)
+    o = O.Oracle(case.mesh, case.motion, case.flow)
+    o.step(case.steps)
+    eps = _eps(o.state(), case.flow.u_inf)
+    assert eps < 100 * max(gold.values())
+
+
+def test_uniform_flow_paper_map():
+    # x = X + A sin(2 pi X/L) sin(2 pi Y/L) sin(2 pi t/t0), A/L = 500/8000,
+    # t0 = 1.5 L / u_inf, Ma 0.2, T 0.2 (Sec. V.A), on a small box
+    L = 24.0
+    fl = I.flow_params(0.2, T_inf=0.2, mu=0.02, chord=L)
+    U = fl.u_inf[0]
+    mot = I.Motion.make(I.MOTION_SINE, 500.0 / 8000.0 * L, L, 1.5 * L / U, 1.0)
+    mesh = I.periodic_box(12, L, 0.2, seed=2)
+    o = O.Oracle(mesh, mot, fl)
+    o.step(40)
+    assert _eps(o.state(), fl.u_inf) < 1e-13
+
+
+def _lattice_state(mesh, T0, u0, amp, seed):
+    rho, ux, uy, T = I.random_state(mesh.n_nodes, 1.0, T0, u0, amp, seed=seed)
+    f = np.stack([O.feq(rho[a], ux[a], uy[a], T[a]) for a in range(mesh.n_nodes)], 1)
+    g = np.stack([O.geq(rho[a], ux[a], uy[a], T[a], 2.5) for a in range(mesh.n_nodes)], 1)
+    return f, g, rho, ux, uy, T
+
+
+def test_lattice_reduction_equals_array_roll_d2q9():
+    """On an unjittered mesh with nodes on the integer lattice and no motion,
+    every departure point is a node: propagation must be the D2Q9 shift."""
+    mesh = I.lattice_box(5)   # 10 x 10 lattice
+    L = int(mesh.period[0])
+    fl = I.Flow(mu=0.02, T_inf=0.2, u_inf=(0.03, 0.01), flags=O.FLAG_PHI_OFF)
+    o = O.Oracle(mesh, I.Motion.make(0), fl)
+    f, g, rho, ux, uy, T = _lattice_state(mesh, 0.2, (0.03, 0.01), 0.01, 3)
+    o.set_state(f, g, rho, ux, uy, T)
+    ix = mesh.X[:, 0].astype(int)
+    iy = mesh.X[:, 1].astype(int)
+    F = np.zeros((9, L, L))
+    G = np.zeros((9, L, L))
+    F[:, iy, ix] = f
+    G[:, iy, ix] = g
+    for step in range(4):
+        for i in range(9):
+            F[i] = np.roll(F[i], (CY[i], CX[i]), axis=(0, 1))
+            G[i] = np.roll(G[i], (CY[i], CX[i]), axis=(0, 1))
+        for y in range(L):
+            for x in range(L):
+                F[:, y, x], G[:, y, x] = O.collide(fl, F[:, y, x], G[:, y, x], 0.0, 0.0)
+        o.step(1)
+        st = o.state()
+        assert np.allclose(st["f"], F[:, iy, ix], rtol=1e-14, atol=1e-16)
+        assert np.allclose(st["g"], G[:, iy, ix], rtol=1e-14, atol=1e-16)
+
+
+def test_lattice_mass_and_energy_conserved_with_corrections():
+    mesh = I.lattice_box(6)
+    fl = I.Flow(mu=0.02, T_inf=0.2, u_inf=(0.02, 0.01))
+    o = O.Oracle(mesh, I.Motion.make(0), fl)
+    f, g, rho, ux, uy, T = _lattice_state(mesh, 0.2, (0.02, 0.01), 0.01, 4)
+    o.set_state(f, g, rho, ux, uy, T)
+    m0, e0 = f.sum(), g.sum()
+    o.step(15)
+    st = o.state()
+    assert np.isclose(st["f"].sum(), m0, rtol=1e-14)
+    assert np.isclose(st["g"].sum(), e0, rtol=1e-14)
+
+
+def test_shear_wave_decays_at_the_kinematic_viscosity():
+    """A transverse wave u_y = U sin(k x) decays as exp(-(mu/rho) k^2 t):
+    checks mu = (1/omega - 1/2) rho T dt (Sec. IV)."""
+    n = 16
+    mesh = I.lattice_box(n)
+    L = 2 * n
+    mu = 0.02
+    fl = I.Flow(mu=mu, T_inf=0.2, u_inf=(0.0, 0.0))
+    o = O.Oracle(mesh, I.Motion.make(0), fl)
+    k = 2 * math.pi / L
+    X = mesh.X[:, 0]
+    U0 = 1e-3
+    rho = np.ones(mesh.n_nodes)
+    ux = np.zeros(mesh.n_nodes)
+    uy = U0 * np.sin(k * X)
+    T = np.full(mesh.n_nodes, 0.2)
+    f = np.stack([O.feq(rho[a], ux[a], uy[a], T[a]) for a in range(mesh.n_nodes)], 1)
+    g = np.stack([O.geq(rho[a], ux[a], uy[a], T[a], 2.5) for a in range(mesh.n_nodes)], 1)
+    o.set_state(f, g, rho, ux, uy, T)
+    amp = lambda: 2 * (o.state()["uy"] * np.sin(k * X)).mean()
+    o.step(40)
+    a1 = amp()
+    o.step(200)
+    a2 = amp()
+    rate = -math.log(a2 / a1) / 200
+    assert rate == pytest.approx(mu * k * k, rel=0.02)
+
+
+def test_fluid_at_rest_with_walls_stays_at_rest():
+    mesh = I.naca_omesh(32, 8, chord=20.0, R=200.0, first=1.0)
+    fl = I.Flow(mu=0.02, T_inf=0.3, u_inf=(0.0, 0.0), chord=20.0)
+    o = O.Oracle(mesh, I.Motion.make(0), fl)
+    o.step(10)
+    st = o.state()
+    assert np.abs(st["rho"] - 1).max() < 1e-13
+    assert np.abs(st["T"] - 0.3).max() < 1e-13
+    assert np.abs(st["ux"]).max() < 1e-13 and np.abs(st["uy"]).max() < 1e-13
+    F = o.forces()
+    # uniform pressure on a closed straight-edged body: zero net force
+    assert np.abs(F[:4]).max() < 1e-12 * 0.3 * 20.0
+
+
+def test_missing_population_classification_matches_brute_force():
+    """Reading R6: a population is missing iff its departure point lies in no
+    element or the node->departure segment properly crosses a boundary edge;
+    checked with exact rationals on a sample of a small O-mesh."""
+    mesh = I.naca_omesh(16, 4, chord=10.0, R=30.0, first=0.6)
+    mot = I.Motion.make(I.MOTION_PITCH, 0.2, 0.3, 0.05, 2.5, 0.0)
+    o = O.Oracle(mesh, mot, _flow())
+    t = 3.0
+    elem, kind = o.locate(t)
+    px, py = o.departures(t)
+    fr = _elem_frames(mesh)
+    bnd = [(fr[e, k], fr[e, (k + 1) % 3], mesh.edge_kind[e, k])
+           for e in range(mesh.n_elems) for k in range(3) if mesh.edge_kind[e, k]]
+
+    def proper(a, p, u, w):
+        return (_orient_frac(a, p, u) * _orient_frac(a, p, w) < 0 and
+                _orient_frac(u, w, a) * _orient_frac(u, w, p) < 0)
+
+    rng = np.random.default_rng(0)
+    wall_nodes = np.unique(np.concatenate([mesh.conn[e, [k, 3 + k, (k + 1) % 3]]
+                                           for e in range(mesh.n_elems) for k in range(3)
+                                           if mesh.edge_kind[e, k]]))
+    sample = list(wall_nodes) + list(rng.choice(mesh.n_nodes, 40, replace=False))
+    n_missing = 0
+    for a in sample:
+        for i in range(9):
+            p = np.array([px[i, a], py[i, a]])
+            Xa = mesh.X[a]
+            if np.array_equal(p, Xa):
+                assert elem[i, a] == -2
+                continue
+            e = _brute_locate(mesh, fr, p)
+            crossed = [k for (u, w, k) in bnd if proper(Xa, p, u, w)]
+            if e < 0 or crossed:
+                n_missing += 1
+                assert elem[i, a] == -1
+                if crossed:
+                    assert kind[i, a] == crossed[0]
+            else:
+                assert elem[i, a] == e
+    assert n_missing > 20
