@@ -1,0 +1,184 @@
+/*
+ * alelb.h -- C-ABI of the GB300 library for the ALE compressible lattice
+ * Boltzmann step on unstructured moving meshes (Saadat & Karlin,
+ * arXiv 2002.04353).
+ *
+ * Conventions for every entry point
+ *   - Return value: alelb_status (0 = OK, < 0 = error).  alelb_last_error()
+ *     gives a message for the most recent error of a solver or mesh.
+ *   - Ownership: the library owns all device memory it allocates; the caller
+ *     owns every host array it passes.  Input host arrays are copied during
+ *     the call and may be freed afterwards; output host arrays are filled
+ *     before the call returns.
+ *   - Node order: arrays exchanged with the caller are in the caller's
+ *     original node numbering; the library renumbers internally.
+ *   - Populations: D2Q9 direction order (0,0), (1,0), (0,1), (-1,0), (0,-1),
+ *     (1,1), (-1,1), (-1,-1), (1,-1); population arrays are laid out
+ *     [direction][node] (9 * n_nodes values for f, the same for g).
+ *   - Units: lattice units, time step dt = 1.
+ *   - Errors raised on the device (walk limit, non-finite state, wait
+ *     limit) are sticky per solver and reported by the next synchronising
+ *     call (alelb_sync, alelb_moments, alelb_get_pops, alelb_forces).
+ */
+#ifndef ALELB_H
+#define ALELB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ALELB_OK = 0,
+    ALELB_ERR_ARG = -1,       /* invalid argument */
+    ALELB_ERR_OOM = -2,       /* device or host allocation failed */
+    ALELB_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    ALELB_ERR_MESH = -4,      /* inverted element, bad connectivity, bad midside node */
+    ALELB_ERR_MAP = -5,       /* det g <= 0 somewhere at the requested time */
+    ALELB_ERR_LOCATE = -6,    /* element walk exceeded its step limit */
+    ALELB_ERR_NONFINITE = -7, /* non-finite or non-positive density/temperature */
+    ALELB_ERR_TIMEOUT = -8,   /* a bounded device wait gave up */
+    ALELB_ERR_STATE = -9      /* call order (e.g. stepping a destroyed solver) */
+} alelb_status;
+
+/* Motion kinds: the map x = G(X, t) of the computational domain onto the
+   physical one (Sec. II).  Parameters in alelb_mesh_desc.motion[]:
+   SINE        {A, L, T, variant}: variant 0: x = X + A sin(2 pi Y/L) s(t),
+               y = Y + A sin(2 pi X/L) s(t); variant 1 (Sec. V.A):
+               x = X + A sin(2 pi X/L) sin(2 pi Y/L) s(t), same for y;
+               s(t) = sin(2 pi t/T)
+   PLUNGE      {h, omega}: x = X, y = Y - h sin(omega t)   (Eq. Plunge_eq)
+   PITCH       {theta0, A, omega, Xc, Yc}: rotation by theta = theta0 +
+               A sin(omega t) about (Xc, Yc)                (Sec. V.C)
+   PITCH_PLUNGE{theta0, A, omega, Xc, Yc, h, omega_h}: pitch plus plunge
+   BLENDED_PITCH{theta0, A, omega, Xc, Yc, r1, r2}: x = X + b(r)[R(theta)
+               (X - Xc) - (X - Xc)], b = 1 for r <= r1, 0 for r >= r2,
+               cubic smoothstep between */
+enum {
+    ALELB_MOTION_NONE = 0,
+    ALELB_MOTION_SINE = 1,
+    ALELB_MOTION_PLUNGE = 2,
+    ALELB_MOTION_PITCH = 3,
+    ALELB_MOTION_PITCH_PLUNGE = 4,
+    ALELB_MOTION_BLENDED_PITCH = 5
+};
+
+enum { ALELB_EDGE_INTERIOR = 0, ALELB_EDGE_WALL = 1, ALELB_EDGE_FARFIELD = 2 };
+enum { ALELB_RENUMBER_NONE = 0, ALELB_RENUMBER_MORTON = 1 };
+enum { ALELB_PREC_FP64 = 0, ALELB_PREC_FP32_DEV = 1 };
+
+/* Solver flags (alelb_params.flags). */
+enum {
+    ALELB_FLAG_PHI_OFF = 1,        /* drop the correction terms phi_i (tests) */
+    ALELB_FLAG_COLLIDE_OFF = 2,    /* pure propagation, no collision (tests) */
+    ALELB_FLAG_LITERAL_VG = 4,     /* c^_i = g^{-1,T} c_i - V_G as printed in Eq. 7 */
+    ALELB_FLAG_BC_EQUILIBRIUM = 8  /* missing populations: equilibrium part only */
+};
+
+/* Mesh description (computational domain, Sec. III).  Straight-sided
+   6-node triangles: conn[6*e .. 6*e+5] = v0 v1 v2 (counter-clockwise), then
+   the midside nodes of edges (v0,v1), (v1,v2), (v2,v0), which must be the
+   exact edge midpoints.  edge_kind[3*e + k] is the kind of edge k
+   (v_k, v_k+1).  period[d] > 0 makes direction d periodic with that period
+   (coordinates in [0, period)).  All pointers are host pointers, read
+   during alelb_mesh_create only. */
+typedef struct {
+    int32_t n_nodes;
+    const double *X;          /* [2 * n_nodes], x0 y0 x1 y1 ... */
+    int32_t n_elems;
+    const int32_t *conn;      /* [6 * n_elems] */
+    const uint8_t *edge_kind; /* [3 * n_elems] */
+    double period[2];
+    int32_t motion_kind;
+    double motion[16];
+    int32_t renumber;         /* ALELB_RENUMBER_* */
+} alelb_mesh_desc;
+
+/* Fluid and run parameters (Sec. IV; R = 1, Cv = 1/(gamma - 1), Cp = Cv + 1,
+   mu constant, Pr = Cp mu / kappa).  stream: a cudaStream_t (NULL = the
+   library's own non-blocking stream); every kernel of the solver runs on it. */
+typedef struct {
+    double gamma, Pr, mu, rho_inf, T_inf, u_inf[2], chord;
+    int32_t precision; /* ALELB_PREC_* */
+    int32_t flags;     /* ALELB_FLAG_* */
+    void *stream;
+} alelb_params;
+
+typedef struct alelb_mesh alelb_mesh;
+typedef struct alelb_solver alelb_solver;
+
+/* Builds the device tables of a mesh: element frames, neighbours across
+   edges (periodic shifts included), node fans, owner elements (Sec. IV:
+   a node on element edges belongs to the incident element of larger
+   area), wall normals and probe points B (Sec. IV.A), static per-node map
+   factors.  Errors: ALELB_ERR_ARG (null/size), ALELB_ERR_MESH,
+   ALELB_ERR_OOM, ALELB_ERR_CUDA.  The mesh must outlive its solvers. */
+alelb_status alelb_mesh_create(const alelb_mesh_desc *desc, alelb_mesh **out);
+void alelb_mesh_destroy(alelb_mesh *mesh);
+
+/* Checks det g > 0 at every node at map time t (Sec. II, Eq. g_inv).
+   Returns ALELB_ERR_MAP if the map folds; does not change any solver. */
+alelb_status alelb_mesh_move(alelb_mesh *mesh, double t);
+
+/* Creates a solver on the mesh and sets the free-stream state
+   f = f^eq(rho_inf, u_inf, T_inf), g = g^eq (impulsive start) at t = 0. */
+alelb_status alelb_lb_init(alelb_mesh *mesh, const alelb_params *p, alelb_solver **out);
+void alelb_solver_destroy(alelb_solver *s);
+
+/* Advances n >= 0 time steps t_k -> t_k + 1 (Eqs. feqn, geqn with the
+   propagation of Eq. Propagation): per step, propagation with element
+   location and the Grad-type missing populations (Sec. IV.A), moments,
+   two FE-derivative passes for X_a (Eq. Xa), collision.  Asynchronous on
+   the solver's stream. */
+alelb_status alelb_lb_step(alelb_solver *s, int32_t n);
+
+/* Waits for the solver's stream and reports any sticky device error. */
+alelb_status alelb_sync(alelb_solver *s);
+
+/* Macroscopic fields of the latest step (rho, u, T; host arrays of
+   n_nodes doubles each, any may be NULL) and the current time. */
+alelb_status alelb_moments(alelb_solver *s, double *rho, double *ux, double *uy, double *T);
+alelb_status alelb_time(alelb_solver *s, double *t, int64_t *step);
+
+/* Post-collision populations (full values, FP64), [9][n_nodes] each, host. */
+alelb_status alelb_get_pops(alelb_solver *s, double *f, double *g);
+/* Sets the post-collision populations and the latest-step fields (used as
+   the previous-step quantities of the wall condition) and the time t.
+   Any field pointer may be NULL: then the field is recomputed from f, g. */
+alelb_status alelb_set_pops(alelb_solver *s, const double *f, const double *g,
+                            const double *rho, const double *ux, const double *uy,
+                            const double *T, double t);
+
+/* Wall forces at the current time: {Fx_p, Fy_p, Fx_v, Fy_v, c_D, c_L} with
+   p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule per straight
+   wall edge of the mapped geometry, c = F / (rho_inf |u_inf|^2 chord / 2)
+   along u_inf (drag) and +90 degrees (lift) (Sec. V.B).  FP64, fixed
+   summation order; synchronous. */
+alelb_status alelb_forces(alelb_solver *s, double out[6]);
+
+/* Element choice of every population for a propagation at map time t,
+   [9][n_nodes] in original numbering: elem = original element id, -2 (the
+   departure point is the node itself) or -1 (missing; kind = 1 wall,
+   2 far field).  Synchronous; does not change the solver state. */
+alelb_status alelb_locate(alelb_solver *s, double t, int32_t *elem, int8_t *kind);
+
+/* Per-kernel device time accumulated with CUDA events on the solver's
+   stream since the last reset: names[k] (static strings), ms[k], launches[k]
+   for k < *n (in: capacity, out: count).  enable != 0 starts timing (adds
+   two events per launch); enable == 0 stops it. */
+alelb_status alelb_profile(alelb_solver *s, int32_t enable);
+alelb_status alelb_kernel_times(alelb_solver *s, const char **names, double *ms,
+                                int64_t *launches, int32_t *n);
+
+/* Sizes and algorithmic traffic of one step: out = {n_nodes, n_elems,
+   bytes_state_per_node, bytes_static_per_node, n_wall_nodes}. */
+alelb_status alelb_info(alelb_solver *s, double out[8]);
+
+const char *alelb_last_error(alelb_solver *s);
+const char *alelb_mesh_last_error(alelb_mesh *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALELB_H */

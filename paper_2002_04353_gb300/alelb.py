@@ -1,0 +1,264 @@
+"""Python binding of the C-ABI in include/alelb.h (argument marshalling only).
+
+Function names mirror the C entry points without the ``alelb_`` prefix.
+Every step of the time stepping runs in the CUDA kernels of
+``csrc/kernels.cuh``; there is no CPU fallback: loading fails loudly when
+the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libalelb.so")
+
+OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_MESH", -5: "ERR_MAP",
+          -6: "ERR_LOCATE", -7: "ERR_NONFINITE", -8: "ERR_TIMEOUT", -9: "ERR_STATE"}
+PREC_FP64 = 0
+PREC_FP32_DEV = 1
+RENUMBER_NONE = 0
+RENUMBER_MORTON = 1
+FLAG_PHI_OFF = 1
+FLAG_COLLIDE_OFF = 2
+FLAG_LITERAL_VG = 4
+FLAG_BC_EQUILIBRIUM = 8
+NQ = 9
+
+# every symbol include/alelb.h declares
+EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_lb_init",
+           "alelb_solver_destroy", "alelb_lb_step", "alelb_sync", "alelb_moments", "alelb_time",
+           "alelb_get_pops", "alelb_set_pops", "alelb_forces", "alelb_locate", "alelb_profile",
+           "alelb_kernel_times", "alelb_info", "alelb_last_error", "alelb_mesh_last_error"]
+
+
+class AlelbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("X", C.c_void_p), ("n_elems", C.c_int32),
+                ("conn", C.c_void_p), ("edge_kind", C.c_void_p), ("period", C.c_double * 2),
+                ("motion_kind", C.c_int32), ("motion", C.c_double * 16), ("renumber", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double),
+                ("rho_inf", C.c_double), ("T_inf", C.c_double), ("u_inf", C.c_double * 2),
+                ("chord", C.c_double), ("precision", C.c_int32), ("flags", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (build it with paper_2002_04353_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run `python -m paper_2002_04353_gb300.build`)")
+    L = C.CDLL(path)
+    p, i32, d = C.c_void_p, C.c_int32, C.c_double
+    L.alelb_mesh_create.argtypes = [C.POINTER(MeshDesc), C.POINTER(p)]
+    L.alelb_mesh_destroy.argtypes = [p]
+    L.alelb_mesh_destroy.restype = None
+    L.alelb_mesh_move.argtypes = [p, d]
+    L.alelb_lb_init.argtypes = [p, C.POINTER(Params), C.POINTER(p)]
+    L.alelb_solver_destroy.argtypes = [p]
+    L.alelb_solver_destroy.restype = None
+    L.alelb_lb_step.argtypes = [p, i32]
+    L.alelb_sync.argtypes = [p]
+    L.alelb_moments.argtypes = [p, p, p, p, p]
+    L.alelb_time.argtypes = [p, C.POINTER(d), C.POINTER(C.c_int64)]
+    L.alelb_get_pops.argtypes = [p, p, p]
+    L.alelb_set_pops.argtypes = [p, p, p, p, p, p, p, d]
+    L.alelb_forces.argtypes = [p, p]
+    L.alelb_locate.argtypes = [p, d, p, p]
+    L.alelb_profile.argtypes = [p, i32]
+    L.alelb_kernel_times.argtypes = [p, C.POINTER(C.c_char_p), p, p, C.POINTER(i32)]
+    L.alelb_info.argtypes = [p, p]
+    L.alelb_last_error.argtypes = [p]
+    L.alelb_last_error.restype = C.c_char_p
+    L.alelb_mesh_last_error.argtypes = [p]
+    L.alelb_mesh_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        if fn.restype is C.c_int:  # default: alelb_status
+            fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Mesh:
+    """alelb_mesh_create / alelb_mesh_move / alelb_mesh_destroy."""
+
+    def __init__(self, mesh, motion, renumber=RENUMBER_MORTON):
+        L = load()
+        self._keep = (_f64(mesh.X).reshape(-1), np.ascontiguousarray(mesh.conn, dtype=np.int32).reshape(-1),
+                      np.ascontiguousarray(mesh.edge_kind, dtype=np.uint8).reshape(-1))
+        X, conn, ek = self._keep
+        d = MeshDesc()
+        d.n_nodes = mesh.n_nodes
+        d.X = X.ctypes.data
+        d.n_elems = mesh.n_elems
+        d.conn = conn.ctypes.data
+        d.edge_kind = ek.ctypes.data
+        d.period[0], d.period[1] = float(mesh.period[0]), float(mesh.period[1])
+        d.motion_kind = int(motion.kind)
+        for k in range(16):
+            d.motion[k] = float(motion.params[k])
+        d.renumber = int(renumber)
+        h = C.c_void_p()
+        st = L.alelb_mesh_create(C.byref(d), C.byref(h))
+        if st != OK:
+            msg = L.alelb_mesh_last_error(h).decode() if h.value else ""
+            if h.value:
+                L.alelb_mesh_destroy(h)
+            raise AlelbError(st, "mesh_create: " + msg)
+        self.h = h
+        self.n_nodes = mesh.n_nodes
+        self.n_elems = mesh.n_elems
+
+    def move(self, t):
+        L = load()
+        st = L.alelb_mesh_move(self.h, float(t))
+        if st != OK:
+            raise AlelbError(st, L.alelb_mesh_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().alelb_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mesh_create(mesh, motion, renumber=RENUMBER_MORTON):
+    return Mesh(mesh, motion, renumber)
+
+
+class Solver:
+    """alelb_lb_init and the per-solver entry points."""
+
+    def __init__(self, mesh: Mesh, flow, precision=PREC_FP64, flags=None, stream=None):
+        L = load()
+        p = Params()
+        p.gamma, p.Pr, p.mu = flow.gamma, flow.Pr, flow.mu
+        p.rho_inf, p.T_inf = flow.rho_inf, flow.T_inf
+        p.u_inf[0], p.u_inf[1] = flow.u_inf
+        p.chord = flow.chord
+        p.precision = int(precision)
+        p.flags = int(flow.flags if flags is None else flags)
+        p.stream = stream
+        h = C.c_void_p()
+        st = L.alelb_lb_init(mesh.h, C.byref(p), C.byref(h))
+        if st != OK:
+            msg = L.alelb_last_error(h).decode() if h.value else ""
+            if h.value:
+                L.alelb_solver_destroy(h)
+            raise AlelbError(st, "lb_init: " + msg)
+        self.h = h
+        self.mesh = mesh
+        self.nn = mesh.n_nodes
+
+    def _check(self, st, what):
+        if st != OK:
+            raise AlelbError(st, f"{what}: " + load().alelb_last_error(self.h).decode())
+
+    def lb_step(self, n=1):
+        self._check(load().alelb_lb_step(self.h, int(n)), "lb_step")
+
+    step = lb_step
+
+    def sync(self):
+        self._check(load().alelb_sync(self.h), "sync")
+
+    def moments(self):
+        out = [np.empty(self.nn) for _ in range(4)]
+        self._check(load().alelb_moments(self.h, *[_ptr(a) for a in out]), "moments")
+        return dict(rho=out[0], ux=out[1], uy=out[2], T=out[3])
+
+    def moments_into(self, rho, ux, uy, T):
+        self._check(load().alelb_moments(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(T)), "moments")
+
+    def time(self):
+        t = C.c_double()
+        n = C.c_int64()
+        self._check(load().alelb_time(self.h, C.byref(t), C.byref(n)), "time")
+        return t.value, n.value
+
+    def get_pops(self, f=None, g=None):
+        f = np.empty((NQ, self.nn)) if f is None else f
+        g = np.empty((NQ, self.nn)) if g is None else g
+        self._check(load().alelb_get_pops(self.h, _ptr(f), _ptr(g)), "get_pops")
+        return f, g
+
+    def set_pops(self, f, g, rho=None, ux=None, uy=None, T=None, t=0.0):
+        f, g = _f64(f), _f64(g)
+        fl = [None if a is None else _f64(a) for a in (rho, ux, uy, T)]
+        self._check(load().alelb_set_pops(self.h, _ptr(f), _ptr(g), *[_ptr(a) for a in fl], float(t)),
+                    "set_pops")
+
+    def forces(self):
+        out = np.empty(6)
+        self._check(load().alelb_forces(self.h, _ptr(out)), "forces")
+        return out
+
+    def locate(self, t):
+        e = np.empty((NQ, self.nn), dtype=np.int32)
+        k = np.empty((NQ, self.nn), dtype=np.int8)
+        self._check(load().alelb_locate(self.h, float(t), _ptr(e), _ptr(k)), "locate")
+        return e, k
+
+    def profile(self, enable=True):
+        self._check(load().alelb_profile(self.h, int(bool(enable))), "profile")
+
+    def kernel_times(self):
+        names = (C.c_char_p * 8)()
+        ms = np.zeros(8)
+        n_l = np.zeros(8, dtype=np.int64)
+        n = C.c_int32(8)
+        self._check(load().alelb_kernel_times(self.h, names, _ptr(ms), _ptr(n_l), C.byref(n)),
+                    "kernel_times")
+        return {names[k].decode(): (float(ms[k]), int(n_l[k])) for k in range(n.value)}
+
+    def info(self):
+        out = np.zeros(8)
+        self._check(load().alelb_info(self.h, _ptr(out)), "info")
+        return dict(n_nodes=int(out[0]), n_elems=int(out[1]), pop_bytes=out[2],
+                    n_wall_nodes=int(out[4]), precision=int(out[5]), n_wall_edges=int(out[6]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().alelb_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lb_init(mesh, flow, precision=PREC_FP64, flags=None, stream=None):
+    return Solver(mesh, flow, precision, flags, stream)

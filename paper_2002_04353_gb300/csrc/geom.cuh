@@ -1,0 +1,389 @@
+// geom.cuh -- device geometry of the ALE propagation (Sec. II, Sec. III):
+// the mesh map and its metrics, the transformed discrete velocities, the
+// departure points, an exact orientation predicate and the straight-line
+// element walk that locates each departure point.
+//
+// Bitwise agreement of element choices with an independent FP64 reference
+// requires that the departure point be computed with one fixed sequence of
+// correctly rounded FP64 operations.  Every FP64 operation on that path is
+// therefore written with __dadd_rn/__dsub_rn/__dmul_rn/__ddiv_rn, which the
+// compiler never contracts into FMAs; the sequence is:
+//   det g = x_X y_Y - y_X x_Y,  inv = 1/det g,
+//   A = g^{-1,T} = [[y_Y inv, -(x_Y inv)], [-(y_X inv), x_X inv]],
+//   w = A V_G,  c^_i = (A c_i) - w,  X_dp = X - c^_i     (dt = 1)
+#pragma once
+#include <cstdint>
+
+namespace alelb {
+
+constexpr int NQ = 9;
+__constant__ int c_cx[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int c_cy[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+enum : int { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
+             MK_BLENDED = 5 };
+enum : int { ERR_LOCATE = 1, ERR_NONFINITE = 2 };
+
+// Per-step scalars of the map (host libm, once per step).
+struct MapScalars {
+    double s, sd;      // sine map: s(t), s'(t)
+    double vy, yoff;   // plunge velocity and offset
+    double c, sn, thd; // rotation: cos, sin, angular rate
+    double cm;         // cos - 1
+};
+
+struct MapStatic {
+    int kind;
+    double Xc, Yc;
+    const double *ms; // per-node static factors, SoA [k * N + a]
+    int N;
+};
+
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+
+// Metrics x_X, x_Y, y_X, y_Y and mesh velocity V_G at a node.
+__device__ __forceinline__ void map_node(const MapStatic &M, const MapScalars &S, int a,
+                                         double X, double Y, double &xX, double &xY,
+                                         double &yX, double &yY, double &Vx, double &Vy)
+{
+    switch (M.kind) {
+    case MK_SINE: {
+        const double *m = M.ms;
+        const int N = M.N;
+        xX = da(1.0, dm(m[2 * N + a], S.s));
+        xY = dm(m[3 * N + a], S.s);
+        yX = dm(m[4 * N + a], S.s);
+        yY = da(1.0, dm(m[5 * N + a], S.s));
+        Vx = dm(m[a], S.sd);
+        Vy = dm(m[N + a], S.sd);
+        break;
+    }
+    case MK_PLUNGE:
+        xX = 1.0;
+        xY = 0.0;
+        yX = 0.0;
+        yY = 1.0;
+        Vx = 0.0;
+        Vy = S.vy;
+        break;
+    case MK_PITCH:
+    case MK_PITCH_PLUNGE: {
+        double dx = ds(X, M.Xc), dy = ds(Y, M.Yc);
+        xX = S.c;
+        xY = -S.sn;
+        yX = S.sn;
+        yY = S.c;
+        Vx = dm(S.thd, ds(dm(-S.sn, dx), dm(S.c, dy)));
+        Vy = da(dm(S.thd, ds(dm(S.c, dx), dm(S.sn, dy))), S.vy);
+        break;
+    }
+    case MK_BLENDED: {
+        const int N = M.N;
+        double dx = ds(X, M.Xc), dy = ds(Y, M.Yc);
+        double b = M.ms[a], bX = M.ms[N + a], bY = M.ms[2 * N + a];
+        double qx = ds(dm(S.cm, dx), dm(S.sn, dy));
+        double qy = da(dm(S.sn, dx), dm(S.cm, dy));
+        double one_bcm = da(1.0, dm(b, S.cm));
+        xX = da(one_bcm, dm(qx, bX));
+        xY = da(-dm(b, S.sn), dm(qx, bY));
+        yX = da(dm(b, S.sn), dm(qy, bX));
+        yY = da(one_bcm, dm(qy, bY));
+        double bt = dm(b, S.thd);
+        Vx = dm(bt, ds(dm(-S.sn, dx), dm(S.c, dy)));
+        Vy = dm(bt, ds(dm(S.c, dx), dm(S.sn, dy)));
+        break;
+    }
+    default:
+        xX = 1.0;
+        xY = 0.0;
+        yX = 0.0;
+        yY = 1.0;
+        Vx = 0.0;
+        Vy = 0.0;
+    }
+}
+
+// Physical position G(X, t) (forces only; not on the bitwise path).
+__device__ __forceinline__ void map_position(const MapStatic &M, const MapScalars &S, int a,
+                                             double X, double Y, double &x, double &y)
+{
+    const int N = M.N;
+    switch (M.kind) {
+    case MK_SINE:
+        x = X + M.ms[a] * S.s;
+        y = Y + M.ms[N + a] * S.s;
+        break;
+    case MK_PLUNGE:
+        x = X;
+        y = Y + S.yoff;
+        break;
+    case MK_PITCH:
+    case MK_PITCH_PLUNGE: {
+        double dx = X - M.Xc, dy = Y - M.Yc;
+        x = M.Xc + (dx * S.c - dy * S.sn);
+        y = M.Yc + (dx * S.sn + dy * S.c) + S.yoff;
+        break;
+    }
+    case MK_BLENDED: {
+        double dx = X - M.Xc, dy = Y - M.Yc, b = M.ms[a];
+        x = X + b * (S.cm * dx - S.sn * dy);
+        y = Y + b * (S.sn * dx + S.cm * dy);
+        break;
+    }
+    default:
+        x = X;
+        y = Y;
+    }
+}
+
+// A = g^{-1,T} = (1/det g) [[y_Y, -x_Y], [-y_X, x_X]]; returns det g.
+__device__ __forceinline__ double metric_inverse_T(double xX, double xY, double yX, double yY,
+                                                   double &a11, double &a12, double &a21,
+                                                   double &a22)
+{
+    double det = ds(dm(xX, yY), dm(yX, xY));
+    double inv = __ddiv_rn(1.0, det);
+    a11 = dm(yY, inv);
+    a12 = -dm(xY, inv);
+    a21 = -dm(yX, inv);
+    a22 = dm(xX, inv);
+    return det;
+}
+
+// ---------------------------------------------------------------------------
+// Exact orientation sign of (a, b, c): sign of (a-c) x (b-c).
+// Stage 1: the FP64 determinant with the certified error bound of Shewchuk
+// (1997), errbound = (3 + 16 eps) eps (|l| + |r|), eps = 2^-53.
+// Stage 2 (rare): the determinant expanded into six products, each split
+// exactly into two doubles with an FMA, and the twelve terms summed exactly
+// as a non-overlapping expansion (Two-Sum / Grow-Expansion).
+// ---------------------------------------------------------------------------
+__device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
+                                         double cy)
+{
+    double pa[6] = {ax, -ax, -cx, -ay, ay, cy};
+    double pb[6] = {by, cy, by, bx, cx, bx};
+    double e[16];
+    int m = 0;
+    for (int k = 0; k < 12; ++k) {
+        double hi = __dmul_rn(pa[k >> 1], pb[k >> 1]);
+        double q = (k & 1) ? __fma_rn(pa[k >> 1], pb[k >> 1], -hi) : hi;
+        int mm = 0;
+        for (int j = 0; j < m; ++j) {
+            double s = __dadd_rn(q, e[j]);
+            double bv = __dsub_rn(s, q);
+            double av = __dsub_rn(s, bv);
+            double err = __dadd_rn(__dsub_rn(q, av), __dsub_rn(e[j], bv));
+            if (err != 0.0) e[mm++] = err;
+            q = s;
+        }
+        if (q != 0.0) e[mm++] = q;
+        m = mm;
+    }
+    if (m == 0) return 0;
+    return e[m - 1] > 0.0 ? 1 : -1;
+}
+
+__device__ __forceinline__ int orient(double ax, double ay, double bx, double by, double cx,
+                                      double cy)
+{
+    double l = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
+    double r = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
+    double det = __dsub_rn(l, r);
+    double bound = 3.3306690738754716e-16 * (fabs(l) + fabs(r));
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+    return orient_exact(ax, ay, bx, by, cx, cy);
+}
+
+// ---------------------------------------------------------------------------
+// Mesh topology for the walk
+// ---------------------------------------------------------------------------
+struct MeshDev {
+    int N, E;
+    double Lx, Ly;
+    const double2 *X;      // [N] node coordinates
+    const double2 *ev;     // [3E] vertex coordinates in each element's frame
+    const int *nbr;        // [3E] neighbour across edge k (-1 on a boundary)
+    const uint32_t *einfo; // [E] per edge k, byte k: kind(2) | nbr edge(2) | dsx+1(2) | dsy+1(2)
+    const int *rank;       // [E] tie-break rank: larger area first, then lower original id
+    const int *conn;       // [6E]
+    const int *fan_ptr;    // [N+1]
+    const int2 *fan;       // (elem, loc | (sx+1)<<4 | (sy+1)<<6)
+    const int2 *owner;     // (elem, local index) of each node
+    const uint8_t *bkind;  // [N] boundary kind of the node (0 interior)
+    const int *wall_idx;   // [N] index into the wall tables or -1
+    const int *probe_e;    // [NW]
+    const double2 *probe_xi; // [NW]
+    const int *orig_elem;  // [E] original element id
+};
+
+struct Loc {
+    int e;      // element (>= 0), or -1 missing, -2 the node itself
+    int sx, sy; // frame shift of e (periods)
+    int kind;   // boundary kind when missing
+    int vnode;  // >= 0: the departure point coincides with this vertex node
+};
+
+__device__ __forceinline__ void load_frame(const MeshDev &M, int e, int sx, int sy, double w[6])
+{
+    double ox = sx ? sx * M.Lx : 0.0, oy = sy ? sy * M.Ly : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double2 v = M.ev[3 * e + k];
+        w[2 * k] = (sx ? __dadd_rn(v.x, ox) : v.x);
+        w[2 * k + 1] = (sy ? __dadd_rn(v.y, oy) : v.y);
+    }
+}
+
+constexpr int WALK_LIMIT = 256;
+
+// Straight-line walk from node a along the segment X_a -> p through the
+// element adjacency (reading of Sec. III's departure-point search: the
+// paper does not name a search).  A population is missing when the walk
+// leaves the mesh through a boundary edge, or when no element of the node's
+// fan holds the first piece of the segment.  A line through a vertex is
+// treated as passing to the vertex's right.  Ties (p on an edge or vertex)
+// go to the containing element of larger computational area, then lower
+// original id.
+__device__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
+                    int *err)
+{
+    Loc r;
+    r.kind = 0;
+    r.vnode = -1;
+    r.sx = r.sy = 0;
+    int beg = M.fan_ptr[a], end = M.fan_ptr[a + 1];
+    int e = -1, loc = 0, sx = 0, sy = 0;
+    double w[6];
+    for (int k = beg; k < end; ++k) {
+        int2 fe = M.fan[k];
+        int ll = fe.y & 15, ssx = ((fe.y >> 4) & 3) - 1, ssy = ((fe.y >> 6) & 3) - 1;
+        load_frame(M, fe.x, ssx, ssy, w);
+        bool hit;
+        if (ll < 3) {
+            int k1 = (ll + 1) % 3, k2 = (ll + 2) % 3;
+            hit = orient(w[2 * ll], w[2 * ll + 1], w[2 * k1], w[2 * k1 + 1], px, py) >= 0 &&
+                  orient(w[2 * ll], w[2 * ll + 1], w[2 * k2], w[2 * k2 + 1], px, py) < 0;
+        } else {
+            int k0 = ll - 3, k1 = (k0 + 1) % 3;
+            hit = orient(w[2 * k0], w[2 * k0 + 1], w[2 * k1], w[2 * k1 + 1], px, py) >= 0;
+        }
+        if (hit) {
+            e = fe.x;
+            loc = ll;
+            sx = ssx;
+            sy = ssy;
+            break;
+        }
+    }
+    if (e < 0) {
+        if (!M.bkind[a]) { // an interior node's sectors cover every direction
+            atomicOr(err, ERR_LOCATE);
+            r.e = -2;
+            return r;
+        }
+        r.e = -1;
+        r.kind = M.bkind[a];
+        return r;
+    }
+    int o[3];
+    int kout;
+    load_frame(M, e, sx, sy, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int k1 = (k + 1) % 3;
+        o[k] = orient(w[2 * k], w[2 * k + 1], w[2 * k1], w[2 * k1 + 1], px, py);
+    }
+    bool found = o[0] >= 0 && o[1] >= 0 && o[2] >= 0;
+    if (!found) {
+        if (loc < 3) {
+            kout = (loc + 1) % 3;
+        } else {
+            int k0 = loc - 3, k2 = (k0 + 2) % 3;
+            kout = orient(Xa, Ya, px, py, w[2 * k2], w[2 * k2 + 1]) >= 0 ? (k0 + 1) % 3 : k2;
+        }
+        int step = 0;
+        for (; step < WALK_LIMIT; ++step) {
+            uint32_t inf = (M.einfo[e] >> (8 * kout)) & 255u;
+            int kind = inf & 3;
+            if (kind) {
+                r.e = -1;
+                r.kind = kind;
+                return r;
+            }
+            int kin = (inf >> 2) & 3;
+            sx += (int)((inf >> 4) & 3) - 1;
+            sy += (int)((inf >> 6) & 3) - 1;
+            e = M.nbr[3 * e + kout];
+            load_frame(M, e, sx, sy, w);
+            int k1 = (kin + 1) % 3, k2 = (kin + 2) % 3;
+            int o1 = orient(w[2 * k1], w[2 * k1 + 1], w[2 * k2], w[2 * k2 + 1], px, py);
+            int o2 = orient(w[2 * k2], w[2 * k2 + 1], w[2 * kin], w[2 * kin + 1], px, py);
+            if (o1 >= 0 && o2 >= 0) {
+                o[kin] = 1;
+                o[k1] = o1;
+                o[k2] = o2;
+                found = true;
+                break;
+            }
+            kout = orient(Xa, Ya, px, py, w[2 * k2], w[2 * k2 + 1]) >= 0 ? k1 : k2;
+        }
+        if (!found) {
+            atomicOr(err, ERR_LOCATE);
+            r.e = -2; // fall back to the node's own value
+            return r;
+        }
+    }
+    int nz = (o[0] == 0) + (o[1] == 0) + (o[2] == 0);
+    if (nz == 1) {
+        int kz = o[0] == 0 ? 0 : (o[1] == 0 ? 1 : 2);
+        uint32_t inf = (M.einfo[e] >> (8 * kz)) & 255u;
+        if ((inf & 3) == 0) {
+            int e2 = M.nbr[3 * e + kz];
+            if (M.rank[e2] < M.rank[e]) {
+                e = e2;
+                sx += (int)((inf >> 4) & 3) - 1;
+                sy += (int)((inf >> 6) & 3) - 1;
+            }
+        }
+    } else if (nz >= 2) {
+        // p is the vertex shared by the two zero edges
+        int vl = (o[0] == 0 && o[1] == 0) ? 1 : ((o[1] == 0 && o[2] == 0) ? 2 : 0);
+        r.vnode = M.conn[6 * e + vl];
+    }
+    r.e = e;
+    r.sx = sx;
+    r.sy = sy;
+    return r;
+}
+
+// Best-ranked element of the fan of node v (the choice for a departure
+// point that coincides with vertex v).
+__device__ __forceinline__ int fan_best(const MeshDev &M, int v)
+{
+    int best = -1;
+    for (int k = M.fan_ptr[v]; k < M.fan_ptr[v + 1]; ++k) {
+        int e = M.fan[k].x;
+        if (best < 0 || M.rank[e] < M.rank[best]) best = e;
+    }
+    return best;
+}
+
+// Local coordinates (xi, eta) of p in element e (frame shift sx, sy).
+__device__ __forceinline__ void local_coords(const MeshDev &M, int e, int sx, int sy, double px,
+                                             double py, double &xi, double &eta)
+{
+    double2 v0 = M.ev[3 * e], v1 = M.ev[3 * e + 1], v2 = M.ev[3 * e + 2];
+    double x0 = v0.x + (sx ? sx * M.Lx : 0.0), y0 = v0.y + (sy ? sy * M.Ly : 0.0);
+    double x_xi = v1.x - v0.x, x_eta = v2.x - v0.x;
+    double y_xi = v1.y - v0.y, y_eta = v2.y - v0.y;
+    double detJ = x_xi * y_eta - y_xi * x_eta;
+    double dx = px - x0, dy = py - y0;
+    xi = (y_eta * dx - x_eta * dy) / detJ;
+    eta = (-y_xi * dx + x_xi * dy) / detJ;
+}
+
+} // namespace alelb

@@ -1,0 +1,385 @@
+// kernels.cuh -- the three kernels of one time step plus the element-choice
+// report and the force reduction.
+//
+//   k_stream   propagation (Eq. Propagation): transformed velocities,
+//              departure points, element walk, P2 interpolation of the
+//              post-collision populations, Grad-type missing populations
+//              (Sec. IV.A); then moments, Q'_aaa (Eq. DeviationTerms) and
+//              mu/(rho T)
+//   k_deriv1   D_a = (mu/rho T) d_a Q'_aaa in the owner element (Eq. Xa,
+//              Eqs. Ph_Derivative / FE_Derivative)
+//   k_collide  X_a = -d_a D_a, then the collision of Eqs. feqn/geqn
+//
+// One thread per node.  Populations are stored structure-of-arrays,
+// pop[q * N + node] with q = 0..8 for f and 9..17 for g.
+#pragma once
+#include "geom.cuh"
+#include "kinetic.cuh"
+
+namespace alelb {
+
+template <class S> struct StateDev {
+    S *post;  // [18 N] post-collision populations (deviations)
+    S *str;   // [18 N] streamed populations
+    S *rho, *ux, *uy, *T; // fields of the latest step
+    S *Qx, *Qy, *mrt;     // Q'_xxx, Q'_yyy, mu/(rho T)
+    S *Dx, *Dy;           // first-pass results
+};
+
+// d N_s / d xi and d N_s / d eta of the P2 triangle at the six node
+// positions (0,0), (1,0), (0,1), (1/2,0), (1/2,1/2), (0,1/2).
+__constant__ double c_dNxi[6][6];
+__constant__ double c_dNeta[6][6];
+
+template <class A> __device__ __forceinline__ void shape6(A xi, A eta, A N[6])
+{
+    A l0 = A(1) - xi - eta;
+    N[0] = l0 * (A(2) * l0 - A(1));
+    N[1] = xi * (A(2) * xi - A(1));
+    N[2] = eta * (A(2) * eta - A(1));
+    N[3] = A(4) * l0 * xi;
+    N[4] = A(4) * xi * eta;
+    N[5] = A(4) * eta * l0;
+}
+
+// d K / d X at node a in its owner element (full P2 derivative).
+template <class S>
+__device__ __forceinline__ void owner_grad(const MeshDev &M, int a, const S *K, double &KX,
+                                           double &KY)
+{
+    int2 ow = M.owner[a];
+    int e = ow.x, l = ow.y;
+    double2 v0 = M.ev[3 * e], v1 = M.ev[3 * e + 1], v2 = M.ev[3 * e + 2];
+    double x_xi = v1.x - v0.x, x_eta = v2.x - v0.x;
+    double y_xi = v1.y - v0.y, y_eta = v2.y - v0.y;
+    double detJ = x_xi * y_eta - y_xi * x_eta;
+    double sxi = 0, seta = 0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        double Ks = (double)K[M.conn[6 * e + s]];
+        sxi += Ks * c_dNxi[l][s];
+        seta += Ks * c_dNeta[l][s];
+    }
+    KX = (y_eta * sxi - y_xi * seta) / detJ;
+    KY = (-x_eta * sxi + x_xi * seta) / detJ;
+}
+
+// First-order d K / d X: gradient of the linear interpolant through the
+// owner element's vertices.
+template <class S>
+__device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const S *K,
+                                                  double &KX, double &KY)
+{
+    int e = M.owner[a].x;
+    double2 v0 = M.ev[3 * e], v1 = M.ev[3 * e + 1], v2 = M.ev[3 * e + 2];
+    double x_xi = v1.x - v0.x, x_eta = v2.x - v0.x;
+    double y_xi = v1.y - v0.y, y_eta = v2.y - v0.y;
+    double detJ = x_xi * y_eta - y_xi * x_eta;
+    double K0 = (double)K[M.conn[6 * e]];
+    double sxi = (double)K[M.conn[6 * e + 1]] - K0;
+    double seta = (double)K[M.conn[6 * e + 2]] - K0;
+    KX = (y_eta * sxi - y_xi * seta) / detJ;
+    KY = (-x_eta * sxi + x_xi * seta) / detJ;
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
+                                                KinParams<A> K, StateDev<S> st, int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = M.N;
+    if (a >= N) return;
+    const double2 Xa = M.X[a];
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    double wx, wy;
+    if (K.flags & FLAG_LITERAL_VG) {
+        wx = Vx;
+        wy = Vy;
+    } else {
+        wx = da(dm(a11, Vx), dm(a12, Vy));
+        wy = da(dm(a21, Vx), dm(a22, Vy));
+    }
+    A fs[NQ], gs[NQ];
+    int miss = 0, far = 0;
+#pragma unroll 1
+    for (int i = 0; i < NQ; ++i) {
+        const double cx = c_cx[i], cy = c_cy[i];
+        const double chx = ds(da(dm(a11, cx), dm(a12, cy)), wx);
+        const double chy = ds(da(dm(a21, cx), dm(a22, cy)), wy);
+        int self = (chx == 0.0 && chy == 0.0);
+        Loc L;
+        if (!self) {
+            const double px = ds(Xa.x, chx), py = ds(Xa.y, chy);
+            L = walk(M, a, Xa.x, Xa.y, px, py, err);
+            if (L.e == -2) self = 1;
+            if (L.e >= 0 && L.vnode < 0) {
+                double xi, eta;
+                local_coords(M, L.e, L.sx, L.sy, px, py, xi, eta);
+                A Nw[6];
+                shape6<A>((A)xi, (A)eta, Nw);
+                A sf = 0, sg = 0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    int b = M.conn[6 * L.e + k];
+                    sf += Nw[k] * (A)st.post[i * N + b];
+                    sg += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                }
+                fs[i] = sf;
+                gs[i] = sg;
+            } else if (L.e >= 0) {
+                fs[i] = (A)st.post[i * N + L.vnode];
+                gs[i] = (A)st.post[(NQ + i) * N + L.vnode];
+            } else if (L.e == -1) {
+                miss |= 1 << i;
+                if (L.kind == 2) far |= 1 << i;
+                fs[i] = 0;
+                gs[i] = 0;
+            }
+        }
+        if (self) {
+            fs[i] = (A)st.post[i * N + a];
+            gs[i] = (A)st.post[(NQ + i) * N + a];
+        }
+    }
+    if (miss & ~far) {
+        // targets (Sec. IV.A): wall node -> u = V_G, rho and T at the probe
+        // point B; other nodes -> their previous-step fields
+        A rt, uxt, uyt, Tt;
+        const int wi = M.wall_idx[a];
+        if (wi >= 0) {
+            const int pe = M.probe_e[wi];
+            const double2 pxi = M.probe_xi[wi];
+            A Nw[6];
+            shape6<A>((A)pxi.x, (A)pxi.y, Nw);
+            A r = 0, t = 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                int b = M.conn[6 * pe + k];
+                r += Nw[k] * (A)st.rho[b];
+                t += Nw[k] * (A)st.T[b];
+            }
+            rt = r;
+            Tt = t;
+            uxt = (A)Vx;
+            uyt = (A)Vy;
+        } else {
+            rt = (A)st.rho[a];
+            uxt = (A)st.ux[a];
+            uyt = (A)st.uy[a];
+            Tt = (A)st.T[a];
+        }
+        A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
+        if (!(K.flags & FLAG_BC_EQ)) {
+            double KX, KY;
+            owner_grad_linear(M, a, st.ux, KX, KY);
+            du[0] = (A)(a11 * KX + a21 * KY);
+            du[1] = (A)(a12 * KX + a22 * KY);
+            owner_grad_linear(M, a, st.uy, KX, KY);
+            du[2] = (A)(a11 * KX + a21 * KY);
+            du[3] = (A)(a12 * KX + a22 * KY);
+            owner_grad_linear(M, a, st.T, KX, KY);
+            dT[0] = (A)(a11 * KX + a21 * KY);
+            dT[1] = (A)(a12 * KX + a22 * KY);
+        }
+        A fm[NQ], gm[NQ];
+        grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+#pragma unroll
+        for (int i = 0; i < NQ; ++i)
+            if ((miss & ~far) >> i & 1) {
+                fs[i] = fm[i];
+                gs[i] = gm[i];
+            }
+    }
+    if (far) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i)
+            if (far >> i & 1) {
+                fs[i] = K.finf[i];
+                gs[i] = K.ginf[i];
+            }
+    }
+    // moments (Sec. IV): rho, u, E, T from the streamed populations
+    A sf = fs[0] + fs[1] + fs[2] + fs[3] + fs[4] + fs[5] + fs[6] + fs[7] + fs[8];
+    A jx = (fs[1] - fs[3]) + (fs[5] - fs[6]) + (fs[8] - fs[7]);
+    A jy = (fs[2] - fs[4]) + (fs[5] - fs[8]) + (fs[6] - fs[7]);
+    A sg = gs[0] + gs[1] + gs[2] + gs[3] + gs[4] + gs[5] + gs[6] + gs[7] + gs[8];
+    A rho = K.rho_ref + sf;
+    A ux = jx / rho, uy = jy / rho;
+    A E = (K.E2_ref + sg) / (A(2) * rho);
+    A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
+    if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        st.str[i * N + a] = (S)fs[i];
+        st.str[(NQ + i) * N + a] = (S)gs[i];
+    }
+    A k3 = A(1) - A(3) * T;
+    st.Qx[a] = (S)(rho * ux * k3 - rho * ux * ux * ux);
+    st.Qy[a] = (S)(rho * uy * k3 - rho * uy * uy * uy);
+    st.mrt[a] = (S)(K.mu / (rho * T));
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScalars sc,
+                                                StateDev<S> st)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= M.N) return;
+    const double2 Xa = M.X[a];
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    double KX, KY;
+    owner_grad(M, a, st.Qx, KX, KY);
+    double dQx = a11 * KX + a21 * KY; // d_x Q'_xxx
+    owner_grad(M, a, st.Qy, KX, KY);
+    double dQy = a12 * KX + a22 * KY; // d_y Q'_yyy
+    double m = (double)st.mrt[a];
+    st.Dx[a] = (S)(m * dQx);
+    st.Dy[a] = (S)(m * dQy);
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapScalars sc,
+                                                 KinParams<A> K, StateDev<S> st, int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = M.N;
+    if (a >= N) return;
+    A Xx = 0, Xy = 0;
+    if (!(K.flags & FLAG_PHI_OFF)) {
+        const double2 Xa = M.X[a];
+        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        double KX, KY;
+        owner_grad(M, a, st.Dx, KX, KY);
+        Xx = (A)(-(a11 * KX + a21 * KY));
+        owner_grad(M, a, st.Dy, KX, KY);
+        Xy = (A)(-(a12 * KX + a22 * KY));
+    }
+    A f[NQ], g[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        f[i] = (A)st.str[i * N + a];
+        g[i] = (A)st.str[(NQ + i) * N + a];
+    }
+    A rho, ux, uy, T;
+    if (!collide_node(K, f, g, Xx, Xy, rho, ux, uy, T)) atomicOr(err, ERR_NONFINITE);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        st.post[i * N + a] = (S)f[i];
+        st.post[(NQ + i) * N + a] = (S)g[i];
+    }
+    st.rho[a] = (S)rho;
+    st.ux[a] = (S)ux;
+    st.uy[a] = (S)uy;
+    st.T[a] = (S)T;
+}
+
+// Element choice of every population at map time t (parity report).
+__global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, int flags, int *elem,
+                         int8_t *kind, int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = M.N;
+    if (a >= N) return;
+    const double2 Xa = M.X[a];
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    double wx, wy;
+    if (flags & FLAG_LITERAL_VG) {
+        wx = Vx;
+        wy = Vy;
+    } else {
+        wx = da(dm(a11, Vx), dm(a12, Vy));
+        wy = da(dm(a21, Vx), dm(a22, Vy));
+    }
+    for (int i = 0; i < NQ; ++i) {
+        const double cx = c_cx[i], cy = c_cy[i];
+        const double chx = ds(da(dm(a11, cx), dm(a12, cy)), wx);
+        const double chy = ds(da(dm(a21, cx), dm(a22, cy)), wy);
+        int e = -2, k = 0;
+        if (!(chx == 0.0 && chy == 0.0)) {
+            Loc L = walk(M, a, Xa.x, Xa.y, ds(Xa.x, chx), ds(Xa.y, chy), err);
+            if (L.e >= 0) {
+                int ee = L.vnode >= 0 ? fan_best(M, L.vnode) : L.e;
+                e = M.orig_elem[ee];
+            } else if (L.e == -1) {
+                e = -1;
+                k = L.kind;
+            }
+        }
+        elem[i * N + a] = e;
+        kind[i * N + a] = (int8_t)k;
+    }
+}
+
+// Wall forces: one block, fixed-order FP64 reduction.
+// out = {Fx_p, Fy_p, Fx_v, Fy_v}.
+template <class S>
+__global__ void __launch_bounds__(256) k_forces(MeshDev M, MapStatic MS, MapScalars sc,
+                                                StateDev<S> st, const int2 *wedges, int nw,
+                                                double mu, double Cv, double *out)
+{
+    __shared__ double red[4][256];
+    double acc[4] = {0, 0, 0, 0};
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        int e = wedges[w].x, k = wedges[w].y, k1 = (k + 1) % 3;
+        int nodes[3] = {M.conn[6 * e + k], M.conn[6 * e + 3 + k], M.conn[6 * e + k1]};
+        double2 A0 = M.X[nodes[0]], B0 = M.X[nodes[2]];
+        double xa, ya, xb, yb;
+        map_position(MS, sc, nodes[0], A0.x, A0.y, xa, ya);
+        map_position(MS, sc, nodes[2], B0.x, B0.y, xb, yb);
+        double tx = xb - xa, ty = yb - ya, L = sqrt(tx * tx + ty * ty);
+        double nx = -ty / L, ny = tx / L; // out of the body, into the fluid
+        double wgt[3] = {L / 6.0, 4.0 * L / 6.0, L / 6.0};
+        for (int j = 0; j < 3; ++j) {
+            int a = nodes[j];
+            double2 Xa = M.X[a];
+            double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+            map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+            double KX, KY, d[4];
+            owner_grad(M, a, st.ux, KX, KY);
+            d[0] = a11 * KX + a21 * KY;
+            d[1] = a12 * KX + a22 * KY;
+            owner_grad(M, a, st.uy, KX, KY);
+            d[2] = a11 * KX + a21 * KY;
+            d[3] = a12 * KX + a22 * KY;
+            double div = d[0] + d[3];
+            double p = (double)st.rho[a] * (double)st.T[a];
+            double txx = mu * (2.0 * d[0] - div / Cv);
+            double tyy = mu * (2.0 * d[3] - div / Cv);
+            double txy = mu * (d[1] + d[2]);
+            acc[0] += wgt[j] * (-p * nx);
+            acc[1] += wgt[j] * (-p * ny);
+            acc[2] += wgt[j] * (txx * nx + txy * ny);
+            acc[3] += wgt[j] * (txy * nx + tyy * ny);
+        }
+    }
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// det g > 0 check at every node (alelb_mesh_move).
+__global__ void k_check_map(MapStatic MS, MapScalars sc, const double2 *X, int N, int *bad)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= N) return;
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+    map_node(MS, sc, a, X[a].x, X[a].y, xX, xY, yX, yY, Vx, Vy);
+    double det = metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    if (!(det > 0.0)) atomicAdd(bad, 1);
+}
+
+} // namespace alelb

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Element choices must agree bit for bit; FP64 populations to 1e-12 relative
+(max |diff| / max |value| per population set); the FP32-deviation mode to
+2e-4 in density, velocity and temperature.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04353_gb300 import alelb, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CV = 1.0 / (1.4 - 1.0)
+TOL64 = 1e-12
+TOL32 = 2e-4
+
+
+def _eq_state(mesh, flow, amp, seed):
+    rho, ux, uy, T = I.random_state(mesh.n_nodes, flow.rho_inf, flow.T_inf, flow.u_inf, amp, seed)
+    f = np.stack([O.feq(rho[a], ux[a], uy[a], T[a]) for a in range(mesh.n_nodes)], 1)
+    g = np.stack([O.geq(rho[a], ux[a], uy[a], T[a], CV) for a in range(mesh.n_nodes)], 1)
+    return f, g, rho, ux, uy, T
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _pair(mesh, motion, flow, prec=alelb.PREC_FP64, flags=None, state=None, renumber=alelb.RENUMBER_MORTON):
+    o = O.Oracle(mesh, motion, flow, flags=flags)
+    m = alelb.Mesh(mesh, motion, renumber)
+    s = alelb.Solver(m, flow, prec, flags=flags)
+    if state is not None:
+        o.set_state(*state)
+        s.set_pops(*state)
+    return o, m, s
+
+
+# ---------------------------------------------------------------------------
+# element choices
+# ---------------------------------------------------------------------------
+
+LOC_CASES = {
+    "box_sine": lambda: (I.periodic_box(16, 32.0, 0.2, seed=1), I.Motion.make(I.MOTION_SINE, 1.6, 32.0, 100.0, 0.0)),
+    "box_paper_map": lambda: (I.periodic_box(12, 24.0, 0.2, seed=2), I.Motion.make(I.MOTION_SINE, 1.5, 24.0, 60.0, 1.0)),
+    "lattice_static": lambda: (I.lattice_box(8), I.Motion.make(I.MOTION_NONE)),
+    "omesh_plunge": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.02)),
+    "omesh_pitch": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.3, 0.003, 50.0, 0.0, 20.0, 0.003)),
+    "omesh_blended": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_BLENDED_PITCH, 0.05, 0.3, 0.004, 50.0, 0.0, 400.0, 2000.0)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LOC_CASES))
+def test_element_choices_bitwise(name):
+    mesh, motion = LOC_CASES[name]()
+    flow = I.Flow(mu=0.02, T_inf=0.3, u_inf=(0.1, 0.0))
+    o = O.Oracle(mesh, motion, flow)
+    m = alelb.Mesh(mesh, motion)
+    s = alelb.Solver(m, flow)
+    for t in (1.0, 17.0, 33.0):
+        eo, ko = o.locate(t)
+        eg, kg = s.locate(t)
+        assert np.array_equal(eo, eg), f"{name} t={t}: {np.sum(eo != eg)} element choices differ"
+        assert np.array_equal(ko, kg)
+
+
+def test_element_choices_literal_vg_flag():
+    mesh, motion = LOC_CASES["omesh_pitch"]()
+    flow = I.Flow(mu=0.02, T_inf=0.3, u_inf=(0.1, 0.0), flags=O.FLAG_LITERAL_VG)
+    o = O.Oracle(mesh, motion, flow)
+    s = alelb.Solver(alelb.Mesh(mesh, motion), flow)
+    eo, ko = o.locate(9.0)
+    eg, kg = s.locate(9.0)
+    assert np.array_equal(eo, eg) and np.array_equal(ko, kg)
+
+
+# ---------------------------------------------------------------------------
+# full step, FP64
+# ---------------------------------------------------------------------------
+
+def _compare64(o, s, what=""):
+    st = o.state()
+    f, g = s.get_pops()
+    mo = s.moments()
+    ef, eg = _rel(f, st["f"]), _rel(g, st["g"])
+    assert ef < TOL64 and eg < TOL64, f"{what}: f {ef:.2e} g {eg:.2e}"
+    for k in ("rho", "ux", "uy", "T"):
+        assert _rel(mo[k], st[k]) < TOL64, f"{what}: {k} {_rel(mo[k], st[k]):.2e}"
+
+
+@pytest.mark.parametrize("flags", [0, O.FLAG_PHI_OFF, O.FLAG_COLLIDE_OFF])
+def test_fp64_steps_periodic_deforming_box(flags):
+    case = I.uniform_flow_case(n=16, L=32.0, period_steps=50.0)
+    st = _eq_state(case.mesh, case.flow, 0.01, seed=3)
+    o, m, s = _pair(case.mesh, case.motion, case.flow, flags=flags, state=st)
+    for k in range(3):
+        o.step(4)
+        s.lb_step(4)
+        _compare64(o, s, f"box flags={flags} after {4 * (k + 1)} steps")
+
+
+def test_fp64_steps_lattice_reduction_mesh():
+    mesh = I.lattice_box(10)
+    flow = I.Flow(mu=0.02, T_inf=0.2, u_inf=(0.02, 0.01))
+    st = _eq_state(mesh, flow, 0.01, seed=4)
+    o, m, s = _pair(mesh, I.Motion.make(0), flow, state=st)
+    o.step(6)
+    s.lb_step(6)
+    _compare64(o, s, "lattice")
+
+
+@pytest.mark.parametrize("motion_name", ["omesh_plunge", "omesh_pitch", "omesh_blended"])
+def test_fp64_steps_airfoil_walls_farfield(motion_name):
+    mesh, motion = LOC_CASES[motion_name]()
+    flow = I.flow_params(0.2, T_inf=0.3, Re=1e3, chord=200.0)
+    o, m, s = _pair(mesh, motion, flow)
+    for k in range(2):
+        o.step(3)
+        s.lb_step(3)
+        _compare64(o, s, f"{motion_name} after {3 * (k + 1)} steps")
+    fo = o.forces()
+    fg = s.forces()
+    assert np.allclose(fg, fo, rtol=1e-10, atol=1e-12 * np.abs(fo).max())
+
+
+def test_fp64_bc_equilibrium_variant():
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    flow = I.flow_params(0.2, T_inf=0.3, Re=1e3, chord=200.0)
+    flow.flags = O.FLAG_BC_EQUILIBRIUM
+    o, m, s = _pair(mesh, motion, flow)
+    o.step(4)
+    s.lb_step(4)
+    _compare64(o, s, "bc-equilibrium")
+
+
+def test_renumbering_does_not_change_results():
+    case = I.uniform_flow_case(n=10, L=20.0, period_steps=30.0)
+    mesh = case.mesh.permuted(7)
+    st = _eq_state(mesh, case.flow, 0.01, seed=5)
+    res = []
+    for ren in (alelb.RENUMBER_NONE, alelb.RENUMBER_MORTON):
+        m = alelb.Mesh(mesh, case.motion, ren)
+        s = alelb.Solver(m, case.flow)
+        s.set_pops(*st)
+        s.lb_step(5)
+        res.append(s.get_pops())
+    assert _rel(res[0][0], res[1][0]) < 1e-14 and _rel(res[0][1], res[1][1]) < 1e-14
+
+
+def test_uniform_flow_config_full_size_200_steps():
+    """The deforming periodic box at its full size (48 x 48 vertices, 9,216
+    P2 nodes, 200 steps): uniform flow preserved to round-off and the state
+    equal to the oracle's."""
+    case = I.uniform_flow_case()
+    o, m, s = _pair(case.mesh, case.motion, case.flow)
+    o.step(case.steps)
+    s.lb_step(case.steps)
+    _compare64(o, s, "config full size")
+    mo = s.moments()
+    u = case.flow.u_inf
+    eps = (np.abs(mo["ux"] - u[0]).sum() + np.abs(mo["uy"] - u[1]).sum()) / (
+        mo["ux"].size * (abs(u[0]) + abs(u[1])))
+    assert eps < 1e-13
+
+
+def test_zero_steps_and_tiny_mesh():
+    mesh = I.periodic_box(3, 6.0, 0.1, seed=9)
+    flow = I.Flow(mu=0.02, T_inf=0.2, u_inf=(0.01, 0.0))
+    st = _eq_state(mesh, flow, 0.01, seed=1)
+    o, m, s = _pair(mesh, I.Motion.make(I.MOTION_SINE, 0.2, 6.0, 20.0, 0.0), flow, state=st)
+    s.lb_step(0)
+    _compare64(o, s, "zero steps")
+    o.step(3)
+    s.lb_step(3)
+    _compare64(o, s, "tiny mesh")
+
+
+def test_mesh_errors_are_reported():
+    mesh = I.periodic_box(6, 12.0, 0.2, seed=1)
+    bad = I.Mesh(mesh.X.copy(), mesh.conn[:, [1, 0, 2, 3, 5, 4]].copy(), mesh.edge_kind, mesh.period)
+    with pytest.raises(alelb.AlelbError) as ex:
+        alelb.Mesh(bad, I.Motion.make(0))
+    assert ex.value.status == -4
+    m = alelb.Mesh(mesh, I.Motion.make(I.MOTION_SINE, 20.0, 12.0, 10.0, 0.0))
+    with pytest.raises(alelb.AlelbError) as ex:
+        m.move(2.5)  # amplitude large enough to fold the map
+    assert ex.value.status == -5
+
+
+# ---------------------------------------------------------------------------
+# FP32-deviation (mixed) mode
+# ---------------------------------------------------------------------------
+
+def _compare_mixed(o, s, what):
+    st = o.state()
+    mo = s.moments()
+    for k in ("rho", "ux", "uy", "T"):
+        scale = 1.0 if k in ("rho", "T") else max(np.abs(st["ux"]).max(), np.abs(st["uy"]).max())
+        err = np.abs(mo[k] - st[k]).max() / scale
+        assert err < TOL32, f"{what}: {k} err {err:.2e}"
+
+
+def test_mixed_box_matches_fp64_oracle():
+    case = I.uniform_flow_case(n=16, L=32.0, period_steps=50.0)
+    st = _eq_state(case.mesh, case.flow, 0.01, seed=6)
+    o, m, s = _pair(case.mesh, case.motion, case.flow, prec=alelb.PREC_FP32_DEV, state=st)
+    o.step(20)
+    s.lb_step(20)
+    _compare_mixed(o, s, "mixed box")
+
+
+def test_mixed_airfoil_matches_fp64_oracle():
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    flow = I.flow_params(0.2, T_inf=0.3, Re=1e3, chord=200.0)
+    o, m, s = _pair(mesh, motion, flow, prec=alelb.PREC_FP32_DEV)
+    o.step(6)
+    s.lb_step(6)
+    _compare_mixed(o, s, "mixed airfoil")
