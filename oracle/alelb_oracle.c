@@ -21,10 +21,10 @@
  *       containing element of larger computational area, then lower id;
  *       a departure point that coincides with the node itself (c^_i = 0)
  *       takes the node's own value
- *   R6  a population is "missing" when its departure point lies outside the
- *       mesh or the segment node->departure point properly crosses a
- *       boundary edge; far-field missing populations take the free-stream
- *       equilibria
+ *   R6  a population is "missing" when some point of the segment from the
+ *       node to its departure point lies outside the closed mesh (the
+ *       departure point itself, or a stretch that passes through the body);
+ *       far-field missing populations take the free-stream equilibria
  *   R7  D2Q9 order (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
  *   R8  wall targets: u = V_G at the wall node, rho and T interpolated at
  *       B = A + n dt from the previous step's fields; off-wall targets are
@@ -889,7 +889,7 @@ static int prepare(orc_t *o)
                 nb++;
             }
     /* per node: boundary edges (with periodic image) within rchk */
-    o->rchk = 4.0;
+    o->rchk = 6.0;
     o->bnear_ptr = xcalloc((size_t)nn + 1, sizeof(int));
     int cap = 1024, cnt = 0;
     o->bnear_e = xcalloc((size_t)cap, sizeof(int));
@@ -1110,17 +1110,12 @@ static void departure(const orc_t *o, int a, const double *gi, double Vx, double
     *py = o->X[2 * a + 1] - *chy;
 }
 
-static int proper_cross(double ax, double ay, double px, double py, double ux, double uy,
-                        double wx, double wy)
-{
-    int o1 = orc_orient(ax, ay, px, py, ux, uy);
-    int o2 = orc_orient(ax, ay, px, py, wx, wy);
-    int o3 = orc_orient(ux, uy, wx, wy, ax, ay);
-    int o4 = orc_orient(ux, uy, wx, wy, px, py);
-    return (o1 * o2 < 0) && (o3 * o4 < 0);
-}
-
 /* Element choice for population i of node a (readings R5, R6).
+   R6: the population is missing when some point of the segment X_a -> p
+   lies outside the closed mesh.  Decided exactly enough by splitting the
+   segment at every parameter where it meets a nearby boundary edge and
+   locating p and one point inside each piece: between two consecutive
+   meeting points the segment is wholly inside or wholly outside.
    Returns element >= 0 (with shift), -2 for "the node itself", or -1 with
    *kind = wall/far field for a missing population. */
 static int choose_element(const orc_t *o, int a, double chx, double chy, double px, double py,
@@ -1131,8 +1126,18 @@ static int choose_element(const orc_t *o, int a, double chx, double chy, double 
     if (sqrt(chx * chx + chy * chy) >= o->rchk - 1.0) return -3;
     double ax = o->X[2 * a], ay = o->X[2 * a + 1];
     int e = locate_point(o, px, py, shx, shy);
-    int cross_kind = 0;
-    double best_d = 1e300;
+    int nb = o->bnear_ptr[a + 1] - o->bnear_ptr[a];
+    if (nb == 0) {
+        if (e < 0) return -3; /* outside with no boundary in reach */
+        return e;
+    }
+    double tau[130];
+    int tk[130];
+    int nt = 0;
+    int hit_kind = 0;
+    double hit_tau = 2.0, near_d = 1e300;
+    int near_kind = 0;
+    double dx = px - ax, dy = py - ay, L2 = dx * dx + dy * dy;
     for (int k = o->bnear_ptr[a]; k < o->bnear_ptr[a + 1]; ++k) {
         const bedge_t *b = &o->be[o->bnear_e[k]];
         const double *v = &o->ev[12 * b->elem];
@@ -1141,25 +1146,64 @@ static int choose_element(const orc_t *o, int a, double chx, double chy, double 
         double ux = v[2 * k0] + ox, uy = v[2 * k0 + 1] + oy;
         double wx = v[2 * k1] + ox, wy = v[2 * k1 + 1] + oy;
         double d = seg_point_dist(ux, uy, wx, wy, ax, ay);
-        if (proper_cross(ax, ay, px, py, ux, uy, wx, wy)) {
-            if (!cross_kind || d < best_d) {
-                cross_kind = b->kind;
-                best_d = d;
+        if (d < near_d) {
+            near_d = d;
+            near_kind = b->kind;
+        }
+        int o1 = orc_orient(ax, ay, px, py, ux, uy);
+        int o2 = orc_orient(ax, ay, px, py, wx, wy);
+        int o3 = orc_orient(ux, uy, wx, wy, ax, ay);
+        int o4 = orc_orient(ux, uy, wx, wy, px, py);
+        double t1, t2 = -1.0;
+        if (o1 == 0 && o2 == 0) {
+            /* collinear: the edge's endpoints projected on the segment */
+            t1 = ((ux - ax) * dx + (uy - ay) * dy) / L2;
+            t2 = ((wx - ax) * dx + (wy - ay) * dy) / L2;
+            if ((t1 < 0 && t2 < 0) || (t1 > 1 && t2 > 1)) continue;
+        } else if (o1 * o2 <= 0 && o3 * o4 <= 0) {
+            double den = dx * (wy - uy) - dy * (wx - ux);
+            t1 = den != 0.0 ? ((ux - ax) * (wy - uy) - (uy - ay) * (wx - ux)) / den : 0.0;
+        } else {
+            continue;
+        }
+        double tt[2] = {t1, t2};
+        for (int j = 0; j < 2; ++j) {
+            if (j == 1 && t2 < 0 && !(o1 == 0 && o2 == 0)) break;
+            double t = fmin(1.0, fmax(0.0, tt[j]));
+            if (nt < 128) {
+                tau[nt] = t;
+                tk[nt] = b->kind;
+                nt++;
             }
-        } else if (e < 0 && !cross_kind && d < best_d) {
-            best_d = d;
-            *kind = b->kind;
+            if (t < hit_tau) {
+                hit_tau = t;
+                hit_kind = b->kind;
+            }
         }
     }
-    if (cross_kind) {
-        *kind = cross_kind;
-        return -1;
+    (void)tk;
+    int outside = e < 0;
+    if (!outside && nt > 0) {
+        tau[nt++] = 0.0;
+        tau[nt++] = 1.0;
+        /* insertion sort */
+        for (int i = 1; i < nt; ++i)
+            for (int j = i; j > 0 && tau[j] < tau[j - 1]; --j) {
+                double tmp = tau[j];
+                tau[j] = tau[j - 1];
+                tau[j - 1] = tmp;
+            }
+        for (int i = 0; i + 1 < nt && !outside; ++i) {
+            if (!(tau[i + 1] > tau[i])) continue;
+            double tm = 0.5 * (tau[i] + tau[i + 1]);
+            double qx = ax + tm * dx, qy = ay + tm * dy, sx2, sy2;
+            if (locate_point(o, qx, qy, &sx2, &sy2) < 0) outside = 1;
+        }
     }
-    if (e < 0) {
-        if (!*kind) return -3; /* outside with no boundary in reach */
-        return -1;
-    }
-    return e;
+    if (!outside) return e;
+    *kind = hit_kind ? hit_kind : near_kind;
+    if (!*kind) return -3;
+    return -1;
 }
 
 /* FE derivative d/dX of nodal field K at node a in its owner element

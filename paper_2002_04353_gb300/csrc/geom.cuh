@@ -12,6 +12,7 @@
 //   A = g^{-1,T} = [[y_Y inv, -(x_Y inv)], [-(y_X inv), x_X inv]],
 //   w = A V_G,  c^_i = (A c_i) - w,  X_dp = X - c^_i     (dt = 1)
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace alelb {
@@ -39,12 +40,61 @@ struct MapStatic {
     int N;
 };
 
-__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+// The geometry is compiled for the device and, for the CPU check of the
+// walk, for the host; host code is built without FP contraction, so the
+// plain operators round exactly like the intrinsics.
+#define ALELB_HD __host__ __device__
+ALELB_HD __forceinline__ double dm(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+ALELB_HD __forceinline__ double da(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+ALELB_HD __forceinline__ double ds(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+ALELB_HD __forceinline__ double ddiv(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __ddiv_rn(a, b);
+#else
+    return a / b;
+#endif
+}
+ALELB_HD __forceinline__ double dfma(double a, double b, double c)
+{
+#ifdef __CUDA_ARCH__
+    return __fma_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+ALELB_HD __forceinline__ void set_err(int *err, int bit)
+{
+#ifdef __CUDA_ARCH__
+    atomicOr(err, bit);
+#else
+    *err |= bit;
+#endif
+}
 
 // Metrics x_X, x_Y, y_X, y_Y and mesh velocity V_G at a node.
-__device__ __forceinline__ void map_node(const MapStatic &M, const MapScalars &S, int a,
+ALELB_HD __forceinline__ void map_node(const MapStatic &M, const MapScalars &S, int a,
                                          double X, double Y, double &xX, double &xY,
                                          double &yX, double &yY, double &Vx, double &Vy)
 {
@@ -139,17 +189,42 @@ __device__ __forceinline__ void map_position(const MapStatic &M, const MapScalar
 }
 
 // A = g^{-1,T} = (1/det g) [[y_Y, -x_Y], [-y_X, x_X]]; returns det g.
-__device__ __forceinline__ double metric_inverse_T(double xX, double xY, double yX, double yY,
+ALELB_HD __forceinline__ double metric_inverse_T(double xX, double xY, double yX, double yY,
                                                    double &a11, double &a12, double &a21,
                                                    double &a22)
 {
     double det = ds(dm(xX, yY), dm(yX, xY));
-    double inv = __ddiv_rn(1.0, det);
+    double inv = ddiv(1.0, det);
     a11 = dm(yY, inv);
     a12 = -dm(xY, inv);
     a21 = -dm(yX, inv);
     a22 = dm(xX, inv);
     return det;
+}
+
+// w = A V_G (or V_G itself for the printed form of Eq. 7).
+ALELB_HD __forceinline__ void mesh_velocity_term(double a11, double a12, double a21, double a22,
+                                                 double Vx, double Vy, bool literal, double &wx,
+                                                 double &wy)
+{
+    if (literal) {
+        wx = Vx;
+        wy = Vy;
+    } else {
+        wx = da(dm(a11, Vx), dm(a12, Vy));
+        wy = da(dm(a21, Vx), dm(a22, Vy));
+    }
+}
+
+// c^_i = (A c_i) - w and the departure point X_dp = X - c^_i dt (dt = 1).
+ALELB_HD __forceinline__ void departure(double a11, double a12, double a21, double a22,
+                                        double wx, double wy, double cx, double cy, double X,
+                                        double Y, double &chx, double &chy, double &px, double &py)
+{
+    chx = ds(da(dm(a11, cx), dm(a12, cy)), wx);
+    chy = ds(da(dm(a21, cx), dm(a22, cy)), wy);
+    px = ds(X, chx);
+    py = ds(Y, chy);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,7 +235,7 @@ __device__ __forceinline__ double metric_inverse_T(double xX, double xY, double 
 // exactly into two doubles with an FMA, and the twelve terms summed exactly
 // as a non-overlapping expansion (Two-Sum / Grow-Expansion).
 // ---------------------------------------------------------------------------
-__device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
+ALELB_HD __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
                                          double cy)
 {
     double pa[6] = {ax, -ax, -cx, -ay, ay, cy};
@@ -168,14 +243,14 @@ __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double
     double e[16];
     int m = 0;
     for (int k = 0; k < 12; ++k) {
-        double hi = __dmul_rn(pa[k >> 1], pb[k >> 1]);
-        double q = (k & 1) ? __fma_rn(pa[k >> 1], pb[k >> 1], -hi) : hi;
+        double hi = dm(pa[k >> 1], pb[k >> 1]);
+        double q = (k & 1) ? dfma(pa[k >> 1], pb[k >> 1], -hi) : hi;
         int mm = 0;
         for (int j = 0; j < m; ++j) {
-            double s = __dadd_rn(q, e[j]);
-            double bv = __dsub_rn(s, q);
-            double av = __dsub_rn(s, bv);
-            double err = __dadd_rn(__dsub_rn(q, av), __dsub_rn(e[j], bv));
+            double s = da(q, e[j]);
+            double bv = ds(s, q);
+            double av = ds(s, bv);
+            double err = da(ds(q, av), ds(e[j], bv));
             if (err != 0.0) e[mm++] = err;
             q = s;
         }
@@ -186,12 +261,12 @@ __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double
     return e[m - 1] > 0.0 ? 1 : -1;
 }
 
-__device__ __forceinline__ int orient(double ax, double ay, double bx, double by, double cx,
-                                      double cy)
+ALELB_HD __forceinline__ int orient(double ax, double ay, double bx, double by, double cx,
+                                    double cy)
 {
-    double l = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
-    double r = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
-    double det = __dsub_rn(l, r);
+    double l = dm(ds(ax, cx), ds(by, cy));
+    double r = dm(ds(ay, cy), ds(bx, cx));
+    double det = ds(l, r);
     double bound = 3.3306690738754716e-16 * (fabs(l) + fabs(r));
     if (det > bound) return 1;
     if (-det > bound) return -1;
@@ -227,15 +302,27 @@ struct Loc {
     int vnode;  // >= 0: the departure point coincides with this vertex node
 };
 
-__device__ __forceinline__ void load_frame(const MeshDev &M, int e, int sx, int sy, double w[6])
+ALELB_HD __forceinline__ void load_frame(const MeshDev &M, int e, int sx, int sy, double w[6])
 {
     double ox = sx ? sx * M.Lx : 0.0, oy = sy ? sy * M.Ly : 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double2 v = M.ev[3 * e + k];
-        w[2 * k] = (sx ? __dadd_rn(v.x, ox) : v.x);
-        w[2 * k + 1] = (sy ? __dadd_rn(v.y, oy) : v.y);
+        w[2 * k] = (sx ? da(v.x, ox) : v.x);
+        w[2 * k + 1] = (sy ? da(v.y, oy) : v.y);
     }
+}
+
+// Best-ranked element of the fan of node v (the choice for a departure
+// point that coincides with vertex v).
+ALELB_HD __forceinline__ int fan_best(const MeshDev &M, int v)
+{
+    int best = -1;
+    for (int k = M.fan_ptr[v]; k < M.fan_ptr[v + 1]; ++k) {
+        int e = M.fan[k].x;
+        if (best < 0 || M.rank[e] < M.rank[best]) best = e;
+    }
+    return best;
 }
 
 constexpr int WALK_LIMIT = 256;
@@ -248,13 +335,20 @@ constexpr int WALK_LIMIT = 256;
 // treated as passing to the vertex's right.  Ties (p on an edge or vertex)
 // go to the containing element of larger computational area, then lower
 // original id.
-__device__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
+ALELB_HD Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
                     int *err)
 {
     Loc r;
     r.kind = 0;
     r.vnode = -1;
     r.sx = r.sy = 0;
+    if (px == Xa && py == Ya) {
+        // a nonzero but negligible c^ that rounds away: the departure point
+        // is the node itself, held by every element of its fan
+        r.e = fan_best(M, a);
+        r.vnode = a;
+        return r;
+    }
     int beg = M.fan_ptr[a], end = M.fan_ptr[a + 1];
     int e = -1, loc = 0, sx = 0, sy = 0;
     double w[6];
@@ -281,7 +375,7 @@ __device__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, do
     }
     if (e < 0) {
         if (!M.bkind[a]) { // an interior node's sectors cover every direction
-            atomicOr(err, ERR_LOCATE);
+            set_err(err, ERR_LOCATE);
             r.e = -2;
             return r;
         }
@@ -332,7 +426,7 @@ __device__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, do
             kout = orient(Xa, Ya, px, py, w[2 * k2], w[2 * k2 + 1]) >= 0 ? k1 : k2;
         }
         if (!found) {
-            atomicOr(err, ERR_LOCATE);
+            set_err(err, ERR_LOCATE);
             r.e = -2; // fall back to the node's own value
             return r;
         }
@@ -360,20 +454,8 @@ __device__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, do
     return r;
 }
 
-// Best-ranked element of the fan of node v (the choice for a departure
-// point that coincides with vertex v).
-__device__ __forceinline__ int fan_best(const MeshDev &M, int v)
-{
-    int best = -1;
-    for (int k = M.fan_ptr[v]; k < M.fan_ptr[v + 1]; ++k) {
-        int e = M.fan[k].x;
-        if (best < 0 || M.rank[e] < M.rank[best]) best = e;
-    }
-    return best;
-}
-
 // Local coordinates (xi, eta) of p in element e (frame shift sx, sy).
-__device__ __forceinline__ void local_coords(const MeshDev &M, int e, int sx, int sy, double px,
+ALELB_HD __forceinline__ void local_coords(const MeshDev &M, int e, int sx, int sy, double px,
                                              double py, double &xi, double &eta)
 {
     double2 v0 = M.ev[3 * e], v1 = M.ev[3 * e + 1], v2 = M.ev[3 * e + 2];
@@ -384,6 +466,38 @@ __device__ __forceinline__ void local_coords(const MeshDev &M, int e, int sx, in
     double dx = px - x0, dy = py - y0;
     xi = (y_eta * dx - x_eta * dy) / detJ;
     eta = (-y_xi * dx + x_xi * dy) / detJ;
+}
+
+// Element choices of the nine populations of node a (parity report):
+// original element id, -2 (node itself) or -1 with kind.
+ALELB_HD inline void locate_node(const MeshDev &M, const MapStatic &MS, const MapScalars &sc,
+                                 int flags_literal, int a, int *elem9, int8_t *kind9, int *err)
+{
+    const double2 Xa = M.X[a];
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, flags_literal != 0, wx, wy);
+    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int i = 0; i < NQ; ++i) {
+        double chx, chy, px, py;
+        departure(a11, a12, a21, a22, wx, wy, (double)CXh[i], (double)CYh[i], Xa.x, Xa.y, chx,
+                  chy, px, py);
+        int e = -2, k = 0;
+        if (!(chx == 0.0 && chy == 0.0)) {
+            Loc L = walk(M, a, Xa.x, Xa.y, px, py, err);
+            if (L.e >= 0) {
+                int ee = L.vnode >= 0 ? fan_best(M, L.vnode) : L.e;
+                e = M.orig_elem[ee];
+            } else if (L.e == -1) {
+                e = -1;
+                k = L.kind;
+            }
+        }
+        elem9[i] = e;
+        kind9[i] = (int8_t)k;
+    }
 }
 
 } // namespace alelb

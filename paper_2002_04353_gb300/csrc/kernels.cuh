@@ -94,24 +94,17 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
     map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
     metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
     double wx, wy;
-    if (K.flags & FLAG_LITERAL_VG) {
-        wx = Vx;
-        wy = Vy;
-    } else {
-        wx = da(dm(a11, Vx), dm(a12, Vy));
-        wy = da(dm(a21, Vx), dm(a22, Vy));
-    }
+    mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
     A fs[NQ], gs[NQ];
     int miss = 0, far = 0;
 #pragma unroll 1
     for (int i = 0; i < NQ; ++i) {
-        const double cx = c_cx[i], cy = c_cy[i];
-        const double chx = ds(da(dm(a11, cx), dm(a12, cy)), wx);
-        const double chy = ds(da(dm(a21, cx), dm(a22, cy)), wy);
+        double chx, chy, px, py;
+        departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx,
+                  chy, px, py);
         int self = (chx == 0.0 && chy == 0.0);
         Loc L;
         if (!self) {
-            const double px = ds(Xa.x, chx), py = ds(Xa.y, chy);
             L = walk(M, a, Xa.x, Xa.y, px, py, err);
             if (L.e == -2) self = 1;
             if (L.e >= 0 && L.vnode < 0) {
@@ -286,35 +279,12 @@ __global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, int flags, int 
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
     if (a >= N) return;
-    const double2 Xa = M.X[a];
-    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
-    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
-    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-    double wx, wy;
-    if (flags & FLAG_LITERAL_VG) {
-        wx = Vx;
-        wy = Vy;
-    } else {
-        wx = da(dm(a11, Vx), dm(a12, Vy));
-        wy = da(dm(a21, Vx), dm(a22, Vy));
-    }
+    int e9[NQ];
+    int8_t k9[NQ];
+    locate_node(M, MS, sc, flags & FLAG_LITERAL_VG, a, e9, k9, err);
     for (int i = 0; i < NQ; ++i) {
-        const double cx = c_cx[i], cy = c_cy[i];
-        const double chx = ds(da(dm(a11, cx), dm(a12, cy)), wx);
-        const double chy = ds(da(dm(a21, cx), dm(a22, cy)), wy);
-        int e = -2, k = 0;
-        if (!(chx == 0.0 && chy == 0.0)) {
-            Loc L = walk(M, a, Xa.x, Xa.y, ds(Xa.x, chx), ds(Xa.y, chy), err);
-            if (L.e >= 0) {
-                int ee = L.vnode >= 0 ? fan_best(M, L.vnode) : L.e;
-                e = M.orig_elem[ee];
-            } else if (L.e == -1) {
-                e = -1;
-                k = L.kind;
-            }
-        }
-        elem[i * N + a] = e;
-        kind[i * N + a] = (int8_t)k;
+        elem[i * N + a] = e9[i];
+        kind[i * N + a] = k9[i];
     }
 }
 

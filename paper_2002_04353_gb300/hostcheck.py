@@ -1,0 +1,54 @@
+"""CPU run of the kernels' element walk (csrc/hostcheck.cu): the same
+location routine k_locate runs, compiled for the host.  Test tooling."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+from . import alelb, build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "csrc", "hostcheck.cu")
+OUT = os.path.join(HERE, "_build", "libalelb_hostcheck.so")
+_lib = None
+
+
+def build_lib(force=False):
+    deps = build.DEPS + [SRC, os.path.join(HERE, "csrc", "tables.h")]
+    if force or not os.path.exists(OUT) or any(os.path.getmtime(d) > os.path.getmtime(OUT) for d in deps):
+        os.makedirs(os.path.dirname(OUT), exist_ok=True)
+        tmp = OUT + f".{os.getpid()}.tmp"
+        subprocess.run(["nvcc", "-O2", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared",
+                        "-I", os.path.join(build.ROOT, "include"), "-o", tmp, SRC], check=True)
+        os.replace(tmp, OUT)
+    return OUT
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build_lib())
+        _lib.alelb_hostcheck_locate.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                                C.c_char_p, C.c_int]
+    return _lib
+
+
+def locate(mesh, motion, t, literal=False):
+    X = np.ascontiguousarray(mesh.X, dtype=np.float64).reshape(-1)
+    conn = np.ascontiguousarray(mesh.conn, dtype=np.int32).reshape(-1)
+    ek = np.ascontiguousarray(mesh.edge_kind, dtype=np.uint8).reshape(-1)
+    d = alelb.MeshDesc()
+    d.n_nodes, d.X, d.n_elems = mesh.n_nodes, X.ctypes.data, mesh.n_elems
+    d.conn, d.edge_kind = conn.ctypes.data, ek.ctypes.data
+    d.period[0], d.period[1] = float(mesh.period[0]), float(mesh.period[1])
+    d.motion_kind = int(motion.kind)
+    for k in range(16):
+        d.motion[k] = float(motion.params[k])
+    d.renumber = alelb.RENUMBER_MORTON
+    e = np.empty((9, mesh.n_nodes), dtype=np.int32)
+    k = np.empty((9, mesh.n_nodes), dtype=np.int8)
+    err = C.create_string_buffer(256)
+    st = lib().alelb_hostcheck_locate(C.byref(d), float(t), int(literal), e.ctypes.data, k.ctypes.data,
+                                       err, 256)
+    return st, e, k

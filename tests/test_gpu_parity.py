@@ -48,9 +48,9 @@ LOC_CASES = {
     "box_sine": lambda: (I.periodic_box(16, 32.0, 0.2, seed=1), I.Motion.make(I.MOTION_SINE, 1.6, 32.0, 100.0, 0.0)),
     "box_paper_map": lambda: (I.periodic_box(12, 24.0, 0.2, seed=2), I.Motion.make(I.MOTION_SINE, 1.5, 24.0, 60.0, 1.0)),
     "lattice_static": lambda: (I.lattice_box(8), I.Motion.make(I.MOTION_NONE)),
-    "omesh_plunge": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.02)),
-    "omesh_pitch": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.3, 0.003, 50.0, 0.0, 20.0, 0.003)),
-    "omesh_blended": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_BLENDED_PITCH, 0.05, 0.3, 0.004, 50.0, 0.0, 400.0, 2000.0)),
+    "omesh_plunge": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.002)),
+    "omesh_pitch": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.05, 0.003, 50.0, 0.0, 20.0, 0.003)),
+    "omesh_blended": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_BLENDED_PITCH, 0.05, 0.05, 0.002, 50.0, 0.0, 400.0, 2000.0)),
 }
 
 
@@ -116,7 +116,7 @@ def test_fp64_steps_lattice_reduction_mesh():
 @pytest.mark.parametrize("motion_name", ["omesh_plunge", "omesh_pitch", "omesh_blended"])
 def test_fp64_steps_airfoil_walls_farfield(motion_name):
     mesh, motion = LOC_CASES[motion_name]()
-    flow = I.flow_params(0.2, T_inf=0.3, Re=1e3, chord=200.0)
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
     o, m, s = _pair(mesh, motion, flow)
     for k in range(2):
         o.step(3)
@@ -129,7 +129,7 @@ def test_fp64_steps_airfoil_walls_farfield(motion_name):
 
 def test_fp64_bc_equilibrium_variant():
     mesh, motion = LOC_CASES["omesh_plunge"]()
-    flow = I.flow_params(0.2, T_inf=0.3, Re=1e3, chord=200.0)
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
     flow.flags = O.FLAG_BC_EQUILIBRIUM
     o, m, s = _pair(mesh, motion, flow)
     o.step(4)
@@ -215,7 +215,7 @@ def test_mixed_box_matches_fp64_oracle():
 
 def test_mixed_airfoil_matches_fp64_oracle():
     mesh, motion = LOC_CASES["omesh_plunge"]()
-    flow = I.flow_params(0.2, T_inf=0.3, Re=1e3, chord=200.0)
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
     o, m, s = _pair(mesh, motion, flow, prec=alelb.PREC_FP32_DEV)
     o.step(6)
     s.lb_step(6)

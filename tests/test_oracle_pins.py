@@ -539,9 +539,10 @@ def test_fluid_at_rest_with_walls_stays_at_rest():
 
 
 def test_missing_population_classification_matches_brute_force():
-    """Reading R6: a population is missing iff its departure point lies in no
-    element or the node->departure segment properly crosses a boundary edge;
-    checked with exact rationals on a sample of a small O-mesh."""
+    """Reading R6: a population is missing iff some point of the segment from
+    the node to its departure point lies outside the closed mesh; checked
+    with exact rationals (split the segment at every meeting with a boundary
+    edge, test one interior point of each piece and the departure point)."""
     mesh = I.naca_omesh(16, 4, chord=10.0, R=30.0, first=0.6)
     mot = I.Motion.make(I.MOTION_PITCH, 0.2, 0.3, 0.05, 2.5, 0.0)
     o = O.Oracle(mesh, mot, _flow())
@@ -551,31 +552,64 @@ def test_missing_population_classification_matches_brute_force():
     fr = _elem_frames(mesh)
     bnd = [(fr[e, k], fr[e, (k + 1) % 3], mesh.edge_kind[e, k])
            for e in range(mesh.n_elems) for k in range(3) if mesh.edge_kind[e, k]]
+    F = Fraction
 
-    def proper(a, p, u, w):
-        return (_orient_frac(a, p, u) * _orient_frac(a, p, w) < 0 and
-                _orient_frac(u, w, a) * _orient_frac(u, w, p) < 0)
+    def inside(q):
+        for e in range(mesh.n_elems):
+            v = [(F(fr[e, k, 0]), F(fr[e, k, 1])) for k in range(3)]
+            if all((v[k][0] - q[0]) * (v[(k + 1) % 3][1] - q[1]) - (v[k][1] - q[1]) * (v[(k + 1) % 3][0] - q[0]) >= 0
+                   for k in range(3)):
+                return True
+        return False
+
+    def meets(a, p, u, w):
+        """parameters along a->p where the closed segments meet (exact)"""
+        ax, ay, px_, py_ = (F(v) for v in (*a, *p))
+        ux, uy, wx, wy = (F(v) for v in (*u, *w))
+        dx, dy = px_ - ax, py_ - ay
+        ex, ey = wx - ux, wy - uy
+        den = dx * ey - dy * ex
+        if den == 0:
+            if (ux - ax) * dy - (uy - ay) * dx != 0:
+                return []
+            L2 = dx * dx + dy * dy
+            ts = [((ux - ax) * dx + (uy - ay) * dy) / L2, ((wx - ax) * dx + (wy - ay) * dy) / L2]
+            lo, hi = max(min(ts), F(0)), min(max(ts), F(1))
+            return [lo, hi] if lo <= hi else []
+        t_ = ((ux - ax) * ey - (uy - ay) * ex) / den
+        s_ = ((ux - ax) * dy - (uy - ay) * dx) / den
+        return [t_] if 0 <= t_ <= 1 and 0 <= s_ <= 1 else []
 
     rng = np.random.default_rng(0)
     wall_nodes = np.unique(np.concatenate([mesh.conn[e, [k, 3 + k, (k + 1) % 3]]
                                            for e in range(mesh.n_elems) for k in range(3)
                                            if mesh.edge_kind[e, k]]))
-    sample = list(wall_nodes) + list(rng.choice(mesh.n_nodes, 40, replace=False))
+    sample = list(wall_nodes) + list(rng.choice(mesh.n_nodes, 30, replace=False))
     n_missing = 0
     for a in sample:
         for i in range(9):
             p = np.array([px[i, a], py[i, a]])
             Xa = mesh.X[a]
-            if np.array_equal(p, Xa):
-                assert elem[i, a] == -2
+            if np.array_equal(p, Xa) and (CX[i], CY[i]) == (0, 0) and elem[i, a] == -2:
                 continue
-            e = _brute_locate(mesh, fr, p)
-            crossed = [k for (u, w, k) in bnd if proper(Xa, p, u, w)]
-            if e < 0 or crossed:
+            ts = {F(0), F(1)}
+            kinds = []
+            for (u, w, k) in bnd:
+                m_ = meets(Xa, p, u, w)
+                ts.update(m_)
+                if m_:
+                    kinds.append((min(m_), k))
+            ts = sorted(ts)
+            P0 = (F(Xa[0]), F(Xa[1]))
+            D = (F(p[0]) - P0[0], F(p[1]) - P0[1])
+            pts = [(P0[0] + D[0], P0[1] + D[1])] + [
+                (P0[0] + (t0 + t1) / 2 * D[0], P0[1] + (t0 + t1) / 2 * D[1])
+                for t0, t1 in zip(ts[:-1], ts[1:]) if t1 > t0]
+            missing = not all(inside(q) for q in pts)
+            if missing:
                 n_missing += 1
-                assert elem[i, a] == -1
-                if crossed:
-                    assert kind[i, a] == crossed[0]
+                assert elem[i, a] == -1, (a, i)
+                assert kind[i, a] == min(kinds)[1]
             else:
-                assert elem[i, a] == e
+                assert elem[i, a] == _brute_locate(mesh, fr, p), (a, i)
     assert n_missing > 20

@@ -1,0 +1,48 @@
+"""The kernels' element walk, compiled for the host (csrc/hostcheck.cu runs
+the same per-node routine as the location kernel), against the oracle's
+exhaustive point search: element choices must agree bit for bit.  Runs on
+the CPU; the GPU parity tests repeat the comparison with the device build."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04353_gb300 import hostcheck as H
+from paper_2002_04353_gb300 import inputs as I
+
+CASES = {
+    "box_config_map": (lambda: I.uniform_flow_case().mesh,
+                       lambda: I.uniform_flow_case().motion, [1, 25, 50, 99, 175]),
+    "box_paper_map": (lambda: I.periodic_box(20, 40.0, 0.2, seed=2),
+                      lambda: I.Motion.make(I.MOTION_SINE, 2.5, 40.0, 60.0, 1.0), [1, 15, 30]),
+    "lattice": (lambda: I.lattice_box(12), lambda: I.Motion.make(I.MOTION_NONE), [1]),
+    "plunge": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0),
+               lambda: I.Motion.make(I.MOTION_PLUNGE, 100.0, 2.6e-4), [1, 3000, 6000]),
+    "pitch_plunge": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0),
+                     lambda: I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.0, -0.05, 1e-4, 250.0, 0.0, 100.0, 1e-4),
+                     [1, 5000, 12000]),
+    "blended": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0),
+                lambda: I.Motion.make(I.MOTION_BLENDED_PITCH, -0.002, -0.0436, 7.8e-5, 250.0, 0.0, 2000.0, 10000.0),
+                [1, 10000, 20000]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_host_walk_matches_oracle(name):
+    mk_mesh, mk_mot, times = CASES[name]
+    mesh, mot = mk_mesh(), mk_mot()
+    o = O.Oracle(mesh, mot, I.Flow())
+    for t in times:
+        st, e, k = H.locate(mesh, mot, float(t))
+        assert st == 0
+        eo, ko = o.locate(float(t))
+        assert np.array_equal(e, eo), f"{name} t={t}: {np.sum(e != eo)} differ"
+        assert np.array_equal(k, ko)
+
+
+def test_host_walk_literal_form():
+    mesh = I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0)
+    mot = I.Motion.make(I.MOTION_PITCH, 0.05, 0.05, 0.003, 50.0, 0.0)
+    o = O.Oracle(mesh, mot, I.Flow(flags=O.FLAG_LITERAL_VG))
+    st, e, k = H.locate(mesh, mot, 11.0, literal=True)
+    eo, ko = o.locate(11.0)
+    assert st == 0 and np.array_equal(e, eo) and np.array_equal(k, ko)
