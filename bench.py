@@ -1,0 +1,337 @@
+"""Throughput of the ALE compressible lattice Boltzmann step on one GB300.
+
+Workload: NACA 0012 plunging, h = 0.1c sin(omega t), k = 1, Mach 0.2,
+Re 1e4, O-mesh of straight-sided P2 triangles (320 x 118 vertex rings,
+150,400 nodes), radius 20c, first cell layer 1e-3 c (c = 1000 lattice
+units), free-stream start.  One step = propagation (departure points,
+element walk, P2 interpolation, wall/far-field missing populations),
+moments, two FE-derivative passes and the collision, for every node.
+
+Metric: million node-updates per second.  `value` is the FP32-deviation
+form (FP32 populations and arithmetic, FP64 map, departure points and
+element location); the plain FP64 form is reported beside it.  The working
+set is smaller than L2, so L2 is flushed (a 512 MiB write) before every
+timed step and only the step itself is timed, with CUDA events on the
+solver's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the sweep
+workloads shard cases across GPUs with no exchange), so scaling is weak.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2002_04353_gb300 import inputs as I  # noqa: E402
+
+METRIC = "M node-updates/s on 1 GB300 (mixed/batched vs FP64 plain) + % HBM roofline"
+UNIT = "M node-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+WORKLOADS = {
+    # NACA 0012 plunging, Mach 0.2, Re 1e4, 150,400 P2 nodes (the headline case)
+    "plunge150k": lambda: I.plunge_case(ni=320, nj=118),
+    # the same flow on a 640 x 235 O-mesh, 600,320 P2 nodes (larger than L2;
+    # used for counter captures)
+    "plunge600k": lambda: I.plunge_case(ni=640, nj=235),
+    # NACA 0012 pitching about c/4 on a blended deforming mesh, Mach 0.75,
+    # 600,320 P2 nodes
+    "pitch600k": lambda: I.pitch_case(ni=640, nj=235),
+}
+
+
+def workload(name="plunge150k"):
+    return WORKLOADS[name]()
+
+
+def algorithmic_bytes_stream(n_nodes, n_elems, pop_bytes):
+    """Bytes the propagation kernel must move per launch: read the 18
+    post-collision populations of every node once, write 18 streamed
+    populations and Q'_x, Q'_y, mu/(rho T); read node coordinates (16 B),
+    the node fans (3 entries of 8 B per node plus the 4 B offset) and each
+    element's walk record once (frame 48 B, neighbours 12 B, edge info 4 B,
+    rank 4 B, connectivity 24 B)."""
+    per_node = 18 * pop_bytes * 2 + 3 * pop_bytes + 16 + 3 * 8 + 4
+    per_elem = 48 + 12 + 4 + 4 + 24
+    return n_nodes * per_node + n_elems * per_elem
+
+
+def algorithmic_bytes_step(n_nodes, n_elems, pop_bytes):
+    """Bytes one whole step must move: the propagation kernel's, plus the
+    derivative pass (read Q'_x, Q'_y, mu/(rho T), write D_x, D_y) and the
+    collision (read D, the 18 streamed populations; write 18 populations
+    and rho, u, T), plus the owner-element records of both passes."""
+    s = algorithmic_bytes_stream(n_nodes, n_elems, pop_bytes)
+    s += n_nodes * (3 * pop_bytes + 2 * pop_bytes + 8)
+    s += n_nodes * (2 * pop_bytes + 36 * pop_bytes + 4 * pop_bytes + 8)
+    return s
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(case, steps):
+    """The FP64 oracle as it stands, single-threaded on a host core, on the
+    same mesh: node-updates/s over `steps` steps from the free-stream start."""
+    import oracle as O
+    o = O.Oracle(case.mesh, case.motion, case.flow)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return case.mesh.n_nodes * steps / dt / 1e6, dt
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    case = workload(args.workload)
+    import oracle as O
+    o = O.Oracle(case.mesh, case.motion, case.flow)
+    o.step(max(0, args.warmup))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = case.mesh.n_nodes * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": case.name, "nodes": case.mesh.n_nodes, "elements": case.mesh.n_elems,
+                   "mach": 0.2, "re": 1e4, "chord": case.mesh.meta["chord"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of the full {case.mesh.n_nodes}-node mesh after "
+                                   f"{args.warmup} warm-up steps, plain FP64 C oracle, one host core"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2002_04353_gb300 import alelb
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = workload(args.workload)
+    mesh = alelb.Mesh(case.mesh, case.motion)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peak, peak_src = measured_peaks()
+
+    def timed(prec, steps, warmup, profile):
+        s = alelb.Solver(mesh, case.flow, prec, stream=stream.cuda_stream)
+        s.lb_step(warmup)
+        s.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            s.profile(True)
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                s.lb_step(1)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        kt = s.kernel_times() if profile else {}
+        s.profile(False)
+        info = s.info()
+        s.close()
+        return ms, kt, info
+
+    W, K = max(3, args.warmup), args.steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms32, kt32, info32 = timed(alelb.PREC_FP32_DEV, K, W, True)
+    clocks = sampler.stop()
+    ms64, kt64, info64 = timed(alelb.PREC_FP64, max(2, K // 4), W, True)
+    if world > 1:
+        t = torch.tensor([ms32, ms64], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms32, ms64 = float(t[0]), float(t[1])
+    N, E = case.mesh.n_nodes, case.mesh.n_elems
+    value = world * N * K / (ms32 * 1e-3) / 1e6
+    value64 = world * N * max(2, K // 4) / (ms64 * 1e-3) / 1e6
+
+    # dominant kernel roofline (FP32-deviation form)
+    top = max(kt32, key=lambda k: kt32[k][0])
+    top_ms, top_n = kt32[top]
+    if top == "k_stream":
+        alg = algorithmic_bytes_stream(N, E, 4)
+    else:
+        alg = algorithmic_bytes_step(N, E, 4) - algorithmic_bytes_stream(N, E, 4)
+    achieved = alg / (top_ms / top_n * 1e-3) / 1e9
+    step_bytes = algorithmic_bytes_step(N, E, 4)
+
+    # end to end through the C-ABI with host buffers: host-resident state,
+    # every step uploads the populations from pinned host memory, advances
+    # one step and reads the new populations back
+    e2e = None
+    if rank == 0 or world > 1:
+        s = alelb.Solver(mesh, case.flow, alelb.PREC_FP32_DEV, stream=stream.cuda_stream)
+        f = torch.empty((9, N), dtype=torch.float64).pin_memory().numpy()
+        g = torch.empty((9, N), dtype=torch.float64).pin_memory().numpy()
+        s.get_pops(f, g)
+        Ke = max(3, K // 4)
+        t0 = time.perf_counter()
+        for k in range(Ke):
+            s.set_pops(f, g, t=float(k))
+            s.lb_step(1)
+            s.get_pops(f, g)
+        dt = time.perf_counter() - t0
+        s.close()
+        e2e = {"value": world * N * Ke / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 18 * N * 8, "d2h_bytes_per_step": 18 * N * 8,
+               "note": "host-resident state: set_pops, lb_step(1), get_pops per step (FP64 host arrays)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt = cpu_baseline(case, args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_steps} steps of the full {N}-node mesh from the free-stream start, "
+                         f"plain FP64 C oracle, one host core ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "precision": "FP32 populations (deviations) and arithmetic; FP64 map, "
+                                         "departure points and element location",
+            "data": "synthetic",
+            "config": {"workload": case.name, "nodes": N, "elements": E,
+                       "mach": round(math.hypot(*case.flow.u_inf) / math.sqrt(1.4 * case.flow.T_inf), 4),
+                       "re": 1e4, "chord": case.mesh.meta["chord"], "motion": args.workload,
+                       "l2": "flushed (512 MiB write) before every timed step; only the step is timed",
+                       "parallelism": f"replicas x{world}"},
+            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / max(2, K // 4)},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": None, "algorithmic_bytes_per_launch": alg,
+                         "launch_ms": top_ms / top_n},
+            "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
+                              "achieved_gbs": step_bytes / (ms32 / K * 1e-3) / 1e9},
+            "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt32.items()},
+            "kernels_fp64": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt64.items()},
+            "gpu_launches": 3 * K,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plunge150k", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -300,6 +300,7 @@ struct alelb_solver {
     double consts[4 * NQ] = {0};
     double *d_consts = nullptr;
     double *d_scratch = nullptr; // 22 N doubles: import/export staging
+    double *h_pinned = nullptr;  // 22 N doubles of page-locked host staging
     int *d_err = nullptr;
     double *d_out = nullptr;
     DevBuf buf;
@@ -445,6 +446,7 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     else put_state(s->buf, s->sf, N, st);
     s->d_consts = s->buf.alloc<double>(4 * NQ, st);
     s->d_scratch = s->buf.alloc<double>((size_t)22 * N, st);
+    if (st == cudaSuccess) st = cudaHostAlloc((void **)&s->h_pinned, (size_t)22 * N * sizeof(double), 0);
     s->d_err = s->buf.alloc<int>(1, st);
     s->d_out = s->buf.alloc<double>(8, st);
     if (st != cudaSuccess) return cuda_fail(s, st);
@@ -479,6 +481,7 @@ extern "C" void alelb_solver_destroy(alelb_solver *s)
     flush_prof(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     s->buf.release();
+    if (s->h_pinned) cudaFreeHost(s->h_pinned);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s; // never touches the mesh: it may already be gone
 
@@ -521,8 +524,7 @@ extern "C" alelb_status alelb_time(alelb_solver *s, double *t, int64_t *step)
 }
 
 namespace {
-alelb_status export_state(alelb_solver *s, bool pops, std::vector<double> &full,
-                          std::vector<double> &fields)
+alelb_status export_state(alelb_solver *s, bool pops, const double **full, const double **fields)
 {
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
@@ -533,15 +535,15 @@ alelb_status export_state(alelb_solver *s, bool pops, std::vector<double> &full,
     else
         k_export<float><<<(N + 255) / 256, 256, 0, s->stream>>>(s->sf, N, s->d_consts, dfull, dfields);
     cudaError_t st = cudaGetLastError();
-    fields.resize((size_t)4 * N);
-    if (pops) full.resize((size_t)18 * N);
     if (st == cudaSuccess && pops)
-        st = cudaMemcpyAsync(full.data(), dfull, (size_t)18 * N * sizeof(double),
+        st = cudaMemcpyAsync(s->h_pinned, dfull, (size_t)18 * N * sizeof(double),
                              cudaMemcpyDeviceToHost, s->stream);
     if (st == cudaSuccess)
-        st = cudaMemcpyAsync(fields.data(), dfields, (size_t)4 * N * sizeof(double),
+        st = cudaMemcpyAsync(s->h_pinned + (size_t)18 * N, dfields, (size_t)4 * N * sizeof(double),
                              cudaMemcpyDeviceToHost, s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
+    *full = s->h_pinned;
+    *fields = s->h_pinned + (size_t)18 * N;
     return alelb_sync(s);
 }
 } // namespace
@@ -549,30 +551,35 @@ alelb_status export_state(alelb_solver *s, bool pops, std::vector<double> &full,
 extern "C" alelb_status alelb_moments(alelb_solver *s, double *rho, double *ux, double *uy, double *T)
 {
     if (!s) return ALELB_ERR_ARG;
-    std::vector<double> full, fields;
-    alelb_status r = export_state(s, false, full, fields);
+    const double *full, *fields;
+    alelb_status r = export_state(s, false, &full, &fields);
     if (r != ALELB_OK) return r;
     const int N = s->mesh->T.N;
+    const int *n2o = s->mesh->T.node_new2old.data();
     double *outs[4] = {rho, ux, uy, T};
     for (int c = 0; c < 4; ++c)
         if (outs[c])
-            for (int a = 0; a < N; ++a) outs[c][s->mesh->T.node_new2old[a]] = fields[(size_t)c * N + a];
+            for (int a = 0; a < N; ++a) outs[c][n2o[a]] = fields[(size_t)c * N + a];
     return ALELB_OK;
 }
 
 extern "C" alelb_status alelb_get_pops(alelb_solver *s, double *f, double *g)
 {
     if (!s) return ALELB_ERR_ARG;
-    std::vector<double> full, fields;
-    alelb_status r = export_state(s, true, full, fields);
+    const double *full, *fields;
+    alelb_status r = export_state(s, true, &full, &fields);
     if (r != ALELB_OK) return r;
     const int N = s->mesh->T.N;
-    for (int i = 0; i < NQ; ++i)
+    const int *n2o = s->mesh->T.node_new2old.data();
+    for (int i = 0; i < NQ; ++i) {
+        const double *fi = full + (size_t)i * N, *gi = full + (size_t)(NQ + i) * N;
+        double *fo = f ? f + (size_t)i * N : nullptr, *go = g ? g + (size_t)i * N : nullptr;
         for (int a = 0; a < N; ++a) {
-            int o = s->mesh->T.node_new2old[a];
-            if (f) f[(size_t)i * N + o] = full[(size_t)i * N + a];
-            if (g) g[(size_t)i * N + o] = full[(size_t)(NQ + i) * N + a];
+            int o = n2o[a];
+            if (fo) fo[o] = fi[a];
+            if (go) go[o] = gi[a];
         }
+    }
     return ALELB_OK;
 }
 
@@ -582,25 +589,33 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
 {
     if (!s || !f || !g) return ALELB_ERR_ARG;
     const int N = s->mesh->T.N;
-    std::vector<double> full((size_t)18 * N), fields((size_t)4 * N, 0.0);
+    const int *n2o = s->mesh->T.node_new2old.data();
+    // wait for earlier transfers out of the staging buffer
+    cudaError_t st = cudaStreamSynchronize(s->stream);
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    double *full = s->h_pinned, *fields = s->h_pinned + (size_t)18 * N;
     bool have = rho && ux && uy && T;
-    for (int a = 0; a < N; ++a) {
-        int o = s->mesh->T.node_new2old[a];
-        for (int i = 0; i < NQ; ++i) {
-            full[(size_t)i * N + a] = f[(size_t)i * N + o];
-            full[(size_t)(NQ + i) * N + a] = g[(size_t)i * N + o];
+    for (int i = 0; i < NQ; ++i) {
+        double *fo = full + (size_t)i * N, *go = full + (size_t)(NQ + i) * N;
+        const double *fi = f + (size_t)i * N, *gi = g + (size_t)i * N;
+        for (int a = 0; a < N; ++a) {
+            int o = n2o[a];
+            fo[a] = fi[o];
+            go[a] = gi[o];
         }
-        if (have) {
+    }
+    if (have)
+        for (int a = 0; a < N; ++a) {
+            int o = n2o[a];
             fields[a] = rho[o];
             fields[(size_t)N + a] = ux[o];
             fields[(size_t)2 * N + a] = uy[o];
             fields[(size_t)3 * N + a] = T[o];
         }
-    }
-    cudaError_t st = cudaMemcpyAsync(s->d_scratch, full.data(), full.size() * sizeof(double),
-                                     cudaMemcpyHostToDevice, s->stream);
-    if (st == cudaSuccess)
-        st = cudaMemcpyAsync(s->d_scratch + (size_t)18 * N, fields.data(), fields.size() * sizeof(double),
+    st = cudaMemcpyAsync(s->d_scratch, full, (size_t)18 * N * sizeof(double), cudaMemcpyHostToDevice,
+                         s->stream);
+    if (st == cudaSuccess && have)
+        st = cudaMemcpyAsync(s->d_scratch + (size_t)18 * N, fields, (size_t)4 * N * sizeof(double),
                              cudaMemcpyHostToDevice, s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
     if (s->prec == ALELB_PREC_FP64)

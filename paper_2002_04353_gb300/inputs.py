@@ -229,7 +229,8 @@ def naca_omesh(ni: int, nj: int, chord: float = 200.0, thickness: float = 0.12,
                R: float = 4000.0, first: float = 0.2, name="naca"):
     """O-mesh of P2 triangles around a NACA 00xx section (leading edge at the
     origin, chord along +x), outer far-field circle of radius R about
-    mid-chord.  ni points around the section (cosine-clustered, even), nj
+    mid-chord.  ni points around the section (even; spacing half
+    cosine-clustered, half uniform), nj
     vertex rings; the first ring sits `first` off the wall along the surface
     normal, ring spacing grows geometrically and blends into concentric
     circles away from the body."""
@@ -237,7 +238,9 @@ def naca_omesh(ni: int, nj: int, chord: float = 200.0, thickness: float = 0.12,
         raise ValueError("ni must be even and >= 16, nj >= 4")
     m = ni // 2
     beta = math.pi * np.arange(m + 1) / m
-    xc = 0.5 * (1.0 - np.cos(beta))
+    # half cosine-clustered, half uniform along the chord: refined at the
+    # leading and trailing edges without sub-lattice slivers there
+    xc = 0.5 * (0.5 * (1.0 - np.cos(beta))) + 0.5 * (beta / math.pi)
     yt = naca_half_thickness(xc, thickness)
     up = np.stack([xc, yt], 1)                      # LE -> TE over the top
     lo = np.stack([xc[m - 1:0:-1], -yt[m - 1:0:-1]], 1)  # TE -> LE underneath
