@@ -175,6 +175,28 @@ alelb_status alelb_kernel_times(alelb_solver *s, const char **names, double *ms,
    bytes_state_per_node, bytes_static_per_node, n_wall_nodes}. */
 alelb_status alelb_info(alelb_solver *s, double out[8]);
 
+/* One FP64 time step t -> t + 1 that allocates nothing (the paper has no
+   counterpart: this entry point exists for callers that cannot allocate
+   device memory once running -- an application whose device memory is
+   pre-reserved by its own allocator, or a loop that must not call
+   cudaMalloc/cudaFree, which can wait for the whole device).
+   The caller owns and passes the state, all device pointers on the current
+   device: post [9][n_nodes] f then [9][n_nodes] g (full FP64 post-collision
+   populations at t, overwritten with those at t + 1) and the latest-step
+   fields rho, ux, uy, T [n_nodes] each (read by the wall condition,
+   overwritten).  The mesh must have been created with ALELB_RENUMBER_NONE
+   (node order = caller order) and have at most 131072 nodes;
+   p->precision must be ALELB_PREC_FP64; the kernels run on p->stream
+   (NULL: the default stream).  The step's
+   scratch lives in a static device array of 23 * 131072 + 64 doubles
+   (about 24 MB) that every GPU loading the library holds until exit.  The
+   first call on a device looks up that array's device address (make that
+   first call before any stream capture).  Calls share the array, so calls
+   that overlap on the GPU race.  Synchronous; returns ALELB_ERR_ARG for a
+   larger mesh or other precision (message in alelb_mesh_last_error). */
+alelb_status alelb_lb_step_noalloc(alelb_mesh *mesh, const alelb_params *p, double t,
+                                   double *post, double *rho, double *ux, double *uy, double *T);
+
 const char *alelb_last_error(alelb_solver *s);
 const char *alelb_mesh_last_error(alelb_mesh *m);
 

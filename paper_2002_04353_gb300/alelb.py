@@ -32,7 +32,8 @@ NQ = 9
 EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_lb_init",
            "alelb_solver_destroy", "alelb_lb_step", "alelb_sync", "alelb_moments", "alelb_time",
            "alelb_get_pops", "alelb_set_pops", "alelb_forces", "alelb_locate", "alelb_profile",
-           "alelb_kernel_times", "alelb_info", "alelb_last_error", "alelb_mesh_last_error"]
+           "alelb_kernel_times", "alelb_info", "alelb_last_error", "alelb_mesh_last_error",
+           "alelb_lb_step_noalloc"]
 
 
 class AlelbError(RuntimeError):
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
     L.alelb_last_error.restype = C.c_char_p
     L.alelb_mesh_last_error.argtypes = [p]
     L.alelb_mesh_last_error.restype = C.c_char_p
+    L.alelb_lb_step_noalloc.argtypes = [p, C.POINTER(Params), d, p, p, p, p, p]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -155,6 +157,28 @@ class Mesh:
 
 def mesh_create(mesh, motion, renumber=RENUMBER_MORTON):
     return Mesh(mesh, motion, renumber)
+
+
+def params_of(flow, precision=PREC_FP64, flags=None, stream=None):
+    p = Params()
+    p.gamma, p.Pr, p.mu = flow.gamma, flow.Pr, flow.mu
+    p.rho_inf, p.T_inf = flow.rho_inf, flow.T_inf
+    p.u_inf[0], p.u_inf[1] = flow.u_inf
+    p.chord = flow.chord
+    p.precision = int(precision)
+    p.flags = int(flow.flags if flags is None else flags)
+    p.stream = stream
+    return p
+
+
+def lb_step_noalloc(mesh: "Mesh", flow, t, post_ptr, rho_ptr, ux_ptr, uy_ptr, T_ptr, stream=None):
+    """One FP64 step on caller-owned device buffers (raw device addresses),
+    allocating nothing; see alelb_lb_step_noalloc in include/alelb.h."""
+    L = load()
+    p = params_of(flow, PREC_FP64, stream=stream)
+    st = L.alelb_lb_step_noalloc(mesh.h, C.byref(p), float(t), post_ptr, rho_ptr, ux_ptr, uy_ptr, T_ptr)
+    if st != OK:
+        raise AlelbError(st, "lb_step_noalloc: " + L.alelb_mesh_last_error(mesh.h).decode())
 
 
 class Solver:

@@ -739,3 +739,127 @@ extern "C" alelb_status alelb_info(alelb_solver *s, double out[8])
 }
 
 extern "C" const char *alelb_last_error(alelb_solver *s) { return s ? s->err.c_str() : "null solver"; }
+
+// ============================================================================
+// One FP64 step that allocates nothing (alelb_lb_step_noalloc).
+//
+// For callers that cannot allocate device memory once they are running: a
+// host application whose device memory is entirely pre-reserved by its own
+// allocator, or a coupling loop that must not call cudaMalloc/cudaFree
+// (cudaFree waits for the whole device).  The caller passes the state; the
+// step's scratch -- the streamed populations, Q'_xxx, Q'_yyy, mu/(rho T),
+// D_x, D_y, the reference/far-field constants and the error word -- lives
+// in the file-scope array below, which every GPU that loads this library
+// holds until the process exits.  All calls share it: it keeps the last
+// call's contents, the error word is cleared at the start of each call, and
+// calls that overlap on the GPU race on it.
+// ============================================================================
+#define ALELB_NOALLOC_MAX_NODES 131072
+namespace {
+constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)23 * ALELB_NOALLOC_MAX_NODES + 64;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+double *g_noalloc_ptr[64] = {nullptr}; // device address of the array, per device
+}
+
+extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params *p, double t,
+                                              double *post, double *rho, double *ux, double *uy,
+                                              double *T)
+{
+    if (!m || !p || !post || !rho || !ux || !uy || !T) return ALELB_ERR_ARG;
+    if (p->precision != ALELB_PREC_FP64 || !(p->gamma > 1.0) || !(p->Pr > 0) || !(p->mu > 0) ||
+        !(p->rho_inf > 0) || !(p->T_inf > 0)) {
+        m->err = "lb_step_noalloc: needs FP64 precision and positive fluid parameters";
+        return ALELB_ERR_ARG;
+    }
+    const int N = m->T.N;
+    if (N > ALELB_NOALLOC_MAX_NODES) {
+        m->err = "lb_step_noalloc: the mesh has " + std::to_string(N) + " nodes; at most " +
+                 std::to_string(ALELB_NOALLOC_MAX_NODES) + " fit the static scratch";
+        return ALELB_ERR_ARG;
+    }
+    for (int a = 0; a < N; ++a)
+        if (m->T.node_new2old[a] != a) {
+            m->err = "lb_step_noalloc: the mesh must be created with ALELB_RENUMBER_NONE";
+            return ALELB_ERR_ARG;
+        }
+    int dev = 0;
+    cudaError_t st = cudaGetDevice(&dev);
+    if (st != cudaSuccess || dev < 0 || dev >= 64) {
+        m->err = "lb_step_noalloc: no usable current device";
+        return ALELB_ERR_CUDA;
+    }
+    // set-up, once per device: the host-side name of the array is not a
+    // device address; ask the runtime for it with this device current
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        st = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (st != cudaSuccess || !ptr) {
+            m->err = std::string("lb_step_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(st);
+            return ALELB_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = (double *)ptr;
+    }
+    double *base = g_noalloc_ptr[dev];
+    cudaStream_t stream = (cudaStream_t)p->stream;
+    StateDev<double> sd{};
+    sd.post = post;
+    sd.rho = rho;
+    sd.ux = ux;
+    sd.uy = uy;
+    sd.T = T;
+    sd.str = base;
+    sd.Qx = base + (size_t)18 * N;
+    sd.Qy = sd.Qx + N;
+    sd.mrt = sd.Qy + N;
+    sd.Dx = sd.mrt + N;
+    sd.Dy = sd.Dx + N;
+    double *consts = base + (size_t)23 * ALELB_NOALLOC_MAX_NODES;     // 36 doubles
+    int *err = (int *)(consts + 4 * NQ);                              // inside the last 64
+    KinParams<double> K{};
+    K.Cv = 1.0 / (p->gamma - 1.0);
+    k_kin_consts<<<1, 1, 0, stream>>>(K, p->rho_inf, p->u_inf[0], p->u_inf[1], p->T_inf, 0, consts);
+    double hc[4 * NQ];
+    st = cudaGetLastError();
+    if (st == cudaSuccess) st = cudaMemsetAsync(err, 0, sizeof(int), stream);
+    if (st == cudaSuccess) st = cudaMemcpyAsync(hc, consts, sizeof(hc), cudaMemcpyDeviceToHost, stream);
+    if (st == cudaSuccess) st = cudaStreamSynchronize(stream);
+    if (st != cudaSuccess) {
+        m->err = cudaGetErrorString(st);
+        return ALELB_ERR_CUDA;
+    }
+    K.Cp = K.Cv + 1.0;
+    K.mu = p->mu;
+    K.Pr = p->Pr;
+    K.rho_ref = 0.0;
+    K.E2_ref = 0.0;
+    K.T_ref = 0.0;
+    for (int i = 0; i < NQ; ++i) {
+        K.fref[i] = 0.0;
+        K.gref[i] = 0.0;
+        K.finf[i] = hc[2 * NQ + i];
+        K.ginf[i] = hc[3 * NQ + i];
+    }
+    K.flags = p->flags;
+    MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
+    k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);
+    if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
+        k_deriv1<double, double><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, sd);
+    k_collide<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);
+    int herr = 0;
+    st = cudaGetLastError();
+    if (st == cudaSuccess) st = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (st == cudaSuccess) st = cudaStreamSynchronize(stream);
+    if (st != cudaSuccess) {
+        m->err = cudaGetErrorString(st);
+        return ALELB_ERR_CUDA;
+    }
+    if (herr & ERR_LOCATE) {
+        m->err = "lb_step_noalloc: element walk exceeded its step limit";
+        return ALELB_ERR_LOCATE;
+    }
+    if (herr & ERR_NONFINITE) {
+        m->err = "lb_step_noalloc: non-finite or non-positive density or temperature";
+        return ALELB_ERR_NONFINITE;
+    }
+    return ALELB_OK;
+}
