@@ -77,6 +77,8 @@ template <class T> void put_state(DevBuf &b, StateDev<T> &s, int N, cudaError_t 
     s.mrt = b.alloc<T>(N, st);
     s.Dx = b.alloc<T>(N, st);
     s.Dy = b.alloc<T>(N, st);
+    s.cache = b.alloc<int>((size_t)9 * N, st);
+    if (st == cudaSuccess) st = cudaMemset(s.cache, 0xff, (size_t)9 * N * sizeof(int)); // -1: empty
 }
 
 
@@ -119,6 +121,8 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.probe_e = B.put(T.probe_e, st);
     D.probe_xi = B.put(T.probe_xi, st);
     D.orig_elem = B.put(T.orig, st);
+    D.ejf = B.put(T.ejf, st);
+    D.bdist = B.put(T.bdist, st);
     m->d_wedges = B.put(T.wedges, st);
     m->nw = (int)T.wedges.size();
     m->mst = T.host_map();
@@ -362,8 +366,10 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
             eb = get_event(s);
             cudaEventRecord(ea, s->stream);
         }
-        if (k == KT_STREAM)
-            k_stream<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err);
+        if (k == KT_STREAM && s->prec == ALELB_PREC_FP32_DEV)
+            k_stream<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err);
+        else if (k == KT_STREAM)
+            k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err);
         else if (k == KT_DERIV1)
             k_deriv1<S, A><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, st);
         else
@@ -841,7 +847,7 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     }
     K.flags = p->flags;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
-    k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);
+    k_stream<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
         k_deriv1<double, double><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, sd);
     k_collide<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);

@@ -293,6 +293,8 @@ struct MeshDev {
     const int *probe_e;    // [NW]
     const double2 *probe_xi; // [NW]
     const int *orig_elem;  // [E] original element id
+    const float4 *ejf;     // [2E] FP32 edge vectors (v1-v0, v2-v0) and inverse Jacobian rows
+    const float *bdist;    // [N] lower bound of the node's distance to the nearest boundary edge
 };
 
 struct Loc {
@@ -498,6 +500,33 @@ ALELB_HD inline void locate_node(const MeshDev &M, const MapStatic &MS, const Ma
         elem9[i] = e;
         kind9[i] = (int8_t)k;
     }
+}
+
+// Certified FP32 test that p lies strictly inside element e (frame shift
+// sx, sy).  Relative coordinates q = p - v0 are formed in FP64 and rounded
+// once; the three orientations e1 x q, (e1 - q) x (e2 - q), e2 x q ... are
+// evaluated in FP32 and accepted only when each clears the error bound
+// 2^-17 M^2 (M the largest |coordinate| involved), which covers the input
+// roundings and the FP32 operations.  A false return decides nothing: the
+// caller then runs the exact walk.  On success q holds the FP32 offset
+// from v0 for the interpolation weights.
+ALELB_HD __forceinline__ bool strictly_inside_f32(const MeshDev &M, int e, int sx, int sy,
+                                                  double px, double py, float &qx, float &qy)
+{
+    double2 v0 = M.ev[3 * e];
+    double x0 = sx ? da(v0.x, sx * M.Lx) : v0.x;
+    double y0 = sy ? da(v0.y, sy * M.Ly) : v0.y;
+    qx = (float)ds(px, x0);
+    qy = (float)ds(py, y0);
+    float4 ed = M.ejf[2 * e];
+    float e1x = ed.x, e1y = ed.y, e2x = ed.z, e2y = ed.w;
+    float m = fmaxf(fmaxf(fmaxf(fabsf(e1x), fabsf(e1y)), fmaxf(fabsf(e2x), fabsf(e2y))),
+                    fmaxf(fabsf(qx), fabsf(qy)));
+    float bound = 7.62939453125e-06f * m * m; // 2^-17 M^2
+    float o0 = e1x * qy - e1y * qx;                 // orient(v0, v1, p)
+    float o1 = (e1x - qx) * (e2y - qy) - (e1y - qy) * (e2x - qx); // orient(v1, v2, p)
+    float o2 = e2y * qx - e2x * qy;                 // orient(v2, v0, p)
+    return o0 > bound && o1 > bound && o2 > bound;
 }
 
 } // namespace alelb

@@ -36,3 +36,22 @@ extern "C" int alelb_hostcheck_locate(const alelb_mesh_desc *d, double t, int li
     }
     return e ? ALELB_ERR_LOCATE : ALELB_OK;
 }
+
+// The certified FP32 strict-containment filter of the fast propagation path,
+// on the host: out[k] = 1 when the filter accepts point k in element elem[k]
+// (internal numbering of the Morton-renumbered mesh; frame shift 0).
+extern "C" int alelb_hostcheck_inside(const alelb_mesh_desc *d, int n, const int32_t *elem_orig,
+                                      const double *px, const double *py, int8_t *out)
+{
+    HostTables T;
+    std::string err;
+    alelb_status st = build_tables(d, T, err);
+    if (st != ALELB_OK) return st;
+    MeshDev M = T.host_view();
+    for (int k = 0; k < n; ++k) {
+        float qx, qy;
+        int e = T.elem_old2new[elem_orig[k]];
+        out[k] = strictly_inside_f32(M, e, 0, 0, px[k], py[k], qx, qy) ? 1 : 0;
+    }
+    return ALELB_OK;
+}

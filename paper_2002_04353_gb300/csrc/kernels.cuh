@@ -24,6 +24,8 @@ template <class S> struct StateDev {
     S *rho, *ux, *uy, *T; // fields of the latest step
     S *Qx, *Qy, *mrt;     // Q'_xxx, Q'_yyy, mu/(rho T)
     S *Dx, *Dy;           // first-pass results
+    int *cache;           // [9 N] element of each population's previous departure point
+                          // (elem | (sx+1)<<28 | (sy+1)<<30), -1 when empty
 };
 
 // d N_s / d xi and d N_s / d eta of the P2 triangle at the six node
@@ -82,7 +84,13 @@ __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const
     KY = (-x_eta * sxi + x_xi * seta) / detJ;
 }
 
-template <class S, class A>
+// FAST (the FP32-deviation form): each population first tries the element
+// its departure point fell in at the previous step, accepted only when the
+// certified FP32 filter shows the point strictly inside it and the departure
+// segment is shorter than the node's distance to any boundary -- then that
+// element is the unique one the walk would return.  Otherwise (and always in
+// the plain form) the exact walk runs and refreshes the cache.
+template <class S, class A, bool FAST>
 __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
                                                 KinParams<A> K, StateDev<S> st, int *err)
 {
@@ -95,119 +103,146 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
     metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
     double wx, wy;
     mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
-    A fs[NQ], gs[NQ];
+    const float bdist = FAST ? M.bdist[a] : 0.0f;
     int miss = 0, far = 0;
+    // running moments of the streamed populations (deviations)
+    A sf = 0, jx = 0, jy = 0, sg = 0;
 #pragma unroll 1
     for (int i = 0; i < NQ; ++i) {
         double chx, chy, px, py;
         departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx,
                   chy, px, py);
-        int self = (chx == 0.0 && chy == 0.0);
-        Loc L;
-        if (!self) {
-            L = walk(M, a, Xa.x, Xa.y, px, py, err);
-            if (L.e == -2) self = 1;
-            if (L.e >= 0 && L.vnode < 0) {
-                double xi, eta;
-                local_coords(M, L.e, L.sx, L.sy, px, py, xi, eta);
+        A fi = 0, gi = 0;
+        int src = -1; // node whose value is taken as is
+        if (chx == 0.0 && chy == 0.0) {
+            src = a;
+        } else {
+            int e = -1, ex = 0, ey = 0;
+            float qx = 0.f, qy = 0.f;
+            bool fast = false;
+            if (FAST) {
+                const int c = st.cache[i * N + a];
+                if (c >= 0 && sqrtf((float)(chx * chx + chy * chy)) * 1.000001f < bdist) {
+                    e = c & 0x0fffffff;
+                    ex = ((c >> 28) & 3) - 1;
+                    ey = ((c >> 30) & 3) - 1;
+                    fast = strictly_inside_f32(M, e, ex, ey, px, py, qx, qy);
+                }
+            }
+            if (!fast) {
+                Loc L = walk(M, a, Xa.x, Xa.y, px, py, err);
+                if (L.e == -2) {
+                    src = a;
+                } else if (L.e == -1) {
+                    miss |= 1 << i;
+                    if (L.kind == 2) far |= 1 << i;
+                    continue;
+                } else if (L.vnode >= 0) {
+                    src = L.vnode;
+                } else {
+                    e = L.e;
+                    ex = L.sx;
+                    ey = L.sy;
+                    if (FAST) st.cache[i * N + a] = e | ((ex + 1) << 28) | ((ey + 1) << 30);
+                }
+            }
+            if (src < 0) {
                 A Nw[6];
-                shape6<A>((A)xi, (A)eta, Nw);
-                A sf = 0, sg = 0;
+                if (FAST) {
+                    if (!fast) {
+                        double2 v0 = M.ev[3 * e];
+                        qx = (float)(px - (ex ? v0.x + ex * M.Lx : v0.x));
+                        qy = (float)(py - (ey ? v0.y + ey * M.Ly : v0.y));
+                    }
+                    float4 J = M.ejf[2 * e + 1];
+                    shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
+                } else {
+                    double xi, eta;
+                    local_coords(M, e, ex, ey, px, py, xi, eta);
+                    shape6<A>((A)xi, (A)eta, Nw);
+                }
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    int b = M.conn[6 * L.e + k];
-                    sf += Nw[k] * (A)st.post[i * N + b];
-                    sg += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                    const int b = M.conn[6 * e + k];
+                    fi += Nw[k] * (A)st.post[i * N + b];
+                    gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
                 }
-                fs[i] = sf;
-                gs[i] = sg;
-            } else if (L.e >= 0) {
-                fs[i] = (A)st.post[i * N + L.vnode];
-                gs[i] = (A)st.post[(NQ + i) * N + L.vnode];
-            } else if (L.e == -1) {
-                miss |= 1 << i;
-                if (L.kind == 2) far |= 1 << i;
-                fs[i] = 0;
-                gs[i] = 0;
             }
         }
-        if (self) {
-            fs[i] = (A)st.post[i * N + a];
-            gs[i] = (A)st.post[(NQ + i) * N + a];
+        if (src >= 0) {
+            fi = (A)st.post[i * N + src];
+            gi = (A)st.post[(NQ + i) * N + src];
         }
+        st.str[i * N + a] = (S)fi;
+        st.str[(NQ + i) * N + a] = (S)gi;
+        sf += fi;
+        jx += (A)c_cx[i] * fi;
+        jy += (A)c_cy[i] * fi;
+        sg += gi;
     }
-    if (miss & ~far) {
-        // targets (Sec. IV.A): wall node -> u = V_G, rho and T at the probe
-        // point B; other nodes -> their previous-step fields
-        A rt, uxt, uyt, Tt;
-        const int wi = M.wall_idx[a];
-        if (wi >= 0) {
-            const int pe = M.probe_e[wi];
-            const double2 pxi = M.probe_xi[wi];
-            A Nw[6];
-            shape6<A>((A)pxi.x, (A)pxi.y, Nw);
-            A r = 0, t = 0;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                int b = M.conn[6 * pe + k];
-                r += Nw[k] * (A)st.rho[b];
-                t += Nw[k] * (A)st.T[b];
-            }
-            rt = r;
-            Tt = t;
-            uxt = (A)Vx;
-            uyt = (A)Vy;
-        } else {
-            rt = (A)st.rho[a];
-            uxt = (A)st.ux[a];
-            uyt = (A)st.uy[a];
-            Tt = (A)st.T[a];
-        }
-        A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
-        if (!(K.flags & FLAG_BC_EQ)) {
-            double KX, KY;
-            owner_grad_linear(M, a, st.ux, KX, KY);
-            du[0] = (A)(a11 * KX + a21 * KY);
-            du[1] = (A)(a12 * KX + a22 * KY);
-            owner_grad_linear(M, a, st.uy, KX, KY);
-            du[2] = (A)(a11 * KX + a21 * KY);
-            du[3] = (A)(a12 * KX + a22 * KY);
-            owner_grad_linear(M, a, st.T, KX, KY);
-            dT[0] = (A)(a11 * KX + a21 * KY);
-            dT[1] = (A)(a12 * KX + a22 * KY);
-        }
+    if (miss) {
         A fm[NQ], gm[NQ];
-        grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+        if (miss & ~far) {
+            // targets (Sec. IV.A): wall node -> u = V_G, rho and T at the
+            // probe point B; other nodes -> their previous-step fields
+            A rt, uxt, uyt, Tt;
+            const int wi = M.wall_idx[a];
+            if (wi >= 0) {
+                const int pe = M.probe_e[wi];
+                const double2 pxi = M.probe_xi[wi];
+                A Nw[6];
+                shape6<A>((A)pxi.x, (A)pxi.y, Nw);
+                A r = 0, t = 0;
 #pragma unroll
-        for (int i = 0; i < NQ; ++i)
-            if ((miss & ~far) >> i & 1) {
-                fs[i] = fm[i];
-                gs[i] = gm[i];
+                for (int k = 0; k < 6; ++k) {
+                    int b = M.conn[6 * pe + k];
+                    r += Nw[k] * (A)st.rho[b];
+                    t += Nw[k] * (A)st.T[b];
+                }
+                rt = r;
+                Tt = t;
+                uxt = (A)Vx;
+                uyt = (A)Vy;
+            } else {
+                rt = (A)st.rho[a];
+                uxt = (A)st.ux[a];
+                uyt = (A)st.uy[a];
+                Tt = (A)st.T[a];
             }
-    }
-    if (far) {
+            A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
+            if (!(K.flags & FLAG_BC_EQ)) {
+                double KX, KY;
+                owner_grad_linear(M, a, st.ux, KX, KY);
+                du[0] = (A)(a11 * KX + a21 * KY);
+                du[1] = (A)(a12 * KX + a22 * KY);
+                owner_grad_linear(M, a, st.uy, KX, KY);
+                du[2] = (A)(a11 * KX + a21 * KY);
+                du[3] = (A)(a12 * KX + a22 * KY);
+                owner_grad_linear(M, a, st.T, KX, KY);
+                dT[0] = (A)(a11 * KX + a21 * KY);
+                dT[1] = (A)(a12 * KX + a22 * KY);
+            }
+            grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+        }
 #pragma unroll
-        for (int i = 0; i < NQ; ++i)
-            if (far >> i & 1) {
-                fs[i] = K.finf[i];
-                gs[i] = K.ginf[i];
-            }
+        for (int i = 0; i < NQ; ++i) {
+            if (!(miss >> i & 1)) continue;
+            A fi = (far >> i & 1) ? K.finf[i] : fm[i];
+            A gi = (far >> i & 1) ? K.ginf[i] : gm[i];
+            st.str[i * N + a] = (S)fi;
+            st.str[(NQ + i) * N + a] = (S)gi;
+            sf += fi;
+            jx += (A)c_cx[i] * fi;
+            jy += (A)c_cy[i] * fi;
+            sg += gi;
+        }
     }
     // moments (Sec. IV): rho, u, E, T from the streamed populations
-    A sf = fs[0] + fs[1] + fs[2] + fs[3] + fs[4] + fs[5] + fs[6] + fs[7] + fs[8];
-    A jx = (fs[1] - fs[3]) + (fs[5] - fs[6]) + (fs[8] - fs[7]);
-    A jy = (fs[2] - fs[4]) + (fs[5] - fs[8]) + (fs[6] - fs[7]);
-    A sg = gs[0] + gs[1] + gs[2] + gs[3] + gs[4] + gs[5] + gs[6] + gs[7] + gs[8];
     A rho = K.rho_ref + sf;
     A ux = jx / rho, uy = jy / rho;
     A E = (K.E2_ref + sg) / (A(2) * rho);
     A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-        st.str[i * N + a] = (S)fs[i];
-        st.str[(NQ + i) * N + a] = (S)gs[i];
-    }
     A k3 = A(1) - A(3) * T;
     st.Qx[a] = (S)(rho * ux * k3 - rho * ux * ux * ux);
     st.Qy[a] = (S)(rho * uy * k3 - rho * uy * uy * uy);

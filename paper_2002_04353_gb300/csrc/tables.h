@@ -60,6 +60,8 @@ struct HostTables {
     std::vector<int2> fan, owner, wedges;
     std::vector<uint8_t> bkind;
     std::vector<double> ms;
+    std::vector<float4> ejf;
+    std::vector<float> bdist;
     int n_wall_nodes = 0;
 
     // a MeshDev whose pointers address these host vectors (host-side walk)
@@ -84,6 +86,8 @@ struct HostTables {
         D.probe_e = probe_e.data();
         D.probe_xi = probe_xi.data();
         D.orig_elem = orig.data();
+        D.ejf = ejf.data();
+        D.bdist = bdist.data();
         return D;
     }
     MapStatic host_map() const
@@ -449,6 +453,57 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
     }
 
     T.n_wall_nodes = (int)T.probe_e.size();
+    // FP32 edge vectors and inverse Jacobians (interpolation weights and the
+    // certified FP32 containment filter)
+    T.ejf.assign((size_t)2 * E, make_float4(0, 0, 0, 0));
+    for (int en = 0; en < E; ++en) {
+        double2 v0 = ev[3 * en], v1 = ev[3 * en + 1], v2 = ev[3 * en + 2];
+        double e1x = v1.x - v0.x, e1y = v1.y - v0.y, e2x = v2.x - v0.x, e2y = v2.y - v0.y;
+        double det = e1x * e2y - e2x * e1y;
+        T.ejf[2 * en] = make_float4((float)e1x, (float)e1y, (float)e2x, (float)e2y);
+        T.ejf[2 * en + 1] = make_float4((float)(e2y / det), (float)(-e2x / det), (float)(-e1y / det),
+                                        (float)(e1x / det));
+    }
+    // lower bound of every node's distance to the nearest boundary edge
+    // (capped at DCAP): a departure segment shorter than this cannot leave
+    // the mesh
+    const double DCAP = 16.0;
+    T.bdist.assign(N, (float)DCAP);
+    {
+        std::vector<std::pair<double2, double2>> be;
+        for (int en = 0; en < E; ++en)
+            for (int k = 0; k < 3; ++k)
+                if ((einfo[en] >> (8 * k)) & 3u) be.push_back({ev[3 * en + k], ev[3 * en + (k + 1) % 3]});
+        if (!be.empty() && (T.Lx > 0 || T.Ly > 0)) {
+            T.bdist.assign(N, 0.0f); // periodic meshes with boundaries: always walk
+        } else if (!be.empty()) {
+            const double cs = DCAP;
+            std::unordered_map<uint64_t, std::vector<int>> grid;
+            auto key = [](long ix, long iy) { return ((uint64_t)(uint32_t)ix << 32) | (uint32_t)iy; };
+            for (size_t b = 0; b < be.size(); ++b) {
+                double x0 = std::min(be[b].first.x, be[b].second.x) - DCAP, x1 = std::max(be[b].first.x, be[b].second.x) + DCAP;
+                double y0 = std::min(be[b].first.y, be[b].second.y) - DCAP, y1 = std::max(be[b].first.y, be[b].second.y) + DCAP;
+                for (long ix = (long)std::floor(x0 / cs); ix <= (long)std::floor(x1 / cs); ++ix)
+                    for (long iy = (long)std::floor(y0 / cs); iy <= (long)std::floor(y1 / cs); ++iy)
+                        grid[key(ix, iy)].push_back((int)b);
+            }
+            for (int a = 0; a < N; ++a) {
+                double px = T.X[a].x, py = T.X[a].y;
+                auto it = grid.find(key((long)std::floor(px / cs), (long)std::floor(py / cs)));
+                if (it == grid.end()) continue;
+                double dmin = DCAP;
+                for (int b : it->second) {
+                    double ax = be[b].first.x, ay = be[b].first.y, bx = be[b].second.x, by = be[b].second.y;
+                    double dx = bx - ax, dy = by - ay, L2 = dx * dx + dy * dy;
+                    double t = L2 > 0 ? ((px - ax) * dx + (py - ay) * dy) / L2 : 0.0;
+                    t = std::min(1.0, std::max(0.0, t));
+                    double qx = ax + t * dx - px, qy = ay + t * dy - py;
+                    dmin = std::min(dmin, std::sqrt(qx * qx + qy * qy));
+                }
+                T.bdist[a] = (float)(dmin * (1.0 - 1e-6));
+            }
+        }
+    }
     return ALELB_OK;
 }
 

@@ -31,7 +31,38 @@ def lib():
         _lib = C.CDLL(build_lib())
         _lib.alelb_hostcheck_locate.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                                 C.c_char_p, C.c_int]
+        _lib.alelb_hostcheck_inside.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.c_void_p]
     return _lib
+
+
+def _desc(mesh, motion):
+    X = np.ascontiguousarray(mesh.X, dtype=np.float64).reshape(-1)
+    conn = np.ascontiguousarray(mesh.conn, dtype=np.int32).reshape(-1)
+    ek = np.ascontiguousarray(mesh.edge_kind, dtype=np.uint8).reshape(-1)
+    d = alelb.MeshDesc()
+    d.n_nodes, d.X, d.n_elems = mesh.n_nodes, X.ctypes.data, mesh.n_elems
+    d.conn, d.edge_kind = conn.ctypes.data, ek.ctypes.data
+    d.period[0], d.period[1] = float(mesh.period[0]), float(mesh.period[1])
+    d.motion_kind = int(motion.kind)
+    for k in range(16):
+        d.motion[k] = float(motion.params[k])
+    d.renumber = alelb.RENUMBER_MORTON
+    return d, (X, conn, ek)
+
+
+def inside_f32(mesh, elem, px, py):
+    """The FP32 strict-containment filter for points (px, py) in elements elem."""
+    from . import inputs as I
+    d, keep = _desc(mesh, I.Motion.make(0))
+    elem = np.ascontiguousarray(elem, dtype=np.int32)
+    px = np.ascontiguousarray(px, dtype=np.float64)
+    py = np.ascontiguousarray(py, dtype=np.float64)
+    out = np.zeros(len(elem), dtype=np.int8)
+    st = lib().alelb_hostcheck_inside(C.byref(d), len(elem), elem.ctypes.data, px.ctypes.data,
+                                      py.ctypes.data, out.ctypes.data)
+    assert st == 0
+    return out.astype(bool)
 
 
 def locate(mesh, motion, t, literal=False):

@@ -46,3 +46,39 @@ def test_host_walk_literal_form():
     st, e, k = H.locate(mesh, mot, 11.0, literal=True)
     eo, ko = o.locate(11.0)
     assert st == 0 and np.array_equal(e, eo) and np.array_equal(k, ko)
+
+
+def test_fp32_filter_never_accepts_a_point_that_is_not_strictly_inside():
+    """The fast path's certified FP32 filter may decline, never err: against
+    exact rationals, on points placed on, just inside and just outside the
+    edges of elements of a graded O-mesh and a jittered box."""
+    from fractions import Fraction as F
+    rng = np.random.default_rng(3)
+    for mesh in (I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0), I.periodic_box(12, 24.0, 0.2, seed=4)):
+        es, pxs, pys, exact, easy = [], [], [], [], []
+        for e in rng.choice(mesh.n_elems, min(400, mesh.n_elems), replace=False):
+            v = mesh.X[mesh.conn[e, :3]].copy()
+            if mesh.period[0] > 0:  # unwrap the element around its first vertex
+                L = mesh.period[0]
+                v[1:] = v[0] + (v[1:] - v[0] + L / 2) % L - L / 2
+                if np.any(v < 0) or np.any(v >= L):
+                    continue
+            for k in range(3):
+                a, b, c = v[k], v[(k + 1) % 3], v[(k + 2) % 3]
+                for s in (0.0, 1e-6, -1e-6, 1e-9, -1e-9, 1e-12, -1e-12, 0.3):
+                    t = rng.uniform(0.05, 0.95)
+                    p = a + t * (b - a) + s * (c - (a + b) / 2)
+                    es.append(e)
+                    pxs.append(p[0])
+                    pys.append(p[1])
+                    o = []
+                    for kk in range(3):
+                        A, B = v[kk], v[(kk + 1) % 3]
+                        o.append((F(A[0]) - F(p[0])) * (F(B[1]) - F(p[1])) - (F(A[1]) - F(p[1])) * (F(B[0]) - F(p[0])))
+                    exact.append(all(x > 0 for x in o))
+                    easy.append(s == 0.3)
+        got = H.inside_f32(mesh, np.array(es), np.array(pxs), np.array(pys))
+        exact = np.array(exact)
+        assert not np.any(got & ~exact), "filter accepted a point that is not strictly inside"
+        easy = np.array(easy) & exact
+        assert got[easy].sum() >= 0.99 * easy.sum()  # and it does decide the clear-cut ones
