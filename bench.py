@@ -217,6 +217,7 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        walks0 = s.info()["walks"]
         if profile:
             s.profile(True)
         with torch.cuda.stream(stream):
@@ -231,6 +232,8 @@ def run_ours(args):
         kt = s.kernel_times() if profile else {}
         s.profile(False)
         info = s.info()
+        info["walks_timed"] = info["walks"] - walks0
+        info["step_ms"] = [a.elapsed_time(b) for a, b in evs]
         s.close()
         return ms, kt, info
 
@@ -308,6 +311,9 @@ def run_ours(args):
             "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt32.items()},
             "kernels_fp64": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt64.items()},
             "gpu_launches": 3 * K,
+            "locate": {"walks_per_step": info32["walks_timed"] / K,
+                       "verified_previous_element_rate": 1.0 - info32["walks_timed"] / (9.0 * N * K)},
+            "step_ms": [round(x, 4) for x in info32["step_ms"]],
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -160,8 +160,11 @@ alelb_status alelb_forces(alelb_solver *s, double out[6]);
 /* Element choice of every population for a propagation at map time t,
    [9][n_nodes] in original numbering: elem = original element id, -2 (the
    departure point is the node itself) or -1 (missing; kind = 1 wall,
-   2 far field).  Synchronous; does not change the solver state. */
-alelb_status alelb_locate(alelb_solver *s, double t, int32_t *elem, int8_t *kind);
+   2 far field).  use_cache = 0: the element walk decides every population;
+   use_cache = 1 (FP32-deviation solvers): the decision the propagation
+   kernel would take now -- the previous-step element where the certified
+   FP32 test accepts it, the walk elsewhere.  Synchronous; changes nothing. */
+alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cache, int32_t *elem, int8_t *kind);
 
 /* Per-kernel device time accumulated with CUDA events on the solver's
    stream since the last reset: names[k] (static strings), ms[k], launches[k]
@@ -171,8 +174,10 @@ alelb_status alelb_profile(alelb_solver *s, int32_t enable);
 alelb_status alelb_kernel_times(alelb_solver *s, const char **names, double *ms,
                                 int64_t *launches, int32_t *n);
 
-/* Sizes and algorithmic traffic of one step: out = {n_nodes, n_elems,
-   bytes_state_per_node, bytes_static_per_node, n_wall_nodes}. */
+/* Sizes and counters: out = {n_nodes, n_elems, bytes per stored population
+   value, 0, n_wall_nodes, precision, n_wall_edges, element walks run by the
+   propagation kernel since lb_init (populations not settled by the verified
+   previous-step element)}.  Synchronous. */
 alelb_status alelb_info(alelb_solver *s, double out[8]);
 
 /* One FP64 time step t -> t + 1 that allocates nothing (the paper has no

@@ -82,7 +82,7 @@ def load(path: str = LIB_PATH):
     L.alelb_get_pops.argtypes = [p, p, p]
     L.alelb_set_pops.argtypes = [p, p, p, p, p, p, p, d]
     L.alelb_forces.argtypes = [p, p]
-    L.alelb_locate.argtypes = [p, d, p, p]
+    L.alelb_locate.argtypes = [p, d, i32, p, p]
     L.alelb_profile.argtypes = [p, i32]
     L.alelb_kernel_times.argtypes = [p, C.POINTER(C.c_char_p), p, p, C.POINTER(i32)]
     L.alelb_info.argtypes = [p, p]
@@ -248,10 +248,10 @@ class Solver:
         self._check(load().alelb_forces(self.h, _ptr(out)), "forces")
         return out
 
-    def locate(self, t):
+    def locate(self, t, use_cache=False):
         e = np.empty((NQ, self.nn), dtype=np.int32)
         k = np.empty((NQ, self.nn), dtype=np.int8)
-        self._check(load().alelb_locate(self.h, float(t), _ptr(e), _ptr(k)), "locate")
+        self._check(load().alelb_locate(self.h, float(t), int(bool(use_cache)), _ptr(e), _ptr(k)), "locate")
         return e, k
 
     def profile(self, enable=True):
@@ -270,7 +270,8 @@ class Solver:
         out = np.zeros(8)
         self._check(load().alelb_info(self.h, _ptr(out)), "info")
         return dict(n_nodes=int(out[0]), n_elems=int(out[1]), pop_bytes=out[2],
-                    n_wall_nodes=int(out[4]), precision=int(out[5]), n_wall_edges=int(out[6]))
+                    n_wall_nodes=int(out[4]), precision=int(out[5]), n_wall_edges=int(out[6]),
+                    walks=int(out[7]))
 
     def close(self):
         if getattr(self, "h", None):

@@ -123,10 +123,13 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.orig_elem = B.put(T.orig, st);
     D.ejf = B.put(T.ejf, st);
     D.bdist = B.put(T.bdist, st);
+    D.Xf = B.put(T.Xf, st);
+    D.v0f = B.put(T.v0f, st);
     m->d_wedges = B.put(T.wedges, st);
     m->nw = (int)T.wedges.size();
     m->mst = T.host_map();
     m->mst.ms = B.put(T.ms, st);
+    m->mst.msf = B.put(T.msf, st);
     // P2 derivative tables at the six node positions
     static const double LXI[6][2] = {{0, 0}, {1, 0}, {0, 1}, {0.5, 0}, {0.5, 0.5}, {0, 0.5}};
     double dxi[6][6], deta[6][6];
@@ -306,6 +309,7 @@ struct alelb_solver {
     double *d_scratch = nullptr; // 22 N doubles: import/export staging
     double *h_pinned = nullptr;  // 22 N doubles of page-locked host staging
     int *d_err = nullptr;
+    unsigned long long *d_stats = nullptr; // [0]: element walks run by the propagation kernel
     double *d_out = nullptr;
     DevBuf buf;
     int sticky = 0;
@@ -352,6 +356,21 @@ cudaEvent_t get_event(alelb_solver *s)
     return e;
 }
 
+MapScalarsF to_f32(const MapScalars &S, const alelb_mesh *m)
+{
+    MapScalarsF F;
+    F.s = (float)S.s;
+    F.sd = (float)S.sd;
+    F.vy = (float)S.vy;
+    F.c = (float)S.c;
+    F.sn = (float)S.sn;
+    F.thd = (float)S.thd;
+    F.cm = (float)S.cm;
+    F.Xc = (float)m->T.mp[3];
+    F.Yc = (float)m->T.mp[4];
+    return F;
+}
+
 template <class S, class A>
 cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const MapScalars &sc)
 {
@@ -367,9 +386,11 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
             cudaEventRecord(ea, s->stream);
         }
         if (k == KT_STREAM && s->prec == ALELB_PREC_FP32_DEV)
-            k_stream<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err);
+            k_stream<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+                                                                         st, s->d_err, s->d_stats);
         else if (k == KT_STREAM)
-            k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err);
+            k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+                                                                          st, s->d_err, s->d_stats);
         else if (k == KT_DERIV1)
             k_deriv1<S, A><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, st);
         else
@@ -454,6 +475,8 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     s->d_scratch = s->buf.alloc<double>((size_t)22 * N, st);
     if (st == cudaSuccess) st = cudaHostAlloc((void **)&s->h_pinned, (size_t)22 * N * sizeof(double), 0);
     s->d_err = s->buf.alloc<int>(1, st);
+    s->d_stats = s->buf.alloc<unsigned long long>(4, st);
+    if (st == cudaSuccess) st = cudaMemset(s->d_stats, 0, 4 * sizeof(unsigned long long));
     s->d_out = s->buf.alloc<double>(8, st);
     if (st != cudaSuccess) return cuda_fail(s, st);
     KinParams<double> K0{};
@@ -669,15 +692,25 @@ extern "C" alelb_status alelb_forces(alelb_solver *s, double out[6])
     return ALELB_OK;
 }
 
-extern "C" alelb_status alelb_locate(alelb_solver *s, double t, int32_t *elem, int8_t *kind)
+extern "C" alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cache, int32_t *elem,
+                                     int8_t *kind)
 {
     if (!s || !elem || !kind) return ALELB_ERR_ARG;
+    const int *cache = nullptr;
+    if (use_cache) {
+        if (s->prec != ALELB_PREC_FP32_DEV) {
+            s->err = "locate: the cached fast decisions exist in the FP32-deviation form only";
+            return ALELB_ERR_ARG;
+        }
+        cache = s->sf.cache;
+    }
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t);
     int *de = (int *)s->d_scratch;
     int8_t *dk = (int8_t *)(s->d_scratch + (size_t)9 * N);
-    k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, s->flags, de, dk, s->d_err);
+    k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), s->flags, cache,
+                                                     de, dk, s->d_err);
     std::vector<int> he((size_t)9 * N);
     std::vector<int8_t> hk((size_t)9 * N);
     cudaError_t st = cudaGetLastError();
@@ -740,7 +773,11 @@ extern "C" alelb_status alelb_info(alelb_solver *s, double out[8])
     out[4] = m->T.n_wall_nodes;
     out[5] = s->prec;
     out[6] = m->nw;
-    out[7] = 0;
+    unsigned long long walks = 0;
+    cudaError_t st = cudaMemcpyAsync(&walks, s->d_stats, sizeof(walks), cudaMemcpyDeviceToHost, s->stream);
+    if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream);
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    out[7] = (double)walks;
     return ALELB_OK;
 }
 
@@ -847,7 +884,8 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     }
     K.flags = p->flags;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
-    k_stream<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);
+    k_stream<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+                                                                       sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
         k_deriv1<double, double><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, sd);
     k_collide<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);

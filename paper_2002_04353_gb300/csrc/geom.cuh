@@ -37,6 +37,7 @@ struct MapStatic {
     int kind;
     double Xc, Yc;
     const double *ms; // per-node static factors, SoA [k * N + a]
+    const float *msf; // the same rounded to FP32
     int N;
 };
 
@@ -188,6 +189,71 @@ __device__ __forceinline__ void map_position(const MapStatic &M, const MapScalar
     }
 }
 
+// The map's metrics and V_G in FP32 (no FP64 operation): an approximation
+// whose error the fast propagation path bounds and absorbs; never used to
+// decide anything on its own.
+struct MapScalarsF {
+    float s, sd, vy, c, sn, thd, cm;
+    float Xc, Yc;
+};
+
+__device__ __forceinline__ void map_node_f32(const MapStatic &M, const MapScalarsF &S, int a,
+                                             float4 Xf, float &xX, float &xY, float &yX,
+                                             float &yY, float &Vx, float &Vy)
+{
+    const int N = M.N;
+    switch (M.kind) {
+    case MK_SINE:
+        xX = 1.0f + M.msf[2 * N + a] * S.s;
+        xY = M.msf[3 * N + a] * S.s;
+        yX = M.msf[4 * N + a] * S.s;
+        yY = 1.0f + M.msf[5 * N + a] * S.s;
+        Vx = M.msf[a] * S.sd;
+        Vy = M.msf[N + a] * S.sd;
+        break;
+    case MK_PLUNGE:
+        xX = 1.0f;
+        xY = 0.0f;
+        yX = 0.0f;
+        yY = 1.0f;
+        Vx = 0.0f;
+        Vy = S.vy;
+        break;
+    case MK_PITCH:
+    case MK_PITCH_PLUNGE: {
+        float dx = (Xf.x - S.Xc) + Xf.z, dy = (Xf.y - S.Yc) + Xf.w;
+        xX = S.c;
+        xY = -S.sn;
+        yX = S.sn;
+        yY = S.c;
+        Vx = S.thd * (-S.sn * dx - S.c * dy);
+        Vy = S.thd * (S.c * dx - S.sn * dy) + S.vy;
+        break;
+    }
+    case MK_BLENDED: {
+        float dx = (Xf.x - S.Xc) + Xf.z, dy = (Xf.y - S.Yc) + Xf.w;
+        float b = M.msf[a], bX = M.msf[N + a], bY = M.msf[2 * N + a];
+        float qx = S.cm * dx - S.sn * dy;
+        float qy = S.sn * dx + S.cm * dy;
+        xX = 1.0f + b * S.cm + qx * bX;
+        xY = -b * S.sn + qx * bY;
+        yX = b * S.sn + qy * bX;
+        yY = 1.0f + b * S.cm + qy * bY;
+        float bt = b * S.thd;
+        Vx = bt * (-S.sn * dx - S.c * dy);
+        Vy = bt * (S.c * dx - S.sn * dy);
+        break;
+    }
+    default:
+        xX = 1.0f;
+        xY = 0.0f;
+        yX = 0.0f;
+        yY = 1.0f;
+        Vx = 0.0f;
+        Vy = 0.0f;
+    }
+}
+
 // A = g^{-1,T} = (1/det g) [[y_Y, -x_Y], [-y_X, x_X]]; returns det g.
 ALELB_HD __forceinline__ double metric_inverse_T(double xX, double xY, double yX, double yY,
                                                    double &a11, double &a12, double &a21,
@@ -295,6 +361,8 @@ struct MeshDev {
     const int *orig_elem;  // [E] original element id
     const float4 *ejf;     // [2E] FP32 edge vectors (v1-v0, v2-v0) and inverse Jacobian rows
     const float *bdist;    // [N] lower bound of the node's distance to the nearest boundary edge
+    const float4 *Xf;      // [N] node coordinates split hi + lo in FP32 (xh, yh, xl, yl)
+    const float4 *v0f;     // [E] first frame vertex split hi + lo in FP32
 };
 
 struct Loc {
@@ -337,7 +405,7 @@ constexpr int WALK_LIMIT = 256;
 // treated as passing to the vertex's right.  Ties (p on an edge or vertex)
 // go to the containing element of larger computational area, then lower
 // original id.
-ALELB_HD Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
+ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
                     int *err)
 {
     Loc r;

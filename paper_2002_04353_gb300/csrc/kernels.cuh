@@ -84,52 +84,142 @@ __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const
     KY = (-x_eta * sxi + x_xi * seta) / detJ;
 }
 
+// Bound of the FP32 transformed velocities c^_i against the FP64 canonical
+// ones, from the FP32 metrics themselves (u = 2^-24):
+//   entries of g:   eps_g   = 16u (1 + G),  G = max |g_ij|
+//   det g:          eps_det = 4 G eps_g + 3u (|x_X y_Y| + |y_X x_Y|)
+//   A = g^{-1,T}:   eps_A   = (eps_g + G eps_det / det) / det + 2u max|A|
+//   V_G:            eps_V   = 8u Vmag (Vmag: sum of the magnitudes entering V)
+//   c^ = A c - A V: eps_c   = 2 [eps_A (2 + 2|V|) + 2 max|A| eps_V + 6u max|A| (2 + 2|V|)]
+struct FastMap {
+    float A11, A12, A21, A22, W1, W2, eps_c;
+    bool ok;
+};
+
+__device__ __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF &sf, int a,
+                                            float4 Xf)
+{
+    const float u = 5.9604644775390625e-08f;
+    float xX, xY, yX, yY, Vx, Vy;
+    map_node_f32(MS, sf, a, Xf, xX, xY, yX, yY, Vx, Vy);
+    FastMap F;
+    float det = xX * yY - yX * xY;
+    float G = fmaxf(fmaxf(fabsf(xX), fabsf(xY)), fmaxf(fabsf(yX), fabsf(yY)));
+    float inv = 1.0f / det;
+    F.A11 = yY * inv;
+    F.A12 = -xY * inv;
+    F.A21 = -yX * inv;
+    F.A22 = xX * inv;
+    F.W1 = F.A11 * Vx + F.A12 * Vy;
+    F.W2 = F.A21 * Vx + F.A22 * Vy;
+    float Amax = fmaxf(fmaxf(fabsf(F.A11), fabsf(F.A12)), fmaxf(fabsf(F.A21), fabsf(F.A22)));
+    float Vmax = fmaxf(fabsf(Vx), fabsf(Vy));
+    float Vmag = fabsf(Vx) + fabsf(Vy);
+    if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE || MS.kind == MK_BLENDED) {
+        float dx = fabsf((Xf.x - sf.Xc) + Xf.z), dy = fabsf((Xf.y - sf.Yc) + Xf.w);
+        Vmag += fabsf(sf.thd) * (dx + dy) + fabsf(sf.vy);
+    }
+    float eps_g = 16.0f * u * (1.0f + G);
+    float eps_det = 4.0f * G * eps_g + 3.0f * u * (fabsf(xX * yY) + fabsf(yX * xY));
+    float eps_A = (eps_g + G * eps_det / det) / det + 2.0f * u * Amax;
+    float eps_V = 8.0f * u * Vmag;
+    float cv = 2.0f + 2.0f * Vmax;
+    F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
+    F.ok = det > 16.0f * eps_det && isfinite(F.eps_c);
+    return F;
+}
+
+// The fast path's decision for population i of a node: true (element e,
+// FP32 offset q from its first vertex) when the cached element c provably
+// holds the FP64 departure point strictly inside and the departure segment
+// cannot reach a boundary.
+__device__ __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, float4 Xf,
+                                            float bdist, int i, int c, int &e, float &qx,
+                                            float &qy)
+{
+    const float cx = (float)c_cx[i], cy = (float)c_cy[i];
+    const float chx = F.A11 * cx + F.A12 * cy - F.W1;
+    const float chy = F.A21 * cx + F.A22 * cy - F.W2;
+    const float len = sqrtf(chx * chx + chy * chy);
+    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eps_c && len + F.eps_c < bdist)) return false;
+    e = c & 0x0fffffff;
+    const float4 v0 = M.v0f[e];
+    const float4 ed = M.ejf[2 * e];
+    const float dx = (Xf.x - v0.x) + (Xf.z - v0.z);
+    const float dy = (Xf.y - v0.y) + (Xf.w - v0.w);
+    qx = dx - chx;
+    qy = dy - chy;
+    const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
+    const float Q = fmaxf(fabsf(qx), fabsf(qy));
+    // |q - (p - v0)| <= eq: c^ bound, the hi/lo difference and its
+    // roundings, and the FP64 rounding of p itself
+    const float eq = F.eps_c + 1.1920928955078125e-07f * fmaxf(fabsf(dx), fabsf(dy)) +
+                     5.9604644775390625e-08f * Q + 2.98023223876953125e-08f;
+    const float EQ = E + Q;
+    const float bound = 8.0f * EQ * eq + 1.9073486328125e-06f * EQ * EQ;
+    const float o0 = ed.x * qy - ed.y * qx;                               // orient(v0, v1, p)
+    const float o1 = (ed.x - qx) * (ed.w - qy) - (ed.y - qy) * (ed.z - qx); // orient(v1, v2, p)
+    const float o2 = ed.w * qx - ed.z * qy;                               // orient(v2, v0, p)
+    return o0 > bound && o1 > bound && o2 > bound;
+}
+
 // FAST (the FP32-deviation form): each population first tries the element
-// its departure point fell in at the previous step, accepted only when the
-// certified FP32 filter shows the point strictly inside it and the departure
-// segment is shorter than the node's distance to any boundary -- then that
-// element is the unique one the walk would return.  Otherwise (and always in
-// the plain form) the exact walk runs and refreshes the cache.
+// its departure point fell in at the previous step.  The departure offset
+// from that element's first vertex is formed in FP32 (map, c^ and the hi/lo
+// coordinate difference) with a rigorous error bound, and the element is
+// accepted only when the certified FP32 orientations show that the FP64
+// canonical departure point lies strictly inside it and the departure
+// segment is shorter than the node's distance to any boundary: then it is
+// the unique element the walk would return.  Otherwise (and always in the
+// plain form) the FP64 departure point and the exact walk decide, and the
+// cache is refreshed.  stats[0] counts the walks.
 template <class S, class A, bool FAST>
 __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
-                                                KinParams<A> K, StateDev<S> st, int *err)
+                                                MapScalarsF sf, KinParams<A> K, StateDev<S> st,
+                                                int *err, unsigned long long *stats)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
     if (a >= N) return;
     const double2 Xa = M.X[a];
-    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
-    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
-    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-    double wx, wy;
-    mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
-    const float bdist = FAST ? M.bdist[a] : 0.0f;
+    FastMap F{};
+    float4 Xf = make_float4(0, 0, 0, 0);
+    float bdist = 0.0f;
+    if (FAST) {
+        Xf = M.Xf[a];
+        bdist = M.bdist[a];
+        F = fast_map(MS, sf, a, Xf);
+        if (K.flags & FLAG_LITERAL_VG) F.ok = false;
+    }
+    bool have64 = false;
+    double a11 = 0, a12 = 0, a21 = 0, a22 = 0, wx = 0, wy = 0, Vx = 0, Vy = 0;
     int miss = 0, far = 0;
+    unsigned walks = 0;
     // running moments of the streamed populations (deviations)
-    A sf = 0, jx = 0, jy = 0, sg = 0;
+    A sfm = 0, jx = 0, jy = 0, sg = 0;
 #pragma unroll 1
     for (int i = 0; i < NQ; ++i) {
-        double chx, chy, px, py;
-        departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx,
-                  chy, px, py);
         A fi = 0, gi = 0;
         int src = -1; // node whose value is taken as is
-        if (chx == 0.0 && chy == 0.0) {
-            src = a;
-        } else {
-            int e = -1, ex = 0, ey = 0;
-            float qx = 0.f, qy = 0.f;
-            bool fast = false;
-            if (FAST) {
-                const int c = st.cache[i * N + a];
-                if (c >= 0 && sqrtf((float)(chx * chx + chy * chy)) * 1.000001f < bdist) {
-                    e = c & 0x0fffffff;
-                    ex = ((c >> 28) & 3) - 1;
-                    ey = ((c >> 30) & 3) - 1;
-                    fast = strictly_inside_f32(M, e, ex, ey, px, py, qx, qy);
-                }
+        int e = -1;
+        float qx = 0.f, qy = 0.f;
+        bool fast = false;
+        if (FAST && F.ok) fast = fast_decide(M, F, Xf, bdist, i, st.cache[i * N + a], e, qx, qy);
+        if (!fast) {
+            if (!have64) {
+                double xX, xY, yX, yY;
+                map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+                metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+                mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
+                have64 = true;
             }
-            if (!fast) {
+            double chx, chy, px, py;
+            departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx,
+                      chy, px, py);
+            if (chx == 0.0 && chy == 0.0) {
+                src = a;
+            } else {
+                ++walks;
                 Loc L = walk(M, a, Xa.x, Xa.y, px, py, err);
                 if (L.e == -2) {
                     src = a;
@@ -141,32 +231,37 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
                     src = L.vnode;
                 } else {
                     e = L.e;
-                    ex = L.sx;
-                    ey = L.sy;
-                    if (FAST) st.cache[i * N + a] = e | ((ex + 1) << 28) | ((ey + 1) << 30);
+                    if (FAST) {
+                        st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
+                        double2 v0 = M.ev[3 * e];
+                        qx = (float)(px - (L.sx ? v0.x + L.sx * M.Lx : v0.x));
+                        qy = (float)(py - (L.sy ? v0.y + L.sy * M.Ly : v0.y));
+                    } else {
+                        double xi, eta;
+                        local_coords(M, e, L.sx, L.sy, px, py, xi, eta);
+                        qx = (float)xi; // unused in the FP64 form
+                        A Nw[6];
+                        shape6<A>((A)xi, (A)eta, Nw);
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) {
+                            const int b = M.conn[6 * e + k];
+                            fi += Nw[k] * (A)st.post[i * N + b];
+                            gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                        }
+                        e = -1; // interpolated already
+                    }
                 }
             }
-            if (src < 0) {
-                A Nw[6];
-                if (FAST) {
-                    if (!fast) {
-                        double2 v0 = M.ev[3 * e];
-                        qx = (float)(px - (ex ? v0.x + ex * M.Lx : v0.x));
-                        qy = (float)(py - (ey ? v0.y + ey * M.Ly : v0.y));
-                    }
-                    float4 J = M.ejf[2 * e + 1];
-                    shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
-                } else {
-                    double xi, eta;
-                    local_coords(M, e, ex, ey, px, py, xi, eta);
-                    shape6<A>((A)xi, (A)eta, Nw);
-                }
+        }
+        if (FAST && e >= 0) {
+            A Nw[6];
+            const float4 J = M.ejf[2 * e + 1];
+            shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const int b = M.conn[6 * e + k];
-                    fi += Nw[k] * (A)st.post[i * N + b];
-                    gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
-                }
+            for (int k = 0; k < 6; ++k) {
+                const int b = M.conn[6 * e + k];
+                fi += Nw[k] * (A)st.post[i * N + b];
+                gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
             }
         }
         if (src >= 0) {
@@ -175,12 +270,18 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
         }
         st.str[i * N + a] = (S)fi;
         st.str[(NQ + i) * N + a] = (S)gi;
-        sf += fi;
+        sfm += fi;
         jx += (A)c_cx[i] * fi;
         jy += (A)c_cy[i] * fi;
         sg += gi;
     }
+    if (stats && walks) atomicAdd(stats, (unsigned long long)walks);
     if (miss) {
+        if (!have64) { // cannot happen (a missing population comes from a walk)
+            double xX, xY, yX, yY;
+            map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        }
         A fm[NQ], gm[NQ];
         if (miss & ~far) {
             // targets (Sec. IV.A): wall node -> u = V_G, rho and T at the
@@ -231,14 +332,14 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
             A gi = (far >> i & 1) ? K.ginf[i] : gm[i];
             st.str[i * N + a] = (S)fi;
             st.str[(NQ + i) * N + a] = (S)gi;
-            sf += fi;
+            sfm += fi;
             jx += (A)c_cx[i] * fi;
             jy += (A)c_cy[i] * fi;
             sg += gi;
         }
     }
     // moments (Sec. IV): rho, u, E, T from the streamed populations
-    A rho = K.rho_ref + sf;
+    A rho = K.rho_ref + sfm;
     A ux = jx / rho, uy = jy / rho;
     A E = (K.E2_ref + sg) / (A(2) * rho);
     A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
@@ -307,9 +408,11 @@ __global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapSca
     st.T[a] = (S)T;
 }
 
-// Element choice of every population at map time t (parity report).
-__global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, int flags, int *elem,
-                         int8_t *kind, int *err)
+// Element choice of every population at map time t (parity report).  With
+// cache != nullptr each population first takes the propagation kernel's
+// fast decision (verified previous-step element), as k_stream would.
+__global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, MapScalarsF sf, int flags,
+                         const int *cache, int *elem, int8_t *kind, int *err)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
@@ -317,6 +420,17 @@ __global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, int flags, int 
     int e9[NQ];
     int8_t k9[NQ];
     locate_node(M, MS, sc, flags & FLAG_LITERAL_VG, a, e9, k9, err);
+    if (cache && !(flags & FLAG_LITERAL_VG)) {
+        const float4 Xf = M.Xf[a];
+        const FastMap F = fast_map(MS, sf, a, Xf);
+        if (F.ok)
+            for (int i = 0; i < NQ; ++i) {
+                int e;
+                float qx, qy;
+                if (fast_decide(M, F, Xf, M.bdist[a], i, cache[i * N + a], e, qx, qy))
+                    e9[i] = M.orig_elem[e], k9[i] = 0;
+            }
+    }
     for (int i = 0; i < NQ; ++i) {
         elem[i * N + a] = e9[i];
         kind[i * N + a] = k9[i];

@@ -60,8 +60,8 @@ struct HostTables {
     std::vector<int2> fan, owner, wedges;
     std::vector<uint8_t> bkind;
     std::vector<double> ms;
-    std::vector<float4> ejf;
-    std::vector<float> bdist;
+    std::vector<float4> ejf, Xf, v0f;
+    std::vector<float> bdist, msf;
     int n_wall_nodes = 0;
 
     // a MeshDev whose pointers address these host vectors (host-side walk)
@@ -88,6 +88,8 @@ struct HostTables {
         D.orig_elem = orig.data();
         D.ejf = ejf.data();
         D.bdist = bdist.data();
+        D.Xf = Xf.data();
+        D.v0f = v0f.data();
         return D;
     }
     MapStatic host_map() const
@@ -98,6 +100,7 @@ struct HostTables {
         S.Yc = mp[4];
         S.N = N;
         S.ms = ms.empty() ? nullptr : ms.data();
+        S.msf = msf.empty() ? nullptr : msf.data();
         return S;
     }
 };
@@ -464,6 +467,17 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
         T.ejf[2 * en + 1] = make_float4((float)(e2y / det), (float)(-e2x / det), (float)(-e1y / det),
                                         (float)(e1x / det));
     }
+    // coordinates split into FP32 hi + lo parts: hi = fl32(x), lo = fl32(x - hi)
+    auto split = [](double2 v) {
+        float xh = (float)v.x, yh = (float)v.y;
+        return make_float4(xh, yh, (float)(v.x - (double)xh), (float)(v.y - (double)yh));
+    };
+    T.Xf.resize(N);
+    for (int a = 0; a < N; ++a) T.Xf[a] = split(T.X[a]);
+    T.v0f.resize(E);
+    for (int en = 0; en < E; ++en) T.v0f[en] = split(ev[3 * en]);
+    T.msf.resize(T.ms.size());
+    for (size_t k = 0; k < T.ms.size(); ++k) T.msf[k] = (float)T.ms[k];
     // lower bound of every node's distance to the nearest boundary edge
     // (capped at DCAP): a departure segment shorter than this cannot leave
     // the mesh

@@ -220,3 +220,24 @@ def test_mixed_airfoil_matches_fp64_oracle():
     o.step(6)
     s.lb_step(6)
     _compare_mixed(o, s, "mixed airfoil")
+
+
+@pytest.mark.parametrize("name", ["box_sine", "box_paper_map", "omesh_plunge", "omesh_pitch", "omesh_blended"])
+def test_fast_path_element_choices_bitwise(name):
+    """The FP32-deviation propagation settles most populations with the
+    previous-step element, verified by certified FP32 arithmetic; its
+    decisions must equal the oracle's exhaustive search bit for bit."""
+    mesh, motion = LOC_CASES[name]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o = O.Oracle(mesh, motion, flow)
+    s = alelb.Solver(alelb.Mesh(mesh, motion), flow, alelb.PREC_FP32_DEV)
+    s.lb_step(3)  # fills the per-population element cache
+    walks_before = s.info()["walks"]
+    s.lb_step(2)
+    settled = 1.0 - (s.info()["walks"] - walks_before) / (2 * 9 * mesh.n_nodes)
+    assert settled > 0.5, f"fast path settled only {settled:.3f} of the populations"
+    t, _ = s.time()
+    eo, ko = o.locate(t + 1.0)
+    eg, kg = s.locate(t + 1.0, use_cache=True)
+    assert np.array_equal(eo, eg), f"{name}: {np.sum(eo != eg)} fast-path element choices differ"
+    assert np.array_equal(ko, kg)
