@@ -144,6 +144,14 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     }
     if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNxi, dxi, sizeof(dxi));
     if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNeta, deta, sizeof(deta));
+    float dxif[6][6], detaf[6][6];
+    for (int l = 0; l < 6; ++l)
+        for (int k = 0; k < 6; ++k) {
+            dxif[l][k] = (float)dxi[l][k];
+            detaf[l][k] = (float)deta[l][k];
+        }
+    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNxif, dxif, sizeof(dxif));
+    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNetaf, detaf, sizeof(detaf));
     *out = m;
     if (st != cudaSuccess) {
         m->buf.release();
@@ -391,10 +399,16 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
         else if (k == KT_STREAM)
             k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
                                                                           st, s->d_err, s->d_stats);
+        else if (k == KT_DERIV1 && s->prec == ALELB_PREC_FP32_DEV)
+            k_deriv1<S, A, true><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), st);
         else if (k == KT_DERIV1)
-            k_deriv1<S, A><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, st);
+            k_deriv1<S, A, false><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), st);
+        else if (s->prec == ALELB_PREC_FP32_DEV)
+            k_collide<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+                                                                          st, s->d_err);
         else
-            k_collide<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err);
+            k_collide<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+                                                                           st, s->d_err);
         if (s->prof) {
             cudaEventRecord(eb, s->stream);
             s->pending.push_back({k, ea, eb});
@@ -887,8 +901,9 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     k_stream<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
                                                                        sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
-        k_deriv1<double, double><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, sd);
-    k_collide<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err);
+        k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), sd);
+    k_collide<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+                                                                        sd, err);
     int herr = 0;
     st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream);

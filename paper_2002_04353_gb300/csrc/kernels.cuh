@@ -133,16 +133,24 @@ __device__ __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalar
 // FP32 offset q from its first vertex) when the cached element c provably
 // holds the FP64 departure point strictly inside and the departure segment
 // cannot reach a boundary.
+// The segment node -> departure point cannot leave the mesh when it is
+// shorter than the node's distance to any boundary, or when the element is
+// one of the node's own (a triangle is convex and holds both ends).
 __device__ __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, float4 Xf,
-                                            float bdist, int i, int c, int &e, float &qx,
+                                            float bdist, int a, int i, int c, int &e, float &qx,
                                             float &qy)
 {
     const float cx = (float)c_cx[i], cy = (float)c_cy[i];
     const float chx = F.A11 * cx + F.A12 * cy - F.W1;
     const float chy = F.A21 * cx + F.A22 * cy - F.W2;
     const float len = sqrtf(chx * chx + chy * chy);
-    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eps_c && len + F.eps_c < bdist)) return false;
+    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eps_c)) return false;
     e = c & 0x0fffffff;
+    if (!(len + F.eps_c < bdist)) {
+        const int *cn = M.conn + 6 * e;
+        if (!(cn[0] == a || cn[1] == a || cn[2] == a || cn[3] == a || cn[4] == a || cn[5] == a))
+            return false;
+    }
     const float4 v0 = M.v0f[e];
     const float4 ed = M.ejf[2 * e];
     const float dx = (Xf.x - v0.x) + (Xf.z - v0.z);
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
         int e = -1;
         float qx = 0.f, qy = 0.f;
         bool fast = false;
-        if (FAST && F.ok) fast = fast_decide(M, F, Xf, bdist, i, st.cache[i * N + a], e, qx, qy);
+        if (FAST && F.ok) fast = fast_decide(M, F, Xf, bdist, a, i, st.cache[i * N + a], e, qx, qy);
         if (!fast) {
             if (!have64) {
                 double xX, xY, yX, yY;
@@ -350,12 +358,47 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
     st.mrt[a] = (S)(K.mu / (rho * T));
 }
 
-template <class S, class A>
+// FP32 owner-element derivative d K / d X (rows of the FP32 inverse
+// Jacobian: grad xi = (j11, j12), grad eta = (j21, j22)).
+__constant__ float c_dNxif[6][6];
+__constant__ float c_dNetaf[6][6];
+
+template <class S>
+__device__ __forceinline__ void owner_grad_f32(const MeshDev &M, int a, const S *K, float &KX,
+                                               float &KY)
+{
+    const int2 ow = M.owner[a];
+    const int e = ow.x, l = ow.y;
+    const float4 J = M.ejf[2 * e + 1];
+    float sxi = 0.f, seta = 0.f;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const float Ks = (float)K[M.conn[6 * e + s]];
+        sxi += Ks * c_dNxif[l][s];
+        seta += Ks * c_dNetaf[l][s];
+    }
+    KX = sxi * J.x + seta * J.z;
+    KY = sxi * J.y + seta * J.w;
+}
+
+template <class S, class A, bool FAST>
 __global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScalars sc,
-                                                StateDev<S> st)
+                                                MapScalarsF sf, StateDev<S> st)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= M.N) return;
+    if (FAST) {
+        const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
+        float KX, KY;
+        owner_grad_f32(M, a, st.Qx, KX, KY);
+        const float dQx = F.A11 * KX + F.A21 * KY; // d_x Q'_xxx
+        owner_grad_f32(M, a, st.Qy, KX, KY);
+        const float dQy = F.A12 * KX + F.A22 * KY; // d_y Q'_yyy
+        const float m = (float)st.mrt[a];
+        st.Dx[a] = (S)(m * dQx);
+        st.Dy[a] = (S)(m * dQy);
+        return;
+    }
     const double2 Xa = M.X[a];
     double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
     map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -370,15 +413,23 @@ __global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScal
     st.Dy[a] = (S)(m * dQy);
 }
 
-template <class S, class A>
+template <class S, class A, bool FAST>
 __global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapScalars sc,
-                                                 KinParams<A> K, StateDev<S> st, int *err)
+                                                 MapScalarsF sf, KinParams<A> K, StateDev<S> st,
+                                                 int *err)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
     if (a >= N) return;
     A Xx = 0, Xy = 0;
-    if (!(K.flags & FLAG_PHI_OFF)) {
+    if (FAST && !(K.flags & FLAG_PHI_OFF)) {
+        const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
+        float KX, KY;
+        owner_grad_f32(M, a, st.Dx, KX, KY);
+        Xx = (A)(-(F.A11 * KX + F.A21 * KY));
+        owner_grad_f32(M, a, st.Dy, KX, KY);
+        Xy = (A)(-(F.A12 * KX + F.A22 * KY));
+    } else if (!(K.flags & FLAG_PHI_OFF)) {
         const double2 Xa = M.X[a];
         double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
         map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -427,7 +478,7 @@ __global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, MapScalarsF sf,
             for (int i = 0; i < NQ; ++i) {
                 int e;
                 float qx, qy;
-                if (fast_decide(M, F, Xf, M.bdist[a], i, cache[i * N + a], e, qx, qy))
+                if (fast_decide(M, F, Xf, M.bdist[a], a, i, cache[i * N + a], e, qx, qy))
                     e9[i] = M.orig_elem[e], k9[i] = 0;
             }
     }
