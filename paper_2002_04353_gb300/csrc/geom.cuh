@@ -197,7 +197,7 @@ struct MapScalarsF {
     float Xc, Yc;
 };
 
-__device__ __forceinline__ void map_node_f32(const MapStatic &M, const MapScalarsF &S, int a,
+ALELB_HD __forceinline__ void map_node_f32(const MapStatic &M, const MapScalarsF &S, int a,
                                              float4 Xf, float &xX, float &xY, float &yX,
                                              float &yY, float &Vx, float &Vy)
 {
@@ -595,6 +595,133 @@ ALELB_HD __forceinline__ bool strictly_inside_f32(const MeshDev &M, int e, int s
     float o1 = (e1x - qx) * (e2y - qy) - (e1y - qy) * (e2x - qx); // orient(v1, v2, p)
     float o2 = e2y * qx - e2x * qy;                 // orient(v2, v0, p)
     return o0 > bound && o1 > bound && o2 > bound;
+}
+
+// Bound of the FP32 transformed velocities c^_i against the FP64 canonical
+// ones, from the FP32 metrics themselves (u = 2^-24):
+//   entries of g:   eps_g   = 16u (1 + G),  G = max |g_ij|
+//   det g:          eps_det = 4 G eps_g + 3u (|x_X y_Y| + |y_X x_Y|)
+//   A = g^{-1,T}:   eps_A   = (eps_g + G eps_det / det) / det + 2u max|A|
+//   V_G:            eps_V   = 8u Vmag (Vmag: sum of the magnitudes entering V)
+//   c^ = A c - A V: eps_c   = 2 [eps_A (2 + 2|V|) + 2 max|A| eps_V + 6u max|A| (2 + 2|V|)]
+struct FastMap {
+    float A11, A12, A21, A22, W1, W2, eps_c;
+    bool ok;
+};
+
+ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF &sf, int a,
+                                            float4 Xf)
+{
+    const float u = 5.9604644775390625e-08f;
+    float xX, xY, yX, yY, Vx, Vy;
+    map_node_f32(MS, sf, a, Xf, xX, xY, yX, yY, Vx, Vy);
+    FastMap F;
+    float det = xX * yY - yX * xY;
+    float G = fmaxf(fmaxf(fabsf(xX), fabsf(xY)), fmaxf(fabsf(yX), fabsf(yY)));
+    float inv = 1.0f / det;
+    F.A11 = yY * inv;
+    F.A12 = -xY * inv;
+    F.A21 = -yX * inv;
+    F.A22 = xX * inv;
+    F.W1 = F.A11 * Vx + F.A12 * Vy;
+    F.W2 = F.A21 * Vx + F.A22 * Vy;
+    float Amax = fmaxf(fmaxf(fabsf(F.A11), fabsf(F.A12)), fmaxf(fabsf(F.A21), fabsf(F.A22)));
+    float Vmax = fmaxf(fabsf(Vx), fabsf(Vy));
+    float Vmag = fabsf(Vx) + fabsf(Vy);
+    if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE || MS.kind == MK_BLENDED) {
+        float dx = fabsf((Xf.x - sf.Xc) + Xf.z), dy = fabsf((Xf.y - sf.Yc) + Xf.w);
+        Vmag += fabsf(sf.thd) * (dx + dy) + fabsf(sf.vy);
+    }
+    // error of the FP32 metric entries against the FP64 canonical ones, by
+    // map kind: exact (identity, plunge), rounded cos/sin (rigid pitch),
+    // a rounded product plus one (sine), a handful of terms (blended)
+    float eps_g = 8.0f * u * (1.0f + G);
+    if (MS.kind == MK_NONE || MS.kind == MK_PLUNGE) eps_g = 0.0f;
+    else if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE) eps_g = 2.0f * u;
+    else if (MS.kind == MK_SINE) eps_g = 4.0f * u * (1.0f + G);
+    float eps_det = 4.0f * G * eps_g + 3.0f * u * (fabsf(xX * yY) + fabsf(yX * xY));
+    float eps_A = (eps_g + G * eps_det / det) / det + 2.0f * u * Amax;
+    float eps_V = 8.0f * u * Vmag;
+    float cv = 2.0f + 2.0f * Vmax;
+    F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
+    F.ok = det > 16.0f * eps_det && isfinite(F.eps_c);
+    return F;
+}
+
+// The fast path's decision for population i of a node: true (element e,
+// FP32 offset q from its first vertex) when the cached element c provably
+// holds the FP64 departure point strictly inside and the departure segment
+// cannot reach a boundary.
+// The segment node -> departure point cannot leave the mesh when it is
+// shorter than the node's distance to any boundary, or when the element is
+// one of the node's own (a triangle is convex and holds both ends).
+ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, float4 Xf,
+                                          float bdist, int a, int i, int c, int &e, float &qx,
+                                          float &qy)
+{
+    const float u = 5.9604644775390625e-08f;
+    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const float cx = (float)CXh[i], cy = (float)CYh[i];
+    const float chx = F.A11 * cx + F.A12 * cy - F.W1;
+    const float chy = F.A21 * cx + F.A22 * cy - F.W2;
+    const float len = sqrtf(chx * chx + chy * chy);
+    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eps_c)) return false;
+    e = c & 0x0fffffff;
+    const int *cn = M.conn + 6 * e;
+    int l = -1;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (cn[k] == a) l = k;
+    if (!(len + F.eps_c < bdist) && l < 0) return false;
+    const float4 ed = M.ejf[2 * e];
+    // vertices relative to v0: w0 = 0, w1 = e1, w2 = e2 (FP32-rounded exact differences)
+    const float wx[3] = {0.0f, ed.x, ed.z}, wy[3] = {0.0f, ed.y, ed.w};
+    const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
+    const float C = fmaxf(fabsf(chx), fabsf(chy));
+    float dx, dy; // node position relative to v0
+    if (l >= 0) {
+        if (l < 3) {
+            dx = wx[l];
+            dy = wy[l];
+        } else {
+            const int k0 = l - 3, k1 = (k0 + 1) % 3;
+            dx = 0.5f * (wx[k0] + wx[k1]);
+            dy = 0.5f * (wy[k0] + wy[k1]);
+        }
+    } else {
+        const float4 v0 = M.v0f[e];
+        dx = (Xf.x - v0.x) + (Xf.z - v0.z);
+        dy = (Xf.y - v0.y) + (Xf.w - v0.w);
+    }
+    qx = dx - chx;
+    qy = dy - chy;
+    const float Q = fmaxf(fabsf(qx), fabsf(qy));
+    // |q - (p - v0)| <= eq: c^ bound, the node offset and its roundings, and
+    // the FP64 rounding of p itself
+    const float eq = F.eps_c + 2.0f * u * fmaxf(fmaxf(fabsf(dx), fabsf(dy)), E) + u * Q +
+                     2.98023223876953125e-08f;
+    const float EQ = E + Q;
+    const float bound = 8.0f * EQ * (eq + u * E) + 12.0f * u * EQ * EQ;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = (k + 1) % 3;
+        const float Dx = wx[k1] - wx[k], Dy = wy[k1] - wy[k];
+        float o, b;
+        if (l == k || l == k1 || l == 3 + k) {
+            // the node lies on this edge: orient = -(D x c^) exactly, whose
+            // error scales with |c^| rather than with the element size
+            o = Dy * chx - Dx * chy;
+            const float D = fmaxf(fabsf(Dx), fabsf(Dy));
+            b = 2.0f * (4.0f * D * F.eps_c + 12.0f * u * E * C + 6.0f * u * D * C) +
+                (l == 3 + k ? 12.0f * u * E * E : 0.0f) + 2.98023223876953125e-08f * D;
+        } else {
+            o = Dx * (qy - wy[k]) - Dy * (qx - wx[k]);
+            b = bound;
+        }
+        if (!(o > b)) return false;
+    }
+    return true;
 }
 
 } // namespace alelb

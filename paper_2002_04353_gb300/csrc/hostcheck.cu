@@ -55,3 +55,73 @@ extern "C" int alelb_hostcheck_inside(const alelb_mesh_desc *d, int n, const int
     }
     return ALELB_OK;
 }
+
+
+// The FP32-deviation propagation's element decisions on the host: the cache
+// is what an exact walk at t_prev leaves (each population's element), then
+// every population at t takes the fast decision where it applies and the
+// walk elsewhere.  fast[] marks the populations the fast path settled.
+extern "C" int alelb_hostcheck_fast(const alelb_mesh_desc *d, double t_prev, double t, int32_t *elem,
+                                    int8_t *kind, int8_t *fast)
+{
+    HostTables T;
+    std::string err;
+    alelb_status st = build_tables(d, T, err);
+    if (st != ALELB_OK) return st;
+    MeshDev M = T.host_view();
+    MapStatic MS = T.host_map();
+    const int N = T.N;
+    std::vector<int> cache((size_t)9 * N, -1);
+    int e = 0;
+    {
+        MapScalars sc = map_scalars(T.mkind, T.mp, t_prev);
+        for (int a = 0; a < N; ++a) {
+            const double2 Xa = M.X[a];
+            double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+            map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+            mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, false, wx, wy);
+            const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            for (int i = 0; i < NQ; ++i) {
+                double chx, chy, px, py;
+                departure(a11, a12, a21, a22, wx, wy, CXh[i], CYh[i], Xa.x, Xa.y, chx, chy, px, py);
+                if (chx == 0.0 && chy == 0.0) continue;
+                Loc L = walk(M, a, Xa.x, Xa.y, px, py, &e);
+                if (L.e >= 0 && L.vnode < 0) cache[(size_t)i * N + a] = L.e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
+            }
+        }
+    }
+    MapScalars sc = map_scalars(T.mkind, T.mp, t);
+    MapScalarsF sf;
+    sf.s = (float)sc.s;
+    sf.sd = (float)sc.sd;
+    sf.vy = (float)sc.vy;
+    sf.c = (float)sc.c;
+    sf.sn = (float)sc.sn;
+    sf.thd = (float)sc.thd;
+    sf.cm = (float)sc.cm;
+    sf.Xc = (float)T.mp[3];
+    sf.Yc = (float)T.mp[4];
+    for (int a = 0; a < N; ++a) {
+        int e9[NQ];
+        int8_t k9[NQ];
+        locate_node(M, MS, sc, 0, a, e9, k9, &e);
+        const float4 Xf = M.Xf[a];
+        const FastMap F = fast_map(MS, sf, a, Xf);
+        const int o = T.node_new2old[a];
+        for (int i = 0; i < NQ; ++i) {
+            int ee;
+            float qx, qy;
+            bool f = F.ok && fast_decide(M, F, Xf, M.bdist[a], a, i, cache[(size_t)i * N + a], ee, qx, qy);
+            if (f) {
+                e9[i] = M.orig_elem[ee];
+                k9[i] = 0;
+            }
+            elem[(size_t)i * N + o] = e9[i];
+            kind[(size_t)i * N + o] = k9[i];
+            fast[(size_t)i * N + o] = f ? 1 : 0;
+        }
+    }
+    return e ? ALELB_ERR_LOCATE : ALELB_OK;
+}

@@ -84,93 +84,6 @@ __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const
     KY = (-x_eta * sxi + x_xi * seta) / detJ;
 }
 
-// Bound of the FP32 transformed velocities c^_i against the FP64 canonical
-// ones, from the FP32 metrics themselves (u = 2^-24):
-//   entries of g:   eps_g   = 16u (1 + G),  G = max |g_ij|
-//   det g:          eps_det = 4 G eps_g + 3u (|x_X y_Y| + |y_X x_Y|)
-//   A = g^{-1,T}:   eps_A   = (eps_g + G eps_det / det) / det + 2u max|A|
-//   V_G:            eps_V   = 8u Vmag (Vmag: sum of the magnitudes entering V)
-//   c^ = A c - A V: eps_c   = 2 [eps_A (2 + 2|V|) + 2 max|A| eps_V + 6u max|A| (2 + 2|V|)]
-struct FastMap {
-    float A11, A12, A21, A22, W1, W2, eps_c;
-    bool ok;
-};
-
-__device__ __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF &sf, int a,
-                                            float4 Xf)
-{
-    const float u = 5.9604644775390625e-08f;
-    float xX, xY, yX, yY, Vx, Vy;
-    map_node_f32(MS, sf, a, Xf, xX, xY, yX, yY, Vx, Vy);
-    FastMap F;
-    float det = xX * yY - yX * xY;
-    float G = fmaxf(fmaxf(fabsf(xX), fabsf(xY)), fmaxf(fabsf(yX), fabsf(yY)));
-    float inv = 1.0f / det;
-    F.A11 = yY * inv;
-    F.A12 = -xY * inv;
-    F.A21 = -yX * inv;
-    F.A22 = xX * inv;
-    F.W1 = F.A11 * Vx + F.A12 * Vy;
-    F.W2 = F.A21 * Vx + F.A22 * Vy;
-    float Amax = fmaxf(fmaxf(fabsf(F.A11), fabsf(F.A12)), fmaxf(fabsf(F.A21), fabsf(F.A22)));
-    float Vmax = fmaxf(fabsf(Vx), fabsf(Vy));
-    float Vmag = fabsf(Vx) + fabsf(Vy);
-    if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE || MS.kind == MK_BLENDED) {
-        float dx = fabsf((Xf.x - sf.Xc) + Xf.z), dy = fabsf((Xf.y - sf.Yc) + Xf.w);
-        Vmag += fabsf(sf.thd) * (dx + dy) + fabsf(sf.vy);
-    }
-    float eps_g = 16.0f * u * (1.0f + G);
-    float eps_det = 4.0f * G * eps_g + 3.0f * u * (fabsf(xX * yY) + fabsf(yX * xY));
-    float eps_A = (eps_g + G * eps_det / det) / det + 2.0f * u * Amax;
-    float eps_V = 8.0f * u * Vmag;
-    float cv = 2.0f + 2.0f * Vmax;
-    F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
-    F.ok = det > 16.0f * eps_det && isfinite(F.eps_c);
-    return F;
-}
-
-// The fast path's decision for population i of a node: true (element e,
-// FP32 offset q from its first vertex) when the cached element c provably
-// holds the FP64 departure point strictly inside and the departure segment
-// cannot reach a boundary.
-// The segment node -> departure point cannot leave the mesh when it is
-// shorter than the node's distance to any boundary, or when the element is
-// one of the node's own (a triangle is convex and holds both ends).
-__device__ __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, float4 Xf,
-                                            float bdist, int a, int i, int c, int &e, float &qx,
-                                            float &qy)
-{
-    const float cx = (float)c_cx[i], cy = (float)c_cy[i];
-    const float chx = F.A11 * cx + F.A12 * cy - F.W1;
-    const float chy = F.A21 * cx + F.A22 * cy - F.W2;
-    const float len = sqrtf(chx * chx + chy * chy);
-    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eps_c)) return false;
-    e = c & 0x0fffffff;
-    if (!(len + F.eps_c < bdist)) {
-        const int *cn = M.conn + 6 * e;
-        if (!(cn[0] == a || cn[1] == a || cn[2] == a || cn[3] == a || cn[4] == a || cn[5] == a))
-            return false;
-    }
-    const float4 v0 = M.v0f[e];
-    const float4 ed = M.ejf[2 * e];
-    const float dx = (Xf.x - v0.x) + (Xf.z - v0.z);
-    const float dy = (Xf.y - v0.y) + (Xf.w - v0.w);
-    qx = dx - chx;
-    qy = dy - chy;
-    const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
-    const float Q = fmaxf(fabsf(qx), fabsf(qy));
-    // |q - (p - v0)| <= eq: c^ bound, the hi/lo difference and its
-    // roundings, and the FP64 rounding of p itself
-    const float eq = F.eps_c + 1.1920928955078125e-07f * fmaxf(fabsf(dx), fabsf(dy)) +
-                     5.9604644775390625e-08f * Q + 2.98023223876953125e-08f;
-    const float EQ = E + Q;
-    const float bound = 8.0f * EQ * eq + 1.9073486328125e-06f * EQ * EQ;
-    const float o0 = ed.x * qy - ed.y * qx;                               // orient(v0, v1, p)
-    const float o1 = (ed.x - qx) * (ed.w - qy) - (ed.y - qy) * (ed.z - qx); // orient(v1, v2, p)
-    const float o2 = ed.w * qx - ed.z * qy;                               // orient(v2, v0, p)
-    return o0 > bound && o1 > bound && o2 > bound;
-}
-
 // FAST (the FP32-deviation form): each population first tries the element
 // its departure point fell in at the previous step.  The departure offset
 // from that element's first vertex is formed in FP32 (map, c^ and the hi/lo

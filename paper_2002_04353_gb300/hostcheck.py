@@ -33,6 +33,8 @@ def lib():
                                                 C.c_char_p, C.c_int]
         _lib.alelb_hostcheck_inside.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                 C.c_void_p]
+        _lib.alelb_hostcheck_fast.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                              C.c_void_p]
     return _lib
 
 
@@ -83,3 +85,15 @@ def locate(mesh, motion, t, literal=False):
     st = lib().alelb_hostcheck_locate(C.byref(d), float(t), int(literal), e.ctypes.data, k.ctypes.data,
                                        err, 256)
     return st, e, k
+
+
+def locate_fast(mesh, motion, t_prev, t):
+    """Element decisions of the FP32-deviation propagation at time t with the
+    cache an exact walk at t_prev leaves; returns (status, elem, kind, fast)."""
+    d, keep = _desc(mesh, motion)
+    e = np.empty((9, mesh.n_nodes), dtype=np.int32)
+    k = np.empty((9, mesh.n_nodes), dtype=np.int8)
+    f = np.empty((9, mesh.n_nodes), dtype=np.int8)
+    st = lib().alelb_hostcheck_fast(C.byref(d), float(t_prev), float(t), e.ctypes.data, k.ctypes.data,
+                                    f.ctypes.data)
+    return st, e, k, f.astype(bool)

@@ -82,3 +82,21 @@ def test_fp32_filter_never_accepts_a_point_that_is_not_strictly_inside():
         assert not np.any(got & ~exact), "filter accepted a point that is not strictly inside"
         easy = np.array(easy) & exact
         assert got[easy].sum() >= 0.99 * easy.sum()  # and it does decide the clear-cut ones
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fast_path_decisions_match_oracle(name):
+    """The FP32-deviation propagation's decisions (previous-step element
+    verified in FP32 with certified bounds, exact walk otherwise), run on the
+    host, equal the oracle's element choices, and settle most populations."""
+    mk_mesh, mk_mot, times = CASES[name]
+    mesh, mot = mk_mesh(), mk_mot()
+    o = O.Oracle(mesh, mot, I.Flow())
+    for t in times[-2:]:
+        st, e, k, fast = H.locate_fast(mesh, mot, float(t) - 1.0, float(t))
+        assert st == 0
+        eo, ko = o.locate(float(t))
+        assert np.array_equal(e, eo), f"{name} t={t}: {np.sum(e != eo)} differ"
+        assert np.array_equal(k, ko)
+        if name != "lattice":  # on the lattice every departure point is a node
+            assert fast.mean() > 0.8, f"{name}: only {fast.mean():.3f} settled by the fast path"
