@@ -79,6 +79,9 @@ template <class T> void put_state(DevBuf &b, StateDev<T> &s, int N, cudaError_t 
     s.Dy = b.alloc<T>(N, st);
     s.cache = b.alloc<int>((size_t)9 * N, st);
     if (st == cudaSuccess) st = cudaMemset(s.cache, 0xff, (size_t)9 * N * sizeof(int)); // -1: empty
+    s.work = b.alloc<int>((size_t)9 * N, st);
+    s.wcount = b.alloc<unsigned>(1, st);
+    if (st == cudaSuccess) st = cudaMemset(s.wcount, 0, sizeof(unsigned));
 }
 
 
@@ -199,8 +202,9 @@ extern "C" alelb_status alelb_mesh_move(alelb_mesh *m, double t)
 // ============================================================================
 namespace {
 
-enum { KT_STREAM = 0, KT_DERIV1 = 1, KT_COLLIDE = 2, KT_N = 3 };
-const char *KT_NAMES[KT_N] = {"k_stream", "k_deriv1", "k_collide"};
+enum { KT_STREAM = 0, KT_FAST = 1, KT_SLOW = 2, KT_MOMENTS = 3, KT_DERIV1 = 4, KT_COLLIDE = 5, KT_N = 6 };
+const char *KT_NAMES[KT_N] = {"k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1",
+                              "k_collide"};
 
 // Reference and far-field populations computed on the device with the
 // same kernel code that the step uses.
@@ -326,8 +330,9 @@ struct alelb_solver {
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int k; cudaEvent_t a, b; };
     std::vector<Rec> pending;
-    double ms_acc[KT_N] = {0, 0, 0};
-    int64_t n_acc[KT_N] = {0, 0, 0};
+    double ms_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    int64_t n_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    int n_sm = 152;
 };
 
 namespace {
@@ -385,30 +390,55 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
     const bool phi = !(s->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF));
-    for (int k = 0; k < KT_N; ++k) {
-        if (k == KT_DERIV1 && !phi) continue;
+    const bool fast = s->prec == ALELB_PREC_FP32_DEV;
+    const MapScalarsF sf = to_f32(sc, m);
+    int seq[6], ns = 0;
+    if (fast) {
+        seq[ns++] = KT_FAST;
+        seq[ns++] = KT_SLOW;
+        seq[ns++] = KT_MOMENTS;
+    } else {
+        seq[ns++] = KT_STREAM;
+    }
+    if (phi) seq[ns++] = KT_DERIV1;
+    seq[ns++] = KT_COLLIDE;
+    for (int q = 0; q < ns; ++q) {
+        const int k = seq[q];
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (s->prof) {
             ea = get_event(s);
             eb = get_event(s);
             cudaEventRecord(ea, s->stream);
         }
-        if (k == KT_STREAM && s->prec == ALELB_PREC_FP32_DEV)
-            k_stream<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
-                                                                         st, s->d_err, s->d_stats);
-        else if (k == KT_STREAM)
-            k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
-                                                                          st, s->d_err, s->d_stats);
-        else if (k == KT_DERIV1 && s->prec == ALELB_PREC_FP32_DEV)
-            k_deriv1<S, A, true><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), st);
-        else if (k == KT_DERIV1)
-            k_deriv1<S, A, false><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), st);
-        else if (s->prec == ALELB_PREC_FP32_DEV)
-            k_collide<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
-                                                                          st, s->d_err);
-        else
-            k_collide<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
-                                                                           st, s->d_err);
+        switch (k) {
+        case KT_STREAM:
+            k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st,
+                                                                          s->d_err, s->d_stats);
+            break;
+        case KT_FAST:
+            k_stream_fast<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sf, K, st);
+            break;
+        case KT_SLOW:
+            k_stream_slow<S, A><<<4 * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err,
+                                                                    s->d_stats);
+            break;
+        case KT_MOMENTS:
+            k_moments<S, A><<<(N + 255) / 256, 256, 0, s->stream>>>(K, st, N, s->d_err);
+            break;
+        case KT_DERIV1:
+            if (fast)
+                k_deriv1<S, A, true><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, sf, st);
+            else
+                k_deriv1<S, A, false><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, sf, st);
+            break;
+        default:
+            if (fast)
+                k_collide<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st,
+                                                                              s->d_err);
+            else
+                k_collide<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st,
+                                                                               s->d_err);
+        }
         if (s->prof) {
             cudaEventRecord(eb, s->stream);
             s->pending.push_back({k, ea, eb});
@@ -483,6 +513,12 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
         s->own_stream = true;
     }
     const int N = m->T.N;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            s->n_sm = nsm;
+    }
     if (s->prec == ALELB_PREC_FP64) put_state(s->buf, s->sd, N, st);
     else put_state(s->buf, s->sf, N, st);
     s->d_consts = s->buf.alloc<double>(4 * NQ, st);

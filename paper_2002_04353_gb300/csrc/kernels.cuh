@@ -26,6 +26,8 @@ template <class S> struct StateDev {
     S *Dx, *Dy;           // first-pass results
     int *cache;           // [9 N] element of each population's previous departure point
                           // (elem | (sx+1)<<28 | (sy+1)<<30), -1 when empty
+    int *work;            // [9 N] populations (9 node + direction) left to the exact path
+    unsigned *wcount;     // number of entries in work
 };
 
 // d N_s / d xi and d N_s / d eta of the P2 triangle at the six node
@@ -266,6 +268,206 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
     A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
     A k3 = A(1) - A(3) * T;
+    st.Qx[a] = (S)(rho * ux * k3 - rho * ux * ux * ux);
+    st.Qy[a] = (S)(rho * uy * k3 - rho * uy * uy * uy);
+    st.mrt[a] = (S)(K.mu / (rho * T));
+}
+
+// ---------------------------------------------------------------------------
+// The FP32-deviation propagation, split by path so that the rare exact
+// work does not stall the warps of the common case:
+//   k_stream_fast  per node: FP32 map; every population whose previous-step
+//                  element is verified (fast_decide) is interpolated and
+//                  stored; the others are appended to a work list
+//   k_stream_slow  per listed population: FP64 map and departure point,
+//                  exact walk, interpolation or the missing-population
+//                  condition (Sec. IV.A); refreshes the element cache
+//   k_moments      per node: moments, Q'_aaa and mu/(rho T) of the streamed
+//                  populations; resets the work list
+// ---------------------------------------------------------------------------
+template <class S, class A>
+__global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
+                                                     KinParams<A> K, StateDev<S> st)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = M.N;
+    const bool valid = a < N;
+    unsigned slow = 0;
+    if (valid) {
+        const float4 Xf = M.Xf[a];
+        const float bd = M.bdist[a];
+        FastMap F = fast_map(MS, sf, a, Xf);
+        if (K.flags & FLAG_LITERAL_VG) F.ok = false;
+        int cache[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) cache[i] = st.cache[i * N + a];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            int e;
+            float qx, qy;
+            if (F.ok && fast_decide(M, F, Xf, bd, a, i, cache[i], e, qx, qy)) {
+                const float4 J = M.ejf[2 * e + 1];
+                A Nw[6];
+                shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
+                A fi = 0, gi = 0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int b = M.conn[6 * e + k];
+                    fi += Nw[k] * (A)st.post[i * N + b];
+                    gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                }
+                st.str[i * N + a] = (S)fi;
+                st.str[(NQ + i) * N + a] = (S)gi;
+            } else {
+                slow |= 1u << i;
+            }
+        }
+    }
+    // warp-aggregated append of the remaining populations
+    const unsigned lane = threadIdx.x & 31u;
+    const int n = __popc(slow);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(st.wcount, (unsigned)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned pos = base + (unsigned)(incl - n);
+    while (slow) {
+        const int i = __ffs(slow) - 1;
+        slow &= slow - 1;
+        st.work[pos++] = a * NQ + i;
+    }
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
+                                                     KinParams<A> K, StateDev<S> st, int *err,
+                                                     unsigned long long *stats)
+{
+    const unsigned n = *st.wcount;
+    const int N = M.N;
+    if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x) {
+        const int code = st.work[w];
+        const int a = code / NQ, i = code % NQ;
+        const double2 Xa = M.X[a];
+        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
+        double chx, chy, px, py;
+        departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx, chy,
+                  px, py);
+        A fi = 0, gi = 0;
+        int src = -1;
+        if (chx == 0.0 && chy == 0.0) {
+            src = a;
+        } else {
+            const Loc L = walk(M, a, Xa.x, Xa.y, px, py, err);
+            if (L.e == -2) {
+                src = a;
+            } else if (L.e >= 0 && L.vnode >= 0) {
+                src = L.vnode;
+            } else if (L.e >= 0) {
+                const int e = L.e;
+                st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
+                const double2 v0 = M.ev[3 * e];
+                const float qx = (float)(px - (L.sx ? v0.x + L.sx * M.Lx : v0.x));
+                const float qy = (float)(py - (L.sy ? v0.y + L.sy * M.Ly : v0.y));
+                const float4 J = M.ejf[2 * e + 1];
+                A Nw[6];
+                shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int b = M.conn[6 * e + k];
+                    fi += Nw[k] * (A)st.post[i * N + b];
+                    gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                }
+            } else if (L.kind == 2) {
+                fi = K.finf[i];
+                gi = K.ginf[i];
+            } else {
+                // missing population (Sec. IV.A): targets and first-order
+                // gradients of the previous-step fields at this node
+                A rt, uxt, uyt, Tt;
+                const int wi = M.wall_idx[a];
+                if (wi >= 0) {
+                    const int pe = M.probe_e[wi];
+                    const double2 pxi = M.probe_xi[wi];
+                    A Nw[6];
+                    shape6<A>((A)pxi.x, (A)pxi.y, Nw);
+                    A r = 0, t = 0;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const int b = M.conn[6 * pe + k];
+                        r += Nw[k] * (A)st.rho[b];
+                        t += Nw[k] * (A)st.T[b];
+                    }
+                    rt = r;
+                    Tt = t;
+                    uxt = (A)Vx;
+                    uyt = (A)Vy;
+                } else {
+                    rt = (A)st.rho[a];
+                    uxt = (A)st.ux[a];
+                    uyt = (A)st.uy[a];
+                    Tt = (A)st.T[a];
+                }
+                A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
+                if (!(K.flags & FLAG_BC_EQ)) {
+                    double KX, KY;
+                    owner_grad_linear(M, a, st.ux, KX, KY);
+                    du[0] = (A)(a11 * KX + a21 * KY);
+                    du[1] = (A)(a12 * KX + a22 * KY);
+                    owner_grad_linear(M, a, st.uy, KX, KY);
+                    du[2] = (A)(a11 * KX + a21 * KY);
+                    du[3] = (A)(a12 * KX + a22 * KY);
+                    owner_grad_linear(M, a, st.T, KX, KY);
+                    dT[0] = (A)(a11 * KX + a21 * KY);
+                    dT[1] = (A)(a12 * KX + a22 * KY);
+                }
+                A fm[NQ], gm[NQ];
+                grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+                fi = fm[i];
+                gi = gm[i];
+            }
+        }
+        if (src >= 0) {
+            fi = (A)st.post[i * N + src];
+            gi = (A)st.post[(NQ + i) * N + src];
+        }
+        st.str[i * N + a] = (S)fi;
+        st.str[(NQ + i) * N + a] = (S)gi;
+    }
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st, int N, int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a == 0) *st.wcount = 0u; // the work list has been consumed
+    if (a >= N) return;
+    A f[NQ], g[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        f[i] = (A)st.str[i * N + a];
+        g[i] = (A)st.str[(NQ + i) * N + a];
+    }
+    const A sf = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const A jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+    const A sg = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    const A rho = K.rho_ref + sf;
+    const A ux = jx / rho, uy = jy / rho;
+    const A E = (K.E2_ref + sg) / (A(2) * rho);
+    const A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
+    if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
+    const A k3 = A(1) - A(3) * T;
     st.Qx[a] = (S)(rho * ux * k3 - rho * ux * ux * ux);
     st.Qy[a] = (S)(rho * uy * k3 - rho * uy * uy * uy);
     st.mrt[a] = (S)(K.mu / (rho * T));
