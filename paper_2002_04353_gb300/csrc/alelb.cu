@@ -128,6 +128,7 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.bdist = B.put(T.bdist, st);
     D.Xf = B.put(T.Xf, st);
     D.v0f = B.put(T.v0f, st);
+    D.evf = B.put(T.evf, st);
     m->d_wedges = B.put(T.wedges, st);
     m->nw = (int)T.wedges.size();
     m->mst = T.host_map();
@@ -419,7 +420,7 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
             k_stream_fast<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sf, K, st);
             break;
         case KT_SLOW:
-            k_stream_slow<S, A><<<4 * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err,
+            k_stream_slow<S, A><<<4 * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st, s->d_err,
                                                                     s->d_stats);
             break;
         case KT_MOMENTS:

@@ -363,6 +363,7 @@ struct MeshDev {
     const float *bdist;    // [N] lower bound of the node's distance to the nearest boundary edge
     const float4 *Xf;      // [N] node coordinates split hi + lo in FP32 (xh, yh, xl, yl)
     const float4 *v0f;     // [E] first frame vertex split hi + lo in FP32
+    const float4 *evf;     // [3E] all frame vertices split hi + lo in FP32
 };
 
 struct Loc {
@@ -397,6 +398,23 @@ ALELB_HD __forceinline__ int fan_best(const MeshDev &M, int v)
 
 constexpr int WALK_LIMIT = 256;
 
+// Orientation provider of the walk: exact FP64 predicates on the FP64
+// departure point p and the element frames.
+struct Pred64 {
+    const MeshDev *M;
+    double Xa, Ya, px, py;
+    double w[6];
+    ALELB_HD void load(int e, int sx, int sy) { load_frame(*M, e, sx, sy, w); }
+    // orient(w_k1, w_k2, p) of the loaded element
+    ALELB_HD int vvp(int k1, int k2)
+    {
+        return orient(w[2 * k1], w[2 * k1 + 1], w[2 * k2], w[2 * k2 + 1], px, py);
+    }
+    // orient(X_a, p, w_k) of the loaded element
+    ALELB_HD int avp(int k) { return orient(Xa, Ya, px, py, w[2 * k], w[2 * k + 1]); }
+    ALELB_HD bool p_is_node() const { return px == Xa && py == Ya; }
+};
+
 // Straight-line walk from node a along the segment X_a -> p through the
 // element adjacency (reading of Sec. III's departure-point search: the
 // paper does not name a search).  A population is missing when the walk
@@ -404,15 +422,14 @@ constexpr int WALK_LIMIT = 256;
 // fan holds the first piece of the segment.  A line through a vertex is
 // treated as passing to the vertex's right.  Ties (p on an edge or vertex)
 // go to the containing element of larger computational area, then lower
-// original id.
-ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
-                    int *err)
+// original id.  P supplies the orientation signs, always exact.
+template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
 {
     Loc r;
     r.kind = 0;
     r.vnode = -1;
     r.sx = r.sy = 0;
-    if (px == Xa && py == Ya) {
+    if (pr.p_is_node()) {
         // a nonzero but negligible c^ that rounds away: the departure point
         // is the node itself, held by every element of its fan
         r.e = fan_best(M, a);
@@ -421,19 +438,17 @@ ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, do
     }
     int beg = M.fan_ptr[a], end = M.fan_ptr[a + 1];
     int e = -1, loc = 0, sx = 0, sy = 0;
-    double w[6];
     for (int k = beg; k < end; ++k) {
         int2 fe = M.fan[k];
         int ll = fe.y & 15, ssx = ((fe.y >> 4) & 3) - 1, ssy = ((fe.y >> 6) & 3) - 1;
-        load_frame(M, fe.x, ssx, ssy, w);
+        pr.load(fe.x, ssx, ssy);
         bool hit;
         if (ll < 3) {
             int k1 = (ll + 1) % 3, k2 = (ll + 2) % 3;
-            hit = orient(w[2 * ll], w[2 * ll + 1], w[2 * k1], w[2 * k1 + 1], px, py) >= 0 &&
-                  orient(w[2 * ll], w[2 * ll + 1], w[2 * k2], w[2 * k2 + 1], px, py) < 0;
+            hit = pr.vvp(ll, k1) >= 0 && pr.vvp(ll, k2) < 0;
         } else {
             int k0 = ll - 3, k1 = (k0 + 1) % 3;
-            hit = orient(w[2 * k0], w[2 * k0 + 1], w[2 * k1], w[2 * k1 + 1], px, py) >= 0;
+            hit = pr.vvp(k0, k1) >= 0;
         }
         if (hit) {
             e = fe.x;
@@ -455,19 +470,16 @@ ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, do
     }
     int o[3];
     int kout;
-    load_frame(M, e, sx, sy, w);
+    pr.load(e, sx, sy);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int k1 = (k + 1) % 3;
-        o[k] = orient(w[2 * k], w[2 * k + 1], w[2 * k1], w[2 * k1 + 1], px, py);
-    }
+    for (int k = 0; k < 3; ++k) o[k] = pr.vvp(k, (k + 1) % 3);
     bool found = o[0] >= 0 && o[1] >= 0 && o[2] >= 0;
     if (!found) {
         if (loc < 3) {
             kout = (loc + 1) % 3;
         } else {
             int k0 = loc - 3, k2 = (k0 + 2) % 3;
-            kout = orient(Xa, Ya, px, py, w[2 * k2], w[2 * k2 + 1]) >= 0 ? (k0 + 1) % 3 : k2;
+            kout = pr.avp(k2) >= 0 ? (k0 + 1) % 3 : k2;
         }
         int step = 0;
         for (; step < WALK_LIMIT; ++step) {
@@ -482,10 +494,10 @@ ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, do
             sx += (int)((inf >> 4) & 3) - 1;
             sy += (int)((inf >> 6) & 3) - 1;
             e = M.nbr[3 * e + kout];
-            load_frame(M, e, sx, sy, w);
+            pr.load(e, sx, sy);
             int k1 = (kin + 1) % 3, k2 = (kin + 2) % 3;
-            int o1 = orient(w[2 * k1], w[2 * k1 + 1], w[2 * k2], w[2 * k2 + 1], px, py);
-            int o2 = orient(w[2 * k2], w[2 * k2 + 1], w[2 * kin], w[2 * kin + 1], px, py);
+            int o1 = pr.vvp(k1, k2);
+            int o2 = pr.vvp(k2, kin);
             if (o1 >= 0 && o2 >= 0) {
                 o[kin] = 1;
                 o[k1] = o1;
@@ -493,7 +505,7 @@ ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, do
                 found = true;
                 break;
             }
-            kout = orient(Xa, Ya, px, py, w[2 * k2], w[2 * k2 + 1]) >= 0 ? k1 : k2;
+            kout = pr.avp(k2) >= 0 ? k1 : k2;
         }
         if (!found) {
             set_err(err, ERR_LOCATE);
@@ -522,6 +534,18 @@ ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, do
     r.sx = sx;
     r.sy = sy;
     return r;
+}
+
+ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
+                               int *err)
+{
+    Pred64 pr;
+    pr.M = &M;
+    pr.Xa = Xa;
+    pr.Ya = Ya;
+    pr.px = px;
+    pr.py = py;
+    return walk_t(M, pr, a, err);
 }
 
 // Local coordinates (xi, eta) of p in element e (frame shift sx, sy).
@@ -605,7 +629,7 @@ ALELB_HD __forceinline__ bool strictly_inside_f32(const MeshDev &M, int e, int s
 //   V_G:            eps_V   = 8u Vmag (Vmag: sum of the magnitudes entering V)
 //   c^ = A c - A V: eps_c   = 2 [eps_A (2 + 2|V|) + 2 max|A| eps_V + 6u max|A| (2 + 2|V|)]
 struct FastMap {
-    float A11, A12, A21, A22, W1, W2, eps_c;
+    float A11, A12, A21, A22, W1, W2, eps_c, Vx, Vy;
     bool ok;
 };
 
@@ -625,6 +649,8 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     F.A22 = xX * inv;
     F.W1 = F.A11 * Vx + F.A12 * Vy;
     F.W2 = F.A21 * Vx + F.A22 * Vy;
+    F.Vx = Vx;
+    F.Vy = Vy;
     float Amax = fmaxf(fmaxf(fabsf(F.A11), fabsf(F.A12)), fmaxf(fabsf(F.A21), fabsf(F.A22)));
     float Vmax = fmaxf(fabsf(Vx), fabsf(Vy));
     float Vmag = fabsf(Vx) + fabsf(Vy);
@@ -722,6 +748,211 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         if (!(o > b)) return false;
     }
     return true;
+}
+
+// Certified FP32 sign of orient(A, B, C) = (A - C) x (B - C) from
+// approximations of A, B, C with per-coordinate error bounds ea, eb, ec:
+// +1 or -1 when certain, 0 when the exact predicate must decide.
+ALELB_HD __forceinline__ int orient3_f32(float ax, float ay, float ea, float bx, float by, float eb,
+                                         float cx, float cy, float ec)
+{
+    const float u = 5.9604644775390625e-08f;
+    const float d1x = ax - cx, d1y = ay - cy, d2x = bx - cx, d2y = by - cy;
+    const float D1 = fmaxf(fabsf(d1x), fabsf(d1y)), D2 = fmaxf(fabsf(d2x), fabsf(d2y));
+    const float e1 = ea + ec + u * D1, e2 = eb + ec + u * D2;
+    const float o = d1x * d2y - d1y * d2x;
+    const float bound = 4.0f * (D1 * e2 + D2 * e1 + e1 * e2) + 8.0f * u * D1 * D2;
+    if (o > bound) return 1;
+    if (o < -bound) return -1;
+    return 0;
+}
+
+// Orientation provider of the walk in FP32: every point relative to the
+// node, the departure point from the FP32 c^ (bound eps_c), element
+// vertices from their hi/lo splits.  Uncertain signs fall back to the exact
+// FP64 predicate on the FP64 canonical departure point, computed lazily.
+struct Pred32 {
+    const MeshDev *M;
+    const MapStatic *MS;
+    const MapScalars *sc;
+    int a, i, literal;
+    float4 Xf;
+    float rpx, rpy, ep;
+    int e, sx, sy;
+    float rx[3], ry[3], er[3];
+    bool have64, wload;
+    double Xa, Ya, px, py;
+    double w[6];
+
+    ALELB_HD void load(int e_, int sx_, int sy_)
+    {
+        const float u = 5.9604644775390625e-08f;
+        e = e_;
+        sx = sx_;
+        sy = sy_;
+        wload = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = M->evf[3 * e + k];
+            const float hx = v.x - Xf.x, hy = v.y - Xf.y;
+            float x = hx + (v.z - Xf.z), y = hy + (v.w - Xf.w);
+            float sh = 0.0f;
+            if (sx) {
+                x += (float)sx * (float)M->Lx;
+                sh = fabsf((float)M->Lx);
+            }
+            if (sy) {
+                y += (float)sy * (float)M->Ly;
+                sh = fmaxf(sh, fabsf((float)M->Ly));
+            }
+            rx[k] = x;
+            ry[k] = y;
+            er[k] = 4.0f * u * (fmaxf(fabsf(x), fabsf(y)) + fmaxf(fabsf(hx), fabsf(hy)) + sh) +
+                    9.313225746154785e-10f;
+        }
+    }
+    ALELB_HD void ensure64()
+    {
+        if (!have64) {
+            double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy, chx, chy;
+            const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            map_node(*MS, *sc, a, Xa, Ya, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+            mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
+            departure(a11, a12, a21, a22, wx, wy, CXh[i], CYh[i], Xa, Ya, chx, chy, px, py);
+            have64 = true;
+        }
+        if (!wload) {
+            load_frame(*M, e, sx, sy, w);
+            wload = true;
+        }
+    }
+    ALELB_HD int vvp(int k1, int k2)
+    {
+        const int s = orient3_f32(rx[k1], ry[k1], er[k1], rx[k2], ry[k2], er[k2], rpx, rpy, ep);
+        if (s) return s;
+        ensure64();
+        return orient(w[2 * k1], w[2 * k1 + 1], w[2 * k2], w[2 * k2 + 1], px, py);
+    }
+    ALELB_HD int avp(int k)
+    {
+        const int s = orient3_f32(0.0f, 0.0f, 0.0f, rpx, rpy, ep, rx[k], ry[k], er[k]);
+        if (s) return s;
+        ensure64();
+        return orient(Xa, Ya, px, py, w[2 * k], w[2 * k + 1]);
+    }
+    ALELB_HD bool p_is_node() const { return false; } // the caller ensures |c^| > 4 eps_c
+};
+
+// The exact element decision of population i of node a in the
+// FP32-deviation form, when the verified previous-step element did not
+// settle it: the walk on certified FP32 predicates (exact fallback) when
+// the FP32 map is usable and c^ is clearly nonzero, else on FP64 ones.
+// Returns the walk's Loc; for an interior element, q = p - v0 in FP32.
+// src >= 0: the population takes node src's value as is.
+ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
+                                         const MapScalars &sc, const FastMap &F, float4 Xf, int a,
+                                         int i, int literal, float &qx, float &qy, int &src,
+                                         int *err)
+{
+    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double2 Xa = M.X[a];
+    src = -1;
+    Loc L;
+    bool done = false;
+    if (F.ok && !literal) {
+        const float cx = (float)CXh[i], cy = (float)CYh[i];
+        const float chx = F.A11 * cx + F.A12 * cy - F.W1;
+        const float chy = F.A21 * cx + F.A22 * cy - F.W2;
+        if (sqrtf(chx * chx + chy * chy) > 4.0f * F.eps_c) {
+            Pred32 pr;
+            pr.M = &M;
+            pr.MS = &MS;
+            pr.sc = &sc;
+            pr.a = a;
+            pr.i = i;
+            pr.literal = literal;
+            pr.Xf = Xf;
+            pr.rpx = -chx;
+            pr.rpy = -chy;
+            pr.ep = F.eps_c + 9.313225746154785e-10f;
+            pr.have64 = false;
+            pr.wload = false;
+            pr.Xa = Xa.x;
+            pr.Ya = Xa.y;
+            L = walk_t(M, pr, a, err);
+            if (L.e >= 0 && L.vnode < 0) {
+                const float4 v = M.evf[3 * L.e];
+                float x0 = (v.x - Xf.x) + (v.z - Xf.z), y0 = (v.y - Xf.y) + (v.w - Xf.w);
+                if (L.sx) x0 += (float)L.sx * (float)M.Lx;
+                if (L.sy) y0 += (float)L.sy * (float)M.Ly;
+                qx = -chx - x0;
+                qy = -chy - y0;
+            }
+            done = true;
+        }
+    }
+    if (!done) {
+        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy, chx, chy, px, py;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
+        departure(a11, a12, a21, a22, wx, wy, CXh[i], CYh[i], Xa.x, Xa.y, chx, chy, px, py);
+        if (chx == 0.0 && chy == 0.0) {
+            L.e = -2;
+            L.vnode = -1;
+            L.kind = 0;
+            L.sx = L.sy = 0;
+            src = a;
+            return L;
+        }
+        L = walk(M, a, Xa.x, Xa.y, px, py, err);
+        if (L.e >= 0 && L.vnode < 0) {
+            const double2 v0 = M.ev[3 * L.e];
+            qx = (float)(px - (L.sx ? v0.x + L.sx * M.Lx : v0.x));
+            qy = (float)(py - (L.sy ? v0.y + L.sy * M.Ly : v0.y));
+        }
+    }
+    if (L.e == -2) src = a;
+    else if (L.e >= 0 && L.vnode >= 0) src = L.vnode;
+    return L;
+}
+
+// Element decisions of the FP32-deviation propagation for the nine
+// populations of node a, given the element cache (parity report and host
+// emulation): the fast decision where it applies, slow_decide elsewhere.
+ALELB_HD inline void mixed_locate_node(const MeshDev &M, const MapStatic &MS,
+                                       const MapScalars &sc, const MapScalarsF &sf,
+                                       const int *cache, int a, int *elem9, int8_t *kind9,
+                                       int8_t *fast9, int *err)
+{
+    const float4 Xf = M.Xf[a];
+    const FastMap F = fast_map(MS, sf, a, Xf);
+    for (int i = 0; i < NQ; ++i) {
+        int e;
+        float qx, qy;
+        const bool f = F.ok && fast_decide(M, F, Xf, M.bdist[a], a, i, cache[(size_t)i * M.N + a], e, qx, qy);
+        if (fast9) fast9[i] = f ? 1 : 0;
+        if (f) {
+            elem9[i] = M.orig_elem[e];
+            kind9[i] = 0;
+            continue;
+        }
+        int src;
+        const Loc L = slow_decide(M, MS, sc, F, Xf, a, i, 0, qx, qy, src, err);
+        if (L.e == -2 && src == a && L.vnode < 0) {
+            elem9[i] = -2;
+            kind9[i] = 0;
+        } else if (L.e >= 0) {
+            elem9[i] = M.orig_elem[L.vnode >= 0 ? fan_best(M, L.vnode) : L.e];
+            kind9[i] = 0;
+        } else {
+            elem9[i] = -1;
+            kind9[i] = (int8_t)L.kind;
+        }
+    }
 }
 
 } // namespace alelb

@@ -105,22 +105,13 @@ extern "C" int alelb_hostcheck_fast(const alelb_mesh_desc *d, double t_prev, dou
     sf.Yc = (float)T.mp[4];
     for (int a = 0; a < N; ++a) {
         int e9[NQ];
-        int8_t k9[NQ];
-        locate_node(M, MS, sc, 0, a, e9, k9, &e);
-        const float4 Xf = M.Xf[a];
-        const FastMap F = fast_map(MS, sf, a, Xf);
+        int8_t k9[NQ], f9[NQ];
+        mixed_locate_node(M, MS, sc, sf, cache.data(), a, e9, k9, f9, &e);
         const int o = T.node_new2old[a];
         for (int i = 0; i < NQ; ++i) {
-            int ee;
-            float qx, qy;
-            bool f = F.ok && fast_decide(M, F, Xf, M.bdist[a], a, i, cache[(size_t)i * N + a], ee, qx, qy);
-            if (f) {
-                e9[i] = M.orig_elem[ee];
-                k9[i] = 0;
-            }
             elem[(size_t)i * N + o] = e9[i];
             kind[(size_t)i * N + o] = k9[i];
-            fast[(size_t)i * N + o] = f ? 1 : 0;
+            fast[(size_t)i * N + o] = f9[i];
         }
     }
     return e ? ALELB_ERR_LOCATE : ALELB_OK;

@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, Ma
 
 template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
-                                                     KinParams<A> K, StateDev<S> st, int *err,
-                                                     unsigned long long *stats)
+                                                     MapScalarsF sf, KinParams<A> K, StateDev<S> st,
+                                                     int *err, unsigned long long *stats)
 {
     const unsigned n = *st.wcount;
     const int N = M.N;
@@ -355,91 +355,96 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
     for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x) {
         const int code = st.work[w];
         const int a = code / NQ, i = code % NQ;
-        const double2 Xa = M.X[a];
-        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
-        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
-        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-        mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
-        double chx, chy, px, py;
-        departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx, chy,
-                  px, py);
+        const float4 Xf = M.Xf[a];
+        const FastMap F = fast_map(MS, sf, a, Xf);
+        const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
+        float qx = 0.f, qy = 0.f;
+        int src;
+        const Loc L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err);
         A fi = 0, gi = 0;
-        int src = -1;
-        if (chx == 0.0 && chy == 0.0) {
-            src = a;
-        } else {
-            const Loc L = walk(M, a, Xa.x, Xa.y, px, py, err);
-            if (L.e == -2) {
-                src = a;
-            } else if (L.e >= 0 && L.vnode >= 0) {
-                src = L.vnode;
-            } else if (L.e >= 0) {
-                const int e = L.e;
-                st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
-                const double2 v0 = M.ev[3 * e];
-                const float qx = (float)(px - (L.sx ? v0.x + L.sx * M.Lx : v0.x));
-                const float qy = (float)(py - (L.sy ? v0.y + L.sy * M.Ly : v0.y));
-                const float4 J = M.ejf[2 * e + 1];
-                A Nw[6];
-                shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const int b = M.conn[6 * e + k];
-                    fi += Nw[k] * (A)st.post[i * N + b];
-                    gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
-                }
-            } else if (L.kind == 2) {
-                fi = K.finf[i];
-                gi = K.ginf[i];
-            } else {
-                // missing population (Sec. IV.A): targets and first-order
-                // gradients of the previous-step fields at this node
-                A rt, uxt, uyt, Tt;
-                const int wi = M.wall_idx[a];
-                if (wi >= 0) {
-                    const int pe = M.probe_e[wi];
-                    const double2 pxi = M.probe_xi[wi];
-                    A Nw[6];
-                    shape6<A>((A)pxi.x, (A)pxi.y, Nw);
-                    A r = 0, t = 0;
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        const int b = M.conn[6 * pe + k];
-                        r += Nw[k] * (A)st.rho[b];
-                        t += Nw[k] * (A)st.T[b];
-                    }
-                    rt = r;
-                    Tt = t;
-                    uxt = (A)Vx;
-                    uyt = (A)Vy;
-                } else {
-                    rt = (A)st.rho[a];
-                    uxt = (A)st.ux[a];
-                    uyt = (A)st.uy[a];
-                    Tt = (A)st.T[a];
-                }
-                A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
-                if (!(K.flags & FLAG_BC_EQ)) {
-                    double KX, KY;
-                    owner_grad_linear(M, a, st.ux, KX, KY);
-                    du[0] = (A)(a11 * KX + a21 * KY);
-                    du[1] = (A)(a12 * KX + a22 * KY);
-                    owner_grad_linear(M, a, st.uy, KX, KY);
-                    du[2] = (A)(a11 * KX + a21 * KY);
-                    du[3] = (A)(a12 * KX + a22 * KY);
-                    owner_grad_linear(M, a, st.T, KX, KY);
-                    dT[0] = (A)(a11 * KX + a21 * KY);
-                    dT[1] = (A)(a12 * KX + a22 * KY);
-                }
-                A fm[NQ], gm[NQ];
-                grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
-                fi = fm[i];
-                gi = gm[i];
-            }
-        }
         if (src >= 0) {
             fi = (A)st.post[i * N + src];
             gi = (A)st.post[(NQ + i) * N + src];
+        } else if (L.e >= 0) {
+            const int e = L.e;
+            st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
+            const float4 J = M.ejf[2 * e + 1];
+            A Nw[6];
+            shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int b = M.conn[6 * e + k];
+                fi += Nw[k] * (A)st.post[i * N + b];
+                gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+            }
+        } else if (L.kind == 2) {
+            fi = K.finf[i];
+            gi = K.ginf[i];
+        } else {
+            // missing population (Sec. IV.A): targets and first-order
+            // gradients of the previous-step fields at this node, with the
+            // FP32 metrics when usable
+            float a11, a12, a21, a22, Vx, Vy;
+            if (F.ok) {
+                a11 = F.A11;
+                a12 = F.A12;
+                a21 = F.A21;
+                a22 = F.A22;
+                Vx = F.Vx;
+                Vy = F.Vy;
+            } else {
+                const double2 Xa = M.X[a];
+                double xX, xY, yX, yY, vx, vy, b11, b12, b21, b22;
+                map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, vx, vy);
+                metric_inverse_T(xX, xY, yX, yY, b11, b12, b21, b22);
+                a11 = (float)b11;
+                a12 = (float)b12;
+                a21 = (float)b21;
+                a22 = (float)b22;
+                Vx = (float)vx;
+                Vy = (float)vy;
+            }
+            A rt, uxt, uyt, Tt;
+            const int wi = M.wall_idx[a];
+            if (wi >= 0) {
+                const int pe = M.probe_e[wi];
+                const double2 pxi = M.probe_xi[wi];
+                A Nw[6];
+                shape6<A>((A)pxi.x, (A)pxi.y, Nw);
+                A r = 0, t = 0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int b = M.conn[6 * pe + k];
+                    r += Nw[k] * (A)st.rho[b];
+                    t += Nw[k] * (A)st.T[b];
+                }
+                rt = r;
+                Tt = t;
+                uxt = (A)Vx;
+                uyt = (A)Vy;
+            } else {
+                rt = (A)st.rho[a];
+                uxt = (A)st.ux[a];
+                uyt = (A)st.uy[a];
+                Tt = (A)st.T[a];
+            }
+            A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
+            if (!(K.flags & FLAG_BC_EQ)) {
+                double KX, KY;
+                owner_grad_linear(M, a, st.ux, KX, KY);
+                du[0] = (A)(a11 * (float)KX + a21 * (float)KY);
+                du[1] = (A)(a12 * (float)KX + a22 * (float)KY);
+                owner_grad_linear(M, a, st.uy, KX, KY);
+                du[2] = (A)(a11 * (float)KX + a21 * (float)KY);
+                du[3] = (A)(a12 * (float)KX + a22 * (float)KY);
+                owner_grad_linear(M, a, st.T, KX, KY);
+                dT[0] = (A)(a11 * (float)KX + a21 * (float)KY);
+                dT[1] = (A)(a12 * (float)KX + a22 * (float)KY);
+            }
+            A fm[NQ], gm[NQ];
+            grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+            fi = fm[i];
+            gi = gm[i];
         }
         st.str[i * N + a] = (S)fi;
         st.str[(NQ + i) * N + a] = (S)gi;
@@ -585,17 +590,10 @@ __global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, MapScalarsF sf,
     if (a >= N) return;
     int e9[NQ];
     int8_t k9[NQ];
-    locate_node(M, MS, sc, flags & FLAG_LITERAL_VG, a, e9, k9, err);
     if (cache && !(flags & FLAG_LITERAL_VG)) {
-        const float4 Xf = M.Xf[a];
-        const FastMap F = fast_map(MS, sf, a, Xf);
-        if (F.ok)
-            for (int i = 0; i < NQ; ++i) {
-                int e;
-                float qx, qy;
-                if (fast_decide(M, F, Xf, M.bdist[a], a, i, cache[i * N + a], e, qx, qy))
-                    e9[i] = M.orig_elem[e], k9[i] = 0;
-            }
+        mixed_locate_node(M, MS, sc, sf, cache, a, e9, k9, nullptr, err);
+    } else {
+        locate_node(M, MS, sc, flags & FLAG_LITERAL_VG, a, e9, k9, err);
     }
     for (int i = 0; i < NQ; ++i) {
         elem[i * N + a] = e9[i];

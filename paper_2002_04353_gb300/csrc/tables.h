@@ -60,7 +60,7 @@ struct HostTables {
     std::vector<int2> fan, owner, wedges;
     std::vector<uint8_t> bkind;
     std::vector<double> ms;
-    std::vector<float4> ejf, Xf, v0f;
+    std::vector<float4> ejf, Xf, v0f, evf;
     std::vector<float> bdist, msf;
     int n_wall_nodes = 0;
 
@@ -90,6 +90,7 @@ struct HostTables {
         D.bdist = bdist.data();
         D.Xf = Xf.data();
         D.v0f = v0f.data();
+        D.evf = evf.data();
         return D;
     }
     MapStatic host_map() const
@@ -476,6 +477,8 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
     for (int a = 0; a < N; ++a) T.Xf[a] = split(T.X[a]);
     T.v0f.resize(E);
     for (int en = 0; en < E; ++en) T.v0f[en] = split(ev[3 * en]);
+    T.evf.resize((size_t)3 * E);
+    for (size_t k = 0; k < (size_t)3 * E; ++k) T.evf[k] = split(ev[k]);
     T.msf.resize(T.ms.size());
     for (size_t k = 0; k < T.ms.size(); ++k) T.msf[k] = (float)T.ms[k];
     // lower bound of every node's distance to the nearest boundary edge
