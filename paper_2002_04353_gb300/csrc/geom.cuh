@@ -330,12 +330,16 @@ ALELB_HD __noinline__ int orient_exact(double ax, double ay, double bx, double b
 ALELB_HD __forceinline__ int orient(double ax, double ay, double bx, double by, double cx,
                                     double cy)
 {
-    double l = dm(ds(ax, cx), ds(by, cy));
-    double r = dm(ds(ay, cy), ds(bx, cx));
+    const double acx = ds(ax, cx), bcy = ds(by, cy), acy = ds(ay, cy), bcx = ds(bx, cx);
+    double l = dm(acx, bcy);
+    double r = dm(acy, bcx);
     double det = ds(l, r);
     double bound = 3.3306690738754716e-16 * (fabs(l) + fabs(r));
     if (det > bound) return 1;
     if (-det > bound) return -1;
+    // fl(a - b) is zero only when a == b: a zero difference is exact, so
+    // when each product has a zero factor the determinant is exactly 0
+    if ((acx == 0.0 || bcy == 0.0) && (acy == 0.0 || bcx == 0.0)) return 0;
     return orient_exact(ax, ay, bx, by, cx, cy);
 }
 
