@@ -413,8 +413,8 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
         }
         switch (k) {
         case KT_STREAM:
-            k_stream<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st,
-                                                                          s->d_err, s->d_stats);
+            k_stream<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err,
+                                                                   s->d_stats);
             break;
         case KT_FAST:
             k_stream_fast<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sf, K, st);
@@ -935,8 +935,7 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     }
     K.flags = p->flags;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
-    k_stream<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
-                                                                       sd, err, nullptr);
+    k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
         k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), sd);
     k_collide<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,

@@ -684,10 +684,19 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
 // cannot reach a boundary.
 // The segment node -> departure point cannot leave the mesh when it is
 // shorter than the node's distance to any boundary, or when the element is
-// one of the node's own (a triangle is convex and holds both ends).
+// one of the node's own (a triangle is convex and holds both ends).  The
+// departure point is strictly inside the element when its three
+// barycentric coordinates (xi, eta, 1 - xi - eta) -- normalised
+// orientations -- exceed their certified error margins:
+//   |q - (p - v0)| <= eq per component, J the FP32-rounded inverse
+//   Jacobian (relative error <= 2u), S_k = |J_k1| + |J_k2|:
+//   |xi - xi_exact|  <= S_1 eq + 2u S_1 Q + 3u (|J_11 q_x| + |J_12 q_y|)
+//   |eta - eta_exact| likewise, |lambda_0 error| <= both + 2u (1 + |xi| + |eta|)
+// (each taken twice).  On success (xi, eta) are the interpolation's local
+// coordinates.
 ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, float4 Xf,
-                                          float bdist, int a, int i, int c, int &e, float &qx,
-                                          float &qy)
+                                          float bdist, int a, int i, int c, int &e, float &xi,
+                                          float &eta)
 {
     const float u = 5.9604644775390625e-08f;
     const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -705,12 +714,10 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         if (cn[k] == a) l = k;
     if (!(len + F.eps_c < bdist) && l < 0) return false;
     const float4 ed = M.ejf[2 * e];
-    // vertices relative to v0: w0 = 0, w1 = e1, w2 = e2 (FP32-rounded exact differences)
-    const float wx[3] = {0.0f, ed.x, ed.z}, wy[3] = {0.0f, ed.y, ed.w};
-    const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
-    const float C = fmaxf(fabsf(chx), fabsf(chy));
+    const float4 J = M.ejf[2 * e + 1];
     float dx, dy; // node position relative to v0
     if (l >= 0) {
+        const float wx[3] = {0.0f, ed.x, ed.z}, wy[3] = {0.0f, ed.y, ed.w};
         if (l < 3) {
             dx = wx[l];
             dy = wy[l];
@@ -724,34 +731,20 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         dx = (Xf.x - v0.x) + (Xf.z - v0.z);
         dy = (Xf.y - v0.y) + (Xf.w - v0.w);
     }
-    qx = dx - chx;
-    qy = dy - chy;
+    const float qx = dx - chx, qy = dy - chy;
+    const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
     const float Q = fmaxf(fabsf(qx), fabsf(qy));
-    // |q - (p - v0)| <= eq: c^ bound, the node offset and its roundings, and
-    // the FP64 rounding of p itself
     const float eq = F.eps_c + 2.0f * u * fmaxf(fmaxf(fabsf(dx), fabsf(dy)), E) + u * Q +
                      2.98023223876953125e-08f;
-    const float EQ = E + Q;
-    const float bound = 8.0f * EQ * (eq + u * E) + 12.0f * u * EQ * EQ;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int k1 = (k + 1) % 3;
-        const float Dx = wx[k1] - wx[k], Dy = wy[k1] - wy[k];
-        float o, b;
-        if (l == k || l == k1 || l == 3 + k) {
-            // the node lies on this edge: orient = -(D x c^) exactly, whose
-            // error scales with |c^| rather than with the element size
-            o = Dy * chx - Dx * chy;
-            const float D = fmaxf(fabsf(Dx), fabsf(Dy));
-            b = 2.0f * (4.0f * D * F.eps_c + 12.0f * u * E * C + 6.0f * u * D * C) +
-                (l == 3 + k ? 12.0f * u * E * E : 0.0f) + 2.98023223876953125e-08f * D;
-        } else {
-            o = Dx * (qy - wy[k]) - Dy * (qx - wx[k]);
-            b = bound;
-        }
-        if (!(o > b)) return false;
-    }
-    return true;
+    const float t11 = J.x * qx, t12 = J.y * qy, t21 = J.z * qx, t22 = J.w * qy;
+    xi = t11 + t12;
+    eta = t21 + t22;
+    const float l0 = 1.0f - xi - eta;
+    const float S1 = fabsf(J.x) + fabsf(J.y), S2 = fabsf(J.z) + fabsf(J.w);
+    const float m1 = 2.0f * (S1 * (eq + 2.0f * u * Q) + 3.0f * u * (fabsf(t11) + fabsf(t12)));
+    const float m2 = 2.0f * (S2 * (eq + 2.0f * u * Q) + 3.0f * u * (fabsf(t21) + fabsf(t22)));
+    const float m0 = m1 + m2 + 4.0f * u * (1.0f + fabsf(xi) + fabsf(eta));
+    return xi > m1 && eta > m2 && l0 > m0;
 }
 
 // Certified FP32 sign of orient(A, B, C) = (A - C) x (B - C) from

@@ -86,34 +86,17 @@ __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const
     KY = (-x_eta * sxi + x_xi * seta) / detJ;
 }
 
-// FAST (the FP32-deviation form): each population first tries the element
-// its departure point fell in at the previous step.  The departure offset
-// from that element's first vertex is formed in FP32 (map, c^ and the hi/lo
-// coordinate difference) with a rigorous error bound, and the element is
-// accepted only when the certified FP32 orientations show that the FP64
-// canonical departure point lies strictly inside it and the departure
-// segment is shorter than the node's distance to any boundary: then it is
-// the unique element the walk would return.  Otherwise (and always in the
-// plain form) the FP64 departure point and the exact walk decide, and the
-// cache is refreshed.  stats[0] counts the walks.
-template <class S, class A, bool FAST>
+// The plain FP64 propagation: every population through the FP64 departure
+// point and the exact walk, one thread per node.
+template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
-                                                MapScalarsF sf, KinParams<A> K, StateDev<S> st,
-                                                int *err, unsigned long long *stats)
+                                                KinParams<A> K, StateDev<S> st, int *err,
+                                                unsigned long long *stats)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
     if (a >= N) return;
     const double2 Xa = M.X[a];
-    FastMap F{};
-    float4 Xf = make_float4(0, 0, 0, 0);
-    float bdist = 0.0f;
-    if (FAST) {
-        Xf = M.Xf[a];
-        bdist = M.bdist[a];
-        F = fast_map(MS, sf, a, Xf);
-        if (K.flags & FLAG_LITERAL_VG) F.ok = false;
-    }
     bool have64 = false;
     double a11 = 0, a12 = 0, a21 = 0, a22 = 0, wx = 0, wy = 0, Vx = 0, Vy = 0;
     int miss = 0, far = 0;
@@ -124,11 +107,7 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
     for (int i = 0; i < NQ; ++i) {
         A fi = 0, gi = 0;
         int src = -1; // node whose value is taken as is
-        int e = -1;
-        float qx = 0.f, qy = 0.f;
-        bool fast = false;
-        if (FAST && F.ok) fast = fast_decide(M, F, Xf, bdist, a, i, st.cache[i * N + a], e, qx, qy);
-        if (!fast) {
+        {
             if (!have64) {
                 double xX, xY, yX, yY;
                 map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -153,38 +132,18 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
                 } else if (L.vnode >= 0) {
                     src = L.vnode;
                 } else {
-                    e = L.e;
-                    if (FAST) {
-                        st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
-                        double2 v0 = M.ev[3 * e];
-                        qx = (float)(px - (L.sx ? v0.x + L.sx * M.Lx : v0.x));
-                        qy = (float)(py - (L.sy ? v0.y + L.sy * M.Ly : v0.y));
-                    } else {
-                        double xi, eta;
-                        local_coords(M, e, L.sx, L.sy, px, py, xi, eta);
-                        qx = (float)xi; // unused in the FP64 form
-                        A Nw[6];
-                        shape6<A>((A)xi, (A)eta, Nw);
+                    const int e = L.e;
+                    double xi, eta;
+                    local_coords(M, e, L.sx, L.sy, px, py, xi, eta);
+                    A Nw[6];
+                    shape6<A>((A)xi, (A)eta, Nw);
 #pragma unroll
-                        for (int k = 0; k < 6; ++k) {
-                            const int b = M.conn[6 * e + k];
-                            fi += Nw[k] * (A)st.post[i * N + b];
-                            gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
-                        }
-                        e = -1; // interpolated already
+                    for (int k = 0; k < 6; ++k) {
+                        const int b = M.conn[6 * e + k];
+                        fi += Nw[k] * (A)st.post[i * N + b];
+                        gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
                     }
                 }
-            }
-        }
-        if (FAST && e >= 0) {
-            A Nw[6];
-            const float4 J = M.ejf[2 * e + 1];
-            shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const int b = M.conn[6 * e + k];
-                fi += Nw[k] * (A)st.post[i * N + b];
-                gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
             }
         }
         if (src >= 0) {
@@ -304,11 +263,10 @@ __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, Ma
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             int e;
-            float qx, qy;
-            if (F.ok && fast_decide(M, F, Xf, bd, a, i, cache[i], e, qx, qy)) {
-                const float4 J = M.ejf[2 * e + 1];
+            float xi, eta;
+            if (F.ok && fast_decide(M, F, Xf, bd, a, i, cache[i], e, xi, eta)) {
                 A Nw[6];
-                shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);
+                shape6<A>((A)xi, (A)eta, Nw);
                 A fi = 0, gi = 0;
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
@@ -430,16 +388,16 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
             }
             A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
             if (!(K.flags & FLAG_BC_EQ)) {
-                double KX, KY;
-                owner_grad_linear(M, a, st.ux, KX, KY);
-                du[0] = (A)(a11 * (float)KX + a21 * (float)KY);
-                du[1] = (A)(a12 * (float)KX + a22 * (float)KY);
-                owner_grad_linear(M, a, st.uy, KX, KY);
-                du[2] = (A)(a11 * (float)KX + a21 * (float)KY);
-                du[3] = (A)(a12 * (float)KX + a22 * (float)KY);
-                owner_grad_linear(M, a, st.T, KX, KY);
-                dT[0] = (A)(a11 * (float)KX + a21 * (float)KY);
-                dT[1] = (A)(a12 * (float)KX + a22 * (float)KY);
+                float KX, KY;
+                owner_grad_linear_f32(M, a, st.ux, KX, KY);
+                du[0] = (A)(a11 * KX + a21 * KY);
+                du[1] = (A)(a12 * KX + a22 * KY);
+                owner_grad_linear_f32(M, a, st.uy, KX, KY);
+                du[2] = (A)(a11 * KX + a21 * KY);
+                du[3] = (A)(a12 * KX + a22 * KY);
+                owner_grad_linear_f32(M, a, st.T, KX, KY);
+                dT[0] = (A)(a11 * KX + a21 * KY);
+                dT[1] = (A)(a12 * KX + a22 * KY);
             }
             A fm[NQ], gm[NQ];
             grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
@@ -497,6 +455,20 @@ __device__ __forceinline__ void owner_grad_f32(const MeshDev &M, int a, const S 
         sxi += Ks * c_dNxif[l][s];
         seta += Ks * c_dNetaf[l][s];
     }
+    KX = sxi * J.x + seta * J.z;
+    KY = sxi * J.y + seta * J.w;
+}
+
+// First-order FP32 d K / d X through the owner element's vertices.
+template <class S>
+__device__ __forceinline__ void owner_grad_linear_f32(const MeshDev &M, int a, const S *K,
+                                                      float &KX, float &KY)
+{
+    const int e = M.owner[a].x;
+    const float4 J = M.ejf[2 * e + 1];
+    const float K0 = (float)K[M.conn[6 * e]];
+    const float sxi = (float)K[M.conn[6 * e + 1]] - K0;
+    const float seta = (float)K[M.conn[6 * e + 2]] - K0;
     KX = sxi * J.x + seta * J.z;
     KY = sxi * J.y + seta * J.w;
 }

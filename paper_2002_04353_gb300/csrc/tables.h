@@ -23,7 +23,7 @@ namespace alelb {
 
 inline int host_orient(double ax, double ay, double bx, double by, double cx, double cy)
 {
-    return orient_exact(ax, ay, bx, by, cx, cy);
+    return orient(ax, ay, bx, by, cx, cy);
 }
 
 inline double unwrap1(double d, double L)
