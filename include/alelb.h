@@ -202,8 +202,64 @@ alelb_status alelb_info(alelb_solver *s, double out[8]);
 alelb_status alelb_lb_step_noalloc(alelb_mesh *mesh, const alelb_params *p, double t,
                                    double *post, double *rho, double *ux, double *uy, double *T);
 
+/* Batched step (the paper runs one case at a time and has no counterpart;
+   this serves parameter sweeps of many independent cases).  A batch groups
+   B = 1..32 distinct solvers of one precision, each on its own mesh, and
+   advances all of them together.  Each phase of the step (Eq. Propagation,
+   Sec. IV.A, moments, the two derivative passes of Eq. Xa, collision) is one
+   launch over all cases: its thread blocks are numbered through a prefix sum
+   of the cases' node-tile counts, so block b works on the case whose tile
+   range holds b; the exact part of the propagation walks every case's work
+   list.  Chunks of up to 64 steps are captured once into a CUDA graph and
+   replayed.  Per case the result is that of alelb_lb_step on that solver
+   alone: the same per-node code with the same per-step map scalars, so the
+   same element choices, with values equal up to rounding (the compiler may
+   fuse multiply-adds of the shared code in another order in the batched
+   kernels).
+   The solvers must outlive the batch and must not be destroyed while it
+   exists; between batch calls they stay usable one by one (alelb_moments,
+   alelb_forces, alelb_get_pops, alelb_set_pops, alelb_lb_step): a batch
+   step waits for earlier work on every case's stream, and every case's
+   stream waits for the batch's last step. */
+typedef struct alelb_batch alelb_batch;
+
+/* cases: host array of B solver handles, read during the call.  stream: the
+   cudaStream_t of the batch's launches (NULL: the batch's own non-blocking
+   stream).  Errors: ALELB_ERR_ARG (B out of 1..32, a null or repeated
+   solver, mixed precision), ALELB_ERR_OOM, ALELB_ERR_CUDA. */
+alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B, void *stream, alelb_batch **out);
+void alelb_batch_destroy(alelb_batch *b);
+
+/* Advances every case by n >= 0 steps; asynchronous on the batch's stream. */
+alelb_status alelb_batch_step(alelb_batch *b, int32_t n);
+
+/* Waits for the batch's stream and reports the first case with a sticky
+   device error (alelb_batch_last_error names the case). */
+alelb_status alelb_batch_sync(alelb_batch *b);
+
+/* Autotuner: runs ONE real step (every case advances by 1) in which each
+   phase kernel is launched `reps` (1..16) times with every candidate launch
+   shape and timed with CUDA events; the fastest shape per kernel is kept
+   for later steps.  Candidates: 64, 128 or 256 threads per block (one
+   node tile per block); for the exact part of the propagation also 1, 2,
+   4, 8 or 16 blocks per SM.  The step's values do not depend on the
+   shapes, and every phase kernel gives the same values when repeated
+   within a step, so tuning changes no result.  choice (may be NULL, else 8
+   values out): block size of {k_stream, k_stream_fast, k_stream_slow,
+   k_moments, k_deriv1, k_collide}, grid of k_stream_slow, 0.
+   Synchronous. */
+alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
+
+/* Per-kernel device times of the batch, as alelb_profile and
+   alelb_kernel_times for a solver.  While enabled, steps are launched one
+   kernel at a time (not through the graph) between two events each. */
+alelb_status alelb_batch_profile(alelb_batch *b, int32_t enable);
+alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **names, double *ms,
+                                      int64_t *launches, int32_t *n);
+
 const char *alelb_last_error(alelb_solver *s);
 const char *alelb_mesh_last_error(alelb_mesh *m);
+const char *alelb_batch_last_error(alelb_batch *b);
 
 #ifdef __cplusplus
 }

@@ -29,9 +29,16 @@
  *   R8  wall targets: u = V_G at the wall node, rho and T interpolated at
  *       B = A + n dt from the previous step's fields; off-wall targets are
  *       the node's previous-step fields; gradients are first-order
- *       (vertex-linear) owner-element FE derivatives of the previous-step
- *       fields (Sec. IV.A).  Flag BC_EQUILIBRIUM drops the non-equilibrium
- *       part (a stabilising variant, not the paper's condition)
+ *       (vertex-linear) FE derivatives of the previous-step fields (Sec.
+ *       IV.A) in the node's wall-side element: among its incident elements
+ *       with a vertex on a wall edge the one of larger computational area
+ *       (then lower id), else its owner element.  The larger-area rule of
+ *       Sec. IV is stated for the correction-term derivatives; applied to a
+ *       node one layer off the wall it takes a difference away from the
+ *       wall, and the normal velocity next to the wall then grows without
+ *       bound.
+ *       Flag BC_EQUILIBRIUM drops the non-equilibrium part (a stabilising
+ *       variant, not the paper's condition)
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
  *       on each straight P2 wall edge of the mapped geometry
  * Parity status of each function is given in its comment; the forces have
@@ -374,6 +381,7 @@ typedef struct {
     double *ev;    /* 12 per element: node coords in the element frame */
     double *area2; /* twice the computational area */
     int *owner, *owner_loc;
+    int *bcel; /* element of the wall condition's gradients (R8) */
     /* point search */
     qnode_t *qn;
     int nqn, cap_qn;
@@ -964,6 +972,22 @@ static int prepare(orc_t *o)
         o->probe_xi[2 * a] = (yeta * (Bx - x0) - xeta * (By - y0)) / detJ;
         o->probe_xi[2 * a + 1] = (-yxi * (Bx - x0) + xxi * (By - y0)) / detJ;
     }
+    /* element of each node's wall-condition gradients (reading R8): the
+       incident element of larger area, then lower id, among those with a
+       vertex on a wall edge; the owner element when none touches a wall */
+    o->bcel = xcalloc((size_t)nn, sizeof(int));
+    for (int a = 0; a < nn; ++a) o->bcel[a] = -1;
+    for (int e = 0; e < o->ne; ++e) {
+        int touches = o->is_wall[o->conn[6 * e]] || o->is_wall[o->conn[6 * e + 1]] ||
+                      o->is_wall[o->conn[6 * e + 2]];
+        if (!touches) continue;
+        for (int l = 0; l < 6; ++l) {
+            int a = o->conn[6 * e + l], b = o->bcel[a];
+            if (b < 0 || o->area2[e] > o->area2[b] || (o->area2[e] == o->area2[b] && e < b)) o->bcel[a] = e;
+        }
+    }
+    for (int a = 0; a < nn; ++a)
+        if (o->bcel[a] < 0) o->bcel[a] = o->owner[a];
     return ST_OK;
 }
 
@@ -1020,7 +1044,7 @@ void orc_destroy(void *h)
 {
     orc_t *o = h;
     if (!o) return;
-    void *ptrs[] = {o->X, o->conn, o->ekind, o->ev, o->area2, o->owner, o->owner_loc, o->qn,
+    void *ptrs[] = {o->X, o->conn, o->ekind, o->ev, o->area2, o->owner, o->owner_loc, o->bcel, o->qn,
                     o->qe, o->be, o->bnear_ptr, o->bnear_e, o->bnear_sx, o->bnear_sy,
                     o->is_wall, o->wall_n, o->probe_e, o->probe_xi, o->ms, o->f, o->g,
                     o->rho, o->ux, o->uy, o->T, o->fs, o->gs, o->m_rt, o->Qx, o->Qy, o->Dx,
@@ -1229,12 +1253,13 @@ static void fe_grad_X(const orc_t *o, int a, const double *K, double *KX, double
 }
 
 /* First-order FE derivative d/dX of a nodal field at node a: the gradient
-   of the linear interpolant through the owner element's three vertices.
-   Used for the non-equilibrium part of the wall condition, where a
-   first-order gradient suffices (Sec. IV.A, last paragraph). */
+   of the linear interpolant through the three vertices of the node's
+   wall-condition element (R8).  Used for the non-equilibrium part of the
+   wall condition, where a first-order gradient suffices (Sec. IV.A, last
+   paragraph). */
 static void fe_grad_X_linear(const orc_t *o, int a, const double *K, double *KX, double *KY)
 {
-    int e = o->owner[a];
+    int e = o->bcel[a];
     const double *v = &o->ev[12 * e];
     double x_xi = v[2] - v[0], x_eta = v[4] - v[0];
     double y_xi = v[3] - v[1], y_eta = v[5] - v[1];

@@ -33,7 +33,9 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_solver_destroy", "alelb_lb_step", "alelb_sync", "alelb_moments", "alelb_time",
            "alelb_get_pops", "alelb_set_pops", "alelb_forces", "alelb_locate", "alelb_profile",
            "alelb_kernel_times", "alelb_info", "alelb_last_error", "alelb_mesh_last_error",
-           "alelb_lb_step_noalloc"]
+           "alelb_lb_step_noalloc", "alelb_batch_create", "alelb_batch_destroy", "alelb_batch_step",
+           "alelb_batch_sync", "alelb_batch_tune", "alelb_batch_profile", "alelb_batch_kernel_times",
+           "alelb_batch_last_error"]
 
 
 class AlelbError(RuntimeError):
@@ -91,6 +93,16 @@ def load(path: str = LIB_PATH):
     L.alelb_mesh_last_error.argtypes = [p]
     L.alelb_mesh_last_error.restype = C.c_char_p
     L.alelb_lb_step_noalloc.argtypes = [p, C.POINTER(Params), d, p, p, p, p, p]
+    L.alelb_batch_create.argtypes = [C.POINTER(p), i32, p, C.POINTER(p)]
+    L.alelb_batch_destroy.argtypes = [p]
+    L.alelb_batch_destroy.restype = None
+    L.alelb_batch_step.argtypes = [p, i32]
+    L.alelb_batch_sync.argtypes = [p]
+    L.alelb_batch_tune.argtypes = [p, i32, p]
+    L.alelb_batch_profile.argtypes = [p, i32]
+    L.alelb_batch_kernel_times.argtypes = [p, C.POINTER(C.c_char_p), p, p, C.POINTER(i32)]
+    L.alelb_batch_last_error.argtypes = [p]
+    L.alelb_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -287,3 +299,62 @@ class Solver:
 
 def lb_init(mesh, flow, precision=PREC_FP64, flags=None, stream=None):
     return Solver(mesh, flow, precision, flags, stream)
+
+
+class Batch:
+    """alelb_batch_*: one batched step over several solvers (kept alive by
+    the batch)."""
+
+    def __init__(self, solvers, stream=None):
+        L = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * max(1, len(self.solvers)))(*[s.h for s in self.solvers])
+        h = C.c_void_p()
+        st = L.alelb_batch_create(arr, len(self.solvers), stream, C.byref(h))
+        if st != OK:
+            msg = L.alelb_batch_last_error(h).decode() if h.value else ""
+            if h.value:
+                L.alelb_batch_destroy(h)
+            raise AlelbError(st, "batch_create: " + msg)
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            raise AlelbError(st, f"{what}: " + load().alelb_batch_last_error(self.h).decode())
+
+    def step(self, n=1):
+        self._check(load().alelb_batch_step(self.h, int(n)), "batch_step")
+
+    def sync(self):
+        self._check(load().alelb_batch_sync(self.h), "batch_sync")
+
+    def tune(self, reps=3):
+        out = np.zeros(8, dtype=np.int32)
+        self._check(load().alelb_batch_tune(self.h, int(reps), _ptr(out)), "batch_tune")
+        keys = ["k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide"]
+        d = {k: int(out[i]) for i, k in enumerate(keys)}
+        d["k_stream_slow_grid"] = int(out[6])
+        return d
+
+    def profile(self, enable=True):
+        self._check(load().alelb_batch_profile(self.h, int(bool(enable))), "batch_profile")
+
+    def kernel_times(self):
+        names = (C.c_char_p * 8)()
+        ms = np.zeros(8)
+        n_l = np.zeros(8, dtype=np.int64)
+        n = C.c_int32(8)
+        self._check(load().alelb_batch_kernel_times(self.h, names, _ptr(ms), _ptr(n_l), C.byref(n)),
+                    "batch_kernel_times")
+        return {names[k].decode(): (float(ms[k]), int(n_l[k])) for k in range(n.value)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().alelb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -14,53 +14,44 @@
 #include <unordered_map>
 #include <vector>
 
-#include "alelb.h"
-#include "kernels.cuh"
-#include "tables.h"
+#include "internal.h"
 
 using namespace alelb;
 
-namespace {
+namespace alelb {
 
+const char *const KT_NAMES[KT_N] = {"k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1",
+                                    "k_collide"};
 
-struct DevBuf {
-    std::vector<void *> ptrs;
-    template <class T> T *put(const std::vector<T> &h, cudaError_t &st)
-    {
-        if (h.empty()) return nullptr;
-        void *p = nullptr;
-        if (st == cudaSuccess) st = cudaMalloc(&p, h.size() * sizeof(T));
-        if (st == cudaSuccess) {
-            ptrs.push_back(p);
-            st = cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-        }
-        return (T *)p;
+MapScalarsF to_f32(const MapScalars &S, const HostTables &T)
+{
+    MapScalarsF F;
+    F.s = (float)S.s;
+    F.sd = (float)S.sd;
+    F.vy = (float)S.vy;
+    F.c = (float)S.c;
+    F.sn = (float)S.sn;
+    F.thd = (float)S.thd;
+    F.cm = (float)S.cm;
+    F.Xc = (float)T.mp[3];
+    F.Yc = (float)T.mp[4];
+    return F;
+}
+
+alelb_status check_sticky(alelb_solver *s)
+{
+    if (s->sticky & ERR_LOCATE) {
+        s->err = "element walk exceeded its step limit";
+        return ALELB_ERR_LOCATE;
     }
-    template <class T> T *alloc(size_t n, cudaError_t &st)
-    {
-        void *p = nullptr;
-        if (st == cudaSuccess) st = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
-        if (st == cudaSuccess) ptrs.push_back(p);
-        return (T *)p;
+    if (s->sticky & ERR_NONFINITE) {
+        s->err = "non-finite or non-positive density or temperature";
+        return ALELB_ERR_NONFINITE;
     }
-    void release()
-    {
-        for (void *p : ptrs) cudaFree(p);
-        ptrs.clear();
-    }
-};
+    return ALELB_OK;
+}
 
-} // namespace
-
-struct alelb_mesh {
-    std::string err;
-    HostTables T;   // host copies of every table (also used by the host-side walk check)
-    MeshDev dev{};
-    MapStatic mst{};
-    int2 *d_wedges = nullptr;
-    int nw = 0;
-    DevBuf buf;
-};
+} // namespace alelb
 
 namespace {
 
@@ -119,6 +110,7 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.fan_ptr = B.put(T.fan_ptr, st);
     D.fan = B.put(T.fan, st);
     D.owner = B.put(T.owner, st);
+    D.bcel = B.put(T.bcel, st);
     D.bkind = B.put(T.bkind, st);
     D.wall_idx = B.put(T.wall_idx, st);
     D.probe_e = B.put(T.probe_e, st);
@@ -134,28 +126,8 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     m->mst = T.host_map();
     m->mst.ms = B.put(T.ms, st);
     m->mst.msf = B.put(T.msf, st);
-    // P2 derivative tables at the six node positions
-    static const double LXI[6][2] = {{0, 0}, {1, 0}, {0, 1}, {0.5, 0}, {0.5, 0.5}, {0, 0.5}};
-    double dxi[6][6], deta[6][6];
-    for (int l = 0; l < 6; ++l) {
-        double xi = LXI[l][0], eta = LXI[l][1], l0 = 1.0 - xi - eta;
-        double nx[6] = {-(4 * l0 - 1), 4 * xi - 1, 0, 4 * (l0 - xi), 4 * eta, -4 * eta};
-        double ne[6] = {-(4 * l0 - 1), 0, 4 * eta - 1, -4 * xi, 4 * xi, 4 * (l0 - eta)};
-        for (int s = 0; s < 6; ++s) {
-            dxi[l][s] = nx[s];
-            deta[l][s] = ne[s];
-        }
-    }
-    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNxi, dxi, sizeof(dxi));
-    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNeta, deta, sizeof(deta));
-    float dxif[6][6], detaf[6][6];
-    for (int l = 0; l < 6; ++l)
-        for (int k = 0; k < 6; ++k) {
-            dxif[l][k] = (float)dxi[l][k];
-            detaf[l][k] = (float)deta[l][k];
-        }
-    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNxif, dxif, sizeof(dxif));
-    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNetaf, detaf, sizeof(detaf));
+    if (st == cudaSuccess) st = upload_fe_tables();
+    if (st == cudaSuccess) st = batch_fe_tables();
     *out = m;
     if (st != cudaSuccess) {
         m->buf.release();
@@ -203,9 +175,6 @@ extern "C" alelb_status alelb_mesh_move(alelb_mesh *m, double t)
 // ============================================================================
 namespace {
 
-enum { KT_STREAM = 0, KT_FAST = 1, KT_SLOW = 2, KT_MOMENTS = 3, KT_DERIV1 = 4, KT_COLLIDE = 5, KT_N = 6 };
-const char *KT_NAMES[KT_N] = {"k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1",
-                              "k_collide"};
 
 // Reference and far-field populations computed on the device with the
 // same kernel code that the step uses.
@@ -303,38 +272,6 @@ __global__ void k_export(StateDev<S> st, int N, const double *consts, double *fu
 
 } // namespace
 
-struct alelb_solver {
-    alelb_mesh *mesh = nullptr;
-    std::string err;
-    int prec = 0, flags = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    double gamma = 1.4, Pr = 0.71, mu = 0, rho_inf = 1, T_inf = 0.3, uinf[2] = {0, 0}, chord = 1;
-    double Cv = 2.5, Cp = 3.5;
-    double t = 0;
-    int64_t nstep = 0;
-    StateDev<double> sd{};
-    StateDev<float> sf{};
-    KinParams<double> kd{};
-    KinParams<float> kf{};
-    double consts[4 * NQ] = {0};
-    double *d_consts = nullptr;
-    double *d_scratch = nullptr; // 22 N doubles: import/export staging
-    double *h_pinned = nullptr;  // 22 N doubles of page-locked host staging
-    int *d_err = nullptr;
-    unsigned long long *d_stats = nullptr; // [0]: element walks run by the propagation kernel
-    double *d_out = nullptr;
-    DevBuf buf;
-    int sticky = 0;
-    // profiling
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;
-    struct Rec { int k; cudaEvent_t a, b; };
-    std::vector<Rec> pending;
-    double ms_acc[KT_N] = {0, 0, 0, 0, 0, 0};
-    int64_t n_acc[KT_N] = {0, 0, 0, 0, 0, 0};
-    int n_sm = 152;
-};
 
 namespace {
 
@@ -370,20 +307,6 @@ cudaEvent_t get_event(alelb_solver *s)
     return e;
 }
 
-MapScalarsF to_f32(const MapScalars &S, const alelb_mesh *m)
-{
-    MapScalarsF F;
-    F.s = (float)S.s;
-    F.sd = (float)S.sd;
-    F.vy = (float)S.vy;
-    F.c = (float)S.c;
-    F.sn = (float)S.sn;
-    F.thd = (float)S.thd;
-    F.cm = (float)S.cm;
-    F.Xc = (float)m->T.mp[3];
-    F.Yc = (float)m->T.mp[4];
-    return F;
-}
 
 template <class S, class A>
 cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const MapScalars &sc)
@@ -392,7 +315,7 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
     const int N = m->T.N;
     const bool phi = !(s->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF));
     const bool fast = s->prec == ALELB_PREC_FP32_DEV;
-    const MapScalarsF sf = to_f32(sc, m);
+    const MapScalarsF sf = to_f32(sc, m->T);
     int seq[6], ns = 0;
     if (fast) {
         seq[ns++] = KT_FAST;
@@ -469,18 +392,6 @@ template <class A> void fill_kin(alelb_solver *s, KinParams<A> &K)
     K.flags = s->flags;
 }
 
-alelb_status check_sticky(alelb_solver *s)
-{
-    if (s->sticky & ERR_LOCATE) {
-        s->err = "element walk exceeded its step limit";
-        return ALELB_ERR_LOCATE;
-    }
-    if (s->sticky & ERR_NONFINITE) {
-        s->err = "non-finite or non-positive density or temperature";
-        return ALELB_ERR_NONFINITE;
-    }
-    return ALELB_OK;
-}
 
 } // namespace
 
@@ -760,7 +671,7 @@ extern "C" alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cach
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t);
     int *de = (int *)s->d_scratch;
     int8_t *dk = (int8_t *)(s->d_scratch + (size_t)9 * N);
-    k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m), s->flags, cache,
+    k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, cache,
                                                      de, dk, s->d_err);
     std::vector<int> he((size_t)9 * N);
     std::vector<int8_t> hk((size_t)9 * N);
@@ -937,8 +848,8 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
     k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
-        k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), sd);
-    k_collide<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m), K,
+        k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), sd);
+    k_collide<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), K,
                                                                         sd, err);
     int herr = 0;
     st = cudaGetLastError();

@@ -1,0 +1,658 @@
+// batch.cu -- the batched step over many independent cases (alelb_batch_*
+// in include/alelb.h).
+//
+// Every phase of the time step is one launch over all cases.  Node-parallel
+// phases number their thread blocks through a prefix sum of the cases' tile
+// counts (off[c] = first tile of case c, a tile being one block of nodes);
+// block b finds its case with one ballot over the B <= 32 offsets, copies
+// the case's descriptor (mesh tables, map statics, kinetic constants, state
+// pointers) into shared memory and runs the same per-node code as the
+// single-case kernels.  The exact part of the propagation walks every case's
+// work list in turn.  Map scalars of each (step, case) are computed on the
+// host, exactly as for a single solver, and staged per chunk of steps; a
+// chunk's launches are captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace alelb;
+
+namespace alelb {
+cudaError_t batch_fe_tables() { return upload_fe_tables(); }
+} // namespace alelb
+
+namespace {
+
+constexpr int BATCH_MAX = 32;
+constexpr int CHUNK_MAX = 64; // steps per captured graph
+constexpr int N_BS = 3;       // block sizes 64, 128, 256
+
+template <class S, class A> struct CaseDev {
+    MeshDev M;
+    MapStatic MS;
+    KinParams<A> K;
+    StateDev<S> st;
+    int *err;
+    unsigned long long *stats;
+};
+
+// Case of tile `tile`: the number of cases whose tile range ends at or
+// before it.  All 32 lanes of the warp take part.
+__device__ __forceinline__ int tile_case(const int *__restrict__ off, int B, int tile)
+{
+    const int lane = threadIdx.x & 31;
+    const int v = lane < B ? __ldg(off + lane + 1) : INT_MAX;
+    return __popc(__ballot_sync(0xffffffffu, tile >= v));
+}
+
+template <class T> __device__ __forceinline__ void copy_words(void *dst, const T *src)
+{
+    static_assert(sizeof(T) % 4 == 0, "descriptor size");
+    const int *s = reinterpret_cast<const int *>(src);
+    for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += blockDim.x) ((int *)dst)[w] = __ldg(s + w);
+}
+
+// Shared-memory copies of one case's descriptor and its map scalars.
+template <class S, class A> struct SharedCase {
+    __align__(16) unsigned char c[sizeof(CaseDev<S, A>)];
+    __align__(16) unsigned char sc[sizeof(MapScalars)];
+    __align__(16) unsigned char sf[sizeof(MapScalarsF)];
+    __device__ const CaseDev<S, A> &C() const { return *reinterpret_cast<const CaseDev<S, A> *>(c); }
+    __device__ const MapScalars &SC() const { return *reinterpret_cast<const MapScalars *>(sc); }
+    __device__ const MapScalarsF &SF() const { return *reinterpret_cast<const MapScalarsF *>(sf); }
+    __device__ void load(const CaseDev<S, A> *cases, const MapScalars *scs, const MapScalarsF *sfs, int k)
+    {
+        copy_words(c, cases + k);
+        if (scs) copy_words(sc, scs + k);
+        if (sfs) copy_words(sf, sfs + k);
+    }
+};
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) kb_stream(const CaseDev<S, A> *__restrict__ cases,
+                                                 const int *__restrict__ off, int B,
+                                                 const MapScalars *__restrict__ sc, int count)
+{
+    __shared__ SharedCase<S, A> sh;
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, sc, nullptr, c);
+    __syncthreads();
+    const CaseDev<S, A> &C = sh.C();
+    const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
+    if (a < C.M.N) stream_plain_node(C.M, C.MS, sh.SC(), C.K, C.st, C.err, count ? C.stats : nullptr, a);
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__ cases,
+                                               const int *__restrict__ off, int B,
+                                               const MapScalarsF *__restrict__ sf)
+{
+    __shared__ SharedCase<S, A> sh;
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, nullptr, sf, c);
+    __syncthreads();
+    const CaseDev<S, A> &C = sh.C();
+    const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
+    const unsigned slow = a < C.M.N ? stream_fast_node(C.M, C.MS, sh.SF(), C.K, C.st, a) : 0u;
+    append_work(C.st, a, slow);
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__ cases, int B,
+                                               const MapScalars *__restrict__ sc,
+                                               const MapScalarsF *__restrict__ sf, int count)
+{
+    __shared__ SharedCase<S, A> sh;
+    for (int c = 0; c < B; ++c) {
+        __syncthreads(); // the previous case's descriptor is no longer read
+        sh.load(cases, sc, sf, c);
+        __syncthreads();
+        const CaseDev<S, A> &C = sh.C();
+        const unsigned n = *C.st.wcount;
+        if (count && C.stats && blockIdx.x == 0 && threadIdx.x == 0 && n)
+            atomicAdd(C.stats, (unsigned long long)n);
+        for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x)
+            stream_slow_item(C.M, C.MS, sh.SC(), sh.SF(), C.K, C.st, C.err, C.st.work[w]);
+    }
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restrict__ cases,
+                                                  const int *__restrict__ off, int B)
+{
+    __shared__ SharedCase<S, A> sh;
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, nullptr, nullptr, c);
+    __syncthreads();
+    const CaseDev<S, A> &C = sh.C();
+    const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
+    if (a == 0) *C.st.wcount = 0u; // the case's work list has been consumed
+    if (a < C.M.N) moments_node(C.K, C.st, C.M.N, C.err, a);
+}
+
+template <class S, class A, bool FAST>
+__global__ void __launch_bounds__(256) kb_deriv1(const CaseDev<S, A> *__restrict__ cases,
+                                                 const int *__restrict__ off, int B,
+                                                 const MapScalars *__restrict__ sc,
+                                                 const MapScalarsF *__restrict__ sf)
+{
+    __shared__ SharedCase<S, A> sh;
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, sc, sf, c);
+    __syncthreads();
+    const CaseDev<S, A> &C = sh.C();
+    const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
+    if (a < C.M.N) deriv1_node<S, A, FAST>(C.M, C.MS, sh.SC(), sh.SF(), C.st, a);
+}
+
+template <class S, class A, bool FAST>
+__global__ void __launch_bounds__(256) kb_collide(const CaseDev<S, A> *__restrict__ cases,
+                                                  const int *__restrict__ off, int B,
+                                                  const MapScalars *__restrict__ sc,
+                                                  const MapScalarsF *__restrict__ sf)
+{
+    __shared__ SharedCase<S, A> sh;
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, sc, sf, c);
+    __syncthreads();
+    const CaseDev<S, A> &C = sh.C();
+    const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
+    if (a < C.M.N) collide_at<S, A, FAST>(C.M, C.MS, sh.SC(), sh.SF(), C.K, C.st, C.err, a);
+}
+
+// Empties every case's work list (before a repeated launch of kb_fast while
+// tuning).
+template <class S, class A>
+__global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
+{
+    const int c = threadIdx.x;
+    if (c < B) *cases[c].st.wcount = 0u;
+}
+
+int bs_index(int bs) { return bs == 64 ? 0 : bs == 128 ? 1 : 2; }
+
+} // namespace
+
+struct alelb_batch {
+    std::string err;
+    std::vector<alelb_solver *> cs;
+    int B = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevBuf buf;
+    void *d_cases = nullptr;
+    int *d_off[N_BS] = {nullptr, nullptr, nullptr};
+    std::vector<int> h_off[N_BS];
+    MapScalars *d_sc = nullptr;
+    MapScalarsF *d_sf = nullptr;
+    MapScalars *h_sc[2] = {nullptr, nullptr};
+    MapScalarsF *h_sf[2] = {nullptr, nullptr};
+    cudaEvent_t h_ev[2] = {nullptr, nullptr};
+    int slot = 0;
+    std::vector<cudaEvent_t> ev_in;
+    cudaEvent_t ev_done = nullptr;
+    // launch shapes (threads per block per kernel; blocks of k_stream_slow)
+    int bs[KT_N] = {128, 128, 128, 256, 256, 128};
+    int slow_grid = 0;
+    int n_sm = 152;
+    std::map<int, cudaGraphExec_t> graphs;
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int k; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    double ms_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    int64_t n_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+alelb_status bfail(alelb_batch *b, cudaError_t st, const char *what)
+{
+    b->err = std::string(what) + ": " + cudaGetErrorString(st);
+    return st == cudaErrorMemoryAllocation ? ALELB_ERR_OOM : ALELB_ERR_CUDA;
+}
+
+cudaEvent_t bget_event(alelb_batch *b)
+{
+    if (b->ev_pool.empty()) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = b->ev_pool.back();
+    b->ev_pool.pop_back();
+    return e;
+}
+
+void bflush_prof(alelb_batch *b)
+{
+    for (auto &r : b->pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            b->ms_acc[r.k] += ms;
+            b->n_acc[r.k] += 1;
+        }
+        b->ev_pool.push_back(r.a);
+        b->ev_pool.push_back(r.b);
+    }
+    b->pending.clear();
+}
+
+void drop_graphs(alelb_batch *b)
+{
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+}
+
+// Phase kernels of one step, in order.
+int step_sequence(const alelb_batch *b, int seq[KT_N])
+{
+    int n = 0;
+    if (b->prec == ALELB_PREC_FP32_DEV) {
+        seq[n++] = KT_FAST;
+        seq[n++] = KT_SLOW;
+        seq[n++] = KT_MOMENTS;
+    } else {
+        seq[n++] = KT_STREAM;
+    }
+    seq[n++] = KT_DERIV1;
+    seq[n++] = KT_COLLIDE;
+    return n;
+}
+
+// One phase kernel over all cases with the scalars of chunk step k.
+// bs: threads per block; grid: blocks (k_stream_slow only).
+template <class S, class A>
+void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count)
+{
+    const auto *cases = reinterpret_cast<const CaseDev<S, A> *>(b->d_cases);
+    const int q = bs_index(bs);
+    const int *off = b->d_off[q];
+    const int tiles = b->h_off[q][b->B];
+    const MapScalars *sc = b->d_sc + (size_t)k * b->B;
+    const MapScalarsF *sf = b->d_sf + (size_t)k * b->B;
+    const int B = b->B;
+    const bool fast = b->prec == ALELB_PREC_FP32_DEV;
+    switch (kt) {
+    case KT_STREAM:
+        kb_stream<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, count);
+        break;
+    case KT_FAST:
+        kb_fast<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B, sf);
+        break;
+    case KT_SLOW:
+        kb_slow<S, A><<<grid, bs, 0, b->stream>>>(cases, B, sc, sf, count);
+        break;
+    case KT_MOMENTS:
+        kb_moments<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B);
+        break;
+    case KT_DERIV1:
+        if (fast) kb_deriv1<S, A, true><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
+        else kb_deriv1<S, A, false><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
+        break;
+    default:
+        if (fast) kb_collide<S, A, true><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
+        else kb_collide<S, A, false><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
+    }
+}
+
+void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count)
+{
+    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count);
+    else launch_phase<double, double>(b, kt, bs, grid, k, count);
+}
+
+void enqueue_step(alelb_batch *b, int k)
+{
+    int seq[KT_N];
+    const int ns = step_sequence(b, seq);
+    for (int q = 0; q < ns; ++q) {
+        const int kt = seq[q];
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (b->prof) {
+            ea = bget_event(b);
+            eb = bget_event(b);
+            cudaEventRecord(ea, b->stream);
+        }
+        launch_kernel(b, kt, b->bs[kt], b->slow_grid, k, 1);
+        if (b->prof) {
+            cudaEventRecord(eb, b->stream);
+            b->pending.push_back({kt, ea, eb});
+        }
+    }
+}
+
+cudaError_t get_graph(alelb_batch *b, int K, cudaGraphExec_t &exec)
+{
+    auto it = b->graphs.find(K);
+    if (it != b->graphs.end()) {
+        exec = it->second;
+        return cudaSuccess;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t st = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (st != cudaSuccess) return st;
+    for (int k = 0; k < K; ++k) enqueue_step(b, k);
+    cudaError_t st_launch = cudaGetLastError();
+    st = cudaStreamEndCapture(b->stream, &g);
+    if (st == cudaSuccess) st = st_launch;
+    if (st == cudaSuccess) st = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st == cudaSuccess) b->graphs[K] = exec;
+    return st;
+}
+
+// Stages the map scalars of chunk steps 0..K-1 (case times t_c + done + k + 1)
+// and copies them to the device table.
+cudaError_t stage_scalars(alelb_batch *b, int done, int K)
+{
+    const int sl = b->slot;
+    cudaError_t st = cudaEventSynchronize(b->h_ev[sl]); // earlier copy out of this slot finished
+    if (st != cudaSuccess) return st;
+    for (int k = 0; k < K; ++k)
+        for (int c = 0; c < b->B; ++c) {
+            const alelb_solver *s = b->cs[c];
+            const HostTables &T = s->mesh->T;
+            const MapScalars sc = map_scalars(T.mkind, T.mp, s->t + (double)(done + k + 1));
+            b->h_sc[sl][(size_t)k * b->B + c] = sc;
+            b->h_sf[sl][(size_t)k * b->B + c] = to_f32(sc, T);
+        }
+    st = cudaMemcpyAsync(b->d_sc, b->h_sc[sl], sizeof(MapScalars) * K * b->B, cudaMemcpyHostToDevice, b->stream);
+    if (st == cudaSuccess)
+        st = cudaMemcpyAsync(b->d_sf, b->h_sf[sl], sizeof(MapScalarsF) * K * b->B, cudaMemcpyHostToDevice,
+                             b->stream);
+    if (st == cudaSuccess) st = cudaEventRecord(b->h_ev[sl], b->stream);
+    b->slot ^= 1;
+    return st;
+}
+
+// Orders the batch's stream after each case's earlier work.
+cudaError_t join_cases(alelb_batch *b)
+{
+    cudaError_t st = cudaSuccess;
+    for (int c = 0; c < b->B && st == cudaSuccess; ++c) {
+        cudaStream_t cs = b->cs[c]->stream;
+        if (cs == b->stream) continue;
+        st = cudaEventRecord(b->ev_in[c], cs);
+        if (st == cudaSuccess) st = cudaStreamWaitEvent(b->stream, b->ev_in[c], 0);
+    }
+    return st;
+}
+
+// Orders each case's stream after the batch's last launch.
+cudaError_t release_cases(alelb_batch *b)
+{
+    cudaError_t st = cudaEventRecord(b->ev_done, b->stream);
+    for (int c = 0; c < b->B && st == cudaSuccess; ++c) {
+        cudaStream_t cs = b->cs[c]->stream;
+        if (cs != b->stream) st = cudaStreamWaitEvent(cs, b->ev_done, 0);
+    }
+    return st;
+}
+
+template <class S, class A> CaseDev<S, A> case_desc(alelb_solver *s);
+template <> CaseDev<float, float> case_desc<float, float>(alelb_solver *s)
+{
+    return CaseDev<float, float>{s->mesh->dev, s->mesh->mst, s->kf, s->sf, s->d_err, s->d_stats};
+}
+template <> CaseDev<double, double> case_desc<double, double>(alelb_solver *s)
+{
+    return CaseDev<double, double>{s->mesh->dev, s->mesh->mst, s->kd, s->sd, s->d_err, s->d_stats};
+}
+
+template <class S, class A> cudaError_t upload_cases(alelb_batch *b)
+{
+    std::vector<CaseDev<S, A>> h(b->B);
+    for (int c = 0; c < b->B; ++c) h[c] = case_desc<S, A>(b->cs[c]);
+    cudaError_t st = cudaSuccess;
+    auto *d = b->buf.alloc<CaseDev<S, A>>(b->B, st);
+    b->d_cases = d;
+    if (st == cudaSuccess) st = cudaMemcpy(d, h.data(), sizeof(CaseDev<S, A>) * b->B, cudaMemcpyHostToDevice);
+    return st;
+}
+
+} // namespace
+
+extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B, void *stream,
+                                           alelb_batch **out)
+{
+    if (!out) return ALELB_ERR_ARG;
+    *out = nullptr;
+    if (!cases || B < 1 || B > BATCH_MAX) return ALELB_ERR_ARG;
+    for (int c = 0; c < B; ++c) {
+        if (!cases[c] || !cases[c]->mesh) return ALELB_ERR_ARG;
+        if (cases[c]->prec != cases[0]->prec) return ALELB_ERR_ARG;
+        for (int d = 0; d < c; ++d)
+            if (cases[d] == cases[c]) return ALELB_ERR_ARG;
+    }
+    alelb_batch *b = new (std::nothrow) alelb_batch();
+    if (!b) return ALELB_ERR_OOM;
+    *out = b;
+    b->cs.assign(cases, cases + B);
+    b->B = B;
+    b->prec = cases[0]->prec;
+    b->n_sm = cases[0]->n_sm;
+    b->slow_grid = 4 * b->n_sm;
+    cudaError_t st = cudaSuccess;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        st = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = st == cudaSuccess;
+    }
+    if (st != cudaSuccess) return bfail(b, st, "stream");
+    // tile offsets per block size
+    for (int q = 0; q < N_BS; ++q) {
+        const int bs = 64 << q;
+        auto &o = b->h_off[q];
+        o.assign(B + 1, 0);
+        for (int c = 0; c < B; ++c) {
+            const int N = b->cs[c]->mesh->T.N;
+            o[c + 1] = o[c] + (N + bs - 1) / bs;
+        }
+        b->d_off[q] = b->buf.put(o, st);
+    }
+    st = b->prec == ALELB_PREC_FP32_DEV ? upload_cases<float, float>(b) : upload_cases<double, double>(b);
+    b->d_sc = b->buf.alloc<MapScalars>((size_t)CHUNK_MAX * B, st);
+    b->d_sf = b->buf.alloc<MapScalarsF>((size_t)CHUNK_MAX * B, st);
+    for (int sl = 0; sl < 2; ++sl) {
+        if (st == cudaSuccess) st = cudaHostAlloc((void **)&b->h_sc[sl], sizeof(MapScalars) * CHUNK_MAX * B, 0);
+        if (st == cudaSuccess) st = cudaHostAlloc((void **)&b->h_sf[sl], sizeof(MapScalarsF) * CHUNK_MAX * B, 0);
+        if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->h_ev[sl], cudaEventDisableTiming);
+    }
+    b->ev_in.assign(B, nullptr);
+    for (int c = 0; c < B && st == cudaSuccess; ++c)
+        st = cudaEventCreateWithFlags(&b->ev_in[c], cudaEventDisableTiming);
+    if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    if (st != cudaSuccess) return bfail(b, st, "batch_create");
+    return ALELB_OK;
+}
+
+extern "C" void alelb_batch_destroy(alelb_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    bflush_prof(b);
+    drop_graphs(b);
+    for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_in)
+        if (e) cudaEventDestroy(e);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    for (int sl = 0; sl < 2; ++sl) {
+        if (b->h_ev[sl]) cudaEventDestroy(b->h_ev[sl]);
+        if (b->h_sc[sl]) cudaFreeHost(b->h_sc[sl]);
+        if (b->h_sf[sl]) cudaFreeHost(b->h_sf[sl]);
+    }
+    b->buf.release();
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+extern "C" const char *alelb_batch_last_error(alelb_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" alelb_status alelb_batch_step(alelb_batch *b, int32_t n)
+{
+    if (!b || n < 0) return ALELB_ERR_ARG;
+    if (n == 0) return ALELB_OK;
+    cudaError_t st = join_cases(b);
+    if (st != cudaSuccess) return bfail(b, st, "batch_step");
+    for (int done = 0; done < n;) {
+        const int K = std::min(CHUNK_MAX, n - done);
+        st = stage_scalars(b, done, K);
+        if (st != cudaSuccess) return bfail(b, st, "batch_step: map scalars");
+        if (b->prof) {
+            for (int k = 0; k < K; ++k) enqueue_step(b, k);
+            st = cudaGetLastError();
+        } else {
+            cudaGraphExec_t g = nullptr;
+            st = get_graph(b, K, g);
+            if (st == cudaSuccess) st = cudaGraphLaunch(g, b->stream);
+        }
+        if (st != cudaSuccess) return bfail(b, st, "batch_step: launch");
+        done += K;
+    }
+    for (alelb_solver *s : b->cs) {
+        s->t += (double)n;
+        s->nstep += n;
+    }
+    st = release_cases(b);
+    if (st != cudaSuccess) return bfail(b, st, "batch_step");
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_sync(alelb_batch *b)
+{
+    if (!b) return ALELB_ERR_ARG;
+    cudaError_t st = cudaStreamSynchronize(b->stream);
+    if (st != cudaSuccess) return bfail(b, st, "batch_sync");
+    if (b->prof) bflush_prof(b);
+    for (int c = 0; c < b->B; ++c) {
+        alelb_solver *s = b->cs[c];
+        int e = 0;
+        st = cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (st != cudaSuccess) return bfail(b, st, "batch_sync");
+        s->sticky |= e;
+        const alelb_status r = check_sticky(s);
+        if (r != ALELB_OK) {
+            b->err = "case " + std::to_string(c) + ": " + s->err;
+            return r;
+        }
+    }
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8])
+{
+    if (!b || reps < 1 || reps > 16) return ALELB_ERR_ARG;
+    cudaError_t st = join_cases(b);
+    if (st == cudaSuccess) st = stage_scalars(b, 0, 1);
+    if (st != cudaSuccess) return bfail(b, st, "batch_tune");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    st = cudaEventCreate(&e0);
+    if (st == cudaSuccess) st = cudaEventCreate(&e1);
+    if (st != cudaSuccess) return bfail(b, st, "batch_tune");
+    int seq[KT_N];
+    const int ns = step_sequence(b, seq);
+    const auto clear = [b]() {
+        if (b->prec == ALELB_PREC_FP32_DEV)
+            kb_clear_work<float, float>
+                <<<1, 32, 0, b->stream>>>(reinterpret_cast<const CaseDev<float, float> *>(b->d_cases), b->B);
+        else
+            kb_clear_work<double, double>
+                <<<1, 32, 0, b->stream>>>(reinterpret_cast<const CaseDev<double, double> *>(b->d_cases), b->B);
+    };
+    for (int q = 0; q < ns && st == cudaSuccess; ++q) {
+        const int kt = seq[q];
+        struct Cand { int bs, grid; };
+        std::vector<Cand> cands;
+        for (int bsq = 0; bsq < N_BS; ++bsq) {
+            const int bs = 64 << bsq;
+            if (kt == KT_SLOW) {
+                for (int gm = 1; gm <= 16; gm *= 2) cands.push_back({bs, gm * b->n_sm});
+            } else {
+                cands.push_back({bs, 0});
+            }
+        }
+        float best = 1e30f;
+        Cand pick = {b->bs[kt], b->slow_grid};
+        for (const Cand &cd : cands) {
+            float tmin = 1e30f;
+            for (int r = 0; r < reps && st == cudaSuccess; ++r) {
+                if (kt == KT_FAST) clear();
+                st = cudaEventRecord(e0, b->stream);
+                launch_kernel(b, kt, cd.bs, cd.grid, 0, 0);
+                if (st == cudaSuccess) st = cudaGetLastError();
+                if (st == cudaSuccess) st = cudaEventRecord(e1, b->stream);
+                if (st == cudaSuccess) st = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (st == cudaSuccess) st = cudaEventElapsedTime(&ms, e0, e1);
+                tmin = std::min(tmin, ms);
+            }
+            if (tmin < best) {
+                best = tmin;
+                pick = cd;
+            }
+        }
+        if (st != cudaSuccess) break;
+        b->bs[kt] = pick.bs;
+        if (kt == KT_SLOW) b->slow_grid = pick.grid;
+        // the launch that counts (walk statistics) with the chosen shape
+        if (kt == KT_FAST) clear();
+        launch_kernel(b, kt, pick.bs, pick.grid, 0, 1);
+        st = cudaGetLastError();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == cudaSuccess) st = cudaStreamSynchronize(b->stream);
+    if (st != cudaSuccess) return bfail(b, st, "batch_tune");
+    for (alelb_solver *s : b->cs) {
+        s->t += 1.0;
+        s->nstep += 1;
+    }
+    drop_graphs(b);
+    st = release_cases(b);
+    if (st != cudaSuccess) return bfail(b, st, "batch_tune");
+    if (choice) {
+        for (int k = 0; k < KT_N; ++k) choice[k] = b->bs[k];
+        choice[6] = b->slow_grid;
+        choice[7] = 0;
+    }
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_profile(alelb_batch *b, int32_t enable)
+{
+    if (!b) return ALELB_ERR_ARG;
+    cudaStreamSynchronize(b->stream);
+    bflush_prof(b);
+    b->prof = enable != 0;
+    for (int k = 0; k < KT_N; ++k) {
+        b->ms_acc[k] = 0;
+        b->n_acc[k] = 0;
+    }
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **names, double *ms,
+                                                 int64_t *launches, int32_t *n)
+{
+    if (!b || !n) return ALELB_ERR_ARG;
+    cudaError_t st = cudaStreamSynchronize(b->stream);
+    if (st != cudaSuccess) return bfail(b, st, "batch_kernel_times");
+    bflush_prof(b);
+    const int m = std::min<int>(*n, KT_N);
+    for (int k = 0; k < m; ++k) {
+        if (names) names[k] = KT_NAMES[k];
+        if (ms) ms[k] = b->ms_acc[k];
+        if (launches) launches[k] = b->n_acc[k];
+    }
+    *n = m;
+    return ALELB_OK;
+}

@@ -301,7 +301,7 @@ ALELB_HD __forceinline__ void departure(double a11, double a12, double a21, doub
 // exactly into two doubles with an FMA, and the twelve terms summed exactly
 // as a non-overlapping expansion (Two-Sum / Grow-Expansion).
 // ---------------------------------------------------------------------------
-ALELB_HD __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
+static ALELB_HD __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
                                          double cy)
 {
     double pa[6] = {ax, -ax, -cx, -ay, ay, cy};
@@ -358,6 +358,7 @@ struct MeshDev {
     const int *fan_ptr;    // [N+1]
     const int2 *fan;       // (elem, loc | (sx+1)<<4 | (sy+1)<<6)
     const int2 *owner;     // (elem, local index) of each node
+    const int *bcel;       // element of each node's wall-condition gradients
     const uint8_t *bkind;  // [N] boundary kind of the node (0 interior)
     const int *wall_idx;   // [N] index into the wall tables or -1
     const int *probe_e;    // [NW]
@@ -540,7 +541,7 @@ template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
     return r;
 }
 
-ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
+static ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
                                int *err)
 {
     Pred64 pr;

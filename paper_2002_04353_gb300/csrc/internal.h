@@ -1,0 +1,101 @@
+// internal.h -- host-side objects shared by the translation units of the
+// library (single-case solver in alelb.cu, batched step in batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "alelb.h"
+#include "kernels.cuh"
+#include "tables.h"
+
+namespace alelb {
+
+// Device allocations released together.
+struct DevBuf {
+    std::vector<void *> ptrs;
+    template <class T> T *put(const std::vector<T> &h, cudaError_t &st)
+    {
+        if (h.empty()) return nullptr;
+        void *p = nullptr;
+        if (st == cudaSuccess) st = cudaMalloc(&p, h.size() * sizeof(T));
+        if (st == cudaSuccess) {
+            ptrs.push_back(p);
+            st = cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+        }
+        return (T *)p;
+    }
+    template <class T> T *alloc(size_t n, cudaError_t &st)
+    {
+        void *p = nullptr;
+        if (st == cudaSuccess) st = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+        if (st == cudaSuccess) ptrs.push_back(p);
+        return (T *)p;
+    }
+    void release()
+    {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+enum { KT_STREAM = 0, KT_FAST = 1, KT_SLOW = 2, KT_MOMENTS = 3, KT_DERIV1 = 4, KT_COLLIDE = 5, KT_N = 6 };
+extern const char *const KT_NAMES[KT_N];
+
+// FP32 copies of the per-step map scalars.
+MapScalarsF to_f32(const MapScalars &S, const HostTables &T);
+// Uploads the P2 derivative tables of batch.cu's module.
+cudaError_t batch_fe_tables();
+// Status of a solver's sticky device errors (message in s->err).
+alelb_status check_sticky(alelb_solver *s);
+
+
+} // namespace alelb
+
+// The C-ABI's opaque objects (global names, as declared in alelb.h).
+using namespace alelb;
+
+struct alelb_mesh {
+    std::string err;
+    HostTables T;   // host copies of every table (also used by the host-side walk check)
+    MeshDev dev{};
+    MapStatic mst{};
+    int2 *d_wedges = nullptr;
+    int nw = 0;
+    DevBuf buf;
+};
+
+struct alelb_solver {
+    alelb_mesh *mesh = nullptr;
+    std::string err;
+    int prec = 0, flags = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double gamma = 1.4, Pr = 0.71, mu = 0, rho_inf = 1, T_inf = 0.3, uinf[2] = {0, 0}, chord = 1;
+    double Cv = 2.5, Cp = 3.5;
+    double t = 0;
+    int64_t nstep = 0;
+    StateDev<double> sd{};
+    StateDev<float> sf{};
+    KinParams<double> kd{};
+    KinParams<float> kf{};
+    double consts[4 * NQ] = {0};
+    double *d_consts = nullptr;
+    double *d_scratch = nullptr; // 22 N doubles: import/export staging
+    double *h_pinned = nullptr;  // 22 N doubles of page-locked host staging
+    int *d_err = nullptr;
+    unsigned long long *d_stats = nullptr; // [0]: element walks run by the propagation kernel
+    double *d_out = nullptr;
+    DevBuf buf;
+    int sticky = 0;
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int k; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    double ms_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    int64_t n_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    int n_sm = 152;
+};

@@ -68,13 +68,14 @@ __device__ __forceinline__ void owner_grad(const MeshDev &M, int a, const S *K, 
     KY = (-x_eta * sxi + x_xi * seta) / detJ;
 }
 
-// First-order d K / d X: gradient of the linear interpolant through the
-// owner element's vertices.
+// First-order d K / d X for the wall condition: gradient of the linear
+// interpolant through the vertices of the node's smallest incident element
+// (the wall-side element of a body-fitted mesh).
 template <class S>
 __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const S *K,
                                                   double &KX, double &KY)
 {
-    int e = M.owner[a].x;
+    int e = M.bcel[a];
     double2 v0 = M.ev[3 * e], v1 = M.ev[3 * e + 1], v2 = M.ev[3 * e + 2];
     double x_xi = v1.x - v0.x, x_eta = v2.x - v0.x;
     double y_xi = v1.y - v0.y, y_eta = v2.y - v0.y;
@@ -89,13 +90,12 @@ __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const
 // The plain FP64 propagation: every population through the FP64 departure
 // point and the exact walk, one thread per node.
 template <class S, class A>
-__global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
-                                                KinParams<A> K, StateDev<S> st, int *err,
-                                                unsigned long long *stats)
+__device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapStatic &MS,
+                                                  const MapScalars &sc, const KinParams<A> &K,
+                                                  const StateDev<S> &st, int *err,
+                                                  unsigned long long *stats, int a)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
-    if (a >= N) return;
     const double2 Xa = M.X[a];
     bool have64 = false;
     double a11 = 0, a12 = 0, a21 = 0, a22 = 0, wx = 0, wy = 0, Vx = 0, Vy = 0;
@@ -232,6 +232,15 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
     st.mrt[a] = (S)(K.mu / (rho * T));
 }
 
+template <class S, class A>
+__global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
+                                                KinParams<A> K, StateDev<S> st, int *err,
+                                                unsigned long long *stats)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < M.N) stream_plain_node(M, MS, sc, K, st, err, stats, a);
+}
+
 // ---------------------------------------------------------------------------
 // The FP32-deviation propagation, split by path so that the rare exact
 // work does not stall the warps of the common case:
@@ -244,15 +253,16 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
 //   k_moments      per node: moments, Q'_aaa and mu/(rho T) of the streamed
 //                  populations; resets the work list
 // ---------------------------------------------------------------------------
+// Interpolates every population of node a whose previous-step element is
+// verified; returns the mask of the others.
 template <class S, class A>
-__global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
-                                                     KinParams<A> K, StateDev<S> st)
+__device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const MapStatic &MS,
+                                                     const MapScalarsF &sf, const KinParams<A> &K,
+                                                     const StateDev<S> &st, int a)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = M.N;
-    const bool valid = a < N;
     unsigned slow = 0;
-    if (valid) {
+    {
         const float4 Xf = M.Xf[a];
         const float bd = M.bdist[a];
         FastMap F = fast_map(MS, sf, a, Xf);
@@ -281,7 +291,14 @@ __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, Ma
             }
         }
     }
-    // warp-aggregated append of the remaining populations
+    return slow;
+}
+
+// Warp-aggregated append of the populations in `slow` (node a) to the work
+// list; all 32 lanes of the warp take part, with slow = 0 where idle.
+template <class S>
+__device__ __forceinline__ void append_work(const StateDev<S> &st, int a, unsigned slow)
+{
     const unsigned lane = threadIdx.x & 31u;
     const int n = __popc(slow);
     int incl = n;
@@ -303,15 +320,24 @@ __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, Ma
 }
 
 template <class S, class A>
-__global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
-                                                     MapScalarsF sf, KinParams<A> K, StateDev<S> st,
-                                                     int *err, unsigned long long *stats)
+__global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
+                                                     KinParams<A> K, StateDev<S> st)
 {
-    const unsigned n = *st.wcount;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned slow = a < M.N ? stream_fast_node(M, MS, sf, K, st, a) : 0u;
+    append_work(st, a, slow);
+}
+
+// One listed population (code = 9 node + direction): exact decision, then
+// interpolation, far-field equilibrium or the missing-population condition.
+template <class S, class A>
+__device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStatic &MS,
+                                                 const MapScalars &sc, const MapScalarsF &sf,
+                                                 const KinParams<A> &K, const StateDev<S> &st,
+                                                 int *err, int code)
+{
     const int N = M.N;
-    if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
-    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x) {
-        const int code = st.work[w];
+    {
         const int a = code / NQ, i = code % NQ;
         const float4 Xf = M.Xf[a];
         const FastMap F = fast_map(MS, sf, a, Xf);
@@ -410,11 +436,20 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
 }
 
 template <class S, class A>
-__global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st, int N, int *err)
+__global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
+                                                     MapScalarsF sf, KinParams<A> K, StateDev<S> st,
+                                                     int *err, unsigned long long *stats)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a == 0) *st.wcount = 0u; // the work list has been consumed
-    if (a >= N) return;
+    const unsigned n = *st.wcount;
+    if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x)
+        stream_slow_item(M, MS, sc, sf, K, st, err, st.work[w]);
+}
+
+template <class S, class A>
+__device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateDev<S> &st, int N,
+                                             int *err, int a)
+{
     A f[NQ], g[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
@@ -436,10 +471,44 @@ __global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st,
     st.mrt[a] = (S)(K.mu / (rho * T));
 }
 
+template <class S, class A>
+__global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st, int N, int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a == 0) *st.wcount = 0u; // the work list has been consumed
+    if (a < N) moments_node(K, st, N, err, a);
+}
+
 // FP32 owner-element derivative d K / d X (rows of the FP32 inverse
 // Jacobian: grad xi = (j11, j12), grad eta = (j21, j22)).
 __constant__ float c_dNxif[6][6];
 __constant__ float c_dNetaf[6][6];
+
+// Fills this module's derivative tables: d N_s / d xi and d N_s / d eta of
+// the P2 shape functions at the six node positions.  Internal linkage, so
+// every translation unit that launches the kernels uploads its own copy.
+static inline cudaError_t upload_fe_tables()
+{
+    static const double LXI[6][2] = {{0, 0}, {1, 0}, {0, 1}, {0.5, 0}, {0.5, 0.5}, {0, 0.5}};
+    double dxi[6][6], deta[6][6];
+    float dxif[6][6], detaf[6][6];
+    for (int l = 0; l < 6; ++l) {
+        const double xi = LXI[l][0], eta = LXI[l][1], l0 = 1.0 - xi - eta;
+        const double nx[6] = {-(4 * l0 - 1), 4 * xi - 1, 0, 4 * (l0 - xi), 4 * eta, -4 * eta};
+        const double ne[6] = {-(4 * l0 - 1), 0, 4 * eta - 1, -4 * xi, 4 * xi, 4 * (l0 - eta)};
+        for (int s = 0; s < 6; ++s) {
+            dxi[l][s] = nx[s];
+            deta[l][s] = ne[s];
+            dxif[l][s] = (float)nx[s];
+            detaf[l][s] = (float)ne[s];
+        }
+    }
+    cudaError_t st = cudaMemcpyToSymbol(c_dNxi, dxi, sizeof(dxi));
+    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNeta, deta, sizeof(deta));
+    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNxif, dxif, sizeof(dxif));
+    if (st == cudaSuccess) st = cudaMemcpyToSymbol(c_dNetaf, detaf, sizeof(detaf));
+    return st;
+}
 
 template <class S>
 __device__ __forceinline__ void owner_grad_f32(const MeshDev &M, int a, const S *K, float &KX,
@@ -459,12 +528,13 @@ __device__ __forceinline__ void owner_grad_f32(const MeshDev &M, int a, const S 
     KY = sxi * J.y + seta * J.w;
 }
 
-// First-order FP32 d K / d X through the owner element's vertices.
+// First-order FP32 d K / d X for the wall condition, through the vertices
+// of the node's smallest incident element.
 template <class S>
 __device__ __forceinline__ void owner_grad_linear_f32(const MeshDev &M, int a, const S *K,
                                                       float &KX, float &KY)
 {
-    const int e = M.owner[a].x;
+    const int e = M.bcel[a];
     const float4 J = M.ejf[2 * e + 1];
     const float K0 = (float)K[M.conn[6 * e]];
     const float sxi = (float)K[M.conn[6 * e + 1]] - K0;
@@ -474,11 +544,10 @@ __device__ __forceinline__ void owner_grad_linear_f32(const MeshDev &M, int a, c
 }
 
 template <class S, class A, bool FAST>
-__global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScalars sc,
-                                                MapScalarsF sf, StateDev<S> st)
+__device__ __forceinline__ void deriv1_node(const MeshDev &M, const MapStatic &MS,
+                                            const MapScalars &sc, const MapScalarsF &sf,
+                                            const StateDev<S> &st, int a)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= M.N) return;
     if (FAST) {
         const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
         float KX, KY;
@@ -506,13 +575,20 @@ __global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScal
 }
 
 template <class S, class A, bool FAST>
-__global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapScalars sc,
-                                                 MapScalarsF sf, KinParams<A> K, StateDev<S> st,
-                                                 int *err)
+__global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScalars sc,
+                                                MapScalarsF sf, StateDev<S> st)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < M.N) deriv1_node<S, A, FAST>(M, MS, sc, sf, st, a);
+}
+
+template <class S, class A, bool FAST>
+__device__ __forceinline__ void collide_at(const MeshDev &M, const MapStatic &MS,
+                                           const MapScalars &sc, const MapScalarsF &sf,
+                                           const KinParams<A> &K, const StateDev<S> &st, int *err,
+                                           int a)
+{
     const int N = M.N;
-    if (a >= N) return;
     A Xx = 0, Xy = 0;
     if (FAST && !(K.flags & FLAG_PHI_OFF)) {
         const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
@@ -551,10 +627,19 @@ __global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapSca
     st.T[a] = (S)T;
 }
 
+template <class S, class A, bool FAST>
+__global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapScalars sc,
+                                                 MapScalarsF sf, KinParams<A> K, StateDev<S> st,
+                                                 int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < M.N) collide_at<S, A, FAST>(M, MS, sc, sf, K, st, err, a);
+}
+
 // Element choice of every population at map time t (parity report).  With
 // cache != nullptr each population first takes the propagation kernel's
 // fast decision (verified previous-step element), as k_stream would.
-__global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, MapScalarsF sf, int flags,
+static __global__ void k_locate(MeshDev M, MapStatic MS, MapScalars sc, MapScalarsF sf, int flags,
                          const int *cache, int *elem, int8_t *kind, int *err)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -627,7 +712,7 @@ __global__ void __launch_bounds__(256) k_forces(MeshDev M, MapStatic MS, MapScal
 }
 
 // det g > 0 check at every node (alelb_mesh_move).
-__global__ void k_check_map(MapStatic MS, MapScalars sc, const double2 *X, int N, int *bad)
+static __global__ void k_check_map(MapStatic MS, MapScalars sc, const double2 *X, int N, int *bad)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;

@@ -55,7 +55,7 @@ struct HostTables {
     double mp[16] = {0};
     std::vector<int> node_old2new, node_new2old, elem_old2new, elem_new2old;
     std::vector<double2> X, ev, probe_xi;
-    std::vector<int> nbr, conn, rank, orig, fan_ptr, wall_idx, probe_e;
+    std::vector<int> nbr, conn, rank, orig, fan_ptr, wall_idx, probe_e, bcel;
     std::vector<uint32_t> einfo;
     std::vector<int2> fan, owner, wedges;
     std::vector<uint8_t> bkind;
@@ -81,6 +81,7 @@ struct HostTables {
         D.fan_ptr = fan_ptr.data();
         D.fan = fan.data();
         D.owner = owner.data();
+        D.bcel = bcel.data();
         D.bkind = bkind.data();
         D.wall_idx = wall_idx.data();
         D.probe_e = probe_e.data();
@@ -300,6 +301,7 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
     auto &owner = T.owner;
     owner.assign(N, make_int2(-1, 0));
+
     for (int en = 0; en < E; ++en) {
         int eo = e2o[en];
         for (int l = 0; l < 6; ++l) {
@@ -347,6 +349,23 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
                 }
             }
         }
+    // element of each node's wall-condition gradients: among the incident
+    // elements with a vertex on a wall edge the one of larger computational
+    // area, then lower original id; the owner element when none touches a
+    // wall
+    auto &bcel = T.bcel;
+    bcel.assign(N, -1);
+    for (int a = 0; a < N; ++a) {
+        int best = -1;
+        for (int k = fan_ptr[a]; k < fan_ptr[a + 1]; ++k) {
+            const int en = fan[k].x;
+            if (!is_wall[conn[6 * en]] && !is_wall[conn[6 * en + 1]] && !is_wall[conn[6 * en + 2]]) continue;
+            const int eo = e2o[en];
+            if (best < 0 || area2[eo] > area2[e2o[best]] || (area2[eo] == area2[e2o[best]] && eo < e2o[best]))
+                best = en;
+        }
+        bcel[a] = best >= 0 ? best : owner[a].x;
+    }
     // wall probes B = A + n dt, located by breadth-first search over the
     // adjacency from the node's fan (tie rule as everywhere else)
     auto &wall_idx = T.wall_idx; auto &probe_e = T.probe_e; auto &probe_xi = T.probe_xi;

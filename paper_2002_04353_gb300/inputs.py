@@ -286,6 +286,37 @@ def naca_omesh(ni: int, nj: int, chord: float = 200.0, thickness: float = 0.12,
                           first=first, growth=q))
 
 
+def wall_channel(nx: int = 12, hx: float = 8.0, first: float = 0.7, growth: float = 1.17,
+                 ny: int = 14, name="channel"):
+    """Flat channel periodic in x: wall edges at y = 0 and at the top ring,
+    nx cells of length hx along the wall, ny layers whose thickness starts
+    at `first` and grows by `growth`, each cell split along its SW-NE
+    diagonal.  Thin near-wall cells like those of an airfoil O-mesh, in a
+    geometry whose uniform-in-x flows stay one-dimensional."""
+    ys = [0.0]
+    d = first
+    for _ in range(ny):
+        ys.append(ys[-1] + d)
+        d *= growth
+    ys = np.array(ys)
+    V = quantize(np.array([[i * hx, y] for y in ys for i in range(nx)]))
+    vid = lambda i, j: (i % nx) + nx * j
+    tris, kinds = [], []
+    for j in range(len(ys) - 1):
+        for i in range(nx):
+            a, b, c, e = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            tris.append((a, b, c))
+            kinds.append((EDGE_WALL if j == 0 else 0, 0, 0))
+            tris.append((a, c, e))
+            kinds.append((0, EDGE_WALL if j == len(ys) - 2 else 0, 0))
+    tris = np.array(tris)
+    kinds = np.array(kinds, dtype=np.uint8)
+    _check_ccw(V, tris, (nx * hx, 0.0))
+    X, conn, ek = p2_from_tris(V, tris, (nx * hx, 0.0), kinds)
+    return Mesh(X, conn, ek, (nx * hx, 0.0), name=f"{name}_{nx}x{ny}",
+                meta=dict(hx=hx, first=first, growth=growth, height=float(ys[-1])))
+
+
 def omesh_size_for(n_nodes: float, aspect: float = 2.7):
     """(ni, nj) of an O-mesh with about n_nodes P2 nodes and ni/nj ~ aspect.
     A ni x nj vertex O-grid has ni*(4*nj - 2) P2 nodes."""

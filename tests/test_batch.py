@@ -1,0 +1,177 @@
+"""The batched step (alelb_batch_*): several independent cases of different
+sizes, motions and flows advanced by one launch per phase.
+
+Per case the batch must give what the case's solver gives alone: against
+the FP64 oracle to 1e-12 (FP64) or 2e-4 in rho, u, T (FP32 deviations);
+against the same solver stepped alone with the same element choices (equal
+walk counts) and values equal up to rounding, since the same per-node code
+is compiled into other kernels, where the compiler may fuse multiply-adds
+in another order (FP64 1e-13, FP32 5e-5 relative after 70 steps).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04353_gb300 import alelb, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-4
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _cases():
+    """Three unlike cases: a deforming periodic box, a plunging and a
+    pitching-plunging O-mesh of different sizes and Mach numbers."""
+    box = I.uniform_flow_case(n=12, L=24.0, period_steps=40.0)
+    om1 = I.naca_omesh(48, 16, chord=200.0, R=4000.0, first=1.0)
+    om2 = I.naca_omesh(64, 20, chord=200.0, thickness=0.15, R=4000.0, first=1.0)
+    return [
+        (box.mesh, box.motion, box.flow),
+        (om1, I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.002), I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)),
+        (om2, I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.05, 0.003, 50.0, 0.0, 20.0, 0.003),
+         I.flow_params(0.15, T_inf=0.3, Re=800.0, chord=200.0, angle_deg=2.0)),
+    ]
+
+
+def _solvers(cases, prec):
+    out = []
+    for mesh, motion, flow in cases:
+        m = alelb.Mesh(mesh, motion)
+        out.append(alelb.Solver(m, flow, prec))
+    return out
+
+
+@pytest.mark.parametrize("prec", [alelb.PREC_FP64, alelb.PREC_FP32_DEV])
+def test_batch_matches_oracle_per_case(prec):
+    cases = _cases()
+    ss = _solvers(cases, prec)
+    b = alelb.Batch(ss)
+    b.step(5)
+    b.sync()
+    for c, ((mesh, motion, flow), s) in enumerate(zip(cases, ss)):
+        o = O.Oracle(mesh, motion, flow)
+        o.step(5)
+        st = o.state()
+        assert s.time() == (5.0, 5)
+        mo = s.moments()
+        if prec == alelb.PREC_FP64:
+            f, g = s.get_pops()
+            assert _rel(f, st["f"]) < TOL64 and _rel(g, st["g"]) < TOL64, f"case {c}"
+            for k in ("rho", "ux", "uy", "T"):
+                assert _rel(mo[k], st[k]) < TOL64, f"case {c}: {k}"
+            if c > 0:
+                fo, fg = o.forces(), s.forces()
+                assert np.allclose(fg, fo, rtol=1e-10, atol=1e-12 * np.abs(fo).max())
+        else:
+            for k in ("rho", "ux", "uy", "T"):
+                scale = 1.0 if k in ("rho", "T") else max(np.abs(st["ux"]).max(), np.abs(st["uy"]).max())
+                err = np.abs(mo[k] - st[k]).max() / scale
+                assert err < TOL32, f"case {c}: {k} err {err:.2e}"
+
+
+@pytest.mark.parametrize("prec", [alelb.PREC_FP64, alelb.PREC_FP32_DEV])
+def test_batch_equals_solvers_stepped_alone(prec):
+    """70 steps cross the 64-step graph chunk; every case must equal the
+    same solver stepped alone up to rounding, with the same walks."""
+    tol = 1e-13 if prec == alelb.PREC_FP64 else 5e-5
+    cases = _cases()
+    alone = _solvers(cases, prec)
+    for s in alone:
+        s.lb_step(70)
+    batched = _solvers(cases, prec)
+    b = alelb.Batch(batched)
+    b.step(40)
+    b.step(30)
+    b.sync()
+    for c, (sa, sb) in enumerate(zip(alone, batched)):
+        fa, ga = sa.get_pops()
+        fb, gb = sb.get_pops()
+        assert _rel(fb, fa) < tol and _rel(gb, ga) < tol, f"case {c}"
+        ma, mb = sa.moments(), sb.moments()
+        for k in ma:
+            assert _rel(mb[k], ma[k]) < tol, f"case {c}: {k}"
+        assert sa.info()["walks"] == sb.info()["walks"]
+
+
+def test_tuning_changes_no_value():
+    cases = _cases()
+    plain = _solvers(cases, alelb.PREC_FP32_DEV)
+    bp = alelb.Batch(plain)
+    bp.step(6)
+    tuned = _solvers(cases, alelb.PREC_FP32_DEV)
+    bt = alelb.Batch(tuned)
+    bt.step(2)
+    choice = bt.tune(reps=2)  # one real step
+    assert all(choice[k] in (64, 128, 256) for k in ("k_stream_fast", "k_stream_slow", "k_moments",
+                                                     "k_deriv1", "k_collide"))
+    assert choice["k_stream_slow_grid"] > 0
+    bt.step(3)
+    bp.sync()
+    bt.sync()
+    for sa, sb in zip(plain, tuned):
+        assert sa.time() == sb.time() == (6.0, 6)
+        fa, ga = sa.get_pops()
+        fb, gb = sb.get_pops()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+        assert sa.info()["walks"] == sb.info()["walks"]
+
+
+def test_batch_and_single_steps_interleave():
+    cases = _cases()[:2]
+    alone = _solvers(cases, alelb.PREC_FP64)
+    for s in alone:
+        s.lb_step(6)
+    mixed = _solvers(cases, alelb.PREC_FP64)
+    b = alelb.Batch(mixed)
+    b.step(2)
+    mixed[0].lb_step(2)
+    mixed[1].lb_step(2)
+    b.step(2)
+    for sa, sb in zip(alone, mixed):
+        fa, ga = sa.get_pops()
+        fb, gb = sb.get_pops()
+        assert _rel(fb, fa) < 1e-13 and _rel(gb, ga) < 1e-13
+
+
+def test_batch_profile_counts_launches():
+    ss = _solvers(_cases(), alelb.PREC_FP32_DEV)
+    b = alelb.Batch(ss)
+    b.profile(True)
+    b.step(3)
+    kt = b.kernel_times()
+    for k in ("k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide"):
+        assert kt[k][1] == 3 and kt[k][0] > 0
+    assert kt["k_stream"][1] == 0
+    b.profile(False)
+
+
+def test_batch_arguments_are_checked():
+    cases = _cases()
+    ss = _solvers(cases[:2], alelb.PREC_FP64)
+    s32 = _solvers(cases[2:], alelb.PREC_FP32_DEV)
+    for bad in ([], [ss[0], ss[0]], [ss[0], s32[0]]):
+        with pytest.raises(alelb.AlelbError) as ex:
+            alelb.Batch(bad)
+        assert ex.value.status == -1
+    with pytest.raises(alelb.AlelbError):
+        alelb.Batch(ss).tune(reps=0)
+
+
+def test_case_error_is_reported_with_its_index():
+    """A non-finite state in one case (made on the host: NaN populations at
+    one node) is reported by batch_sync, naming that case."""
+    cases = _cases()
+    ss = _solvers(cases, alelb.PREC_FP64)
+    f, g = ss[1].get_pops()
+    f[:, 7] = np.nan
+    ss[1].set_pops(f, g)
+    b = alelb.Batch(ss)
+    b.step(1)
+    with pytest.raises(alelb.AlelbError) as ex:
+        b.sync()
+    assert ex.value.status == -7 and "case 1" in str(ex.value)

@@ -613,3 +613,27 @@ def test_missing_population_classification_matches_brute_force():
             else:
                 assert elem[i, a] == _brute_locate(mesh, fr, p), (a, i)
     assert n_missing > 20
+
+
+def test_wall_condition_thin_first_layer_stays_bounded():
+    """Reading R8 (the wall condition's first-order gradients in the node's
+    wall-side, i.e. smallest, incident element).  In a flat channel whose
+    first cell layer (0.7) is thinner than one lattice unit, the nodes one
+    layer off the wall have missing populations and take their own
+    previous-step fields as targets (Sec. IV.A).  A uniform tangential flow
+    at Mach 0.2 must then develop a boundary layer: the normal velocity
+    stays small (only the weak compression waves of the impulsive start
+    and of the growing layer, under 1e-3 against a free stream of 0.13)
+    and the density stays within 2% of 1.  The larger-element gradient, a difference taken
+    away from the wall at those nodes, blows this case up within 40 steps."""
+    mesh = I.wall_channel()
+    flow = I.flow_params(0.2, T_inf=0.3, Re=1e4, chord=1000.0)
+    o = O.Oracle(mesh, I.Motion.make(0), flow)
+    o.step(120)
+    st = o.state()
+    assert np.isfinite(st["rho"]).all()
+    assert np.abs(st["rho"] - 1.0).max() < 0.02
+    assert np.abs(st["uy"]).max() < 1e-3
+    # no slip: the wall nodes' tangential velocity well below the free stream
+    wall = np.abs(mesh.X[:, 1]) < 1e-12
+    assert np.abs(st["ux"][wall]).max() < 0.5 * flow.u_inf[0]
