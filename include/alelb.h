@@ -257,9 +257,77 @@ alelb_status alelb_batch_profile(alelb_batch *b, int32_t enable);
 alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **names, double *ms,
                                       int64_t *launches, int32_t *n);
 
+/* Learned departure-element proposal (the paper has no counterpart: it
+   locates every departure point by search, Sec. III).  A small network
+   (6 features -> 64 tanh -> 64 tanh -> 32 slot logits + 3 barycentric
+   guesses, 6883 parameters, flat order W1[64][6], b1[64], W2[64][64],
+   b2[64], W3[35][64], b3[35]) proposes, for a population left to the exact
+   path of the FP32-deviation propagation, an element of the node's
+   neighbour ring (its own elements by angle, then the elements across
+   their edges by angle, at most 32).  A proposal is used only when the
+   certified FP32 test that accepts previous-step elements accepts it
+   (departure point strictly inside; the segment from the node cannot
+   leave the mesh); the exact walk decides otherwise.  Streamed values are
+   bit-identical with and without the network.
+   Features of query (node a, direction i), FP32: d = -c^_i / h with h the
+   square root of the mean area of a's elements: d_x, d_y, |d|,
+   atan2(d_y, d_x) / pi, (number of a's elements) / 16, (ring size) / 32. */
+typedef struct alelb_mlp alelb_mlp;
+
+/* params: host array of 6883 FP32 values, or NULL for Glorot-uniform
+   weights and zero biases drawn from seed (splitmix64). */
+alelb_status alelb_mlp_create(const float *params, uint64_t seed, alelb_mlp **out);
+void alelb_mlp_destroy(alelb_mlp *m);
+/* The FP32 master parameters (rounded = 0) or the FP16 copies the network
+   runs with, widened to FP32 (rounded != 0); host array of 6883. */
+alelb_status alelb_mlp_get_params(alelb_mlp *m, int32_t rounded, float *params);
+
+/* Training data from a solver: for every query (internal node order,
+   q = 9 * ... laid out [direction][node]) at the next step's map time: its
+   features feat[q][6], the slot of the exact element (FP64 departure point,
+   exact walk) in the node's ring or -1 (departure on the node itself, a
+   node, outside the mesh, an element outside the ring, or no certified
+   FP32 map), the barycentric coordinates there bary[q][3] and the ring size
+   nring[q].  DEVICE arrays of 9 * n_nodes entries, caller-owned.
+   Synchronous. */
+alelb_status alelb_samples(alelb_solver *s, float *feat, int16_t *slot, float *bary, uint8_t *nring);
+
+/* Mean loss over n (1..2^31-1) samples -- cross-entropy of the softmax of
+   the first nring logits at slot, plus w_bary times the mean squared error
+   of the 3 guesses -- and its gradient (host, 6883 FP32, may be NULL),
+   computed with the FP16 weights in FP32 arithmetic.  Every slot must lie
+   in 0..nring-1.  DEVICE inputs.  Synchronous. */
+alelb_status alelb_mlp_loss_grad(alelb_mlp *m, const float *feat, const int16_t *slot,
+                                 const float *bary, const uint8_t *nring, int64_t n,
+                                 float w_bary, double *loss, float *grad);
+/* Adam (beta 0.9, 0.999, eps 1e-8) on that loss over `epochs` passes of
+   the n samples in minibatches of `batch`, the order of each pass a seeded
+   affine permutation of the samples; FP32 master weights, FP16 copies for
+   the forward pass.  epoch_loss (host, may be NULL): mean loss of each
+   pass.  DEVICE inputs.  Synchronous. */
+alelb_status alelb_mlp_train(alelb_mlp *m, const float *feat, const int16_t *slot,
+                             const float *bary, const uint8_t *nring, int64_t n, int32_t epochs,
+                             int32_t batch, float lr, float w_bary, uint64_t seed,
+                             double *epoch_loss);
+/* Inference as the propagation runs it (FP16 tensor-core MMA, FP32
+   accumulation): slot[q] = largest of the first nring logits (-1 when
+   nring = 0); out[q][35] all outputs (may be NULL).  DEVICE arrays.
+   Synchronous. */
+alelb_status alelb_mlp_predict(alelb_mlp *m, const float *feat, const uint8_t *nring, int64_t n,
+                               int32_t *slot, float *out);
+
+/* Use network m (NULL: none) for the proposals of an FP32-deviation
+   solver's later steps.  The network is not copied and must outlive its
+   use; ALELB_ERR_ARG for an FP64 solver. */
+alelb_status alelb_solver_set_mlp(alelb_solver *s, alelb_mlp *m);
+/* Counters since lb_init: {populations left to the exact path, proposals
+   made, proposals accepted}.  Synchronous. */
+alelb_status alelb_mlp_stats(alelb_solver *s, int64_t out[3]);
+
 const char *alelb_last_error(alelb_solver *s);
 const char *alelb_mesh_last_error(alelb_mesh *m);
 const char *alelb_batch_last_error(alelb_batch *b);
+const char *alelb_mlp_last_error(alelb_mlp *m);
 
 #ifdef __cplusplus
 }

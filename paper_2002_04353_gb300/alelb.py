@@ -35,7 +35,9 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_kernel_times", "alelb_info", "alelb_last_error", "alelb_mesh_last_error",
            "alelb_lb_step_noalloc", "alelb_batch_create", "alelb_batch_destroy", "alelb_batch_step",
            "alelb_batch_sync", "alelb_batch_tune", "alelb_batch_profile", "alelb_batch_kernel_times",
-           "alelb_batch_last_error"]
+           "alelb_batch_last_error", "alelb_mlp_create", "alelb_mlp_destroy", "alelb_mlp_get_params",
+           "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
+           "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error"]
 
 
 class AlelbError(RuntimeError):
@@ -103,6 +105,18 @@ def load(path: str = LIB_PATH):
     L.alelb_batch_kernel_times.argtypes = [p, C.POINTER(C.c_char_p), p, p, C.POINTER(i32)]
     L.alelb_batch_last_error.argtypes = [p]
     L.alelb_batch_last_error.restype = C.c_char_p
+    L.alelb_mlp_create.argtypes = [p, C.c_uint64, C.POINTER(p)]
+    L.alelb_mlp_destroy.argtypes = [p]
+    L.alelb_mlp_destroy.restype = None
+    L.alelb_mlp_get_params.argtypes = [p, i32, p]
+    L.alelb_samples.argtypes = [p, p, p, p, p]
+    L.alelb_mlp_loss_grad.argtypes = [p, p, p, p, p, C.c_int64, C.c_float, C.POINTER(d), p]
+    L.alelb_mlp_train.argtypes = [p, p, p, p, p, C.c_int64, i32, i32, C.c_float, C.c_float, C.c_uint64, p]
+    L.alelb_mlp_predict.argtypes = [p, p, p, C.c_int64, p, p]
+    L.alelb_solver_set_mlp.argtypes = [p, p]
+    L.alelb_mlp_stats.argtypes = [p, p]
+    L.alelb_mlp_last_error.argtypes = [p]
+    L.alelb_mlp_last_error.restype = C.c_char_p
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -113,6 +127,11 @@ def load(path: str = LIB_PATH):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data
+
+
+def _dptr(t):
+    """Device address of a CUDA tensor (or None)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
 
 
 def _f64(a):
@@ -278,6 +297,21 @@ class Solver:
                     "kernel_times")
         return {names[k].decode(): (float(ms[k]), int(n_l[k])) for k in range(n.value)}
 
+    def samples(self, feat, slot, bary, nring):
+        """Training data of the next step's queries into DEVICE tensors
+        (feat [9N, 6] f32, slot [9N] i16, bary [9N, 3] f32, nring [9N] u8)."""
+        self._check(load().alelb_samples(self.h, _dptr(feat), _dptr(slot), _dptr(bary), _dptr(nring)),
+                    "samples")
+
+    def set_mlp(self, net):
+        self._check(load().alelb_solver_set_mlp(self.h, None if net is None else net.h), "set_mlp")
+        self._net = net  # keep the network alive while in use
+
+    def mlp_stats(self):
+        out = np.zeros(3, dtype=np.int64)
+        self._check(load().alelb_mlp_stats(self.h, _ptr(out)), "mlp_stats")
+        return dict(exact_path=int(out[0]), proposed=int(out[1]), accepted=int(out[2]))
+
     def info(self):
         out = np.zeros(8)
         self._check(load().alelb_info(self.h, _ptr(out)), "info")
@@ -351,6 +385,64 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             load().alelb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+
+class Mlp:
+    """alelb_mlp_*: the learned departure-element proposal network.  Device
+    arrays are CUDA tensors (anything with data_ptr())."""
+    N_PARAMS = 6883
+
+    def __init__(self, params=None, seed=0):
+        L = load()
+        h = C.c_void_p()
+        arr = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        st = L.alelb_mlp_create(_ptr(arr), int(seed), C.byref(h))
+        if st != OK:
+            msg = L.alelb_mlp_last_error(h).decode() if h.value else ""
+            if h.value:
+                L.alelb_mlp_destroy(h)
+            raise AlelbError(st, "mlp_create: " + msg)
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            raise AlelbError(st, f"{what}: " + load().alelb_mlp_last_error(self.h).decode())
+
+    def params(self, rounded=False):
+        out = np.empty(self.N_PARAMS, dtype=np.float32)
+        self._check(load().alelb_mlp_get_params(self.h, int(bool(rounded)), _ptr(out)), "mlp_get_params")
+        return out
+
+    def loss_grad(self, feat, slot, bary, nring, w_bary=1.0):
+        loss = C.c_double()
+        g = np.empty(self.N_PARAMS, dtype=np.float32)
+        self._check(load().alelb_mlp_loss_grad(self.h, _dptr(feat), _dptr(slot), _dptr(bary), _dptr(nring),
+                                               int(slot.shape[0]), float(w_bary), C.byref(loss), _ptr(g)),
+                    "mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, feat, slot, bary, nring, epochs=1, batch=4096, lr=1e-3, w_bary=1.0, seed=0):
+        out = np.zeros(max(1, epochs))
+        self._check(load().alelb_mlp_train(self.h, _dptr(feat), _dptr(slot), _dptr(bary), _dptr(nring),
+                                           int(slot.shape[0]), int(epochs), int(batch), float(lr),
+                                           float(w_bary), int(seed), _ptr(out)), "mlp_train")
+        return out[:epochs]
+
+    def predict(self, feat, nring, slot_out, out=None):
+        self._check(load().alelb_mlp_predict(self.h, _dptr(feat), _dptr(nring), int(nring.shape[0]),
+                                             _dptr(slot_out), _dptr(out)), "mlp_predict")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().alelb_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -21,7 +21,7 @@ using namespace alelb;
 namespace alelb {
 
 const char *const KT_NAMES[KT_N] = {"k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1",
-                                    "k_collide"};
+                                    "k_collide", "k_propose"};
 
 MapScalarsF to_f32(const MapScalars &S, const HostTables &T)
 {
@@ -111,6 +111,9 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.fan = B.put(T.fan, st);
     D.owner = B.put(T.owner, st);
     D.bcel = B.put(T.bcel, st);
+    D.ring_ptr = B.put(T.ring_ptr, st);
+    D.ring = B.put(T.ring, st);
+    D.nscale = B.put(T.nscale, st);
     D.bkind = B.put(T.bkind, st);
     D.wall_idx = B.put(T.wall_idx, st);
     D.probe_e = B.put(T.probe_e, st);
@@ -316,9 +319,10 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
     const bool phi = !(s->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF));
     const bool fast = s->prec == ALELB_PREC_FP32_DEV;
     const MapScalarsF sf = to_f32(sc, m->T);
-    int seq[6], ns = 0;
+    int seq[KT_N], ns = 0;
     if (fast) {
         seq[ns++] = KT_FAST;
+        if (s->mlp) seq[ns++] = KT_PROPOSE;
         seq[ns++] = KT_SLOW;
         seq[ns++] = KT_MOMENTS;
     } else {
@@ -344,7 +348,10 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
             break;
         case KT_SLOW:
             k_stream_slow<S, A><<<4 * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st, s->d_err,
-                                                                    s->d_stats);
+                                                                    s->d_stats, s->mlp ? s->d_prop : nullptr);
+            break;
+        case KT_PROPOSE:
+            mlp_propose(s, sf);
             break;
         case KT_MOMENTS:
             k_moments<S, A><<<(N + 255) / 256, 256, 0, s->stream>>>(K, st, N, s->d_err);

@@ -198,7 +198,7 @@ struct alelb_batch {
     std::vector<cudaEvent_t> ev_in;
     cudaEvent_t ev_done = nullptr;
     // launch shapes (threads per block per kernel; blocks of k_stream_slow)
-    int bs[KT_N] = {128, 128, 128, 256, 256, 128};
+    int bs[KT_N] = {128, 128, 128, 256, 256, 128, 128};
     int slow_grid = 0;
     int n_sm = 152;
     std::map<int, cudaGraphExec_t> graphs;
@@ -207,8 +207,8 @@ struct alelb_batch {
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int k; cudaEvent_t a, b; };
     std::vector<Rec> pending;
-    double ms_acc[KT_N] = {0, 0, 0, 0, 0, 0};
-    int64_t n_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    double ms_acc[KT_N] = {};
+    int64_t n_acc[KT_N] = {};
 };
 
 namespace {

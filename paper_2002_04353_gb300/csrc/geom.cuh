@@ -359,6 +359,9 @@ struct MeshDev {
     const int2 *fan;       // (elem, loc | (sx+1)<<4 | (sy+1)<<6)
     const int2 *owner;     // (elem, local index) of each node
     const int *bcel;       // element of each node's wall-condition gradients
+    const int *ring_ptr;   // [N + 1] neighbour ring of each node (learned proposal)
+    const int *ring;       // ring elements, cache code of an unshifted element
+    const float2 *nscale;  // (length scale, number of own elements) per node
     const uint8_t *bkind;  // [N] boundary kind of the node (0 interior)
     const int *wall_idx;   // [N] index into the wall tables or -1
     const int *probe_e;    // [NW]

@@ -41,7 +41,8 @@ struct DevBuf {
     }
 };
 
-enum { KT_STREAM = 0, KT_FAST = 1, KT_SLOW = 2, KT_MOMENTS = 3, KT_DERIV1 = 4, KT_COLLIDE = 5, KT_N = 6 };
+enum { KT_STREAM = 0, KT_FAST = 1, KT_SLOW = 2, KT_MOMENTS = 3, KT_DERIV1 = 4, KT_COLLIDE = 5, KT_PROPOSE = 6,
+       KT_N = 7 };
 extern const char *const KT_NAMES[KT_N];
 
 // FP32 copies of the per-step map scalars.
@@ -50,6 +51,8 @@ MapScalarsF to_f32(const MapScalars &S, const HostTables &T);
 cudaError_t batch_fe_tables();
 // Status of a solver's sticky device errors (message in s->err).
 alelb_status check_sticky(alelb_solver *s);
+// Learned proposals for the solver's current work list (mlp.cu).
+cudaError_t mlp_propose(alelb_solver *s, const MapScalarsF &sf);
 
 
 } // namespace alelb
@@ -95,7 +98,9 @@ struct alelb_solver {
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int k; cudaEvent_t a, b; };
     std::vector<Rec> pending;
-    double ms_acc[KT_N] = {0, 0, 0, 0, 0, 0};
-    int64_t n_acc[KT_N] = {0, 0, 0, 0, 0, 0};
+    double ms_acc[KT_N] = {};
+    int64_t n_acc[KT_N] = {};
     int n_sm = 152;
+    alelb_mlp *mlp = nullptr; // learned proposal (not owned), FP32-deviation solvers
+    int *d_prop = nullptr;    // [9 N] proposal per work-list entry
 };

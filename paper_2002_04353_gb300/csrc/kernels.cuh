@@ -330,11 +330,16 @@ __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, Ma
 
 // One listed population (code = 9 node + direction): exact decision, then
 // interpolation, far-field equilibrium or the missing-population condition.
+// pc: a proposed element (cache code) or -1; it is taken only when the
+// certified test that accepts previous-step elements accepts it, with the
+// interpolation offset formed as the FP32 walk forms it, so the result is
+// the walk's bit for bit.  hits (may be null) counts the accepted ones.
 template <class S, class A>
 __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStatic &MS,
                                                  const MapScalars &sc, const MapScalarsF &sf,
                                                  const KinParams<A> &K, const StateDev<S> &st,
-                                                 int *err, int code)
+                                                 int *err, int code, int pc = -1,
+                                                 unsigned long long *hits = nullptr)
 {
     const int N = M.N;
     {
@@ -344,7 +349,28 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
         float qx = 0.f, qy = 0.f;
         int src;
-        const Loc L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err);
+        Loc L;
+        int pe;
+        float pxi, peta;
+        if (pc >= 0 && F.ok && !literal && fast_decide(M, F, Xf, M.bdist[a], a, i, pc, pe, pxi, peta)) {
+            // strictly inside element pe: the walk finds pe with no shift and
+            // forms the offset from the element's first vertex as below
+            const float cx = (float)c_cx[i], cy = (float)c_cy[i];
+            const float chx = F.A11 * cx + F.A12 * cy - F.W1;
+            const float chy = F.A21 * cx + F.A22 * cy - F.W2;
+            const float4 v = M.evf[3 * pe];
+            const float x0 = (v.x - Xf.x) + (v.z - Xf.z), y0 = (v.y - Xf.y) + (v.w - Xf.w);
+            qx = -chx - x0;
+            qy = -chy - y0;
+            L.e = pe;
+            L.sx = L.sy = 0;
+            L.kind = 0;
+            L.vnode = -1;
+            src = -1;
+            if (hits) atomicAdd(hits, 1ull);
+        } else {
+            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err);
+        }
         A fi = 0, gi = 0;
         if (src >= 0) {
             fi = (A)st.post[i * N + src];
@@ -438,12 +464,14 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
 template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
                                                      MapScalarsF sf, KinParams<A> K, StateDev<S> st,
-                                                     int *err, unsigned long long *stats)
+                                                     int *err, unsigned long long *stats,
+                                                     const int *prop)
 {
     const unsigned n = *st.wcount;
     if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
     for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x)
-        stream_slow_item(M, MS, sc, sf, K, st, err, st.work[w]);
+        stream_slow_item(M, MS, sc, sf, K, st, err, st.work[w], prop ? prop[w] : -1,
+                         prop && stats ? stats + 1 : nullptr);
 }
 
 template <class S, class A>

@@ -55,7 +55,8 @@ struct HostTables {
     double mp[16] = {0};
     std::vector<int> node_old2new, node_new2old, elem_old2new, elem_new2old;
     std::vector<double2> X, ev, probe_xi;
-    std::vector<int> nbr, conn, rank, orig, fan_ptr, wall_idx, probe_e, bcel;
+    std::vector<int> nbr, conn, rank, orig, fan_ptr, wall_idx, probe_e, bcel, ring_ptr, ring;
+    std::vector<float2> nscale;
     std::vector<uint32_t> einfo;
     std::vector<int2> fan, owner, wedges;
     std::vector<uint8_t> bkind;
@@ -92,6 +93,9 @@ struct HostTables {
         D.Xf = Xf.data();
         D.v0f = v0f.data();
         D.evf = evf.data();
+        D.ring_ptr = ring_ptr.data();
+        D.ring = ring.data();
+        D.nscale = nscale.data();
         return D;
     }
     MapStatic host_map() const
@@ -136,6 +140,65 @@ inline MapScalars map_scalars(int kind, const double *p, double t)
 
 // Validates the description and fills T.  Returns ALELB_OK or an error
 // with a message in err.
+// Neighbour ring of each node for the learned departure-element proposal:
+// the node's own elements sorted by the angle of their centroid about the
+// node, then the elements across their edges (not already listed) sorted
+// the same way, at most RING_MAX, in the cache code of an unshifted
+// element (elements reached through a periodic shift are left out: the
+// verified fast test accepts unshifted elements only).  nscale[a] = (h, n):
+// h the square root of the mean area of the node's elements, n their count.
+constexpr int RING_MAX = 32;
+inline void build_rings(HostTables &T, const std::vector<double> &area2)
+{
+    const int N = T.N;
+    T.ring_ptr.assign(N + 1, 0);
+    T.ring.clear();
+    T.nscale.assign(N, make_float2(1.0f, 0.0f));
+    std::vector<std::pair<double, int>> g1, g2;
+    std::vector<int> seen(T.E, -1);
+    for (int a = 0; a < N; ++a) {
+        g1.clear();
+        g2.clear();
+        const double ax = T.X[a].x, ay = T.X[a].y;
+        double asum = 0;
+        int nf = 0;
+        auto angle = [&](int e) {
+            const double cx = (T.ev[3 * e].x + T.ev[3 * e + 1].x + T.ev[3 * e + 2].x) / 3.0;
+            const double cy = (T.ev[3 * e].y + T.ev[3 * e + 1].y + T.ev[3 * e + 2].y) / 3.0;
+            return std::atan2(cy - ay, cx - ax);
+        };
+        for (int k = T.fan_ptr[a]; k < T.fan_ptr[a + 1]; ++k) {
+            const int e = T.fan[k].x, code = T.fan[k].y;
+            asum += 0.5 * area2[T.orig[e]];
+            ++nf;
+            seen[e] = a;
+            if (((code >> 4) & 3) != 1 || ((code >> 6) & 3) != 1) continue; // shifted
+            g1.push_back({angle(e), e});
+        }
+        for (int k = T.fan_ptr[a]; k < T.fan_ptr[a + 1]; ++k) {
+            const int e = T.fan[k].x, code = T.fan[k].y;
+            if (((code >> 4) & 3) != 1 || ((code >> 6) & 3) != 1) continue;
+            for (int j = 0; j < 3; ++j) {
+                const int nb = T.nbr[3 * e + j];
+                if (nb < 0 || seen[nb] == a) continue;
+                seen[nb] = a;
+                const uint32_t inf = (T.einfo[e] >> (8 * j)) & 255u;
+                if (((inf >> 4) & 3) != 1 || ((inf >> 6) & 3) != 1) continue; // across a periodic edge
+                g2.push_back({angle(nb), nb});
+            }
+        }
+        std::sort(g1.begin(), g1.end());
+        std::sort(g2.begin(), g2.end());
+        int n = 0;
+        for (auto &p : g1)
+            if (n < RING_MAX) { T.ring.push_back(p.second | (1 << 28) | (1 << 30)); ++n; }
+        for (auto &p : g2)
+            if (n < RING_MAX) { T.ring.push_back(p.second | (1 << 28) | (1 << 30)); ++n; }
+        T.ring_ptr[a + 1] = T.ring_ptr[a] + n;
+        T.nscale[a] = make_float2((float)std::sqrt(asum / std::max(nf, 1)), (float)nf);
+    }
+}
+
 inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::string &err)
 {
     if (!d || d->n_nodes <= 0 || d->n_elems <= 0 || !d->X || !d->conn || !d->edge_kind) {
@@ -540,6 +603,7 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
             }
         }
     }
+    build_rings(T, area2);
     return ALELB_OK;
 }
 
