@@ -248,6 +248,97 @@ def run_batched(alelb, torch, dev, world, rank, args):
             "gpu_launches": 5 * K}
 
 
+def run_learned(alelb, torch, dev, args):
+    """The learned departure-element proposal.  Training data: every query of
+    the 600,320-node deforming pitching mesh (Mach 0.75, k = 0.08) at 10
+    map times evenly spread over one pitch period (samples depend on the
+    map only, not on the flow).  Deployment: the 1,999,200-node pitching
+    mesh (1200 x 417 rings) at Mach 0.5, alpha = 2.5 deg sin(omega t),
+    stepped with and without the network from the same start; the
+    populations must come out bit-identical."""
+    import math as _m
+    c3 = I.pitch_case(ni=640, nj=235)
+    s3 = alelb.Solver(alelb.Mesh(c3.mesh, c3.motion), c3.flow, alelb.PREC_FP32_DEV)
+    om = float(c3.motion.params[2])
+    period = 2.0 * _m.pi / om
+    q = 9 * c3.mesh.n_nodes
+    parts = []
+    t0 = time.perf_counter()
+    for k in range(10):
+        feat = torch.empty((q, 6), dtype=torch.float32, device=dev)
+        slot = torch.empty(q, dtype=torch.int16, device=dev)
+        bary = torch.empty((q, 3), dtype=torch.float32, device=dev)
+        nring = torch.empty(q, dtype=torch.uint8, device=dev)
+        s3.samples(feat, slot, bary, nring, t=1.0 + k * period / 10.0)
+        keep = slot >= 0
+        parts.append((feat[keep], slot[keep], bary[keep], nring[keep]))
+    s3.close()
+    logged = 10 * q
+    feat, slot, bary, nring = [torch.cat([p_[k] for p_ in parts]).contiguous() for k in range(4)]
+    del parts
+    log_s = time.perf_counter() - t0
+    net = alelb.Mlp(seed=0)
+    n = int(slot.shape[0])
+    ps = torch.empty(n, dtype=torch.int32, device=dev)
+    t0 = time.perf_counter()
+    losses = net.train(feat, slot, bary, nring, epochs=args.mlp_epochs, batch=8192, lr=2e-3, w_bary=0.5, seed=1)
+    train_s = time.perf_counter() - t0
+    net.predict(feat, nring, ps)
+    train_hit = (ps == slot.int()).float().mean().item()
+    del feat, slot, bary, nring, ps
+    c5 = I.pitch_case(ni=1200, nj=417, Ma=0.5, alpha0_deg=0.0)
+    m5 = alelb.Mesh(c5.mesh, c5.motion)
+    N = c5.mesh.n_nodes
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    pops = {}
+    for label, use in (("without", False), ("with", True)):
+        s = alelb.Solver(m5, c5.flow, alelb.PREC_FP32_DEV, stream=stream.cuda_stream)
+        if use:
+            s.set_mlp(net)
+        s.lb_step(max(3, args.warmup))
+        s.sync()
+        st0 = s.mlp_stats()
+        K = args.mlp_steps
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        s.profile(True)
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                evs[k][0].record(stream)
+                s.lb_step(1)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        kt = s.kernel_times()
+        s.profile(False)
+        st1 = s.mlp_stats()
+        exact = st1["exact_path"] - st0["exact_path"]
+        prop = st1["proposed"] - st0["proposed"]
+        acc = st1["accepted"] - st0["accepted"]
+        res[label] = {"value": N * K / (ms * 1e-3) / 1e6, "ms_per_step": ms / K,
+                      "exact_path_per_step": exact / K,
+                      "kernels": {k_: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]}
+                                  for k_, v in kt.items() if v[1]}}
+        if use:
+            res[label].update({"proposals_per_step": prop / K, "hit_rate": acc / max(1, prop),
+                               "fallback_rate": 1.0 - acc / max(1, exact)})
+        pops[label] = s.get_pops()
+        s.close()
+    identical = bool(np.array_equal(pops["with"][0], pops["without"][0]) and
+                     np.array_equal(pops["with"][1], pops["without"][1]))
+    net.close()
+    return {"unit": UNIT, "workload": f"pitch {N} nodes, Mach 0.5, alpha 2.5 deg sin(wt), k 0.08",
+            "steps": args.mlp_steps, "without": res["without"], "with": res["with"],
+            "gain": res["with"]["value"] / res["without"]["value"],
+            "bit_identical_populations": identical,
+            "training": {"samples_logged": logged, "samples_in_ring": n, "epochs": args.mlp_epochs,
+                         "loss_per_epoch": [round(float(x), 4) for x in losses], "hit_rate_on_training_data": train_hit,
+                         "log_seconds": log_s, "train_seconds": train_s,
+                         "source": f"pitch mesh {c3.mesh.n_nodes} nodes, 10 map times over one period"}}
+
+
 def run_ours(args):
     import torch
     from paper_2002_04353_gb300 import alelb
@@ -339,6 +430,7 @@ def run_ours(args):
                "note": "host-resident state: set_pops, lb_step(1), get_pops per step (FP64 host arrays)"}
 
     batched = None if args.no_batched else run_batched(alelb, torch, dev, world, rank, args)
+    learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -370,6 +462,7 @@ def run_ours(args):
             "kernels_fp64": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt64.items()},
             "gpu_launches": 5 * K,
             "batched": batched,
+            "learned_proposal": learned,
             "locate": {"walks_per_step": info32["walks_timed"] / K,
                        "verified_previous_element_rate": 1.0 - info32["walks_timed"] / (9.0 * N * K)},
             "step_ms": [round(x, 4) for x in info32["step_ms"]],
@@ -393,6 +486,9 @@ def main():
     ap.add_argument("--workload", default="plunge150k", choices=sorted(WORKLOADS))
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--mlp-epochs", type=int, default=2)
+    ap.add_argument("--mlp-steps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

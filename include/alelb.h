@@ -282,15 +282,17 @@ void alelb_mlp_destroy(alelb_mlp *m);
    runs with, widened to FP32 (rounded != 0); host array of 6883. */
 alelb_status alelb_mlp_get_params(alelb_mlp *m, int32_t rounded, float *params);
 
-/* Training data from a solver: for every query (internal node order,
-   q = 9 * ... laid out [direction][node]) at the next step's map time: its
+/* Training data from a solver's mesh and map: for every query at map time
+   t (internal node order, laid out [direction][node]), with no change to
+   the solver's state: its
    features feat[q][6], the slot of the exact element (FP64 departure point,
    exact walk) in the node's ring or -1 (departure on the node itself, a
    node, outside the mesh, an element outside the ring, or no certified
    FP32 map), the barycentric coordinates there bary[q][3] and the ring size
    nring[q].  DEVICE arrays of 9 * n_nodes entries, caller-owned.
    Synchronous. */
-alelb_status alelb_samples(alelb_solver *s, float *feat, int16_t *slot, float *bary, uint8_t *nring);
+alelb_status alelb_samples(alelb_solver *s, double t, float *feat, int16_t *slot, float *bary,
+                           uint8_t *nring);
 
 /* Mean loss over n (1..2^31-1) samples -- cross-entropy of the softmax of
    the first nring logits at slot, plus w_bary times the mean squared error

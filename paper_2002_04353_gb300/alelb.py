@@ -109,7 +109,7 @@ def load(path: str = LIB_PATH):
     L.alelb_mlp_destroy.argtypes = [p]
     L.alelb_mlp_destroy.restype = None
     L.alelb_mlp_get_params.argtypes = [p, i32, p]
-    L.alelb_samples.argtypes = [p, p, p, p, p]
+    L.alelb_samples.argtypes = [p, d, p, p, p, p]
     L.alelb_mlp_loss_grad.argtypes = [p, p, p, p, p, C.c_int64, C.c_float, C.POINTER(d), p]
     L.alelb_mlp_train.argtypes = [p, p, p, p, p, C.c_int64, i32, i32, C.c_float, C.c_float, C.c_uint64, p]
     L.alelb_mlp_predict.argtypes = [p, p, p, C.c_int64, p, p]
@@ -297,11 +297,14 @@ class Solver:
                     "kernel_times")
         return {names[k].decode(): (float(ms[k]), int(n_l[k])) for k in range(n.value)}
 
-    def samples(self, feat, slot, bary, nring):
-        """Training data of the next step's queries into DEVICE tensors
-        (feat [9N, 6] f32, slot [9N] i16, bary [9N, 3] f32, nring [9N] u8)."""
-        self._check(load().alelb_samples(self.h, _dptr(feat), _dptr(slot), _dptr(bary), _dptr(nring)),
-                    "samples")
+    def samples(self, feat, slot, bary, nring, t=None):
+        """Training data of the queries at map time t (default: the next
+        step's) into DEVICE tensors (feat [9N, 6] f32, slot [9N] i16,
+        bary [9N, 3] f32, nring [9N] u8)."""
+        if t is None:
+            t = self.time()[0] + 1.0
+        self._check(load().alelb_samples(self.h, float(t), _dptr(feat), _dptr(slot), _dptr(bary),
+                                         _dptr(nring)), "samples")
 
     def set_mlp(self, net):
         self._check(load().alelb_solver_set_mlp(self.h, None if net is None else net.h), "set_mlp")

@@ -115,6 +115,7 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.ring = B.put(T.ring, st);
     D.nscale = B.put(T.nscale, st);
     D.bkind = B.put(T.bkind, st);
+    D.vzero = B.put(T.vzero, st);
     D.wall_idx = B.put(T.wall_idx, st);
     D.probe_e = B.put(T.probe_e, st);
     D.probe_xi = B.put(T.probe_xi, st);

@@ -363,6 +363,7 @@ struct MeshDev {
     const int *ring;       // ring elements, cache code of an unshifted element
     const float2 *nscale;  // (length scale, number of own elements) per node
     const uint8_t *bkind;  // [N] boundary kind of the node (0 interior)
+    const uint8_t *vzero;  // [N] 1: mesh velocity exactly zero at all times
     const int *wall_idx;   // [N] index into the wall tables or -1
     const int *probe_e;    // [NW]
     const double2 *probe_xi; // [NW]
@@ -717,8 +718,29 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
     for (int k = 0; k < 6; ++k)
         if (cn[k] == a) l = k;
     if (!(len + F.eps_c < bdist) && l < 0) return false;
-    const float4 ed = M.ejf[2 * e];
     const float4 J = M.ejf[2 * e + 1];
+    if (l >= 0) {
+        // the node is node l of element e: its local coordinates are exact
+        // (0, 1/2 or 1), so only the small offset -c^ is taken through the
+        // FP32 inverse Jacobian; errors: eps_c on c^ (plus 2^-25 for the
+        // FP64 rounding of the canonical departure point), u/2 on each J
+        // entry, the products, the sums and the additions to the node's
+        // coordinates
+        const float xl[6] = {0.0f, 1.0f, 0.0f, 0.5f, 0.5f, 0.0f};
+        const float el[6] = {0.0f, 0.0f, 1.0f, 0.0f, 0.5f, 0.5f};
+        const float rx = -chx, ry = -chy;
+        const float t11 = J.x * rx, t12 = J.y * ry, t21 = J.z * rx, t22 = J.w * ry;
+        xi = xl[l] + (t11 + t12);
+        eta = el[l] + (t21 + t22);
+        const float l0 = 1.0f - xi - eta;
+        const float eq = F.eps_c + 2.98023223876953125e-08f;
+        const float S1 = fabsf(J.x) + fabsf(J.y), S2 = fabsf(J.z) + fabsf(J.w);
+        const float m1 = 2.0f * (S1 * eq + 3.0f * u * (fabsf(t11) + fabsf(t12))) + 2.0f * u * fabsf(xi);
+        const float m2 = 2.0f * (S2 * eq + 3.0f * u * (fabsf(t21) + fabsf(t22))) + 2.0f * u * fabsf(eta);
+        const float m0 = m1 + m2 + 4.0f * u * (1.0f + fabsf(xi) + fabsf(eta));
+        return xi > m1 && eta > m2 && l0 > m0;
+    }
+    const float4 ed = M.ejf[2 * e];
     float dx, dy; // node position relative to v0
     if (l >= 0) {
         const float wx[3] = {0.0f, ed.x, ed.z}, wy[3] = {0.0f, ed.y, ed.w};
@@ -934,6 +956,12 @@ ALELB_HD inline void mixed_locate_node(const MeshDev &M, const MapStatic &MS,
     for (int i = 0; i < NQ; ++i) {
         int e;
         float qx, qy;
+        if (i == 0 && M.vzero[a]) { // c^_0 is exactly zero: the node's own value
+            if (fast9) fast9[i] = 1;
+            elem9[i] = -2;
+            kind9[i] = 0;
+            continue;
+        }
         const bool f = F.ok && fast_decide(M, F, Xf, M.bdist[a], a, i, cache[(size_t)i * M.N + a], e, qx, qy);
         if (fast9) fast9[i] = f ? 1 : 0;
         if (f) {

@@ -270,11 +270,15 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
         int cache[NQ];
 #pragma unroll
         for (int i = 0; i < NQ; ++i) cache[i] = st.cache[i * N + a];
+        const bool v0 = M.vzero[a];
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             int e;
             float xi, eta;
-            if (F.ok && fast_decide(M, F, Xf, bd, a, i, cache[i], e, xi, eta)) {
+            if (i == 0 && v0) { // c^_0 exactly zero: the node's own value
+                st.str[a] = st.post[a];
+                st.str[NQ * N + a] = st.post[NQ * N + a];
+            } else if (F.ok && fast_decide(M, F, Xf, bd, a, i, cache[i], e, xi, eta)) {
                 A Nw[6];
                 shape6<A>((A)xi, (A)eta, Nw);
                 A fi = 0, gi = 0;

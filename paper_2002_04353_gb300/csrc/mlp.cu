@@ -665,11 +665,12 @@ extern "C" alelb_status alelb_mlp_predict(alelb_mlp *m, const float *feat, const
     return ALELB_OK;
 }
 
-extern "C" alelb_status alelb_samples(alelb_solver *s, float *feat, int16_t *slot, float *bary, uint8_t *nring)
+extern "C" alelb_status alelb_samples(alelb_solver *s, double t, float *feat, int16_t *slot, float *bary,
+                                      uint8_t *nring)
 {
     if (!s || !s->mesh || !feat || !slot || !bary || !nring) return ALELB_ERR_ARG;
     alelb_mesh *m = s->mesh;
-    const MapScalars sc = map_scalars(m->T.mkind, m->T.mp, s->t + 1.0);
+    const MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t);
     k_samples<<<(m->T.N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, feat,
                                                             slot, bary, nring, s->d_err);
     cudaError_t st = cudaGetLastError();

@@ -59,7 +59,7 @@ struct HostTables {
     std::vector<float2> nscale;
     std::vector<uint32_t> einfo;
     std::vector<int2> fan, owner, wedges;
-    std::vector<uint8_t> bkind;
+    std::vector<uint8_t> bkind, vzero;
     std::vector<double> ms;
     std::vector<float4> ejf, Xf, v0f, evf;
     std::vector<float> bdist, msf;
@@ -84,6 +84,7 @@ struct HostTables {
         D.owner = owner.data();
         D.bcel = bcel.data();
         D.bkind = bkind.data();
+        D.vzero = vzero.data();
         D.wall_idx = wall_idx.data();
         D.probe_e = probe_e.data();
         D.probe_xi = probe_xi.data();
@@ -563,6 +564,12 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
     for (size_t k = 0; k < (size_t)3 * E; ++k) T.evf[k] = split(ev[k]);
     T.msf.resize(T.ms.size());
     for (size_t k = 0; k < T.ms.size(); ++k) T.msf[k] = (float)T.ms[k];
+    // nodes whose mesh velocity is exactly zero at every time: no motion, or
+    // a blended map whose blending factor is exactly zero there (then the
+    // rest population's c^ is exactly zero and it keeps the node's value)
+    T.vzero.assign(N, 0);
+    for (int a = 0; a < N; ++a)
+        T.vzero[a] = (uint8_t)(T.mkind == MK_NONE || (T.mkind == MK_BLENDED && T.ms[a] == 0.0));
     // lower bound of every node's distance to the nearest boundary edge
     // (capped at DCAP): a departure segment shorter than this cannot leave
     // the mesh
