@@ -57,27 +57,49 @@ def workload(name="plunge150k"):
     return WORKLOADS[name]()
 
 
-def algorithmic_bytes_stream(n_nodes, n_elems, pop_bytes):
-    """Bytes the propagation kernel must move per launch: read the 18
-    post-collision populations of every node once, write 18 streamed
-    populations and Q'_x, Q'_y, mu/(rho T); read node coordinates (16 B),
-    the node fans (3 entries of 8 B per node plus the 4 B offset) and each
-    element's walk record once (frame 48 B, neighbours 12 B, edge info 4 B,
-    rank 4 B, connectivity 24 B)."""
-    per_node = 18 * pop_bytes * 2 + 3 * pop_bytes + 16 + 3 * 8 + 4
-    per_elem = 48 + 12 + 4 + 4 + 24
-    return n_nodes * per_node + n_elems * per_elem
+def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4):
+    """Algorithmic bytes of one launch: every value the kernel must read or
+    write, each counted once (FP32-deviation form, pop_bytes = 4).
 
-
-def algorithmic_bytes_step(n_nodes, n_elems, pop_bytes):
-    """Bytes one whole step must move: the propagation kernel's, plus the
-    derivative pass (read Q'_x, Q'_y, mu/(rho T), write D_x, D_y) and the
-    collision (read D, the 18 streamed populations; write 18 populations
-    and rho, u, T), plus the owner-element records of both passes."""
-    s = algorithmic_bytes_stream(n_nodes, n_elems, pop_bytes)
-    s += n_nodes * (3 * pop_bytes + 2 * pop_bytes + 8)
-    s += n_nodes * (2 * pop_bytes + 36 * pop_bytes + 4 * pop_bytes + 8)
-    return s
+    k_stream_fast   per node: 18 post-collision populations read and (for the
+                    settled ones, about all) 18 streamed written, 9 element-
+                    cache words, the FP32 hi/lo coordinates (16 B), the
+                    boundary distance and the zero-velocity flag (5 B); per
+                    element the FP32 inverse Jacobian and edge vectors (32 B)
+                    and the connectivity (24 B)
+    k_stream_slow   per exact-path population: its work entry, node
+                    coordinates, six post-collision values of f and of g,
+                    two streamed values, its cache word, the element record
+                    (FP32 frame 48 B, inverse Jacobian 32 B, connectivity
+                    24 B): 4 + 16 + 12 pop + 2 pop + 4 + 104 B
+    k_moments       per node: 18 streamed populations read, Q'_x, Q'_y,
+                    mu/(rho T) written
+    k_deriv1        per node: Q'_x, Q'_y, mu/(rho T) read (own values and the
+                    owner element's, each once), owner record (8 B), node
+                    coordinates (16 B), D_x, D_y written; per element the
+                    inverse Jacobian (16 B) and connectivity (24 B)
+    k_collide       per node: 18 streamed populations read, D_x, D_y, owner
+                    record, coordinates; 18 populations and rho, u, T
+                    written; per element the same 40 B
+    k_stream        (FP64 form) per node: 18 populations read and written,
+                    Q', mu/(rho T) written, FP64 coordinates, fan entries;
+                    per element frame, neighbours, edge info, rank,
+                    connectivity (92 B)
+    """
+    N, E, W, p = n_nodes, n_elems, exact_items, pop_bytes
+    if kernel == "k_stream_fast":
+        return N * (36 * p + 36 + 16 + 5) + E * 56
+    if kernel == "k_stream_slow":
+        return W * (4 + 16 + 14 * p + 4 + 104)
+    if kernel == "k_moments":
+        return N * (18 * p + 3 * p)
+    if kernel == "k_deriv1":
+        return N * (3 * p + 8 + 16 + 2 * p) + E * 40
+    if kernel == "k_collide":
+        return N * (18 * p + 2 * p + 8 + 16 + 18 * p + 4 * p) + E * 40
+    if kernel == "k_stream":
+        return N * (36 * p + 3 * p + 16 + 3 * 8 + 4) + E * 92
+    return 0
 
 
 def measured_peaks():
@@ -399,14 +421,16 @@ def run_ours(args):
     value64 = world * N * max(2, K // 4) / (ms64 * 1e-3) / 1e6
 
     # dominant kernel roofline (FP32-deviation form)
+    W = info32["walks_timed"] / K
     top = max(kt32, key=lambda k: kt32[k][0])
     top_ms, top_n = kt32[top]
-    if top == "k_stream":
-        alg = algorithmic_bytes_stream(N, E, 4)
-    else:
-        alg = algorithmic_bytes_step(N, E, 4) - algorithmic_bytes_stream(N, E, 4)
+    alg = kernel_bytes(top, N, E, W)
     achieved = alg / (top_ms / top_n * 1e-3) / 1e9
-    step_bytes = algorithmic_bytes_step(N, E, 4)
+    per_kernel = {k: {"algorithmic_bytes": kernel_bytes(k, N, E, W),
+                      "achieved_gbs": kernel_bytes(k, N, E, W) / (v[0] / v[1] * 1e-3) / 1e9}
+                  for k, v in kt32.items() if v[1]}
+    step_bytes = sum(kernel_bytes(k, N, E, W) for k in ("k_stream_fast", "k_stream_slow", "k_moments",
+                                                        "k_deriv1", "k_collide"))
 
     # end to end through the C-ABI with host buffers: host-resident state,
     # every step uploads the populations from pinned host memory, advances
@@ -455,9 +479,13 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": None, "algorithmic_bytes_per_launch": alg,
-                         "launch_ms": top_ms / top_n},
+                         "launch_ms": top_ms / top_n,
+                         "note": ("the exact-path kernel is latency-bound (one short dependent chain per "
+                                  "listed population), not bandwidth-bound" if top == "k_stream_slow" else "")},
+            "kernel_rooflines": per_kernel,
             "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
-                              "achieved_gbs": step_bytes / (ms32 / K * 1e-3) / 1e9},
+                              "achieved_gbs": step_bytes / (ms32 / K * 1e-3) / 1e9,
+                              "frac": step_bytes / (ms32 / K * 1e-3) / 1e9 / peak},
             "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt32.items()},
             "kernels_fp64": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt64.items()},
             "gpu_launches": 5 * K,

@@ -289,10 +289,10 @@ class Solver:
         self._check(load().alelb_profile(self.h, int(bool(enable))), "profile")
 
     def kernel_times(self):
-        names = (C.c_char_p * 8)()
-        ms = np.zeros(8)
-        n_l = np.zeros(8, dtype=np.int64)
-        n = C.c_int32(8)
+        names = (C.c_char_p * 16)()
+        ms = np.zeros(16)
+        n_l = np.zeros(16, dtype=np.int64)
+        n = C.c_int32(16)
         self._check(load().alelb_kernel_times(self.h, names, _ptr(ms), _ptr(n_l), C.byref(n)),
                     "kernel_times")
         return {names[k].decode(): (float(ms[k]), int(n_l[k])) for k in range(n.value)}
@@ -377,10 +377,10 @@ class Batch:
         self._check(load().alelb_batch_profile(self.h, int(bool(enable))), "batch_profile")
 
     def kernel_times(self):
-        names = (C.c_char_p * 8)()
-        ms = np.zeros(8)
-        n_l = np.zeros(8, dtype=np.int64)
-        n = C.c_int32(8)
+        names = (C.c_char_p * 16)()
+        ms = np.zeros(16)
+        n_l = np.zeros(16, dtype=np.int64)
+        n = C.c_int32(16)
         self._check(load().alelb_batch_kernel_times(self.h, names, _ptr(ms), _ptr(n_l), C.byref(n)),
                     "batch_kernel_times")
         return {names[k].decode(): (float(ms[k]), int(n_l[k])) for k in range(n.value)}

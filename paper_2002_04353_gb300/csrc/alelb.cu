@@ -116,6 +116,8 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.nscale = B.put(T.nscale, st);
     D.bkind = B.put(T.bkind, st);
     D.vzero = B.put(T.vzero, st);
+    D.cone = B.put(T.cone, st);
+    D.conek = B.put(T.conek, st);
     D.wall_idx = B.put(T.wall_idx, st);
     D.probe_e = B.put(T.probe_e, st);
     D.probe_xi = B.put(T.probe_xi, st);

@@ -103,22 +103,38 @@ __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__
     append_work(C.st, a, slow);
 }
 
+// The exact path over the work lists of all cases as one list: block-local
+// prefix sum of the cases' counts, one population per thread, its case by a
+// ballot over the prefix sums; the case descriptor is read from global
+// memory (the populations of a warp mostly share one case).
 template <class S, class A>
 __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__ cases, int B,
                                                const MapScalars *__restrict__ sc,
                                                const MapScalarsF *__restrict__ sf, int count)
 {
-    __shared__ SharedCase<S, A> sh;
-    for (int c = 0; c < B; ++c) {
-        __syncthreads(); // the previous case's descriptor is no longer read
-        sh.load(cases, sc, sf, c);
-        __syncthreads();
-        const CaseDev<S, A> &C = sh.C();
-        const unsigned n = *C.st.wcount;
-        if (count && C.stats && blockIdx.x == 0 && threadIdx.x == 0 && n)
-            atomicAdd(C.stats, (unsigned long long)n);
-        for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x)
-            stream_slow_item(C.M, C.MS, sh.SC(), sh.SF(), C.K, C.st, C.err, C.st.work[w]);
+    __shared__ unsigned pre[BATCH_MAX + 1];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned n = lane < B ? *cases[lane].st.wcount : 0u;
+        unsigned incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        pre[lane + 1] = incl;
+        if (lane == 0) pre[0] = 0u;
+        if (count && lane < B && n && blockIdx.x == 0 && cases[lane].stats)
+            atomicAdd(cases[lane].stats, (unsigned long long)n);
+    }
+    __syncthreads();
+    const unsigned total = pre[B];
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+        int c = 0;
+        while (c + 1 < B && w >= pre[c + 1]) ++c;
+        const CaseDev<S, A> &C = cases[c];
+        const int code = C.st.work[w - pre[c]];
+        stream_slow_item(C.M, C.MS, sc[c], sf[c], C.K, C.st, C.err, code);
     }
 }
 
@@ -620,7 +636,7 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     st = release_cases(b);
     if (st != cudaSuccess) return bfail(b, st, "batch_tune");
     if (choice) {
-        for (int k = 0; k < KT_N; ++k) choice[k] = b->bs[k];
+        for (int k = 0; k < 6; ++k) choice[k] = b->bs[k];
         choice[6] = b->slow_grid;
         choice[7] = 0;
     }

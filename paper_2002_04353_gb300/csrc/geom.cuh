@@ -21,6 +21,7 @@ constexpr int NQ = 9;
 __constant__ int c_cx[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __constant__ int c_cy[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
+
 enum : int { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
              MK_BLENDED = 5 };
 enum : int { ERR_LOCATE = 1, ERR_NONFINITE = 2 };
@@ -45,6 +46,17 @@ struct MapStatic {
 // walk, for the host; host code is built without FP contraction, so the
 // plain operators round exactly like the intrinsics.
 #define ALELB_HD __host__ __device__
+
+// The same lattice velocities for a run-time direction index, formed from
+// comparisons so that they stay in registers.
+ALELB_HD __forceinline__ int lat_cx(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+ALELB_HD __forceinline__ int lat_cy(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
 ALELB_HD __forceinline__ double dm(double a, double b)
 {
 #ifdef __CUDA_ARCH__
@@ -364,6 +376,8 @@ struct MeshDev {
     const float2 *nscale;  // (length scale, number of own elements) per node
     const uint8_t *bkind;  // [N] boundary kind of the node (0 interior)
     const uint8_t *vzero;  // [N] 1: mesh velocity exactly zero at all times
+    const float4 *cone;    // [N] boundary node: outgoing, incoming boundary edge (domain on the left)
+    const uint8_t *conek;  // [N] kind of those edges, 0 when the node has no such pair
     const int *wall_idx;   // [N] index into the wall tables or -1
     const int *probe_e;    // [NW]
     const double2 *probe_xi; // [NW]
@@ -409,11 +423,27 @@ constexpr int WALK_LIMIT = 256;
 
 // Orientation provider of the walk: exact FP64 predicates on the FP64
 // departure point p and the element frames.
+// Frame vertices of element e shifted by (sx, sy) periods, from the table
+// itself (the predicate providers keep table pointers, never the address of
+// a kernel parameter, so that they stay in registers).
+ALELB_HD __forceinline__ void load_frame_t(const double2 *ev, double Lx, double Ly, int e, int sx,
+                                           int sy, double w[6])
+{
+    double ox = sx ? sx * Lx : 0.0, oy = sy ? sy * Ly : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double2 v = ev[3 * e + k];
+        w[2 * k] = (sx ? da(v.x, ox) : v.x);
+        w[2 * k + 1] = (sy ? da(v.y, oy) : v.y);
+    }
+}
+
 struct Pred64 {
-    const MeshDev *M;
+    const double2 *ev;
+    double Lx, Ly;
     double Xa, Ya, px, py;
     double w[6];
-    ALELB_HD void load(int e, int sx, int sy) { load_frame(*M, e, sx, sy, w); }
+    ALELB_HD void load(int e, int sx, int sy) { load_frame_t(ev, Lx, Ly, e, sx, sy, w); }
     // orient(w_k1, w_k2, p) of the loaded element
     ALELB_HD int vvp(int k1, int k2)
     {
@@ -432,7 +462,7 @@ struct Pred64 {
 // treated as passing to the vertex's right.  Ties (p on an edge or vertex)
 // go to the containing element of larger computational area, then lower
 // original id.  P supplies the orientation signs, always exact.
-template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
+template <class P> ALELB_HD __forceinline__ Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
 {
     Loc r;
     r.kind = 0;
@@ -477,12 +507,13 @@ template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
         r.kind = M.bkind[a];
         return r;
     }
-    int o[3];
+    int o0, o1, o2; // orientation of p against edges 0, 1, 2 of e
     int kout;
     pr.load(e, sx, sy);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) o[k] = pr.vvp(k, (k + 1) % 3);
-    bool found = o[0] >= 0 && o[1] >= 0 && o[2] >= 0;
+    o0 = pr.vvp(0, 1);
+    o1 = pr.vvp(1, 2);
+    o2 = pr.vvp(2, 0);
+    bool found = o0 >= 0 && o1 >= 0 && o2 >= 0;
     if (!found) {
         if (loc < 3) {
             kout = (loc + 1) % 3;
@@ -505,12 +536,13 @@ template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
             e = M.nbr[3 * e + kout];
             pr.load(e, sx, sy);
             int k1 = (kin + 1) % 3, k2 = (kin + 2) % 3;
-            int o1 = pr.vvp(k1, k2);
-            int o2 = pr.vvp(k2, kin);
-            if (o1 >= 0 && o2 >= 0) {
-                o[kin] = 1;
-                o[k1] = o1;
-                o[k2] = o2;
+            int s1 = pr.vvp(k1, k2);
+            int s2 = pr.vvp(k2, kin);
+            if (s1 >= 0 && s2 >= 0) {
+                // edge kin was crossed from outside: p lies strictly inside it
+                o0 = kin == 0 ? 1 : (k1 == 0 ? s1 : s2);
+                o1 = kin == 1 ? 1 : (k1 == 1 ? s1 : s2);
+                o2 = kin == 2 ? 1 : (k1 == 2 ? s1 : s2);
                 found = true;
                 break;
             }
@@ -522,9 +554,9 @@ template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
             return r;
         }
     }
-    int nz = (o[0] == 0) + (o[1] == 0) + (o[2] == 0);
+    int nz = (o0 == 0) + (o1 == 0) + (o2 == 0);
     if (nz == 1) {
-        int kz = o[0] == 0 ? 0 : (o[1] == 0 ? 1 : 2);
+        int kz = o0 == 0 ? 0 : (o1 == 0 ? 1 : 2);
         uint32_t inf = (M.einfo[e] >> (8 * kz)) & 255u;
         if ((inf & 3) == 0) {
             int e2 = M.nbr[3 * e + kz];
@@ -536,7 +568,7 @@ template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
         }
     } else if (nz >= 2) {
         // p is the vertex shared by the two zero edges
-        int vl = (o[0] == 0 && o[1] == 0) ? 1 : ((o[1] == 0 && o[2] == 0) ? 2 : 0);
+        int vl = (o0 == 0 && o1 == 0) ? 1 : ((o1 == 0 && o2 == 0) ? 2 : 0);
         r.vnode = M.conn[6 * e + vl];
     }
     r.e = e;
@@ -545,11 +577,13 @@ template <class P> ALELB_HD Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
     return r;
 }
 
-static ALELB_HD __noinline__ Loc walk(const MeshDev &M, int a, double Xa, double Ya, double px, double py,
+static ALELB_HD __noinline__ Loc walk(const MeshDev M, int a, double Xa, double Ya, double px, double py,
                                int *err)
 {
     Pred64 pr;
-    pr.M = &M;
+    pr.ev = M.ev;
+    pr.Lx = M.Lx;
+    pr.Ly = M.Ly;
     pr.Xa = Xa;
     pr.Ya = Ya;
     pr.px = px;
@@ -581,11 +615,9 @@ ALELB_HD inline void locate_node(const MeshDev &M, const MapStatic &MS, const Ma
     map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
     metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
     mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, flags_literal != 0, wx, wy);
-    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     for (int i = 0; i < NQ; ++i) {
         double chx, chy, px, py;
-        departure(a11, a12, a21, a22, wx, wy, (double)CXh[i], (double)CYh[i], Xa.x, Xa.y, chx,
+        departure(a11, a12, a21, a22, wx, wy, (double)lat_cx(i), (double)lat_cy(i), Xa.x, Xa.y, chx,
                   chy, px, py);
         int e = -2, k = 0;
         if (!(chx == 0.0 && chy == 0.0)) {
@@ -704,9 +736,7 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
                                           float &eta)
 {
     const float u = 5.9604644775390625e-08f;
-    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    const float cx = (float)CXh[i], cy = (float)CYh[i];
+    const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
     const float chx = F.A11 * cx + F.A12 * cy - F.W1;
     const float chy = F.A21 * cx + F.A22 * cy - F.W2;
     const float len = sqrtf(chx * chx + chy * chy);
@@ -773,6 +803,30 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
     return xi > m1 && eta > m2 && l0 > m0;
 }
 
+// Certified FP32 test that population i of boundary node a is missing
+// because its departure direction -c^ points strictly into the exterior at
+// the node: strictly to the right of both boundary edges through the node
+// (the domain lies on their left).  The points of the segment next to the
+// node then lie outside the closed mesh.  Returns the boundary kind, or 0
+// when not certain.  Errors: eps_c (+ 2^-25) per component of -c^, the FP32
+// rounding of the edge vectors and of the cross products.
+ALELB_HD __forceinline__ int cone_missing(const MeshDev &M, const FastMap &F, int a, int i)
+{
+    const int k = M.conek[a];
+    if (!k) return 0;
+    const float u = 5.9604644775390625e-08f;
+    const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
+    const float dx = -(F.A11 * cx + F.A12 * cy - F.W1);
+    const float dy = -(F.A21 * cx + F.A22 * cy - F.W2);
+    if (!(sqrtf(dx * dx + dy * dy) > 4.0f * F.eps_c)) return 0;
+    const float4 c = M.cone[a];
+    const float eq = F.eps_c + 2.98023223876953125e-08f;
+    const float s1 = c.x * dy - c.y * dx, s2 = c.z * dy - c.w * dx;
+    const float b1 = 2.0f * (3.0f * u * (fabsf(c.x * dy) + fabsf(c.y * dx)) + (fabsf(c.x) + fabsf(c.y)) * eq);
+    const float b2 = 2.0f * (3.0f * u * (fabsf(c.z * dy) + fabsf(c.w * dx)) + (fabsf(c.z) + fabsf(c.w)) * eq);
+    return (s1 < -b1 && s2 < -b2) ? k : 0;
+}
+
 // Certified FP32 sign of orient(A, B, C) = (A - C) x (B - C) from
 // approximations of A, B, C with per-coordinate error bounds ea, eb, ec:
 // +1 or -1 when certain, 0 when the exact predicate must decide.
@@ -795,17 +849,28 @@ ALELB_HD __forceinline__ int orient3_f32(float ax, float ay, float ea, float bx,
 // vertices from their hi/lo splits.  Uncertain signs fall back to the exact
 // FP64 predicate on the FP64 canonical departure point, computed lazily.
 struct Pred32 {
-    const MeshDev *M;
-    const MapStatic *MS;
-    const MapScalars *sc;
+    const float4 *evf;
+    const double2 *ev;
+    double Lx, Ly;
+    MapStatic MS;
+    MapScalars sc;
     int a, i, literal;
     float4 Xf;
     float rpx, rpy, ep;
     int e, sx, sy;
-    float rx[3], ry[3], er[3];
+    // the element's vertices relative to the node and their error bounds
+    // (scalars with selectors rather than arrays: run-time indices would
+    // put arrays in local memory)
+    float rx0, rx1, rx2, ry0, ry1, ry2, er0, er1, er2;
     bool have64, wload;
     double Xa, Ya, px, py;
-    double w[6];
+    double w0, w1, w2, w3, w4, w5;
+
+    ALELB_HD float RX(int k) const { return k == 0 ? rx0 : (k == 1 ? rx1 : rx2); }
+    ALELB_HD float RY(int k) const { return k == 0 ? ry0 : (k == 1 ? ry1 : ry2); }
+    ALELB_HD float ER(int k) const { return k == 0 ? er0 : (k == 1 ? er1 : er2); }
+    ALELB_HD double WX(int k) const { return k == 0 ? w0 : (k == 1 ? w2 : w4); }
+    ALELB_HD double WY(int k) const { return k == 0 ? w1 : (k == 1 ? w3 : w5); }
 
     ALELB_HD void load(int e_, int sx_, int sy_)
     {
@@ -816,54 +881,70 @@ struct Pred32 {
         wload = false;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float4 v = M->evf[3 * e + k];
+            const float4 v = evf[3 * e + k];
             const float hx = v.x - Xf.x, hy = v.y - Xf.y;
             float x = hx + (v.z - Xf.z), y = hy + (v.w - Xf.w);
             float sh = 0.0f;
             if (sx) {
-                x += (float)sx * (float)M->Lx;
-                sh = fabsf((float)M->Lx);
+                x += (float)sx * (float)Lx;
+                sh = fabsf((float)Lx);
             }
             if (sy) {
-                y += (float)sy * (float)M->Ly;
-                sh = fmaxf(sh, fabsf((float)M->Ly));
+                y += (float)sy * (float)Ly;
+                sh = fmaxf(sh, fabsf((float)Ly));
             }
-            rx[k] = x;
-            ry[k] = y;
-            er[k] = 4.0f * u * (fmaxf(fabsf(x), fabsf(y)) + fmaxf(fabsf(hx), fabsf(hy)) + sh) +
-                    9.313225746154785e-10f;
+            const float ek = 4.0f * u * (fmaxf(fabsf(x), fabsf(y)) + fmaxf(fabsf(hx), fabsf(hy)) + sh) +
+                             9.313225746154785e-10f;
+            if (k == 0) {
+                rx0 = x;
+                ry0 = y;
+                er0 = ek;
+            } else if (k == 1) {
+                rx1 = x;
+                ry1 = y;
+                er1 = ek;
+            } else {
+                rx2 = x;
+                ry2 = y;
+                er2 = ek;
+            }
         }
     }
     ALELB_HD void ensure64()
     {
         if (!have64) {
             double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy, chx, chy;
-            const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-            const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-            map_node(*MS, *sc, a, Xa, Ya, xX, xY, yX, yY, Vx, Vy);
+            map_node(MS, sc, a, Xa, Ya, xX, xY, yX, yY, Vx, Vy);
             metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
             mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
-            departure(a11, a12, a21, a22, wx, wy, CXh[i], CYh[i], Xa, Ya, chx, chy, px, py);
+            departure(a11, a12, a21, a22, wx, wy, lat_cx(i), lat_cy(i), Xa, Ya, chx, chy, px, py);
             have64 = true;
         }
         if (!wload) {
-            load_frame(*M, e, sx, sy, w);
+            double w[6];
+            load_frame_t(ev, Lx, Ly, e, sx, sy, w);
+            w0 = w[0];
+            w1 = w[1];
+            w2 = w[2];
+            w3 = w[3];
+            w4 = w[4];
+            w5 = w[5];
             wload = true;
         }
     }
     ALELB_HD int vvp(int k1, int k2)
     {
-        const int s = orient3_f32(rx[k1], ry[k1], er[k1], rx[k2], ry[k2], er[k2], rpx, rpy, ep);
+        const int s = orient3_f32(RX(k1), RY(k1), ER(k1), RX(k2), RY(k2), ER(k2), rpx, rpy, ep);
         if (s) return s;
         ensure64();
-        return orient(w[2 * k1], w[2 * k1 + 1], w[2 * k2], w[2 * k2 + 1], px, py);
+        return orient(WX(k1), WY(k1), WX(k2), WY(k2), px, py);
     }
     ALELB_HD int avp(int k)
     {
-        const int s = orient3_f32(0.0f, 0.0f, 0.0f, rpx, rpy, ep, rx[k], ry[k], er[k]);
+        const int s = orient3_f32(0.0f, 0.0f, 0.0f, rpx, rpy, ep, RX(k), RY(k), ER(k));
         if (s) return s;
         ensure64();
-        return orient(Xa, Ya, px, py, w[2 * k], w[2 * k + 1]);
+        return orient(Xa, Ya, px, py, WX(k), WY(k));
     }
     ALELB_HD bool p_is_node() const { return false; } // the caller ensures |c^| > 4 eps_c
 };
@@ -879,21 +960,22 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                                          int i, int literal, float &qx, float &qy, int &src,
                                          int *err)
 {
-    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double2 Xa = M.X[a];
     src = -1;
     Loc L;
     bool done = false;
     if (F.ok && !literal) {
-        const float cx = (float)CXh[i], cy = (float)CYh[i];
+        const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
         const float chx = F.A11 * cx + F.A12 * cy - F.W1;
         const float chy = F.A21 * cx + F.A22 * cy - F.W2;
         if (sqrtf(chx * chx + chy * chy) > 4.0f * F.eps_c) {
             Pred32 pr;
-            pr.M = &M;
-            pr.MS = &MS;
-            pr.sc = &sc;
+            pr.evf = M.evf;
+            pr.ev = M.ev;
+            pr.Lx = M.Lx;
+            pr.Ly = M.Ly;
+            pr.MS = MS;
+            pr.sc = sc;
             pr.a = a;
             pr.i = i;
             pr.literal = literal;
@@ -922,7 +1004,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
         map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
         metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
         mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
-        departure(a11, a12, a21, a22, wx, wy, CXh[i], CYh[i], Xa.x, Xa.y, chx, chy, px, py);
+        departure(a11, a12, a21, a22, wx, wy, lat_cx(i), lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
         if (chx == 0.0 && chy == 0.0) {
             L.e = -2;
             L.vnode = -1;
@@ -967,6 +1049,13 @@ ALELB_HD inline void mixed_locate_node(const MeshDev &M, const MapStatic &MS,
         if (f) {
             elem9[i] = M.orig_elem[e];
             kind9[i] = 0;
+            continue;
+        }
+        const int ck = F.ok ? cone_missing(M, F, a, i) : 0;
+        if (ck) { // certified missing at the node itself
+            if (fast9) fast9[i] = 1;
+            elem9[i] = -1;
+            kind9[i] = (int8_t)ck;
             continue;
         }
         int src;

@@ -253,6 +253,84 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
 //   k_moments      per node: moments, Q'_aaa and mu/(rho T) of the streamed
 //                  populations; resets the work list
 // ---------------------------------------------------------------------------
+// Missing populations at walls (Sec. IV.A) of node a, the directions in
+// mask: the targets (wall node: u = V_G, rho and T at the probe B; other
+// nodes: their previous-step fields) and first-order gradients are formed
+// once, then every direction of the mask is written.
+template <class S, class A>
+__device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic &MS,
+                                               const MapScalars &sc, const MapScalarsF &sf,
+                                               const KinParams<A> &K, const StateDev<S> &st, int a,
+                                               const FastMap &F, unsigned mask)
+{
+    const int N = M.N;
+    float a11, a12, a21, a22, Vx, Vy;
+    if (F.ok) {
+        a11 = F.A11;
+        a12 = F.A12;
+        a21 = F.A21;
+        a22 = F.A22;
+        Vx = F.Vx;
+        Vy = F.Vy;
+    } else {
+        const double2 Xa = M.X[a];
+        double xX, xY, yX, yY, vx, vy, b11, b12, b21, b22;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, vx, vy);
+        metric_inverse_T(xX, xY, yX, yY, b11, b12, b21, b22);
+        a11 = (float)b11;
+        a12 = (float)b12;
+        a21 = (float)b21;
+        a22 = (float)b22;
+        Vx = (float)vx;
+        Vy = (float)vy;
+    }
+    A rt, uxt, uyt, Tt;
+    const int wi = M.wall_idx[a];
+    if (wi >= 0) {
+        const int pe = M.probe_e[wi];
+        const double2 pxi = M.probe_xi[wi];
+        A Nw[6];
+        shape6<A>((A)pxi.x, (A)pxi.y, Nw);
+        A r = 0, t = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int b = M.conn[6 * pe + k];
+            r += Nw[k] * (A)st.rho[b];
+            t += Nw[k] * (A)st.T[b];
+        }
+        rt = r;
+        Tt = t;
+        uxt = (A)Vx;
+        uyt = (A)Vy;
+    } else {
+        rt = (A)st.rho[a];
+        uxt = (A)st.ux[a];
+        uyt = (A)st.uy[a];
+        Tt = (A)st.T[a];
+    }
+    A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
+    if (!(K.flags & FLAG_BC_EQ)) {
+        float KX, KY;
+        owner_grad_linear_f32(M, a, st.ux, KX, KY);
+        du[0] = (A)(a11 * KX + a21 * KY);
+        du[1] = (A)(a12 * KX + a22 * KY);
+        owner_grad_linear_f32(M, a, st.uy, KX, KY);
+        du[2] = (A)(a11 * KX + a21 * KY);
+        du[3] = (A)(a12 * KX + a22 * KY);
+        owner_grad_linear_f32(M, a, st.T, KX, KY);
+        dT[0] = (A)(a11 * KX + a21 * KY);
+        dT[1] = (A)(a12 * KX + a22 * KY);
+    }
+    A fm[NQ], gm[NQ];
+    grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i)
+        if (mask >> i & 1u) {
+            st.str[i * N + a] = (S)fm[i];
+            st.str[(NQ + i) * N + a] = (S)gm[i];
+        }
+}
+
 // Interpolates every population of node a whose previous-step element is
 // verified; returns the mask of the others.
 template <class S, class A>
@@ -271,6 +349,7 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
 #pragma unroll
         for (int i = 0; i < NQ; ++i) cache[i] = st.cache[i * N + a];
         const bool v0 = M.vzero[a];
+        unsigned wall = 0; // directions certified missing at a wall
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             int e;
@@ -291,9 +370,20 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
                 st.str[i * N + a] = (S)fi;
                 st.str[(NQ + i) * N + a] = (S)gi;
             } else {
-                slow |= 1u << i;
+                const int ck = F.ok ? cone_missing(M, F, a, i) : 0;
+                if (ck == 2) { // far field: free-stream equilibria
+                    st.str[i * N + a] = (S)K.finf[i];
+                    st.str[(NQ + i) * N + a] = (S)K.ginf[i];
+                } else if (ck == 1) {
+                    wall |= 1u << i;
+                } else {
+                    slow |= 1u << i;
+                }
             }
         }
+        // (the cone test runs with a usable FP32 map only, so the FP64 map
+        // scalars are not needed here)
+        if (wall) stream_bc_node<S, A>(M, MS, MapScalars{}, sf, K, st, a, F, wall);
     }
     return slow;
 }
@@ -395,70 +485,8 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             fi = K.finf[i];
             gi = K.ginf[i];
         } else {
-            // missing population (Sec. IV.A): targets and first-order
-            // gradients of the previous-step fields at this node, with the
-            // FP32 metrics when usable
-            float a11, a12, a21, a22, Vx, Vy;
-            if (F.ok) {
-                a11 = F.A11;
-                a12 = F.A12;
-                a21 = F.A21;
-                a22 = F.A22;
-                Vx = F.Vx;
-                Vy = F.Vy;
-            } else {
-                const double2 Xa = M.X[a];
-                double xX, xY, yX, yY, vx, vy, b11, b12, b21, b22;
-                map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, vx, vy);
-                metric_inverse_T(xX, xY, yX, yY, b11, b12, b21, b22);
-                a11 = (float)b11;
-                a12 = (float)b12;
-                a21 = (float)b21;
-                a22 = (float)b22;
-                Vx = (float)vx;
-                Vy = (float)vy;
-            }
-            A rt, uxt, uyt, Tt;
-            const int wi = M.wall_idx[a];
-            if (wi >= 0) {
-                const int pe = M.probe_e[wi];
-                const double2 pxi = M.probe_xi[wi];
-                A Nw[6];
-                shape6<A>((A)pxi.x, (A)pxi.y, Nw);
-                A r = 0, t = 0;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const int b = M.conn[6 * pe + k];
-                    r += Nw[k] * (A)st.rho[b];
-                    t += Nw[k] * (A)st.T[b];
-                }
-                rt = r;
-                Tt = t;
-                uxt = (A)Vx;
-                uyt = (A)Vy;
-            } else {
-                rt = (A)st.rho[a];
-                uxt = (A)st.ux[a];
-                uyt = (A)st.uy[a];
-                Tt = (A)st.T[a];
-            }
-            A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
-            if (!(K.flags & FLAG_BC_EQ)) {
-                float KX, KY;
-                owner_grad_linear_f32(M, a, st.ux, KX, KY);
-                du[0] = (A)(a11 * KX + a21 * KY);
-                du[1] = (A)(a12 * KX + a22 * KY);
-                owner_grad_linear_f32(M, a, st.uy, KX, KY);
-                du[2] = (A)(a11 * KX + a21 * KY);
-                du[3] = (A)(a12 * KX + a22 * KY);
-                owner_grad_linear_f32(M, a, st.T, KX, KY);
-                dT[0] = (A)(a11 * KX + a21 * KY);
-                dT[1] = (A)(a12 * KX + a22 * KY);
-            }
-            A fm[NQ], gm[NQ];
-            grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
-            fi = fm[i];
-            gi = gm[i];
+            stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
+            return;
         }
         st.str[i * N + a] = (S)fi;
         st.str[(NQ + i) * N + a] = (S)gi;
@@ -477,6 +505,7 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
         stream_slow_item(M, MS, sc, sf, K, st, err, st.work[w], prop ? prop[w] : -1,
                          prop && stats ? stats + 1 : nullptr);
 }
+
 
 template <class S, class A>
 __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateDev<S> &st, int N,

@@ -23,9 +23,7 @@ constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 384, MLP_OFF_W2 = 448, MLP_OFF_B2 = 4
 ALELB_HD __forceinline__ int mlp_features(const MeshDev &M, const FastMap &F, int a, int i,
                                           float f[MLP_IN])
 {
-    const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    const float cx = (float)CXh[i], cy = (float)CYh[i];
+    const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
     const float chx = F.A11 * cx + F.A12 * cy - F.W1;
     const float chy = F.A21 * cx + F.A22 * cy - F.W2;
     const float2 ns = M.nscale[a];

@@ -59,7 +59,8 @@ struct HostTables {
     std::vector<float2> nscale;
     std::vector<uint32_t> einfo;
     std::vector<int2> fan, owner, wedges;
-    std::vector<uint8_t> bkind, vzero;
+    std::vector<uint8_t> bkind, vzero, conek;
+    std::vector<float4> cone;
     std::vector<double> ms;
     std::vector<float4> ejf, Xf, v0f, evf;
     std::vector<float> bdist, msf;
@@ -85,6 +86,8 @@ struct HostTables {
         D.bcel = bcel.data();
         D.bkind = bkind.data();
         D.vzero = vzero.data();
+        D.cone = cone.data();
+        D.conek = conek.data();
         D.wall_idx = wall_idx.data();
         D.probe_e = probe_e.data();
         D.probe_xi = probe_xi.data();
@@ -413,6 +416,35 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
                 }
             }
         }
+    // exterior cone of each boundary node: its outgoing and incoming boundary
+    // edges (the domain on their left) when it has exactly one of each, of
+    // one kind; a departure direction strictly right of both leaves the mesh
+    // at once (the population is missing)
+    {
+        std::vector<int> nout(N, 0), nin(N, 0), kk(N, 0);
+        T.cone.assign(N, make_float4(0, 0, 0, 0));
+        T.conek.assign(N, 0);
+        for (int en = 0; en < E; ++en)
+            for (int k = 0; k < 3; ++k) {
+                const int kind = (int)((einfo[en] >> (8 * k)) & 3u);
+                if (!kind) continue;
+                const int k1 = (k + 1) % 3;
+                const double ex = ev[3 * en + k1].x - ev[3 * en + k].x, ey = ev[3 * en + k1].y - ev[3 * en + k].y;
+                const int va = conn[6 * en + k], vb = conn[6 * en + k1], mid = conn[6 * en + 3 + k];
+                auto add = [&](int node, bool out, double x, double y) {
+                    if (kk[node] && kk[node] != kind) kk[node] = -1;
+                    else if (!kk[node]) kk[node] = kind;
+                    if (out) { nout[node]++; T.cone[node].x = (float)x; T.cone[node].y = (float)y; }
+                    else { nin[node]++; T.cone[node].z = (float)x; T.cone[node].w = (float)y; }
+                };
+                add(va, true, ex, ey);
+                add(vb, false, ex, ey);
+                add(mid, true, 0.5 * ex, 0.5 * ey);
+                add(mid, false, 0.5 * ex, 0.5 * ey);
+            }
+        for (int a = 0; a < N; ++a)
+            if (nout[a] == 1 && nin[a] == 1 && kk[a] > 0) T.conek[a] = (uint8_t)kk[a];
+    }
     // element of each node's wall-condition gradients: among the incident
     // elements with a vertex on a wall edge the one of larger computational
     // area, then lower original id; the owner element when none touches a
