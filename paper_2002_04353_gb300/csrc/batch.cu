@@ -100,40 +100,61 @@ __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__
     const CaseDev<S, A> &C = sh.C();
     const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
     const unsigned slow = a < C.M.N ? stream_fast_node(C.M, C.MS, sh.SF(), C.K, C.st, a) : 0u;
-    append_work(C.st, a, slow);
+    append_work(C.st, a, C.M.N, slow);
 }
 
-// The exact path over the work lists of all cases as one list: block-local
-// prefix sum of the cases' counts, one population per thread, its case by a
-// ballot over the prefix sums; the case descriptor is read from global
-// memory (the populations of a warp mostly share one case).
+// The exact path over the work lists of all cases as one list, numbered
+// case by case and, within a case, direction by direction: block-local
+// prefix sums of the B x 9 segment counts, one population per thread, its
+// segment by binary search; the case descriptor is read from global memory
+// (the populations of a warp mostly share one case and one direction).
 template <class S, class A>
 __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__ cases, int B,
                                                const MapScalars *__restrict__ sc,
                                                const MapScalarsF *__restrict__ sf, int count)
 {
-    __shared__ unsigned pre[BATCH_MAX + 1];
+    __shared__ unsigned pre[BATCH_MAX * NQ + 1];
+    const int nseg = B * NQ;
     if (threadIdx.x < 32) {
+        // lane l sums segments [l * 9, l * 9 + 9) (case l), then a warp scan
         const int lane = threadIdx.x;
-        const unsigned n = lane < B ? *cases[lane].st.wcount : 0u;
-        unsigned incl = n;
+        unsigned loc[NQ];
+        unsigned s = 0;
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            loc[i] = lane < B ? cases[lane].st.wcount[i] : 0u;
+            s += loc[i];
+        }
+        unsigned incl = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        pre[lane + 1] = incl;
-        if (lane == 0) pre[0] = 0u;
-        if (count && lane < B && n && blockIdx.x == 0 && cases[lane].stats)
-            atomicAdd(cases[lane].stats, (unsigned long long)n);
+        if (lane < B) {
+            unsigned run = incl - s;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                pre[lane * NQ + i] = run;
+                run += loc[i];
+            }
+            if (lane == B - 1) pre[nseg] = run;
+            if (count && s && blockIdx.x == 0 && cases[lane].stats)
+                atomicAdd(cases[lane].stats, (unsigned long long)s);
+        }
     }
     __syncthreads();
-    const unsigned total = pre[B];
+    const unsigned total = pre[nseg];
     for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
-        int c = 0;
-        while (c + 1 < B && w >= pre[c + 1]) ++c;
+        int lo = 0, hi = nseg - 1; // last segment with pre <= w
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const int c = lo / NQ, i = lo % NQ;
         const CaseDev<S, A> &C = cases[c];
-        const int code = C.st.work[w - pre[c]];
+        const int code = C.st.work[(size_t)i * C.M.N + (w - pre[lo])];
         stream_slow_item(C.M, C.MS, sc[c], sf[c], C.K, C.st, C.err, code);
     }
 }
@@ -148,7 +169,7 @@ __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restric
     __syncthreads();
     const CaseDev<S, A> &C = sh.C();
     const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
-    if (a == 0) *C.st.wcount = 0u; // the case's work list has been consumed
+    if (a < NQ) C.st.wcount[a] = 0u; // the case's work list has been consumed
     if (a < C.M.N) moments_node(C.K, C.st, C.M.N, C.err, a);
 }
 
@@ -188,7 +209,8 @@ template <class S, class A>
 __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
 {
     const int c = threadIdx.x;
-    if (c < B) *cases[c].st.wcount = 0u;
+    if (c < B)
+        for (int i = 0; i < NQ; ++i) cases[c].st.wcount[i] = 0u;
 }
 
 int bs_index(int bs) { return bs == 64 ? 0 : bs == 128 ? 1 : 2; }

@@ -26,9 +26,26 @@ template <class S> struct StateDev {
     S *Dx, *Dy;           // first-pass results
     int *cache;           // [9 N] element of each population's previous departure point
                           // (elem | (sx+1)<<28 | (sy+1)<<30), -1 when empty
-    int *work;            // [9 N] populations (9 node + direction) left to the exact path
-    unsigned *wcount;     // number of entries in work
+    int *work;            // [9 N] populations (9 node + direction) left to the exact path,
+                          // direction i's at work[i N + k], k < wcount[i]
+    unsigned *wcount;     // [9] entries of each direction
 };
+
+// The exact-path kernels number the work list direction by direction
+// (populations of one direction at neighbouring nodes take similar paths,
+// so the lanes of a warp stay together): pre[i] = entries before direction i.
+__device__ __forceinline__ void work_prefix(const unsigned *wcount, unsigned pre[NQ + 1])
+{
+    pre[0] = 0u;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) pre[i + 1] = pre[i] + wcount[i];
+}
+__device__ __forceinline__ int work_at(const int *work, int N, const unsigned *pre, unsigned w)
+{
+    int i = 0;
+    while (i < NQ - 1 && w >= pre[i + 1]) ++i;
+    return work[(size_t)i * N + (w - pre[i])];
+}
 
 // d N_s / d xi and d N_s / d eta of the P2 triangle at the six node
 // positions (0,0), (1,0), (0,1), (1/2,0), (1/2,1/2), (0,1/2).
@@ -349,7 +366,6 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
 #pragma unroll
         for (int i = 0; i < NQ; ++i) cache[i] = st.cache[i * N + a];
         const bool v0 = M.vzero[a];
-        unsigned wall = 0; // directions certified missing at a wall
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             int e;
@@ -374,42 +390,35 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
                 if (ck == 2) { // far field: free-stream equilibria
                     st.str[i * N + a] = (S)K.finf[i];
                     st.str[(NQ + i) * N + a] = (S)K.ginf[i];
-                } else if (ck == 1) {
-                    wall |= 1u << i;
                 } else {
+                    // walls: the exact-path kernel, which repeats the cone
+                    // test and then needs no walk
                     slow |= 1u << i;
                 }
             }
         }
-        // (the cone test runs with a usable FP32 map only, so the FP64 map
-        // scalars are not needed here)
-        if (wall) stream_bc_node<S, A>(M, MS, MapScalars{}, sf, K, st, a, F, wall);
     }
     return slow;
 }
 
 // Warp-aggregated append of the populations in `slow` (node a) to the work
-// list; all 32 lanes of the warp take part, with slow = 0 where idle.
+// list, per direction; all 32 lanes of the warp take part, with slow = 0
+// where idle.
 template <class S>
-__device__ __forceinline__ void append_work(const StateDev<S> &st, int a, unsigned slow)
+__device__ __forceinline__ void append_work(const StateDev<S> &st, int a, int N, unsigned slow)
 {
     const unsigned lane = threadIdx.x & 31u;
-    const int n = __popc(slow);
-    int incl = n;
+    if (!__any_sync(0xffffffffu, slow != 0u)) return;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (unsigned)o) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned base = 0;
-    if (lane == 31 && total > 0) base = atomicAdd(st.wcount, (unsigned)total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    unsigned pos = base + (unsigned)(incl - n);
-    while (slow) {
-        const int i = __ffs(slow) - 1;
-        slow &= slow - 1;
-        st.work[pos++] = a * NQ + i;
+    for (int i = 0; i < NQ; ++i) {
+        const bool mine = (slow >> i) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, mine);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        unsigned base = 0;
+        if ((int)lane == leader) base = atomicAdd(st.wcount + i, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (mine) st.work[(size_t)i * N + base + __popc(m & ((1u << lane) - 1u))] = a * NQ + i;
     }
 }
 
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, Ma
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned slow = a < M.N ? stream_fast_node(M, MS, sf, K, st, a) : 0u;
-    append_work(st, a, slow);
+    append_work(st, a, M.N, slow);
 }
 
 // One listed population (code = 9 node + direction): exact decision, then
@@ -443,6 +452,10 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
         float qx = 0.f, qy = 0.f;
         int src;
+        if (F.ok && !literal && cone_missing(M, F, a, i) == 1) { // leaves through a wall at the node
+            stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
+            return;
+        }
         Loc L;
         int pe;
         float pxi, peta;
@@ -499,10 +512,13 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
                                                      int *err, unsigned long long *stats,
                                                      const int *prop)
 {
-    const unsigned n = *st.wcount;
+    __shared__ unsigned pre[NQ + 1];
+    if (threadIdx.x == 0) work_prefix(st.wcount, pre);
+    __syncthreads();
+    const unsigned n = pre[NQ];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
     for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x)
-        stream_slow_item(M, MS, sc, sf, K, st, err, st.work[w], prop ? prop[w] : -1,
+        stream_slow_item(M, MS, sc, sf, K, st, err, work_at(st.work, M.N, pre, w), prop ? prop[w] : -1,
                          prop && stats ? stats + 1 : nullptr);
 }
 
@@ -536,7 +552,7 @@ template <class S, class A>
 __global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st, int N, int *err)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a == 0) *st.wcount = 0u; // the work list has been consumed
+    if (a < NQ) st.wcount[a] = 0u; // the work list has been consumed
     if (a < N) moments_node(K, st, N, err, a);
 }
 

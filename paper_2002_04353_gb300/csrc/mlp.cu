@@ -386,7 +386,10 @@ k_propose(MeshDev M, MapStatic MS, MapScalarsF sf, StateDev<T> st, const __half 
     __shared__ PredSmem S;
     load_pred_weights(S, Wh);
     __syncthreads();
-    const unsigned n = *st.wcount;
+    __shared__ unsigned pre[NQ + 1];
+    if (threadIdx.x == 0) work_prefix(st.wcount, pre);
+    __syncthreads();
+    const unsigned n = pre[NQ];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned nwarps = gridDim.x * PRED_WARPS;
     unsigned count = 0;
@@ -396,7 +399,7 @@ k_propose(MeshDev M, MapStatic MS, MapScalarsF sf, StateDev<T> st, const __half 
         if (lane < 16) {
             float f[MLP_IN] = {0, 0, 0, 0, 0, 0};
             if (q < n) {
-                const int code = st.work[q];
+                const int code = work_at(st.work, M.N, pre, q);
                 a = code / NQ;
                 const int i = code % NQ;
                 const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
