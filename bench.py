@@ -102,6 +102,13 @@ def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4):
     return 0
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# FP32-deviation kernels on the 150,400-node plunge workload, from one ncu
+# capture of the current kernels; writes stay in L2 during these launches.
+NCU_TRAFFIC_150K = {"k_stream_fast": 23.96e6, "k_stream_slow": 1.59e6, "k_moments": 10.84e6,
+                    "k_deriv1": 7.21e6, "k_collide": 17.45e6}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -487,7 +494,8 @@ def run_ours(args):
             "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / max(2, K // 4)},
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": None, "algorithmic_bytes_per_launch": alg,
+                         "traffic": NCU_TRAFFIC_150K.get(top) if args.workload == "plunge150k" else None,
+                         "algorithmic_bytes_per_launch": alg,
                          "launch_ms": top_ms / top_n,
                          "note": ("the exact-path kernel is latency-bound (one short dependent chain per "
                                   "listed population), not bandwidth-bound" if top == "k_stream_slow" else "")},
