@@ -73,7 +73,10 @@ enum {
     ALELB_FLAG_PHI_OFF = 1,        /* drop the correction terms phi_i (tests) */
     ALELB_FLAG_COLLIDE_OFF = 2,    /* pure propagation, no collision (tests) */
     ALELB_FLAG_LITERAL_VG = 4,     /* c^_i = g^{-1,T} c_i - V_G as printed in Eq. 7 */
-    ALELB_FLAG_BC_EQUILIBRIUM = 8  /* missing populations: equilibrium part only */
+    ALELB_FLAG_BC_EQUILIBRIUM = 8, /* missing populations: equilibrium part only */
+    ALELB_FLAG_SLIP_WALL = 16      /* slip (inviscid) walls: at wall nodes the target velocity is
+                                      V_G plus the tangential part of u_B - V_G at the probe B,
+                                      and the non-equilibrium part is dropped (no wall shear) */
 };
 
 /* Mesh description (computational domain, Sec. III).  Straight-sided

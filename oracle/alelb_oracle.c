@@ -38,7 +38,10 @@
  *       wall, and the normal velocity next to the wall then grows without
  *       bound.
  *       Flag BC_EQUILIBRIUM drops the non-equilibrium part (a stabilising
- *       variant, not the paper's condition)
+ *       variant, not the paper's condition).  Flag SLIP_WALL (the inviscid
+ *       variant; the paper has none): wall nodes take u = V_G plus the
+ *       tangential part of u_B - V_G at the probe B, tangent taken in the
+ *       physical frame, and no non-equilibrium part (no wall shear)
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
  *       on each straight P2 wall edge of the mapped geometry
  * Parity status of each function is given in its comment; the forces have
@@ -57,7 +60,8 @@ static const int CYI[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 enum { ST_OK = 0, ST_ARG = -1, ST_OOM = -2, ST_MESH = -4, ST_MAP = -5, ST_LOCATE = -6,
        ST_NONFINITE = -7 };
-enum { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQUILIBRIUM = 8 };
+enum { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQUILIBRIUM = 8,
+       FLAG_SLIP_WALL = 16 };
 enum { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
        MK_BLENDED = 5 };
 enum { EK_INTERIOR = 0, EK_WALL = 1, EK_FAR = 2 };
@@ -1347,16 +1351,30 @@ static int stream_node(orc_t *o, int a, const mscal_t *S)
                     int pe = o->probe_e[a];
                     double N[6];
                     orc_shape(o->probe_xi[2 * a], o->probe_xi[2 * a + 1], N);
-                    double rB = 0, TB = 0;
+                    double rB = 0, TB = 0, uB = 0, vB = 0;
                     for (int k = 0; k < 6; ++k) {
                         int b = o->conn[6 * pe + k];
                         rB += N[k] * o->rho[b];
                         TB += N[k] * o->T[b];
+                        uB += N[k] * o->ux[b];
+                        vB += N[k] * o->uy[b];
                     }
                     tgt[0] = rB;
                     tgt[1] = Vx; /* wall velocity: the mesh velocity of the wall node */
                     tgt[2] = Vy;
                     tgt[3] = TB;
+                    if (o->K.flags & FLAG_SLIP_WALL) {
+                        /* slip wall (reading of the inviscid variant): V_G plus the
+                           tangential part of u_B - V_G; the physical normal is
+                           g^{-1,T} applied to the computational one */
+                        double nx, ny;
+                        phys_grad(gi, o->wall_n[2 * a], o->wall_n[2 * a + 1], &nx, &ny);
+                        double L = sqrt(nx * nx + ny * ny);
+                        double tx = -ny / L, ty = nx / L;
+                        double ut = (uB - Vx) * tx + (vB - Vy) * ty;
+                        tgt[1] = Vx + ut * tx;
+                        tgt[2] = Vy + ut * ty;
+                    }
                 } else {
                     tgt[0] = o->rho[a];
                     tgt[1] = o->ux[a];
@@ -1370,7 +1388,7 @@ static int stream_node(orc_t *o, int a, const mscal_t *S)
                 phys_grad(gi, KX, KY, &du[2], &du[3]);
                 fe_grad_X_linear(o, a, o->T, &KX, &KY);
                 phys_grad(gi, KX, KY, &dT[0], &dT[1]);
-                if (o->K.flags & FLAG_BC_EQUILIBRIUM) {
+                if ((o->K.flags & FLAG_BC_EQUILIBRIUM) || ((o->K.flags & FLAG_SLIP_WALL) && o->is_wall[a])) {
                     du[0] = du[1] = du[2] = du[3] = 0.0;
                     dT[0] = dT[1] = 0.0;
                 }

@@ -26,6 +26,7 @@ FLAG_PHI_OFF = 1
 FLAG_COLLIDE_OFF = 2
 FLAG_LITERAL_VG = 4
 FLAG_BC_EQUILIBRIUM = 8
+FLAG_SLIP_WALL = 16
 NQ = 9
 
 # every symbol include/alelb.h declares

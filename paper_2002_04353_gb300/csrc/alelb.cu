@@ -121,6 +121,7 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.wall_idx = B.put(T.wall_idx, st);
     D.probe_e = B.put(T.probe_e, st);
     D.probe_xi = B.put(T.probe_xi, st);
+    D.wall_nrm = B.put(T.wall_nrm, st);
     D.orig_elem = B.put(T.orig, st);
     D.ejf = B.put(T.ejf, st);
     D.bdist = B.put(T.bdist, st);

@@ -381,6 +381,7 @@ struct MeshDev {
     const int *wall_idx;   // [N] index into the wall tables or -1
     const int *probe_e;    // [NW]
     const double2 *probe_xi; // [NW]
+    const double2 *wall_nrm; // [NW] unit wall normal into the fluid, computational frame
     const int *orig_elem;  // [E] original element id
     const float4 *ejf;     // [2E] FP32 edge vectors (v1-v0, v2-v0) and inverse Jacobian rows
     const float *bdist;    // [N] lower bound of the node's distance to the nearest boundary edge

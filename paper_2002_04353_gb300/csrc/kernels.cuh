@@ -63,6 +63,23 @@ template <class A> __device__ __forceinline__ void shape6(A xi, A eta, A N[6])
     N[5] = A(4) * eta * l0;
 }
 
+// Slip wall (inviscid variant): the target velocity keeps the wall's
+// velocity V_G plus the tangential part of the previous-step velocity
+// u_B - V_G at the probe point B.  The tangent is the physical one: the
+// computational normal n maps to g^{-1,T} n (normals transform like
+// gradients), and t is that vector turned by +90 degrees, normalised.
+template <class A>
+__device__ __forceinline__ void slip_target(A a11, A a12, A a21, A a22, A nX, A nY, A uB, A vB,
+                                            A Vx, A Vy, A &ux, A &uy)
+{
+    const A nx = a11 * nX + a21 * nY, ny = a12 * nX + a22 * nY;
+    const A L = sqrt(nx * nx + ny * ny);
+    const A tx = -ny / L, ty = nx / L;
+    const A ut = (uB - Vx) * tx + (vB - Vy) * ty;
+    ux = Vx + ut * tx;
+    uy = Vy + ut * ty;
+}
+
 // d K / d X at node a in its owner element (full P2 derivative).
 template <class S>
 __device__ __forceinline__ void owner_grad(const MeshDev &M, int a, const S *K, double &KX,
@@ -192,17 +209,25 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
                 const double2 pxi = M.probe_xi[wi];
                 A Nw[6];
                 shape6<A>((A)pxi.x, (A)pxi.y, Nw);
-                A r = 0, t = 0;
+                A r = 0, t = 0, ub = 0, vb = 0;
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
                     int b = M.conn[6 * pe + k];
                     r += Nw[k] * (A)st.rho[b];
                     t += Nw[k] * (A)st.T[b];
+                    if (K.flags & FLAG_SLIP) {
+                        ub += Nw[k] * (A)st.ux[b];
+                        vb += Nw[k] * (A)st.uy[b];
+                    }
                 }
                 rt = r;
                 Tt = t;
                 uxt = (A)Vx;
                 uyt = (A)Vy;
+                if (K.flags & FLAG_SLIP) {
+                    const double2 nw = M.wall_nrm[wi];
+                    slip_target<A>((A)a11, (A)a12, (A)a21, (A)a22, (A)nw.x, (A)nw.y, ub, vb, (A)Vx, (A)Vy, uxt, uyt);
+                }
             } else {
                 rt = (A)st.rho[a];
                 uxt = (A)st.ux[a];
@@ -210,7 +235,7 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
                 Tt = (A)st.T[a];
             }
             A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
-            if (!(K.flags & FLAG_BC_EQ)) {
+            if (!(K.flags & FLAG_BC_EQ) && !((K.flags & FLAG_SLIP) && wi >= 0)) {
                 double KX, KY;
                 owner_grad_linear(M, a, st.ux, KX, KY);
                 du[0] = (A)(a11 * KX + a21 * KY);
@@ -308,17 +333,25 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
         const double2 pxi = M.probe_xi[wi];
         A Nw[6];
         shape6<A>((A)pxi.x, (A)pxi.y, Nw);
-        A r = 0, t = 0;
+        A r = 0, t = 0, ub = 0, vb = 0;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int b = M.conn[6 * pe + k];
             r += Nw[k] * (A)st.rho[b];
             t += Nw[k] * (A)st.T[b];
+            if (K.flags & FLAG_SLIP) {
+                ub += Nw[k] * (A)st.ux[b];
+                vb += Nw[k] * (A)st.uy[b];
+            }
         }
         rt = r;
         Tt = t;
         uxt = (A)Vx;
         uyt = (A)Vy;
+        if (K.flags & FLAG_SLIP) {
+            const double2 nw = M.wall_nrm[wi];
+            slip_target<A>((A)a11, (A)a12, (A)a21, (A)a22, (A)nw.x, (A)nw.y, ub, vb, (A)Vx, (A)Vy, uxt, uyt);
+        }
     } else {
         rt = (A)st.rho[a];
         uxt = (A)st.ux[a];
@@ -326,7 +359,7 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
         Tt = (A)st.T[a];
     }
     A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
-    if (!(K.flags & FLAG_BC_EQ)) {
+    if (!(K.flags & FLAG_BC_EQ) && !((K.flags & FLAG_SLIP) && wi >= 0)) {
         float KX, KY;
         owner_grad_linear_f32(M, a, st.ux, KX, KY);
         du[0] = (A)(a11 * KX + a21 * KY);

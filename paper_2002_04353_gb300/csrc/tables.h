@@ -54,7 +54,7 @@ struct HostTables {
     int mkind = 0;
     double mp[16] = {0};
     std::vector<int> node_old2new, node_new2old, elem_old2new, elem_new2old;
-    std::vector<double2> X, ev, probe_xi;
+    std::vector<double2> X, ev, probe_xi, wall_nrm;
     std::vector<int> nbr, conn, rank, orig, fan_ptr, wall_idx, probe_e, bcel, ring_ptr, ring;
     std::vector<float2> nscale;
     std::vector<uint32_t> einfo;
@@ -91,6 +91,7 @@ struct HostTables {
         D.wall_idx = wall_idx.data();
         D.probe_e = probe_e.data();
         D.probe_xi = probe_xi.data();
+        D.wall_nrm = wall_nrm.data();
         D.orig_elem = orig.data();
         D.ejf = ejf.data();
         D.bdist = bdist.data();
@@ -468,6 +469,7 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
     wall_idx.assign(N, -1);
     probe_e.clear();
     probe_xi.clear();
+    T.wall_nrm.clear();
     {
         std::vector<int> seen(E, -1);
         for (int a = 0; a < N; ++a) {
@@ -516,6 +518,7 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
             double x_xi = v1.x - v0.x, x_eta = v2.x - v0.x, y_xi = v1.y - v0.y, y_eta = v2.y - v0.y;
             double detJ = x_xi * y_eta - y_xi * x_eta;
             wall_idx[a] = (int)probe_e.size();
+            T.wall_nrm.push_back(make_double2(nx, ny));
             probe_e.push_back(best);
             probe_xi.push_back(make_double2((y_eta * (Bx - x0) - x_eta * (By - y0)) / detJ,
                                             (-y_xi * (Bx - x0) + x_xi * (By - y0)) / detJ));

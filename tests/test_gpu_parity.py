@@ -137,6 +137,22 @@ def test_fp64_bc_equilibrium_variant():
     _compare64(o, s, "bc-equilibrium")
 
 
+@pytest.mark.parametrize("prec", [alelb.PREC_FP64, alelb.PREC_FP32_DEV])
+def test_slip_wall_variant(prec):
+    """The slip (inviscid) wall variant on a pitching-plunging airfoil: wall
+    tangent in the physical frame, probe velocity, no non-equilibrium part."""
+    mesh, motion = LOC_CASES["omesh_pitch"]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    flow.flags = O.FLAG_SLIP_WALL
+    o, m, s = _pair(mesh, motion, flow, prec=prec)
+    o.step(6)
+    s.lb_step(6)
+    if prec == alelb.PREC_FP64:
+        _compare64(o, s, "slip wall")
+    else:
+        _compare_mixed(o, s, "slip wall mixed")
+
+
 def test_renumbering_does_not_change_results():
     case = I.uniform_flow_case(n=10, L=20.0, period_steps=30.0)
     mesh = case.mesh.permuted(7)

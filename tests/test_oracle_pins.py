@@ -637,3 +637,25 @@ def test_wall_condition_thin_first_layer_stays_bounded():
     # no slip: the wall nodes' tangential velocity well below the free stream
     wall = np.abs(mesh.X[:, 1]) < 1e-12
     assert np.abs(st["ux"][wall]).max() < 0.5 * flow.u_inf[0]
+
+
+def test_slip_walls_keep_uniform_tangential_flow():
+    """Slip-wall variant (flag SLIP_WALL; the paper has no inviscid wall, the
+    reading takes V_G plus the tangential part of the probe velocity and no
+    non-equilibrium part): a uniform flow along the flat walls of a channel
+    is an exact solution and must stay uniform to round-off, while the
+    no-slip condition of Sec. IV.A slows the wall nodes down."""
+    mesh = I.wall_channel(first=1.0)
+    flow = I.flow_params(0.2, T_inf=0.3, Re=1e4, chord=1000.0)
+    u0 = flow.u_inf[0]
+    flow.flags = O.FLAG_SLIP_WALL
+    o = O.Oracle(mesh, I.Motion.make(0), flow)
+    o.step(50)
+    st = o.state()
+    assert np.abs(st["ux"] - u0).max() < 1e-12 and np.abs(st["uy"]).max() < 1e-12
+    assert np.abs(st["rho"] - 1.0).max() < 1e-12 and np.abs(st["T"] - 0.3).max() < 1e-12
+    flow.flags = 0
+    o = O.Oracle(mesh, I.Motion.make(0), flow)
+    o.step(50)
+    wall = np.abs(mesh.X[:, 1]) < 1e-12
+    assert np.abs(o.state()["ux"][wall]).max() < 0.5 * u0
