@@ -70,9 +70,10 @@ template <class T> void put_state(DevBuf &b, StateDev<T> &s, int N, cudaError_t 
     s.Dy = b.alloc<T>(N, st);
     s.cache = b.alloc<int>((size_t)9 * N, st);
     if (st == cudaSuccess) st = cudaMemset(s.cache, 0xff, (size_t)9 * N * sizeof(int)); // -1: empty
-    s.work = b.alloc<int>((size_t)9 * N, st);
-    s.wcount = b.alloc<unsigned>(NQ, st);
-    if (st == cudaSuccess) st = cudaMemset(s.wcount, 0, NQ * sizeof(unsigned));
+    s.work = b.alloc<int>((size_t)10 * N, st);
+    s.wcount = b.alloc<unsigned>(NQ + 1, st);
+    if (st == cudaSuccess) st = cudaMemset(s.wcount, 0, (NQ + 1) * sizeof(unsigned));
+    s.wmask = b.alloc<unsigned short>(N, st);
 }
 
 

@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__
 }
 
 // The exact path over the work lists of all cases as one list, numbered
-// case by case and, within a case, direction by direction: block-local
-// prefix sums of the B x 9 segment counts, one population per thread, its
+// case by case and, within a case, direction by direction and then the
+// listed wall nodes: block-local prefix sums of the B x 10 segment counts, one population per thread, its
 // segment by binary search; the case descriptor is read from global memory
 // (the populations of a warp mostly share one case and one direction).
 template <class S, class A>
@@ -113,17 +113,19 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
                                                const MapScalars *__restrict__ sc,
                                                const MapScalarsF *__restrict__ sf, int count)
 {
-    __shared__ unsigned pre[BATCH_MAX * NQ + 1];
-    const int nseg = B * NQ;
+    constexpr int NS = NQ + 1; // segments per case: nine directions, then wall nodes
+    __shared__ unsigned pre[BATCH_MAX * NS + 1];
+    const int nseg = B * NS;
     if (threadIdx.x < 32) {
-        // lane l sums segments [l * 9, l * 9 + 9) (case l), then a warp scan
+        // lane l sums the segments of case l, then a warp scan
         const int lane = threadIdx.x;
-        unsigned loc[NQ];
-        unsigned s = 0;
+        unsigned loc[NS];
+        unsigned s = 0, npop = 0;
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) {
+        for (int i = 0; i < NS; ++i) {
             loc[i] = lane < B ? cases[lane].st.wcount[i] : 0u;
             s += loc[i];
+            if (i < NQ) npop += loc[i];
         }
         unsigned incl = s;
 #pragma unroll
@@ -134,13 +136,13 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
         if (lane < B) {
             unsigned run = incl - s;
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) {
-                pre[lane * NQ + i] = run;
+            for (int i = 0; i < NS; ++i) {
+                pre[lane * NS + i] = run;
                 run += loc[i];
             }
             if (lane == B - 1) pre[nseg] = run;
-            if (count && s && blockIdx.x == 0 && cases[lane].stats)
-                atomicAdd(cases[lane].stats, (unsigned long long)s);
+            if (count && npop && blockIdx.x == 0 && cases[lane].stats)
+                atomicAdd(cases[lane].stats, (unsigned long long)npop);
         }
     }
     __syncthreads();
@@ -152,10 +154,17 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
             if (pre[mid] <= w) lo = mid;
             else hi = mid - 1;
         }
-        const int c = lo / NQ, i = lo % NQ;
+        const int c = lo / NS, i = lo % NS;
         const CaseDev<S, A> &C = cases[c];
-        const int code = C.st.work[(size_t)i * C.M.N + (w - pre[lo])];
-        stream_slow_item(C.M, C.MS, sc[c], sf[c], C.K, C.st, C.err, code);
+        const int entry = C.st.work[(size_t)i * C.M.N + (w - pre[lo])];
+        if (i < NQ) {
+            stream_slow_item(C.M, C.MS, sc[c], sf[c], C.K, C.st, C.err, entry);
+        } else {
+            const unsigned mask = C.st.wmask[entry];
+            if (count && C.stats) atomicAdd(C.stats, (unsigned long long)__popc(mask));
+            stream_bc_node<S, A>(C.M, C.MS, sc[c], sf[c], C.K, C.st, entry,
+                                 fast_map(C.MS, sf[c], entry, C.M.Xf[entry]), mask);
+        }
     }
 }
 
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restric
     __syncthreads();
     const CaseDev<S, A> &C = sh.C();
     const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
-    if (a < NQ) C.st.wcount[a] = 0u; // the case's work list has been consumed
+    if (a <= NQ) C.st.wcount[a] = 0u; // the case's work list has been consumed
     if (a < C.M.N) moments_node(C.K, C.st, C.M.N, C.err, a);
 }
 
@@ -210,7 +219,7 @@ __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
 {
     const int c = threadIdx.x;
     if (c < B)
-        for (int i = 0; i < NQ; ++i) cases[c].st.wcount[i] = 0u;
+        for (int i = 0; i <= NQ; ++i) cases[c].st.wcount[i] = 0u;
 }
 
 int bs_index(int bs) { return bs == 64 ? 0 : bs == 128 ? 1 : 2; }

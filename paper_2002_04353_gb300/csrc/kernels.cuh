@@ -26,14 +26,18 @@ template <class S> struct StateDev {
     S *Dx, *Dy;           // first-pass results
     int *cache;           // [9 N] element of each population's previous departure point
                           // (elem | (sx+1)<<28 | (sy+1)<<30), -1 when empty
-    int *work;            // [9 N] populations (9 node + direction) left to the exact path,
-                          // direction i's at work[i N + k], k < wcount[i]
-    unsigned *wcount;     // [9] entries of each direction
+    int *work;            // [10 N] populations (9 node + direction) left to the exact path,
+                          // direction i's at work[i N + k], k < wcount[i]; then the nodes
+                          // with populations certified missing at a wall, at work[9 N + k],
+                          // k < wcount[9], their directions in wmask
+    unsigned *wcount;     // [10] entries of each segment
+    unsigned short *wmask; // [N] directions certified missing at a wall (listed nodes only)
 };
 
 // The exact-path kernels number the work list direction by direction
 // (populations of one direction at neighbouring nodes take similar paths,
-// so the lanes of a warp stay together): pre[i] = entries before direction i.
+// so the lanes of a warp stay together): pre[i] = entries before direction
+// i; the listed wall nodes follow the nine directions.
 __device__ __forceinline__ void work_prefix(const unsigned *wcount, unsigned pre[NQ + 1])
 {
     pre[0] = 0u;
@@ -382,7 +386,9 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
 }
 
 // Interpolates every population of node a whose previous-step element is
-// verified; returns the mask of the others.
+// verified and settles those certified missing at the far field; returns
+// the mask of the populations left to the exact path (bits 0-8) and of those
+// certified missing at a wall (bits 16-24, also stored in wmask).
 template <class S, class A>
 __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const MapStatic &MS,
                                                      const MapScalarsF &sf, const KinParams<A> &K,
@@ -399,6 +405,7 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
 #pragma unroll
         for (int i = 0; i < NQ; ++i) cache[i] = st.cache[i * N + a];
         const bool v0 = M.vzero[a];
+        unsigned wall = 0; // directions certified missing at a wall
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             int e;
@@ -423,13 +430,15 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
                 if (ck == 2) { // far field: free-stream equilibria
                     st.str[i * N + a] = (S)K.finf[i];
                     st.str[(NQ + i) * N + a] = (S)K.ginf[i];
+                } else if (ck == 1) {
+                    wall |= 1u << i; // the wall condition runs once per node in k_stream_slow
                 } else {
-                    // walls: the exact-path kernel, which repeats the cone
-                    // test and then needs no walk
                     slow |= 1u << i;
                 }
             }
         }
+        if (wall) st.wmask[a] = (unsigned short)wall;
+        slow |= wall << 16; // bits 16 and up: the node goes onto the wall-node list
     }
     return slow;
 }
@@ -443,17 +452,19 @@ __device__ __forceinline__ void append_work(const StateDev<S> &st, int a, int N,
     const unsigned lane = threadIdx.x & 31u;
     if (!__any_sync(0xffffffffu, slow != 0u)) return;
 #pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-        const bool mine = (slow >> i) & 1u;
+    for (int i = 0; i <= NQ; ++i) { // segment NQ: nodes with wall-missing populations
+        const bool mine = i < NQ ? ((slow >> i) & 1u) : (slow >> 16) != 0u;
         const unsigned m = __ballot_sync(0xffffffffu, mine);
         if (!m) continue;
         const int leader = __ffs(m) - 1;
         unsigned base = 0;
         if ((int)lane == leader) base = atomicAdd(st.wcount + i, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (mine) st.work[(size_t)i * N + base + __popc(m & ((1u << lane) - 1u))] = a * NQ + i;
+        if (mine)
+            st.work[(size_t)i * N + base + __popc(m & ((1u << lane) - 1u))] = i < NQ ? a * NQ + i : a;
     }
 }
+
 
 template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
@@ -539,6 +550,27 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
     }
 }
 
+// Entry w of the exact path's numbering (work_prefix over the 10 segments):
+// a population (9 node + direction), or a listed wall node, whose wall
+// condition is computed once for all its certified directions.
+template <class S, class A>
+__device__ __forceinline__ void slow_entry(const MeshDev &M, const MapStatic &MS,
+                                           const MapScalars &sc, const MapScalarsF &sf,
+                                           const KinParams<A> &K, const StateDev<S> &st, int *err,
+                                           const unsigned *pre, unsigned w, const int *prop,
+                                           unsigned long long *stats)
+{
+    if (w < pre[NQ]) {
+        stream_slow_item(M, MS, sc, sf, K, st, err, work_at(st.work, M.N, pre, w), prop ? prop[w] : -1,
+                         prop && stats ? stats + 1 : nullptr);
+    } else {
+        const int a = st.work[(size_t)NQ * M.N + (w - pre[NQ])];
+        const unsigned mask = st.wmask[a];
+        if (stats) atomicAdd(stats, (unsigned long long)__popc(mask));
+        stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, fast_map(MS, sf, a, M.Xf[a]), mask);
+    }
+}
+
 template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
                                                      MapScalarsF sf, KinParams<A> K, StateDev<S> st,
@@ -549,10 +581,10 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
     if (threadIdx.x == 0) work_prefix(st.wcount, pre);
     __syncthreads();
     const unsigned n = pre[NQ];
+    const unsigned total = n + st.wcount[NQ];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
-    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x)
-        stream_slow_item(M, MS, sc, sf, K, st, err, work_at(st.work, M.N, pre, w), prop ? prop[w] : -1,
-                         prop && stats ? stats + 1 : nullptr);
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x)
+        slow_entry(M, MS, sc, sf, K, st, err, pre, w, prop, stats);
 }
 
 
@@ -585,7 +617,7 @@ template <class S, class A>
 __global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st, int N, int *err)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < NQ) st.wcount[a] = 0u; // the work list has been consumed
+    if (a <= NQ) st.wcount[a] = 0u; // the work list has been consumed
     if (a < N) moments_node(K, st, N, err, a);
 }
 
