@@ -57,9 +57,10 @@ def workload(name="plunge150k"):
     return WORKLOADS[name]()
 
 
-def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4):
+def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4):
     """Algorithmic bytes of one launch: every value the kernel must read or
-    write, each counted once (FP32-deviation form, pop_bytes = 4).
+    write, each counted once (FP32-deviation form: pop_bytes = fld_bytes = 4;
+    16-bit forms: pop_bytes = 2, node fields still 4).
 
     k_stream_fast   per node: 18 post-collision populations read and (for the
                     settled ones, about all) 18 streamed written, 9 element-
@@ -86,20 +87,23 @@ def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4):
                     per element frame, neighbours, edge info, rank,
                     connectivity (92 B)
     """
-    N, E, W, p = n_nodes, n_elems, exact_items, pop_bytes
+    N, E, W, p, f = n_nodes, n_elems, exact_items, pop_bytes, fld_bytes
     if kernel == "k_stream_fast":
         return N * (36 * p + 36 + 16 + 5) + E * 56
     if kernel == "k_stream_slow":
         return W * (4 + 16 + 14 * p + 4 + 104)
     if kernel == "k_moments":
-        return N * (18 * p + 3 * p)
+        return N * (18 * p + 3 * f)
     if kernel == "k_deriv1":
-        return N * (3 * p + 8 + 16 + 2 * p) + E * 40
+        return N * (3 * f + 8 + 16 + 2 * f) + E * 40
     if kernel == "k_collide":
-        return N * (18 * p + 2 * p + 8 + 16 + 18 * p + 4 * p) + E * 40
+        return N * (18 * p + 2 * f + 8 + 16 + 18 * p + 4 * f) + E * 40
     if kernel == "k_stream":
-        return N * (36 * p + 3 * p + 16 + 3 * 8 + 4) + E * 92
+        return N * (36 * p + 3 * f + 16 + 3 * 8 + 4) + E * 92
     return 0
+
+
+STEP_KERNELS = ("k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide")
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -369,6 +373,86 @@ def run_learned(alelb, torch, dev, args):
                          "source": f"pitch mesh {c3.mesh.n_nodes} nodes, 10 map times over one period"}}
 
 
+def run_precision(alelb, torch, dev, args):
+    """Storage precision on the 600,320-node deforming pitching mesh
+    (alpha = 0.1 + 2.5 deg sin(omega t), k = 0.08, Mach `--prec-mach`): the
+    FP64, FP32-deviation, BF16-deviation and FP16-deviation forms advance
+    the same free-stream start by the same steps.  Each deviation form
+    reports its throughput over the last `--prec-steps` steps (L2 flushed
+    before each) and the error of rho, u, T against the FP64 form (max and
+    RMS over the nodes, normalised by rho_inf, |u_inf| and T_inf) twice:
+    after 20 steps, where it is the storage rounding, and at the end, where
+    the start transient next to the suction side has amplified it (every
+    form, FP32 included, differs there from FP64 by far more than its
+    rounding).  A form whose state leaves the admissible range is reported
+    as diverged."""
+    case = I.pitch_case(ni=640, nj=235, Ma=args.prec_mach)
+    mesh = alelb.Mesh(case.mesh, case.motion)
+    N, E = case.mesh.n_nodes, case.mesh.n_elems
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    W, K = max(20, args.warmup), args.prec_steps
+    U = math.hypot(*case.flow.u_inf)
+    out, ref, ref_early = {}, None, None
+
+    def errors(mo, base):
+        err = {}
+        for k, sc in (("rho", case.flow.rho_inf), ("ux", U), ("uy", U), ("T", case.flow.T_inf)):
+            d = (mo[k] - base[k]) / sc
+            err[k] = {"max": float(np.abs(d).max()), "rms": float(np.sqrt(np.mean(d * d)))}
+        return err
+
+    forms = (("fp64", alelb.PREC_FP64, 8), ("fp32_dev", alelb.PREC_FP32_DEV, 4),
+             ("bf16_dev", alelb.PREC_BF16_DEV, 2), ("fp16_dev", alelb.PREC_FP16_DEV, 2))
+    for label, prec, pb in forms:
+        s = alelb.Solver(mesh, case.flow, prec, stream=stream.cuda_stream)
+        s.lb_step(W)
+        try:
+            s.sync()
+        except alelb.AlelbError as e:
+            out[label] = {"diverged": str(e), "within_steps": W}
+            s.close()
+            continue
+        early = s.moments()
+        walks0 = s.info()["walks"]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                s.lb_step(1)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        try:
+            s.sync()
+        except alelb.AlelbError as e:
+            out[label] = {"diverged": str(e), "within_steps": W + K}
+            s.close()
+            continue
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        n_exact = (s.info()["walks"] - walks0) / K
+        mo = s.moments()
+        s.close()
+        r = {"value": N * K / (ms * 1e-3) / 1e6, "ms_per_step": ms / K, "pop_bytes": pb}
+        if prec != alelb.PREC_FP64:
+            step_bytes = sum(kernel_bytes(k, N, E, n_exact, pop_bytes=pb) for k in STEP_KERNELS)
+            r["algorithmic_bytes_per_step"] = step_bytes
+            r["achieved_gbs"] = step_bytes / (ms / K * 1e-3) / 1e9
+        if prec == alelb.PREC_FP64:
+            ref, ref_early = mo, early
+        elif ref is None:
+            r["error_vs_fp64"] = None
+        else:
+            r[f"error_vs_fp64_step{W}"] = errors(early, ref_early)
+            r[f"error_vs_fp64_step{W + K}"] = errors(mo, ref)
+        out[label] = r
+    return {"unit": UNIT, "workload": f"pitch600k: deforming O-mesh {N} nodes, Mach {args.prec_mach}, "
+                                      f"alpha 0.1 + 2.5 deg sin(wt), k 0.08", "steps": W + K, "timed_steps": K,
+            "errors": f"normalised by rho_inf, |u_inf|, T_inf; max and RMS over nodes after {W} and {W + K} steps",
+            **out}
+
+
 def run_ours(args):
     import torch
     from paper_2002_04353_gb300 import alelb
@@ -445,8 +529,7 @@ def run_ours(args):
     per_kernel = {k: {"algorithmic_bytes": kernel_bytes(k, N, E, n_exact),
                       "achieved_gbs": kernel_bytes(k, N, E, n_exact) / (v[0] / v[1] * 1e-3) / 1e9}
                   for k, v in kt32.items() if v[1]}
-    step_bytes = sum(kernel_bytes(k, N, E, n_exact) for k in ("k_stream_fast", "k_stream_slow", "k_moments",
-                                                              "k_deriv1", "k_collide"))
+    step_bytes = sum(kernel_bytes(k, N, E, n_exact) for k in STEP_KERNELS)
 
     # end to end through the C-ABI with host buffers: host-resident state,
     # every step uploads the populations from pinned host memory, advances
@@ -471,6 +554,7 @@ def run_ours(args):
 
     batched = None if args.no_batched else run_batched(alelb, torch, dev, world, rank, args)
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
+    precision = None if (args.no_precision or world > 1) else run_precision(alelb, torch, dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -508,6 +592,7 @@ def run_ours(args):
             "gpu_launches": 5 * K,
             "batched": batched,
             "learned_proposal": learned,
+            "precision_study": precision,
             "locate": {"walks_per_step": info32["walks_timed"] / K,
                        "verified_previous_element_rate": 1.0 - info32["walks_timed"] / (9.0 * N * K)},
             "step_ms": [round(x, 4) for x in info32["step_ms"]],
@@ -534,6 +619,9 @@ def main():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=10)
+    ap.add_argument("--prec-steps", type=int, default=200)
+    ap.add_argument("--prec-mach", type=float, default=0.3)
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -66,7 +66,20 @@ enum {
 
 enum { ALELB_EDGE_INTERIOR = 0, ALELB_EDGE_WALL = 1, ALELB_EDGE_FARFIELD = 2 };
 enum { ALELB_RENUMBER_NONE = 0, ALELB_RENUMBER_MORTON = 1 };
-enum { ALELB_PREC_FP64 = 0, ALELB_PREC_FP32_DEV = 1 };
+/* Storage and arithmetic of a solver (Sec. IV's populations; the paper
+   computes in FP64 and gives no reduced-precision form):
+     FP64      full populations and fields in FP64, FP64 arithmetic, every
+               departure point through the exact element walk;
+     FP32_DEV  populations stored in FP32 as deviations from the rest
+               equilibria at (rho_inf, T_inf), fields in FP32, FP32
+               arithmetic with FP64 (certified) element decisions;
+     BF16_DEV  as FP32_DEV, populations stored in bfloat16 as deviations
+               from the far-field equilibria at (rho_inf, u_inf, T_inf);
+     FP16_DEV  as BF16_DEV, populations stored in IEEE binary16 as 2^10
+               times the deviation (|deviation| < 64).
+   Element choices are the same in every form; values differ by the
+   storage rounding. */
+enum { ALELB_PREC_FP64 = 0, ALELB_PREC_FP32_DEV = 1, ALELB_PREC_BF16_DEV = 2, ALELB_PREC_FP16_DEV = 3 };
 
 /* Solver flags (alelb_params.flags). */
 enum {
@@ -164,7 +177,7 @@ alelb_status alelb_forces(alelb_solver *s, double out[6]);
    [9][n_nodes] in original numbering: elem = original element id, -2 (the
    departure point is the node itself) or -1 (missing; kind = 1 wall,
    2 far field).  use_cache = 0: the element walk decides every population;
-   use_cache = 1 (FP32-deviation solvers): the decision the propagation
+   use_cache = 1 (deviation-form solvers): the decision the propagation
    kernel would take now -- the previous-step element where the certified
    FP32 test accepts it, the walk elsewhere.  Synchronous; changes nothing. */
 alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cache, int32_t *elem, int8_t *kind);
@@ -229,7 +242,7 @@ typedef struct alelb_batch alelb_batch;
 /* cases: host array of B solver handles, read during the call.  stream: the
    cudaStream_t of the batch's launches (NULL: the batch's own non-blocking
    stream).  Errors: ALELB_ERR_ARG (B out of 1..32, a null or repeated
-   solver, mixed precision), ALELB_ERR_OOM, ALELB_ERR_CUDA. */
+   solver, mixed precision, a 16-bit form), ALELB_ERR_OOM, ALELB_ERR_CUDA. */
 alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B, void *stream, alelb_batch **out);
 void alelb_batch_destroy(alelb_batch *b);
 
@@ -321,7 +334,7 @@ alelb_status alelb_mlp_train(alelb_mlp *m, const float *feat, const int16_t *slo
 alelb_status alelb_mlp_predict(alelb_mlp *m, const float *feat, const uint8_t *nring, int64_t n,
                                int32_t *slot, float *out);
 
-/* Use network m (NULL: none) for the proposals of an FP32-deviation
+/* Use network m (NULL: none) for the proposals of a deviation-form
    solver's later steps.  The network is not copied and must outlive its
    use; ALELB_ERR_ARG for an FP64 solver. */
 alelb_status alelb_solver_set_mlp(alelb_solver *s, alelb_mlp *m);

@@ -20,6 +20,8 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_MESH",
           -6: "ERR_LOCATE", -7: "ERR_NONFINITE", -8: "ERR_TIMEOUT", -9: "ERR_STATE"}
 PREC_FP64 = 0
 PREC_FP32_DEV = 1
+PREC_BF16_DEV = 2
+PREC_FP16_DEV = 3
 RENUMBER_NONE = 0
 RENUMBER_MORTON = 1
 FLAG_PHI_OFF = 1

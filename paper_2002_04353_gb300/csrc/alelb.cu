@@ -55,19 +55,21 @@ alelb_status check_sticky(alelb_solver *s)
 
 namespace {
 
-template <class T> void put_state(DevBuf &b, StateDev<T> &s, int N, cudaError_t &st)
+template <class S> void put_state(DevBuf &b, StateDev<S> &s, int N, cudaError_t &st)
 {
-    s.post = b.alloc<T>((size_t)18 * N, st);
-    s.str = b.alloc<T>((size_t)18 * N, st);
-    s.rho = b.alloc<T>(N, st);
-    s.ux = b.alloc<T>(N, st);
-    s.uy = b.alloc<T>(N, st);
-    s.T = b.alloc<T>(N, st);
-    s.Qx = b.alloc<T>(N, st);
-    s.Qy = b.alloc<T>(N, st);
-    s.mrt = b.alloc<T>(N, st);
-    s.Dx = b.alloc<T>(N, st);
-    s.Dy = b.alloc<T>(N, st);
+    using P = pop_t<S>;
+    using F = fld_t<S>;
+    s.post = b.alloc<P>((size_t)18 * N, st);
+    s.str = b.alloc<P>((size_t)18 * N, st);
+    s.rho = b.alloc<F>(N, st);
+    s.ux = b.alloc<F>(N, st);
+    s.uy = b.alloc<F>(N, st);
+    s.T = b.alloc<F>(N, st);
+    s.Qx = b.alloc<F>(N, st);
+    s.Qy = b.alloc<F>(N, st);
+    s.mrt = b.alloc<F>(N, st);
+    s.Dx = b.alloc<F>(N, st);
+    s.Dy = b.alloc<F>(N, st);
     s.cache = b.alloc<int>((size_t)9 * N, st);
     if (st == cudaSuccess) st = cudaMemset(s.cache, 0xff, (size_t)9 * N * sizeof(int)); // -1: empty
     s.work = b.alloc<int>((size_t)10 * N, st);
@@ -136,6 +138,9 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     m->mst.msf = B.put(T.msf, st);
     if (st == cudaSuccess) st = upload_fe_tables();
     if (st == cudaSuccess) st = batch_fe_tables();
+    // the uploads above run on the legacy default stream, which solvers on
+    // non-blocking streams do not wait for
+    if (st == cudaSuccess) st = cudaDeviceSynchronize();
     *out = m;
     if (st != cudaSuccess) {
         m->buf.release();
@@ -185,20 +190,24 @@ namespace {
 
 
 // Reference and far-field populations computed on the device with the
-// same kernel code that the step uses.
+// same kernel code that the step uses.  Reference: none (ref_mode 0, the
+// FP64 form stores full populations), the equilibria at rest at rho_inf,
+// T_inf (1, FP32 deviations), or the far-field equilibria (2, the 16-bit
+// forms: far from the body the stored deviations are then close to zero,
+// where the 16-bit formats have their finest absolute spacing).
 __global__ void k_kin_consts(KinParams<double> K, double rho_inf, double uxi, double uyi,
-                             double T_inf, int dev_mode, double *out)
+                             double T_inf, int ref_mode, double *out)
 {
     double f[NQ], g[NQ], M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py;
-    // reference state (rest at rho_inf, T_inf)
-    feq9(rho_inf, 0.0, 0.0, T_inf, f);
-    double E0 = K.Cv * T_inf;
-    gmoments(rho_inf, 0.0, 0.0, T_inf, E0, M0, qx, qy, Rxx, Rxy, Ryy);
-    psi_terms(rho_inf, 0.0, 0.0, T_inf, E0, pr, px, py);
+    const double urx = ref_mode == 2 ? uxi : 0.0, ury = ref_mode == 2 ? uyi : 0.0;
+    feq9(rho_inf, urx, ury, T_inf, f);
+    double E0 = K.Cv * T_inf + 0.5 * (urx * urx + ury * ury);
+    gmoments(rho_inf, urx, ury, T_inf, E0, M0, qx, qy, Rxx, Rxy, Ryy);
+    psi_terms(rho_inf, urx, ury, T_inf, E0, pr, px, py);
     gform9(T_inf, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, g);
     for (int i = 0; i < NQ; ++i) {
-        out[i] = dev_mode ? f[i] : 0.0;
-        out[NQ + i] = dev_mode ? g[i] : 0.0;
+        out[i] = ref_mode ? f[i] : 0.0;
+        out[NQ + i] = ref_mode ? g[i] : 0.0;
     }
     // far field
     feq9(rho_inf, uxi, uyi, T_inf, f);
@@ -220,13 +229,13 @@ __global__ void k_fill_uniform(StateDev<S> st, int N, const double *consts, doub
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
     for (int i = 0; i < NQ; ++i) {
-        st.post[i * N + a] = (S)(consts[2 * NQ + i] - consts[i]);
-        st.post[(NQ + i) * N + a] = (S)(consts[3 * NQ + i] - consts[NQ + i]);
+        pop_put(st.post + (i * N + a), consts[2 * NQ + i] - consts[i]);
+        pop_put(st.post + ((NQ + i) * N + a), consts[3 * NQ + i] - consts[NQ + i]);
     }
-    st.rho[a] = (S)rho;
-    st.ux[a] = (S)ux;
-    st.uy[a] = (S)uy;
-    st.T[a] = (S)T;
+    st.rho[a] = (fld_t<S>)rho;
+    st.ux[a] = (fld_t<S>)ux;
+    st.uy[a] = (fld_t<S>)uy;
+    st.T[a] = (fld_t<S>)T;
 }
 
 // Full FP64 populations <-> stored deviations (internal order).
@@ -239,24 +248,24 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
     double r = 0, jx = 0, jy = 0, e2 = 0;
     for (int i = 0; i < NQ; ++i) {
         double f = full[i * N + a], g = full[(NQ + i) * N + a];
-        st.post[i * N + a] = (S)(f - consts[i]);
-        st.post[(NQ + i) * N + a] = (S)(g - consts[NQ + i]);
+        pop_put(st.post + (i * N + a), f - consts[i]);
+        pop_put(st.post + ((NQ + i) * N + a), g - consts[NQ + i]);
         r += f;
         jx += c_cx[i] * f;
         jy += c_cy[i] * f;
         e2 += g;
     }
     if (have_fields) {
-        st.rho[a] = (S)fields[a];
-        st.ux[a] = (S)fields[N + a];
-        st.uy[a] = (S)fields[2 * N + a];
-        st.T[a] = (S)fields[3 * N + a];
+        st.rho[a] = (fld_t<S>)fields[a];
+        st.ux[a] = (fld_t<S>)fields[N + a];
+        st.uy[a] = (fld_t<S>)fields[2 * N + a];
+        st.T[a] = (fld_t<S>)fields[3 * N + a];
     } else {
         double ux = jx / r, uy = jy / r, E = e2 / (2 * r);
-        st.rho[a] = (S)r;
-        st.ux[a] = (S)ux;
-        st.uy[a] = (S)uy;
-        st.T[a] = (S)((E - 0.5 * (ux * ux + uy * uy)) / Cv);
+        st.rho[a] = (fld_t<S>)r;
+        st.ux[a] = (fld_t<S>)ux;
+        st.uy[a] = (fld_t<S>)uy;
+        st.T[a] = (fld_t<S>)((E - 0.5 * (ux * ux + uy * uy)) / Cv);
     }
 }
 
@@ -267,8 +276,8 @@ __global__ void k_export(StateDev<S> st, int N, const double *consts, double *fu
     if (a >= N) return;
     if (full)
         for (int i = 0; i < NQ; ++i) {
-            full[i * N + a] = (double)st.post[i * N + a] + consts[i];
-            full[(NQ + i) * N + a] = (double)st.post[(NQ + i) * N + a] + consts[NQ + i];
+            full[i * N + a] = pop_in<double>(st.post[i * N + a]) + consts[i];
+            full[(NQ + i) * N + a] = pop_in<double>(st.post[(NQ + i) * N + a]) + consts[NQ + i];
         }
     if (fields) {
         fields[a] = (double)st.rho[a];
@@ -322,7 +331,7 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
     const bool phi = !(s->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF));
-    const bool fast = s->prec == ALELB_PREC_FP32_DEV;
+    const bool fast = s->prec != ALELB_PREC_FP64;
     const MapScalarsF sf = to_f32(sc, m->T);
     int seq[KT_N], ns = 0;
     if (fast) {
@@ -389,18 +398,28 @@ template <class A> void fill_kin(alelb_solver *s, KinParams<A> &K)
     K.Cp = (A)s->Cp;
     K.mu = (A)s->mu;
     K.Pr = (A)s->Pr;
-    double rref = 0, e2 = 0;
+    double r = 0, jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0, e2 = 0;
     for (int i = 0; i < NQ; ++i) {
-        K.fref[i] = (A)s->consts[i];
+        const double fr = s->consts[i];
+        K.fref[i] = (A)fr;
         K.gref[i] = (A)s->consts[NQ + i];
-        K.finf[i] = (A)(s->consts[2 * NQ + i] - s->consts[i]);
+        K.finf[i] = (A)(s->consts[2 * NQ + i] - fr);
         K.ginf[i] = (A)(s->consts[3 * NQ + i] - s->consts[NQ + i]);
-        rref += s->consts[i];
+        r += fr;
+        jx += lat_cx(i) * fr;
+        jy += lat_cy(i) * fr;
+        pxx += lat_cx(i) * lat_cx(i) * fr;
+        pxy += lat_cx(i) * lat_cy(i) * fr;
+        pyy += lat_cy(i) * lat_cy(i) * fr;
         e2 += s->consts[NQ + i];
     }
-    K.rho_ref = (A)rref;
+    K.rho_ref = (A)r;
+    K.jx_ref = (A)jx;
+    K.jy_ref = (A)jy;
+    K.Pxx_ref = (A)pxx;
+    K.Pxy_ref = (A)pxy;
+    K.Pyy_ref = (A)pyy;
     K.E2_ref = (A)e2;
-    K.T_ref = (A)(s->prec == ALELB_PREC_FP64 ? 0.0 : s->T_inf);
     K.flags = s->flags;
 }
 
@@ -411,7 +430,7 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
 {
     if (!m || !p || !out) return ALELB_ERR_ARG;
     if (!(p->gamma > 1.0) || !(p->Pr > 0) || !(p->mu > 0) || !(p->rho_inf > 0) || !(p->T_inf > 0) ||
-        (p->precision != ALELB_PREC_FP64 && p->precision != ALELB_PREC_FP32_DEV))
+        p->precision < ALELB_PREC_FP64 || p->precision > ALELB_PREC_FP16_DEV)
         return ALELB_ERR_ARG;
     alelb_solver *s = new (std::nothrow) alelb_solver();
     if (!s) return ALELB_ERR_OOM;
@@ -443,8 +462,7 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
             s->n_sm = nsm;
     }
-    if (s->prec == ALELB_PREC_FP64) put_state(s->buf, s->sd, N, st);
-    else put_state(s->buf, s->sf, N, st);
+    with_state(s, [&](auto &sx, auto &) { put_state(s->buf, sx, N, st); });
     s->d_consts = s->buf.alloc<double>(4 * NQ, st);
     s->d_scratch = s->buf.alloc<double>((size_t)22 * N, st);
     if (st == cudaSuccess) st = cudaHostAlloc((void **)&s->h_pinned, (size_t)22 * N * sizeof(double), 0);
@@ -452,11 +470,13 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     s->d_stats = s->buf.alloc<unsigned long long>(4, st);
     if (st == cudaSuccess) st = cudaMemset(s->d_stats, 0, 4 * sizeof(unsigned long long));
     s->d_out = s->buf.alloc<double>(8, st);
+    if (st == cudaSuccess) st = cudaDeviceSynchronize(); // the memsets above (legacy default stream)
     if (st != cudaSuccess) return cuda_fail(s, st);
     KinParams<double> K0{};
     K0.Cv = s->Cv;
-    k_kin_consts<<<1, 1, 0, s->stream>>>(K0, s->rho_inf, s->uinf[0], s->uinf[1], s->T_inf,
-                                         s->prec == ALELB_PREC_FP32_DEV, s->d_consts);
+    const int ref_mode = s->prec == ALELB_PREC_FP64 ? 0 : s->prec == ALELB_PREC_FP32_DEV ? 1 : 2;
+    k_kin_consts<<<1, 1, 0, s->stream>>>(K0, s->rho_inf, s->uinf[0], s->uinf[1], s->T_inf, ref_mode,
+                                         s->d_consts);
     st = cudaGetLastError();
     if (st == cudaSuccess)
         st = cudaMemcpyAsync(s->consts, s->d_consts, sizeof(s->consts), cudaMemcpyDeviceToHost, s->stream);
@@ -465,12 +485,10 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     if (st != cudaSuccess) return cuda_fail(s, st);
     fill_kin(s, s->kd);
     fill_kin(s, s->kf);
-    if (s->prec == ALELB_PREC_FP64)
-        k_fill_uniform<double><<<(N + 255) / 256, 256, 0, s->stream>>>(
-            s->sd, N, s->d_consts, s->rho_inf, s->uinf[0], s->uinf[1], s->T_inf);
-    else
-        k_fill_uniform<float><<<(N + 255) / 256, 256, 0, s->stream>>>(
-            s->sf, N, s->d_consts, s->rho_inf, s->uinf[0], s->uinf[1], s->T_inf);
+    with_state(s, [&](auto &sx, auto &) {
+        k_fill_uniform<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, s->rho_inf, s->uinf[0],
+                                                                s->uinf[1], s->T_inf);
+    });
     st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
@@ -497,8 +515,7 @@ extern "C" alelb_status alelb_lb_step(alelb_solver *s, int32_t n)
     for (int k = 0; k < n; ++k) {
         double t1 = s->t + 1.0;
         MapScalars sc = map_scalars(s->mesh->T.mkind, s->mesh->T.mp, t1);
-        cudaError_t st = s->prec == ALELB_PREC_FP64 ? launch_step(s, s->sd, s->kd, sc)
-                                                     : launch_step(s, s->sf, s->kf, sc);
+        cudaError_t st = with_state(s, [&](auto &sx, auto &K) { return launch_step(s, sx, K, sc); });
         if (st != cudaSuccess) return cuda_fail(s, st);
         s->t = t1;
         s->nstep++;
@@ -533,10 +550,9 @@ alelb_status export_state(alelb_solver *s, bool pops, const double **full, const
     const int N = m->T.N;
     double *dfull = pops ? s->d_scratch : nullptr;
     double *dfields = s->d_scratch + (size_t)18 * N;
-    if (s->prec == ALELB_PREC_FP64)
-        k_export<double><<<(N + 255) / 256, 256, 0, s->stream>>>(s->sd, N, s->d_consts, dfull, dfields);
-    else
-        k_export<float><<<(N + 255) / 256, 256, 0, s->stream>>>(s->sf, N, s->d_consts, dfull, dfields);
+    with_state(s, [&](auto &sx, auto &) {
+        k_export<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, dfull, dfields);
+    });
     cudaError_t st = cudaGetLastError();
     if (st == cudaSuccess && pops)
         st = cudaMemcpyAsync(s->h_pinned, dfull, (size_t)18 * N * sizeof(double),
@@ -621,12 +637,10 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
         st = cudaMemcpyAsync(s->d_scratch + (size_t)18 * N, fields, (size_t)4 * N * sizeof(double),
                              cudaMemcpyHostToDevice, s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
-    if (s->prec == ALELB_PREC_FP64)
-        k_import<double><<<(N + 255) / 256, 256, 0, s->stream>>>(
-            s->sd, N, s->d_consts, s->d_scratch, s->d_scratch + (size_t)18 * N, have, s->Cv);
-    else
-        k_import<float><<<(N + 255) / 256, 256, 0, s->stream>>>(
-            s->sf, N, s->d_consts, s->d_scratch, s->d_scratch + (size_t)18 * N, have, s->Cv);
+    with_state(s, [&](auto &sx, auto &) {
+        k_import<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch,
+                                                          s->d_scratch + (size_t)18 * N, have, s->Cv);
+    });
     st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
@@ -640,12 +654,10 @@ extern "C" alelb_status alelb_forces(alelb_solver *s, double out[6])
     alelb_mesh *m = s->mesh;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, s->t);
     if (m->nw > 0) {
-        if (s->prec == ALELB_PREC_FP64)
-            k_forces<double><<<1, 256, 0, s->stream>>>(m->dev, m->mst, sc, s->sd, m->d_wedges, m->nw,
-                                                       s->mu, s->Cv, s->d_out);
-        else
-            k_forces<float><<<1, 256, 0, s->stream>>>(m->dev, m->mst, sc, s->sf, m->d_wedges, m->nw,
-                                                      s->mu, s->Cv, s->d_out);
+        with_state(s, [&](auto &sx, auto &) {
+            k_forces<<<1, 256, 0, s->stream>>>(m->dev, m->mst, sc, sx, m->d_wedges, m->nw, s->mu, s->Cv,
+                                               s->d_out);
+        });
     } else {
         cudaMemsetAsync(s->d_out, 0, 4 * sizeof(double), s->stream);
     }
@@ -672,11 +684,11 @@ extern "C" alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cach
     if (!s || !elem || !kind) return ALELB_ERR_ARG;
     const int *cache = nullptr;
     if (use_cache) {
-        if (s->prec != ALELB_PREC_FP32_DEV) {
-            s->err = "locate: the cached fast decisions exist in the FP32-deviation form only";
+        if (s->prec == ALELB_PREC_FP64) {
+            s->err = "locate: the cached fast decisions exist in the deviation forms only";
             return ALELB_ERR_ARG;
         }
-        cache = s->sf.cache;
+        with_state(s, [&](auto &sx, auto &) { cache = sx.cache; });
     }
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
@@ -739,7 +751,7 @@ extern "C" alelb_status alelb_info(alelb_solver *s, double out[8])
 {
     if (!s || !out) return ALELB_ERR_ARG;
     alelb_mesh *m = s->mesh;
-    double sz = s->prec == ALELB_PREC_FP64 ? 8.0 : 4.0;
+    double sz = s->prec == ALELB_PREC_FP64 ? 8.0 : s->prec == ALELB_PREC_FP32_DEV ? 4.0 : 2.0;
     out[0] = m->T.N;
     out[1] = m->T.E;
     out[2] = sz;
@@ -849,7 +861,6 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     K.Pr = p->Pr;
     K.rho_ref = 0.0;
     K.E2_ref = 0.0;
-    K.T_ref = 0.0;
     for (int i = 0; i < NQ; ++i) {
         K.fref[i] = 0.0;
         K.gref[i] = 0.0;

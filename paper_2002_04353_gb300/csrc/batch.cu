@@ -476,6 +476,8 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     for (int c = 0; c < B; ++c) {
         if (!cases[c] || !cases[c]->mesh) return ALELB_ERR_ARG;
         if (cases[c]->prec != cases[0]->prec) return ALELB_ERR_ARG;
+        // the batched kernels are built for the FP64 and FP32-deviation forms
+        if (cases[c]->prec != ALELB_PREC_FP64 && cases[c]->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
         for (int d = 0; d < c; ++d)
             if (cases[d] == cases[c]) return ALELB_ERR_ARG;
     }
@@ -506,7 +508,8 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         }
         b->d_off[q] = b->buf.put(o, st);
     }
-    st = b->prec == ALELB_PREC_FP32_DEV ? upload_cases<float, float>(b) : upload_cases<double, double>(b);
+    if (st == cudaSuccess)
+        st = b->prec == ALELB_PREC_FP32_DEV ? upload_cases<float, float>(b) : upload_cases<double, double>(b);
     b->d_sc = b->buf.alloc<MapScalars>((size_t)CHUNK_MAX * B, st);
     b->d_sf = b->buf.alloc<MapScalarsF>((size_t)CHUNK_MAX * B, st);
     for (int sl = 0; sl < 2; ++sl) {
@@ -518,6 +521,9 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     for (int c = 0; c < B && st == cudaSuccess; ++c)
         st = cudaEventCreateWithFlags(&b->ev_in[c], cudaEventDisableTiming);
     if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    // the table uploads above run on the legacy default stream, which the
+    // batch's non-blocking stream does not wait for
+    if (st == cudaSuccess) st = cudaDeviceSynchronize();
     if (st != cudaSuccess) return bfail(b, st, "batch_create");
     return ALELB_OK;
 }

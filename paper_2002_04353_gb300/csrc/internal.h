@@ -80,8 +80,10 @@ struct alelb_solver {
     double Cv = 2.5, Cp = 3.5;
     double t = 0;
     int64_t nstep = 0;
-    StateDev<double> sd{};
-    StateDev<float> sf{};
+    StateDev<double> sd{};  // ALELB_PREC_FP64
+    StateDev<float> sf{};   // ALELB_PREC_FP32_DEV
+    StateDev<Bf16Dev> sb{}; // ALELB_PREC_BF16_DEV
+    StateDev<Fp16Dev> sh{}; // ALELB_PREC_FP16_DEV
     KinParams<double> kd{};
     KinParams<float> kf{};
     double consts[4 * NQ] = {0};
@@ -101,6 +103,20 @@ struct alelb_solver {
     double ms_acc[KT_N] = {};
     int64_t n_acc[KT_N] = {};
     int n_sm = 152;
-    alelb_mlp *mlp = nullptr; // learned proposal (not owned), FP32-deviation solvers
+    alelb_mlp *mlp = nullptr; // learned proposal (not owned), deviation-form solvers
     int *d_prop = nullptr;    // [9 N] proposal per work-list entry
 };
+
+namespace alelb {
+// Calls fn(state, kinetic parameters) with the solver's state of its
+// precision (the deviation forms share the FP32 kinetic parameters).
+template <class Fn> auto with_state(alelb_solver *s, Fn &&fn)
+{
+    switch (s->prec) {
+    case ALELB_PREC_FP64: return fn(s->sd, s->kd);
+    case ALELB_PREC_FP32_DEV: return fn(s->sf, s->kf);
+    case ALELB_PREC_BF16_DEV: return fn(s->sb, s->kf);
+    default: return fn(s->sh, s->kf);
+    }
+}
+} // namespace alelb

@@ -13,17 +13,58 @@
 // One thread per node.  Populations are stored structure-of-arrays,
 // pop[q * N + node] with q = 0..8 for f and 9..17 for g.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "geom.cuh"
 #include "kinetic.cuh"
 
 namespace alelb {
 
+// Storage of a state: populations (deviations from the reference state) in
+// pop_t<S>, node fields in fld_t<S>.  S = double or float stores both in S.
+// The two 16-bit forms store the populations in 2 bytes and everything else,
+// the arithmetic included, in FP32:
+//   Bf16Dev  bfloat16 (8 significant bits, round to nearest even);
+//   Fp16Dev  IEEE binary16 of the deviation times 2^10 (11 significant bits;
+//            the power-of-two scale is exact and moves deviations down to
+//            about 6e-8 out of the subnormal range; |deviation| < 64).
+struct Bf16Dev {};
+struct Fp16Dev {};
+template <class S> struct Store { using pop = S; using fld = S; };
+template <> struct Store<Bf16Dev> { using pop = __nv_bfloat16; using fld = float; };
+template <> struct Store<Fp16Dev> { using pop = __half; using fld = float; };
+template <class S> using pop_t = typename Store<S>::pop;
+template <class S> using fld_t = typename Store<S>::fld;
+
+constexpr float FP16_DEV_SCALE = 1024.f, FP16_DEV_UNSCALE = 1.f / 1024.f;
+
+template <class A> __device__ __forceinline__ A pop_in(double v) { return (A)v; }
+template <class A> __device__ __forceinline__ A pop_in(float v) { return (A)v; }
+template <class A> __device__ __forceinline__ A pop_in(__nv_bfloat16 v) { return (A)__bfloat162float(v); }
+template <class A> __device__ __forceinline__ A pop_in(__half v)
+{
+    return (A)(__half2float(v) * FP16_DEV_UNSCALE);
+}
+template <class A> __device__ __forceinline__ void pop_put(double *p, A v) { *p = (double)v; }
+template <class A> __device__ __forceinline__ void pop_put(float *p, A v) { *p = (float)v; }
+template <class A> __device__ __forceinline__ void pop_put(__nv_bfloat16 *p, A v)
+{
+    *p = __float2bfloat16_rn((float)v);
+}
+template <class A> __device__ __forceinline__ void pop_put(__half *p, A v)
+{
+    *p = __float2half_rn((float)v * FP16_DEV_SCALE);
+}
+
 template <class S> struct StateDev {
-    S *post;  // [18 N] post-collision populations (deviations)
-    S *str;   // [18 N] streamed populations
-    S *rho, *ux, *uy, *T; // fields of the latest step
-    S *Qx, *Qy, *mrt;     // Q'_xxx, Q'_yyy, mu/(rho T)
-    S *Dx, *Dy;           // first-pass results
+    using P = pop_t<S>;
+    using F = fld_t<S>;
+    P *post;  // [18 N] post-collision populations (deviations)
+    P *str;   // [18 N] streamed populations
+    F *rho, *ux, *uy, *T; // fields of the latest step
+    F *Qx, *Qy, *mrt;     // Q'_xxx, Q'_yyy, mu/(rho T)
+    F *Dx, *Dy;           // first-pass results
     int *cache;           // [9 N] element of each population's previous departure point
                           // (elem | (sx+1)<<28 | (sy+1)<<30), -1 when empty
     int *work;            // [10 N] populations (9 node + direction) left to the exact path,
@@ -178,18 +219,18 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
                         const int b = M.conn[6 * e + k];
-                        fi += Nw[k] * (A)st.post[i * N + b];
-                        gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                        fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
+                        gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
                     }
                 }
             }
         }
         if (src >= 0) {
-            fi = (A)st.post[i * N + src];
-            gi = (A)st.post[(NQ + i) * N + src];
+            fi = pop_in<A>(st.post[i * N + src]);
+            gi = pop_in<A>(st.post[(NQ + i) * N + src]);
         }
-        st.str[i * N + a] = (S)fi;
-        st.str[(NQ + i) * N + a] = (S)gi;
+        pop_put(st.str + (i * N + a), fi);
+        pop_put(st.str + ((NQ + i) * N + a), gi);
         sfm += fi;
         jx += (A)c_cx[i] * fi;
         jy += (A)c_cy[i] * fi;
@@ -258,8 +299,8 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
             if (!(miss >> i & 1)) continue;
             A fi = (far >> i & 1) ? K.finf[i] : fm[i];
             A gi = (far >> i & 1) ? K.ginf[i] : gm[i];
-            st.str[i * N + a] = (S)fi;
-            st.str[(NQ + i) * N + a] = (S)gi;
+            pop_put(st.str + (i * N + a), fi);
+            pop_put(st.str + ((NQ + i) * N + a), gi);
             sfm += fi;
             jx += (A)c_cx[i] * fi;
             jy += (A)c_cy[i] * fi;
@@ -268,14 +309,14 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
     }
     // moments (Sec. IV): rho, u, E, T from the streamed populations
     A rho = K.rho_ref + sfm;
-    A ux = jx / rho, uy = jy / rho;
+    A ux = (K.jx_ref + jx) / rho, uy = (K.jy_ref + jy) / rho;
     A E = (K.E2_ref + sg) / (A(2) * rho);
     A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
     A k3 = A(1) - A(3) * T;
-    st.Qx[a] = (S)(rho * ux * k3 - rho * ux * ux * ux);
-    st.Qy[a] = (S)(rho * uy * k3 - rho * uy * uy * uy);
-    st.mrt[a] = (S)(K.mu / (rho * T));
+    st.Qx[a] = (fld_t<S>)(rho * ux * k3 - rho * ux * ux * ux);
+    st.Qy[a] = (fld_t<S>)(rho * uy * k3 - rho * uy * uy * uy);
+    st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
 }
 
 template <class S, class A>
@@ -380,8 +421,8 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
 #pragma unroll
     for (int i = 0; i < NQ; ++i)
         if (mask >> i & 1u) {
-            st.str[i * N + a] = (S)fm[i];
-            st.str[(NQ + i) * N + a] = (S)gm[i];
+            pop_put(st.str + (i * N + a), fm[i]);
+            pop_put(st.str + ((NQ + i) * N + a), gm[i]);
         }
 }
 
@@ -420,16 +461,16 @@ __device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const Map
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
                     const int b = M.conn[6 * e + k];
-                    fi += Nw[k] * (A)st.post[i * N + b];
-                    gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                    fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
+                    gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
                 }
-                st.str[i * N + a] = (S)fi;
-                st.str[(NQ + i) * N + a] = (S)gi;
+                pop_put(st.str + (i * N + a), fi);
+                pop_put(st.str + ((NQ + i) * N + a), gi);
             } else {
                 const int ck = F.ok ? cone_missing(M, F, a, i) : 0;
                 if (ck == 2) { // far field: free-stream equilibria
-                    st.str[i * N + a] = (S)K.finf[i];
-                    st.str[(NQ + i) * N + a] = (S)K.ginf[i];
+                    pop_put(st.str + (i * N + a), K.finf[i]);
+                    pop_put(st.str + ((NQ + i) * N + a), K.ginf[i]);
                 } else if (ck == 1) {
                     wall |= 1u << i; // the wall condition runs once per node in k_stream_slow
                 } else {
@@ -524,8 +565,8 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         }
         A fi = 0, gi = 0;
         if (src >= 0) {
-            fi = (A)st.post[i * N + src];
-            gi = (A)st.post[(NQ + i) * N + src];
+            fi = pop_in<A>(st.post[i * N + src]);
+            gi = pop_in<A>(st.post[(NQ + i) * N + src]);
         } else if (L.e >= 0) {
             const int e = L.e;
             st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
@@ -535,8 +576,8 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const int b = M.conn[6 * e + k];
-                fi += Nw[k] * (A)st.post[i * N + b];
-                gi += Nw[k] * (A)st.post[(NQ + i) * N + b];
+                fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
+                gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
             }
         } else if (L.kind == 2) {
             fi = K.finf[i];
@@ -545,8 +586,8 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
             return;
         }
-        st.str[i * N + a] = (S)fi;
-        st.str[(NQ + i) * N + a] = (S)gi;
+        pop_put(st.str + (i * N + a), fi);
+        pop_put(st.str + ((NQ + i) * N + a), gi);
     }
 }
 
@@ -595,12 +636,12 @@ __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateD
     A f[NQ], g[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        f[i] = (A)st.str[i * N + a];
-        g[i] = (A)st.str[(NQ + i) * N + a];
+        f[i] = pop_in<A>(st.str[i * N + a]);
+        g[i] = pop_in<A>(st.str[(NQ + i) * N + a]);
     }
     const A sf = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const A jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+    const A jx = K.jx_ref + ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
+    const A jy = K.jy_ref + ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
     const A sg = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
     const A rho = K.rho_ref + sf;
     const A ux = jx / rho, uy = jy / rho;
@@ -608,9 +649,9 @@ __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateD
     const A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
     const A k3 = A(1) - A(3) * T;
-    st.Qx[a] = (S)(rho * ux * k3 - rho * ux * ux * ux);
-    st.Qy[a] = (S)(rho * uy * k3 - rho * uy * uy * uy);
-    st.mrt[a] = (S)(K.mu / (rho * T));
+    st.Qx[a] = (fld_t<S>)(rho * ux * k3 - rho * ux * ux * ux);
+    st.Qy[a] = (fld_t<S>)(rho * uy * k3 - rho * uy * uy * uy);
+    st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
 }
 
 template <class S, class A>
@@ -698,8 +739,8 @@ __device__ __forceinline__ void deriv1_node(const MeshDev &M, const MapStatic &M
         owner_grad_f32(M, a, st.Qy, KX, KY);
         const float dQy = F.A12 * KX + F.A22 * KY; // d_y Q'_yyy
         const float m = (float)st.mrt[a];
-        st.Dx[a] = (S)(m * dQx);
-        st.Dy[a] = (S)(m * dQy);
+        st.Dx[a] = (fld_t<S>)(m * dQx);
+        st.Dy[a] = (fld_t<S>)(m * dQy);
         return;
     }
     const double2 Xa = M.X[a];
@@ -712,8 +753,8 @@ __device__ __forceinline__ void deriv1_node(const MeshDev &M, const MapStatic &M
     owner_grad(M, a, st.Qy, KX, KY);
     double dQy = a12 * KX + a22 * KY; // d_y Q'_yyy
     double m = (double)st.mrt[a];
-    st.Dx[a] = (S)(m * dQx);
-    st.Dy[a] = (S)(m * dQy);
+    st.Dx[a] = (fld_t<S>)(m * dQx);
+    st.Dy[a] = (fld_t<S>)(m * dQy);
 }
 
 template <class S, class A, bool FAST>
@@ -753,20 +794,20 @@ __device__ __forceinline__ void collide_at(const MeshDev &M, const MapStatic &MS
     A f[NQ], g[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        f[i] = (A)st.str[i * N + a];
-        g[i] = (A)st.str[(NQ + i) * N + a];
+        f[i] = pop_in<A>(st.str[i * N + a]);
+        g[i] = pop_in<A>(st.str[(NQ + i) * N + a]);
     }
     A rho, ux, uy, T;
     if (!collide_node(K, f, g, Xx, Xy, rho, ux, uy, T)) atomicOr(err, ERR_NONFINITE);
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        st.post[i * N + a] = (S)f[i];
-        st.post[(NQ + i) * N + a] = (S)g[i];
+        pop_put(st.post + (i * N + a), f[i]);
+        pop_put(st.post + ((NQ + i) * N + a), g[i]);
     }
-    st.rho[a] = (S)rho;
-    st.ux[a] = (S)ux;
-    st.uy[a] = (S)uy;
-    st.T[a] = (S)T;
+    st.rho[a] = (fld_t<S>)rho;
+    st.ux[a] = (fld_t<S>)ux;
+    st.uy[a] = (fld_t<S>)uy;
+    st.T[a] = (fld_t<S>)T;
 }
 
 template <class S, class A, bool FAST>

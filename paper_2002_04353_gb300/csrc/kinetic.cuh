@@ -13,7 +13,9 @@ namespace alelb {
 
 template <class A> struct KinParams {
     A Cv, Cp, mu, Pr;
-    A rho_ref, T_ref, E2_ref;       // sum f_ref, temperature of the reference, sum g_ref
+    // moments of the reference populations: sum f_ref, sum c f_ref,
+    // sum c c f_ref, sum g_ref
+    A rho_ref, jx_ref, jy_ref, Pxx_ref, Pxy_ref, Pyy_ref, E2_ref;
     A fref[NQ], gref[NQ];           // reference populations (zero in FP64 mode)
     A finf[NQ], ginf[NQ];           // far-field populations minus the reference
     int flags;
@@ -115,8 +117,8 @@ __device__ __forceinline__ bool collide_node(const KinParams<A> &K, A f[NQ], A g
 #pragma unroll
     for (int i = 0; i < NQ; ++i) sg += g[i];
     sf = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+    jx = K.jx_ref + ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
+    jy = K.jy_ref + ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
     dxx = f[1] + f[3] + f[5] + f[6] + f[7] + f[8];
     dyy = f[2] + f[4] + f[5] + f[6] + f[7] + f[8];
     dxy = (f[5] + f[7]) - (f[6] + f[8]);
@@ -130,8 +132,8 @@ __device__ __forceinline__ bool collide_node(const KinParams<A> &K, A f[NQ], A g
     T_o = T;
     if (!(rho > A(0)) || !(T > A(0))) return false;
     if (K.flags & FLAG_COLLIDE_OFF) return true;
-    // P_ab - P^eq_ab from deviations: the reference carries rho_ref T_ref I
-    A Pxx = K.rho_ref * K.T_ref + dxx, Pyy = K.rho_ref * K.T_ref + dyy, Pxy = dxy;
+    // P_ab - P^eq_ab from deviations plus the reference's own P_ab
+    A Pxx = K.Pxx_ref + dxx, Pyy = K.Pyy_ref + dyy, Pxy = K.Pxy_ref + dxy;
     A dPxx = Pxx - (rho * ux * ux + rho * T);
     A dPxy = Pxy - rho * ux * uy;
     A dPyy = Pyy - (rho * uy * uy + rho * T);

@@ -520,12 +520,14 @@ cudaError_t fwd_bwd(alelb_mlp *m, const float *feat, const int16_t *slot, const 
 
 namespace alelb {
 
-// Proposals for the solver's current work list (FP32-deviation step).
+// Proposals for the solver's current work list (deviation-form step).
 cudaError_t mlp_propose(alelb_solver *s, const MapScalarsF &sf)
 {
     alelb_mesh *m = s->mesh;
-    k_propose<float><<<2 * s->n_sm, PRED_WARPS * 32, 0, s->stream>>>(m->dev, m->mst, sf, s->sf, s->mlp->d_h,
-                                                                     s->flags, s->d_prop, s->d_stats + 2);
+    with_state(s, [&](auto &st, auto &) {
+        k_propose<<<2 * s->n_sm, PRED_WARPS * 32, 0, s->stream>>>(m->dev, m->mst, sf, st, s->mlp->d_h, s->flags,
+                                                                   s->d_prop, s->d_stats + 2);
+    });
     return cudaGetLastError();
 }
 
@@ -565,6 +567,7 @@ extern "C" alelb_status alelb_mlp_create(const float *params, uint64_t seed, ale
     if (st == cudaSuccess) st = cudaMemset(m->d_m, 0, MLP_NP * sizeof(float));
     if (st == cudaSuccess) st = cudaMemset(m->d_v, 0, MLP_NP * sizeof(float));
     if (st == cudaSuccess) st = cudaMemset(m->d_g, 0, MLP_NP * sizeof(float));
+    if (st == cudaSuccess) st = cudaDeviceSynchronize(); // legacy-stream uploads before m->stream work
     if (st == cudaSuccess) st = refresh_half(m);
     if (st == cudaSuccess) st = cudaStreamSynchronize(m->stream);
     if (st != cudaSuccess) return mfail(m, st, "mlp_create");
@@ -688,8 +691,8 @@ extern "C" alelb_status alelb_samples(alelb_solver *s, double t, float *feat, in
 extern "C" alelb_status alelb_solver_set_mlp(alelb_solver *s, alelb_mlp *m)
 {
     if (!s) return ALELB_ERR_ARG;
-    if (m && s->prec != ALELB_PREC_FP32_DEV) {
-        s->err = "the learned proposal serves the FP32-deviation propagation only";
+    if (m && s->prec == ALELB_PREC_FP64) {
+        s->err = "the learned proposal serves the deviation-form propagation only";
         return ALELB_ERR_ARG;
     }
     if (m && !s->d_prop) {

@@ -257,3 +257,91 @@ def test_fast_path_element_choices_bitwise(name):
     eg, kg = s.locate(t + 1.0, use_cache=True)
     assert np.array_equal(eo, eg), f"{name}: {np.sum(eo != eg)} fast-path element choices differ"
     assert np.array_equal(ko, kg)
+
+
+# ---------------------------------------------------------------------------
+# 16-bit population storage (BF16 and scaled FP16 deviations, FP32 arithmetic)
+# ---------------------------------------------------------------------------
+
+# Half a unit in the last place of the stored significand: bfloat16 keeps 8
+# significant bits, binary16 11.
+U16 = {alelb.PREC_BF16_DEV: 2.0 ** -8, alelb.PREC_FP16_DEV: 2.0 ** -11}
+PREC16 = [alelb.PREC_BF16_DEV, alelb.PREC_FP16_DEV]
+
+
+def _compare16(o, s, prec, flow, n, what):
+    """First-order model of the storage error: each step rounds every stored
+    deviation twice (streamed and post-collision values), each rounding at
+    most U16 times the deviation from the far-field equilibria, which the
+    16-bit forms store.  The moments take sums over 9 populations and a
+    division by rho, so a field moves by at most 2 n U16 D / rho_min with
+    D = max over nodes of sum_i (|f_i - f_inf,i| + |g_i - g_inf,i|); the
+    temperature carries one more factor 1/Cv + |u|^2.  The bound drops the
+    rounding's propagation through later interpolations (P2 weights sum to
+    one) and adds the FP32 bound."""
+    st = o.state()
+    fi = O.feq(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf)
+    gi = O.geq(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf, CV)
+    D = (np.abs(st["f"] - fi[:, None]).sum(0) + np.abs(st["g"] - gi[:, None]).sum(0)).max()
+    rmin = st["rho"].min()
+    base = 2 * n * U16[prec] * D / rmin
+    umax = max(np.abs(st["ux"]).max(), np.abs(st["uy"]).max())
+    mo = s.moments()
+    errs = {}
+    for k in ("rho", "ux", "uy", "T"):
+        scale = 1.0 if k in ("rho", "T") else umax
+        tol = base * (1.0 / CV + umax ** 2 + 1.0 if k == "T" else 1.0) / scale + TOL32
+        err = np.abs(mo[k] - st[k]).max() / scale
+        errs[k] = err
+        assert err < tol, f"{what}: {k} err {err:.2e} > {tol:.2e} (D {D:.2e})"
+    return errs
+
+
+@pytest.mark.parametrize("prec", PREC16)
+def test_16bit_box_matches_fp64_oracle(prec):
+    case = I.uniform_flow_case(n=16, L=32.0, period_steps=50.0)
+    st = _eq_state(case.mesh, case.flow, 0.01, seed=6)
+    o, m, s = _pair(case.mesh, case.motion, case.flow, prec=prec, state=st)
+    o.step(20)
+    s.lb_step(20)
+    _compare16(o, s, prec, case.flow, 20, "16-bit box")
+
+
+@pytest.mark.parametrize("prec", PREC16)
+def test_16bit_airfoil_matches_fp64_oracle(prec):
+    mesh, motion = LOC_CASES["omesh_pitch"]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o, m, s = _pair(mesh, motion, flow, prec=prec)
+    o.step(8)
+    s.lb_step(8)
+    _compare16(o, s, prec, flow, 8, "16-bit airfoil")
+
+
+@pytest.mark.parametrize("prec", PREC16)
+def test_16bit_uniform_flow_preserved(prec):
+    """Uniform flow on the deforming box: the stored deviations from the
+    far-field equilibria stay at the FP32 rounding of the equilibria."""
+    case = I.uniform_flow_case(n=16, L=32.0, period_steps=50.0)
+    s = alelb.Solver(alelb.Mesh(case.mesh, case.motion), case.flow, prec)
+    s.lb_step(50)
+    mo = s.moments()
+    u = case.flow.u_inf
+    assert np.abs(mo["rho"] - case.flow.rho_inf).max() < 1e-6
+    assert np.abs(mo["T"] - case.flow.T_inf).max() < 1e-6
+    assert max(np.abs(mo["ux"] - u[0]).max(), np.abs(mo["uy"] - u[1]).max()) < 1e-6
+
+
+@pytest.mark.parametrize("prec", PREC16)
+def test_16bit_element_choices_and_info(prec):
+    """Storage does not enter the departure points: the deviation forms take
+    the same element decisions, and info() reports 2-byte values."""
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o = O.Oracle(mesh, motion, flow)
+    s = alelb.Solver(alelb.Mesh(mesh, motion), flow, prec)
+    s.lb_step(4)
+    assert s.info()["pop_bytes"] == 2
+    t, _ = s.time()
+    eo, ko = o.locate(t + 1.0)
+    eg, kg = s.locate(t + 1.0, use_cache=True)
+    assert np.array_equal(eo, eg) and np.array_equal(ko, kg)
