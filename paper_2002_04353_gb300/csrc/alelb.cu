@@ -75,7 +75,8 @@ template <class S> void put_state(DevBuf &b, StateDev<S> &s, int N, cudaError_t 
     s.work = b.alloc<int>((size_t)10 * N, st);
     s.wcount = b.alloc<unsigned>(NQ + 1, st);
     if (st == cudaSuccess) st = cudaMemset(s.wcount, 0, (NQ + 1) * sizeof(unsigned));
-    s.wmask = b.alloc<unsigned short>(N, st);
+    s.wmask = b.alloc<unsigned>(N, st);
+    if (st == cudaSuccess) st = cudaMemset(s.wmask, 0, (size_t)N * sizeof(unsigned));
 }
 
 
@@ -131,6 +132,9 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.Xf = B.put(T.Xf, st);
     D.v0f = B.put(T.v0f, st);
     D.evf = B.put(T.evf, st);
+    D.nb_ptr = B.put(T.nb_ptr, st);
+    D.nb = B.put(T.nb, st);
+    D.nbf = B.put(T.nbf, st);
     m->d_wedges = B.put(T.wedges, st);
     m->nw = (int)T.wedges.size();
     m->mst = T.host_map();
@@ -358,12 +362,21 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                                                                    s->d_stats);
             break;
         case KT_FAST:
-            k_stream_fast<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sf, K, st);
+            k_stream_fast<S, A><<<dim3((N + 127) / 128, NQ / FAST_G), 128, 0, s->stream>>>(m->dev, m->mst, sf, K,
+                                                                                         st);
             break;
-        case KT_SLOW:
-            k_stream_slow<S, A><<<4 * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st, s->d_err,
-                                                                    s->d_stats, s->mlp ? s->d_prop : nullptr);
+        case KT_SLOW: {
+            // every block resident at once: the list is spread over all
+            // blocks, and a second wave would wait for the first one's walks
+            static const int per_sm = [] {
+                int v = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_stream_slow<S, A>, 128, 0);
+                return v > 0 ? v : 1;
+            }();
+            k_stream_slow<S, A><<<per_sm * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st, s->d_err,
+                                                                         s->d_stats, s->mlp ? s->d_prop : nullptr);
             break;
+        }
         case KT_PROPOSE:
             mlp_propose(s, sf);
             break;

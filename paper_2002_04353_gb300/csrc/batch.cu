@@ -98,9 +98,8 @@ __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__
     sh.load(cases, nullptr, sf, c);
     __syncthreads();
     const CaseDev<S, A> &C = sh.C();
-    const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
-    const unsigned slow = a < C.M.N ? stream_fast_node(C.M, C.MS, sh.SF(), C.K, C.st, a) : 0u;
-    append_work(C.st, a, C.M.N, slow);
+    stream_fast_group<BATCH_FAST_G>(C.M, C.MS, sh.SF(), C.K, C.st,
+                                    (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x);
 }
 
 // The exact path over the work lists of all cases as one list, numbered
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
     }
     __syncthreads();
     const unsigned total = pre[nseg];
-    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+    for (unsigned w = spread_first(); w < total; w += spread_stride()) {
         int lo = 0, hi = nseg - 1; // last segment with pre <= w
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -218,11 +217,22 @@ template <class S, class A>
 __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
 {
     const int c = threadIdx.x;
-    if (c < B)
-        for (int i = 0; i <= NQ; ++i) cases[c].st.wcount[i] = 0u;
+    if (c < B) {
+        const StateDev<S> &st = cases[c].st;
+        for (unsigned k = 0; k < st.wcount[NQ]; ++k) st.wmask[st.work[(size_t)NQ * cases[c].M.N + k]] = 0u;
+        for (int i = 0; i <= NQ; ++i) st.wcount[i] = 0u;
+    }
 }
 
 int bs_index(int bs) { return bs == 64 ? 0 : bs == 128 ? 1 : 2; }
+
+// Blocks of the exact-path kernel resident per SM at block size bs.
+template <class S, class A> int slow_resident_t(int bs)
+{
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kb_slow<S, A>, bs, 0);
+    return v > 0 ? v : 1;
+}
 
 } // namespace
 
@@ -257,6 +267,13 @@ struct alelb_batch {
     double ms_acc[KT_N] = {};
     int64_t n_acc[KT_N] = {};
 };
+
+namespace {
+int slow_resident(const alelb_batch *b, int bs)
+{
+    return b->prec == ALELB_PREC_FP32_DEV ? slow_resident_t<float, float>(bs) : slow_resident_t<double, double>(bs);
+}
+} // namespace
 
 namespace {
 
@@ -332,7 +349,7 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count)
         kb_stream<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, count);
         break;
     case KT_FAST:
-        kb_fast<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B, sf);
+        kb_fast<S, A><<<dim3(tiles, NQ / BATCH_FAST_G), bs, 0, b->stream>>>(cases, off, B, sf);
         break;
     case KT_SLOW:
         kb_slow<S, A><<<grid, bs, 0, b->stream>>>(cases, B, sc, sf, count);
@@ -488,7 +505,7 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     b->B = B;
     b->prec = cases[0]->prec;
     b->n_sm = cases[0]->n_sm;
-    b->slow_grid = 4 * b->n_sm;
+    b->slow_grid = slow_resident(b, 128) * b->n_sm;
     cudaError_t st = cudaSuccess;
     if (stream) {
         b->stream = (cudaStream_t)stream;
@@ -629,6 +646,7 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
             const int bs = 64 << bsq;
             if (kt == KT_SLOW) {
                 for (int gm = 1; gm <= 16; gm *= 2) cands.push_back({bs, gm * b->n_sm});
+                cands.push_back({bs, slow_resident(b, bs) * b->n_sm}); // one wave
             } else {
                 cands.push_back({bs, 0});
             }

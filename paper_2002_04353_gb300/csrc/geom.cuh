@@ -14,6 +14,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 namespace alelb {
 
@@ -309,9 +310,11 @@ ALELB_HD __forceinline__ void departure(double a11, double a12, double a21, doub
 // Exact orientation sign of (a, b, c): sign of (a-c) x (b-c).
 // Stage 1: the FP64 determinant with the certified error bound of Shewchuk
 // (1997), errbound = (3 + 16 eps) eps (|l| + |r|), eps = 2^-53.
-// Stage 2 (rare): the determinant expanded into six products, each split
-// exactly into two doubles with an FMA, and the twelve terms summed exactly
-// as a non-overlapping expansion (Two-Sum / Grow-Expansion).
+// Stage 2: exact integer evaluation (orient_int below) when the operands
+// of each coordinate difference have nearby exponents.
+// Stage 3 (otherwise): the determinant expanded into six products, each
+// split exactly into two doubles with an FMA, and the twelve terms summed
+// exactly as a non-overlapping expansion (Two-Sum / Grow-Expansion).
 // ---------------------------------------------------------------------------
 static ALELB_HD __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
                                          double cy)
@@ -339,6 +342,96 @@ static ALELB_HD __noinline__ int orient_exact(double ax, double ay, double bx, d
     return e[m - 1] > 0.0 ? 1 : -1;
 }
 
+// ---------------------------------------------------------------------------
+// Stage 2 of the exact orientation, in integers: the exact sign from the
+// binary representations.  A
+// finite double is m 2^k with |m| < 2^53.  When the two operands of each
+// difference have exponents at most 9 apart, the difference is D 2^K with
+// |D| < 2^63 exactly; each product is then an exact 128-bit integer times a
+// power of two, and the two products are compared exactly (a term whose
+// leading bit lies above the other's after alignment decides alone).
+// Returns 2 when the exponents are too far apart (stage 3 decides).  Only
+// integer arithmetic: FP64 throughput on this GPU is a small fraction of
+// its integer throughput.
+// ---------------------------------------------------------------------------
+ALELB_HD __forceinline__ void dsplit(double x, long long &m, int &k)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long b;
+    std::memcpy(&b, &x, sizeof b);
+#endif
+    const int ex = (int)((b >> 52) & 0x7ffu);
+    unsigned long long f = b & ((1ull << 52) - 1ull);
+    if (ex) {
+        f |= 1ull << 52;
+        k = ex - 1075;
+    } else {
+        k = -1074;
+    }
+    m = (b >> 63) ? -(long long)f : (long long)f;
+}
+
+ALELB_HD __forceinline__ bool ddiff_int(double a, double c, long long &D, int &K)
+{
+    long long ma, mc;
+    int ka, kc;
+    dsplit(a, ma, ka);
+    dsplit(c, mc, kc);
+    if (ma == 0) {
+        D = -mc;
+        K = kc;
+        return true;
+    }
+    if (mc == 0) {
+        D = ma;
+        K = ka;
+        return true;
+    }
+    const int km = ka < kc ? ka : kc;
+    if (ka - km > 9 || kc - km > 9) return false;
+    D = ma * (1ll << (ka - km)) - mc * (1ll << (kc - km));
+    K = km;
+    return true;
+}
+
+ALELB_HD __forceinline__ int bitlen128(__int128 v)
+{
+    const unsigned __int128 u = v < 0 ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+#ifdef __CUDA_ARCH__
+    return hi ? 128 - __clzll((long long)hi) : (lo ? 64 - __clzll((long long)lo) : 0);
+#else
+    return hi ? 128 - __builtin_clzll(hi) : (lo ? 64 - __builtin_clzll(lo) : 0);
+#endif
+}
+
+static ALELB_HD __noinline__ int orient_int(double ax, double ay, double bx, double by, double cx,
+                                            double cy)
+{
+    long long d1, d2, d3, d4;
+    int k1, k2, k3, k4;
+    if (!ddiff_int(ax, cx, d1, k1) || !ddiff_int(by, cy, d2, k2) || !ddiff_int(ay, cy, d3, k3) ||
+        !ddiff_int(bx, cx, d4, k4))
+        return 2;
+    __int128 P = (__int128)d1 * d2, R = (__int128)d3 * d4; // det = P 2^KP - R 2^KR
+    const int KP = k1 + k2, KR = k3 + k4;
+    if (P == 0) return R > 0 ? -1 : (R < 0 ? 1 : 0);
+    if (R == 0) return P > 0 ? 1 : -1;
+    const int bp = bitlen128(P), br = bitlen128(R);
+    if (KP >= KR) {
+        const int sh = KP - KR;
+        if (bp + sh - 1 >= br) return P > 0 ? 1 : -1;
+        P *= (__int128)1 << sh;
+    } else {
+        const int sh = KR - KP;
+        if (br + sh - 1 >= bp) return R > 0 ? -1 : 1;
+        R *= (__int128)1 << sh;
+    }
+    return P > R ? 1 : (P < R ? -1 : 0);
+}
+
 ALELB_HD __forceinline__ int orient(double ax, double ay, double bx, double by, double cx,
                                     double cy)
 {
@@ -352,6 +445,8 @@ ALELB_HD __forceinline__ int orient(double ax, double ay, double bx, double by, 
     // fl(a - b) is zero only when a == b: a zero difference is exact, so
     // when each product has a zero factor the determinant is exactly 0
     if ((acx == 0.0 || bcy == 0.0) && (acy == 0.0 || bcx == 0.0)) return 0;
+    const int si = orient_int(ax, ay, bx, by, cx, cy);
+    if (si != 2) return si;
     return orient_exact(ax, ay, bx, by, cx, cy);
 }
 
@@ -377,7 +472,8 @@ struct MeshDev {
     const uint8_t *bkind;  // [N] boundary kind of the node (0 interior)
     const uint8_t *vzero;  // [N] 1: mesh velocity exactly zero at all times
     const float4 *cone;    // [N] boundary node: outgoing, incoming boundary edge (domain on the left)
-    const uint8_t *conek;  // [N] kind of those edges, 0 when the node has no such pair
+    const uint8_t *conek;  // [N] kind of those edges (0 when the node has no such pair), | 4 at a
+                           // convex corner of the domain, | 8 at a reflex one
     const int *wall_idx;   // [N] index into the wall tables or -1
     const int *probe_e;    // [NW]
     const double2 *probe_xi; // [NW]
@@ -388,7 +484,15 @@ struct MeshDev {
     const float4 *Xf;      // [N] node coordinates split hi + lo in FP32 (xh, yh, xl, yl)
     const float4 *v0f;     // [E] first frame vertex split hi + lo in FP32
     const float4 *evf;     // [3E] all frame vertices split hi + lo in FP32
+    const int *nb_ptr;     // [N + 1] wall and far-field edges within NEAR_R of each node
+    const float4 *nb;      // (P - X_a, Q - X_a) in FP32, the domain on the left of P -> Q
+    const uint8_t *nbf;    // kind | 4 when the node lies on the edge
 };
+
+// Radius of the per-node lists of nearby boundary edges (lattice units).
+// Every departure segment shorter than it lies in the disk that the list
+// covers.
+constexpr float NEAR_R = 2.5f;
 
 struct Loc {
     int e;      // element (>= 0), or -1 missing, -2 the node itself
@@ -463,6 +567,38 @@ struct Pred64 {
 // treated as passing to the vertex's right.  Ties (p on an edge or vertex)
 // go to the containing element of larger computational area, then lower
 // original id.  P supplies the orientation signs, always exact.
+// The location of a departure point in the closed element e (frame shift
+// sx, sy), given its orientations against the three edges: strictly inside
+// e; on one edge, then the element of lower rank (larger area, then lower
+// original id) of the two that share it; on a vertex, which is then named.
+ALELB_HD __forceinline__ Loc finish_loc(const MeshDev &M, int e, int sx, int sy, int o0, int o1, int o2)
+{
+    Loc r;
+    r.kind = 0;
+    r.vnode = -1;
+    int nz = (o0 == 0) + (o1 == 0) + (o2 == 0);
+    if (nz == 1) {
+        int kz = o0 == 0 ? 0 : (o1 == 0 ? 1 : 2);
+        uint32_t inf = (M.einfo[e] >> (8 * kz)) & 255u;
+        if ((inf & 3) == 0) {
+            int e2 = M.nbr[3 * e + kz];
+            if (M.rank[e2] < M.rank[e]) {
+                e = e2;
+                sx += (int)((inf >> 4) & 3) - 1;
+                sy += (int)((inf >> 6) & 3) - 1;
+            }
+        }
+    } else if (nz >= 2) {
+        // p is the vertex shared by the two zero edges
+        int vl = (o0 == 0 && o1 == 0) ? 1 : ((o1 == 0 && o2 == 0) ? 2 : 0);
+        r.vnode = M.conn[6 * e + vl];
+    }
+    r.e = e;
+    r.sx = sx;
+    r.sy = sy;
+    return r;
+}
+
 template <class P> ALELB_HD __forceinline__ Loc walk_t(const MeshDev &M, P &pr, int a, int *err)
 {
     Loc r;
@@ -555,27 +691,7 @@ template <class P> ALELB_HD __forceinline__ Loc walk_t(const MeshDev &M, P &pr, 
             return r;
         }
     }
-    int nz = (o0 == 0) + (o1 == 0) + (o2 == 0);
-    if (nz == 1) {
-        int kz = o0 == 0 ? 0 : (o1 == 0 ? 1 : 2);
-        uint32_t inf = (M.einfo[e] >> (8 * kz)) & 255u;
-        if ((inf & 3) == 0) {
-            int e2 = M.nbr[3 * e + kz];
-            if (M.rank[e2] < M.rank[e]) {
-                e = e2;
-                sx += (int)((inf >> 4) & 3) - 1;
-                sy += (int)((inf >> 6) & 3) - 1;
-            }
-        }
-    } else if (nz >= 2) {
-        // p is the vertex shared by the two zero edges
-        int vl = (o0 == 0 && o1 == 0) ? 1 : ((o1 == 0 && o2 == 0) ? 2 : 0);
-        r.vnode = M.conn[6 * e + vl];
-    }
-    r.e = e;
-    r.sx = sx;
-    r.sy = sy;
-    return r;
+    return finish_loc(M, e, sx, sy, o0, o1, o2);
 }
 
 static ALELB_HD __noinline__ Loc walk(const MeshDev M, int a, double Xa, double Ya, double px, double py,
@@ -663,6 +779,92 @@ ALELB_HD __forceinline__ bool strictly_inside_f32(const MeshDev &M, int e, int s
     return o0 > bound && o1 > bound && o2 > bound;
 }
 
+// Certified FP32 sign of orient(A, B, C) = (A - C) x (B - C) from
+// approximations of A, B, C with per-coordinate error bounds ea, eb, ec:
+// +1 or -1 when certain, 0 when the exact predicate must decide.
+ALELB_HD __forceinline__ int orient3_f32(float ax, float ay, float ea, float bx, float by, float eb,
+                                         float cx, float cy, float ec)
+{
+    const float u = 5.9604644775390625e-08f;
+    const float d1x = ax - cx, d1y = ay - cy, d2x = bx - cx, d2y = by - cy;
+    const float D1 = fmaxf(fabsf(d1x), fabsf(d1y)), D2 = fmaxf(fabsf(d2x), fabsf(d2y));
+    const float e1 = ea + ec + u * D1, e2 = eb + ec + u * D2;
+    const float o = d1x * d2y - d1y * d2x;
+    const float bound = 4.0f * (D1 * e2 + D2 * e1 + e1 * e2) + 8.0f * u * D1 * D2;
+    if (o > bound) return 1;
+    if (o < -bound) return -1;
+    return 0;
+}
+
+// Error bound of a listed boundary-edge endpoint (relative to the node): the
+// FP32 rounding of the FP64 difference, plus 2^-25 for that difference's own
+// rounding.
+ALELB_HD __forceinline__ float nb_err(float x, float y)
+{
+    return 5.9604644775390625e-08f * fmaxf(fabsf(x), fabsf(y)) + 2.98023223876953125e-08f;
+}
+
+// Certified: the segment from node a to its departure point a + (bx, by)
+// (error eb per component) meets no wall or far-field edge, except at the
+// node itself on the edges through the node, from where it enters the
+// domain: strictly left of every such edge's line, or, at a reflex corner
+// of the domain (the union of the two left half-planes), of one of them (a
+// straight segment meets the line of an edge through its start only
+// there).  The segment lies in the disk of the node's edge list (caller:
+// length + eb < NEAR_R).  Another edge is passed when both ends of the
+// segment lie strictly on one side of its line, or both ends of the edge
+// strictly on one side of the segment's line.
+ALELB_HD __forceinline__ bool seg_clear(const MeshDev &M, int a, float bx, float by, float eb)
+{
+    const int beg = M.nb_ptr[a], end = M.nb_ptr[a + 1];
+    int inc = 0, left = 0;
+    for (int k = beg; k < end; ++k) {
+        const float4 E = M.nb[k];
+        const float eP = nb_err(E.x, E.y), eQ = nb_err(E.z, E.w);
+        const int sB = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, bx, by, eb);
+        if (M.nbf[k] & 4) { // the node lies on this edge
+            ++inc;
+            left += sB > 0;
+            continue;
+        }
+        const int sA = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, 0.0f, 0.0f, 0.0f);
+        if (sA != 0 && sA == sB) continue;
+        const int sP = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.x, E.y, eP);
+        const int sQ = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.z, E.w, eQ);
+        if (sP != 0 && sP == sQ) continue;
+        return false;
+    }
+    return left == inc || (left > 0 && inc == 2 && (M.conek[a] & 8));
+}
+
+// Certified: the segment from node a to a + (bx, by) crosses a listed edge
+// not through the node properly (strictly opposite sides both ways), so
+// some of its points lie outside the mesh and the population is missing.
+// Returns the boundary kind when every listed edge has the same kind (the
+// first boundary the segment meets is then of that kind), else 0.  Caller:
+// length + eb < NEAR_R.
+ALELB_HD __forceinline__ int cross_missing(const MeshDev &M, int a, float bx, float by, float eb)
+{
+    const int beg = M.nb_ptr[a], end = M.nb_ptr[a + 1];
+    int kind = 0;
+    bool crossed = false;
+    for (int k = beg; k < end; ++k) {
+        const int f = M.nbf[k];
+        if (kind && (f & 3) != kind) return 0;
+        kind = f & 3;
+        if (crossed || (f & 4)) continue;
+        const float4 E = M.nb[k];
+        const float eP = nb_err(E.x, E.y), eQ = nb_err(E.z, E.w);
+        const int sA = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, 0.0f, 0.0f, 0.0f);
+        const int sB = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, bx, by, eb);
+        if (sA * sB >= 0) continue;
+        const int sP = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.x, E.y, eP);
+        const int sQ = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.z, E.w, eQ);
+        crossed = sP * sQ < 0;
+    }
+    return crossed ? kind : 0;
+}
+
 // Bound of the FP32 transformed velocities c^_i against the FP64 canonical
 // ones, from the FP32 metrics themselves (u = 2^-24):
 //   entries of g:   eps_g   = 16u (1 + G),  G = max |g_ij|
@@ -748,6 +950,8 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
 #pragma unroll
     for (int k = 0; k < 6; ++k)
         if (cn[k] == a) l = k;
+    // near a boundary the exact path decides (with the segment certificate
+    // against the node's nearby boundary edges)
     if (!(len + F.eps_c < bdist) && l < 0) return false;
     const float4 J = M.ejf[2 * e + 1];
     if (l >= 0) {
@@ -807,14 +1011,16 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
 // Certified FP32 test that population i of boundary node a is missing
 // because its departure direction -c^ points strictly into the exterior at
 // the node: strictly to the right of both boundary edges through the node
-// (the domain lies on their left).  The points of the segment next to the
+// (the domain lies on their left), or, at a convex corner of the domain,
+// strictly to the right of either.  The points of the segment next to the
 // node then lie outside the closed mesh.  Returns the boundary kind, or 0
 // when not certain.  Errors: eps_c (+ 2^-25) per component of -c^, the FP32
 // rounding of the edge vectors and of the cross products.
 ALELB_HD __forceinline__ int cone_missing(const MeshDev &M, const FastMap &F, int a, int i)
 {
-    const int k = M.conek[a];
-    if (!k) return 0;
+    const int ck = M.conek[a];
+    if (!ck) return 0;
+    const int k = ck & 3;
     const float u = 5.9604644775390625e-08f;
     const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
     const float dx = -(F.A11 * cx + F.A12 * cy - F.W1);
@@ -825,25 +1031,26 @@ ALELB_HD __forceinline__ int cone_missing(const MeshDev &M, const FastMap &F, in
     const float s1 = c.x * dy - c.y * dx, s2 = c.z * dy - c.w * dx;
     const float b1 = 2.0f * (3.0f * u * (fabsf(c.x * dy) + fabsf(c.y * dx)) + (fabsf(c.x) + fabsf(c.y)) * eq);
     const float b2 = 2.0f * (3.0f * u * (fabsf(c.z * dy) + fabsf(c.w * dx)) + (fabsf(c.z) + fabsf(c.w)) * eq);
+    if (ck & 4) return (s1 < -b1 || s2 < -b2) ? k : 0; // convex corner: either edge
     return (s1 < -b1 && s2 < -b2) ? k : 0;
 }
 
-// Certified FP32 sign of orient(A, B, C) = (A - C) x (B - C) from
-// approximations of A, B, C with per-coordinate error bounds ea, eb, ec:
-// +1 or -1 when certain, 0 when the exact predicate must decide.
-ALELB_HD __forceinline__ int orient3_f32(float ax, float ay, float ea, float bx, float by, float eb,
-                                         float cx, float cy, float ec)
+// A population certified missing without the walk: the exterior cone at a
+// boundary node, else a certified crossing of one of the node's nearby
+// boundary edges.  Returns the boundary kind, or 0 when not certain.
+ALELB_HD __forceinline__ int certified_missing(const MeshDev &M, const FastMap &F, int a, int i)
 {
-    const float u = 5.9604644775390625e-08f;
-    const float d1x = ax - cx, d1y = ay - cy, d2x = bx - cx, d2y = by - cy;
-    const float D1 = fmaxf(fabsf(d1x), fabsf(d1y)), D2 = fmaxf(fabsf(d2x), fabsf(d2y));
-    const float e1 = ea + ec + u * D1, e2 = eb + ec + u * D2;
-    const float o = d1x * d2y - d1y * d2x;
-    const float bound = 4.0f * (D1 * e2 + D2 * e1 + e1 * e2) + 8.0f * u * D1 * D2;
-    if (o > bound) return 1;
-    if (o < -bound) return -1;
-    return 0;
+    const int ck = cone_missing(M, F, a, i);
+    if (ck || M.nb_ptr[a] == M.nb_ptr[a + 1]) return ck;
+    const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
+    const float chx = F.A11 * cx + F.A12 * cy - F.W1;
+    const float chy = F.A21 * cx + F.A22 * cy - F.W2;
+    const float len = sqrtf(chx * chx + chy * chy);
+    const float eb = F.eps_c + 2.98023223876953125e-08f;
+    if (!(len > 4.0f * F.eps_c) || !(len + eb < NEAR_R)) return 0;
+    return cross_missing(M, a, -chx, -chy, eb);
 }
+
 
 // Orientation provider of the walk in FP32: every point relative to the
 // node, the departure point from the FP32 c^ (bound eps_c), element
@@ -956,10 +1163,18 @@ struct Pred32 {
 // the FP32 map is usable and c^ is clearly nonzero, else on FP64 ones.
 // Returns the walk's Loc; for an interior element, q = p - v0 in FP32.
 // src >= 0: the population takes node src's value as is.
+// hint: the population's element cache entry.  When it names an unshifted
+// element and the segment provably stays in the mesh (the element is one
+// of the node's own, or the segment is shorter than the boundary distance,
+// or it passes the nearby boundary edges), the three exact orientations
+// against that element decide: a departure point in the closed element is
+// located there by the walk too, with the same rule for edges and vertices
+// (a departure point near an element edge, where the FP32 margins fail, no
+// longer needs the scan of the node's fan).
 ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                                          const MapScalars &sc, const FastMap &F, float4 Xf, int a,
                                          int i, int literal, float &qx, float &qy, int &src,
-                                         int *err)
+                                         int *err, int hint = -1)
 {
     const double2 Xa = M.X[a];
     src = -1;
@@ -988,7 +1203,31 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
             pr.wload = false;
             pr.Xa = Xa.x;
             pr.Ya = Xa.y;
-            L = walk_t(M, pr, a, err);
+            bool have = false;
+            if (hint >= 0 && (hint >> 28) == 5) {
+                const int ce = hint & 0x0fffffff;
+                bool own = false;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) own |= M.conn[6 * ce + k] == a;
+                const float len = sqrtf(chx * chx + chy * chy);
+                const float eb = F.eps_c + 2.98023223876953125e-08f;
+                if (own || len + F.eps_c < M.bdist[a] ||
+                    (len + eb < NEAR_R && seg_clear(M, a, -chx, -chy, eb))) {
+                    pr.load(ce, 0, 0);
+                    const int o0 = pr.vvp(0, 1);
+                    if (o0 >= 0) {
+                        const int o1 = pr.vvp(1, 2);
+                        if (o1 >= 0) {
+                            const int o2 = pr.vvp(2, 0);
+                            if (o2 >= 0) {
+                                L = finish_loc(M, ce, 0, 0, o0, o1, o2);
+                                have = true;
+                            }
+                        }
+                    }
+                }
+            }
+            if (!have) L = walk_t(M, pr, a, err);
             if (L.e >= 0 && L.vnode < 0) {
                 const float4 v = M.evf[3 * L.e];
                 float x0 = (v.x - Xf.x) + (v.z - Xf.z), y0 = (v.y - Xf.y) + (v.w - Xf.w);
@@ -1059,8 +1298,16 @@ ALELB_HD inline void mixed_locate_node(const MeshDev &M, const MapStatic &MS,
             kind9[i] = (int8_t)ck;
             continue;
         }
+        // the exact path: a certified crossing of a nearby boundary edge,
+        // else the decision of slow_decide
+        const int cx = F.ok ? certified_missing(M, F, a, i) : 0;
+        if (cx) {
+            elem9[i] = -1;
+            kind9[i] = (int8_t)cx;
+            continue;
+        }
         int src;
-        const Loc L = slow_decide(M, MS, sc, F, Xf, a, i, 0, qx, qy, src, err);
+        const Loc L = slow_decide(M, MS, sc, F, Xf, a, i, 0, qx, qy, src, err, cache[(size_t)i * M.N + a]);
         if (L.e == -2 && src == a && L.vnode < 0) {
             elem9[i] = -2;
             kind9[i] = 0;

@@ -116,3 +116,15 @@ extern "C" int alelb_hostcheck_fast(const alelb_mesh_desc *d, double t_prev, dou
     }
     return e ? ALELB_ERR_LOCATE : ALELB_OK;
 }
+
+// The library's exact orientation predicate on the host: out[k] = sign of
+// orient(a, b, c) for the k-th six doubles (ax, ay, bx, by, cx, cy); stage[k]
+// = the integer stage's answer alone (2 where it does not apply).
+extern "C" void alelb_hostcheck_orient(const double *p, int n, int32_t *out, int32_t *stage)
+{
+    for (int k = 0; k < n; ++k) {
+        const double *q = p + 6 * k;
+        out[k] = orient(q[0], q[1], q[2], q[3], q[4], q[5]);
+        stage[k] = orient_int(q[0], q[1], q[2], q[3], q[4], q[5]);
+    }
+}

@@ -72,7 +72,9 @@ template <class S> struct StateDev {
                           // with populations certified missing at a wall, at work[9 N + k],
                           // k < wcount[9], their directions in wmask
     unsigned *wcount;     // [10] entries of each segment
-    unsigned short *wmask; // [N] directions certified missing at a wall (listed nodes only)
+    unsigned *wmask;      // [N] directions certified missing at a wall; set by the
+                          // propagation kernel, read by the exact path, cleared by the
+                          // moments kernel
 };
 
 // The exact-path kernels number the work list direction by direction
@@ -426,94 +428,120 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
         }
 }
 
-// Interpolates every population of node a whose previous-step element is
-// verified and settles those certified missing at the far field; returns
-// the mask of the populations left to the exact path (bits 0-8) and of those
-// certified missing at a wall (bits 16-24, also stored in wmask).
+// Population i of node a (one thread each): interpolated when its
+// previous-step element is verified, the node's own value when c^_0 is
+// exactly zero, free-stream equilibria when certified missing at the far
+// field.  Returns 0 when settled, 1 when left to the exact path, 2 when
+// certified missing at a wall (the wall condition then runs once per node
+// in the exact-path kernel).
 template <class S, class A>
-__device__ __forceinline__ unsigned stream_fast_node(const MeshDev &M, const MapStatic &MS,
-                                                     const MapScalarsF &sf, const KinParams<A> &K,
-                                                     const StateDev<S> &st, int a)
+__device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams<A> &K,
+                                               const StateDev<S> &st, int a, int i,
+                                               const FastMap &F, float4 Xf, float bd, int c)
 {
     const int N = M.N;
-    unsigned slow = 0;
-    {
-        const float4 Xf = M.Xf[a];
-        const float bd = M.bdist[a];
-        FastMap F = fast_map(MS, sf, a, Xf);
-        if (K.flags & FLAG_LITERAL_VG) F.ok = false;
-        int cache[NQ];
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) cache[i] = st.cache[i * N + a];
-        const bool v0 = M.vzero[a];
-        unsigned wall = 0; // directions certified missing at a wall
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-            int e;
-            float xi, eta;
-            if (i == 0 && v0) { // c^_0 exactly zero: the node's own value
-                st.str[a] = st.post[a];
-                st.str[NQ * N + a] = st.post[NQ * N + a];
-            } else if (F.ok && fast_decide(M, F, Xf, bd, a, i, cache[i], e, xi, eta)) {
-                A Nw[6];
-                shape6<A>((A)xi, (A)eta, Nw);
-                A fi = 0, gi = 0;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const int b = M.conn[6 * e + k];
-                    fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
-                    gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
-                }
-                pop_put(st.str + (i * N + a), fi);
-                pop_put(st.str + ((NQ + i) * N + a), gi);
-            } else {
-                const int ck = F.ok ? cone_missing(M, F, a, i) : 0;
-                if (ck == 2) { // far field: free-stream equilibria
-                    pop_put(st.str + (i * N + a), K.finf[i]);
-                    pop_put(st.str + ((NQ + i) * N + a), K.ginf[i]);
-                } else if (ck == 1) {
-                    wall |= 1u << i; // the wall condition runs once per node in k_stream_slow
-                } else {
-                    slow |= 1u << i;
-                }
-            }
-        }
-        if (wall) st.wmask[a] = (unsigned short)wall;
-        slow |= wall << 16; // bits 16 and up: the node goes onto the wall-node list
+    if (i == 0 && M.vzero[a]) { // c^_0 exactly zero: the node's own value
+        st.str[a] = st.post[a];
+        st.str[NQ * N + a] = st.post[NQ * N + a];
+        return 0;
     }
-    return slow;
+    if (!F.ok) return 1;
+    int e;
+    float xi, eta;
+    if (fast_decide(M, F, Xf, bd, a, i, c, e, xi, eta)) {
+        A Nw[6];
+        shape6<A>((A)xi, (A)eta, Nw);
+        A fi = 0, gi = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int b = M.conn[6 * e + k];
+            fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
+            gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
+        }
+        pop_put(st.str + (i * N + a), fi);
+        pop_put(st.str + ((NQ + i) * N + a), gi);
+        return 0;
+    }
+    const int ck = cone_missing(M, F, a, i);
+    if (ck == 2) { // far field: free-stream equilibria
+        pop_put(st.str + (i * N + a), K.finf[i]);
+        pop_put(st.str + ((NQ + i) * N + a), K.ginf[i]);
+        return 0;
+    }
+    return ck == 1 ? 2 : 1;
 }
 
-// Warp-aggregated append of the populations in `slow` (node a) to the work
-// list, per direction; all 32 lanes of the warp take part, with slow = 0
-// where idle.
+// Work-list entries of the lanes of a warp (all lanes take part; direction
+// i is the same for the whole warp): code 1 appends population (a, i) to
+// direction i's segment, code 2 sets bit i of the node's wall mask, and the
+// lane that set the first bit appends the node to the wall-node segment.
+// The moments kernel clears the masks once the exact path has used them.
 template <class S>
-__device__ __forceinline__ void append_work(const StateDev<S> &st, int a, int N, unsigned slow)
+__device__ __forceinline__ void append_pop(const StateDev<S> &st, int a, int N, int i, int code)
 {
     const unsigned lane = threadIdx.x & 31u;
-    if (!__any_sync(0xffffffffu, slow != 0u)) return;
+    bool first = false;
+    if (code == 2) first = atomicOr(st.wmask + a, 1u << i) == 0u;
 #pragma unroll
-    for (int i = 0; i <= NQ; ++i) { // segment NQ: nodes with wall-missing populations
-        const bool mine = i < NQ ? ((slow >> i) & 1u) : (slow >> 16) != 0u;
+    for (int r = 0; r < 2; ++r) {
+        const bool mine = r == 0 ? code == 1 : first;
         const unsigned m = __ballot_sync(0xffffffffu, mine);
         if (!m) continue;
+        const int seg = r == 0 ? i : NQ;
         const int leader = __ffs(m) - 1;
         unsigned base = 0;
-        if ((int)lane == leader) base = atomicAdd(st.wcount + i, (unsigned)__popc(m));
+        if ((int)lane == leader) base = atomicAdd(st.wcount + seg, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (mine)
-            st.work[(size_t)i * N + base + __popc(m & ((1u << lane) - 1u))] = i < NQ ? a * NQ + i : a;
+        if (mine) st.work[(size_t)seg * N + base + __popc(m & ((1u << lane) - 1u))] = r == 0 ? a * NQ + i : a;
     }
 }
 
+// Directions per thread of the propagation kernels (single case, batch):
+// the grid's y extent is 9 / G; a thread evaluates the node's FP32 map once
+// for its G populations.
+#ifndef ALELB_FAST_G
+#define ALELB_FAST_G 1
+#endif
+#ifndef ALELB_BATCH_FAST_G
+#define ALELB_BATCH_FAST_G 9
+#endif
+constexpr int FAST_G = ALELB_FAST_G, BATCH_FAST_G = ALELB_BATCH_FAST_G;
+static_assert(NQ % FAST_G == 0 && NQ % BATCH_FAST_G == 0, "directions per thread");
 
+// Populations G y .. G y + G - 1 of node a (y = blockIdx.y): settled, or
+// entered in the work list.
+template <int G, class S, class A>
+__device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapStatic &MS,
+                                                  const MapScalarsF &sf, const KinParams<A> &K,
+                                                  const StateDev<S> &st, int a)
+{
+    const int i0 = G * blockIdx.y;
+    int code[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) code[j] = 0;
+    if (a < M.N) {
+        // the loads of the thread's cache entries go out together (the
+        // stores of the populations would otherwise order them one by one)
+        int c[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) c[j] = st.cache[(i0 + j) * M.N + a];
+        const float bd = M.bdist[a];
+        const float4 Xf = M.Xf[a];
+        FastMap F = fast_map(MS, sf, a, Xf);
+        if (K.flags & FLAG_LITERAL_VG) F.ok = false;
+#pragma unroll
+        for (int j = 0; j < G; ++j) code[j] = stream_fast_pop(M, K, st, a, i0 + j, F, Xf, bd, c[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) append_pop(st, a, M.N, i0 + j, code[j]);
+}
+
+// Grid (node blocks, 9 / FAST_G direction groups).
 template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
                                                      KinParams<A> K, StateDev<S> st)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned slow = a < M.N ? stream_fast_node(M, MS, sf, K, st, a) : 0u;
-    append_work(st, a, M.N, slow);
+    stream_fast_group<FAST_G>(M, MS, sf, K, st, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // One listed population (code = 9 node + direction): exact decision, then
@@ -537,8 +565,14 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
         float qx = 0.f, qy = 0.f;
         int src;
-        if (F.ok && !literal && cone_missing(M, F, a, i) == 1) { // leaves through a wall at the node
+        const int ck = F.ok && !literal ? certified_missing(M, F, a, i) : 0;
+        if (ck == 1) { // certified to meet a wall first
             stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
+            return;
+        }
+        if (ck == 2) { // certified to leave through the far field
+            pop_put(st.str + (i * N + a), K.finf[i]);
+            pop_put(st.str + ((NQ + i) * N + a), K.ginf[i]);
             return;
         }
         Loc L;
@@ -561,7 +595,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             src = -1;
             if (hits) atomicAdd(hits, 1ull);
         } else {
-            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err);
+            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err, st.cache[i * N + a]);
         }
         A fi = 0, gi = 0;
         if (src >= 0) {
@@ -590,6 +624,17 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         pop_put(st.str + ((NQ + i) * N + a), gi);
     }
 }
+
+// First entry of the exact-path list taken by this thread, and the stride:
+// 32 consecutive entries per warp (one direction, coherent), warps dealt
+// out across the blocks first, so that a short list spreads over all SMs
+// rather than filling the first few (its walks are latency chains that
+// would otherwise queue on those SMs' few FP64 units).
+__device__ __forceinline__ unsigned spread_first()
+{
+    return (blockIdx.x + (threadIdx.x >> 5) * gridDim.x) * 32u + (threadIdx.x & 31u);
+}
+__device__ __forceinline__ unsigned spread_stride() { return gridDim.x * blockDim.x; }
 
 // Entry w of the exact path's numbering (work_prefix over the 10 segments):
 // a population (9 node + direction), or a listed wall node, whose wall
@@ -624,7 +669,7 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
     const unsigned n = pre[NQ];
     const unsigned total = n + st.wcount[NQ];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
-    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x)
+    for (unsigned w = spread_first(); w < total; w += spread_stride())
         slow_entry(M, MS, sc, sf, K, st, err, pre, w, prop, stats);
 }
 
@@ -633,6 +678,7 @@ template <class S, class A>
 __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateDev<S> &st, int N,
                                              int *err, int a)
 {
+    st.wmask[a] = 0u; // used by the exact path of this step
     A f[NQ], g[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {

@@ -64,6 +64,9 @@ struct HostTables {
     std::vector<double> ms;
     std::vector<float4> ejf, Xf, v0f, evf;
     std::vector<float> bdist, msf;
+    std::vector<int> nb_ptr;
+    std::vector<float4> nb;
+    std::vector<uint8_t> nbf;
     int n_wall_nodes = 0;
 
     // a MeshDev whose pointers address these host vectors (host-side walk)
@@ -101,6 +104,9 @@ struct HostTables {
         D.ring_ptr = ring_ptr.data();
         D.ring = ring.data();
         D.nscale = nscale.data();
+        D.nb_ptr = nb_ptr.data();
+        D.nb = nb.data();
+        D.nbf = nbf.data();
         return D;
     }
     MapStatic host_map() const
@@ -443,8 +449,18 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
                 add(mid, true, 0.5 * ex, 0.5 * ey);
                 add(mid, false, 0.5 * ex, 0.5 * ey);
             }
+        // bit 2: a convex corner of the domain (the boundary turns left by a
+        // clear margin), where the domain near the node is the intersection
+        // of the two left half-planes, so leaving across either edge line
+        // leaves the mesh; bit 3: a reflex corner (turns right by a clear
+        // margin), where the domain near the node is their union
         for (int a = 0; a < N; ++a)
-            if (nout[a] == 1 && nin[a] == 1 && kk[a] > 0) T.conek[a] = (uint8_t)kk[a];
+            if (nout[a] == 1 && nin[a] == 1 && kk[a] > 0) {
+                const double ox = T.cone[a].x, oy = T.cone[a].y, ix = T.cone[a].z, iy = T.cone[a].w;
+                const double cr = ix * oy - iy * ox;
+                const double tol = 1e-6 * std::sqrt((ix * ix + iy * iy) * (ox * ox + oy * oy));
+                T.conek[a] = (uint8_t)(kk[a] | (cr > tol ? 4 : 0) | (cr < -tol ? 8 : 0));
+            }
     }
     // element of each node's wall-condition gradients: among the incident
     // elements with a vertex on a wall edge the one of larger computational
@@ -608,13 +624,27 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
     // lower bound of every node's distance to the nearest boundary edge
     // (capped at DCAP): a departure segment shorter than this cannot leave
     // the mesh
+    // The same pass lists, for non-periodic meshes, every wall or far-field
+    // edge within NEAR_R of each node, relative to the node (the departure
+    // segment certificates of the fast path).
     const double DCAP = 16.0;
     T.bdist.assign(N, (float)DCAP);
+    T.nb_ptr.assign(N + 1, 0);
+    T.nb.clear();
+    T.nbf.clear();
     {
         std::vector<std::pair<double2, double2>> be;
+        std::vector<int> bkd, bn0, bn1, bn2;
         for (int en = 0; en < E; ++en)
             for (int k = 0; k < 3; ++k)
-                if ((einfo[en] >> (8 * k)) & 3u) be.push_back({ev[3 * en + k], ev[3 * en + (k + 1) % 3]});
+                if ((einfo[en] >> (8 * k)) & 3u) {
+                    const int k1 = (k + 1) % 3;
+                    be.push_back({ev[3 * en + k], ev[3 * en + k1]});
+                    bkd.push_back((int)((einfo[en] >> (8 * k)) & 3u));
+                    bn0.push_back(conn[6 * en + k]);
+                    bn1.push_back(conn[6 * en + k1]);
+                    bn2.push_back(conn[6 * en + 3 + k]);
+                }
         if (!be.empty() && (T.Lx > 0 || T.Ly > 0)) {
             T.bdist.assign(N, 0.0f); // periodic meshes with boundaries: always walk
         } else if (!be.empty()) {
@@ -628,7 +658,9 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
                     for (long iy = (long)std::floor(y0 / cs); iy <= (long)std::floor(y1 / cs); ++iy)
                         grid[key(ix, iy)].push_back((int)b);
             }
+            const double RN = (double)NEAR_R * (1.0 + 1e-6) + 1e-6;
             for (int a = 0; a < N; ++a) {
+                T.nb_ptr[a + 1] = T.nb_ptr[a];
                 double px = T.X[a].x, py = T.X[a].y;
                 auto it = grid.find(key((long)std::floor(px / cs), (long)std::floor(py / cs)));
                 if (it == grid.end()) continue;
@@ -639,7 +671,15 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
                     double t = L2 > 0 ? ((px - ax) * dx + (py - ay) * dy) / L2 : 0.0;
                     t = std::min(1.0, std::max(0.0, t));
                     double qx = ax + t * dx - px, qy = ay + t * dy - py;
-                    dmin = std::min(dmin, std::sqrt(qx * qx + qy * qy));
+                    const double d = std::sqrt(qx * qx + qy * qy);
+                    dmin = std::min(dmin, d);
+                    if (d < RN) {
+                        const bool on = bn0[b] == a || bn1[b] == a || bn2[b] == a;
+                        T.nb.push_back(make_float4((float)(ax - px), (float)(ay - py), (float)(bx - px),
+                                                   (float)(by - py)));
+                        T.nbf.push_back((uint8_t)(bkd[b] | (on ? 4 : 0)));
+                        T.nb_ptr[a + 1]++;
+                    }
                 }
                 T.bdist[a] = (float)(dmin * (1.0 - 1e-6));
             }

@@ -35,6 +35,8 @@ def lib():
                                                 C.c_void_p]
         _lib.alelb_hostcheck_fast.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                               C.c_void_p]
+        _lib.alelb_hostcheck_orient.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        _lib.alelb_hostcheck_orient.restype = None
     return _lib
 
 
@@ -97,3 +99,13 @@ def locate_fast(mesh, motion, t_prev, t):
     st = lib().alelb_hostcheck_fast(C.byref(d), float(t_prev), float(t), e.ctypes.data, k.ctypes.data,
                                     f.ctypes.data)
     return st, e, k, f.astype(bool)
+
+
+def orient(pts):
+    """The library's exact orientation sign for rows (ax, ay, bx, by, cx, cy),
+    and the integer stage's answer alone (2 where it does not apply)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 6)
+    out = np.empty(len(pts), dtype=np.int32)
+    stage = np.empty(len(pts), dtype=np.int32)
+    lib().alelb_hostcheck_orient(pts.ctypes.data, len(pts), out.ctypes.data, stage.ctypes.data)
+    return out, stage

@@ -100,3 +100,48 @@ def test_fast_path_decisions_match_oracle(name):
         assert np.array_equal(k, ko)
         if name != "lattice":  # on the lattice every departure point is a node
             assert fast.mean() > 0.8, f"{name}: only {fast.mean():.3f} settled by the fast path"
+
+
+def _exact_sign(r):
+    from fractions import Fraction as F
+    ax, ay, bx, by, cx, cy = (F(float(v)) for v in r)
+    d = (ax - cx) * (by - cy) - (ay - cy) * (bx - cx)
+    return (d > 0) - (d < 0)
+
+
+def test_library_orientation_is_exact():
+    """The walk's orientation predicate (FP64 filter, integer stage, expansion
+    stage) against rational arithmetic: exact ties (collinear points on
+    quantised and unquantised lines), near ties one ulp off, far-apart
+    exponents, and random points."""
+    rng = np.random.default_rng(7)
+    rows = []
+    for _ in range(400):
+        # a quantised segment and a point on its line or one ulp off it
+        a = np.round(rng.uniform(-5e3, 5e3, 2) * 2**20) / 2**20
+        d = np.round(rng.uniform(-8, 8, 2) * 2**20) / 2**20
+        t = rng.choice([0.5, 0.25, 2.0, -1.0, 3.0])
+        c = a + t * d
+        b = a + d
+        rows.append([*a, *b, *c])
+        for s in (1, -1):
+            rows.append([*a, *b, np.nextafter(c[0], c[0] + s), c[1]])
+            rows.append([*a, *b, c[0], np.nextafter(c[1], c[1] - s)])
+        # departure-like point: node plus a small FP64 offset along the edge
+        off = rng.uniform(1e-3, 1.0)
+        p = np.array([a[0] + off * d[0], a[1] + off * d[1]])
+        rows.append([*a, *b, *p])
+    for _ in range(200):
+        # operands of very different magnitude (the expansion stage)
+        big = rng.uniform(-1e6, 1e6, 2)
+        small = rng.uniform(-1e-9, 1e-9, 4)
+        rows.append([big[0], big[1], small[0], small[1], small[2], small[3]])
+        rows.append([*rng.uniform(-1, 1, 6)])
+    rows = np.array(rows)
+    got, stage = H.orient(rows)
+    want = np.array([_exact_sign(r) for r in rows])
+    assert np.array_equal(got, want), f"{np.sum(got != want)} orientation signs differ"
+    used = stage != 2
+    assert used.sum() > 0.5 * len(rows)  # the integer stage decides the common cases
+    assert np.array_equal(stage[used], want[used])
+    assert (want == 0).sum() > 300  # exact ties are present
