@@ -867,14 +867,24 @@ ALELB_HD __forceinline__ int cross_missing(const MeshDev &M, int a, float bx, fl
 
 // Bound of the FP32 transformed velocities c^_i against the FP64 canonical
 // ones, from the FP32 metrics themselves (u = 2^-24):
-//   entries of g:   eps_g   = 16u (1 + G),  G = max |g_ij|
+//   entries of g:   eps_g   = 8u (1 + G) (blended map; 4u (1 + G) sine, 2u
+//                   rigid pitch, 0 identity and plunge),  G = max |g_ij|
 //   det g:          eps_det = 4 G eps_g + 3u (|x_X y_Y| + |y_X x_Y|)
 //   A = g^{-1,T}:   eps_A   = (eps_g + G eps_det / det) / det + 2u max|A|
 //   V_G:            eps_V   = 8u Vmag (Vmag: sum of the magnitudes entering V)
 //   c^ = A c - A V: eps_c   = 2 [eps_A (2 + 2|V|) + 2 max|A| eps_V + 6u max|A| (2 + 2|V|)]
+//   c^_0 = -A V:    eps_0   = 2 [eps_A 2|V| + 2 max|A| eps_V + 6u max|A| 2|V|]
+//                   (c_0 = 0: the rest population's bound scales with the mesh
+//                   velocity, which is small wherever the mesh barely moves)
+// and er, the FP64 rounding of the canonical departure point X - c^ (at
+// most 2^-53 (max|X| + 2) per component, taken twice).
 struct FastMap {
-    float A11, A12, A21, A22, W1, W2, eps_c, Vx, Vy;
+    float A11, A12, A21, A22, W1, W2, eps_c, Vx, Vy, eps0, er;
     bool ok;
+    // bound of c^_i, and of the departure offset -c^_i against the
+    // canonical FP64 departure point relative to the node
+    ALELB_HD float eps(int i) const { return i ? eps_c : eps0; }
+    ALELB_HD float eq(int i) const { return (i ? eps_c : eps0) + er; }
 };
 
 ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF &sf, int a,
@@ -914,6 +924,9 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     float eps_V = 8.0f * u * Vmag;
     float cv = 2.0f + 2.0f * Vmax;
     F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
+    const float cv0 = 2.0f * Vmax;
+    F.eps0 = 2.0f * (eps_A * cv0 + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv0);
+    F.er = 2.3e-16f * (fmaxf(fabsf(Xf.x), fabsf(Xf.y)) + 2.0f);
     F.ok = det > 16.0f * eps_det && isfinite(F.eps_c);
     return F;
 }
@@ -943,7 +956,7 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
     const float chx = F.A11 * cx + F.A12 * cy - F.W1;
     const float chy = F.A21 * cx + F.A22 * cy - F.W2;
     const float len = sqrtf(chx * chx + chy * chy);
-    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eps_c)) return false;
+    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eq(i))) return false;
     e = c & 0x0fffffff;
     const int *cn = M.conn + 6 * e;
     int l = -1;
@@ -952,12 +965,12 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         if (cn[k] == a) l = k;
     // near a boundary the exact path decides (with the segment certificate
     // against the node's nearby boundary edges)
-    if (!(len + F.eps_c < bdist) && l < 0) return false;
+    if (!(len + F.eq(i) < bdist) && l < 0) return false;
     const float4 J = M.ejf[2 * e + 1];
     if (l >= 0) {
         // the node is node l of element e: its local coordinates are exact
         // (0, 1/2 or 1), so only the small offset -c^ is taken through the
-        // FP32 inverse Jacobian; errors: eps_c on c^ (plus 2^-25 for the
+        // FP32 inverse Jacobian; errors: F.eq(i) on c^ (eps of the direction plus the
         // FP64 rounding of the canonical departure point), u/2 on each J
         // entry, the products, the sums and the additions to the node's
         // coordinates
@@ -965,14 +978,19 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         const float el[6] = {0.0f, 0.0f, 1.0f, 0.0f, 0.5f, 0.5f};
         const float rx = -chx, ry = -chy;
         const float t11 = J.x * rx, t12 = J.y * ry, t21 = J.z * rx, t22 = J.w * ry;
-        xi = xl[l] + (t11 + t12);
-        eta = el[l] + (t21 + t22);
-        const float l0 = 1.0f - xi - eta;
-        const float eq = F.eps_c + 2.98023223876953125e-08f;
+        const float T1 = t11 + t12, T2 = t21 + t22;
+        xi = xl[l] + T1;
+        eta = el[l] + T2;
+        // the third coordinate from its exact value at the node minus the
+        // offsets (1 - xi - eta would cancel at nodes where it is zero)
+        const float l0 = (1.0f - xl[l] - el[l]) - (T1 + T2);
+        const float eq = F.eq(i);
         const float S1 = fabsf(J.x) + fabsf(J.y), S2 = fabsf(J.z) + fabsf(J.w);
-        const float m1 = 2.0f * (S1 * eq + 3.0f * u * (fabsf(t11) + fabsf(t12))) + 2.0f * u * fabsf(xi);
-        const float m2 = 2.0f * (S2 * eq + 3.0f * u * (fabsf(t21) + fabsf(t22))) + 2.0f * u * fabsf(eta);
-        const float m0 = m1 + m2 + 4.0f * u * (1.0f + fabsf(xi) + fabsf(eta));
+        const float d1 = 2.0f * (S1 * eq + 3.0f * u * (fabsf(t11) + fabsf(t12)));
+        const float d2 = 2.0f * (S2 * eq + 3.0f * u * (fabsf(t21) + fabsf(t22)));
+        const float m1 = d1 + 2.0f * u * fabsf(xi);
+        const float m2 = d2 + 2.0f * u * fabsf(eta);
+        const float m0 = d1 + d2 + 2.0f * u * (fabsf(T1) + fabsf(T2) + fabsf(l0));
         return xi > m1 && eta > m2 && l0 > m0;
     }
     const float4 ed = M.ejf[2 * e];
@@ -995,8 +1013,7 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
     const float qx = dx - chx, qy = dy - chy;
     const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
     const float Q = fmaxf(fabsf(qx), fabsf(qy));
-    const float eq = F.eps_c + 2.0f * u * fmaxf(fmaxf(fabsf(dx), fabsf(dy)), E) + u * Q +
-                     2.98023223876953125e-08f;
+    const float eq = F.eq(i) + 2.0f * u * fmaxf(fmaxf(fabsf(dx), fabsf(dy)), E) + u * Q;
     const float t11 = J.x * qx, t12 = J.y * qy, t21 = J.z * qx, t22 = J.w * qy;
     xi = t11 + t12;
     eta = t21 + t22;
@@ -1014,7 +1031,7 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
 // (the domain lies on their left), or, at a convex corner of the domain,
 // strictly to the right of either.  The points of the segment next to the
 // node then lie outside the closed mesh.  Returns the boundary kind, or 0
-// when not certain.  Errors: eps_c (+ 2^-25) per component of -c^, the FP32
+// when not certain.  Errors: F.eq(i) per component of -c^, the FP32
 // rounding of the edge vectors and of the cross products.
 ALELB_HD __forceinline__ int cone_missing(const MeshDev &M, const FastMap &F, int a, int i)
 {
@@ -1025,9 +1042,9 @@ ALELB_HD __forceinline__ int cone_missing(const MeshDev &M, const FastMap &F, in
     const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
     const float dx = -(F.A11 * cx + F.A12 * cy - F.W1);
     const float dy = -(F.A21 * cx + F.A22 * cy - F.W2);
-    if (!(sqrtf(dx * dx + dy * dy) > 4.0f * F.eps_c)) return 0;
+    if (!(sqrtf(dx * dx + dy * dy) > 4.0f * F.eq(i))) return 0;
     const float4 c = M.cone[a];
-    const float eq = F.eps_c + 2.98023223876953125e-08f;
+    const float eq = F.eq(i);
     const float s1 = c.x * dy - c.y * dx, s2 = c.z * dy - c.w * dx;
     const float b1 = 2.0f * (3.0f * u * (fabsf(c.x * dy) + fabsf(c.y * dx)) + (fabsf(c.x) + fabsf(c.y)) * eq);
     const float b2 = 2.0f * (3.0f * u * (fabsf(c.z * dy) + fabsf(c.w * dx)) + (fabsf(c.z) + fabsf(c.w)) * eq);
@@ -1046,14 +1063,14 @@ ALELB_HD __forceinline__ int certified_missing(const MeshDev &M, const FastMap &
     const float chx = F.A11 * cx + F.A12 * cy - F.W1;
     const float chy = F.A21 * cx + F.A22 * cy - F.W2;
     const float len = sqrtf(chx * chx + chy * chy);
-    const float eb = F.eps_c + 2.98023223876953125e-08f;
-    if (!(len > 4.0f * F.eps_c) || !(len + eb < NEAR_R)) return 0;
+    const float eb = F.eq(i);
+    if (!(len > 4.0f * F.eq(i)) || !(len + eb < NEAR_R)) return 0;
     return cross_missing(M, a, -chx, -chy, eb);
 }
 
 
 // Orientation provider of the walk in FP32: every point relative to the
-// node, the departure point from the FP32 c^ (bound eps_c), element
+// node, the departure point from the FP32 c^ (bound F.eq(i)), element
 // vertices from their hi/lo splits.  Uncertain signs fall back to the exact
 // FP64 predicate on the FP64 canonical departure point, computed lazily.
 struct Pred32 {
@@ -1154,7 +1171,9 @@ struct Pred32 {
         ensure64();
         return orient(Xa, Ya, px, py, WX(k), WY(k));
     }
-    ALELB_HD bool p_is_node() const { return false; } // the caller ensures |c^| > 4 eps_c
+    // the caller ensures |c^| > 4 F.eq(i): then the FP64 departure point is
+    // not the node
+    ALELB_HD bool p_is_node() const { return false; }
 };
 
 // The exact element decision of population i of node a in the
@@ -1184,7 +1203,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
         const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
         const float chx = F.A11 * cx + F.A12 * cy - F.W1;
         const float chy = F.A21 * cx + F.A22 * cy - F.W2;
-        if (sqrtf(chx * chx + chy * chy) > 4.0f * F.eps_c) {
+        if (sqrtf(chx * chx + chy * chy) > 4.0f * F.eq(i)) {
             Pred32 pr;
             pr.evf = M.evf;
             pr.ev = M.ev;
@@ -1198,7 +1217,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
             pr.Xf = Xf;
             pr.rpx = -chx;
             pr.rpy = -chy;
-            pr.ep = F.eps_c + 9.313225746154785e-10f;
+            pr.ep = F.eq(i);
             pr.have64 = false;
             pr.wload = false;
             pr.Xa = Xa.x;
@@ -1210,8 +1229,8 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
 #pragma unroll
                 for (int k = 0; k < 6; ++k) own |= M.conn[6 * ce + k] == a;
                 const float len = sqrtf(chx * chx + chy * chy);
-                const float eb = F.eps_c + 2.98023223876953125e-08f;
-                if (own || len + F.eps_c < M.bdist[a] ||
+                const float eb = F.eq(i);
+                if (own || len + eb < M.bdist[a] ||
                     (len + eb < NEAR_R && seg_clear(M, a, -chx, -chy, eb))) {
                     pr.load(ce, 0, 0);
                     const int o0 = pr.vvp(0, 1);
