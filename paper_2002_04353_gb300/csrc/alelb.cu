@@ -233,8 +233,7 @@ __global__ void k_fill_uniform(StateDev<S> st, int N, const double *consts, doub
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
     for (int i = 0; i < NQ; ++i) {
-        pop_put(st.post + (i * N + a), consts[2 * NQ + i] - consts[i]);
-        pop_put(st.post + ((NQ + i) * N + a), consts[3 * NQ + i] - consts[NQ + i]);
+        fg_put(st.post, i, a, N, consts[2 * NQ + i] - consts[i], consts[3 * NQ + i] - consts[NQ + i]);
     }
     st.rho[a] = (fld_t<S>)rho;
     st.ux[a] = (fld_t<S>)ux;
@@ -252,8 +251,7 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
     double r = 0, jx = 0, jy = 0, e2 = 0;
     for (int i = 0; i < NQ; ++i) {
         double f = full[i * N + a], g = full[(NQ + i) * N + a];
-        pop_put(st.post + (i * N + a), f - consts[i]);
-        pop_put(st.post + ((NQ + i) * N + a), g - consts[NQ + i]);
+        fg_put(st.post, i, a, N, f - consts[i], g - consts[NQ + i]);
         r += f;
         jx += c_cx[i] * f;
         jy += c_cy[i] * f;
@@ -280,8 +278,10 @@ __global__ void k_export(StateDev<S> st, int N, const double *consts, double *fu
     if (a >= N) return;
     if (full)
         for (int i = 0; i < NQ; ++i) {
-            full[i * N + a] = pop_in<double>(st.post[i * N + a]) + consts[i];
-            full[(NQ + i) * N + a] = pop_in<double>(st.post[(NQ + i) * N + a]) + consts[NQ + i];
+            double f, g;
+            fg_get(st.post, i, a, N, f, g);
+            full[i * N + a] = f + consts[i];
+            full[(NQ + i) * N + a] = g + consts[NQ + i];
         }
     if (fields) {
         fields[a] = (double)st.rho[a];

@@ -10,8 +10,9 @@
 //              Eqs. Ph_Derivative / FE_Derivative)
 //   k_collide  X_a = -d_a D_a, then the collision of Eqs. feqn/geqn
 //
-// One thread per node.  Populations are stored structure-of-arrays,
-// pop[q * N + node] with q = 0..8 for f and 9..17 for g.
+// One thread per node.  Populations are stored by direction: FP64 buffers
+// as pop[q * N + node] with q = 0..8 for f and 9..17 for g, the deviation
+// forms as (f_i, g_i) pairs, pop[2 (i N + node) + {0, 1}] (fg_get).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -39,28 +40,68 @@ template <class S> using fld_t = typename Store<S>::fld;
 
 constexpr float FP16_DEV_SCALE = 1024.f, FP16_DEV_UNSCALE = 1.f / 1024.f;
 
-template <class A> __device__ __forceinline__ A pop_in(double v) { return (A)v; }
-template <class A> __device__ __forceinline__ A pop_in(float v) { return (A)v; }
-template <class A> __device__ __forceinline__ A pop_in(__nv_bfloat16 v) { return (A)__bfloat162float(v); }
-template <class A> __device__ __forceinline__ A pop_in(__half v)
+// The pair (f_i, g_i) of node x in a population buffer.  FP64 buffers keep
+// f and g in separate planes, pop[q N + x] with q = i for f and 9 + i for
+// g.  The deviation forms keep the two side by side, pop[2 (i N + x)] and
+// pop[2 (i N + x) + 1], so that one 8-byte (FP32) or 4-byte (16-bit) access
+// moves both: the interpolation gathers them at the same six nodes.
+template <class A> __device__ __forceinline__ void fg_get(const double *p, int i, int x, int N, A &f, A &g)
 {
-    return (A)(__half2float(v) * FP16_DEV_UNSCALE);
+    f = (A)p[i * N + x];
+    g = (A)p[(NQ + i) * N + x];
 }
-template <class A> __device__ __forceinline__ void pop_put(double *p, A v) { *p = (double)v; }
-template <class A> __device__ __forceinline__ void pop_put(float *p, A v) { *p = (float)v; }
-template <class A> __device__ __forceinline__ void pop_put(__nv_bfloat16 *p, A v)
+template <class A> __device__ __forceinline__ void fg_get(const float *p, int i, int x, int N, A &f, A &g)
 {
-    *p = __float2bfloat16_rn((float)v);
+    const float2 v = reinterpret_cast<const float2 *>(p)[i * N + x];
+    f = (A)v.x;
+    g = (A)v.y;
 }
-template <class A> __device__ __forceinline__ void pop_put(__half *p, A v)
+template <class A>
+__device__ __forceinline__ void fg_get(const __nv_bfloat16 *p, int i, int x, int N, A &f, A &g)
 {
-    *p = __float2half_rn((float)v * FP16_DEV_SCALE);
+    const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(p)[i * N + x];
+    f = (A)__low2float(v);
+    g = (A)__high2float(v);
+}
+template <class A> __device__ __forceinline__ void fg_get(const __half *p, int i, int x, int N, A &f, A &g)
+{
+    const __half2 v = reinterpret_cast<const __half2 *>(p)[i * N + x];
+    f = (A)(__low2float(v) * FP16_DEV_UNSCALE);
+    g = (A)(__high2float(v) * FP16_DEV_UNSCALE);
+}
+template <class A> __device__ __forceinline__ void fg_put(double *p, int i, int x, int N, A f, A g)
+{
+    p[i * N + x] = (double)f;
+    p[(NQ + i) * N + x] = (double)g;
+}
+template <class A> __device__ __forceinline__ void fg_put(float *p, int i, int x, int N, A f, A g)
+{
+    reinterpret_cast<float2 *>(p)[i * N + x] = make_float2((float)f, (float)g);
+}
+template <class A> __device__ __forceinline__ void fg_put(__nv_bfloat16 *p, int i, int x, int N, A f, A g)
+{
+    reinterpret_cast<__nv_bfloat162 *>(p)[i * N + x] = __floats2bfloat162_rn((float)f, (float)g);
+}
+template <class A> __device__ __forceinline__ void fg_put(__half *p, int i, int x, int N, A f, A g)
+{
+    reinterpret_cast<__half2 *>(p)[i * N + x] =
+        __floats2half2_rn((float)f * FP16_DEV_SCALE, (float)g * FP16_DEV_SCALE);
+}
+template <class P> __device__ __forceinline__ void fg_copy(P *dst, const P *src, int i, int x, int N)
+{
+    if (sizeof(P) == 8) { // FP64 planes
+        dst[i * N + x] = src[i * N + x];
+        dst[(NQ + i) * N + x] = src[(NQ + i) * N + x];
+    } else {
+        dst[2 * (i * N + x)] = src[2 * (i * N + x)];
+        dst[2 * (i * N + x) + 1] = src[2 * (i * N + x) + 1];
+    }
 }
 
 template <class S> struct StateDev {
     using P = pop_t<S>;
     using F = fld_t<S>;
-    P *post;  // [18 N] post-collision populations (deviations)
+    P *post;  // [18 N] post-collision populations (deviations), layout of fg_get
     P *str;   // [18 N] streamed populations
     F *rho, *ux, *uy, *T; // fields of the latest step
     F *Qx, *Qy, *mrt;     // Q'_xxx, Q'_yyy, mu/(rho T)
@@ -221,18 +262,18 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
                         const int b = M.conn[6 * e + k];
-                        fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
-                        gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
+                        A fb, gb;
+                        fg_get(st.post, i, b, N, fb, gb);
+                        fi += Nw[k] * fb;
+                        gi += Nw[k] * gb;
                     }
                 }
             }
         }
         if (src >= 0) {
-            fi = pop_in<A>(st.post[i * N + src]);
-            gi = pop_in<A>(st.post[(NQ + i) * N + src]);
+            fg_get(st.post, i, src, N, fi, gi);
         }
-        pop_put(st.str + (i * N + a), fi);
-        pop_put(st.str + ((NQ + i) * N + a), gi);
+        fg_put(st.str, i, a, N, fi, gi);
         sfm += fi;
         jx += (A)c_cx[i] * fi;
         jy += (A)c_cy[i] * fi;
@@ -301,8 +342,7 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
             if (!(miss >> i & 1)) continue;
             A fi = (far >> i & 1) ? K.finf[i] : fm[i];
             A gi = (far >> i & 1) ? K.ginf[i] : gm[i];
-            pop_put(st.str + (i * N + a), fi);
-            pop_put(st.str + ((NQ + i) * N + a), gi);
+            fg_put(st.str, i, a, N, fi, gi);
             sfm += fi;
             jx += (A)c_cx[i] * fi;
             jy += (A)c_cy[i] * fi;
@@ -423,8 +463,7 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
 #pragma unroll
     for (int i = 0; i < NQ; ++i)
         if (mask >> i & 1u) {
-            pop_put(st.str + (i * N + a), fm[i]);
-            pop_put(st.str + ((NQ + i) * N + a), gm[i]);
+            fg_put(st.str, i, a, N, fm[i], gm[i]);
         }
 }
 
@@ -441,8 +480,7 @@ __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams
 {
     const int N = M.N;
     if (i == 0 && M.vzero[a]) { // c^_0 exactly zero: the node's own value
-        st.str[a] = st.post[a];
-        st.str[NQ * N + a] = st.post[NQ * N + a];
+        fg_copy(st.str, st.post, 0, a, N);
         return 0;
     }
     if (!F.ok) return 1;
@@ -455,17 +493,17 @@ __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int b = M.conn[6 * e + k];
-            fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
-            gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
+            A fb, gb;
+            fg_get(st.post, i, b, N, fb, gb);
+            fi += Nw[k] * fb;
+            gi += Nw[k] * gb;
         }
-        pop_put(st.str + (i * N + a), fi);
-        pop_put(st.str + ((NQ + i) * N + a), gi);
+        fg_put(st.str, i, a, N, fi, gi);
         return 0;
     }
     const int ck = cone_missing(M, F, a, i);
     if (ck == 2) { // far field: free-stream equilibria
-        pop_put(st.str + (i * N + a), K.finf[i]);
-        pop_put(st.str + ((NQ + i) * N + a), K.ginf[i]);
+        fg_put(st.str, i, a, N, K.finf[i], K.ginf[i]);
         return 0;
     }
     return ck == 1 ? 2 : 1;
@@ -571,8 +609,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             return;
         }
         if (ck == 2) { // certified to leave through the far field
-            pop_put(st.str + (i * N + a), K.finf[i]);
-            pop_put(st.str + ((NQ + i) * N + a), K.ginf[i]);
+            fg_put(st.str, i, a, N, K.finf[i], K.ginf[i]);
             return;
         }
         Loc L;
@@ -599,8 +636,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         }
         A fi = 0, gi = 0;
         if (src >= 0) {
-            fi = pop_in<A>(st.post[i * N + src]);
-            gi = pop_in<A>(st.post[(NQ + i) * N + src]);
+            fg_get(st.post, i, src, N, fi, gi);
         } else if (L.e >= 0) {
             const int e = L.e;
             st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
@@ -610,8 +646,10 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const int b = M.conn[6 * e + k];
-                fi += Nw[k] * pop_in<A>(st.post[i * N + b]);
-                gi += Nw[k] * pop_in<A>(st.post[(NQ + i) * N + b]);
+                A fb, gb;
+                fg_get(st.post, i, b, N, fb, gb);
+                fi += Nw[k] * fb;
+                gi += Nw[k] * gb;
             }
         } else if (L.kind == 2) {
             fi = K.finf[i];
@@ -620,8 +658,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
             return;
         }
-        pop_put(st.str + (i * N + a), fi);
-        pop_put(st.str + ((NQ + i) * N + a), gi);
+        fg_put(st.str, i, a, N, fi, gi);
     }
 }
 
@@ -682,8 +719,7 @@ __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateD
     A f[NQ], g[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        f[i] = pop_in<A>(st.str[i * N + a]);
-        g[i] = pop_in<A>(st.str[(NQ + i) * N + a]);
+        fg_get(st.str, i, a, N, f[i], g[i]);
     }
     const A sf = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
     const A jx = K.jx_ref + ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
@@ -840,15 +876,13 @@ __device__ __forceinline__ void collide_at(const MeshDev &M, const MapStatic &MS
     A f[NQ], g[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        f[i] = pop_in<A>(st.str[i * N + a]);
-        g[i] = pop_in<A>(st.str[(NQ + i) * N + a]);
+        fg_get(st.str, i, a, N, f[i], g[i]);
     }
     A rho, ux, uy, T;
     if (!collide_node(K, f, g, Xx, Xy, rho, ux, uy, T)) atomicOr(err, ERR_NONFINITE);
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        pop_put(st.post + (i * N + a), f[i]);
-        pop_put(st.post + ((NQ + i) * N + a), g[i]);
+        fg_put(st.post, i, a, N, f[i], g[i]);
     }
     st.rho[a] = (fld_t<S>)rho;
     st.ux[a] = (fld_t<S>)ux;
