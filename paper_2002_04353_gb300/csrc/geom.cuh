@@ -804,65 +804,67 @@ ALELB_HD __forceinline__ float nb_err(float x, float y)
     return 5.9604644775390625e-08f * fmaxf(fabsf(x), fabsf(y)) + 2.98023223876953125e-08f;
 }
 
-// Certified: the segment from node a to its departure point a + (bx, by)
-// (error eb per component) meets no wall or far-field edge, except at the
-// node itself on the edges through the node, from where it enters the
-// domain: strictly left of every such edge's line, or, at a reflex corner
-// of the domain (the union of the two left half-planes), of one of them (a
-// straight segment meets the line of an edge through its start only
-// there).  The segment lies in the disk of the node's edge list (caller:
-// length + eb < NEAR_R).  Another edge is passed when both ends of the
-// segment lie strictly on one side of its line, or both ends of the edge
-// strictly on one side of the segment's line.
-ALELB_HD __forceinline__ bool seg_clear(const MeshDev &M, int a, float bx, float by, float eb)
+// One pass over node a's nearby boundary edges for the segment from the
+// node to its departure point a + (bx, by) (error eb per component; the
+// caller ensures length + eb < NEAR_R, so the segment lies in the disk the
+// list covers).  Up to 8 entries are loaded at once.
+//   clear: certified to meet no listed edge, except at the node itself on
+//     the edges through the node, from where it enters the domain: strictly
+//     left of every such edge's line, or, at a reflex corner of the domain
+//     (the union of the two left half-planes), of one of them (a straight
+//     segment meets the line of an edge through its start only there).
+//     Another edge is passed when both ends of the segment lie strictly on
+//     one side of its line, or both ends of the edge strictly on one side
+//     of the segment's line.
+//   cross: the boundary kind when the segment certainly crosses a listed
+//     edge not through the node (strictly opposite sides both ways: some of
+//     its points lie outside the mesh, so the population is missing) and
+//     every listed edge has that kind (the first boundary it meets is then
+//     of that kind); 0 otherwise.
+struct NbTest {
+    bool clear;
+    int cross;
+};
+ALELB_HD __forceinline__ NbTest nb_test(const MeshDev &M, int a, float bx, float by, float eb)
 {
+    constexpr int PRE = 8;
     const int beg = M.nb_ptr[a], end = M.nb_ptr[a + 1];
-    int inc = 0, left = 0;
-    for (int k = beg; k < end; ++k) {
-        const float4 E = M.nb[k];
-        const float eP = nb_err(E.x, E.y), eQ = nb_err(E.z, E.w);
-        const int sB = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, bx, by, eb);
-        if (M.nbf[k] & 4) { // the node lies on this edge
-            ++inc;
-            left += sB > 0;
-            continue;
+    int inc = 0, left = 0, kind = 0;
+    bool mixed = false, crossed = false, clear = true;
+    for (int base = beg; base < end; base += PRE) {
+        float4 E[PRE];
+        int fl[PRE];
+#pragma unroll
+        for (int j = 0; j < PRE; ++j) {
+            E[j] = base + j < end ? M.nb[base + j] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            fl[j] = base + j < end ? (int)M.nbf[base + j] : 0;
         }
-        const int sA = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, 0.0f, 0.0f, 0.0f);
-        if (sA != 0 && sA == sB) continue;
-        const int sP = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.x, E.y, eP);
-        const int sQ = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.z, E.w, eQ);
-        if (sP != 0 && sP == sQ) continue;
-        return false;
+#pragma unroll
+        for (int j = 0; j < PRE; ++j) {
+            if (base + j >= end) break;
+            const int f = fl[j];
+            if (kind && (f & 3) != kind) mixed = true;
+            kind = f & 3;
+            const float eP = nb_err(E[j].x, E[j].y), eQ = nb_err(E[j].z, E[j].w);
+            const int sB = orient3_f32(E[j].x, E[j].y, eP, E[j].z, E[j].w, eQ, bx, by, eb);
+            if (f & 4) { // the node lies on this edge
+                ++inc;
+                left += sB > 0;
+                continue;
+            }
+            const int sA = orient3_f32(E[j].x, E[j].y, eP, E[j].z, E[j].w, eQ, 0.0f, 0.0f, 0.0f);
+            if (sA != 0 && sA == sB) continue; // the segment stays on one side of the line
+            const int sP = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E[j].x, E[j].y, eP);
+            const int sQ = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E[j].z, E[j].w, eQ);
+            if (sP != 0 && sP == sQ) continue; // the edge stays on one side of the segment
+            clear = false;
+            if (sA * sB < 0 && sP * sQ < 0) crossed = true;
+        }
     }
-    return left == inc || (left > 0 && inc == 2 && (M.conek[a] & 8));
-}
-
-// Certified: the segment from node a to a + (bx, by) crosses a listed edge
-// not through the node properly (strictly opposite sides both ways), so
-// some of its points lie outside the mesh and the population is missing.
-// Returns the boundary kind when every listed edge has the same kind (the
-// first boundary the segment meets is then of that kind), else 0.  Caller:
-// length + eb < NEAR_R.
-ALELB_HD __forceinline__ int cross_missing(const MeshDev &M, int a, float bx, float by, float eb)
-{
-    const int beg = M.nb_ptr[a], end = M.nb_ptr[a + 1];
-    int kind = 0;
-    bool crossed = false;
-    for (int k = beg; k < end; ++k) {
-        const int f = M.nbf[k];
-        if (kind && (f & 3) != kind) return 0;
-        kind = f & 3;
-        if (crossed || (f & 4)) continue;
-        const float4 E = M.nb[k];
-        const float eP = nb_err(E.x, E.y), eQ = nb_err(E.z, E.w);
-        const int sA = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, 0.0f, 0.0f, 0.0f);
-        const int sB = orient3_f32(E.x, E.y, eP, E.z, E.w, eQ, bx, by, eb);
-        if (sA * sB >= 0) continue;
-        const int sP = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.x, E.y, eP);
-        const int sQ = orient3_f32(0.0f, 0.0f, 0.0f, bx, by, eb, E.z, E.w, eQ);
-        crossed = sP * sQ < 0;
-    }
-    return crossed ? kind : 0;
+    NbTest r;
+    r.clear = clear && (left == inc || (left > 0 && inc == 2 && (M.conek[a] & 8)));
+    r.cross = crossed && !mixed ? kind : 0;
+    return r;
 }
 
 // Bound of the FP32 transformed velocities c^_i against the FP64 canonical
@@ -1054,9 +1056,13 @@ ALELB_HD __forceinline__ int cone_missing(const MeshDev &M, const FastMap &F, in
 
 // A population certified missing without the walk: the exterior cone at a
 // boundary node, else a certified crossing of one of the node's nearby
-// boundary edges.  Returns the boundary kind, or 0 when not certain.
-ALELB_HD __forceinline__ int certified_missing(const MeshDev &M, const FastMap &F, int a, int i)
+// boundary edges.  Returns the boundary kind, or 0 when not certain; clear
+// (when given) receives the segment test of the same pass over the nearby
+// edges (1 clear, 0 not, -1 not evaluated).
+ALELB_HD __forceinline__ int certified_missing(const MeshDev &M, const FastMap &F, int a, int i,
+                                               int *clear = nullptr)
 {
+    if (clear) *clear = -1;
     const int ck = cone_missing(M, F, a, i);
     if (ck || M.nb_ptr[a] == M.nb_ptr[a + 1]) return ck;
     const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
@@ -1065,7 +1071,9 @@ ALELB_HD __forceinline__ int certified_missing(const MeshDev &M, const FastMap &
     const float len = sqrtf(chx * chx + chy * chy);
     const float eb = F.eq(i);
     if (!(len > 4.0f * F.eq(i)) || !(len + eb < NEAR_R)) return 0;
-    return cross_missing(M, a, -chx, -chy, eb);
+    const NbTest t = nb_test(M, a, -chx, -chy, eb);
+    if (clear) *clear = t.clear ? 1 : 0;
+    return t.cross;
 }
 
 
@@ -1193,7 +1201,7 @@ struct Pred32 {
 ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                                          const MapScalars &sc, const FastMap &F, float4 Xf, int a,
                                          int i, int literal, float &qx, float &qy, int &src,
-                                         int *err, int hint = -1)
+                                         int *err, int hint = -1, int clear = -1)
 {
     const double2 Xa = M.X[a];
     src = -1;
@@ -1231,7 +1239,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                 const float len = sqrtf(chx * chx + chy * chy);
                 const float eb = F.eq(i);
                 if (own || len + eb < M.bdist[a] ||
-                    (len + eb < NEAR_R && seg_clear(M, a, -chx, -chy, eb))) {
+                    (clear >= 0 ? clear == 1 : (len + eb < NEAR_R && nb_test(M, a, -chx, -chy, eb).clear))) {
                     pr.load(ce, 0, 0);
                     const int o0 = pr.vvp(0, 1);
                     if (o0 >= 0) {

@@ -603,7 +603,8 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
         float qx = 0.f, qy = 0.f;
         int src;
-        const int ck = F.ok && !literal ? certified_missing(M, F, a, i) : 0;
+        int clear = -1; // the segment test of the nearby-edge pass, for slow_decide
+        const int ck = F.ok && !literal ? certified_missing(M, F, a, i, &clear) : 0;
         if (ck == 1) { // certified to meet a wall first
             stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
             return;
@@ -632,7 +633,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             src = -1;
             if (hits) atomicAdd(hits, 1ull);
         } else {
-            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err, st.cache[i * N + a]);
+            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err, st.cache[i * N + a], clear);
         }
         A fi = 0, gi = 0;
         if (src >= 0) {
