@@ -358,12 +358,12 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
         }
         switch (k) {
         case KT_STREAM:
-            k_stream<S, A><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, K, st, s->d_err,
-                                                                   s->d_stats);
+            launch_pdl(k_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->dev, m->mst, sc, K, st,
+                       s->d_err, s->d_stats);
             break;
         case KT_FAST:
-            k_stream_fast<S, A><<<dim3((N + 127) / 128, NQ / FAST_G), 128, 0, s->stream>>>(m->dev, m->mst, sf, K,
-                                                                                         st);
+            launch_pdl(k_stream_fast<S, A>, dim3((N + 127) / 128, NQ / FAST_G), dim3(128), s->stream, m->dev,
+                       m->mst, sf, K, st);
             break;
         case KT_SLOW: {
             // every block resident at once: the list is spread over all
@@ -373,29 +373,31 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_stream_slow<S, A>, 128, 0);
                 return v > 0 ? v : 1;
             }();
-            k_stream_slow<S, A><<<per_sm * s->n_sm, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st, s->d_err,
-                                                                         s->d_stats, s->mlp ? s->d_prop : nullptr);
+            launch_pdl(k_stream_slow<S, A>, dim3(per_sm * s->n_sm), dim3(128), s->stream, m->dev, m->mst, sc, sf,
+                       K, st, s->d_err, s->d_stats, (const int *)(s->mlp ? s->d_prop : nullptr));
             break;
         }
         case KT_PROPOSE:
             mlp_propose(s, sf);
             break;
         case KT_MOMENTS:
-            k_moments<S, A><<<(N + 255) / 256, 256, 0, s->stream>>>(K, st, N, s->d_err);
+            launch_pdl(k_moments<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, K, st, N, s->d_err);
             break;
         case KT_DERIV1:
             if (fast)
-                k_deriv1<S, A, true><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, sf, st);
+                launch_pdl(k_deriv1<S, A, true>, dim3((N + 255) / 256), dim3(256), s->stream, m->dev, m->mst, sc,
+                           sf, st);
             else
-                k_deriv1<S, A, false><<<(N + 255) / 256, 256, 0, s->stream>>>(m->dev, m->mst, sc, sf, st);
+                launch_pdl(k_deriv1<S, A, false>, dim3((N + 255) / 256), dim3(256), s->stream, m->dev, m->mst, sc,
+                           sf, st);
             break;
         default:
             if (fast)
-                k_collide<S, A, true><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st,
-                                                                              s->d_err);
+                launch_pdl(k_collide<S, A, true>, dim3((N + 127) / 128), dim3(128), s->stream, m->dev, m->mst, sc,
+                           sf, K, st, s->d_err);
             else
-                k_collide<S, A, false><<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, sf, K, st,
-                                                                               s->d_err);
+                launch_pdl(k_collide<S, A, false>, dim3((N + 127) / 128), dim3(128), s->stream, m->dev, m->mst,
+                           sc, sf, K, st, s->d_err);
         }
         if (s->prof) {
             cudaEventRecord(eb, s->stream);

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) kb_stream(const CaseDev<S, A> *__restrict
                                                  const int *__restrict__ off, int B,
                                                  const MapScalars *__restrict__ sc, int count)
 {
+    wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
     const int c = tile_case(off, B, blockIdx.x);
     sh.load(cases, sc, nullptr, c);
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__
                                                const int *__restrict__ off, int B,
                                                const MapScalarsF *__restrict__ sf)
 {
+    wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
     const int c = tile_case(off, B, blockIdx.x);
     sh.load(cases, nullptr, sf, c);
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
                                                const MapScalars *__restrict__ sc,
                                                const MapScalarsF *__restrict__ sf, int count)
 {
+    wait_prior_grid();
     constexpr int NS = NQ + 1; // segments per case: nine directions, then wall nodes
     __shared__ unsigned pre[BATCH_MAX * NS + 1];
     const int nseg = B * NS;
@@ -171,6 +174,7 @@ template <class S, class A>
 __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restrict__ cases,
                                                   const int *__restrict__ off, int B)
 {
+    wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
     const int c = tile_case(off, B, blockIdx.x);
     sh.load(cases, nullptr, nullptr, c);
@@ -187,6 +191,7 @@ __global__ void __launch_bounds__(256) kb_deriv1(const CaseDev<S, A> *__restrict
                                                  const MapScalars *__restrict__ sc,
                                                  const MapScalarsF *__restrict__ sf)
 {
+    wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
     const int c = tile_case(off, B, blockIdx.x);
     sh.load(cases, sc, sf, c);
@@ -202,6 +207,7 @@ __global__ void __launch_bounds__(256) kb_collide(const CaseDev<S, A> *__restric
                                                   const MapScalars *__restrict__ sc,
                                                   const MapScalarsF *__restrict__ sf)
 {
+    wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
     const int c = tile_case(off, B, blockIdx.x);
     sh.load(cases, sc, sf, c);
@@ -346,24 +352,24 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count)
     const bool fast = b->prec == ALELB_PREC_FP32_DEV;
     switch (kt) {
     case KT_STREAM:
-        kb_stream<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, count);
+        launch_pdl(kb_stream<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, count);
         break;
     case KT_FAST:
-        kb_fast<S, A><<<dim3(tiles, NQ / BATCH_FAST_G), bs, 0, b->stream>>>(cases, off, B, sf);
+        launch_pdl(kb_fast<S, A>, dim3(tiles, NQ / BATCH_FAST_G), dim3(bs), b->stream, cases, off, B, sf);
         break;
     case KT_SLOW:
-        kb_slow<S, A><<<grid, bs, 0, b->stream>>>(cases, B, sc, sf, count);
+        launch_pdl(kb_slow<S, A>, dim3(grid), dim3(bs), b->stream, cases, B, sc, sf, count);
         break;
     case KT_MOMENTS:
-        kb_moments<S, A><<<tiles, bs, 0, b->stream>>>(cases, off, B);
+        launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B);
         break;
     case KT_DERIV1:
-        if (fast) kb_deriv1<S, A, true><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
-        else kb_deriv1<S, A, false><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
+        if (fast) launch_pdl(kb_deriv1<S, A, true>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
+        else launch_pdl(kb_deriv1<S, A, false>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
         break;
     default:
-        if (fast) kb_collide<S, A, true><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
-        else kb_collide<S, A, false><<<tiles, bs, 0, b->stream>>>(cases, off, B, sc, sf);
+        if (fast) launch_pdl(kb_collide<S, A, true>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
+        else launch_pdl(kb_collide<S, A, false>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
     }
 }
 

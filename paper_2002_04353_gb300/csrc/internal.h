@@ -45,6 +45,25 @@ enum { KT_STREAM = 0, KT_FAST = 1, KT_SLOW = 2, KT_MOMENTS = 3, KT_DERIV1 = 4, K
        KT_N = 7 };
 extern const char *const KT_NAMES[KT_N];
 
+// A kernel of the step, launched with programmatic stream serialization:
+// its blocks may start while the previous kernel drains (each waits in
+// wait_prior_grid before touching memory).
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // FP32 copies of the per-step map scalars.
 MapScalarsF to_f32(const MapScalars &S, const HostTables &T);
 // Uploads the P2 derivative tables of batch.cu's module.

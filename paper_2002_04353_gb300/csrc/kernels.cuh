@@ -98,6 +98,13 @@ template <class P> __device__ __forceinline__ void fg_copy(P *dst, const P *src,
     }
 }
 
+// Waits until the grids this one depends on have completed and their
+// stores are visible.  The step's kernels are launched with programmatic
+// stream serialization: a kernel's blocks may start while the previous
+// kernel drains, and each waits here before touching memory.  A kernel
+// launched the ordinary way returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <class S> struct StateDev {
     using P = pop_t<S>;
     using F = fld_t<S>;
@@ -366,6 +373,7 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
                                                 KinParams<A> K, StateDev<S> st, int *err,
                                                 unsigned long long *stats)
 {
+    wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < M.N) stream_plain_node(M, MS, sc, K, st, err, stats, a);
 }
@@ -579,6 +587,7 @@ template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
                                                      KinParams<A> K, StateDev<S> st)
 {
+    wait_prior_grid();
     stream_fast_group<FAST_G>(M, MS, sf, K, st, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -701,6 +710,7 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
                                                      int *err, unsigned long long *stats,
                                                      const int *prop)
 {
+    wait_prior_grid();
     __shared__ unsigned pre[NQ + 1];
     if (threadIdx.x == 0) work_prefix(st.wcount, pre);
     __syncthreads();
@@ -740,6 +750,7 @@ __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateD
 template <class S, class A>
 __global__ void __launch_bounds__(256) k_moments(KinParams<A> K, StateDev<S> st, int N, int *err)
 {
+    wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a <= NQ) st.wcount[a] = 0u; // the work list has been consumed
     if (a < N) moments_node(K, st, N, err, a);
@@ -844,6 +855,7 @@ template <class S, class A, bool FAST>
 __global__ void __launch_bounds__(256) k_deriv1(MeshDev M, MapStatic MS, MapScalars sc,
                                                 MapScalarsF sf, StateDev<S> st)
 {
+    wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < M.N) deriv1_node<S, A, FAST>(M, MS, sc, sf, st, a);
 }
@@ -896,6 +908,7 @@ __global__ void __launch_bounds__(128) k_collide(MeshDev M, MapStatic MS, MapSca
                                                  MapScalarsF sf, KinParams<A> K, StateDev<S> st,
                                                  int *err)
 {
+    wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < M.N) collide_at<S, A, FAST>(M, MS, sc, sf, K, st, err, a);
 }

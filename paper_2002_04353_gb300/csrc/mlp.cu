@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(PRED_WARPS * 32)
 k_propose(MeshDev M, MapStatic MS, MapScalarsF sf, StateDev<T> st, const __half *__restrict__ Wh,
           int flags, int *prop, unsigned long long *made)
 {
+    wait_prior_grid();
     __shared__ PredSmem S;
     load_pred_weights(S, Wh);
     __syncthreads();
