@@ -229,9 +229,13 @@ def run_batched(alelb, torch, dev, world, rank, args):
     """The 32-case airfoil sweep (NACA 00xx, 8-18% thick, 20k-300k P2 nodes
     log-uniform, Mach 0.1-0.8, pitch 0-5 deg, plunge 0-0.2c, k 0.05-1) in
     one batch: FP32-deviation solvers, one launch per phase over all cases,
-    steps replayed from captured CUDA graphs.  Under torchrun every rank
-    takes the cases c = rank (mod N) (no exchange: weak in cases)."""
-    cases = [c for k, c in enumerate(I.batched_sweep()) if k % world == rank]
+    steps replayed from captured CUDA graphs.  Under torchrun the cases are
+    shared out by node count (shard.assign_cases) and every rank steps its
+    own (no exchange: weak in cases)."""
+    from paper_2002_04353_gb300 import shard
+    sweep = I.batched_sweep()
+    mine = shard.assign_cases([c.mesh.n_nodes for c in sweep], world)[rank]
+    cases = [sweep[k] for k in mine]
     meshes = [alelb.Mesh(c.mesh, c.motion) for c in cases]
     solvers = [alelb.Solver(m, c.flow, alelb.PREC_FP32_DEV) for m, c in zip(meshes, cases)]
     stream = torch.cuda.Stream(device=dev)
@@ -257,15 +261,8 @@ def run_batched(alelb, torch, dev, world, rank, args):
             finite += 1
         except alelb.AlelbError:
             pass
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t[0])
-        nn = torch.tensor([n_nodes], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(nn)
-        n_total = int(nn[0])
-    else:
-        n_total = n_nodes
+    ms = shard.max_over_ranks(ms, torch, dev)
+    n_total = int(shard.sum_over_ranks(n_nodes, torch, dev))
     # per-kernel times of the batched phases (launched one by one)
     b.profile(True)
     b.step(3)
@@ -274,7 +271,7 @@ def run_batched(alelb, torch, dev, world, rank, args):
     b.close()
     total_nodes = n_total
     return {"value": total_nodes * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "steps": K,
-            "cases": len(I.batched_sweep()) if world == 1 else f"{len(cases)} of 32 per rank",
+            "cases": len(sweep) if world == 1 else f"{len(cases)} of {len(sweep)} on rank {rank}",
             "nodes": total_nodes, "cases_finite_after_timing": finite, "tuned_launch_shapes": choice,
             "l2": "inputs larger than L2 (FP32 populations of all cases about 585 MB, double-buffered)",
             "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt.items()},
@@ -512,10 +509,8 @@ def run_ours(args):
     ms32, kt32, info32 = timed(alelb.PREC_FP32_DEV, K, W, True)
     clocks = sampler.stop()
     ms64, kt64, info64 = timed(alelb.PREC_FP64, max(2, K // 4), W, True)
-    if world > 1:
-        t = torch.tensor([ms32, ms64], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms32, ms64 = float(t[0]), float(t[1])
+    from paper_2002_04353_gb300 import shard
+    ms32, ms64 = shard.max_over_ranks(ms32, torch, dev), shard.max_over_ranks(ms64, torch, dev)
     N, E = case.mesh.n_nodes, case.mesh.n_elems
     value = world * N * K / (ms32 * 1e-3) / 1e6
     value64 = world * N * max(2, K // 4) / (ms64 * 1e-3) / 1e6
