@@ -136,6 +136,7 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.nb = B.put(T.nb, st);
     D.nbf = B.put(T.nbf, st);
     m->d_wedges = B.put(T.wedges, st);
+    m->d_n2o = B.put(T.node_new2old, st);
     m->nw = (int)T.wedges.size();
     m->mst = T.host_map();
     m->mst.ms = B.put(T.ms, st);
@@ -242,15 +243,18 @@ __global__ void k_fill_uniform(StateDev<S> st, int N, const double *consts, doub
 }
 
 // Full FP64 populations <-> stored deviations (internal order).
+// full and fields are in the caller's node order: internal node a is
+// caller node n2o[a].
 template <class S>
 __global__ void k_import(StateDev<S> st, int N, const double *consts, const double *full,
-                         const double *fields, int have_fields, double Cv)
+                         const double *fields, int have_fields, double Cv, const int *n2o)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
+    const int o = n2o[a];
     double r = 0, jx = 0, jy = 0, e2 = 0;
     for (int i = 0; i < NQ; ++i) {
-        double f = full[i * N + a], g = full[(NQ + i) * N + a];
+        double f = full[i * N + o], g = full[(NQ + i) * N + o];
         fg_put(st.post, i, a, N, f - consts[i], g - consts[NQ + i]);
         r += f;
         jx += c_cx[i] * f;
@@ -258,10 +262,10 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
         e2 += g;
     }
     if (have_fields) {
-        st.rho[a] = (fld_t<S>)fields[a];
-        st.ux[a] = (fld_t<S>)fields[N + a];
-        st.uy[a] = (fld_t<S>)fields[2 * N + a];
-        st.T[a] = (fld_t<S>)fields[3 * N + a];
+        st.rho[a] = (fld_t<S>)fields[o];
+        st.ux[a] = (fld_t<S>)fields[N + o];
+        st.uy[a] = (fld_t<S>)fields[2 * N + o];
+        st.T[a] = (fld_t<S>)fields[3 * N + o];
     } else {
         double ux = jx / r, uy = jy / r, E = e2 / (2 * r);
         st.rho[a] = (fld_t<S>)r;
@@ -272,22 +276,24 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
 }
 
 template <class S>
-__global__ void k_export(StateDev<S> st, int N, const double *consts, double *full, double *fields)
+__global__ void k_export(StateDev<S> st, int N, const double *consts, double *full, double *fields,
+                         const int *n2o)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
+    const int o = n2o[a];
     if (full)
         for (int i = 0; i < NQ; ++i) {
             double f, g;
             fg_get(st.post, i, a, N, f, g);
-            full[i * N + a] = f + consts[i];
-            full[(NQ + i) * N + a] = g + consts[NQ + i];
+            full[i * N + o] = f + consts[i];
+            full[(NQ + i) * N + o] = g + consts[NQ + i];
         }
     if (fields) {
-        fields[a] = (double)st.rho[a];
-        fields[N + a] = (double)st.ux[a];
-        fields[2 * N + a] = (double)st.uy[a];
-        fields[3 * N + a] = (double)st.T[a];
+        fields[o] = (double)st.rho[a];
+        fields[N + o] = (double)st.ux[a];
+        fields[2 * N + o] = (double)st.uy[a];
+        fields[3 * N + o] = (double)st.T[a];
     }
 }
 
@@ -480,7 +486,6 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     with_state(s, [&](auto &sx, auto &) { put_state(s->buf, sx, N, st); });
     s->d_consts = s->buf.alloc<double>(4 * NQ, st);
     s->d_scratch = s->buf.alloc<double>((size_t)22 * N, st);
-    if (st == cudaSuccess) st = cudaHostAlloc((void **)&s->h_pinned, (size_t)22 * N * sizeof(double), 0);
     s->d_err = s->buf.alloc<int>(1, st);
     s->d_stats = s->buf.alloc<unsigned long long>(4, st);
     if (st == cudaSuccess) st = cudaMemset(s->d_stats, 0, 4 * sizeof(unsigned long long));
@@ -517,7 +522,6 @@ extern "C" void alelb_solver_destroy(alelb_solver *s)
     flush_prof(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     s->buf.release();
-    if (s->h_pinned) cudaFreeHost(s->h_pinned);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s; // never touches the mesh: it may already be gone
 
@@ -559,25 +563,29 @@ extern "C" alelb_status alelb_time(alelb_solver *s, double *t, int64_t *step)
 }
 
 namespace {
-alelb_status export_state(alelb_solver *s, bool pops, const double **full, const double **fields)
+// Device state -> the caller's host arrays, in the caller's node order (the
+// permutation runs on the device; each array is one copy).  Null pointers
+// are skipped.
+alelb_status export_to_host(alelb_solver *s, double *f, double *g, double *const fld[4])
 {
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
+    const bool pops = f || g;
     double *dfull = pops ? s->d_scratch : nullptr;
     double *dfields = s->d_scratch + (size_t)18 * N;
     with_state(s, [&](auto &sx, auto &) {
-        k_export<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, dfull, dfields);
+        k_export<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, dfull, dfields, m->d_n2o);
     });
     cudaError_t st = cudaGetLastError();
-    if (st == cudaSuccess && pops)
-        st = cudaMemcpyAsync(s->h_pinned, dfull, (size_t)18 * N * sizeof(double),
-                             cudaMemcpyDeviceToHost, s->stream);
-    if (st == cudaSuccess)
-        st = cudaMemcpyAsync(s->h_pinned + (size_t)18 * N, dfields, (size_t)4 * N * sizeof(double),
-                             cudaMemcpyDeviceToHost, s->stream);
+    const size_t plane = (size_t)9 * N * sizeof(double);
+    if (st == cudaSuccess && f) st = cudaMemcpyAsync(f, s->d_scratch, plane, cudaMemcpyDeviceToHost, s->stream);
+    if (st == cudaSuccess && g)
+        st = cudaMemcpyAsync(g, s->d_scratch + (size_t)9 * N, plane, cudaMemcpyDeviceToHost, s->stream);
+    for (int c = 0; c < 4 && st == cudaSuccess; ++c)
+        if (fld && fld[c])
+            st = cudaMemcpyAsync(fld[c], dfields + (size_t)c * N, (size_t)N * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
-    *full = s->h_pinned;
-    *fields = s->h_pinned + (size_t)18 * N;
     return alelb_sync(s);
 }
 } // namespace
@@ -585,36 +593,14 @@ alelb_status export_state(alelb_solver *s, bool pops, const double **full, const
 extern "C" alelb_status alelb_moments(alelb_solver *s, double *rho, double *ux, double *uy, double *T)
 {
     if (!s) return ALELB_ERR_ARG;
-    const double *full, *fields;
-    alelb_status r = export_state(s, false, &full, &fields);
-    if (r != ALELB_OK) return r;
-    const int N = s->mesh->T.N;
-    const int *n2o = s->mesh->T.node_new2old.data();
-    double *outs[4] = {rho, ux, uy, T};
-    for (int c = 0; c < 4; ++c)
-        if (outs[c])
-            for (int a = 0; a < N; ++a) outs[c][n2o[a]] = fields[(size_t)c * N + a];
-    return ALELB_OK;
+    double *const fld[4] = {rho, ux, uy, T};
+    return export_to_host(s, nullptr, nullptr, fld);
 }
 
 extern "C" alelb_status alelb_get_pops(alelb_solver *s, double *f, double *g)
 {
     if (!s) return ALELB_ERR_ARG;
-    const double *full, *fields;
-    alelb_status r = export_state(s, true, &full, &fields);
-    if (r != ALELB_OK) return r;
-    const int N = s->mesh->T.N;
-    const int *n2o = s->mesh->T.node_new2old.data();
-    for (int i = 0; i < NQ; ++i) {
-        const double *fi = full + (size_t)i * N, *gi = full + (size_t)(NQ + i) * N;
-        double *fo = f ? f + (size_t)i * N : nullptr, *go = g ? g + (size_t)i * N : nullptr;
-        for (int a = 0; a < N; ++a) {
-            int o = n2o[a];
-            if (fo) fo[o] = fi[a];
-            if (go) go[o] = gi[a];
-        }
-    }
-    return ALELB_OK;
+    return export_to_host(s, f, g, nullptr);
 }
 
 extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const double *g,
@@ -623,41 +609,23 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
 {
     if (!s || !f || !g) return ALELB_ERR_ARG;
     const int N = s->mesh->T.N;
-    const int *n2o = s->mesh->T.node_new2old.data();
-    // wait for earlier transfers out of the staging buffer
-    cudaError_t st = cudaStreamSynchronize(s->stream);
-    if (st != cudaSuccess) return cuda_fail(s, st);
-    double *full = s->h_pinned, *fields = s->h_pinned + (size_t)18 * N;
-    bool have = rho && ux && uy && T;
-    for (int i = 0; i < NQ; ++i) {
-        double *fo = full + (size_t)i * N, *go = full + (size_t)(NQ + i) * N;
-        const double *fi = f + (size_t)i * N, *gi = g + (size_t)i * N;
-        for (int a = 0; a < N; ++a) {
-            int o = n2o[a];
-            fo[a] = fi[o];
-            go[a] = gi[o];
-        }
-    }
-    if (have)
-        for (int a = 0; a < N; ++a) {
-            int o = n2o[a];
-            fields[a] = rho[o];
-            fields[(size_t)N + a] = ux[o];
-            fields[(size_t)2 * N + a] = uy[o];
-            fields[(size_t)3 * N + a] = T[o];
-        }
-    st = cudaMemcpyAsync(s->d_scratch, full, (size_t)18 * N * sizeof(double), cudaMemcpyHostToDevice,
-                         s->stream);
-    if (st == cudaSuccess && have)
-        st = cudaMemcpyAsync(s->d_scratch + (size_t)18 * N, fields, (size_t)4 * N * sizeof(double),
+    const bool have = rho && ux && uy && T;
+    const size_t plane = (size_t)9 * N * sizeof(double);
+    cudaError_t st = cudaMemcpyAsync(s->d_scratch, f, plane, cudaMemcpyHostToDevice, s->stream);
+    if (st == cudaSuccess)
+        st = cudaMemcpyAsync(s->d_scratch + (size_t)9 * N, g, plane, cudaMemcpyHostToDevice, s->stream);
+    const double *fl[4] = {rho, ux, uy, T};
+    for (int c = 0; c < 4 && have && st == cudaSuccess; ++c)
+        st = cudaMemcpyAsync(s->d_scratch + (size_t)(18 + c) * N, fl[c], (size_t)N * sizeof(double),
                              cudaMemcpyHostToDevice, s->stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
     with_state(s, [&](auto &sx, auto &) {
         k_import<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch,
-                                                          s->d_scratch + (size_t)18 * N, have, s->Cv);
+                                                          s->d_scratch + (size_t)18 * N, have, s->Cv,
+                                                          s->mesh->d_n2o);
     });
     st = cudaGetLastError();
-    if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream);
+    if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the caller's arrays are free again
     if (st != cudaSuccess) return cuda_fail(s, st);
     s->t = t;
     return ALELB_OK;

@@ -85,6 +85,7 @@ struct alelb_mesh {
     MeshDev dev{};
     MapStatic mst{};
     int2 *d_wedges = nullptr;
+    int *d_n2o = nullptr; // [N] caller's node number of each internal node
     int nw = 0;
     DevBuf buf;
 };
@@ -107,8 +108,7 @@ struct alelb_solver {
     KinParams<float> kf{};
     double consts[4 * NQ] = {0};
     double *d_consts = nullptr;
-    double *d_scratch = nullptr; // 22 N doubles: import/export staging
-    double *h_pinned = nullptr;  // 22 N doubles of page-locked host staging
+    double *d_scratch = nullptr; // 22 N doubles: import/export staging (caller's node order)
     int *d_err = nullptr;
     unsigned long long *d_stats = nullptr; // [0]: element walks run by the propagation kernel
     double *d_out = nullptr;
