@@ -368,7 +368,7 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                        s->d_err, s->d_stats);
             break;
         case KT_FAST:
-            launch_pdl(k_stream_fast<S, A>, dim3((N + 127) / 128, NQ / FAST_G), dim3(128), s->stream, m->dev,
+            launch_pdl(k_stream_fast<S, A>, dim3((N + FAST_BS - 1) / FAST_BS, NQ / FAST_G), dim3(FAST_BS), s->stream, m->dev,
                        m->mst, sf, K, st);
             break;
         case KT_SLOW: {

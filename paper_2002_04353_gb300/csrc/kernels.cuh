@@ -582,9 +582,15 @@ __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapSta
     for (int j = 0; j < G; ++j) append_pop(st, a, M.N, i0 + j, code[j]);
 }
 
+// Threads per block of the single-case propagation kernel.
+#ifndef ALELB_FAST_BS
+#define ALELB_FAST_BS 128
+#endif
+constexpr int FAST_BS = ALELB_FAST_BS;
+
 // Grid (node blocks, 9 / FAST_G direction groups).
 template <class S, class A>
-__global__ void __launch_bounds__(128) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
+__global__ void __launch_bounds__(FAST_BS) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
                                                      KinParams<A> K, StateDev<S> st)
 {
     wait_prior_grid();
