@@ -98,6 +98,9 @@ template <class P> __device__ __forceinline__ void fg_copy(P *dst, const P *src,
     }
 }
 
+// Requests the line holding p into L1 (no result; a later load hits there).
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // Waits until the grids this one depends on have completed and their
 // stores are visible.  The step's kernels are launched with programmatic
 // stream serialization: a kernel's blocks may start while the previous
@@ -613,6 +616,21 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
     const int N = M.N;
     {
         const int a = code / NQ, i = code % NQ;
+        // the entry's chain of dependent loads is its latency: the node's
+        // and the cached element's records are requested into L1 up front
+        prefetch_l1(M.X + a);
+        prefetch_l1(M.bdist + a);
+        prefetch_l1(M.nb_ptr + a);
+        prefetch_l1(M.fan_ptr + a);
+        prefetch_l1(M.conek + a);
+        const int hint = st.cache[i * N + a];
+        if (hint >= 0) {
+            const int e = hint & 0x0fffffff;
+            prefetch_l1(M.conn + 6 * e);
+            prefetch_l1(M.evf + 3 * e);
+            prefetch_l1(M.evf + 3 * e + 2);
+            prefetch_l1(M.ejf + 2 * e + 1);
+        }
         const float4 Xf = M.Xf[a];
         const FastMap F = fast_map(MS, sf, a, Xf);
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
@@ -648,7 +666,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             src = -1;
             if (hits) atomicAdd(hits, 1ull);
         } else {
-            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err, st.cache[i * N + a], clear);
+            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err, hint, clear);
         }
         A fi = 0, gi = 0;
         if (src >= 0) {
