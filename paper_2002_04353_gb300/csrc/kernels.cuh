@@ -1,5 +1,5 @@
-// kernels.cuh -- the three kernels of one time step plus the element-choice
-// report and the force reduction.
+// kernels.cuh -- the kernels of one time step plus the element-choice
+// report and the force reduction.  The plain FP64 form:
 //
 //   k_stream   propagation (Eq. Propagation): transformed velocities,
 //              departure points, element walk, P2 interpolation of the
@@ -10,7 +10,9 @@
 //              Eqs. Ph_Derivative / FE_Derivative)
 //   k_collide  X_a = -d_a D_a, then the collision of Eqs. feqn/geqn
 //
-// One thread per node.  Populations are stored by direction: FP64 buffers
+// and the deviation forms' propagation (k_stream_fast, k_stream_slow,
+// k_moments, below), which share k_deriv1 and k_collide.  One thread per
+// node unless noted.  Populations are stored by direction: FP64 buffers
 // as pop[q * N + node] with q = 0..8 for f and 9..17 for g, the deviation
 // forms as (f_i, g_i) pairs, pop[2 (i N + node) + {0, 1}] (fg_get).
 #pragma once
@@ -382,14 +384,21 @@ __global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScal
 }
 
 // ---------------------------------------------------------------------------
-// The FP32-deviation propagation, split by path so that the rare exact
+// The deviation-form propagation, split by path so that the rare exact
 // work does not stall the warps of the common case:
-//   k_stream_fast  per node: FP32 map; every population whose previous-step
-//                  element is verified (fast_decide) is interpolated and
-//                  stored; the others are appended to a work list
-//   k_stream_slow  per listed population: FP64 map and departure point,
-//                  exact walk, interpolation or the missing-population
-//                  condition (Sec. IV.A); refreshes the element cache
+//   k_stream_fast  per population: FP32 map; a population whose
+//                  previous-step element is verified (fast_decide) is
+//                  interpolated and stored, one certified missing by the
+//                  exterior cone takes the far-field equilibria or marks
+//                  the node's wall mask; the others are appended to a work
+//                  list by direction
+//   k_stream_slow  per listed entry: the nearby-edge certificates, the
+//                  exact check of the cached element, else the walk on
+//                  certified FP32 predicates with exact fallback; then the
+//                  interpolation or the missing-population condition
+//                  (Sec. IV.A); refreshes the element cache.  A listed wall
+//                  node runs the wall condition once for its masked
+//                  directions
 //   k_moments      per node: moments, Q'_aaa and mu/(rho T) of the streamed
 //                  populations; resets the work list
 // ---------------------------------------------------------------------------
