@@ -87,9 +87,13 @@ enum {
     ALELB_FLAG_COLLIDE_OFF = 2,    /* pure propagation, no collision (tests) */
     ALELB_FLAG_LITERAL_VG = 4,     /* c^_i = g^{-1,T} c_i - V_G as printed in Eq. 7 */
     ALELB_FLAG_BC_EQUILIBRIUM = 8, /* missing populations: equilibrium part only */
-    ALELB_FLAG_SLIP_WALL = 16      /* slip (inviscid) walls: at wall nodes the target velocity is
+    ALELB_FLAG_SLIP_WALL = 16,     /* slip (inviscid) walls: at wall nodes the target velocity is
                                       V_G plus the tangential part of u_B - V_G at the probe B,
                                       and the non-equilibrium part is dropped (no wall shear) */
+    ALELB_FLAG_MIDPOINT = 32       /* the transformed velocities c^_i of a step t_n -> t_{n+1}
+                                      use g and V_G at t_{n+1/2} (Eq. 7 at the midpoint time;
+                                      the wall condition and the derivatives stay at t_{n+1}).
+                                      Single-case solvers only: alelb_batch_create refuses it */
 };
 
 /* Mesh description (computational domain, Sec. III).  Straight-sided

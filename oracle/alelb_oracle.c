@@ -13,7 +13,8 @@
  * Everything is FP64, one node at a time, in the order the paper states.
  * Where the paper is silent the reading used is stated at the spot:
  *   R1  transformed velocity  c^_i = g^{-1,T} (c_i - V_G)        (Eq. 7 + chain rule)
- *   R2  map, Jacobian and V_G evaluated at the arrival time t_{n+1}
+ *   R2  map, Jacobian and V_G evaluated at the arrival time t_{n+1}; flag
+ *       MIDPOINT evaluates those of the transformed velocities at t_{n+1/2}
  *   R3  q*_a = q^eq_a + 2 u_b (P_ab - P^eq_ab)   (Table I's q* as printed drops q^eq)
  *   R4  forcing enters as + dt*phi_i with phi from the same time level; the
  *       equilibria use the plain velocity sum(c f)/rho
@@ -61,7 +62,7 @@ static const int CYI[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 enum { ST_OK = 0, ST_ARG = -1, ST_OOM = -2, ST_MESH = -4, ST_MAP = -5, ST_LOCATE = -6,
        ST_NONFINITE = -7 };
 enum { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQUILIBRIUM = 8,
-       FLAG_SLIP_WALL = 16 };
+       FLAG_SLIP_WALL = 16, FLAG_MIDPOINT = 32 };
 enum { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
        MK_BLENDED = 5 };
 enum { EK_INTERIOR = 0, EK_WALL = 1, EK_FAR = 2 };
@@ -1301,17 +1302,28 @@ static double interp_field(const orc_t *o, int e, double sx, double sy, double p
 
 /* Semi-Lagrangian FE propagation (Eq. Propagation) of all populations of
    one node; the missing ones from the Grad boundary condition. */
-static int stream_node(orc_t *o, int a, const mscal_t *S)
+/* Sd: map scalars of the transformed velocities (the arrival time S, or
+   t_{n+1/2} under FLAG_MIDPOINT, reading R2); the wall condition and the
+   derivatives keep S. */
+static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd)
 {
     int nn = o->nn;
     const double *gi = &o->gi[4 * a];
     double xX, xY, yX, yY, Vx, Vy;
     motion_node(o, a, S, &xX, &xY, &yX, &yY, &Vx, &Vy);
+    double gd[4], Vdx = Vx, Vdy = Vy;
+    const double *gdep = gi;
+    if (Sd != S) {
+        double dxX, dxY, dyX, dyY;
+        motion_node(o, a, Sd, &dxX, &dxY, &dyX, &dyY, &Vdx, &Vdy);
+        if (metric_inverse(dxX, dxY, dyX, dyY, gd)) return ST_MAP;
+        gdep = gd;
+    }
     int have_bc = 0;
     double tgt[4], du[4], dT[2];
     for (int i = 0; i < NQ; ++i) {
         double chx, chy, px, py, sx, sy;
-        departure(o, a, gi, Vx, Vy, i, &chx, &chy, &px, &py);
+        departure(o, a, gdep, Vdx, Vdy, i, &chx, &chy, &px, &py);
         int kind;
         int e = choose_element(o, a, chx, chy, px, py, &sx, &sy, &kind);
         if (e == -3) return ST_LOCATE;
@@ -1407,8 +1419,13 @@ static int step_once(orc_t *o)
 {
     int nn = o->nn;
     double t1 = o->t + 1.0;
-    mscal_t S;
+    mscal_t S, Sh;
     motion_scalars(o, t1, &S);
+    const mscal_t *Sd = &S;
+    if (o->K.flags & FLAG_MIDPOINT) { /* transformed velocities at t_{n+1/2} */
+        motion_scalars(o, t1 - 0.5, &Sh);
+        Sd = &Sh;
+    }
     for (int a = 0; a < nn; ++a) {
         double xX, xY, yX, yY, Vx, Vy;
         motion_node(o, a, &S, &xX, &xY, &yX, &yY, &Vx, &Vy);
@@ -1416,7 +1433,7 @@ static int step_once(orc_t *o)
     }
     /* propagation */
     for (int a = 0; a < nn; ++a) {
-        int st = stream_node(o, a, &S);
+        int st = stream_node(o, a, &S, Sd);
         if (st) return st;
     }
     /* moments, Q'_aaa = rho u_a (1 - 3T) - rho u_a^3 (Eq. DeviationTerms), mu/(rho T) */

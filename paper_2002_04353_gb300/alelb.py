@@ -29,6 +29,7 @@ FLAG_COLLIDE_OFF = 2
 FLAG_LITERAL_VG = 4
 FLAG_BC_EQUILIBRIUM = 8
 FLAG_SLIP_WALL = 16
+FLAG_MIDPOINT = 32
 NQ = 9
 
 # every symbol include/alelb.h declares

@@ -343,6 +343,9 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
     const bool phi = !(s->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF));
     const bool fast = s->prec != ALELB_PREC_FP64;
     const MapScalarsF sf = to_f32(sc, m->T);
+    // the transformed velocities' map: arrival time, or t_{n+1/2} (flag)
+    const MapScalars scd = (s->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, s->t + 0.5) : sc;
+    const MapScalarsF sfd = to_f32(scd, m->T);
     int seq[KT_N], ns = 0;
     if (fast) {
         seq[ns++] = KT_FAST;
@@ -364,12 +367,12 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
         }
         switch (k) {
         case KT_STREAM:
-            launch_pdl(k_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->dev, m->mst, sc, K, st,
+            launch_pdl(k_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->dev, m->mst, sc, scd, K, st,
                        s->d_err, s->d_stats);
             break;
         case KT_FAST:
             launch_pdl(k_stream_fast<S, A>, dim3((N + FAST_BS - 1) / FAST_BS, NQ / FAST_G), dim3(FAST_BS), s->stream, m->dev,
-                       m->mst, sf, K, st);
+                       m->mst, sfd, K, st);
             break;
         case KT_SLOW: {
             // every block resident at once: the list is spread over all
@@ -380,11 +383,11 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                 return v > 0 ? v : 1;
             }();
             launch_pdl(k_stream_slow<S, A>, dim3(per_sm * s->n_sm), dim3(128), s->stream, m->dev, m->mst, sc, sf,
-                       K, st, s->d_err, s->d_stats, (const int *)(s->mlp ? s->d_prop : nullptr));
+                       scd, sfd, K, st, s->d_err, s->d_stats, (const int *)(s->mlp ? s->d_prop : nullptr));
             break;
         }
         case KT_PROPOSE:
-            mlp_propose(s, sf);
+            mlp_propose(s, sfd);
             break;
         case KT_MOMENTS:
             launch_pdl(k_moments<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, K, st, N, s->d_err);
@@ -852,7 +855,8 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     }
     K.flags = p->flags;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
-    k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, K, sd, err, nullptr);
+    const MapScalars scd = (p->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, t + 0.5) : sc;
+    k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, scd, K, sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
         k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), sd);
     k_collide<double, double, false><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), K,

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) kb_stream(const CaseDev<S, A> *__restrict
     __syncthreads();
     const CaseDev<S, A> &C = sh.C();
     const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
-    if (a < C.M.N) stream_plain_node(C.M, C.MS, sh.SC(), C.K, C.st, C.err, count ? C.stats : nullptr, a);
+    if (a < C.M.N) stream_plain_node(C.M, C.MS, sh.SC(), sh.SC(), C.K, C.st, C.err, count ? C.stats : nullptr, a);
 }
 
 template <class S, class A>
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
         const CaseDev<S, A> &C = cases[c];
         const int entry = C.st.work[(size_t)i * C.M.N + (w - pre[lo])];
         if (i < NQ) {
-            stream_slow_item(C.M, C.MS, sc[c], sf[c], C.K, C.st, C.err, entry);
+            stream_slow_item(C.M, C.MS, sc[c], sf[c], sc[c], sf[c], C.K, C.st, C.err, entry);
         } else {
             const unsigned mask = C.st.wmask[entry];
             if (count && C.stats) atomicAdd(C.stats, (unsigned long long)__popc(mask));
@@ -500,7 +500,9 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         if (!cases[c] || !cases[c]->mesh) return ALELB_ERR_ARG;
         if (cases[c]->prec != cases[0]->prec) return ALELB_ERR_ARG;
         // the batched kernels are built for the FP64 and FP32-deviation forms
+        // and the arrival-time transformed velocities
         if (cases[c]->prec != ALELB_PREC_FP64 && cases[c]->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
+        if (cases[c]->flags & ALELB_FLAG_MIDPOINT) return ALELB_ERR_ARG;
         for (int d = 0; d < c; ++d)
             if (cases[d] == cases[c]) return ALELB_ERR_ARG;
     }

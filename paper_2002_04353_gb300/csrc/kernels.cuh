@@ -223,11 +223,13 @@ __device__ __forceinline__ void owner_grad_linear(const MeshDev &M, int a, const
 
 // The plain FP64 propagation: every population through the FP64 departure
 // point and the exact walk, one thread per node.
+// scd: map scalars of the transformed velocities (sc, or those of the
+// midpoint time under FLAG_MIDPOINT); the wall condition keeps sc.
 template <class S, class A>
 __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapStatic &MS,
-                                                  const MapScalars &sc, const KinParams<A> &K,
-                                                  const StateDev<S> &st, int *err,
-                                                  unsigned long long *stats, int a)
+                                                  const MapScalars &sc, const MapScalars &scd,
+                                                  const KinParams<A> &K, const StateDev<S> &st,
+                                                  int *err, unsigned long long *stats, int a)
 {
     const int N = M.N;
     const double2 Xa = M.X[a];
@@ -244,7 +246,7 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
         {
             if (!have64) {
                 double xX, xY, yX, yY;
-                map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+                map_node(MS, scd, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
                 metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
                 mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
                 have64 = true;
@@ -293,7 +295,7 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
     }
     if (stats && walks) atomicAdd(stats, (unsigned long long)walks);
     if (miss) {
-        if (!have64) { // cannot happen (a missing population comes from a walk)
+        if (!have64 || (K.flags & FLAG_MIDPOINT)) { // the wall condition's map: arrival time
             double xX, xY, yX, yY;
             map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
             metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
@@ -374,13 +376,13 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
 }
 
 template <class S, class A>
-__global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc,
+__global__ void __launch_bounds__(128) k_stream(MeshDev M, MapStatic MS, MapScalars sc, MapScalars scd,
                                                 KinParams<A> K, StateDev<S> st, int *err,
                                                 unsigned long long *stats)
 {
     wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < M.N) stream_plain_node(M, MS, sc, K, st, err, stats, a);
+    if (a < M.N) stream_plain_node(M, MS, sc, scd, K, st, err, stats, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,9 +617,13 @@ __global__ void __launch_bounds__(FAST_BS) k_stream_fast(MeshDev M, MapStatic MS
 // certified test that accepts previous-step elements accepts it, with the
 // interpolation offset formed as the FP32 walk forms it, so the result is
 // the walk's bit for bit.  hits (may be null) counts the accepted ones.
+// sc, sf: the map at the arrival time (wall condition); scd, sfd: the map
+// of the transformed velocities (the same, or the midpoint time under
+// FLAG_MIDPOINT).
 template <class S, class A>
 __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStatic &MS,
                                                  const MapScalars &sc, const MapScalarsF &sf,
+                                                 const MapScalars &scd, const MapScalarsF &sfd,
                                                  const KinParams<A> &K, const StateDev<S> &st,
                                                  int *err, int code, int pc = -1,
                                                  unsigned long long *hits = nullptr)
@@ -641,14 +647,15 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             prefetch_l1(M.ejf + 2 * e + 1);
         }
         const float4 Xf = M.Xf[a];
-        const FastMap F = fast_map(MS, sf, a, Xf);
+        const FastMap F = fast_map(MS, sfd, a, Xf);
+        const FastMap Fb = (K.flags & FLAG_MIDPOINT) ? fast_map(MS, sf, a, Xf) : F; // wall condition
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
         float qx = 0.f, qy = 0.f;
         int src;
         int clear = -1; // the segment test of the nearby-edge pass, for slow_decide
         const int ck = F.ok && !literal ? certified_missing(M, F, a, i, &clear) : 0;
         if (ck == 1) { // certified to meet a wall first
-            stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
+            stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, Fb, 1u << i);
             return;
         }
         if (ck == 2) { // certified to leave through the far field
@@ -675,7 +682,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             src = -1;
             if (hits) atomicAdd(hits, 1ull);
         } else {
-            L = slow_decide(M, MS, sc, F, Xf, a, i, literal, qx, qy, src, err, hint, clear);
+            L = slow_decide(M, MS, scd, F, Xf, a, i, literal, qx, qy, src, err, hint, clear);
         }
         A fi = 0, gi = 0;
         if (src >= 0) {
@@ -698,7 +705,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             fi = K.finf[i];
             gi = K.ginf[i];
         } else {
-            stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, F, 1u << i);
+            stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, Fb, 1u << i);
             return;
         }
         fg_put(st.str, i, a, N, fi, gi);
@@ -722,13 +729,14 @@ __device__ __forceinline__ unsigned spread_stride() { return gridDim.x * blockDi
 template <class S, class A>
 __device__ __forceinline__ void slow_entry(const MeshDev &M, const MapStatic &MS,
                                            const MapScalars &sc, const MapScalarsF &sf,
+                                           const MapScalars &scd, const MapScalarsF &sfd,
                                            const KinParams<A> &K, const StateDev<S> &st, int *err,
                                            const unsigned *pre, unsigned w, const int *prop,
                                            unsigned long long *stats)
 {
     if (w < pre[NQ]) {
-        stream_slow_item(M, MS, sc, sf, K, st, err, work_at(st.work, M.N, pre, w), prop ? prop[w] : -1,
-                         prop && stats ? stats + 1 : nullptr);
+        stream_slow_item(M, MS, sc, sf, scd, sfd, K, st, err, work_at(st.work, M.N, pre, w),
+                         prop ? prop[w] : -1, prop && stats ? stats + 1 : nullptr);
     } else {
         const int a = st.work[(size_t)NQ * M.N + (w - pre[NQ])];
         const unsigned mask = st.wmask[a];
@@ -739,9 +747,9 @@ __device__ __forceinline__ void slow_entry(const MeshDev &M, const MapStatic &MS
 
 template <class S, class A>
 __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, MapScalars sc,
-                                                     MapScalarsF sf, KinParams<A> K, StateDev<S> st,
-                                                     int *err, unsigned long long *stats,
-                                                     const int *prop)
+                                                     MapScalarsF sf, MapScalars scd, MapScalarsF sfd,
+                                                     KinParams<A> K, StateDev<S> st, int *err,
+                                                     unsigned long long *stats, const int *prop)
 {
     wait_prior_grid();
     __shared__ unsigned pre[NQ + 1];
@@ -751,7 +759,7 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
     const unsigned total = n + st.wcount[NQ];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
     for (unsigned w = spread_first(); w < total; w += spread_stride())
-        slow_entry(M, MS, sc, sf, K, st, err, pre, w, prop, stats);
+        slow_entry(M, MS, sc, sf, scd, sfd, K, st, err, pre, w, prop, stats);
 }
 
 

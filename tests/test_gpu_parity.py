@@ -345,3 +345,46 @@ def test_16bit_element_choices_and_info(prec):
     eo, ko = o.locate(t + 1.0)
     eg, kg = s.locate(t + 1.0, use_cache=True)
     assert np.array_equal(eo, eg) and np.array_equal(ko, kg)
+
+
+# ---------------------------------------------------------------------------
+# transformed velocities at the midpoint time (flag MIDPOINT)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("motion_name", ["omesh_pitch", "omesh_blended", "omesh_plunge"])
+def test_midpoint_variant_fp64_and_fp32(motion_name):
+    mesh, motion = LOC_CASES[motion_name]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o, m, s = _pair(mesh, motion, flow, flags=O.FLAG_MIDPOINT)
+    o.step(4)
+    s.lb_step(4)
+    _compare64(o, s, f"{motion_name} midpoint FP64")
+    o2, m2, s2 = _pair(mesh, motion, flow, prec=alelb.PREC_FP32_DEV, flags=O.FLAG_MIDPOINT)
+    o2.step(4)
+    s2.lb_step(4)
+    _compare_mixed(o2, s2, f"{motion_name} midpoint FP32")
+    # the flag changes the result (the map moves between t_{n+1/2} and t_{n+1})
+    o3 = O.Oracle(mesh, motion, flow)
+    o3.step(4)
+    assert _rel(o3.state()["f"], o.state()["f"]) > 1e-12
+
+
+def test_midpoint_variant_fast_path_decisions_bitwise():
+    mesh, motion = LOC_CASES["omesh_pitch"]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o = O.Oracle(mesh, motion, flow, flags=O.FLAG_MIDPOINT)
+    s = alelb.Solver(alelb.Mesh(mesh, motion), flow, alelb.PREC_FP32_DEV, flags=O.FLAG_MIDPOINT)
+    s.lb_step(5)
+    t, _ = s.time()
+    eo, ko = o.locate(t + 0.5)  # the next step's departure map time
+    eg, kg = s.locate(t + 0.5, use_cache=True)
+    assert np.array_equal(eo, eg) and np.array_equal(ko, kg)
+
+
+def test_batch_refuses_the_midpoint_variant():
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    s = alelb.Solver(alelb.Mesh(mesh, motion), flow, alelb.PREC_FP32_DEV, flags=O.FLAG_MIDPOINT)
+    with pytest.raises(alelb.AlelbError) as ex:
+        alelb.Batch([s])
+    assert ex.value.status == -1

@@ -403,6 +403,48 @@ def test_transformed_velocity_is_the_characteristic_slope(mot):
     assert worst_lit > 1e-3  # the printed form differs whenever g != I and V_G != 0
 
 
+def test_midpoint_variant_follows_the_characteristic_to_third_order():
+    """Flag MIDPOINT (reading R2's variant): the transformed velocities of a
+    step t_n -> t_{n+1} use g and V_G at t_{n+1/2}.  For the plunge map
+    y = Y - h sin(w t) (g = I, V_G = (0, -h w cos w t)), one step of pure
+    propagation of a field linear in Y reproduces it at the departure point,
+    so the departure offset reads off the result.  Closed forms: the
+    midpoint offset is -c_y - h w cos(w t_{n+1/2}), the arrival-time one
+    -c_y - h w cos(w t_{n+1}), the exact characteristic's
+    -c_y - h (sin w t_{n+1} - sin w t_n); the midpoint error is O(w^3), the
+    arrival-time one O(w^2)."""
+    L, h, w = 32.0, 2.0, 0.03
+    mesh = I.periodic_box(16, L, 0.2, seed=8)
+    mot = I.Motion.make(I.MOTION_PLUNGE, h, w)
+    fl = _flow()
+    Y = mesh.X[:, 1]
+    base_f = O.feq(1.0, 0.0, 0.0, 0.3)
+    base_g = O.geq(1.0, 0.0, 0.0, 0.3, CV)
+    slope = 1e-3 / L
+    f = base_f[:, None] * (1.0 + slope * Y[None, :])
+    g = base_g[:, None] * (1.0 + slope * Y[None, :])
+    n = mesh.n_nodes
+    t0 = 7.0
+    inner = (Y > 4.0) & (Y < L - 4.0)
+    got = {}
+    for name, flags in (("mid", O.FLAG_MIDPOINT), ("end", 0)):
+        o = O.Oracle(mesh, mot, fl, flags=flags | O.FLAG_COLLIDE_OFF | O.FLAG_PHI_OFF)
+        o.set_state(f, g, np.ones(n), np.zeros(n), np.zeros(n), np.full(n, 0.3), t=t0)
+        o.step(1)
+        fs = o.state()["f"]
+        got[name] = (fs / base_f[:, None] - 1.0) / slope - Y[None, :]  # Y_dp - Y per direction
+    t1 = t0 + 1.0
+    for i in range(9):
+        cy = CY[i]
+        mid = -cy - h * w * math.cos(w * (t1 - 0.5))
+        end = -cy - h * w * math.cos(w * t1)
+        exact = -cy - h * (math.sin(w * t1) - math.sin(w * t0))
+        assert np.abs(got["mid"][i, inner] - mid).max() < 1e-9
+        assert np.abs(got["end"][i, inner] - end).max() < 1e-9
+        assert abs(mid - exact) < 1.01 * h * w ** 3 / 24 + 1e-12
+        assert abs(end - exact) > 10 * abs(mid - exact)
+
+
 def test_mesh_velocity_is_time_derivative_of_the_map():
     mot = I.Motion.make(I.MOTION_BLENDED_PITCH, 0.1, 0.3, 0.01, 50.0, 0.0, 200.0, 1000.0)
     mesh = I.naca_omesh(32, 12, chord=200.0, R=4000.0, first=1.0)
