@@ -556,16 +556,20 @@ __device__ __forceinline__ void append_pop(const StateDev<S> &st, int a, int N, 
     }
 }
 
-// Directions per thread of the propagation kernels (single case, batch):
-// the grid's y extent is 9 / G; a thread evaluates the node's FP32 map once
-// for its G populations.
+// Directions per thread of the propagation kernels: the grid's y extent is
+// 9 / G; a thread evaluates the node's FP32 map once for its G populations.
+// One per thread hides the gathers' latency best on small meshes; nine
+// (one thread per node) evaluates each node's map once and wins on large
+// meshes with a rotating or deforming map (single case: FAST_G below
+// FAST_G_NODES nodes or for translations, else 9; the batch takes
+// BATCH_FAST_G).
 #ifndef ALELB_FAST_G
 #define ALELB_FAST_G 1
 #endif
 #ifndef ALELB_BATCH_FAST_G
 #define ALELB_BATCH_FAST_G 9
 #endif
-constexpr int FAST_G = ALELB_FAST_G, BATCH_FAST_G = ALELB_BATCH_FAST_G;
+constexpr int FAST_G = ALELB_FAST_G, BATCH_FAST_G = ALELB_BATCH_FAST_G, FAST_G_NODES = 300000;
 static_assert(NQ % FAST_G == 0 && NQ % BATCH_FAST_G == 0, "directions per thread");
 
 // Populations G y .. G y + G - 1 of node a (y = blockIdx.y): settled, or
@@ -602,13 +606,13 @@ __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapSta
 #endif
 constexpr int FAST_BS = ALELB_FAST_BS;
 
-// Grid (node blocks, 9 / FAST_G direction groups).
-template <class S, class A>
+// Grid (node blocks, 9 / G direction groups).
+template <class S, class A, int G>
 __global__ void __launch_bounds__(FAST_BS) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
                                                      KinParams<A> K, StateDev<S> st)
 {
     wait_prior_grid();
-    stream_fast_group<FAST_G>(M, MS, sf, K, st, blockIdx.x * blockDim.x + threadIdx.x);
+    stream_fast_group<G>(M, MS, sf, K, st, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // One listed population (code = 9 node + direction): exact decision, then
