@@ -388,3 +388,22 @@ def test_batch_refuses_the_midpoint_variant():
     with pytest.raises(alelb.AlelbError) as ex:
         alelb.Batch([s])
     assert ex.value.status == -1
+
+
+@pytest.mark.parametrize("prec", [alelb.PREC_FP32_DEV, alelb.PREC_BF16_DEV, alelb.PREC_FP16_DEV])
+@pytest.mark.parametrize("flags", [0, O.FLAG_MIDPOINT])
+def test_deviation_forms_on_a_tiny_mesh(prec, flags):
+    """A 3 x 3 periodic box (18 nodes: every warp partly empty, every
+    element touching the periodic seams), zero steps, then three."""
+    mesh = I.periodic_box(3, 6.0, 0.1, seed=9)
+    flow = I.Flow(mu=0.02, T_inf=0.2, u_inf=(0.01, 0.0))
+    st = _eq_state(mesh, flow, 0.01, seed=1)
+    motion = I.Motion.make(I.MOTION_SINE, 0.2, 6.0, 20.0, 0.0)
+    o, m, s = _pair(mesh, motion, flow, prec=prec, flags=flags, state=st)
+    s.lb_step(0)
+    o.step(3)
+    s.lb_step(3)
+    if prec == alelb.PREC_FP32_DEV:
+        _compare_mixed(o, s, "tiny mesh")
+    else:
+        _compare16(o, s, prec, flow, 3, "tiny mesh")
