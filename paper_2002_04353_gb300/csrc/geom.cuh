@@ -489,6 +489,19 @@ struct MeshDev {
     const uint8_t *nbf;    // kind | 4 when the node lies on the edge
 };
 
+// Element cache code of a population: element (bits 0-24) | node's local
+// index in it + 1 (bits 25-27; 7: not one of the node's elements; 0: not
+// recorded) | (sx + 1) << 28 | (sy + 1) << 30 (frame shift), or -1.
+constexpr int CACHE_ELEM = 0x01ffffff;
+ALELB_HD __forceinline__ int cache_code(const MeshDev &M, int e, int sx, int sy, int a)
+{
+    int lb = 7;
+    if (sx == 0 && sy == 0)
+        for (int k = 0; k < 6; ++k)
+            if (M.conn[6 * e + k] == a) lb = k + 1;
+    return e | (lb << 25) | ((sx + 1) << 28) | ((sy + 1) << 30);
+}
+
 // Radius of the per-node lists of nearby boundary edges (lattice units).
 // Every departure segment shorter than it lies in the disk that the list
 // covers.
@@ -957,17 +970,24 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
     const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
     const float chx = F.A11 * cx + F.A12 * cy - F.W1;
     const float chy = F.A21 * cx + F.A22 * cy - F.W2;
-    const float len = sqrtf(chx * chx + chy * chy);
-    if (!(c >= 0 && (c >> 28) == 5 && len > 4.0f * F.eq(i))) return false;
-    e = c & 0x0fffffff;
-    const int *cn = M.conn + 6 * e;
-    int l = -1;
+    // lengths compared squared (the margins have ample slack for the
+    // rounding of the squares; bdist carries a 1e-6 relative reserve)
+    const float len2 = chx * chx + chy * chy;
+    const float q4 = 4.0f * F.eq(i);
+    if (!(c >= 0 && (c >> 28) == 5 && len2 > q4 * q4)) return false;
+    e = c & CACHE_ELEM;
+    const int lb = (c >> 25) & 7; // node's local index + 1, 7 not own, 0 unknown
+    int l = lb == 7 ? -1 : lb - 1;
+    if (lb == 0) {
+        const int *cn = M.conn + 6 * e;
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-        if (cn[k] == a) l = k;
+        for (int k = 0; k < 6; ++k)
+            if (cn[k] == a) l = k;
+    }
     // near a boundary the exact path decides (with the segment certificate
     // against the node's nearby boundary edges)
-    if (!(len + F.eq(i) < bdist) && l < 0) return false;
+    const float room = bdist - F.eq(i);
+    if (l < 0 && !(room > 0.0f && len2 < room * room)) return false;
     const float4 J = M.ejf[2 * e + 1];
     if (l >= 0) {
         // the node is node l of element e: its local coordinates are exact
@@ -1232,10 +1252,12 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
             pr.Ya = Xa.y;
             bool have = false;
             if (hint >= 0 && (hint >> 28) == 5) {
-                const int ce = hint & 0x0fffffff;
-                bool own = false;
+                const int ce = hint & CACHE_ELEM;
+                const int lb = (hint >> 25) & 7;
+                bool own = lb != 0 && lb != 7;
+                if (lb == 0)
 #pragma unroll
-                for (int k = 0; k < 6; ++k) own |= M.conn[6 * ce + k] == a;
+                    for (int k = 0; k < 6; ++k) own |= M.conn[6 * ce + k] == a;
                 const float len = sqrtf(chx * chx + chy * chy);
                 const float eb = F.eq(i);
                 if (own || len + eb < M.bdist[a] ||

@@ -644,7 +644,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
         prefetch_l1(M.conek + a);
         const int hint = st.cache[i * N + a];
         if (hint >= 0) {
-            const int e = hint & 0x0fffffff;
+            const int e = hint & CACHE_ELEM;
             prefetch_l1(M.conn + 6 * e);
             prefetch_l1(M.evf + 3 * e);
             prefetch_l1(M.evf + 3 * e + 2);
@@ -693,7 +693,7 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             fg_get(st.post, i, src, N, fi, gi);
         } else if (L.e >= 0) {
             const int e = L.e;
-            st.cache[i * N + a] = e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
+            st.cache[i * N + a] = cache_code(M, e, L.sx, L.sy, a);
             const float4 J = M.ejf[2 * e + 1];
             A Nw[6];
             shape6<A>((A)(J.x * qx + J.y * qy), (A)(J.z * qx + J.w * qy), Nw);

@@ -217,6 +217,10 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
         return ALELB_ERR_ARG;
     }
     const int N = d->n_nodes, E = d->n_elems;
+    if (E > CACHE_ELEM) { // the element cache codes hold 25 bits of element
+        err = "more than 2^25 - 1 elements";
+        return ALELB_ERR_ARG;
+    }
     T.N = N;
     T.E = E;
     T.Lx = d->period[0] > 0 ? d->period[0] : 0.0;
