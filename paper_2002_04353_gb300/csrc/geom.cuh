@@ -935,7 +935,8 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     else if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE) eps_g = 2.0f * u;
     else if (MS.kind == MK_SINE) eps_g = 4.0f * u * (1.0f + G);
     float eps_det = 4.0f * G * eps_g + 3.0f * u * (fabsf(xX * yY) + fabsf(yX * xY));
-    float eps_A = (eps_g + G * eps_det / det) / det + 2.0f * u * Amax;
+    // (the bound's own roundings, a few u relative, vanish against its factor 2)
+    float eps_A = (eps_g + G * eps_det * inv) * inv + 2.0f * u * Amax;
     float eps_V = 8.0f * u * Vmag;
     float cv = 2.0f + 2.0f * Vmax;
     F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
