@@ -30,6 +30,7 @@ FLAG_LITERAL_VG = 4
 FLAG_BC_EQUILIBRIUM = 8
 FLAG_SLIP_WALL = 16
 FLAG_MIDPOINT = 32
+FLAG_EXACT_CHAR = 64
 
 
 def build(force: bool = False) -> str:
@@ -67,6 +68,8 @@ def lib():
             L.orc_locate.restype = i
             L.orc_departures.argtypes = [p, d, dp, dp]
             L.orc_departures.restype = i
+            L.orc_departures_exact.argtypes = [p, d, dp, dp]
+            L.orc_departures_exact.restype = i
             L.orc_map.argtypes = [p, d, i, dp]
             L.orc_fe_grad.argtypes = [p, d, dp, dp, dp]
             L.orc_fe_grad.restype = i
@@ -161,6 +164,15 @@ class Oracle:
         st = lib().orc_departures(self.h, float(t), px, py)
         if st:
             raise OracleError(f"oracle departures failed: status {st}")
+        return px.reshape(NQ, self.nn), py.reshape(NQ, self.nn)
+
+    def departures_exact(self, t1):
+        """Departure points on the exact characteristic of a step arriving at t1."""
+        px = np.empty(NQ * self.nn)
+        py = np.empty(NQ * self.nn)
+        st = lib().orc_departures_exact(self.h, float(t1), px, py)
+        if st:
+            raise OracleError(f"oracle exact departures failed: status {st}")
         return px.reshape(NQ, self.nn), py.reshape(NQ, self.nn)
 
     def map(self, t, a):

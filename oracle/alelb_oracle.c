@@ -14,7 +14,10 @@
  * Where the paper is silent the reading used is stated at the spot:
  *   R1  transformed velocity  c^_i = g^{-1,T} (c_i - V_G)        (Eq. 7 + chain rule)
  *   R2  map, Jacobian and V_G evaluated at the arrival time t_{n+1}; flag
- *       MIDPOINT evaluates those of the transformed velocities at t_{n+1/2}
+ *       MIDPOINT evaluates those of the transformed velocities at t_{n+1/2};
+ *       flag EXACT_CHAR takes the departure point on the exact characteristic,
+ *       X_dp = G^-1(G(X, t_{n+1}) - c_i dt, t_n), for maps with a closed-form
+ *       inverse (none, plunge, rigid pitch, pitch with plunge)
  *   R3  q*_a = q^eq_a + 2 u_b (P_ab - P^eq_ab)   (Table I's q* as printed drops q^eq)
  *   R4  forcing enters as + dt*phi_i with phi from the same time level; the
  *       equilibria use the plain velocity sum(c f)/rho
@@ -62,7 +65,7 @@ static const int CYI[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 enum { ST_OK = 0, ST_ARG = -1, ST_OOM = -2, ST_MESH = -4, ST_MAP = -5, ST_LOCATE = -6,
        ST_NONFINITE = -7 };
 enum { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQUILIBRIUM = 8,
-       FLAG_SLIP_WALL = 16, FLAG_MIDPOINT = 32 };
+       FLAG_SLIP_WALL = 16, FLAG_MIDPOINT = 32, FLAG_EXACT_CHAR = 64 };
 enum { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
        MK_BLENDED = 5 };
 enum { EK_INTERIOR = 0, EK_WALL = 1, EK_FAR = 2 };
@@ -1139,6 +1142,35 @@ static void departure(const orc_t *o, int a, const double *gi, double Vx, double
     *py = o->X[2 * a + 1] - *chy;
 }
 
+/* Departure point on the exact characteristic (flag EXACT_CHAR): the
+   physical position G(X_a, t1) moved back by c_i dt (dt = 1), mapped back
+   to the computational frame with the map of t0 = t1 - 1.  The inverses:
+   plunge y -> y - yoff(t0); rigid pitch x -> X_c + R(theta(t0))^T (x - X_c
+   - (0, yoff(t0))). */
+static void exact_departure(const orc_t *o, int a, const mscal_t *S1, const mscal_t *S0, int i,
+                            double *px, double *py)
+{
+    double x1, y1;
+    motion_position(o, a, S1, &x1, &y1);
+    double x0 = x1 - CXI[i], y0 = y1 - CYI[i];
+    switch (o->mkind) {
+    case MK_PLUNGE:
+        *px = x0;
+        *py = y0 - S0->yoff;
+        break;
+    case MK_PITCH:
+    case MK_PITCH_PLUNGE: {
+        double dx = x0 - o->mp[3], dy = (y0 - o->mp[4]) - S0->yoff;
+        *px = o->mp[3] + (dx * S0->c + dy * S0->sn);
+        *py = o->mp[4] + (dy * S0->c - dx * S0->sn);
+        break;
+    }
+    default:
+        *px = x0;
+        *py = y0;
+    }
+}
+
 /* Element choice for population i of node a (readings R5, R6).
    R6: the population is missing when some point of the segment X_a -> p
    lies outside the closed mesh.  Decided exactly enough by splitting the
@@ -1305,7 +1337,7 @@ static double interp_field(const orc_t *o, int e, double sx, double sy, double p
 /* Sd: map scalars of the transformed velocities (the arrival time S, or
    t_{n+1/2} under FLAG_MIDPOINT, reading R2); the wall condition and the
    derivatives keep S. */
-static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd)
+static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd, const mscal_t *S0)
 {
     int nn = o->nn;
     const double *gi = &o->gi[4 * a];
@@ -1323,7 +1355,13 @@ static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd)
     double tgt[4], du[4], dT[2];
     for (int i = 0; i < NQ; ++i) {
         double chx, chy, px, py, sx, sy;
-        departure(o, a, gdep, Vdx, Vdy, i, &chx, &chy, &px, &py);
+        if (S0) { /* the exact characteristic */
+            exact_departure(o, a, S, S0, i, &px, &py);
+            chx = o->X[2 * a] - px;
+            chy = o->X[2 * a + 1] - py;
+        } else {
+            departure(o, a, gdep, Vdx, Vdy, i, &chx, &chy, &px, &py);
+        }
         int kind;
         int e = choose_element(o, a, chx, chy, px, py, &sx, &sy, &kind);
         if (e == -3) return ST_LOCATE;
@@ -1419,10 +1457,16 @@ static int step_once(orc_t *o)
 {
     int nn = o->nn;
     double t1 = o->t + 1.0;
-    mscal_t S, Sh;
+    mscal_t S, Sh, Sz;
     motion_scalars(o, t1, &S);
-    const mscal_t *Sd = &S;
-    if (o->K.flags & FLAG_MIDPOINT) { /* transformed velocities at t_{n+1/2} */
+    const mscal_t *Sd = &S, *S0 = NULL;
+    if (o->K.flags & FLAG_EXACT_CHAR) { /* departure on the exact characteristic */
+        if (!(o->mkind == MK_NONE || o->mkind == MK_PLUNGE || o->mkind == MK_PITCH ||
+              o->mkind == MK_PITCH_PLUNGE))
+            return ST_ARG;
+        motion_scalars(o, o->t, &Sz);
+        S0 = &Sz;
+    } else if (o->K.flags & FLAG_MIDPOINT) { /* transformed velocities at t_{n+1/2} */
         motion_scalars(o, t1 - 0.5, &Sh);
         Sd = &Sh;
     }
@@ -1433,7 +1477,7 @@ static int step_once(orc_t *o)
     }
     /* propagation */
     for (int a = 0; a < nn; ++a) {
-        int st = stream_node(o, a, &S, Sd);
+        int st = stream_node(o, a, &S, Sd, S0);
         if (st) return st;
     }
     /* moments, Q'_aaa = rho u_a (1 - 3T) - rho u_a^3 (Eq. DeviationTerms), mu/(rho T) */
@@ -1574,6 +1618,23 @@ int orc_departures(void *h, double t, double *px_out, double *py_out)
                       &py_out[(size_t)i * o->nn + a]);
         }
     }
+    return ST_OK;
+}
+
+/* Departure points on the exact characteristic of a step arriving at t1
+   (flag EXACT_CHAR's rule, whatever the flags; x and y, [i*nn + a]). */
+int orc_departures_exact(void *h, double t1, double *px_out, double *py_out)
+{
+    orc_t *o = h;
+    if (!(o->mkind == MK_NONE || o->mkind == MK_PLUNGE || o->mkind == MK_PITCH ||
+          o->mkind == MK_PITCH_PLUNGE))
+        return ST_ARG;
+    mscal_t S1, S0;
+    motion_scalars(o, t1, &S1);
+    motion_scalars(o, t1 - 1.0, &S0);
+    for (int a = 0; a < o->nn; ++a)
+        for (int i = 0; i < NQ; ++i)
+            exact_departure(o, a, &S1, &S0, i, &px_out[(size_t)i * o->nn + a], &py_out[(size_t)i * o->nn + a]);
     return ST_OK;
 }
 

@@ -346,11 +346,16 @@ def test_physical_gradient_of_a_physically_linear_field(kind):
 
 def _G(mot, X, t):
     p = mot.params
-    if mot.kind == I.MOTION_PITCH:
+    if mot.kind in (I.MOTION_PITCH, I.MOTION_PITCH_PLUNGE):
         th = p[0] + p[1] * math.sin(p[2] * t)
         d = X - p[3:5]
         R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
-        return p[3:5] + R @ d
+        x = p[3:5] + R @ d
+        if mot.kind == I.MOTION_PITCH_PLUNGE:  # plunge y -= h sin(w_h t)
+            x = x + np.array([0.0, -p[5] * math.sin(p[6] * t)])
+        return x
+    if mot.kind == I.MOTION_PLUNGE:
+        return np.array([X[0], X[1] - p[0] * math.sin(p[1] * t)])
     if mot.kind == I.MOTION_SINE:
         A, L, Tp = p[0], p[1], p[2]
         s = math.sin(2 * math.pi * t / Tp)
@@ -427,7 +432,7 @@ def test_midpoint_variant_follows_the_characteristic_to_third_order():
     t0 = 7.0
     inner = (Y > 4.0) & (Y < L - 4.0)
     got = {}
-    for name, flags in (("mid", O.FLAG_MIDPOINT), ("end", 0)):
+    for name, flags in (("mid", O.FLAG_MIDPOINT), ("end", 0), ("exact", O.FLAG_EXACT_CHAR)):
         o = O.Oracle(mesh, mot, fl, flags=flags | O.FLAG_COLLIDE_OFF | O.FLAG_PHI_OFF)
         o.set_state(f, g, np.ones(n), np.zeros(n), np.zeros(n), np.full(n, 0.3), t=t0)
         o.step(1)
@@ -441,8 +446,34 @@ def test_midpoint_variant_follows_the_characteristic_to_third_order():
         exact = -cy - h * (math.sin(w * t1) - math.sin(w * t0))
         assert np.abs(got["mid"][i, inner] - mid).max() < 1e-9
         assert np.abs(got["end"][i, inner] - end).max() < 1e-9
+        assert np.abs(got["exact"][i, inner] - exact).max() < 1e-9  # flag EXACT_CHAR
         assert abs(mid - exact) < 1.01 * h * w ** 3 / 24 + 1e-12
         assert abs(end - exact) > 10 * abs(mid - exact)
+
+
+@pytest.mark.parametrize("kind", ["plunge", "pitch", "pitch_plunge"])
+def test_exact_characteristic_departure_inverts_the_map(kind):
+    """Flag EXACT_CHAR: X_dp = G^-1(G(X, t1) - c_i, t1 - 1), against the
+    map inverted by Newton's method in this file (closed forms of G for
+    plunge, rigid pitch and pitch with plunge)."""
+    mot = {"plunge": I.Motion.make(I.MOTION_PLUNGE, 3.0, 0.05),
+           "pitch": I.Motion.make(I.MOTION_PITCH, 0.05, 0.3, 0.04, 10.0, 2.0),
+           "pitch_plunge": I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.3, 0.04, 10.0, 2.0, 2.0, 0.03)}[kind]
+    mesh = I.periodic_box(8, 32.0, 0.2, seed=5)
+    o = O.Oracle(mesh, mot, _flow(), flags=O.FLAG_EXACT_CHAR)
+    t1 = 9.0
+    px, py = o.departures_exact(t1)
+    worst = 0.0
+    for a in range(0, mesh.n_nodes, 5):
+        Xa = mesh.X[a]
+        xa = _G(mot, Xa, t1)
+        for i in range(9):
+            c = np.array([CX[i], CY[i]], float)
+            X0 = _Ginv(mot, xa - c, t1 - 1.0, Xa)
+            worst = max(worst, abs(X0[0] - px[i, a]), abs(X0[1] - py[i, a]))
+    assert worst < 1e-9
+    with pytest.raises(O.OracleError):  # no closed-form inverse: refused
+        O.Oracle(mesh, I.Motion.make(I.MOTION_SINE, 1.0, 32.0, 50.0, 0.0), _flow()).departures_exact(t1)
 
 
 def test_mesh_velocity_is_time_derivative_of_the_map():
