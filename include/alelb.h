@@ -90,10 +90,20 @@ enum {
     ALELB_FLAG_SLIP_WALL = 16,     /* slip (inviscid) walls: at wall nodes the target velocity is
                                       V_G plus the tangential part of u_B - V_G at the probe B,
                                       and the non-equilibrium part is dropped (no wall shear) */
-    ALELB_FLAG_MIDPOINT = 32       /* the transformed velocities c^_i of a step t_n -> t_{n+1}
+    ALELB_FLAG_MIDPOINT = 32,      /* the transformed velocities c^_i of a step t_n -> t_{n+1}
                                       use g and V_G at t_{n+1/2} (Eq. 7 at the midpoint time;
                                       the wall condition and the derivatives stay at t_{n+1}).
                                       Single-case solvers only: alelb_batch_create refuses it */
+    ALELB_FLAG_EXACT_CHAR = 64     /* the departure point of population i is the reference position
+                                      at t_n of the physical point G(X, t_{n+1}) - c_i, on the
+                                      exact characteristic of Sec. III, in place of X - c^_i;
+                                      rigid maps only (none, plunge, pitch, pitch with plunge):
+                                      alelb_lb_init and alelb_lb_step_noalloc return
+                                      ALELB_ERR_ARG for the others.  Every population of the
+                                      deviation forms takes the exact path (its FP32
+                                      certificates bound X - c^_i only).  Single-case solvers
+                                      only: alelb_batch_create refuses it.  Takes precedence
+                                      over ALELB_FLAG_MIDPOINT */
 };
 
 /* Mesh description (computational domain, Sec. III).  Straight-sided

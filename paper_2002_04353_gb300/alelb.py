@@ -30,6 +30,7 @@ FLAG_LITERAL_VG = 4
 FLAG_BC_EQUILIBRIUM = 8
 FLAG_SLIP_WALL = 16
 FLAG_MIDPOINT = 32
+FLAG_EXACT_CHAR = 64
 NQ = 9
 
 # every symbol include/alelb.h declares

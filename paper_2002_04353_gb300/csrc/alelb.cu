@@ -344,7 +344,10 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
     const bool fast = s->prec != ALELB_PREC_FP64;
     const MapScalarsF sf = to_f32(sc, m->T);
     // the transformed velocities' map: arrival time, or t_{n+1/2} (flag)
-    const MapScalars scd = (s->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, s->t + 0.5) : sc;
+    // (the departure time under ALELB_FLAG_EXACT_CHAR)
+    const MapScalars scd = (s->flags & ALELB_FLAG_EXACT_CHAR) ? map_scalars(m->T.mkind, m->T.mp, s->t)
+                           : (s->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, s->t + 0.5)
+                                                              : sc;
     const MapScalarsF sfd = to_f32(scd, m->T);
     int seq[KT_N], ns = 0;
     if (fast) {
@@ -462,6 +465,10 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     if (!(p->gamma > 1.0) || !(p->Pr > 0) || !(p->mu > 0) || !(p->rho_inf > 0) || !(p->T_inf > 0) ||
         p->precision < ALELB_PREC_FP64 || p->precision > ALELB_PREC_FP16_DEV)
         return ALELB_ERR_ARG;
+    if ((p->flags & ALELB_FLAG_EXACT_CHAR) && (m->T.mkind == MK_SINE || m->T.mkind == MK_BLENDED)) {
+        m->err = "lb_init: the exact characteristic needs a rigid map (none, plunge, pitch, pitch with plunge)";
+        return ALELB_ERR_ARG;
+    }
     alelb_solver *s = new (std::nothrow) alelb_solver();
     if (!s) return ALELB_ERR_OOM;
     *out = s;
@@ -792,6 +799,10 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
         m->err = "lb_step_noalloc: needs FP64 precision and positive fluid parameters";
         return ALELB_ERR_ARG;
     }
+    if ((p->flags & ALELB_FLAG_EXACT_CHAR) && (m->T.mkind == MK_SINE || m->T.mkind == MK_BLENDED)) {
+        m->err = "lb_step_noalloc: the exact characteristic needs a rigid map (none, plunge, pitch, pitch with plunge)";
+        return ALELB_ERR_ARG;
+    }
     const int N = m->T.N;
     if (N > ALELB_NOALLOC_MAX_NODES) {
         m->err = "lb_step_noalloc: the mesh has " + std::to_string(N) + " nodes; at most " +
@@ -861,7 +872,9 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     }
     K.flags = p->flags;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
-    const MapScalars scd = (p->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, t + 0.5) : sc;
+    const MapScalars scd = (p->flags & ALELB_FLAG_EXACT_CHAR) ? map_scalars(m->T.mkind, m->T.mp, t)
+                           : (p->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, t + 0.5)
+                                                              : sc;
     k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, scd, K, sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
         k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), sd);

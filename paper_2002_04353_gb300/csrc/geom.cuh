@@ -306,6 +306,40 @@ ALELB_HD __forceinline__ void departure(double a11, double a12, double a21, doub
     py = ds(Y, chy);
 }
 
+// Departure point on the exact characteristic of a rigid map (no map,
+// plunge, pitch, pitch with plunge; the characteristic of Sec. III with
+// the motions of Sec. V): the arrival point x = G(X, t), the point
+// x - c_i one time unit earlier, and its reference position
+// G^-1(x - c_i, t - 1).  S1, S0: the map at t and at t - 1.  The rotation
+// is applied about the centre, with no detour through absolute positions.
+ALELB_HD __forceinline__ void exact_departure(const MapStatic &M, const MapScalars &S1,
+                                              const MapScalars &S0, double cx, double cy,
+                                              double X, double Y, double &chx, double &chy,
+                                              double &px, double &py)
+{
+    switch (M.kind) {
+    case MK_PLUNGE:
+        px = ds(X, cx);
+        py = ds(ds(da(Y, S1.yoff), cy), S0.yoff);
+        break;
+    case MK_PITCH:
+    case MK_PITCH_PLUNGE: {
+        const double dx = ds(X, M.Xc), dy = ds(Y, M.Yc);
+        // x - c_i - (centre at t - 1), relative to the reference centre
+        const double rx = ds(ds(dm(dx, S1.c), dm(dy, S1.sn)), cx);
+        const double ry = ds(da(da(dm(dx, S1.sn), dm(dy, S1.c)), ds(S1.yoff, S0.yoff)), cy);
+        px = da(M.Xc, da(dm(rx, S0.c), dm(ry, S0.sn)));
+        py = da(M.Yc, ds(dm(ry, S0.c), dm(rx, S0.sn)));
+        break;
+    }
+    default:
+        px = ds(X, cx);
+        py = ds(Y, cy);
+    }
+    chx = ds(X, px);
+    chy = ds(Y, py);
+}
+
 // ---------------------------------------------------------------------------
 // Exact orientation sign of (a, b, c): sign of (a-c) x (b-c).
 // Stage 1: the FP64 determinant with the certified error bound of Shewchuk
@@ -1219,10 +1253,13 @@ struct Pred32 {
 // located there by the walk too, with the same rule for edges and vertices
 // (a departure point near an element edge, where the FP32 margins fail, no
 // longer needs the scan of the node's fan).
+// s1 (not null): the departure point on the exact characteristic, s1 the
+// map at the arrival time and sc at the departure time (F is then not ok).
 ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                                          const MapScalars &sc, const FastMap &F, float4 Xf, int a,
                                          int i, int literal, float &qx, float &qy, int &src,
-                                         int *err, int hint = -1, int clear = -1)
+                                         int *err, int hint = -1, int clear = -1,
+                                         const MapScalars *s1 = nullptr)
 {
     const double2 Xa = M.X[a];
     src = -1;
@@ -1290,11 +1327,16 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
         }
     }
     if (!done) {
-        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy, chx, chy, px, py;
-        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
-        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-        mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
-        departure(a11, a12, a21, a22, wx, wy, lat_cx(i), lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
+        double chx, chy, px, py;
+        if (s1) { // the exact characteristic: s1 the arrival map, sc the departure map
+            exact_departure(MS, *s1, sc, lat_cx(i), lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
+        } else {
+            double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+            map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+            mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
+            departure(a11, a12, a21, a22, wx, wy, lat_cx(i), lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
+        }
         if (chx == 0.0 && chy == 0.0) {
             L.e = -2;
             L.vnode = -1;

@@ -244,7 +244,7 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
         A fi = 0, gi = 0;
         int src = -1; // node whose value is taken as is
         {
-            if (!have64) {
+            if (!have64 && !(K.flags & FLAG_EXACT_CHAR)) {
                 double xX, xY, yX, yY;
                 map_node(MS, scd, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
                 metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
@@ -252,8 +252,11 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
                 have64 = true;
             }
             double chx, chy, px, py;
-            departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx,
-                      chy, px, py);
+            if (K.flags & FLAG_EXACT_CHAR)
+                exact_departure(MS, sc, scd, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx, chy, px, py);
+            else
+                departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx,
+                          chy, px, py);
             if (chx == 0.0 && chy == 0.0) {
                 src = a;
             } else {
@@ -592,7 +595,7 @@ __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapSta
         const float bd = M.bdist[a];
         const float4 Xf = M.Xf[a];
         FastMap F = fast_map(MS, sf, a, Xf);
-        if (K.flags & FLAG_LITERAL_VG) F.ok = false;
+        if (K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
 #pragma unroll
         for (int j = 0; j < G; ++j) code[j] = stream_fast_pop(M, K, st, a, i0 + j, F, Xf, bd, c[j]);
     }
@@ -651,8 +654,10 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             prefetch_l1(M.ejf + 2 * e + 1);
         }
         const float4 Xf = M.Xf[a];
-        const FastMap F = fast_map(MS, sfd, a, Xf);
-        const FastMap Fb = (K.flags & FLAG_MIDPOINT) ? fast_map(MS, sf, a, Xf) : F; // wall condition
+        FastMap F = fast_map(MS, sfd, a, Xf);
+        const FastMap Fb = (K.flags & (FLAG_MIDPOINT | FLAG_EXACT_CHAR)) ? fast_map(MS, sf, a, Xf) : F; // wall condition
+        const bool exact_char = (K.flags & FLAG_EXACT_CHAR) != 0;
+        if (exact_char) F.ok = false; // the FP32 certificates bound the c^ departure only
         const int literal = (K.flags & FLAG_LITERAL_VG) != 0;
         float qx = 0.f, qy = 0.f;
         int src;
@@ -686,7 +691,8 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             src = -1;
             if (hits) atomicAdd(hits, 1ull);
         } else {
-            L = slow_decide(M, MS, scd, F, Xf, a, i, literal, qx, qy, src, err, hint, clear);
+            L = slow_decide(M, MS, scd, F, Xf, a, i, literal, qx, qy, src, err, hint, clear,
+                            exact_char ? &sc : nullptr);
         }
         A fi = 0, gi = 0;
         if (src >= 0) {

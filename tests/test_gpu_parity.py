@@ -390,6 +390,50 @@ def test_batch_refuses_the_midpoint_variant():
     assert ex.value.status == -1
 
 
+# ---------------------------------------------------------------------------
+# departure on the exact characteristic of a rigid map (flag EXACT_CHAR)
+# ---------------------------------------------------------------------------
+
+EXACT_CASES = {
+    "omesh_plunge": LOC_CASES["omesh_plunge"],
+    "omesh_pitch_plunge": LOC_CASES["omesh_pitch"],
+    "omesh_pitch": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0),
+                            I.Motion.make(I.MOTION_PITCH, 0.05, 0.05, 0.003, 50.0, 0.0)),
+}
+
+
+@pytest.mark.parametrize("motion_name", sorted(EXACT_CASES))
+def test_exact_characteristic_fp64_and_fp32(motion_name):
+    mesh, motion = EXACT_CASES[motion_name]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o, m, s = _pair(mesh, motion, flow, flags=O.FLAG_EXACT_CHAR)
+    o.step(4)
+    s.lb_step(4)
+    _compare64(o, s, f"{motion_name} exact characteristic FP64")
+    o2, m2, s2 = _pair(mesh, motion, flow, prec=alelb.PREC_FP32_DEV, flags=O.FLAG_EXACT_CHAR)
+    o2.step(4)
+    s2.lb_step(4)
+    _compare_mixed(o2, s2, f"{motion_name} exact characteristic FP32")
+    # the flag changes the result (X - c^ is the first-order departure)
+    o3 = O.Oracle(mesh, motion, flow)
+    o3.step(4)
+    assert _rel(o3.state()["f"], o.state()["f"]) > 1e-12
+
+
+def test_exact_characteristic_refused_where_the_map_has_no_closed_inverse():
+    mesh, motion = LOC_CASES["omesh_blended"]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    m = alelb.Mesh(mesh, motion)
+    with pytest.raises(alelb.AlelbError) as ex:
+        alelb.Solver(m, flow, alelb.PREC_FP64, flags=O.FLAG_EXACT_CHAR)
+    assert ex.value.status == -1
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    s = alelb.Solver(alelb.Mesh(mesh, motion), flow, alelb.PREC_FP32_DEV, flags=O.FLAG_EXACT_CHAR)
+    with pytest.raises(alelb.AlelbError) as ex:
+        alelb.Batch([s])
+    assert ex.value.status == -1
+
+
 @pytest.mark.parametrize("prec", [alelb.PREC_FP32_DEV, alelb.PREC_BF16_DEV, alelb.PREC_FP16_DEV])
 @pytest.mark.parametrize("flags", [0, O.FLAG_MIDPOINT])
 def test_deviation_forms_on_a_tiny_mesh(prec, flags):

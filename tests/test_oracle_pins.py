@@ -451,6 +451,31 @@ def test_midpoint_variant_follows_the_characteristic_to_third_order():
         assert abs(end - exact) > 10 * abs(mid - exact)
 
 
+def test_departure_variants_against_the_exact_characteristic():
+    """Accuracy of the two c^ departures X - c^(t) against the exact
+    characteristic's (flag EXACT_CHAR), t = t_{n+1} or t_{n+1/2}, as the
+    motion slows.  Plunge (c^ depends on time only): the midpoint departure
+    is about a hundred times closer.  Rigid pitch: c^ also varies along the
+    characteristic through V_G, which no time level captures, so both stay
+    first order in the pitch rate and the midpoint only halves the error."""
+    mesh = I.periodic_box(8, 32.0, 0.2, seed=5)
+    errs = {}
+    for kind in ("plunge", "pitch"):
+        for w in (0.04, 0.02):
+            mot = (I.Motion.make(I.MOTION_PLUNGE, 3.0, w) if kind == "plunge"
+                   else I.Motion.make(I.MOTION_PITCH, 0.05, 0.3, w, 16.0, 16.0))
+            o = O.Oracle(mesh, mot, _flow())
+            t1 = 9.0
+            ex = np.stack(o.departures_exact(t1))
+            errs[kind, w] = tuple(np.abs(np.stack(o.departures(t)) - ex).max() for t in (t1, t1 - 0.5))
+    for w in (0.04, 0.02):
+        end, mid = errs["plunge", w]
+        assert mid < end / 50
+        end, mid = errs["pitch", w]
+        assert 0.4 < mid / end < 0.6
+    assert 1.8 < errs["pitch", 0.04][0] / errs["pitch", 0.02][0] < 2.4  # first order in the rate
+
+
 @pytest.mark.parametrize("kind", ["plunge", "pitch", "pitch_plunge"])
 def test_exact_characteristic_departure_inverts_the_map(kind):
     """Flag EXACT_CHAR: X_dp = G^-1(G(X, t1) - c_i, t1 - 1), against the
