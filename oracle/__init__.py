@@ -84,6 +84,9 @@ def lib():
             L.orc_feq.argtypes = [d, d, d, d, dp]
             L.orc_geq.argtypes = [d, d, d, d, d, dp]
             L.orc_gqe.argtypes = [d, d, d, d, d, d, d, d, dp]
+            L.orc_feq_shift.argtypes = [d, d, d, d, d, d, dp]
+            L.orc_geq_shift.argtypes = [d, d, d, d, d, d, d, dp]
+            L.orc_gqe_shift.argtypes = [d, d, d, d, d, d, d, d, d, d, dp]
             L.orc_collide.argtypes = [dp, dp, dp, d, d, dp, dp]
             L.orc_grad_bc.argtypes = [dp, d, d, d, d, dp, dp, dp, dp]
             L.orc_shape.argtypes = [d, d, dp]
@@ -237,6 +240,26 @@ def geq(rho, ux, uy, T, Cv):
 def gqe(rho, ux, uy, T, Cv, Pxx, Pxy, Pyy):
     out = np.empty(NQ)
     lib().orc_gqe(rho, ux, uy, T, Cv, Pxx, Pxy, Pyy, out)
+    return out
+
+
+def feq_shift(rho, ux, uy, T, U):
+    """f^eq on the lattice c_i + U (lab-frame velocity u)."""
+    out = np.empty(NQ)
+    lib().orc_feq_shift(rho, ux, uy, T, float(U[0]), float(U[1]), out)
+    return out
+
+
+def geq_shift(rho, ux, uy, T, Cv, U):
+    out = np.empty(NQ)
+    lib().orc_geq_shift(rho, ux, uy, T, Cv, float(U[0]), float(U[1]), out)
+    return out
+
+
+def gqe_shift(rho, ux, uy, T, Cv, U, Pxx, Pxy, Pyy):
+    """g* on the lattice c_i + U; P the lab-frame second moments of f."""
+    out = np.empty(NQ)
+    lib().orc_gqe_shift(rho, ux, uy, T, Cv, float(U[0]), float(U[1]), Pxx, Pxy, Pyy, out)
     return out
 
 

@@ -48,6 +48,13 @@
  *       physical frame, and no non-equilibrium part (no wall shear)
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
  *       on each straight P2 wall edge of the mapped geometry
+ *   R14 shifted lattice (velocities c_i + U, Sec. V.D; the model itself is
+ *       deferred to another paper): every population set carries the same
+ *       lab-frame moments as on the plain lattice -- f^eq in u - U, the
+ *       general form on moments taken about U, psi the correction of the
+ *       diagonal second central moments (the printed psi at U = 0), Q' in
+ *       u - U, phi_i = A_ia X_a on the relative velocities c_i; the
+ *       departure uses c_i + U and the moments sum (c_i + U) f
  * Parity status of each function is given in its comment; the forces have
  * no value the paper prints for these setups ("parity unpinned" beyond the
  * closed-body invariant).
@@ -128,6 +135,7 @@ typedef struct {
     double gamma, Pr, mu, rho_inf, T_inf, ux_inf, uy_inf, chord;
     int flags;
     double Cv, Cp;
+    double Ux, Uy; /* lattice shift U: the discrete velocities are c_i + U (Sec. V.D) */
 } kin_t;
 
 static void kin_from(const double *k, kin_t *K)
@@ -141,6 +149,8 @@ static void kin_from(const double *k, kin_t *K)
     K->uy_inf = k[6];
     K->chord = k[7];
     K->flags = (int)k[8];
+    K->Ux = k[9];
+    K->Uy = k[10];
     K->Cv = 1.0 / (K->gamma - 1.0); /* R = 1 */
     K->Cp = K->Cv + 1.0;
 }
@@ -233,6 +243,93 @@ void orc_gqe(double rho, double ux, double uy, double T, double Cv, double Pxx, 
     gform(T, 2.0 * rho * E, qx, qy, R[0], R[1], R[2], psi, g);
 }
 
+/* ----------------------------------------------------------------------
+ * Shifted lattice (Sec. V.D: velocities c_i + U, U = (0.3, 0) for the
+ * transonic case; the model's details are deferred to its own reference,
+ * so this is reading R14).  Every population set is built to carry the
+ * same lab-frame moments as on the plain lattice:
+ *   f^eq: the product form in the relative velocity u - U (its moments
+ *         {1, c, cc} about U are those of the Maxwellian about U, hence
+ *         {1, c + U, (c + U)(c + U)} give rho, rho u, rho(uu + T I));
+ *   general form: the lab moments M0, M_a, M_ab are converted to moments
+ *         about U, M'_a = M_a - U_a M0, M'_ab = M_ab - U_a M_b - U_b M_a
+ *         + U_a U_b M0, and Eq. geq_gstar is applied on the relative
+ *         velocities c_i;
+ *   psi:  on the plain lattice psi_i restores the diagonal second moments
+ *         that Eq. geq_gstar misses (sum W_i c_a^4 = T, not 3 T^2):
+ *         sum c_a^2 G_i = M0 T + (M_aa - M0 T)(1 - T)/(2T).  The printed
+ *         psi is exactly that correction for g^eq; on the shifted lattice
+ *         the same correction is taken of the central moments,
+ *         Y_a = (M'_aa - M0 T)(1 - 3T)/(2T), psi_i = B_ia Y_a.
+ * ------------------------------------------------------------------- */
+void orc_feq_shift(double rho, double ux, double uy, double T, double Ux, double Uy, double *f)
+{
+    orc_feq(rho, ux - Ux, uy - Uy, T, f);
+}
+
+/* General form of lab moments on the lattice shifted by U (psi only when
+   with_psi). */
+static void gform_shift(double T, double Ux, double Uy, double M0, double Mx, double My,
+                        double Mxx, double Mxy, double Myy, int with_psi, double *G)
+{
+    double cMx = Mx - Ux * M0, cMy = My - Uy * M0;
+    double cMxx = Mxx - 2.0 * Ux * Mx + Ux * Ux * M0;
+    double cMxy = Mxy - Ux * My - Uy * Mx + Ux * Uy * M0;
+    double cMyy = Myy - 2.0 * Uy * My + Uy * Uy * M0;
+    double psi[NQ];
+    if (with_psi) {
+        double Y[2] = {(cMxx - M0 * T) * (1.0 - 3.0 * T) / (2.0 * T),
+                       (cMyy - M0 * T) * (1.0 - 3.0 * T) / (2.0 * T)};
+        for (int i = 0; i < NQ; ++i) {
+            double c[2] = {CXI[i], CYI[i]};
+            double c2 = c[0] * c[0] + c[1] * c[1];
+            double sum = 0.0;
+            for (int a = 0; a < 2; ++a) sum += ((c2 == 0.0) ? 1.0 : -fabs(c[a] - 0.5 * c[a] * c2)) * Y[a];
+            psi[i] = sum;
+        }
+    }
+    gform(T, M0, cMx, cMy, cMxx, cMxy, cMyy, with_psi ? psi : NULL, G);
+}
+
+/* g^eq and g* on the shifted lattice: the lab moments of Table I. */
+void orc_geq_shift(double rho, double ux, double uy, double T, double Cv, double Ux, double Uy,
+                   double *g)
+{
+    double E = Cv * T + 0.5 * (ux * ux + uy * uy);
+    double R[3];
+    Req(rho, ux, uy, T, E, R);
+    gform_shift(T, Ux, Uy, 2.0 * rho * E, 2.0 * rho * ux * (E + T), 2.0 * rho * uy * (E + T), R[0],
+                R[1], R[2], 1, g);
+}
+
+/* Pxx, Pxy, Pyy: the lab-frame second moments sum (c + U)(c + U) f. */
+void orc_gqe_shift(double rho, double ux, double uy, double T, double Cv, double Ux, double Uy,
+                   double Pxx, double Pxy, double Pyy, double *g)
+{
+    double E = Cv * T + 0.5 * (ux * ux + uy * uy);
+    double R[3];
+    Req(rho, ux, uy, T, E, R);
+    double dPxx = Pxx - (rho * ux * ux + rho * T);
+    double dPxy = Pxy - (rho * ux * uy);
+    double dPyy = Pyy - (rho * uy * uy + rho * T);
+    double qx = 2.0 * rho * ux * (E + T) + 2.0 * (ux * dPxx + uy * dPxy);
+    double qy = 2.0 * rho * uy * (E + T) + 2.0 * (ux * dPxy + uy * dPyy);
+    gform_shift(T, Ux, Uy, 2.0 * rho * E, qx, qy, R[0], R[1], R[2], 1, g);
+}
+
+static int shifted(const kin_t *K) { return K->Ux != 0.0 || K->Uy != 0.0; }
+
+/* Equilibria of the solver's lattice (the printed forms when unshifted). */
+static void feq_K(const kin_t *K, double rho, double ux, double uy, double T, double *f)
+{
+    orc_feq_shift(rho, ux, uy, T, K->Ux, K->Uy, f);
+}
+static void geq_K(const kin_t *K, double rho, double ux, double uy, double T, double *g)
+{
+    if (shifted(K)) orc_geq_shift(rho, ux, uy, T, K->Cv, K->Ux, K->Uy, g);
+    else orc_geq(rho, ux, uy, T, K->Cv, g);
+}
+
 /* Local collision of Eqs. feqn/geqn at one node, given the streamed
    populations f, g and the correction source X_a.  Writes the
    post-collision populations.  Pinned: sum f and sum g conserved exactly,
@@ -242,12 +339,13 @@ static void collide(const kin_t *K, const double *f, const double *g, double Xx,
 {
     double rho = 0, jx = 0, jy = 0, Pxx = 0, Pxy = 0, Pyy = 0, e2 = 0;
     for (int i = 0; i < NQ; ++i) {
+        double vx = CXI[i] + K->Ux, vy = CYI[i] + K->Uy; /* the lattice velocity */
         rho += f[i];
-        jx += CXI[i] * f[i];
-        jy += CYI[i] * f[i];
-        Pxx += CXI[i] * CXI[i] * f[i];
-        Pxy += CXI[i] * CYI[i] * f[i];
-        Pyy += CYI[i] * CYI[i] * f[i];
+        jx += vx * f[i];
+        jy += vy * f[i];
+        Pxx += vx * vx * f[i];
+        Pxy += vx * vy * f[i];
+        Pyy += vy * vy * f[i];
         e2 += g[i];
     }
     double ux = jx / rho, uy = jy / rho;
@@ -258,10 +356,12 @@ static void collide(const kin_t *K, const double *f, const double *g, double Xx,
     double omega = 1.0 / (K->mu / (rho * T) + 0.5);
     double omega1 = 1.0 / ((1.0 / omega - 0.5) / K->Pr + 0.5);
     double feq[NQ], geq[NQ], gqe[NQ];
-    orc_feq(rho, ux, uy, T, feq);
-    orc_geq(rho, ux, uy, T, K->Cv, geq);
-    orc_gqe(rho, ux, uy, T, K->Cv, Pxx, Pxy, Pyy, gqe);
+    feq_K(K, rho, ux, uy, T, feq);
+    geq_K(K, rho, ux, uy, T, geq);
+    if (shifted(K)) orc_gqe_shift(rho, ux, uy, T, K->Cv, K->Ux, K->Uy, Pxx, Pxy, Pyy, gqe);
+    else orc_gqe(rho, ux, uy, T, K->Cv, Pxx, Pxy, Pyy, gqe);
     for (int i = 0; i < NQ; ++i) {
+        /* A_ia on the relative velocities c_i (reading R14) */
         double cx = CXI[i], cy = CYI[i], c2 = cx * cx + cy * cy;
         double phi = (cx - 0.5 * cx * c2) * Xx + (cy - 0.5 * cy * c2) * Xy; /* A_ia X_a */
         fo[i] = f[i] + omega * (feq[i] - f[i]) + 1.0 * phi;
@@ -307,10 +407,15 @@ static void grad_bc(const kin_t *K, double rho, double ux, double uy, double T,
     double R1xy = -(2.0 / omega1) * rho * T * (Sxy * (E + 2.0 * T) + ux * dEy + uy * dEx);
     double R1yy = -(2.0 / omega1) * rho * T * (Syy * (E + 2.0 * T) + uy * dEy + uy * dEy);
     double feq[NQ], geq[NQ], f1[NQ], g1[NQ];
-    orc_feq(rho, ux, uy, T, feq);
-    orc_geq(rho, ux, uy, T, K->Cv, geq);
-    gform(T, 0.0, 0.0, 0.0, P1xx, P1xy, P1yy, NULL, f1);
-    gform(T, 0.0, q1x, q1y, R1xx, R1xy, R1yy, NULL, g1);
+    feq_K(K, rho, ux, uy, T, feq);
+    geq_K(K, rho, ux, uy, T, geq);
+    if (shifted(K)) { /* the same lab moments, taken about U */
+        gform_shift(T, K->Ux, K->Uy, 0.0, 0.0, 0.0, P1xx, P1xy, P1yy, 0, f1);
+        gform_shift(T, K->Ux, K->Uy, 0.0, q1x, q1y, R1xx, R1xy, R1yy, 0, g1);
+    } else {
+        gform(T, 0.0, 0.0, 0.0, P1xx, P1xy, P1yy, NULL, f1);
+        gform(T, 0.0, q1x, q1y, R1xx, R1xy, R1yy, NULL, g1);
+    }
     for (int i = 0; i < NQ; ++i) {
         f[i] = feq[i] + 1.0 * f1[i];
         g[i] = geq[i] + 1.0 * g1[i];
@@ -1066,8 +1171,8 @@ void orc_init(void *h)
 {
     orc_t *o = h;
     double fe[NQ], ge[NQ];
-    orc_feq(o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, fe);
-    orc_geq(o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, o->K.Cv, ge);
+    feq_K(&o->K, o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, fe);
+    geq_K(&o->K, o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, ge);
     for (int a = 0; a < o->nn; ++a) {
         for (int i = 0; i < NQ; ++i) {
             o->f[(size_t)i * o->nn + a] = fe[i];
@@ -1127,7 +1232,7 @@ int orc_owner(void *h, int *owner, int *loc)
 static void departure(const orc_t *o, int a, const double *gi, double Vx, double Vy, int i,
                       double *chx, double *chy, double *px, double *py)
 {
-    double cx = CXI[i], cy = CYI[i];
+    double cx = CXI[i] + o->K.Ux, cy = CYI[i] + o->K.Uy; /* the lattice velocity */
     double wx, wy;
     if (o->K.flags & FLAG_LITERAL_VG) {
         wx = Vx;
@@ -1152,7 +1257,7 @@ static void exact_departure(const orc_t *o, int a, const mscal_t *S1, const msca
 {
     double x1, y1;
     motion_position(o, a, S1, &x1, &y1);
-    double x0 = x1 - CXI[i], y0 = y1 - CYI[i];
+    double x0 = x1 - (CXI[i] + o->K.Ux), y0 = y1 - (CYI[i] + o->K.Uy);
     switch (o->mkind) {
     case MK_PLUNGE:
         *px = x0;
@@ -1393,8 +1498,8 @@ static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd, con
         /* missing population */
         double fm[NQ], gm[NQ];
         if (kind == EK_FAR) {
-            orc_feq(o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, fm);
-            orc_geq(o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, o->K.Cv, gm);
+            feq_K(&o->K, o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, fm);
+            geq_K(&o->K, o->K.rho_inf, o->K.ux_inf, o->K.uy_inf, o->K.T_inf, gm);
         } else {
             if (!have_bc) {
                 if (o->is_wall[a]) {
@@ -1480,7 +1585,8 @@ static int step_once(orc_t *o)
         int st = stream_node(o, a, &S, Sd, S0);
         if (st) return st;
     }
-    /* moments, Q'_aaa = rho u_a (1 - 3T) - rho u_a^3 (Eq. DeviationTerms), mu/(rho T) */
+    /* moments, Q'_aaa = rho w_a (1 - 3T) - rho w_a^3 with w = u - U (Eq. DeviationTerms),
+       mu/(rho T) */
     double *R = xcalloc(nn, sizeof(double)), *UX = xcalloc(nn, sizeof(double)),
            *UY = xcalloc(nn, sizeof(double)), *TT = xcalloc(nn, sizeof(double));
     for (int a = 0; a < nn; ++a) {
@@ -1488,8 +1594,8 @@ static int step_once(orc_t *o)
         for (int i = 0; i < NQ; ++i) {
             double f = o->fs[(size_t)i * nn + a];
             r += f;
-            jx += CXI[i] * f;
-            jy += CYI[i] * f;
+            jx += (CXI[i] + o->K.Ux) * f;
+            jy += (CYI[i] + o->K.Uy) * f;
             e2 += o->gs[(size_t)i * nn + a];
         }
         double ux = jx / r, uy = jy / r, E = e2 / (2.0 * r);
@@ -1505,8 +1611,11 @@ static int step_once(orc_t *o)
         UX[a] = ux;
         UY[a] = uy;
         TT[a] = T;
-        o->Qx[a] = r * ux * (1.0 - 3.0 * T) - r * ux * ux * ux;
-        o->Qy[a] = r * uy * (1.0 - 3.0 * T) - r * uy * uy * uy;
+        /* on the shifted lattice only sum c_a^3 f = sum c_a f about U departs
+           from the Maxwellian: Q' in the relative velocity w = u - U (R14) */
+        double wx = ux - o->K.Ux, wy = uy - o->K.Uy;
+        o->Qx[a] = r * wx * (1.0 - 3.0 * T) - r * wx * wx * wx;
+        o->Qy[a] = r * wy * (1.0 - 3.0 * T) - r * wy * wy * wy;
         o->m_rt[a] = o->K.mu / (r * T);
     }
     /* first derivative pass: D_a = (mu / rho T) d_a Q'_aaa (Eq. Xa) */

@@ -100,11 +100,13 @@ class Flow:
     u_inf: tuple = (0.0, 0.0)
     chord: float = 1.0
     flags: int = 0
+    shift: tuple = (0.0, 0.0)  # lattice shift U (velocities c_i + U)
 
     def as_array(self):
         return np.array([self.gamma, self.Pr, self.mu, self.rho_inf, self.T_inf,
-                         self.u_inf[0], self.u_inf[1], self.chord, float(self.flags)]
-                        + [0.0] * 7, dtype=np.float64)
+                         self.u_inf[0], self.u_inf[1], self.chord, float(self.flags),
+                         float(self.shift[0]), float(self.shift[1])]
+                        + [0.0] * 5, dtype=np.float64)
 
 
 # --------------------------------------------------------------------------
@@ -336,13 +338,14 @@ def speed_of(Ma, T_inf, gamma=1.4):
 
 
 def flow_params(Ma, T_inf=0.3, Re=None, chord=200.0, angle_deg=0.0, mu=None,
-                gamma=1.4, Pr=0.71, rho_inf=1.0, flags=0):
+                gamma=1.4, Pr=0.71, rho_inf=1.0, flags=0, shift=(0.0, 0.0)):
     U = speed_of(Ma, T_inf, gamma)
     if mu is None:
         mu = rho_inf * U * chord / Re
     a = math.radians(angle_deg)
     return Flow(gamma=gamma, Pr=Pr, mu=mu, rho_inf=rho_inf, T_inf=T_inf,
-                u_inf=(U * math.cos(a), U * math.sin(a)), chord=chord, flags=flags)
+                u_inf=(U * math.cos(a), U * math.sin(a)), chord=chord, flags=flags,
+                shift=tuple(float(x) for x in shift))
 
 
 @dataclasses.dataclass
