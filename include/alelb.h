@@ -133,6 +133,15 @@ typedef struct {
     int32_t precision; /* ALELB_PREC_* */
     int32_t flags;     /* ALELB_FLAG_* */
     void *stream;
+    double shift[2];   /* lattice shift U (Sec. V.D): the discrete velocities are c_i + U.
+                          Zero is the plain lattice.  Each component finite, |U_d| <= 1 and
+                          exactly representable in FP32, else ALELB_ERR_ARG.  On the shifted
+                          lattice the equilibria take the relative velocity u - U, the
+                          general form of Eq. geq_gstar is applied to moments taken about U,
+                          psi restores the diagonal second moments about U, Q' is taken in
+                          u - U, and rho u = sum (c_i + U) f_i; the populations that
+                          alelb_set_pops and alelb_get_pops exchange are those of c_i + U.
+                          alelb_batch_create refuses shifted solvers */
 } alelb_params;
 
 typedef struct alelb_mesh alelb_mesh;

@@ -61,7 +61,7 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double),
                 ("rho_inf", C.c_double), ("T_inf", C.c_double), ("u_inf", C.c_double * 2),
                 ("chord", C.c_double), ("precision", C.c_int32), ("flags", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("shift", C.c_double * 2)]
 
 
 _lib = None
@@ -204,6 +204,7 @@ def params_of(flow, precision=PREC_FP64, flags=None, stream=None):
     p.precision = int(precision)
     p.flags = int(flow.flags if flags is None else flags)
     p.stream = stream
+    p.shift[0], p.shift[1] = getattr(flow, "shift", (0.0, 0.0))
     return p
 
 
@@ -222,14 +223,7 @@ class Solver:
 
     def __init__(self, mesh: Mesh, flow, precision=PREC_FP64, flags=None, stream=None):
         L = load()
-        p = Params()
-        p.gamma, p.Pr, p.mu = flow.gamma, flow.Pr, flow.mu
-        p.rho_inf, p.T_inf = flow.rho_inf, flow.T_inf
-        p.u_inf[0], p.u_inf[1] = flow.u_inf
-        p.chord = flow.chord
-        p.precision = int(precision)
-        p.flags = int(flow.flags if flags is None else flags)
-        p.stream = stream
+        p = params_of(flow, precision, flags, stream)
         h = C.c_void_p()
         st = L.alelb_lb_init(mesh.h, C.byref(p), C.byref(h))
         if st != OK:

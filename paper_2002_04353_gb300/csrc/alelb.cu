@@ -23,6 +23,15 @@ namespace alelb {
 const char *const KT_NAMES[KT_N] = {"k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1",
                                     "k_collide", "k_propose"};
 
+// A lattice shift the library accepts: finite, |U_d| <= 1, and exact in
+// FP32, so that the FP32 and FP64 paths see the same velocities c_i + U.
+static bool shift_ok(const double U[2])
+{
+    for (int d = 0; d < 2; ++d)
+        if (!std::isfinite(U[d]) || std::fabs(U[d]) > 1.0 || (double)(float)U[d] != U[d]) return false;
+    return true;
+}
+
 MapScalarsF to_f32(const MapScalars &S, const HostTables &T)
 {
     MapScalarsF F;
@@ -35,6 +44,8 @@ MapScalarsF to_f32(const MapScalars &S, const HostTables &T)
     F.cm = (float)S.cm;
     F.Xc = (float)T.mp[3];
     F.Yc = (float)T.mp[4];
+    F.Ux = (float)S.Ux;
+    F.Uy = (float)S.Uy;
     return F;
 }
 
@@ -203,23 +214,15 @@ namespace {
 __global__ void k_kin_consts(KinParams<double> K, double rho_inf, double uxi, double uyi,
                              double T_inf, int ref_mode, double *out)
 {
-    double f[NQ], g[NQ], M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py;
+    double f[NQ], g[NQ];
     const double urx = ref_mode == 2 ? uxi : 0.0, ury = ref_mode == 2 ? uyi : 0.0;
-    feq9(rho_inf, urx, ury, T_inf, f);
-    double E0 = K.Cv * T_inf + 0.5 * (urx * urx + ury * ury);
-    gmoments(rho_inf, urx, ury, T_inf, E0, M0, qx, qy, Rxx, Rxy, Ryy);
-    psi_terms(rho_inf, urx, ury, T_inf, E0, pr, px, py);
-    gform9(T_inf, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, g);
+    equilibria(K, rho_inf, urx, ury, T_inf, f, g);
     for (int i = 0; i < NQ; ++i) {
         out[i] = ref_mode ? f[i] : 0.0;
         out[NQ + i] = ref_mode ? g[i] : 0.0;
     }
     // far field
-    feq9(rho_inf, uxi, uyi, T_inf, f);
-    double E = K.Cv * T_inf + 0.5 * (uxi * uxi + uyi * uyi);
-    gmoments(rho_inf, uxi, uyi, T_inf, E, M0, qx, qy, Rxx, Rxy, Ryy);
-    psi_terms(rho_inf, uxi, uyi, T_inf, E, pr, px, py);
-    gform9(T_inf, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, g);
+    equilibria(K, rho_inf, uxi, uyi, T_inf, f, g);
     for (int i = 0; i < NQ; ++i) {
         out[2 * NQ + i] = f[i];
         out[3 * NQ + i] = g[i];
@@ -247,7 +250,8 @@ __global__ void k_fill_uniform(StateDev<S> st, int N, const double *consts, doub
 // caller node n2o[a].
 template <class S>
 __global__ void k_import(StateDev<S> st, int N, const double *consts, const double *full,
-                         const double *fields, int have_fields, double Cv, const int *n2o)
+                         const double *fields, int have_fields, double Cv, double Ux, double Uy,
+                         const int *n2o)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
@@ -267,7 +271,7 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
         st.uy[a] = (fld_t<S>)fields[2 * N + o];
         st.T[a] = (fld_t<S>)fields[3 * N + o];
     } else {
-        double ux = jx / r, uy = jy / r, E = e2 / (2 * r);
+        double ux = jx / r + Ux, uy = jy / r + Uy, E = e2 / (2 * r); // lattice c_i + U
         st.rho[a] = (fld_t<S>)r;
         st.ux[a] = (fld_t<S>)ux;
         st.uy[a] = (fld_t<S>)uy;
@@ -336,17 +340,18 @@ cudaEvent_t get_event(alelb_solver *s)
 
 
 template <class S, class A>
-cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const MapScalars &sc)
+cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const MapScalars &sc_in)
 {
     alelb_mesh *m = s->mesh;
+    const MapScalars sc = solver_map(s, sc_in);
     const int N = m->T.N;
     const bool phi = !(s->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF));
     const bool fast = s->prec != ALELB_PREC_FP64;
     const MapScalarsF sf = to_f32(sc, m->T);
     // the transformed velocities' map: arrival time, or t_{n+1/2} (flag)
     // (the departure time under ALELB_FLAG_EXACT_CHAR)
-    const MapScalars scd = (s->flags & ALELB_FLAG_EXACT_CHAR) ? map_scalars(m->T.mkind, m->T.mp, s->t)
-                           : (s->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, s->t + 0.5)
+    const MapScalars scd = (s->flags & ALELB_FLAG_EXACT_CHAR) ? solver_map(s, map_scalars(m->T.mkind, m->T.mp, s->t))
+                           : (s->flags & ALELB_FLAG_MIDPOINT) ? solver_map(s, map_scalars(m->T.mkind, m->T.mp, s->t + 0.5))
                                                               : sc;
     const MapScalarsF sfd = to_f32(scd, m->T);
     int seq[KT_N], ns = 0;
@@ -453,7 +458,9 @@ template <class A> void fill_kin(alelb_solver *s, KinParams<A> &K)
     K.Pxy_ref = (A)pxy;
     K.Pyy_ref = (A)pyy;
     K.E2_ref = (A)e2;
-    K.flags = s->flags;
+    K.Ux = (A)s->U[0];
+    K.Uy = (A)s->U[1];
+    K.flags = (s->flags & ~FLAG_SHIFT) | shift_flag(s->U);
 }
 
 
@@ -469,12 +476,18 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
         m->err = "lb_init: the exact characteristic needs a rigid map (none, plunge, pitch, pitch with plunge)";
         return ALELB_ERR_ARG;
     }
+    if (!shift_ok(p->shift)) {
+        m->err = "lb_init: the lattice shift must be finite, at most 1 per component, and exact in FP32";
+        return ALELB_ERR_ARG;
+    }
     alelb_solver *s = new (std::nothrow) alelb_solver();
     if (!s) return ALELB_ERR_OOM;
     *out = s;
     s->mesh = m;
     s->prec = p->precision;
-    s->flags = p->flags;
+    s->flags = p->flags & ~FLAG_SHIFT;
+    s->U[0] = p->shift[0];
+    s->U[1] = p->shift[1];
     s->gamma = p->gamma;
     s->Pr = p->Pr;
     s->mu = p->mu;
@@ -510,6 +523,9 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
     if (st != cudaSuccess) return cuda_fail(s, st);
     KinParams<double> K0{};
     K0.Cv = s->Cv;
+    K0.Ux = s->U[0];
+    K0.Uy = s->U[1];
+    K0.flags = shift_flag(s->U);
     const int ref_mode = s->prec == ALELB_PREC_FP64 ? 0 : s->prec == ALELB_PREC_FP32_DEV ? 1 : 2;
     k_kin_consts<<<1, 1, 0, s->stream>>>(K0, s->rho_inf, s->uinf[0], s->uinf[1], s->T_inf, ref_mode,
                                          s->d_consts);
@@ -638,7 +654,7 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
     with_state(s, [&](auto &sx, auto &) {
         k_import<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch,
                                                           s->d_scratch + (size_t)18 * N, have, s->Cv,
-                                                          s->mesh->d_n2o);
+                                                          s->U[0], s->U[1], s->mesh->d_n2o);
     });
     st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the caller's arrays are free again
@@ -691,7 +707,7 @@ extern "C" alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cach
     }
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
-    MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t);
+    const MapScalars sc = solver_map(s, map_scalars(m->T.mkind, m->T.mp, t));
     int *de = (int *)s->d_scratch;
     int8_t *dk = (int8_t *)(s->d_scratch + (size_t)9 * N);
     k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, cache,
@@ -803,6 +819,10 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
         m->err = "lb_step_noalloc: the exact characteristic needs a rigid map (none, plunge, pitch, pitch with plunge)";
         return ALELB_ERR_ARG;
     }
+    if (!shift_ok(p->shift)) {
+        m->err = "lb_step_noalloc: the lattice shift must be finite, at most 1 per component, and exact in FP32";
+        return ALELB_ERR_ARG;
+    }
     const int N = m->T.N;
     if (N > ALELB_NOALLOC_MAX_NODES) {
         m->err = "lb_step_noalloc: the mesh has " + std::to_string(N) + " nodes; at most " +
@@ -849,6 +869,9 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     int *err = (int *)(consts + 4 * NQ);                              // inside the last 64
     KinParams<double> K{};
     K.Cv = 1.0 / (p->gamma - 1.0);
+    K.Ux = p->shift[0];
+    K.Uy = p->shift[1];
+    K.flags = shift_flag(p->shift);
     k_kin_consts<<<1, 1, 0, stream>>>(K, p->rho_inf, p->u_inf[0], p->u_inf[1], p->T_inf, 0, consts);
     double hc[4 * NQ];
     st = cudaGetLastError();
@@ -870,11 +893,12 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
         K.finf[i] = hc[2 * NQ + i];
         K.ginf[i] = hc[3 * NQ + i];
     }
-    K.flags = p->flags;
-    MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t + 1.0);
-    const MapScalars scd = (p->flags & ALELB_FLAG_EXACT_CHAR) ? map_scalars(m->T.mkind, m->T.mp, t)
-                           : (p->flags & ALELB_FLAG_MIDPOINT) ? map_scalars(m->T.mkind, m->T.mp, t + 0.5)
-                                                              : sc;
+    K.flags = (p->flags & ~FLAG_SHIFT) | shift_flag(p->shift);
+    MapScalars sc = with_shift(map_scalars(m->T.mkind, m->T.mp, t + 1.0), p->shift);
+    const MapScalars scd =
+        (p->flags & ALELB_FLAG_EXACT_CHAR) ? with_shift(map_scalars(m->T.mkind, m->T.mp, t), p->shift)
+        : (p->flags & ALELB_FLAG_MIDPOINT) ? with_shift(map_scalars(m->T.mkind, m->T.mp, t + 0.5), p->shift)
+                                           : sc;
     k_stream<double, double><<<(N + 127) / 128, 128, 0, stream>>>(m->dev, m->mst, sc, scd, K, sd, err, nullptr);
     if (!(p->flags & (ALELB_FLAG_PHI_OFF | ALELB_FLAG_COLLIDE_OFF)))
         k_deriv1<double, double, false><<<(N + 255) / 256, 256, 0, stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), sd);

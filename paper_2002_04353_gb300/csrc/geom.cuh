@@ -33,6 +33,7 @@ struct MapScalars {
     double vy, yoff;   // plunge velocity and offset
     double c, sn, thd; // rotation: cos, sin, angular rate
     double cm;         // cos - 1
+    double Ux, Uy;     // lattice shift U: the velocities are c_i + U (zero when unshifted)
 };
 
 struct MapStatic {
@@ -208,6 +209,7 @@ __device__ __forceinline__ void map_position(const MapStatic &M, const MapScalar
 struct MapScalarsF {
     float s, sd, vy, c, sn, thd, cm;
     float Xc, Yc;
+    float Ux, Uy; // lattice shift (FP32-exact)
 };
 
 ALELB_HD __forceinline__ void map_node_f32(const MapStatic &M, const MapScalarsF &S, int a,
@@ -317,6 +319,8 @@ ALELB_HD __forceinline__ void exact_departure(const MapStatic &M, const MapScala
                                               double X, double Y, double &chx, double &chy,
                                               double &px, double &py)
 {
+    cx = da(cx, S1.Ux); // the lattice velocity c_i + U
+    cy = da(cy, S1.Uy);
     switch (M.kind) {
     case MK_PLUNGE:
         px = ds(X, cx);
@@ -778,7 +782,7 @@ ALELB_HD inline void locate_node(const MeshDev &M, const MapStatic &MS, const Ma
     double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
     map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
     metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-    mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, flags_literal != 0, wx, wy);
+    mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), flags_literal != 0, wx, wy);
     for (int i = 0; i < NQ; ++i) {
         double chx, chy, px, py;
         departure(a11, a12, a21, a22, wx, wy, (double)lat_cx(i), (double)lat_cy(i), Xa.x, Xa.y, chx,
@@ -950,13 +954,17 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     F.A12 = -xY * inv;
     F.A21 = -yX * inv;
     F.A22 = xX * inv;
-    F.W1 = F.A11 * Vx + F.A12 * Vy;
-    F.W2 = F.A21 * Vx + F.A22 * Vy;
+    // the departure sees V_G - U (U the lattice shift, exact in FP32); the
+    // wall condition keeps V_G
+    const float Wx = Vx - sf.Ux, Wy = Vy - sf.Uy;
+    F.W1 = F.A11 * Wx + F.A12 * Wy;
+    F.W2 = F.A21 * Wx + F.A22 * Wy;
     F.Vx = Vx;
     F.Vy = Vy;
     float Amax = fmaxf(fmaxf(fabsf(F.A11), fabsf(F.A12)), fmaxf(fabsf(F.A21), fabsf(F.A22)));
-    float Vmax = fmaxf(fabsf(Vx), fabsf(Vy));
-    float Vmag = fabsf(Vx) + fabsf(Vy);
+    float Vmax = fmaxf(fabsf(Wx), fabsf(Wy));
+    const float Us = fabsf(sf.Ux) + fabsf(sf.Uy);
+    float Vmag = fabsf(Vx) + fabsf(Vy) + Us; // (the subtraction's rounding: u |V - U|)
     if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE || MS.kind == MK_BLENDED) {
         float dx = fabsf((Xf.x - sf.Xc) + Xf.z), dy = fabsf((Xf.y - sf.Yc) + Xf.w);
         Vmag += fabsf(sf.thd) * (dx + dy) + fabsf(sf.vy);
@@ -976,7 +984,7 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
     const float cv0 = 2.0f * Vmax;
     F.eps0 = 2.0f * (eps_A * cv0 + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv0);
-    F.er = 2.3e-16f * (fmaxf(fabsf(Xf.x), fabsf(Xf.y)) + 2.0f);
+    F.er = 2.3e-16f * (fmaxf(fabsf(Xf.x), fabsf(Xf.y)) + 2.0f + 2.0f * Us);
     F.ok = det > 16.0f * eps_det && isfinite(F.eps_c);
     return F;
 }
@@ -1204,7 +1212,7 @@ struct Pred32 {
             double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy, chx, chy;
             map_node(MS, sc, a, Xa, Ya, xX, xY, yX, yY, Vx, Vy);
             metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-            mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
+            mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), literal != 0, wx, wy);
             departure(a11, a12, a21, a22, wx, wy, lat_cx(i), lat_cy(i), Xa, Ya, chx, chy, px, py);
             have64 = true;
         }
@@ -1334,7 +1342,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
             double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
             map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
             metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-            mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
+            mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), literal != 0, wx, wy);
             departure(a11, a12, a21, a22, wx, wy, lat_cx(i), lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
         }
         if (chx == 0.0 && chy == 0.0) {
@@ -1370,7 +1378,7 @@ ALELB_HD inline void mixed_locate_node(const MeshDev &M, const MapStatic &MS,
     for (int i = 0; i < NQ; ++i) {
         int e;
         float qx, qy;
-        if (i == 0 && M.vzero[a]) { // c^_0 is exactly zero: the node's own value
+        if (i == 0 && M.vzero[a] && sf.Ux == 0.0f && sf.Uy == 0.0f) { // c^_0 exactly zero: the node's own value
             if (fast9) fast9[i] = 1;
             elem9[i] = -2;
             kind9[i] = 0;

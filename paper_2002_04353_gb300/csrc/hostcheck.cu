@@ -80,7 +80,7 @@ extern "C" int alelb_hostcheck_fast(const alelb_mesh_desc *d, double t_prev, dou
             double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
             map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
             metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-            mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, false, wx, wy);
+            mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), false, wx, wy);
             const int CXh[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
             const int CYh[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
             for (int i = 0; i < NQ; ++i) {
@@ -93,7 +93,7 @@ extern "C" int alelb_hostcheck_fast(const alelb_mesh_desc *d, double t_prev, dou
         }
     }
     MapScalars sc = map_scalars(T.mkind, T.mp, t);
-    MapScalarsF sf;
+    MapScalarsF sf{};
     sf.s = (float)sc.s;
     sf.sd = (float)sc.sd;
     sf.vy = (float)sc.vy;

@@ -98,6 +98,7 @@ struct alelb_solver {
     bool own_stream = false;
     double gamma = 1.4, Pr = 0.71, mu = 0, rho_inf = 1, T_inf = 0.3, uinf[2] = {0, 0}, chord = 1;
     double Cv = 2.5, Cp = 3.5;
+    double U[2] = {0, 0}; // lattice shift: velocities c_i + U
     double t = 0;
     int64_t nstep = 0;
     StateDev<double> sd{};  // ALELB_PREC_FP64
@@ -127,6 +128,17 @@ struct alelb_solver {
 };
 
 namespace alelb {
+// The internal flag bit of a shifted lattice.
+inline int shift_flag(const double U[2]) { return (U[0] != 0.0 || U[1] != 0.0) ? FLAG_SHIFT : 0; }
+// Map scalars carrying the lattice shift U.
+inline MapScalars with_shift(MapScalars S, const double U[2])
+{
+    S.Ux = U[0];
+    S.Uy = U[1];
+    return S;
+}
+inline MapScalars solver_map(const alelb_solver *s, const MapScalars &S) { return with_shift(S, s->U); }
+
 // Calls fn(state, kinetic parameters) with the solver's state of its
 // precision (the deviation forms share the FP32 kinetic parameters).
 template <class Fn> auto with_state(alelb_solver *s, Fn &&fn)

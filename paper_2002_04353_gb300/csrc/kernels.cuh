@@ -248,7 +248,8 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
                 double xX, xY, yX, yY;
                 map_node(MS, scd, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
                 metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
-                mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
+                mesh_velocity_term(a11, a12, a21, a22, ds(Vx, scd.Ux), ds(Vy, scd.Uy),
+                                   (K.flags & FLAG_LITERAL_VG) != 0, wx, wy);
                 have64 = true;
             }
             double chx, chy, px, py;
@@ -368,13 +369,15 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
     }
     // moments (Sec. IV): rho, u, E, T from the streamed populations
     A rho = K.rho_ref + sfm;
-    A ux = (K.jx_ref + jx) / rho, uy = (K.jy_ref + jy) / rho;
+    // w = u - U (relative to the lattice shift), u = w + U
+    A rwx = (K.jx_ref + jx) / rho, rwy = (K.jy_ref + jy) / rho;
+    A ux = rwx + K.Ux, uy = rwy + K.Uy;
     A E = (K.E2_ref + sg) / (A(2) * rho);
     A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
     A k3 = A(1) - A(3) * T;
-    st.Qx[a] = (fld_t<S>)(rho * ux * k3 - rho * ux * ux * ux);
-    st.Qy[a] = (fld_t<S>)(rho * uy * k3 - rho * uy * uy * uy);
+    st.Qx[a] = (fld_t<S>)(rho * rwx * k3 - rho * rwx * rwx * rwx);
+    st.Qy[a] = (fld_t<S>)(rho * rwy * k3 - rho * rwy * rwy * rwy);
     st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
 }
 
@@ -504,7 +507,7 @@ __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams
                                                const FastMap &F, float4 Xf, float bd, int c)
 {
     const int N = M.N;
-    if (i == 0 && M.vzero[a]) { // c^_0 exactly zero: the node's own value
+    if (i == 0 && M.vzero[a] && !(K.flags & FLAG_SHIFT)) { // c^_0 exactly zero: the node's own value
         fg_copy(st.str, st.post, 0, a, N);
         return 0;
     }
@@ -788,13 +791,14 @@ __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateD
     const A jy = K.jy_ref + ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
     const A sg = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
     const A rho = K.rho_ref + sf;
-    const A ux = jx / rho, uy = jy / rho;
+    const A wx = jx / rho, wy = jy / rho; // u - U
+    const A ux = wx + K.Ux, uy = wy + K.Uy;
     const A E = (K.E2_ref + sg) / (A(2) * rho);
     const A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
     const A k3 = A(1) - A(3) * T;
-    st.Qx[a] = (fld_t<S>)(rho * ux * k3 - rho * ux * ux * ux);
-    st.Qy[a] = (fld_t<S>)(rho * uy * k3 - rho * uy * uy * uy);
+    st.Qx[a] = (fld_t<S>)(rho * wx * k3 - rho * wx * wx * wx);
+    st.Qy[a] = (fld_t<S>)(rho * wy * k3 - rho * wy * wy * wy);
     st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
 }
 

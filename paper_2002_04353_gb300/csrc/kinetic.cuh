@@ -7,6 +7,14 @@
 // reference state; with ref = 0 (FP64 mode) they are the populations
 // themselves.  In FP32 mode ref_i = f^eq_i(rho_inf, 0, T_inf) and
 // g^eq_i(rho_inf, 0, T_inf), which keeps the stored numbers small.
+//
+// Shifted lattice (Sec. V.D: velocities c_i + U; the model is deferred to
+// another paper, so this is a reading): every population set carries the
+// lab-frame moments it carries on the plain lattice.  f^eq is the product
+// form in u - U; the general form of Eq. geq_gstar is applied to moments
+// taken about U; psi restores the diagonal second central moments (the
+// printed psi at U = 0); Q' is taken in u - U; phi_i = A_ia X_a stays on
+// the relative velocities c_i.  Moments: rho u = sum (c_i + U) f_i.
 #pragma once
 
 namespace alelb {
@@ -18,11 +26,13 @@ template <class A> struct KinParams {
     A rho_ref, jx_ref, jy_ref, Pxx_ref, Pxy_ref, Pyy_ref, E2_ref;
     A fref[NQ], gref[NQ];           // reference populations (zero in FP64 mode)
     A finf[NQ], ginf[NQ];           // far-field populations minus the reference
+    A Ux, Uy;                       // lattice shift U (zero on the plain lattice)
     int flags;
 };
 
 enum : int { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQ = 8, FLAG_SLIP = 16,
-             FLAG_MIDPOINT = 32, FLAG_EXACT_CHAR = 64 };
+             FLAG_MIDPOINT = 32, FLAG_EXACT_CHAR = 64,
+             FLAG_SHIFT = 128 /* internal: U != 0 */ };
 
 // One-dimensional factors Phi_c(u, T) of Eq. feq.
 template <class A> __device__ __forceinline__ void phi3(A u, A T, A &m, A &z, A &p)
@@ -92,6 +102,31 @@ __device__ __forceinline__ void psi_terms(A rho, A ux, A uy, A T, A E, A &pr, A 
     py = A(-0.5) * Yy;
 }
 
+// General form of lab-frame moments on the lattice shifted by U: the
+// moments about U, M'_a = M_a - U_a M0, M'_ab = M_ab - U_a M_b - U_b M_a +
+// U_a U_b M0, then Eq. geq_gstar on the relative velocities, with psi
+// (when with_psi) Y_a = (M'_aa - M0 T)(1 - 3T)/(2T) on the rest (+) and
+// axis (-1/2) velocities: the part of the diagonal second moments that
+// the W_i-weighted form misses on the lattice (sum W_i c_a^4 = T).
+template <class A>
+__device__ __forceinline__ void gform_about(A Ux, A Uy, A T, A M0, A Mx, A My, A Mxx, A Mxy, A Myy,
+                                            bool with_psi, A G[NQ])
+{
+    const A cMx = Mx - Ux * M0, cMy = My - Uy * M0;
+    const A cMxx = Mxx - A(2) * Ux * Mx + Ux * Ux * M0;
+    const A cMxy = Mxy - Ux * My - Uy * Mx + Ux * Uy * M0;
+    const A cMyy = Myy - A(2) * Uy * My + Uy * Uy * M0;
+    A pr = 0, px = 0, py = 0;
+    if (with_psi) {
+        const A k = (A(1) - A(3) * T) / (A(2) * T);
+        const A Yx = (cMxx - M0 * T) * k, Yy = (cMyy - M0 * T) * k;
+        pr = Yx + Yy;
+        px = A(-0.5) * Yx;
+        py = A(-0.5) * Yy;
+    }
+    gform9(T, M0, cMx, cMy, cMxx, cMxy, cMyy, pr, px, py, G);
+}
+
 // g^eq (Table I, first row) or g* (second row, with q*_a = q^eq_a +
 // 2 u_b (P_ab - P^eq_ab)) for the given macroscopic state.
 template <class A>
@@ -106,6 +141,22 @@ __device__ __forceinline__ void gmoments(A rho, A ux, A uy, A T, A E, A &M0, A &
     Rxx = a * (T + ux * ux) + b * (T + A(2) * ux * ux);
     Rxy = a * (ux * uy) + b * (A(2) * ux * uy);
     Ryy = a * (T + uy * uy) + b * (T + A(2) * uy * uy);
+}
+
+// f^eq and g^eq (Table I, first row) of the solver's lattice at (rho, u, T).
+template <class A>
+__device__ __forceinline__ void equilibria(const KinParams<A> &K, A rho, A ux, A uy, A T, A f[NQ], A g[NQ])
+{
+    feq9(rho, ux - K.Ux, uy - K.Uy, T, f);
+    const A E = K.Cv * T + A(0.5) * (ux * ux + uy * uy);
+    A M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py;
+    gmoments(rho, ux, uy, T, E, M0, qx, qy, Rxx, Rxy, Ryy);
+    if (K.flags & FLAG_SHIFT) {
+        gform_about(K.Ux, K.Uy, T, M0, qx, qy, Rxx, Rxy, Ryy, true, g);
+    } else {
+        psi_terms(rho, ux, uy, T, E, pr, px, py);
+        gform9(T, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, g);
+    }
 }
 
 // Collision of one node on deviations: f, g in (streamed, deviations),
@@ -124,7 +175,9 @@ __device__ __forceinline__ bool collide_node(const KinParams<A> &K, A f[NQ], A g
     dyy = f[2] + f[4] + f[5] + f[6] + f[7] + f[8];
     dxy = (f[5] + f[7]) - (f[6] + f[8]);
     A rho = K.rho_ref + sf;
-    A ux = jx / rho, uy = jy / rho;
+    // relative velocity w = sum c_i f_i / rho; lab velocity u = w + U
+    const A wx = jx / rho, wy = jy / rho;
+    A ux = wx + K.Ux, uy = wy + K.Uy;
     A E = (K.E2_ref + sg) / (A(2) * rho);
     A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
     rho_o = rho;
@@ -133,22 +186,28 @@ __device__ __forceinline__ bool collide_node(const KinParams<A> &K, A f[NQ], A g
     T_o = T;
     if (!(rho > A(0)) || !(T > A(0))) return false;
     if (K.flags & FLAG_COLLIDE_OFF) return true;
-    // P_ab - P^eq_ab from deviations plus the reference's own P_ab
+    // P_ab - P^eq_ab from deviations plus the reference's own P_ab (about
+    // U on the shifted lattice: the difference is the same in every frame)
     A Pxx = K.Pxx_ref + dxx, Pyy = K.Pyy_ref + dyy, Pxy = K.Pxy_ref + dxy;
-    A dPxx = Pxx - (rho * ux * ux + rho * T);
-    A dPxy = Pxy - rho * ux * uy;
-    A dPyy = Pyy - (rho * uy * uy + rho * T);
+    A dPxx = Pxx - (rho * wx * wx + rho * T);
+    A dPxy = Pxy - rho * wx * wy;
+    A dPyy = Pyy - (rho * wy * wy + rho * T);
     A omega = A(1) / (K.mu / (rho * T) + A(0.5));
     A omega1 = A(1) / ((A(1) / omega - A(0.5)) / K.Pr + A(0.5));
     A fe[NQ], ge[NQ], gs[NQ];
-    feq9(rho, ux, uy, T, fe);
+    feq9(rho, wx, wy, T, fe);
     A M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py;
     gmoments(rho, ux, uy, T, E, M0, qx, qy, Rxx, Rxy, Ryy);
-    psi_terms(rho, ux, uy, T, E, pr, px, py);
-    gform9(T, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, ge);
     A qsx = qx + A(2) * (ux * dPxx + uy * dPxy);
     A qsy = qy + A(2) * (ux * dPxy + uy * dPyy);
-    gform9(T, M0, qsx, qsy, Rxx, Rxy, Ryy, pr, px, py, gs);
+    if (K.flags & FLAG_SHIFT) {
+        gform_about(K.Ux, K.Uy, T, M0, qx, qy, Rxx, Rxy, Ryy, true, ge);
+        gform_about(K.Ux, K.Uy, T, M0, qsx, qsy, Rxx, Rxy, Ryy, true, gs);
+    } else {
+        psi_terms(rho, ux, uy, T, E, pr, px, py);
+        gform9(T, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, ge);
+        gform9(T, M0, qsx, qsy, Rxx, Rxy, Ryy, pr, px, py, gs);
+    }
     A hx = A(0.5) * Xx, hy = A(0.5) * Xy; // phi_i = A_ia X_a: +-X/2 on the axis velocities
     A om1 = omega1 - omega;
 #pragma unroll
@@ -189,13 +248,18 @@ __device__ __forceinline__ void grad_missing(const KinParams<A> &K, A rho, A ux,
     A R1xy = c2 * (Sxy * ET2 + ux * dEy + uy * dEx);
     A R1yy = c2 * (Syy * ET2 + A(2) * uy * dEy);
     A fe[NQ], ge[NQ], f1[NQ], g1[NQ];
-    feq9(rho, ux, uy, T, fe);
+    feq9(rho, ux - K.Ux, uy - K.Uy, T, fe);
     A M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py;
     gmoments(rho, ux, uy, T, E, M0, qx, qy, Rxx, Rxy, Ryy);
-    psi_terms(rho, ux, uy, T, E, pr, px, py);
-    gform9(T, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, ge);
     gform9(T, A(0), A(0), A(0), P1xx, P1xy, P1yy, A(0), A(0), A(0), f1);
-    gform9(T, A(0), q1x, q1y, R1xx, R1xy, R1yy, A(0), A(0), A(0), g1);
+    if (K.flags & FLAG_SHIFT) {
+        gform_about(K.Ux, K.Uy, T, M0, qx, qy, Rxx, Rxy, Ryy, true, ge);
+        gform_about(K.Ux, K.Uy, T, A(0), q1x, q1y, R1xx, R1xy, R1yy, false, g1);
+    } else {
+        psi_terms(rho, ux, uy, T, E, pr, px, py);
+        gform9(T, M0, qx, qy, Rxx, Rxy, Ryy, pr, px, py, ge);
+        gform9(T, A(0), q1x, q1y, R1xx, R1xy, R1yy, A(0), A(0), A(0), g1);
+    }
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
         f[i] = (fe[i] - K.fref[i]) + f1[i];

@@ -47,7 +47,7 @@ __global__ void k_samples(MeshDev M, MapStatic MS, MapScalars sc, MapScalarsF sf
     map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
     metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
     const int literal = (flags & FLAG_LITERAL_VG) != 0;
-    mesh_velocity_term(a11, a12, a21, a22, Vx, Vy, literal != 0, wx, wy);
+    mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), literal != 0, wx, wy);
     const int r0 = M.ring_ptr[a], r1 = M.ring_ptr[a + 1];
     for (int i = 0; i < NQ; ++i) {
         const size_t q = (size_t)i * N + a;
@@ -677,7 +677,7 @@ extern "C" alelb_status alelb_samples(alelb_solver *s, double t, float *feat, in
 {
     if (!s || !s->mesh || !feat || !slot || !bary || !nring) return ALELB_ERR_ARG;
     alelb_mesh *m = s->mesh;
-    const MapScalars sc = map_scalars(m->T.mkind, m->T.mp, t);
+    const MapScalars sc = solver_map(s, map_scalars(m->T.mkind, m->T.mp, t));
     k_samples<<<(m->T.N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, feat,
                                                             slot, bary, nring, s->d_err);
     cudaError_t st = cudaGetLastError();

@@ -4,6 +4,7 @@ Element choices must agree bit for bit; FP64 populations to 1e-12 relative
 (max |diff| / max |value| per population set); the FP32-deviation mode to
 2e-4 in density, velocity and temperature.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -21,8 +22,13 @@ TOL32 = 2e-4
 
 def _eq_state(mesh, flow, amp, seed):
     rho, ux, uy, T = I.random_state(mesh.n_nodes, flow.rho_inf, flow.T_inf, flow.u_inf, amp, seed)
-    f = np.stack([O.feq(rho[a], ux[a], uy[a], T[a]) for a in range(mesh.n_nodes)], 1)
-    g = np.stack([O.geq(rho[a], ux[a], uy[a], T[a], CV) for a in range(mesh.n_nodes)], 1)
+    U = getattr(flow, "shift", (0.0, 0.0))
+    if any(U):  # populations of the shifted lattice c_i + U
+        f = np.stack([O.feq_shift(rho[a], ux[a], uy[a], T[a], U) for a in range(mesh.n_nodes)], 1)
+        g = np.stack([O.geq_shift(rho[a], ux[a], uy[a], T[a], CV, U) for a in range(mesh.n_nodes)], 1)
+    else:
+        f = np.stack([O.feq(rho[a], ux[a], uy[a], T[a]) for a in range(mesh.n_nodes)], 1)
+        g = np.stack([O.geq(rho[a], ux[a], uy[a], T[a], CV) for a in range(mesh.n_nodes)], 1)
     return f, g, rho, ux, uy, T
 
 
@@ -280,8 +286,12 @@ def _compare16(o, s, prec, flow, n, what):
     rounding's propagation through later interpolations (P2 weights sum to
     one) and adds the FP32 bound."""
     st = o.state()
-    fi = O.feq(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf)
-    gi = O.geq(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf, CV)
+    if any(flow.shift):
+        fi = O.feq_shift(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf, flow.shift)
+        gi = O.geq_shift(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf, CV, flow.shift)
+    else:
+        fi = O.feq(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf)
+        gi = O.geq(flow.rho_inf, flow.u_inf[0], flow.u_inf[1], flow.T_inf, CV)
     D = (np.abs(st["f"] - fi[:, None]).sum(0) + np.abs(st["g"] - gi[:, None]).sum(0)).max()
     rmin = st["rho"].min()
     base = 2 * n * U16[prec] * D / rmin
@@ -429,6 +439,71 @@ def test_exact_characteristic_refused_where_the_map_has_no_closed_inverse():
     assert ex.value.status == -1
     mesh, motion = LOC_CASES["omesh_plunge"]()
     s = alelb.Solver(alelb.Mesh(mesh, motion), flow, alelb.PREC_FP32_DEV, flags=O.FLAG_EXACT_CHAR)
+    with pytest.raises(alelb.AlelbError) as ex:
+        alelb.Batch([s])
+    assert ex.value.status == -1
+
+
+# ---------------------------------------------------------------------------
+# shifted lattice (velocities c_i + U; Sec. V.D's transonic case)
+# ---------------------------------------------------------------------------
+
+U03 = (float(np.float32(0.3)), 0.0)  # 0.3 rounded to FP32: the library wants U exact in FP32
+
+
+def _shift_cases():
+    mesh, motion = LOC_CASES["omesh_pitch"]()
+    yield "pitching airfoil Ma 0.75", mesh, motion, I.flow_params(0.75, T_inf=0.3, Re=500.0, chord=200.0,
+                                                                   shift=U03)
+    box = I.uniform_flow_case(n=16, L=32.0, period_steps=50.0, Ma=0.85, T_inf=0.3)
+    fl = dataclasses.replace(box.flow, shift=(U03[0], float(np.float32(-0.05))))
+    st = _eq_state(box.mesh, fl, 0.01, seed=5)
+    yield "deforming box Ma 0.85", box.mesh, box.motion, (fl, st)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_shifted_lattice_fp64_fp32_and_16bit(which):
+    name, mesh, motion, fl = list(_shift_cases())[which]
+    fl, st = fl if isinstance(fl, tuple) else (fl, None)
+    o, m, s = _pair(mesh, motion, fl, state=st)
+    o.step(4)
+    s.lb_step(4)
+    _compare64(o, s, f"{name}, shifted, FP64")
+    o2, m2, s2 = _pair(mesh, motion, fl, prec=alelb.PREC_FP32_DEV, state=st)
+    o2.step(4)
+    s2.lb_step(4)
+    _compare_mixed(o2, s2, f"{name}, shifted, FP32")
+    for prec in PREC16:
+        o3, m3, s3 = _pair(mesh, motion, fl, prec=prec, state=st)
+        o3.step(4)
+        s3.lb_step(4)
+        _compare16(o3, s3, prec, fl, 4, f"{name}, shifted")
+    # the shift changes the result
+    o4 = O.Oracle(mesh, motion, dataclasses.replace(fl, shift=(0.0, 0.0)))
+    if st is not None:
+        o4.set_state(*_eq_state(mesh, dataclasses.replace(fl, shift=(0.0, 0.0)), 0.01, seed=5))
+    o4.step(4)
+    assert _rel(o4.state()["ux"], o.state()["ux"]) > 1e-9
+
+
+def test_shifted_lattice_with_the_exact_characteristic():
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    fl = I.flow_params(0.5, T_inf=0.3, Re=500.0, chord=200.0, shift=U03)
+    o, m, s = _pair(mesh, motion, fl, flags=O.FLAG_EXACT_CHAR)
+    o.step(3)
+    s.lb_step(3)
+    _compare64(o, s, "plunging airfoil, shifted, exact characteristic")
+
+
+def test_shifted_lattice_refusals():
+    mesh, motion = LOC_CASES["omesh_plunge"]()
+    m = alelb.Mesh(mesh, motion)
+    for bad in ((0.3, 0.0), (1.5, 0.0), (float("nan"), 0.0)):  # 0.3 is not exact in FP32
+        fl = I.flow_params(0.5, T_inf=0.3, Re=500.0, chord=200.0, shift=bad)
+        with pytest.raises(alelb.AlelbError) as ex:
+            alelb.Solver(m, fl, alelb.PREC_FP32_DEV)
+        assert ex.value.status == -1
+    s = alelb.Solver(m, I.flow_params(0.5, T_inf=0.3, Re=500.0, chord=200.0, shift=U03), alelb.PREC_FP32_DEV)
     with pytest.raises(alelb.AlelbError) as ex:
         alelb.Batch([s])
     assert ex.value.status == -1

@@ -23,19 +23,21 @@ CV = 1.0 / (1.4 - 1.0)
 
 def _state(mesh, flow, seed):
     rho, ux, uy, T = I.random_state(mesh.n_nodes, flow.rho_inf, flow.T_inf, flow.u_inf, 0.01, seed)
-    f = np.stack([O.feq(rho[a], ux[a], uy[a], T[a]) for a in range(mesh.n_nodes)], 1)
-    g = np.stack([O.geq(rho[a], ux[a], uy[a], T[a], CV) for a in range(mesh.n_nodes)], 1)
+    U = flow.shift
+    f = np.stack([O.feq_shift(rho[a], ux[a], uy[a], T[a], U) for a in range(mesh.n_nodes)], 1)
+    g = np.stack([O.geq_shift(rho[a], ux[a], uy[a], T[a], CV, U) for a in range(mesh.n_nodes)], 1)
     return f, g, rho, ux, uy, T
 
 
-@pytest.mark.parametrize("which", ["airfoil", "box"])
+@pytest.mark.parametrize("which", ["airfoil", "box", "shifted airfoil"])
 def test_noalloc_step_matches_the_allocating_solver_twice(which):
     import torch
 
-    if which == "airfoil":
+    if which != "box":
         mesh = I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0)
         motion = I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.002)
-        flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+        shift = (float(np.float32(0.3)), 0.0) if which == "shifted airfoil" else (0.0, 0.0)
+        flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0, shift=shift)
     else:
         case = I.uniform_flow_case(n=16, L=32.0, period_steps=50.0)
         mesh, motion, flow = case.mesh, case.motion, case.flow
