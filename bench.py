@@ -20,6 +20,7 @@ Under torchrun (N > 1) every rank runs an independent replica (the sweep
 workloads shard cases across GPUs with no exchange), so scaling is weak.
 """
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -38,6 +39,7 @@ from paper_2002_04353_gb300 import inputs as I  # noqa: E402
 
 METRIC = "M node-updates/s on 1 GB300 (mixed/batched vs FP64 plain) + % HBM roofline"
 UNIT = "M node-updates/s"
+SHIFT03 = float(np.float32(0.3))  # the transonic case's lattice shift, rounded to FP32
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -370,9 +372,10 @@ def run_learned(alelb, torch, dev, args):
                          "source": f"pitch mesh {c3.mesh.n_nodes} nodes, 10 map times over one period"}}
 
 
-def run_precision(alelb, torch, dev, args):
+def run_precision(alelb, torch, dev, args, Ma, shift=(0.0, 0.0), flags=0):
     """Storage precision on the 600,320-node deforming pitching mesh
-    (alpha = 0.1 + 2.5 deg sin(omega t), k = 0.08, Mach `--prec-mach`): the
+    (alpha = 0.1 + 2.5 deg sin(omega t), k = 0.08, Mach Ma, lattice shift
+    `shift`, solver flags `flags`): the
     FP64, FP32-deviation, BF16-deviation and FP16-deviation forms advance
     the same free-stream start by the same steps.  Each deviation form
     reports its throughput over the last `--prec-steps` steps (L2 flushed
@@ -383,7 +386,8 @@ def run_precision(alelb, torch, dev, args):
     form, FP32 included, differs there from FP64 by far more than its
     rounding).  A form whose state leaves the admissible range is reported
     as diverged."""
-    case = I.pitch_case(ni=640, nj=235, Ma=args.prec_mach)
+    case = I.pitch_case(ni=640, nj=235, Ma=Ma)
+    case = dataclasses.replace(case, flow=dataclasses.replace(case.flow, shift=shift, flags=flags))
     mesh = alelb.Mesh(case.mesh, case.motion)
     N, E = case.mesh.n_nodes, case.mesh.n_elems
     stream = torch.cuda.Stream(device=dev)
@@ -444,8 +448,11 @@ def run_precision(alelb, torch, dev, args):
             r[f"error_vs_fp64_step{W}"] = errors(early, ref_early)
             r[f"error_vs_fp64_step{W + K}"] = errors(mo, ref)
         out[label] = r
-    return {"unit": UNIT, "workload": f"pitch600k: deforming O-mesh {N} nodes, Mach {args.prec_mach}, "
-                                      f"alpha 0.1 + 2.5 deg sin(wt), k 0.08", "steps": W + K, "timed_steps": K,
+    walls = ("slip walls, equilibrium missing populations" if flags == (alelb.FLAG_SLIP_WALL | alelb.FLAG_BC_EQUILIBRIUM)
+             else "the paper's wall condition" if flags == 0 else f"flags {flags}")
+    return {"unit": UNIT, "workload": f"pitch600k: deforming O-mesh {N} nodes, Mach {Ma}, "
+                                      f"alpha 0.1 + 2.5 deg sin(wt), k 0.08, lattice shift {shift}, {walls}",
+            "steps": W + K, "timed_steps": K,
             "errors": f"normalised by rho_inf, |u_inf|, T_inf; max and RMS over nodes after {W} and {W + K} steps",
             **out}
 
@@ -549,7 +556,14 @@ def run_ours(args):
 
     batched = None if args.no_batched else run_batched(alelb, torch, dev, world, rank, args)
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
-    precision = None if (args.no_precision or world > 1) else run_precision(alelb, torch, dev, args)
+    precision = precision_low = None
+    if not (args.no_precision or world > 1):
+        # config 3 at its own Mach number: the shifted lattice of the transonic
+        # case and the inviscid-wall variant (equilibrium missing populations)
+        precision = run_precision(alelb, torch, dev, args, args.prec_mach, (SHIFT03, 0.0),
+                                  alelb.FLAG_SLIP_WALL | alelb.FLAG_BC_EQUILIBRIUM)
+        # the paper's wall condition on the plain lattice, at a Mach number it holds
+        precision_low = run_precision(alelb, torch, dev, args, 0.3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -588,6 +602,7 @@ def run_ours(args):
             "batched": batched,
             "learned_proposal": learned,
             "precision_study": precision,
+            "precision_study_ma03": precision_low,
             "locate": {"walks_per_step": info32["walks_timed"] / K,
                        "verified_previous_element_rate": 1.0 - info32["walks_timed"] / (9.0 * N * K)},
             "step_ms": [round(x, 4) for x in info32["step_ms"]],
@@ -615,7 +630,7 @@ def main():
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=10)
     ap.add_argument("--prec-steps", type=int, default=200)
-    ap.add_argument("--prec-mach", type=float, default=0.3)
+    ap.add_argument("--prec-mach", type=float, default=0.75)
     ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

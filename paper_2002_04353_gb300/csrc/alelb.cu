@@ -46,6 +46,8 @@ MapScalarsF to_f32(const MapScalars &S, const HostTables &T)
     F.Yc = (float)T.mp[4];
     F.Ux = (float)S.Ux;
     F.Uy = (float)S.Uy;
+    F.Us = std::fabs(F.Ux) + std::fabs(F.Uy);
+    F.er0 = 2.0f + 2.0f * F.Us;
     return F;
 }
 

@@ -210,6 +210,8 @@ struct MapScalarsF {
     float s, sd, vy, c, sn, thd, cm;
     float Xc, Yc;
     float Ux, Uy; // lattice shift (FP32-exact)
+    float Us;     // |Ux| + |Uy|
+    float er0;    // 2 + 2 Us: the offset's reach in the canonical point's rounding bound
 };
 
 ALELB_HD __forceinline__ void map_node_f32(const MapStatic &M, const MapScalarsF &S, int a,
@@ -963,8 +965,7 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     F.Vy = Vy;
     float Amax = fmaxf(fmaxf(fabsf(F.A11), fabsf(F.A12)), fmaxf(fabsf(F.A21), fabsf(F.A22)));
     float Vmax = fmaxf(fabsf(Wx), fabsf(Wy));
-    const float Us = fabsf(sf.Ux) + fabsf(sf.Uy);
-    float Vmag = fabsf(Vx) + fabsf(Vy) + Us; // (the subtraction's rounding: u |V - U|)
+    float Vmag = fabsf(Vx) + fabsf(Vy) + sf.Us; // (the subtraction's rounding: u |V - U|)
     if (MS.kind == MK_PITCH || MS.kind == MK_PITCH_PLUNGE || MS.kind == MK_BLENDED) {
         float dx = fabsf((Xf.x - sf.Xc) + Xf.z), dy = fabsf((Xf.y - sf.Yc) + Xf.w);
         Vmag += fabsf(sf.thd) * (dx + dy) + fabsf(sf.vy);
@@ -984,7 +985,7 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     F.eps_c = 2.0f * (eps_A * cv + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv);
     const float cv0 = 2.0f * Vmax;
     F.eps0 = 2.0f * (eps_A * cv0 + 2.0f * Amax * eps_V + 6.0f * u * Amax * cv0);
-    F.er = 2.3e-16f * (fmaxf(fabsf(Xf.x), fabsf(Xf.y)) + 2.0f + 2.0f * Us);
+    F.er = 2.3e-16f * (fmaxf(fabsf(Xf.x), fabsf(Xf.y)) + sf.er0);
     F.ok = det > 16.0f * eps_det && isfinite(F.eps_c);
     return F;
 }

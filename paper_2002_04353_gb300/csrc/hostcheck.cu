@@ -103,6 +103,7 @@ extern "C" int alelb_hostcheck_fast(const alelb_mesh_desc *d, double t_prev, dou
     sf.cm = (float)sc.cm;
     sf.Xc = (float)T.mp[3];
     sf.Yc = (float)T.mp[4];
+    sf.er0 = 2.0f;
     for (int a = 0; a < N; ++a) {
         int e9[NQ];
         int8_t k9[NQ], f9[NQ];
