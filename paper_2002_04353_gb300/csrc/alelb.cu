@@ -383,12 +383,15 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
         case KT_FAST:
             // one thread per node saves the nine map evaluations of a node,
             // which count on large meshes unless the map is a translation
-            if (N < FAST_G_NODES || m->T.mkind == MK_NONE || m->T.mkind == MK_PLUNGE)
-                launch_pdl(k_stream_fast<S, A, FAST_G>, dim3((N + FAST_BS - 1) / FAST_BS, NQ / FAST_G),
+            if (m->T.mkind == MK_NONE || m->T.mkind == MK_PLUNGE)
+                launch_pdl(k_stream_fast<S, A, FAST_G, true>, dim3((N + FAST_BS - 1) / FAST_BS, NQ / FAST_G),
+                           dim3(FAST_BS), s->stream, m->dev, m->mst, sfd, K, st);
+            else if (N < FAST_G_NODES)
+                launch_pdl(k_stream_fast<S, A, FAST_G, false>, dim3((N + FAST_BS - 1) / FAST_BS, NQ / FAST_G),
                            dim3(FAST_BS), s->stream, m->dev, m->mst, sfd, K, st);
             else
-                launch_pdl(k_stream_fast<S, A, NQ>, dim3((N + FAST_BS - 1) / FAST_BS, 1), dim3(FAST_BS), s->stream,
-                           m->dev, m->mst, sfd, K, st);
+                launch_pdl(k_stream_fast<S, A, NQ, false>, dim3((N + FAST_BS - 1) / FAST_BS, 1), dim3(FAST_BS),
+                           s->stream, m->dev, m->mst, sfd, K, st);
             break;
         case KT_SLOW: {
             // every block resident at once: the list is spread over all

@@ -990,6 +990,38 @@ ALELB_HD __forceinline__ FastMap fast_map(const MapStatic &MS, const MapScalarsF
     return F;
 }
 
+// fast_map for the translations (no map, plunge): the identity metric and
+// V_G = (0, vy), with every term of the general bound that is fixed by them
+// written as its value (det = G = Amax = 1, eps_g = 0, eps_det = 3u,
+// eps_A = 5u, all exact); saves the general map's instructions in the
+// propagation kernel, which is bound by instruction issue.
+ALELB_HD __forceinline__ FastMap fast_map_translation(const MapScalarsF &sf, float4 Xf)
+{
+    const float u = 5.9604644775390625e-08f;
+    FastMap F;
+    F.A11 = 1.0f;
+    F.A12 = -0.0f;
+    F.A21 = -0.0f;
+    F.A22 = 1.0f;
+    const float Vy = sf.vy; // zero without a map
+    const float Wx = 0.0f - sf.Ux, Wy = Vy - sf.Uy;
+    F.W1 = Wx;
+    F.W2 = Wy;
+    F.Vx = 0.0f;
+    F.Vy = Vy;
+    const float Vmax = fmaxf(fabsf(Wx), fabsf(Wy));
+    const float Vmag = fabsf(Vy) + sf.Us;
+    const float eps_A = 5.0f * u;
+    const float eps_V = 8.0f * u * Vmag;
+    const float cv = 2.0f + 2.0f * Vmax;
+    F.eps_c = 2.0f * (eps_A * cv + 2.0f * eps_V + 6.0f * u * cv);
+    const float cv0 = 2.0f * Vmax;
+    F.eps0 = 2.0f * (eps_A * cv0 + 2.0f * eps_V + 6.0f * u * cv0);
+    F.er = 2.3e-16f * (fmaxf(fabsf(Xf.x), fabsf(Xf.y)) + sf.er0);
+    F.ok = isfinite(F.eps_c); // det = 1 > 16 eps_det
+    return F;
+}
+
 // The fast path's decision for population i of a node: true (element e,
 // FP32 offset q from its first vertex) when the cached element c provably
 // holds the FP64 departure point strictly inside and the departure segment

@@ -580,7 +580,7 @@ static_assert(NQ % FAST_G == 0 && NQ % BATCH_FAST_G == 0, "directions per thread
 
 // Populations G y .. G y + G - 1 of node a (y = blockIdx.y): settled, or
 // entered in the work list.
-template <int G, class S, class A>
+template <int G, class S, class A, bool TR = false>
 __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapStatic &MS,
                                                   const MapScalarsF &sf, const KinParams<A> &K,
                                                   const StateDev<S> &st, int a)
@@ -597,7 +597,8 @@ __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapSta
         for (int j = 0; j < G; ++j) c[j] = st.cache[(i0 + j) * M.N + a];
         const float bd = M.bdist[a];
         const float4 Xf = M.Xf[a];
-        FastMap F = fast_map(MS, sf, a, Xf);
+        // TR: the map is a translation (no map, plunge)
+        FastMap F = TR ? fast_map_translation(sf, Xf) : fast_map(MS, sf, a, Xf);
         if (K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
 #pragma unroll
         for (int j = 0; j < G; ++j) code[j] = stream_fast_pop(M, K, st, a, i0 + j, F, Xf, bd, c[j]);
@@ -612,13 +613,14 @@ __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapSta
 #endif
 constexpr int FAST_BS = ALELB_FAST_BS;
 
-// Grid (node blocks, 9 / G direction groups).
-template <class S, class A, int G>
+// Grid (node blocks, 9 / G direction groups).  TR: the map is a
+// translation (no map, plunge).
+template <class S, class A, int G, bool TR>
 __global__ void __launch_bounds__(FAST_BS) k_stream_fast(MeshDev M, MapStatic MS, MapScalarsF sf,
                                                      KinParams<A> K, StateDev<S> st)
 {
     wait_prior_grid();
-    stream_fast_group<G>(M, MS, sf, K, st, blockIdx.x * blockDim.x + threadIdx.x);
+    stream_fast_group<G, S, A, TR>(M, MS, sf, K, st, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // One listed population (code = 9 node + direction): exact decision, then
