@@ -517,10 +517,20 @@ __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams
     if (fast_decide(M, F, Xf, bd, a, i, c, e, xi, eta)) {
         A Nw[6];
         shape6<A>((A)xi, (A)eta, Nw);
+        // the element's six nodes in three 8-byte loads (conn is 8-byte
+        // aligned at every element: 24 bytes per element)
+        int nb[6];
+        const int2 *cp = reinterpret_cast<const int2 *>(M.conn + 6 * e);
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+            const int2 v = cp[h];
+            nb[2 * h] = v.x;
+            nb[2 * h + 1] = v.y;
+        }
         A fi = 0, gi = 0;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const int b = M.conn[6 * e + k];
+            const int b = nb[k];
             A fb, gb;
             fg_get(st.post, i, b, N, fb, gb);
             fi += Nw[k] * fb;
