@@ -183,12 +183,16 @@ alelb_status alelb_time(alelb_solver *s, double *t, int64_t *step);
 /* Post-collision populations (full values, FP64), [9][n_nodes] each, host,
    in the caller's node order.  Each array is one device-to-host copy (the
    renumbering runs on the device); page-locked arrays are written by DMA.
+   The f copy goes through a second stream the library owns, overlapping
+   the device-side work of g; every kernel stays on the solver's stream.
    Synchronous. */
 alelb_status alelb_get_pops(alelb_solver *s, double *f, double *g);
 /* Sets the post-collision populations and the latest-step fields (used as
    the previous-step quantities of the wall condition) and the time t.
    Any field pointer may be NULL: then the field is recomputed from f, g.
-   Each array is one host-to-device copy; returns when they may be reused. */
+   Each array is one host-to-device copy (g and the fields through a
+   second stream the library owns, so that the device-side work of f
+   overlaps them); returns when they may be reused. */
 alelb_status alelb_set_pops(alelb_solver *s, const double *f, const double *g,
                             const double *rho, const double *ux, const double *uy,
                             const double *T, double t);

@@ -247,33 +247,44 @@ __global__ void k_fill_uniform(StateDev<S> st, int N, const double *consts, doub
     st.T[a] = (fld_t<S>)T;
 }
 
-// Full FP64 populations <-> stored deviations (internal order).
-// full and fields are in the caller's node order: internal node a is
-// caller node n2o[a].
+// Full FP64 populations <-> stored deviations (internal order), one
+// population set per launch so that each half's kernel overlaps the other
+// half's host copy.  plane ([9 N]) and fields are in the caller's node
+// order: internal node a is caller node n2o[a].
+// part 0: the f plane; without fields, rho and u = sum (c_i + U) f_i / rho
+// go to tmp ([3 N], internal order, FP64).  part 1: the g plane, then the
+// fields (given, or T from sum g_i and tmp).
 template <class S>
-__global__ void k_import(StateDev<S> st, int N, const double *consts, const double *full,
+__global__ void k_import(StateDev<S> st, int N, const double *consts, const double *plane,
                          const double *fields, int have_fields, double Cv, double Ux, double Uy,
-                         const int *n2o)
+                         const int *n2o, double *tmp, int part)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
     const int o = n2o[a];
-    double r = 0, jx = 0, jy = 0, e2 = 0;
+    double sum = 0, jx = 0, jy = 0;
     for (int i = 0; i < NQ; ++i) {
-        double f = full[i * N + o], g = full[(NQ + i) * N + o];
-        fg_put(st.post, i, a, N, f - consts[i], g - consts[NQ + i]);
-        r += f;
-        jx += c_cx[i] * f;
-        jy += c_cy[i] * f;
-        e2 += g;
+        const double v = plane[i * N + o];
+        pop_put1(st.post, i, a, N, part, v - consts[part * NQ + i]);
+        sum += v;
+        if (part == 0) {
+            jx += c_cx[i] * v;
+            jy += c_cy[i] * v;
+        }
     }
-    if (have_fields) {
+    if (part == 0) {
+        if (!have_fields) {
+            tmp[a] = sum;
+            tmp[N + a] = jx / sum + Ux; // lattice c_i + U
+            tmp[2 * N + a] = jy / sum + Uy;
+        }
+    } else if (have_fields) {
         st.rho[a] = (fld_t<S>)fields[o];
         st.ux[a] = (fld_t<S>)fields[N + o];
         st.uy[a] = (fld_t<S>)fields[2 * N + o];
         st.T[a] = (fld_t<S>)fields[3 * N + o];
     } else {
-        double ux = jx / r + Ux, uy = jy / r + Uy, E = e2 / (2 * r); // lattice c_i + U
+        const double r = tmp[a], ux = tmp[N + a], uy = tmp[2 * N + a], E = sum / (2 * r);
         st.rho[a] = (fld_t<S>)r;
         st.ux[a] = (fld_t<S>)ux;
         st.uy[a] = (fld_t<S>)uy;
@@ -281,20 +292,22 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
     }
 }
 
+// part 0: the f plane into plane; part 1: the g plane (plane may be
+// null) and the fields (may be null).
 template <class S>
-__global__ void k_export(StateDev<S> st, int N, const double *consts, double *full, double *fields,
-                         const int *n2o)
+__global__ void k_export(StateDev<S> st, int N, const double *consts, double *plane, double *fields,
+                         const int *n2o, int part)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
     const int o = n2o[a];
-    if (full)
+    if (plane)
         for (int i = 0; i < NQ; ++i) {
             double f, g;
             fg_get(st.post, i, a, N, f, g);
-            full[i * N + o] = f + consts[i];
-            full[(NQ + i) * N + o] = g + consts[NQ + i];
+            plane[i * N + o] = (part == 0 ? f : g) + consts[part * NQ + i];
         }
+    if (part == 0) return;
     if (fields) {
         fields[o] = (double)st.rho[a];
         fields[N + o] = (double)st.ux[a];
@@ -510,6 +523,10 @@ extern "C" alelb_status alelb_lb_init(alelb_mesh *m, const alelb_params *p, alel
         st = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
         s->own_stream = true;
     }
+    // host exchange: a second stream for copies, ordered by two events
+    if (st == cudaSuccess) st = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && st == cudaSuccess; ++k)
+        st = cudaEventCreateWithFlags(&s->ev_copy[k], cudaEventDisableTiming);
     const int N = m->T.N;
     {
         int dev = 0, nsm = 0;
@@ -559,6 +576,12 @@ extern "C" void alelb_solver_destroy(alelb_solver *s)
     flush_prof(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     s->buf.release();
+    if (s->copy_stream) {
+        cudaStreamSynchronize(s->copy_stream);
+        cudaStreamDestroy(s->copy_stream);
+    }
+    for (cudaEvent_t e : s->ev_copy)
+        if (e) cudaEventDestroy(e);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s; // never touches the mesh: it may already be gone
 
@@ -607,21 +630,36 @@ alelb_status export_to_host(alelb_solver *s, double *f, double *g, double *const
 {
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
-    const bool pops = f || g;
-    double *dfull = pops ? s->d_scratch : nullptr;
     double *dfields = s->d_scratch + (size_t)18 * N;
-    with_state(s, [&](auto &sx, auto &) {
-        k_export<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, dfull, dfields, m->d_n2o);
-    });
-    cudaError_t st = cudaGetLastError();
     const size_t plane = (size_t)9 * N * sizeof(double);
-    if (st == cudaSuccess && f) st = cudaMemcpyAsync(f, s->d_scratch, plane, cudaMemcpyDeviceToHost, s->stream);
+    const dim3 grid((N + 255) / 256), block(256);
+    cudaError_t st = cudaSuccess;
+    // the f plane first; its copy on the copy stream overlaps the g half's
+    // kernel on the solver's stream (every kernel stays on that stream)
+    if (f) {
+        with_state(s, [&](auto &sx, auto &) {
+            k_export<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch, nullptr, m->d_n2o, 0);
+        });
+        st = cudaGetLastError();
+        if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[0], s->stream);
+        if (st == cudaSuccess) st = cudaStreamWaitEvent(s->copy_stream, s->ev_copy[0], 0);
+        if (st == cudaSuccess) st = cudaMemcpyAsync(f, s->d_scratch, plane, cudaMemcpyDeviceToHost, s->copy_stream);
+        if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
+    }
+    if (st == cudaSuccess && (g || fld)) {
+        with_state(s, [&](auto &sx, auto &) {
+            k_export<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, g ? s->d_scratch + (size_t)9 * N : nullptr,
+                                                    fld ? dfields : nullptr, m->d_n2o, 1);
+        });
+        st = cudaGetLastError();
+    }
     if (st == cudaSuccess && g)
         st = cudaMemcpyAsync(g, s->d_scratch + (size_t)9 * N, plane, cudaMemcpyDeviceToHost, s->stream);
     for (int c = 0; c < 4 && st == cudaSuccess; ++c)
         if (fld && fld[c])
             st = cudaMemcpyAsync(fld[c], dfields + (size_t)c * N, (size_t)N * sizeof(double),
                                  cudaMemcpyDeviceToHost, s->stream);
+    if (st == cudaSuccess && f) st = cudaStreamWaitEvent(s->stream, s->ev_copy[1], 0); // the f copy too
     if (st != cudaSuccess) return cuda_fail(s, st);
     return alelb_sync(s);
 }
@@ -648,20 +686,33 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
     const int N = s->mesh->T.N;
     const bool have = rho && ux && uy && T;
     const size_t plane = (size_t)9 * N * sizeof(double);
+    double *dfields = s->d_scratch + (size_t)18 * N; // the fields, or the f half's rho and u
+    // f on the solver's stream; g (and the fields) on the copy stream once f
+    // is in, so that the f half's kernel overlaps the g copy
     cudaError_t st = cudaMemcpyAsync(s->d_scratch, f, plane, cudaMemcpyHostToDevice, s->stream);
+    if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[0], s->stream);
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(s->copy_stream, s->ev_copy[0], 0);
     if (st == cudaSuccess)
-        st = cudaMemcpyAsync(s->d_scratch + (size_t)9 * N, g, plane, cudaMemcpyHostToDevice, s->stream);
+        st = cudaMemcpyAsync(s->d_scratch + (size_t)9 * N, g, plane, cudaMemcpyHostToDevice, s->copy_stream);
     const double *fl[4] = {rho, ux, uy, T};
     for (int c = 0; c < 4 && have && st == cudaSuccess; ++c)
-        st = cudaMemcpyAsync(s->d_scratch + (size_t)(18 + c) * N, fl[c], (size_t)N * sizeof(double),
-                             cudaMemcpyHostToDevice, s->stream);
+        st = cudaMemcpyAsync(dfields + (size_t)c * N, fl[c], (size_t)N * sizeof(double), cudaMemcpyHostToDevice,
+                             s->copy_stream);
+    if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
     if (st != cudaSuccess) return cuda_fail(s, st);
+    const dim3 grid((N + 255) / 256), block(256);
     with_state(s, [&](auto &sx, auto &) {
-        k_import<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch,
-                                                          s->d_scratch + (size_t)18 * N, have, s->Cv,
-                                                          s->U[0], s->U[1], s->mesh->d_n2o);
+        k_import<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch, dfields, have, s->Cv, s->U[0],
+                                                s->U[1], s->mesh->d_n2o, dfields, 0);
     });
     st = cudaGetLastError();
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(s->stream, s->ev_copy[1], 0);
+    if (st == cudaSuccess)
+        with_state(s, [&](auto &sx, auto &) {
+            k_import<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch + (size_t)9 * N, dfields,
+                                                    have, s->Cv, s->U[0], s->U[1], s->mesh->d_n2o, dfields, 1);
+        });
+    if (st == cudaSuccess) st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the caller's arrays are free again
     if (st != cudaSuccess) return cuda_fail(s, st);
     s->t = t;

@@ -96,6 +96,8 @@ struct alelb_solver {
     int prec = 0, flags = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;        // host exchange copies (set_pops, get_pops)
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr}; // orders them against the solver's stream
     double gamma = 1.4, Pr = 0.71, mu = 0, rho_inf = 1, T_inf = 0.3, uinf[2] = {0, 0}, chord = 1;
     double Cv = 2.5, Cp = 3.5;
     double U[2] = {0, 0}; // lattice shift: velocities c_i + U

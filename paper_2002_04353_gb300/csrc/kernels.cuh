@@ -89,6 +89,24 @@ template <class A> __device__ __forceinline__ void fg_put(__half *p, int i, int 
     reinterpret_cast<__half2 *>(p)[i * N + x] =
         __floats2half2_rn((float)f * FP16_DEV_SCALE, (float)g * FP16_DEV_SCALE);
 }
+// One half of the pair: part 0 writes f_i, part 1 writes g_i (rounded as
+// fg_put rounds it).
+__device__ __forceinline__ void pop_put1(double *p, int i, int x, int N, int part, double v)
+{
+    p[(part * NQ + i) * N + x] = v;
+}
+__device__ __forceinline__ void pop_put1(float *p, int i, int x, int N, int part, double v)
+{
+    p[2 * (i * N + x) + part] = (float)v;
+}
+__device__ __forceinline__ void pop_put1(__nv_bfloat16 *p, int i, int x, int N, int part, double v)
+{
+    p[2 * (i * N + x) + part] = __float2bfloat16_rn((float)v);
+}
+__device__ __forceinline__ void pop_put1(__half *p, int i, int x, int N, int part, double v)
+{
+    p[2 * (i * N + x) + part] = __float2half_rn((float)v * FP16_DEV_SCALE);
+}
 template <class P> __device__ __forceinline__ void fg_copy(P *dst, const P *src, int i, int x, int N)
 {
     if (sizeof(P) == 8) { // FP64 planes
