@@ -94,7 +94,7 @@ enum {
                                       use g and V_G at t_{n+1/2} (Eq. 7 at the midpoint time;
                                       the wall condition and the derivatives stay at t_{n+1}).
                                       Single-case solvers only: alelb_batch_create refuses it */
-    ALELB_FLAG_EXACT_CHAR = 64     /* the departure point of population i is the reference position
+    ALELB_FLAG_EXACT_CHAR = 64,    /* the departure point of population i is the reference position
                                       at t_n of the physical point G(X, t_{n+1}) - c_i, on the
                                       exact characteristic of Sec. III, in place of X - c^_i;
                                       rigid maps only (none, plunge, pitch, pitch with plunge):
@@ -104,6 +104,15 @@ enum {
                                       certificates bound X - c^_i only).  Single-case solvers
                                       only: alelb_batch_create refuses it.  Takes precedence
                                       over ALELB_FLAG_MIDPOINT */
+    /* 128 is reserved (internal). */
+    ALELB_FLAG_OFFWALL_VG = 256    /* missing populations of off-wall nodes (nodes next to a moving
+                                      wall whose departure segment crosses it) take the mesh
+                                      velocity V_G at the node as their target velocity, in place
+                                      of the node's previous-step velocity; density and
+                                      temperature stay the node's.  The paper states targets for
+                                      wall nodes only; with this reading the fluid layer that a
+                                      receding wall leaves behind follows the wall, and the
+                                      plunging airfoils stay stable over whole runs */
 };
 
 /* Mesh description (computational domain, Sec. III).  Straight-sided

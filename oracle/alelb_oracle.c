@@ -46,6 +46,9 @@
  *       variant; the paper has none): wall nodes take u = V_G plus the
  *       tangential part of u_B - V_G at the probe B, tangent taken in the
  *       physical frame, and no non-equilibrium part (no wall shear)
+ *   R8c flag OFFWALL_VG: off-wall nodes' missing populations take the mesh
+ *       velocity V_G at the node as the target velocity (the paper states
+ *       targets for wall nodes only)
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
  *       on each straight P2 wall edge of the mapped geometry
  *   R14 shifted lattice (velocities c_i + U, Sec. V.D; the model itself is
@@ -72,7 +75,7 @@ static const int CYI[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 enum { ST_OK = 0, ST_ARG = -1, ST_OOM = -2, ST_MESH = -4, ST_MAP = -5, ST_LOCATE = -6,
        ST_NONFINITE = -7 };
 enum { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQUILIBRIUM = 8,
-       FLAG_SLIP_WALL = 16, FLAG_MIDPOINT = 32, FLAG_EXACT_CHAR = 64 };
+       FLAG_SLIP_WALL = 16, FLAG_MIDPOINT = 32, FLAG_EXACT_CHAR = 64, FLAG_OFFWALL_VG = 256 };
 enum { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
        MK_BLENDED = 5 };
 enum { EK_INTERIOR = 0, EK_WALL = 1, EK_FAR = 2 };
@@ -1535,6 +1538,10 @@ static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd, con
                     tgt[1] = o->ux[a];
                     tgt[2] = o->uy[a];
                     tgt[3] = o->T[a];
+                    if (o->K.flags & FLAG_OFFWALL_VG) { /* reading R8c: the mesh velocity */
+                        tgt[1] = Vx;
+                        tgt[2] = Vy;
+                    }
                 }
                 double KX, KY;
                 fe_grad_X_linear(o, a, o->ux, &KX, &KY);

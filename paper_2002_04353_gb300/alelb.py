@@ -31,6 +31,7 @@ FLAG_BC_EQUILIBRIUM = 8
 FLAG_SLIP_WALL = 16
 FLAG_MIDPOINT = 32
 FLAG_EXACT_CHAR = 64
+FLAG_OFFWALL_VG = 256
 NQ = 9
 
 # every symbol include/alelb.h declares

@@ -353,9 +353,12 @@ __device__ __forceinline__ void stream_plain_node(const MeshDev &M, const MapSta
                     slip_target<A>((A)a11, (A)a12, (A)a21, (A)a22, (A)nw.x, (A)nw.y, ub, vb, (A)Vx, (A)Vy, uxt, uyt);
                 }
             } else {
+                // off-wall node: its previous-step fields; the velocity is the
+                // mesh velocity instead under FLAG_OFFWALL_VG
+                const bool vg = (K.flags & FLAG_OFFWALL_VG) != 0;
                 rt = (A)st.rho[a];
-                uxt = (A)st.ux[a];
-                uyt = (A)st.uy[a];
+                uxt = vg ? (A)Vx : (A)st.ux[a];
+                uyt = vg ? (A)Vy : (A)st.uy[a];
                 Tt = (A)st.T[a];
             }
             A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
@@ -486,9 +489,10 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
             slip_target<A>((A)a11, (A)a12, (A)a21, (A)a22, (A)nw.x, (A)nw.y, ub, vb, (A)Vx, (A)Vy, uxt, uyt);
         }
     } else {
+        const bool vg = (K.flags & FLAG_OFFWALL_VG) != 0; // mesh velocity as the target
         rt = (A)st.rho[a];
-        uxt = (A)st.ux[a];
-        uyt = (A)st.uy[a];
+        uxt = vg ? (A)Vx : (A)st.ux[a];
+        uyt = vg ? (A)Vy : (A)st.uy[a];
         Tt = (A)st.T[a];
     }
     A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};

@@ -32,7 +32,7 @@ template <class A> struct KinParams {
 
 enum : int { FLAG_PHI_OFF = 1, FLAG_COLLIDE_OFF = 2, FLAG_LITERAL_VG = 4, FLAG_BC_EQ = 8, FLAG_SLIP = 16,
              FLAG_MIDPOINT = 32, FLAG_EXACT_CHAR = 64,
-             FLAG_SHIFT = 128 /* internal: U != 0 */ };
+             FLAG_SHIFT = 128 /* internal: U != 0 */, FLAG_OFFWALL_VG = 256 };
 
 // One-dimensional factors Phi_c(u, T) of Eq. feq.
 template <class A> __device__ __forceinline__ void phi3(A u, A T, A &m, A &z, A &p)

@@ -495,6 +495,25 @@ def test_shifted_lattice_with_the_exact_characteristic():
     _compare64(o, s, "plunging airfoil, shifted, exact characteristic")
 
 
+@pytest.mark.parametrize("motion_name", ["omesh_plunge", "omesh_pitch"])
+def test_offwall_mesh_velocity_target(motion_name):
+    """Flag OFFWALL_VG (reading R8c): FP64 and FP32 against the oracle on
+    moving airfoils, where off-wall nodes have missing populations."""
+    mesh, motion = LOC_CASES[motion_name]()
+    flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
+    o, m, s = _pair(mesh, motion, flow, flags=O.FLAG_OFFWALL_VG)
+    o.step(4)
+    s.lb_step(4)
+    _compare64(o, s, f"{motion_name} off-wall V_G FP64")
+    o2, m2, s2 = _pair(mesh, motion, flow, prec=alelb.PREC_FP32_DEV, flags=O.FLAG_OFFWALL_VG)
+    o2.step(4)
+    s2.lb_step(4)
+    _compare_mixed(o2, s2, f"{motion_name} off-wall V_G FP32")
+    o3 = O.Oracle(mesh, motion, flow)
+    o3.step(4)
+    assert _rel(o3.state()["f"], o.state()["f"]) > 1e-14  # the flag acts on these meshes
+
+
 def test_shifted_lattice_refusals():
     mesh, motion = LOC_CASES["omesh_plunge"]()
     m = alelb.Mesh(mesh, motion)

@@ -636,6 +636,20 @@ def test_fluid_at_rest_with_walls_stays_at_rest():
     assert np.abs(F[:4]).max() < 1e-12 * 0.3 * 20.0
 
 
+def test_offwall_mesh_velocity_target_keeps_rest_state():
+    """Flag OFFWALL_VG (reading R8c, where the paper is silent): off-wall
+    missing populations take the mesh velocity as the target.  Its only
+    closed-form consequence: a fluid at rest around a body at rest stays at
+    rest exactly (V_G = 0 is then the fluid's velocity)."""
+    mesh = I.naca_omesh(32, 8, chord=20.0, R=200.0, first=1.0)
+    fl = I.Flow(mu=0.02, T_inf=0.3, u_inf=(0.0, 0.0), chord=20.0)
+    o = O.Oracle(mesh, I.Motion.make(0), fl, flags=O.FLAG_OFFWALL_VG)
+    o.step(10)
+    st = o.state()
+    assert np.abs(st["rho"] - 1).max() < 1e-13 and np.abs(st["T"] - 0.3).max() < 1e-13
+    assert np.abs(st["ux"]).max() < 1e-13 and np.abs(st["uy"]).max() < 1e-13
+
+
 def test_missing_population_classification_matches_brute_force():
     """Reading R6: a population is missing iff some point of the segment from
     the node to its departure point lies outside the closed mesh; checked
