@@ -150,7 +150,7 @@ typedef struct {
                           psi restores the diagonal second moments about U, Q' is taken in
                           u - U, and rho u = sum (c_i + U) f_i; the populations that
                           alelb_set_pops and alelb_get_pops exchange are those of c_i + U.
-                          alelb_batch_create refuses shifted solvers */
+                          A batch may mix shifted and plain solvers */
 } alelb_params;
 
 typedef struct alelb_mesh alelb_mesh;

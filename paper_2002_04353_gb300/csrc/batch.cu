@@ -430,7 +430,7 @@ cudaError_t stage_scalars(alelb_batch *b, int done, int K)
         for (int c = 0; c < b->B; ++c) {
             const alelb_solver *s = b->cs[c];
             const HostTables &T = s->mesh->T;
-            const MapScalars sc = map_scalars(T.mkind, T.mp, s->t + (double)(done + k + 1));
+            const MapScalars sc = solver_map(s, map_scalars(T.mkind, T.mp, s->t + (double)(done + k + 1)));
             b->h_sc[sl][(size_t)k * b->B + c] = sc;
             b->h_sf[sl][(size_t)k * b->B + c] = to_f32(sc, T);
         }
@@ -503,7 +503,6 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         // and the arrival-time transformed velocities
         if (cases[c]->prec != ALELB_PREC_FP64 && cases[c]->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
         if (cases[c]->flags & (ALELB_FLAG_MIDPOINT | ALELB_FLAG_EXACT_CHAR)) return ALELB_ERR_ARG;
-        if (cases[c]->U[0] != 0.0 || cases[c]->U[1] != 0.0) return ALELB_ERR_ARG; // shifted lattice
         for (int d = 0; d < c; ++d)
             if (cases[d] == cases[c]) return ALELB_ERR_ARG;
     }

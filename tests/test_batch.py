@@ -25,8 +25,9 @@ def _rel(a, b):
 
 
 def _cases():
-    """Three unlike cases: a deforming periodic box, a plunging and a
-    pitching-plunging O-mesh of different sizes and Mach numbers."""
+    """Four unlike cases: a deforming periodic box, a plunging and a
+    pitching-plunging O-mesh of different sizes and Mach numbers, and a
+    plunging O-mesh at Mach 0.6 on the lattice shifted by U = (0.3, 0)."""
     box = I.uniform_flow_case(n=12, L=24.0, period_steps=40.0)
     om1 = I.naca_omesh(48, 16, chord=200.0, R=4000.0, first=1.0)
     om2 = I.naca_omesh(64, 20, chord=200.0, thickness=0.15, R=4000.0, first=1.0)
@@ -35,6 +36,8 @@ def _cases():
         (om1, I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.002), I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)),
         (om2, I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.05, 0.003, 50.0, 0.0, 20.0, 0.003),
          I.flow_params(0.15, T_inf=0.3, Re=800.0, chord=200.0, angle_deg=2.0)),
+        (om1, I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.002),
+         I.flow_params(0.6, T_inf=0.3, Re=500.0, chord=200.0, shift=(float(np.float32(0.3)), 0.0))),
     ]
 
 

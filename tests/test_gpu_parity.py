@@ -522,10 +522,6 @@ def test_shifted_lattice_refusals():
         with pytest.raises(alelb.AlelbError) as ex:
             alelb.Solver(m, fl, alelb.PREC_FP32_DEV)
         assert ex.value.status == -1
-    s = alelb.Solver(m, I.flow_params(0.5, T_inf=0.3, Re=500.0, chord=200.0, shift=U03), alelb.PREC_FP32_DEV)
-    with pytest.raises(alelb.AlelbError) as ex:
-        alelb.Batch([s])
-    assert ex.value.status == -1
 
 
 @pytest.mark.parametrize("prec", [alelb.PREC_FP32_DEV, alelb.PREC_BF16_DEV, alelb.PREC_FP16_DEV])
