@@ -39,3 +39,29 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             alelb.load(str(tmp_path / "missing.so"))
     finally:
         alelb._lib = old
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of alelb_params and alelb_mesh_desc have the
+    header's size and field offsets (the host compiler lays out the C
+    structs; a field added on one side only would shift the others)."""
+    import subprocess
+    fields = {"alelb_params": (alelb.Params, ["gamma", "Pr", "mu", "rho_inf", "T_inf", "u_inf", "chord",
+                                               "precision", "flags", "stream", "shift"]),
+              "alelb_mesh_desc": (alelb.MeshDesc, [f[0] for f in alelb.MeshDesc._fields_])}
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "alelb.h"', "int main(void) {"]
+    for struct, (_, names) in fields.items():
+        src.append(f'printf("{struct} size %zu\\n", sizeof({struct}));')
+        for n in names:
+            src.append(f'printf("{struct} {n} %zu\\n", offsetof({struct}, {n}));')
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line}
+    for struct, (cls, names) in fields.items():
+        assert got[(struct, "size")] == ctypes.sizeof(cls), struct
+        for n in names:
+            assert got[(struct, n)] == getattr(cls, n).offset, f"{struct}.{n}"
