@@ -486,13 +486,20 @@ def test_shifted_lattice_fp64_fp32_and_16bit(which):
     assert _rel(o4.state()["ux"], o.state()["ux"]) > 1e-9
 
 
-def test_shifted_lattice_with_the_exact_characteristic():
+@pytest.mark.parametrize("flags", [O.FLAG_EXACT_CHAR, O.FLAG_MIDPOINT, O.FLAG_OFFWALL_VG])
+def test_shifted_lattice_with_the_variants(flags):
+    """The shift combined with the departure variants and the off-wall
+    target reading, FP64 and FP32 against the oracle."""
     mesh, motion = LOC_CASES["omesh_plunge"]()
     fl = I.flow_params(0.5, T_inf=0.3, Re=500.0, chord=200.0, shift=U03)
-    o, m, s = _pair(mesh, motion, fl, flags=O.FLAG_EXACT_CHAR)
+    o, m, s = _pair(mesh, motion, fl, flags=flags)
     o.step(3)
     s.lb_step(3)
-    _compare64(o, s, "plunging airfoil, shifted, exact characteristic")
+    _compare64(o, s, f"plunging airfoil, shifted, flags {flags}")
+    o2, m2, s2 = _pair(mesh, motion, fl, prec=alelb.PREC_FP32_DEV, flags=flags)
+    o2.step(3)
+    s2.lb_step(3)
+    _compare_mixed(o2, s2, f"plunging airfoil, shifted, flags {flags}, FP32")
 
 
 @pytest.mark.parametrize("motion_name", ["omesh_plunge", "omesh_pitch"])
