@@ -48,7 +48,8 @@
  *       physical frame, and no non-equilibrium part (no wall shear)
  *   R8c flag OFFWALL_VG: off-wall nodes' missing populations take the mesh
  *       velocity V_G at the node as the target velocity (the paper states
- *       targets for wall nodes only)
+ *       targets for wall nodes only); parity unpinned beyond the invariant
+ *       that a fluid at rest around a body at rest stays at rest
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
  *       on each straight P2 wall edge of the mapped geometry
  *   R14 shifted lattice (velocities c_i + U, Sec. V.D; the model itself is
