@@ -48,8 +48,8 @@
  *       physical frame, and no non-equilibrium part (no wall shear)
  *   R8c flag OFFWALL_VG: off-wall nodes' missing populations take the mesh
  *       velocity V_G at the node as the target velocity (the paper states
- *       targets for wall nodes only); parity unpinned beyond the invariant
- *       that a fluid at rest around a body at rest stays at rest
+ *       targets for wall nodes only); pinned by the one-step closed form
+ *       next to a receding wall (the reading itself has no passage)
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
  *       on each straight P2 wall edge of the mapped geometry
  *   R14 shifted lattice (velocities c_i + U, Sec. V.D; the model itself is
@@ -59,9 +59,11 @@
  *       diagonal second central moments (the printed psi at U = 0), Q' in
  *       u - U, phi_i = A_ia X_a on the relative velocities c_i; the
  *       departure uses c_i + U and the moments sum (c_i + U) f
- * Parity status of each function is given in its comment; the forces have
- * no value the paper prints for these setups ("parity unpinned" beyond the
- * closed-body invariant).
+ * Parity status of each function is given in its comment.  The forces, the
+ * probe point B, the wall condition's gradient element and the R8c target
+ * are pinned by closed forms (quadratic fields on a closed body through the
+ * divergence theorem; one step without collision against the Grad
+ * reconstruction); the paper prints no force values for these setups.
  */
 #include <math.h>
 #include <stdint.h>
