@@ -241,6 +241,8 @@ alelb_status alelb_info(alelb_solver *s, double out[8]);
    device memory once running -- an application whose device memory is
    pre-reserved by its own allocator, or a loop that must not call
    cudaMalloc/cudaFree, which can wait for the whole device).
+   The current device must be the one that was current at
+   alelb_mesh_create (else ALELB_ERR_ARG).
    The caller owns and passes the state, all device pointers on the current
    device: post [9][n_nodes] f then [9][n_nodes] g (full FP64 post-collision
    populations at t, overwritten with those at t + 1) and the latest-step
@@ -251,12 +253,42 @@ alelb_status alelb_info(alelb_solver *s, double out[8]);
    (NULL: the default stream).  The step's
    scratch lives in a static device array of 23 * 131072 + 64 doubles
    (about 24 MB) that every GPU loading the library holds until exit.  The
-   first call on a device looks up that array's device address (make that
-   first call before any stream capture).  Calls share the array, so calls
+   first call on a device, and the first call after each alelb_mesh_create
+   on that device (a device reset frees every mesh, so this also follows a
+   reset), looks up that array's device address: make that call before any
+   stream capture.  Calls share the array, so calls
    that overlap on the GPU race.  Synchronous; returns ALELB_ERR_ARG for a
    larger mesh or other precision (message in alelb_mesh_last_error). */
 alelb_status alelb_lb_step_noalloc(alelb_mesh *mesh, const alelb_params *p, double t,
                                    double *post, double *rho, double *ux, double *uy, double *T);
+
+/* Checkpoints (the paper has no counterpart: it describes no restart).
+   alelb_save writes the solver's state to the file `path`: the stored
+   post-collision populations, the latest-step fields (the wall condition's
+   previous-step values), the deviation forms' element cache, the time, the
+   step count and the walk counters, with the fluid parameters, the mesh's
+   fingerprint and FNV-1a checksums of header and data.  It first waits for
+   the solver's stream (returning any sticky device error instead of
+   saving), writes `path`.tmp and renames it to `path`.  alelb_load reads
+   such a file into a solver created with alelb_lb_init on the same mesh
+   (same node coordinates, connectivity, edge kinds and motion), precision,
+   lattice shift, gamma and free stream; the viscosity, Prandtl number,
+   chord and flags may differ and take effect from the next step.  After a
+   load, stepping continues exactly as the saved solver would have: the
+   results are bit-identical to an uninterrupted run.  Both are
+   synchronous.  Errors: ALELB_ERR_ARG for a path that cannot be opened or
+   written and for a file that is not a complete, intact checkpoint
+   (truncated, bad magic or version, checksum mismatch, trailing bytes);
+   ALELB_ERR_STATE for an intact checkpoint of a different mesh, precision,
+   shift or free stream (the solver is then unchanged); ALELB_ERR_CUDA. */
+alelb_status alelb_save(alelb_solver *s, const char *path);
+alelb_status alelb_load(alelb_solver *s, const char *path);
+/* Checks a checkpoint file on the host alone (no device is touched) with
+   the tests alelb_load applies to the file itself.  out (may be NULL):
+   {precision, n_nodes, n_elems, step count}; t (may be NULL): its time;
+   msg (may be NULL): the reason of a failure, at most msg_len bytes with
+   the terminating zero.  Errors as alelb_load's file errors. */
+alelb_status alelb_checkpoint_info(const char *path, int64_t out[4], double *t, char *msg, int32_t msg_len);
 
 /* Batched step (the paper runs one case at a time and has no counterpart;
    this serves parameter sweeps of many independent cases).  A batch groups

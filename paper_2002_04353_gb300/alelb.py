@@ -43,7 +43,8 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_batch_sync", "alelb_batch_tune", "alelb_batch_profile", "alelb_batch_kernel_times",
            "alelb_batch_last_error", "alelb_mlp_create", "alelb_mlp_destroy", "alelb_mlp_get_params",
            "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
-           "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error"]
+           "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
+           "alelb_checkpoint_info"]
 
 
 class AlelbError(RuntimeError):
@@ -123,6 +124,9 @@ def load(path: str = LIB_PATH):
     L.alelb_mlp_stats.argtypes = [p, p]
     L.alelb_mlp_last_error.argtypes = [p]
     L.alelb_mlp_last_error.restype = C.c_char_p
+    L.alelb_save.argtypes = [p, C.c_char_p]
+    L.alelb_load.argtypes = [p, C.c_char_p]
+    L.alelb_checkpoint_info.argtypes = [C.c_char_p, p, p, C.c_char_p, i32]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -209,6 +213,20 @@ def params_of(flow, precision=PREC_FP64, flags=None, stream=None):
     return p
 
 
+def checkpoint_info(path):
+    """alelb_checkpoint_info: checks a checkpoint file on the host; returns
+    dict(precision, n_nodes, n_elems, step, t) or raises AlelbError."""
+    L = load()
+    out = np.zeros(4, dtype=np.int64)
+    t = C.c_double()
+    msg = C.create_string_buffer(512)
+    st = L.alelb_checkpoint_info(os.fsencode(path), _ptr(out), C.byref(t), msg, 512)
+    if st != OK:
+        raise AlelbError(st, msg.value.decode())
+    return dict(precision=int(out[0]), n_nodes=int(out[1]), n_elems=int(out[2]), step=int(out[3]),
+                t=t.value)
+
+
 def lb_step_noalloc(mesh: "Mesh", flow, t, post_ptr, rho_ptr, ux_ptr, uy_ptr, T_ptr, stream=None):
     """One FP64 step on caller-owned device buffers (raw device addresses),
     allocating nothing; see alelb_lb_step_noalloc in include/alelb.h."""
@@ -273,6 +291,12 @@ class Solver:
         fl = [None if a is None else _f64(a) for a in (rho, ux, uy, T)]
         self._check(load().alelb_set_pops(self.h, _ptr(f), _ptr(g), *[_ptr(a) for a in fl], float(t)),
                     "set_pops")
+
+    def save(self, path):
+        self._check(load().alelb_save(self.h, os.fsencode(path)), "save")
+
+    def load(self, path):
+        self._check(load().alelb_load(self.h, os.fsencode(path)), "load")
 
     def forces(self):
         out = np.empty(6)

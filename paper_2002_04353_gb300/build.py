@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-UNITS = [os.path.join(CSRC, f) for f in ("alelb.cu", "batch.cu", "mlp.cu")]
+UNITS = [os.path.join(CSRC, f) for f in ("alelb.cu", "batch.cu", "mlp.cu", "checkpoint.cu")]
 OUT = os.path.join(HERE, "_build", "libalelb.so")
 DEPS = UNITS + [os.path.join(CSRC, f) for f in ("geom.cuh", "kinetic.cuh", "kernels.cuh", "tables.h",
                                                  "internal.h", "mlp.cuh")] + [os.path.join(ROOT, "include", "alelb.h")]

@@ -18,6 +18,10 @@
 
 using namespace alelb;
 
+namespace {
+void forget_noalloc_scratch(int dev);
+}
+
 namespace alelb {
 
 const char *const KT_NAMES[KT_N] = {"k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1",
@@ -110,8 +114,27 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
         *out = m; // returned so that alelb_mesh_last_error can be read
         return bs;
     }
+    {
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&h](const void *p, size_t n) {
+            const unsigned char *b = (const unsigned char *)p;
+            for (size_t k = 0; k < n; ++k) {
+                h ^= b[k];
+                h *= 1099511628211ull;
+            }
+        };
+        mix(T.X.data(), T.X.size() * sizeof(double2));
+        mix(T.conn.data(), T.conn.size() * sizeof(int));
+        mix(T.einfo.data(), T.einfo.size() * sizeof(uint32_t));
+        mix(&T.Lx, sizeof(double));
+        mix(&T.Ly, sizeof(double));
+        mix(&T.mkind, sizeof(int));
+        mix(T.mp, sizeof(T.mp));
+        m->fingerprint = h;
+    }
     // upload
-    cudaError_t st = cudaSuccess;
+    cudaError_t st = cudaGetDevice(&m->device);
+    if (st == cudaSuccess) forget_noalloc_scratch(m->device);
     DevBuf &B = m->buf;
     MeshDev &D = m->dev;
     D.N = T.N;
@@ -859,6 +882,13 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)23 * ALELB_NOALLOC_MAX_NODES + 64;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 double *g_noalloc_ptr[64] = {nullptr}; // device address of the array, per device
+// A new mesh on a device drops the cached address: after a device reset
+// (which frees every table, so meshes must be created again) the next call
+// asks the runtime again instead of using an address of the old context.
+void forget_noalloc_scratch(int dev)
+{
+    if (dev >= 0 && dev < 64) g_noalloc_ptr[dev] = nullptr;
+}
 }
 
 extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params *p, double t,
@@ -895,6 +925,11 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     if (st != cudaSuccess || dev < 0 || dev >= 64) {
         m->err = "lb_step_noalloc: no usable current device";
         return ALELB_ERR_CUDA;
+    }
+    if (dev != m->device) {
+        m->err = "lb_step_noalloc: the current device (" + std::to_string(dev) +
+                 ") is not the one the mesh was created on (" + std::to_string(m->device) + ")";
+        return ALELB_ERR_ARG;
     }
     // set-up, once per device: the host-side name of the array is not a
     // device address; ask the runtime for it with this device current

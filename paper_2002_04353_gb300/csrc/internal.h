@@ -87,6 +87,9 @@ struct alelb_mesh {
     int2 *d_wedges = nullptr;
     int *d_n2o = nullptr; // [N] caller's node number of each internal node
     int nw = 0;
+    int device = 0; // the CUDA device current at alelb_mesh_create, which holds the tables
+    uint64_t fingerprint = 0; // FNV-1a of the node coordinates, connectivity, edge kinds,
+                              // periods and motion (checkpoints name the mesh by it)
     DevBuf buf;
 };
 

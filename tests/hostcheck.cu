@@ -1,6 +1,6 @@
-// hostcheck.cu -- the device element walk compiled for the host, for CPU
-// tests of the walk against the oracle (test tooling; not on the product
-// path).  Builds the same tables as alelb_mesh_create and runs the same
+// hostcheck.cu -- the library's device element walk compiled for the host,
+// for CPU tests of the walk against the oracle (test tooling; not on the
+// product path).  Builds the same tables as alelb_mesh_create and runs the same
 // per-node location routine that k_locate runs.
 #include <cstring>
 #include <string>

@@ -1,26 +1,26 @@
-"""CPU run of the kernels' element walk (csrc/hostcheck.cu): the same
-location routine k_locate runs, compiled for the host.  Test tooling."""
+"""CPU run of the kernels' element walk (hostcheck.cu beside this file): the
+same location routine k_locate runs, compiled for the host.  Test tooling."""
 import ctypes as C
 import os
 import subprocess
 
 import numpy as np
 
-from . import alelb, build
+from paper_2002_04353_gb300 import alelb, build
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "csrc", "hostcheck.cu")
+SRC = os.path.join(HERE, "hostcheck.cu")
 OUT = os.path.join(HERE, "_build", "libalelb_hostcheck.so")
 _lib = None
 
 
 def build_lib(force=False):
-    deps = build.DEPS + [SRC, os.path.join(HERE, "csrc", "tables.h")]
+    deps = build.DEPS + [SRC]
     if force or not os.path.exists(OUT) or any(os.path.getmtime(d) > os.path.getmtime(OUT) for d in deps):
         os.makedirs(os.path.dirname(OUT), exist_ok=True)
         tmp = OUT + f".{os.getpid()}.tmp"
         subprocess.run(["nvcc", "-O2", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared",
-                        "-I", os.path.join(build.ROOT, "include"), "-o", tmp, SRC], check=True)
+                        "-I", os.path.join(build.ROOT, "include"), "-I", build.CSRC, "-o", tmp, SRC], check=True)
         os.replace(tmp, OUT)
     return OUT
 
@@ -57,7 +57,7 @@ def _desc(mesh, motion):
 
 def inside_f32(mesh, elem, px, py):
     """The FP32 strict-containment filter for points (px, py) in elements elem."""
-    from . import inputs as I
+    from paper_2002_04353_gb300 import inputs as I
     d, keep = _desc(mesh, I.Motion.make(0))
     elem = np.ascontiguousarray(elem, dtype=np.int32)
     px = np.ascontiguousarray(px, dtype=np.float64)

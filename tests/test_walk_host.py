@@ -1,4 +1,4 @@
-"""The kernels' element walk, compiled for the host (csrc/hostcheck.cu runs
+"""The kernels' element walk, compiled for the host (hostcheck.cu runs
 the same per-node routine as the location kernel), against the oracle's
 exhaustive point search: element choices must agree bit for bit.  Runs on
 the CPU; the GPU parity tests repeat the comparison with the device build."""
@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_2002_04353_gb300 import hostcheck as H
+import hostcheck as H
 from paper_2002_04353_gb300 import inputs as I
 
 CASES = {
