@@ -1,23 +1,29 @@
 """Throughput of the ALE compressible lattice Boltzmann step on one GB300.
 
-Workload: NACA 0012 plunging, h = 0.1c sin(omega t), k = 1, Mach 0.2,
-Re 1e4, O-mesh of straight-sided P2 triangles (320 x 118 vertex rings,
-150,400 nodes), radius 20c, first cell layer 1e-3 c (c = 1000 lattice
-units), free-stream start.  One step = propagation (departure points,
-element walk, P2 interpolation, wall/far-field missing populations),
-moments, two FE-derivative passes and the collision, for every node.
+Headline workload (`value`): the batched airfoil sweep -- 32 NACA 00xx cases
+(thickness 8-18%, 20k-300k P2 nodes each, log-uniform; 4,056,108 nodes in
+all), Mach 0.1-0.8, rigid pitch 0-5 deg plus plunge 0-0.2c, k 0.05-1,
+Re 1e4, chord 1000 lattice units, free-stream start -- advanced together by
+the batched step (one launch per phase over all cases, replayed from CUDA
+graphs), FP32 populations stored as deviations, FP64 map, departure points
+and element decisions.  One step = propagation (departure points, element
+location, P2 interpolation, wall/far-field missing populations), moments,
+two FE-derivative passes and the collision, for every node of every case.
+Cases at Mach >= 0.5 run on the lattice shifted by U = (0.3, 0) (Sec. V.D).
 
-Metric: million node-updates per second.  `value` is the FP32-deviation
-form (FP32 populations and arithmetic, FP64 map, departure points and
-element location); the plain FP64 form is reported beside it.  The working
-set is smaller than L2, so L2 is flushed (a 512 MiB write) before every
-timed step and only the step itself is timed, with CUDA events on the
-solver's stream.
+Metric: million node-updates per second.  The FP32 populations of the sweep
+(585 MB, double-buffered) are larger than L2, so steps are timed back to
+back with CUDA events on the batch's stream.  Beside it: the plain FP64
+single-case form (the comparison the metric names) and the FP32 single
+case on the 150,400-node plunge (L2 flushed before each of its steps), the
+learned proposal on a 2M-node pitching mesh, storage-precision studies,
+force histories, and the FP64 oracle on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank runs an independent replica (the sweep
-workloads shard cases across GPUs with no exchange), so scaling is weak.
+Under torchrun (N > 1) the sweep's cases are shared out over the ranks by
+node count, each rank steps its own with no exchange (weak scaling in
+cases).
 """
 import argparse
 import dataclasses
@@ -106,6 +112,7 @@ def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4
 
 
 STEP_KERNELS = ("k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide")
+SWEEP_NAME = "batched_sweep_32_naca00xx_4.06M"
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -113,6 +120,11 @@ STEP_KERNELS = ("k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_co
 # capture of the current kernels; writes stay in L2 during these launches.
 NCU_TRAFFIC_150K = {"k_stream_fast": 23.93e6, "k_stream_slow": 1.48e6, "k_moments": 10.84e6,
                     "k_deriv1": 7.21e6, "k_collide": 17.45e6}
+
+
+# DRAM bytes per launch of the batched phase kernels on the 32-case sweep,
+# from one ncu capture of the current kernels (filled in from profiles/).
+NCU_TRAFFIC_SWEEP = {}
 
 
 def measured_peaks():
@@ -182,15 +194,56 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(case, steps):
-    """The FP64 oracle as it stands, single-threaded on a host core, on the
-    same mesh: node-updates/s over `steps` steps from the free-stream start."""
+def cpu_model():
+    """The host CPU's model name and logical core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        import platform
+        name = platform.processor() or platform.machine()
+    return name, os.cpu_count()
+
+
+def sweep_lattice(flow):
+    """Cases at Mach >= 0.5 run on the lattice shifted by U = (0.3, 0)."""
+    Ma = math.hypot(*flow.u_inf) / math.sqrt(flow.gamma * flow.T_inf)
+    return dataclasses.replace(flow, shift=(SHIFT03, 0.0)) if Ma >= 0.5 else flow
+
+
+def representative_cases(sweep):
+    """The smallest, median and largest cases of the sweep by node count."""
+    order = sorted(range(len(sweep)), key=lambda k: sweep[k].mesh.n_nodes)
+    return [order[0], order[len(order) // 2], order[-1]]
+
+
+def cpu_baseline(sweep, steps, threads):
+    """The FP64 oracle as it stands on the sweep's representative cases
+    (smallest, median, largest), `steps` steps each after one untimed step,
+    its node loops on `threads` host threads: node-updates/s."""
     import oracle as O
-    o = O.Oracle(case.mesh, case.motion, case.flow)
-    t0 = time.perf_counter()
-    o.step(steps)
-    dt = time.perf_counter() - t0
-    return case.mesh.n_nodes * steps / dt / 1e6, dt
+    n0 = O.threads()
+    used = O.threads(threads)
+    work, dt = 0, 0.0
+    try:
+        for k in representative_cases(sweep):
+            c = sweep[k]
+            o = O.Oracle(c.mesh, c.motion, sweep_lattice(c.flow))
+            o.step(1)
+            t0 = time.perf_counter()
+            o.step(steps)
+            dt += time.perf_counter() - t0
+            work += c.mesh.n_nodes * steps
+            del o
+    finally:
+        O.threads(n0)
+    return work / dt / 1e6, dt, used, work
 
 
 def dist_setup():
@@ -201,33 +254,54 @@ def dist_setup():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (all of them,
+    OpenMP over nodes), on the sweep.  One reference step is one oracle step
+    of the sweep's median case (80,028 nodes), a bounded sample of a sweep
+    step that keeps --steps K --warmup W within a few minutes."""
     world, rank, local = dist_setup()
     if rank != 0:
         return
-    case = workload(args.workload)
     import oracle as O
-    o = O.Oracle(case.mesh, case.motion, case.flow)
+    sweep = I.batched_sweep()
+    k = representative_cases(sweep)[1]
+    c = sweep[k]
+    threads = O.threads(os.cpu_count() or 1)
+    o = O.Oracle(c.mesh, c.motion, sweep_lattice(c.flow))
     o.step(max(0, args.warmup))
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
-    v = case.mesh.n_nodes * args.steps / dt / 1e6
+    v = c.mesh.n_nodes * args.steps / dt / 1e6
+    model, ncpu = cpu_model()
+    sample = (f"{args.steps} oracle steps of sweep case {k} ({c.mesh.n_nodes} nodes, the median case) after "
+              f"{args.warmup} warm-up steps, plain FP64 C oracle, OpenMP over nodes on {threads} threads "
+              f"({model}, {ncpu} logical cores)")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": case.name, "nodes": case.mesh.n_nodes, "elements": case.mesh.n_elems,
-                   "mach": 0.2, "re": 1e4, "chord": case.mesh.meta["chord"]},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps of the full {case.mesh.n_nodes}-node mesh after "
-                                   f"{args.warmup} warm-up steps, plain FP64 C oracle, one host core"},
+        "config": {"workload": SWEEP_NAME, "nodes": sum(x.mesh.n_nodes for x in sweep), "cases": len(sweep),
+                   "sample_case": k, "sample_nodes": c.mesh.n_nodes},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": model, "nproc": ncpu},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_batched(alelb, torch, dev, world, rank, args):
+def method_bytes(n_nodes, n_elems):
+    """The method's own bytes per step (FP32-deviation storage): every
+    population read once and written once (2 x 18 x 4 B per node), the
+    derivative passes' node fields (Q'_x, Q'_y, rho T written and read,
+    D_x, D_y written and read, rho, u, T written: 56 B per node), the node's
+    owner and home element (8 B), and per element the connectivity (24 B),
+    neighbours (12 B) and FP64 vertices (48 B); rigid maps need no per-node
+    map factors.  About 250 B per node-update on O-meshes (E = N/2)."""
+    return n_nodes * (144 + 56 + 8) + n_elems * (24 + 12 + 48)
+
+
+def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     """The 32-case airfoil sweep (NACA 00xx, 8-18% thick, 20k-300k P2 nodes
     log-uniform, Mach 0.1-0.8, pitch 0-5 deg, plunge 0-0.2c, k 0.05-1) in
     one batch: FP32-deviation solvers, one launch per phase over all cases,
@@ -236,16 +310,15 @@ def run_batched(alelb, torch, dev, world, rank, args):
     transonic case; on the plain lattice several of them leave the
     admissible range within the timed steps.  Under torchrun the cases are
     shared out by node count (shard.assign_cases) and every rank steps its
-    own (no exchange: weak in cases)."""
+    own (no exchange: weak in cases).  Returns the timed result, the
+    batched kernels' rooflines and the end-to-end figure (host-resident
+    state through the C-ABI)."""
     from paper_2002_04353_gb300 import shard
     sweep = I.batched_sweep()
     mine = shard.assign_cases([c.mesh.n_nodes for c in sweep], world)[rank]
     cases = [sweep[k] for k in mine]
     meshes = [alelb.Mesh(c.mesh, c.motion) for c in cases]
-    def lattice(flow):
-        Ma = math.hypot(*flow.u_inf) / math.sqrt(flow.gamma * flow.T_inf)
-        return dataclasses.replace(flow, shift=(SHIFT03, 0.0)) if Ma >= 0.5 else flow
-    flows = [lattice(c.flow) for c in cases]
+    flows = [sweep_lattice(c.flow) for c in cases]
     solvers = [alelb.Solver(m, fl, alelb.PREC_FP32_DEV) for m, fl in zip(meshes, flows)]
     stream = torch.cuda.Stream(device=dev)
     b = alelb.Batch(solvers, stream=stream.cuda_stream)
@@ -253,15 +326,20 @@ def run_batched(alelb, torch, dev, world, rank, args):
     b.step(max(3, args.warmup) - 1)
     b.sync()
     n_nodes = sum(c.mesh.n_nodes for c in cases)
-    K = args.batched_steps
+    n_elems = sum(c.mesh.n_elems for c in cases)
+    K = args.steps
+    walks0 = sum(s.info()["walks"] for s in solvers)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
     e0.record(stream)
     b.step(K)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
     finite = 0
     for s in solvers:
@@ -270,22 +348,56 @@ def run_batched(alelb, torch, dev, world, rank, args):
             finite += 1
         except alelb.AlelbError:
             pass
+    n_exact = (sum(s.info()["walks"] for s in solvers) - walks0) / K  # exact-path populations per step
     ms = shard.max_over_ranks(ms, torch, dev)
     n_total = int(shard.sum_over_ranks(n_nodes, torch, dev))
-    # per-kernel times of the batched phases (launched one by one)
+    # per-kernel device times of the batched phases, measured right after
+    # the timed region with events around every launch (launched one by one)
     b.profile(True)
-    b.step(3)
+    b.step(20)
     kt = b.kernel_times()
     b.profile(False)
+    kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt.items() if v[1]}
+    rl = {}  # the phase kernels carry the single-case names (kb_fast runs as k_stream_fast, ...)
+    for k, v in kernels.items():
+        alg = kernel_bytes(k, n_nodes, n_elems, n_exact)
+        if alg:
+            rl[k] = {"algorithmic_bytes": alg, "achieved_gbs": alg / (v["ms_per_launch"] * 1e-3) / 1e9}
+    # end to end with host buffers: every step uploads every case's
+    # populations from pinned host memory (alelb_set_pops), advances the
+    # batch one step and reads every case's populations back (alelb_get_pops)
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for s, c in zip(solvers, cases):
+            f = torch.empty((9, c.mesh.n_nodes), dtype=torch.float64).pin_memory().numpy()
+            g = torch.empty((9, c.mesh.n_nodes), dtype=torch.float64).pin_memory().numpy()
+            s.get_pops(f, g)
+            host.append((f, g))
+        Ke = args.e2e_steps
+        t_now = [s.time()[0] for s in solvers]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(Ke):
+            for s, (f, g), t in zip(solvers, host, t_now):
+                s.set_pops(f, g, t=t + k)
+            b.step(1)
+            for s, (f, g) in zip(solvers, host):
+                s.get_pops(f, g)
+        dt = time.perf_counter() - t0
+        bytes_step = 18 * 8 * n_nodes
+        e2e = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
+               "d2h_bytes_per_step": bytes_step, "steps": Ke,
+               "note": "host-resident state: per step alelb_set_pops of every case from pinned FP64 host "
+                       "arrays, alelb_batch_step(1), alelb_get_pops of every case"}
     b.close()
-    total_nodes = n_total
-    return {"value": total_nodes * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "steps": K,
+    return {"value": n_total * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "steps": K,
             "cases": len(sweep) if world == 1 else f"{len(cases)} of {len(sweep)} on rank {rank}",
-            "nodes": total_nodes, "cases_finite_after_timing": finite,
+            "nodes": n_total, "elements": n_elems, "cases_finite_after_timing": finite,
+            "exact_path_per_step": n_exact,
             "cases_on_shifted_lattice": sum(1 for fl in flows if any(fl.shift)), "tuned_launch_shapes": choice,
-            "l2": "inputs larger than L2 (FP32 populations of all cases about 585 MB, double-buffered)",
-            "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt.items()},
-            "gpu_launches": 5 * K}
+            "kernels": kernels, "kernel_rooflines": rl, "method_bytes_per_step": method_bytes(n_nodes, n_elems),
+            "e2e": e2e, "clocks": clocks, "gpu_launches": 5 * K}
 
 
 def run_learned(alelb, torch, dev, args):
@@ -529,21 +641,16 @@ def run_force_history(alelb, args):
     return out
 
 
-def run_ours(args):
-    import torch
-    from paper_2002_04353_gb300 import alelb
-
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    case = workload(args.workload)
+def run_single(alelb, torch, dev, world, args):
+    """The 150,400-node plunge (h = 0.1c, k = 1, Mach 0.2, Re 1e4): the
+    FP32-deviation form and the plain FP64 form, one case.  Its working set
+    fits in L2, so L2 is flushed (a 512 MiB write) before every timed step
+    and only the step is timed.  Also the end-to-end figure of one case
+    (host-resident state through the C-ABI)."""
+    case = workload("plunge150k")
     mesh = alelb.Mesh(case.mesh, case.motion)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    peak, peak_src = measured_peaks()
 
     def timed(prec, steps, warmup, profile):
         s = alelb.Solver(mesh, case.flow, prec, stream=stream.cuda_stream)
@@ -551,8 +658,6 @@ def run_ours(args):
         s.sync()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
-        if world > 1:
-            torch.distributed.barrier()
         torch.cuda.synchronize()
         walks0 = s.info()["walks"]
         with torch.cuda.stream(stream):
@@ -566,11 +671,8 @@ def run_ours(args):
         ms = sum(a.elapsed_time(b) for a, b in evs)
         info = s.info()
         info["walks_timed"] = info["walks"] - walks0
-        info["step_ms"] = [a.elapsed_time(b) for a, b in evs]
         kt = {}
         if profile:
-            # per-kernel device times from a separate run of the same steps
-            # (events around every launch), outside the timed region
             s.profile(True)
             with torch.cuda.stream(stream):
                 for k in range(min(steps, 10)):
@@ -582,34 +684,17 @@ def run_ours(args):
         s.close()
         return ms, kt, info
 
-    W, K = max(3, args.warmup), args.steps
-    sampler = ClockSampler(local)
-    sampler.start()
+    W, K = max(3, args.warmup), args.single_steps
     ms32, kt32, info32 = timed(alelb.PREC_FP32_DEV, K, W, True)
-    clocks = sampler.stop()
-    ms64, kt64, info64 = timed(alelb.PREC_FP64, max(2, K // 4), W, True)
-    from paper_2002_04353_gb300 import shard
-    ms32, ms64 = shard.max_over_ranks(ms32, torch, dev), shard.max_over_ranks(ms64, torch, dev)
+    K64 = max(2, K // 4)
+    ms64, kt64, _ = timed(alelb.PREC_FP64, K64, W, True)
     N, E = case.mesh.n_nodes, case.mesh.n_elems
-    value = world * N * K / (ms32 * 1e-3) / 1e6
-    value64 = world * N * max(2, K // 4) / (ms64 * 1e-3) / 1e6
-
-    # dominant kernel roofline (FP32-deviation form)
-    n_exact = info32["walks_timed"] / K  # populations through the exact path per step
-    top = max(kt32, key=lambda k: kt32[k][0])
-    top_ms, top_n = kt32[top]
-    alg = kernel_bytes(top, N, E, n_exact)
-    achieved = alg / (top_ms / top_n * 1e-3) / 1e9
-    per_kernel = {k: {"algorithmic_bytes": kernel_bytes(k, N, E, n_exact),
+    n_exact = info32["walks_timed"] / K
+    per_kernel = {k: {"ms_per_launch": v[0] / v[1], "algorithmic_bytes": kernel_bytes(k, N, E, n_exact),
                       "achieved_gbs": kernel_bytes(k, N, E, n_exact) / (v[0] / v[1] * 1e-3) / 1e9}
                   for k, v in kt32.items() if v[1]}
-    step_bytes = sum(kernel_bytes(k, N, E, n_exact) for k in STEP_KERNELS)
-
-    # end to end through the C-ABI with host buffers: host-resident state,
-    # every step uploads the populations from pinned host memory, advances
-    # one step and reads the new populations back
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         s = alelb.Solver(mesh, case.flow, alelb.PREC_FP32_DEV, stream=stream.cuda_stream)
         f = torch.empty((9, N), dtype=torch.float64).pin_memory().numpy()
         g = torch.empty((9, N), dtype=torch.float64).pin_memory().numpy()
@@ -622,11 +707,58 @@ def run_ours(args):
             s.get_pops(f, g)
         dt = time.perf_counter() - t0
         s.close()
-        e2e = {"value": world * N * Ke / dt / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": 18 * N * 8, "d2h_bytes_per_step": 18 * N * 8,
-               "note": "host-resident state: set_pops, lb_step(1), get_pops per step (FP64 host arrays)"}
+        e2e = {"value": world * N * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 18 * N * 8,
+               "d2h_bytes_per_step": 18 * N * 8}
+    return {
+        "workload": case.name, "nodes": N, "elements": E,
+        "fp32_dev": {"value": world * N * K / (ms32 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms32 / K,
+                     "steps": K, "kernels": per_kernel,
+                     "step_algorithmic_gbs": sum(kernel_bytes(k, N, E, n_exact) for k in STEP_KERNELS)
+                     / (ms32 / K * 1e-3) / 1e9,
+                     "method_bytes_frac": method_bytes(N, E) / (ms32 / K * 1e-3) / 1e9 / measured_peaks()[0],
+                     "walks_per_step": n_exact,
+                     "verified_previous_element_rate": 1.0 - n_exact / (9.0 * N),
+                     "traffic_ncu_per_launch": NCU_TRAFFIC_150K,
+                     "l2": "flushed (512 MiB write) before every timed step; only the step is timed"},
+        "fp64_plain": {"value": world * N * K64 / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64 / K64,
+                       "steps": K64,
+                       "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1])} for k, v in kt64.items() if v[1]}},
+        "e2e": e2e,
+    }
 
-    batched = None if args.no_batched else run_batched(alelb, torch, dev, world, rank, args)
+
+def run_ours(args):
+    import torch
+    from paper_2002_04353_gb300 import alelb
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peak, peak_src = measured_peaks()
+    W, K = max(3, args.warmup), args.steps
+
+    # headline: the batched sweep, clocks sampled during its timed region
+    sampler = ClockSampler(local)
+    bat = run_batched(alelb, torch, dev, world, rank, args, sampler)
+    ms_step = bat["ms_per_step"]
+    top = max(bat["kernels"], key=lambda k: bat["kernels"][k]["ms_per_launch"])
+    top_rl = bat["kernel_rooflines"].get(top, {})
+    roofline = {"bound": "hbm", "kernel": top, "achieved": top_rl.get("achieved_gbs"), "peak": peak,
+                "unit": "GB/s", "frac": (top_rl.get("achieved_gbs") or 0.0) / peak, "peak_source": peak_src,
+                "traffic": NCU_TRAFFIC_SWEEP.get(top), "algorithmic_bytes_per_launch": top_rl.get("algorithmic_bytes"),
+                "launch_ms": bat["kernels"][top]["ms_per_launch"],
+                "note": ("achieved = algorithmic bytes of one launch over the sweep / its CUDA-event duration "
+                         "(launched one by one right after the timed region); traffic = ncu dram bytes of one "
+                         "launch on this workload")}
+    mb = bat["method_bytes_per_step"]
+    step_rl = {"method_bytes_per_step": mb, "method_bytes_per_node": mb / bat["nodes"],
+               "achieved_gbs": mb / (ms_step * 1e-3) / 1e9, "frac": mb / (ms_step * 1e-3) / 1e9 / peak,
+               "note": "the method's own bytes (populations once each way, derivative-pass fields, geometry)"}
+
+    single = None if args.no_single else run_single(alelb, torch, dev, world, args)
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
     forces = None if (args.no_forces or world > 1) else run_force_history(alelb, args)
     precision = precision_low = None
@@ -638,51 +770,49 @@ def run_ours(args):
         # the paper's wall condition on the plain lattice, at a Mach number it holds
         precision_low = run_precision(alelb, torch, dev, args, 0.3)
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt = cpu_baseline(case, args.cpu_steps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_steps} steps of the full {N}-node mesh from the free-stream start, "
-                         f"plain FP64 C oracle, one host core ({dt:.1f} s)"}
+        sweep = I.batched_sweep()
+        model, ncpu = cpu_model()
+        reps = representative_cases(sweep)
+        nodes = [sweep[k].mesh.n_nodes for k in reps]
+        v, dt, used, work = cpu_baseline(sweep, args.cpu_steps, ncpu or 1)
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "cpu_model": model, "nproc": ncpu,
+               "sample": f"{args.cpu_steps} steps each of the sweep's smallest, median and largest cases "
+                         f"({nodes} nodes) after one untimed step, plain FP64 C oracle, OpenMP over nodes on "
+                         f"{used} threads ({dt:.1f} s)"}
+        v1, dt1, used1, _ = cpu_baseline(sweep, args.cpu_steps_1core, 1)
+        cpu1 = {"value": v1, "unit": UNIT, "cores": used1, "kind": "oracle", "cpu_model": model,
+                "sample": f"{args.cpu_steps_1core} steps each of the same three cases, one thread ({dt1:.1f} s)"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "metric": METRIC, "value": bat["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "precision": "FP32 populations (deviations) and arithmetic; FP64 map, "
-                                         "departure points and element location",
+                                         "departure points and element decisions",
             "data": "synthetic",
-            "config": {"workload": case.name, "nodes": N, "elements": E,
-                       "mach": round(math.hypot(*case.flow.u_inf) / math.sqrt(1.4 * case.flow.T_inf), 4),
-                       "re": 1e4, "chord": case.mesh.meta["chord"], "motion": args.workload,
-                       "l2": "flushed (512 MiB write) before every timed step; only the step is timed",
-                       "parallelism": f"replicas x{world}"},
-            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / max(2, K // 4)},
-            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": NCU_TRAFFIC_150K.get(top) if args.workload == "plunge150k" else None,
-                         "algorithmic_bytes_per_launch": alg,
-                         "launch_ms": top_ms / top_n,
-                         "note": ("the exact-path kernel is latency-bound (one short dependent chain per "
-                                  "listed population), not bandwidth-bound" if top == "k_stream_slow" else "")},
-            "kernel_rooflines": per_kernel,
-            "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
-                              "achieved_gbs": step_bytes / (ms32 / K * 1e-3) / 1e9,
-                              "frac": step_bytes / (ms32 / K * 1e-3) / 1e9 / peak},
-            "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt32.items()},
-            "kernels_fp64": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt64.items()},
-            "gpu_launches": 5 * K,
-            "batched": batched,
+            "config": {"workload": SWEEP_NAME, "cases": 32, "nodes": bat["nodes"], "elements": bat["elements"],
+                       "mach": "0.1-0.8 (cases >= 0.5 on the lattice shifted by (0.3, 0))", "re": 1e4,
+                       "chord": 1000.0, "motion": "rigid pitch 0-5 deg + plunge 0-0.2c, k 0.05-1",
+                       "l2": "inputs larger than L2 (FP32 populations of all cases 585 MB, double-buffered); "
+                             "steps timed back to back",
+                       "parallelism": f"cases sharded over {world} GPU(s)" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "step_roofline": step_rl,
+            "batched": {k: v for k, v in bat.items() if k not in ("e2e", "clocks")},
+            "fp64_plain": None if single is None else dict(single["fp64_plain"], workload=single["workload"]),
+            "single_case": None if single is None else dict(single["fp32_dev"], workload=single["workload"],
+                                                            e2e=single["e2e"]),
+            "gpu_launches": bat["gpu_launches"],
             "learned_proposal": learned,
             "precision_study": precision,
             "force_history": forces,
             "precision_study_ma03": precision_low,
-            "locate": {"walks_per_step": info32["walks_timed"] / K,
-                       "verified_previous_element_rate": 1.0 - info32["walks_timed"] / (9.0 * N * K)},
-            "step_ms": [round(x, 4) for x in info32["step_ms"]],
-            "e2e": e2e,
+            "e2e": bat["e2e"],
             "cpu_baseline": cpu,
-            "clocks": clocks,
+            "cpu_baseline_1core": cpu1,
+            "clocks": bat["clocks"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -692,14 +822,16 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=1000, help="timed steps of the batched sweep (the headline)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-steps-1core", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plunge150k", choices=sorted(WORKLOADS))
-    ap.add_argument("--batched-steps", type=int, default=20)
-    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--single-steps", type=int, default=40)
+    ap.add_argument("--no-single", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=10)
@@ -707,7 +839,12 @@ def main():
     ap.add_argument("--prec-mach", type=float, default=0.75)
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-forces", action="store_true")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="the headline alone (no single case, e2e, network, precision, forces, CPU baseline)")
     args = ap.parse_args()
+    if args.only_batched:
+        args.no_single = args.no_e2e = args.no_mlp = args.no_precision = args.no_forces = True
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -36,11 +36,12 @@ FLAG_OFFWALL_VG = 256
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (plain C99, -O2,
-    -ffp-contract=off so that every FP64 operation rounds as written)."""
+    -ffp-contract=off so that every FP64 operation rounds as written;
+    OpenMP over the independent node loops of a step)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC",
+        cmd = ["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-fopenmp",
                "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
@@ -93,6 +94,8 @@ def lib():
             L.orc_shape.argtypes = [d, d, dp]
             L.orc_status.argtypes = [p]
             L.orc_status.restype = i
+            L.orc_threads.argtypes = [i]
+            L.orc_threads.restype = i
             _lib = L
     return _lib
 
@@ -218,6 +221,12 @@ class Oracle:
         nb = lib().orc_wall_info(self.h, w, n, pe, px)
         return dict(is_wall=w.astype(bool), normal=n.reshape(nn, 2), probe_e=pe,
                     probe_xi=px.reshape(nn, 2), n_boundary_edges=nb)
+
+
+def threads(n=0):
+    """Threads of the oracle's node loops: n > 0 sets the count; returns the
+    count in use."""
+    return lib().orc_threads(int(n))
 
 
 # ---- node-local hooks -------------------------------------------------------

@@ -66,6 +66,9 @@
  * reconstruction); the paper prints no force values for these setups.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -1585,20 +1588,34 @@ static int step_once(orc_t *o)
         motion_scalars(o, t1 - 0.5, &Sh);
         Sd = &Sh;
     }
+    /* Every node below is computed on its own from shared read-only data and
+       writes only its own entries, so the node loops may run on several
+       threads (OpenMP) with results independent of the thread count. */
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int a = 0; a < nn; ++a) {
         double xX, xY, yX, yY, Vx, Vy;
         motion_node(o, a, &S, &xX, &xY, &yX, &yY, &Vx, &Vy);
-        if (metric_inverse(xX, xY, yX, yY, &o->gi[4 * a])) return ST_MAP;
+        if (metric_inverse(xX, xY, yX, yY, &o->gi[4 * a])) bad = 1;
     }
+    if (bad) return ST_MAP;
     /* propagation */
+    int first_err = 0;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int a = 0; a < nn; ++a) {
         int st = stream_node(o, a, &S, Sd, S0);
-        if (st) return st;
+        if (st) {
+#pragma omp critical(orc_err)
+            if (!first_err) first_err = st;
+        }
     }
+    if (first_err) return first_err;
     /* moments, Q'_aaa = rho w_a (1 - 3T) - rho w_a^3 with w = u - U (Eq. DeviationTerms),
        mu/(rho T) */
     double *R = xcalloc(nn, sizeof(double)), *UX = xcalloc(nn, sizeof(double)),
            *UY = xcalloc(nn, sizeof(double)), *TT = xcalloc(nn, sizeof(double));
+    int nonfinite = 0;
+#pragma omp parallel for schedule(static) reduction(| : nonfinite)
     for (int a = 0; a < nn; ++a) {
         double r = 0, jx = 0, jy = 0, e2 = 0;
         for (int i = 0; i < NQ; ++i) {
@@ -1611,11 +1628,8 @@ static int step_once(orc_t *o)
         double ux = jx / r, uy = jy / r, E = e2 / (2.0 * r);
         double T = (E - 0.5 * (ux * ux + uy * uy)) / o->K.Cv;
         if (!isfinite(r) || !isfinite(T) || !(r > 0) || !(T > 0)) {
-            free(R);
-            free(UX);
-            free(UY);
-            free(TT);
-            return ST_NONFINITE;
+            nonfinite = 1;
+            continue;
         }
         R[a] = r;
         UX[a] = ux;
@@ -1628,7 +1642,15 @@ static int step_once(orc_t *o)
         o->Qy[a] = r * wy * (1.0 - 3.0 * T) - r * wy * wy * wy;
         o->m_rt[a] = o->K.mu / (r * T);
     }
+    if (nonfinite) {
+        free(R);
+        free(UX);
+        free(UY);
+        free(TT);
+        return ST_NONFINITE;
+    }
     /* first derivative pass: D_a = (mu / rho T) d_a Q'_aaa (Eq. Xa) */
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < nn; ++a) {
         double KX, KY, dx, dy;
         fe_grad_X(o, a, o->Qx, &KX, &KY);
@@ -1639,6 +1661,7 @@ static int step_once(orc_t *o)
         o->Dy[a] = o->m_rt[a] * dy;
     }
     /* second pass: X_a = -d_a D_a */
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < nn; ++a) {
         double KX, KY, dx, dy;
         fe_grad_X(o, a, o->Dx, &KX, &KY);
@@ -1653,6 +1676,7 @@ static int step_once(orc_t *o)
         }
     }
     /* collision */
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < nn; ++a) {
         double f[NQ], g[NQ], fo[NQ], go[NQ];
         for (int i = 0; i < NQ; ++i) {
@@ -1704,21 +1728,26 @@ int orc_locate(void *h, double t, int *elem, int8_t *kind)
     orc_t *o = h;
     mscal_t S;
     motion_scalars(o, t, &S);
+    int bad = 0; /* 1: folded map, 2: walk limit */
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
     for (int a = 0; a < o->nn; ++a) {
         double xX, xY, yX, yY, Vx, Vy, gi[4];
         motion_node(o, a, &S, &xX, &xY, &yX, &yY, &Vx, &Vy);
-        if (metric_inverse(xX, xY, yX, yY, gi)) return ST_MAP;
+        if (metric_inverse(xX, xY, yX, yY, gi)) {
+            bad |= 1;
+            continue;
+        }
         for (int i = 0; i < NQ; ++i) {
             double chx, chy, px, py, sx, sy;
             int kd;
             departure(o, a, gi, Vx, Vy, i, &chx, &chy, &px, &py);
             int e = choose_element(o, a, chx, chy, px, py, &sx, &sy, &kd);
-            if (e == -3) return ST_LOCATE;
+            if (e == -3) bad |= 2;
             elem[(size_t)i * o->nn + a] = e;
             kind[(size_t)i * o->nn + a] = (int8_t)(e == -1 ? kd : 0);
         }
     }
-    return ST_OK;
+    return (bad & 1) ? ST_MAP : (bad & 2) ? ST_LOCATE : ST_OK;
 }
 
 /* Departure points at map time t (x and y, [i*nn + a]). */
@@ -1865,3 +1894,16 @@ int orc_forces(void *h, double *out)
 }
 
 int orc_status(void *h) { return ((orc_t *)h)->status; }
+
+/* Threads of the node loops of a step: n > 0 sets the count (OpenMP),
+   n <= 0 leaves it; returns the count in use (1 without OpenMP). */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

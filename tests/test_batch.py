@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import parity_util
 from paper_2002_04353_gb300 import alelb, inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -20,8 +21,7 @@ TOL64 = 1e-12
 TOL32 = 2e-4
 
 
-def _rel(a, b):
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+_rel = parity_util.rel
 
 
 def _cases():
@@ -65,15 +65,13 @@ def test_batch_matches_oracle_per_case(prec):
         if prec == alelb.PREC_FP64:
             f, g = s.get_pops()
             assert _rel(f, st["f"]) < TOL64 and _rel(g, st["g"]) < TOL64, f"case {c}"
-            for k in ("rho", "ux", "uy", "T"):
-                assert _rel(mo[k], st[k]) < TOL64, f"case {c}: {k}"
+            for k, e in parity_util.field_errors(mo, st).items():
+                assert e < TOL64, f"case {c}: {k} {e:.2e}"
             if c > 0:
                 fo, fg = o.forces(), s.forces()
                 assert np.allclose(fg, fo, rtol=1e-10, atol=1e-12 * np.abs(fo).max())
         else:
-            for k in ("rho", "ux", "uy", "T"):
-                scale = 1.0 if k in ("rho", "T") else max(np.abs(st["ux"]).max(), np.abs(st["uy"]).max())
-                err = np.abs(mo[k] - st[k]).max() / scale
+            for k, err in parity_util.field_errors(mo, st).items():
                 assert err < TOL32, f"case {c}: {k} err {err:.2e}"
 
 
@@ -96,8 +94,8 @@ def test_batch_equals_solvers_stepped_alone(prec):
         fb, gb = sb.get_pops()
         assert _rel(fb, fa) < tol and _rel(gb, ga) < tol, f"case {c}"
         ma, mb = sa.moments(), sb.moments()
-        for k in ma:
-            assert _rel(mb[k], ma[k]) < tol, f"case {c}: {k}"
+        for k, e in parity_util.field_errors(mb, ma).items():
+            assert e < tol, f"case {c}: {k} {e:.2e}"
         assert sa.info()["walks"] == sb.info()["walks"]
 
 
