@@ -59,7 +59,7 @@ def lib():
             u8p = np.ctypeslib.ndpointer(np.uint8, flags="C")
             i8p = np.ctypeslib.ndpointer(np.int8, flags="C")
             L.orc_create.restype = p
-            L.orc_create.argtypes = [i, dp, i, ip, u8p, d, d, i, dp, dp, C.POINTER(C.c_int)]
+            L.orc_create.argtypes = [i, dp, i, ip, u8p, i, d, d, i, dp, dp, C.POINTER(C.c_int)]
             L.orc_destroy.argtypes = [p]
             L.orc_init.argtypes = [p]
             L.orc_step.argtypes = [p, i]
@@ -92,6 +92,9 @@ def lib():
             L.orc_collide.argtypes = [dp, dp, dp, d, d, dp, dp]
             L.orc_grad_bc.argtypes = [dp, d, d, d, d, dp, dp, dp, dp]
             L.orc_shape.argtypes = [d, d, dp]
+            L.orc_shape_q2.argtypes = [d, d, dp]
+            L.orc_local.argtypes = [p, i, d, d, dp]
+            L.orc_local.restype = i
             L.orc_status.argtypes = [p]
             L.orc_status.restype = i
             L.orc_threads.argtypes = [i]
@@ -122,8 +125,8 @@ class Oracle:
         X = np.ascontiguousarray(mesh.X, dtype=np.float64).reshape(-1)
         conn = np.ascontiguousarray(mesh.conn, dtype=np.int32).reshape(-1)
         ek = np.ascontiguousarray(mesh.edge_kind, dtype=np.uint8).reshape(-1)
-        self.h = L.orc_create(mesh.n_nodes, X, mesh.n_elems, conn, ek, float(mesh.period[0]),
-                              float(mesh.period[1]), int(motion.kind),
+        self.h = L.orc_create(mesh.n_nodes, X, mesh.n_elems, conn, ek, int(getattr(mesh, "elem_type", 0)),
+                              float(mesh.period[0]), float(mesh.period[1]), int(motion.kind),
                               np.ascontiguousarray(motion.params, dtype=np.float64), self.kin,
                               C.byref(st))
         self.nn = mesh.n_nodes
@@ -200,6 +203,14 @@ class Oracle:
         e = lib().orc_interp(self.h, float(px), float(py), np.ascontiguousarray(K, dtype=np.float64),
                              out)
         return e, out[0]
+
+    def local(self, e, px, py):
+        """Local coordinates of computational point (px, py) in element e."""
+        out = np.empty(2)
+        st = lib().orc_local(self.h, int(e), float(px), float(py), out)
+        if st:
+            raise OracleError(f"oracle local coordinates failed: status {st}")
+        return out
 
     def forces(self):
         out = np.empty(6)
@@ -292,4 +303,11 @@ def grad_bc(flow, rho, ux, uy, T, du, dT):
 def shape(xi, eta):
     out = np.empty(6)
     lib().orc_shape(xi, eta, out)
+    return out
+
+
+def shape_q2(xi, eta):
+    """The 9-node quadrilateral's shape functions at (xi, eta) in [-1, 1]^2."""
+    out = np.empty(9)
+    lib().orc_shape_q2(xi, eta, out)
     return out

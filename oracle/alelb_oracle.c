@@ -51,7 +51,13 @@
  *       targets for wall nodes only); pinned by the one-step closed form
  *       next to a receding wall (the reading itself has no passage)
  *   R9  forces: p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule
- *       on each straight P2 wall edge of the mapped geometry
+ *       on each straight 3-node wall edge of the mapped geometry
+ *   R12 elements: straight-sided 6-node triangles, or the paper's 9-node
+ *       quadrilaterals (Sec. III) whose local coordinates solve the
+ *       bilinear system of Eq. NonLinear_Eq by Newton's method from the
+ *       cell centre with a fixed number of iterations (the paper names no
+ *       method); on quadrilaterals the wall condition's first-order
+ *       gradient is that of the bilinear interpolant of the vertex values
  *   R14 shifted lattice (velocities c_i + U, Sec. V.D; the model itself is
  *       deferred to another paper): every population set carries the same
  *       lab-frame moments as on the plain lattice -- f^eq in u - U, the
@@ -476,6 +482,109 @@ static void shape_dxi(double xi, double eta, double *Nxi, double *Neta)
 static const double LOCAL_XI[6][2] = {{0, 0}, {1, 0}, {0, 1}, {0.5, 0}, {0.5, 0.5}, {0, 0.5}};
 
 /* ======================================================================
+ * The paper's 9-node quadrilateral (Sec. III, Eq. Propagation with
+ * s = 1..9): second-order Lagrange polynomials on the nine equidistant
+ * collocation nodes of the reference cell -1 <= xi, eta <= 1, i.e. the
+ * products of the one-dimensional quadratics through -1, 0, 1.  Node
+ * order: corners v0 (-1,-1), v1 (1,-1), v2 (1,1), v3 (-1,1)
+ * (counter-clockwise), midside nodes of edges (v0,v1), (v1,v2), (v2,v3),
+ * (v3,v0), then the centre.  Pinned: partition of unity, Kronecker
+ * property, reproduction of every polynomial of degree <= 2 in each of
+ * xi and eta.
+ * ==================================================================== */
+static const int Q2_I[9] = {0, 2, 2, 0, 1, 2, 1, 0, 1}; /* xi  = Q2_I - 1 */
+static const int Q2_J[9] = {0, 0, 2, 2, 0, 1, 2, 1, 1}; /* eta = Q2_J - 1 */
+
+static void lagrange3(double s, double *L, double *dL)
+{
+    L[0] = 0.5 * s * (s - 1.0);
+    L[1] = (1.0 - s) * (1.0 + s);
+    L[2] = 0.5 * s * (s + 1.0);
+    if (dL) {
+        dL[0] = s - 0.5;
+        dL[1] = -2.0 * s;
+        dL[2] = s + 0.5;
+    }
+}
+
+void orc_shape_q2(double xi, double eta, double *N)
+{
+    double Lx[3], Ly[3];
+    lagrange3(xi, Lx, NULL);
+    lagrange3(eta, Ly, NULL);
+    for (int s = 0; s < 9; ++s) N[s] = Lx[Q2_I[s]] * Ly[Q2_J[s]];
+}
+
+static void shape_dxi_q2(double xi, double eta, double *Nxi, double *Neta)
+{
+    double Lx[3], Ly[3], dLx[3], dLy[3];
+    lagrange3(xi, Lx, dLx);
+    lagrange3(eta, Ly, dLy);
+    for (int s = 0; s < 9; ++s) {
+        Nxi[s] = dLx[Q2_I[s]] * Ly[Q2_J[s]];
+        Neta[s] = Lx[Q2_I[s]] * dLy[Q2_J[s]];
+    }
+}
+
+/* The bilinear map of Eq. NonLinear_Eq, x(xi, eta) = sum_{s=1..4} N_s x_s
+   over the corners, N_s = (1 +- xi)(1 +- eta)/4, with its Jacobian
+   J = {x_xi, x_eta, y_xi, y_eta}.  w: the 4 corners (x, y). */
+static void bilinear(const double *w, double xi, double eta, double *x, double *y, double *J)
+{
+    double n[4] = {0.25 * (1.0 - xi) * (1.0 - eta), 0.25 * (1.0 + xi) * (1.0 - eta),
+                   0.25 * (1.0 + xi) * (1.0 + eta), 0.25 * (1.0 - xi) * (1.0 + eta)};
+    double nxi[4] = {-0.25 * (1.0 - eta), 0.25 * (1.0 - eta), 0.25 * (1.0 + eta), -0.25 * (1.0 + eta)};
+    double neta[4] = {-0.25 * (1.0 - xi), -0.25 * (1.0 + xi), 0.25 * (1.0 + xi), 0.25 * (1.0 - xi)};
+    double sx = 0, sy = 0, a = 0, b = 0, c = 0, d = 0;
+    for (int k = 0; k < 4; ++k) {
+        sx += n[k] * w[2 * k];
+        sy += n[k] * w[2 * k + 1];
+        a += nxi[k] * w[2 * k];
+        b += neta[k] * w[2 * k];
+        c += nxi[k] * w[2 * k + 1];
+        d += neta[k] * w[2 * k + 1];
+    }
+    if (x) *x = sx;
+    if (y) *y = sy;
+    if (J) {
+        J[0] = a;
+        J[1] = b;
+        J[2] = c;
+        J[3] = d;
+    }
+}
+
+/* Local coordinates of the departure point in a quadrilateral: Newton's
+   method on the bilinear system of Eq. NonLinear_Eq, which the paper
+   solves every step without naming a method (reading Q5): start at the
+   centre (0, 0), a fixed number of iterations so that every run takes the
+   same steps, then the last update must be negligible.  The corners are
+   taken relative to p.  Returns 0, or ST_LOCATE when it has not converged. */
+#define Q2_NEWTON_ITERS 8
+static int q2_local(const double *v, double sx, double sy, double px, double py, double *xi,
+                    double *eta)
+{
+    double w[8];
+    for (int k = 0; k < 4; ++k) {
+        w[2 * k] = (v[2 * k] + sx) - px;
+        w[2 * k + 1] = (v[2 * k + 1] + sy) - py;
+    }
+    double a = 0.0, b = 0.0, da = 0.0, db = 0.0;
+    for (int it = 0; it < Q2_NEWTON_ITERS; ++it) {
+        double rx, ry, J[4];
+        bilinear(w, a, b, &rx, &ry, J);
+        double det = J[0] * J[3] - J[1] * J[2];
+        da = (J[3] * rx - J[1] * ry) / det;
+        db = (-J[2] * rx + J[0] * ry) / det;
+        a -= da;
+        b -= db;
+    }
+    *xi = a;
+    *eta = b;
+    return (fabs(da) <= 1e-9 && fabs(db) <= 1e-9) ? 0 : ST_LOCATE;
+}
+
+/* ======================================================================
  * Oracle state
  * ==================================================================== */
 typedef struct {
@@ -496,11 +605,13 @@ typedef struct {
 typedef struct {
     /* mesh */
     int nn, ne;
+    int etype;    /* 0: 6-node triangles, 1: 9-node quadrilaterals */
+    int nv, nne;  /* vertices and nodes per element (3, 6 or 4, 9) */
     double *X;
     int *conn;
     uint8_t *ekind;
     double Lx, Ly;
-    double *ev;    /* 12 per element: node coords in the element frame */
+    double *ev;    /* EVS per element: node coords in the element frame */
     double *area2; /* twice the computational area */
     int *owner, *owner_loc;
     int *bcel; /* element of the wall condition's gradients (R8) */
@@ -536,6 +647,8 @@ typedef struct {
     double *fs, *gs, *m_rt, *Qx, *Qy, *Dx, *Dy, *Xx, *Xy, *gi;
 } orc_t;
 
+#define EVS 18 /* doubles of element frame: 9 nodes x (x, y) */
+
 static void *xcalloc(size_t n, size_t s)
 {
     void *p = calloc(n ? n : 1, s);
@@ -553,6 +666,68 @@ static double unwrap1(double d, double L)
         else if (d < -0.5 * L) d += L;
     }
     return d;
+}
+
+/* ---------------------------------------------------------------------
+ * Element kinds.  Both are straight-sided: the 6-node triangle, whose
+ * local coordinates follow from the affine map in closed form, and the
+ * paper's 9-node quadrilateral, whose local coordinates solve the bilinear
+ * system of Eq. NonLinear_Eq.
+ * ------------------------------------------------------------------- */
+/* Local coordinates of p in element e shifted by (sx, sy).  Returns 0 or
+   ST_LOCATE (Newton did not converge). */
+static int elem_local(const orc_t *o, int e, double sx, double sy, double px, double py, double *xi,
+                      double *eta)
+{
+    const double *v = &o->ev[EVS * e];
+    if (o->etype == 1) return q2_local(v, sx, sy, px, py, xi, eta);
+    double x0 = v[0] + sx, y0 = v[1] + sy;
+    double x_xi = v[2] - v[0], x_eta = v[4] - v[0];
+    double y_xi = v[3] - v[1], y_eta = v[5] - v[1];
+    double detJ = x_xi * y_eta - y_xi * x_eta;
+    *xi = (y_eta * (px - x0) - x_eta * (py - y0)) / detJ;
+    *eta = (-y_xi * (px - x0) + x_xi * (py - y0)) / detJ;
+    return 0;
+}
+
+static void elem_shape(const orc_t *o, double xi, double eta, double *N)
+{
+    if (o->etype == 1) orc_shape_q2(xi, eta, N);
+    else orc_shape(xi, eta, N);
+}
+
+/* Local coordinates of local node l. */
+static void node_local(const orc_t *o, int l, double *xi, double *eta)
+{
+    if (o->etype == 1) {
+        *xi = Q2_I[l] - 1.0;
+        *eta = Q2_J[l] - 1.0;
+    } else {
+        *xi = LOCAL_XI[l][0];
+        *eta = LOCAL_XI[l][1];
+    }
+}
+
+/* Jacobian {x_xi, x_eta, y_xi, y_eta} of element e at (xi, eta). */
+static void elem_jacobian(const orc_t *o, int e, double xi, double eta, double *J)
+{
+    const double *v = &o->ev[EVS * e];
+    if (o->etype == 1) {
+        bilinear(v, xi, eta, NULL, NULL, J);
+        return;
+    }
+    J[0] = v[2] - v[0];
+    J[1] = v[4] - v[0];
+    J[2] = v[3] - v[1];
+    J[3] = v[5] - v[1];
+}
+
+/* Local index of node a in element e, or -1. */
+static int local_index(const orc_t *o, int e, int a)
+{
+    for (int l = 0; l < o->nne; ++l)
+        if (o->conn[o->nne * e + l] == a) return l;
+    return -1;
 }
 
 /* ---------------------------------------------------------------------
@@ -774,9 +949,9 @@ static void qt_push_ent(orc_t *o, qent_t e)
 
 static void ent_bbox(const orc_t *o, qent_t q, double *b)
 {
-    const double *v = &o->ev[12 * q.e];
+    const double *v = &o->ev[EVS * q.e];
     double x0 = v[0], x1 = v[0], y0 = v[1], y1 = v[1];
-    for (int k = 1; k < 3; ++k) {
+    for (int k = 1; k < o->nv; ++k) {
         x0 = fmin(x0, v[2 * k]);
         x1 = fmax(x1, v[2 * k]);
         y0 = fmin(y0, v[2 * k + 1]);
@@ -847,12 +1022,14 @@ static int qt_leaf(const orc_t *o, double x, double y)
     return node;
 }
 
-static int contains_closed(const double *v, double sx, double sy, double px, double py,
+/* p in the closed (convex, straight-edged) element with nv vertices v,
+   shifted by (sx, sy): exact signs against every edge. */
+static int contains_closed(const double *v, int nv, double sx, double sy, double px, double py,
                            int *zeros)
 {
     int z = 0;
-    for (int k = 0; k < 3; ++k) {
-        int k1 = (k + 1) % 3;
+    for (int k = 0; k < nv; ++k) {
+        int k1 = (k + 1) % nv;
         int s = orc_orient(v[2 * k] + sx, v[2 * k + 1] + sy, v[2 * k1] + sx, v[2 * k1 + 1] + sy,
                            px, py);
         if (s < 0) return 0;
@@ -889,11 +1066,17 @@ static int locate_point(const orc_t *o, double px, double py, double *shx, doubl
     for (int k = 0; k < nd->count; ++k) {
         qent_t q = o->qe[nd->start + k];
         double sx = (q.sx + kx) * o->Lx, sy = (q.sy + ky) * o->Ly;
-        const double *v = &o->ev[12 * q.e];
-        if (px < fmin(v[0], fmin(v[2], v[4])) + sx || px > fmax(v[0], fmax(v[2], v[4])) + sx ||
-            py < fmin(v[1], fmin(v[3], v[5])) + sy || py > fmax(v[1], fmax(v[3], v[5])) + sy)
+        const double *v = &o->ev[EVS * q.e];
+        double x0 = v[0], x1 = v[0], y0 = v[1], y1 = v[1];
+        for (int j = 1; j < o->nv; ++j) {
+            x0 = fmin(x0, v[2 * j]);
+            x1 = fmax(x1, v[2 * j]);
+            y0 = fmin(y0, v[2 * j + 1]);
+            y1 = fmax(y1, v[2 * j + 1]);
+        }
+        if (px < x0 + sx || px > x1 + sx || py < y0 + sy || py > y1 + sy)
             continue; /* outside the bounding box: cannot contain p */
-        if (!contains_closed(v, sx, sy, px, py, NULL)) continue;
+        if (!contains_closed(v, o->nv, sx, sy, px, py, NULL)) continue;
         if (best < 0 || o->area2[q.e] > o->area2[best] ||
             (o->area2[q.e] == o->area2[best] && q.e < best)) {
             best = q.e;
@@ -918,26 +1101,44 @@ static double seg_point_dist(double ax, double ay, double bx, double by, double 
 
 static int prepare(orc_t *o)
 {
-    int nn = o->nn, ne = o->ne;
-    o->ev = xcalloc((size_t)12 * ne, sizeof(double));
+    int nn = o->nn, ne = o->ne, nv = o->nv, nne = o->nne;
+    o->ev = xcalloc((size_t)EVS * ne, sizeof(double));
     o->area2 = xcalloc((size_t)ne, sizeof(double));
     for (int e = 0; e < ne; ++e) {
-        const int *c = &o->conn[6 * e];
+        const int *c = &o->conn[nne * e];
         double x0 = o->X[2 * c[0]], y0 = o->X[2 * c[0] + 1];
-        for (int l = 0; l < 6; ++l) {
+        for (int l = 0; l < nne; ++l) {
             double x = o->X[2 * c[l]], y = o->X[2 * c[l] + 1];
-            o->ev[12 * e + 2 * l] = x0 + unwrap1(x - x0, o->Lx);
-            o->ev[12 * e + 2 * l + 1] = y0 + unwrap1(y - y0, o->Ly);
+            o->ev[EVS * e + 2 * l] = x0 + unwrap1(x - x0, o->Lx);
+            o->ev[EVS * e + 2 * l + 1] = y0 + unwrap1(y - y0, o->Ly);
         }
-        const double *v = &o->ev[12 * e];
-        double a2 = (v[2] - v[0]) * (v[5] - v[1]) - (v[4] - v[0]) * (v[3] - v[1]);
+        const double *v = &o->ev[EVS * e];
+        double a2;
+        if (o->etype == 1) {
+            /* twice the area of the quadrilateral: half the cross product
+               of its diagonals, doubled; every corner must turn left (a
+               strictly convex cell, so that the bilinear map is one-to-one) */
+            a2 = (v[4] - v[0]) * (v[7] - v[3]) - (v[6] - v[2]) * (v[5] - v[1]);
+            for (int k = 0; k < 4; ++k) {
+                int k1 = (k + 1) % 4, k2 = (k + 2) % 4;
+                double cr = (v[2 * k1] - v[2 * k]) * (v[2 * k2 + 1] - v[2 * k1 + 1]) -
+                            (v[2 * k1 + 1] - v[2 * k + 1]) * (v[2 * k2] - v[2 * k1]);
+                if (!(cr > 0)) return ST_MESH;
+            }
+            /* the centre node is the bilinear map's value at (0, 0) */
+            if (v[16] != 0.25 * (((v[0] + v[2]) + v[4]) + v[6]) ||
+                v[17] != 0.25 * (((v[1] + v[3]) + v[5]) + v[7]))
+                return ST_MESH;
+        } else {
+            a2 = (v[2] - v[0]) * (v[5] - v[1]) - (v[4] - v[0]) * (v[3] - v[1]);
+        }
         if (!(a2 > 0)) return ST_MESH;
         o->area2[e] = a2;
         /* midside nodes must be the exact edge midpoints */
-        for (int k = 0; k < 3; ++k) {
-            int k1 = (k + 1) % 3;
-            if (v[6 + 2 * k] != 0.5 * (v[2 * k] + v[2 * k1]) ||
-                v[7 + 2 * k] != 0.5 * (v[2 * k + 1] + v[2 * k1 + 1]))
+        for (int k = 0; k < nv; ++k) {
+            int k1 = (k + 1) % nv;
+            if (v[2 * nv + 2 * k] != 0.5 * (v[2 * k] + v[2 * k1]) ||
+                v[2 * nv + 2 * k + 1] != 0.5 * (v[2 * k + 1] + v[2 * k1 + 1]))
                 return ST_MESH;
         }
     }
@@ -948,8 +1149,8 @@ static int prepare(orc_t *o)
     o->owner_loc = xcalloc((size_t)nn, sizeof(int));
     for (int a = 0; a < nn; ++a) o->owner[a] = -1;
     for (int e = 0; e < ne; ++e)
-        for (int l = 0; l < 6; ++l) {
-            int a = o->conn[6 * e + l];
+        for (int l = 0; l < nne; ++l) {
+            int a = o->conn[nne * e + l];
             int b = o->owner[a];
             if (b < 0 || o->area2[e] > o->area2[b] || (o->area2[e] == o->area2[b] && e < b)) {
                 o->owner[a] = e;
@@ -1006,16 +1207,16 @@ static int prepare(orc_t *o)
     /* boundary edges */
     o->nbe = 0;
     for (int e = 0; e < ne; ++e)
-        for (int k = 0; k < 3; ++k)
-            if (o->ekind[3 * e + k] != EK_INTERIOR) o->nbe++;
+        for (int k = 0; k < nv; ++k)
+            if (o->ekind[nv * e + k] != EK_INTERIOR) o->nbe++;
     o->be = xcalloc((size_t)o->nbe, sizeof(bedge_t));
     int nb = 0;
     for (int e = 0; e < ne; ++e)
-        for (int k = 0; k < 3; ++k)
-            if (o->ekind[3 * e + k] != EK_INTERIOR) {
+        for (int k = 0; k < nv; ++k)
+            if (o->ekind[nv * e + k] != EK_INTERIOR) {
                 o->be[nb].elem = e;
                 o->be[nb].k = k;
-                o->be[nb].kind = o->ekind[3 * e + k];
+                o->be[nb].kind = o->ekind[nv * e + k];
                 nb++;
             }
     /* per node: boundary edges (with periodic image) within rchk */
@@ -1029,8 +1230,8 @@ static int prepare(orc_t *o)
         o->bnear_ptr[a] = cnt;
         double px = o->X[2 * a], py = o->X[2 * a + 1];
         for (int b = 0; b < o->nbe; ++b) {
-            const double *v = &o->ev[12 * o->be[b].elem];
-            int k = o->be[b].k, k1 = (k + 1) % 3;
+            const double *v = &o->ev[EVS * o->be[b].elem];
+            int k = o->be[b].k, k1 = (k + 1) % nv;
             for (int sy = -1; sy <= 1; ++sy)
                 for (int sx = -1; sx <= 1; ++sx) {
                     if ((sx && o->Lx <= 0) || (sy && o->Ly <= 0)) continue;
@@ -1061,12 +1262,12 @@ static int prepare(orc_t *o)
     o->probe_xi = xcalloc((size_t)2 * nn, sizeof(double));
     for (int b = 0; b < o->nbe; ++b) {
         if (o->be[b].kind != EK_WALL) continue;
-        int e = o->be[b].elem, k = o->be[b].k, k1 = (k + 1) % 3;
-        const double *v = &o->ev[12 * e];
+        int e = o->be[b].elem, k = o->be[b].k, k1 = (k + 1) % nv;
+        const double *v = &o->ev[EVS * e];
         double tx = v[2 * k1] - v[2 * k], ty = v[2 * k1 + 1] - v[2 * k + 1];
         double L = sqrt(tx * tx + ty * ty);
         double nx = -ty / L, ny = tx / L; /* left of v_k -> v_k+1: into the element */
-        int nodes[3] = {o->conn[6 * e + k], o->conn[6 * e + 3 + k], o->conn[6 * e + k1]};
+        int nodes[3] = {o->conn[nne * e + k], o->conn[nne * e + nv + k], o->conn[nne * e + k1]};
         for (int j = 0; j < 3; ++j) {
             o->is_wall[nodes[j]] = 1;
             o->wall_n[2 * nodes[j]] += nx;
@@ -1086,13 +1287,8 @@ static int prepare(orc_t *o)
         double sx, sy;
         int e = locate_point(o, Bx, By, &sx, &sy);
         if (e < 0) return ST_MESH;
-        const double *v = &o->ev[12 * e];
-        double x0 = v[0] + sx, y0 = v[1] + sy;
-        double xxi = v[2] - v[0], xeta = v[4] - v[0], yxi = v[3] - v[1], yeta = v[5] - v[1];
-        double detJ = xxi * yeta - yxi * xeta;
         o->probe_e[a] = e;
-        o->probe_xi[2 * a] = (yeta * (Bx - x0) - xeta * (By - y0)) / detJ;
-        o->probe_xi[2 * a + 1] = (-yxi * (Bx - x0) + xxi * (By - y0)) / detJ;
+        if (elem_local(o, e, sx, sy, Bx, By, &o->probe_xi[2 * a], &o->probe_xi[2 * a + 1])) return ST_MESH;
     }
     /* element of each node's wall-condition gradients (reading R8): the
        incident element of larger area, then lower id, among those with a
@@ -1100,11 +1296,11 @@ static int prepare(orc_t *o)
     o->bcel = xcalloc((size_t)nn, sizeof(int));
     for (int a = 0; a < nn; ++a) o->bcel[a] = -1;
     for (int e = 0; e < o->ne; ++e) {
-        int touches = o->is_wall[o->conn[6 * e]] || o->is_wall[o->conn[6 * e + 1]] ||
-                      o->is_wall[o->conn[6 * e + 2]];
+        int touches = 0;
+        for (int k = 0; k < nv; ++k) touches |= o->is_wall[o->conn[nne * e + k]];
         if (!touches) continue;
-        for (int l = 0; l < 6; ++l) {
-            int a = o->conn[6 * e + l], b = o->bcel[a];
+        for (int l = 0; l < nne; ++l) {
+            int a = o->conn[nne * e + l], b = o->bcel[a];
             if (b < 0 || o->area2[e] > o->area2[b] || (o->area2[e] == o->area2[b] && e < b)) o->bcel[a] = e;
         }
     }
@@ -1116,25 +1312,30 @@ static int prepare(orc_t *o)
 /* ---------------------------------------------------------------------
  * Creation, state access
  * ------------------------------------------------------------------- */
-void *orc_create(int nn, const double *X, int ne, const int *conn, const uint8_t *ekind,
+/* etype 0: 6-node triangles (conn [6 ne], ekind [3 ne]); 1: the paper's
+   9-node quadrilaterals (conn [9 ne], ekind [4 ne]). */
+void *orc_create(int nn, const double *X, int ne, const int *conn, const uint8_t *ekind, int etype,
                  double Lx, double Ly, int mkind, const double *mp, const double *kin,
                  int *status)
 {
     orc_t *o = xcalloc(1, sizeof(orc_t));
     o->nn = nn;
     o->ne = ne;
+    o->etype = etype == 1 ? 1 : 0;
+    o->nv = o->etype ? 4 : 3;
+    o->nne = o->etype ? 9 : 6;
     o->X = xcalloc((size_t)2 * nn, sizeof(double));
     memcpy(o->X, X, (size_t)2 * nn * sizeof(double));
-    o->conn = xcalloc((size_t)6 * ne, sizeof(int));
-    memcpy(o->conn, conn, (size_t)6 * ne * sizeof(int));
-    o->ekind = xcalloc((size_t)3 * ne, 1);
-    memcpy(o->ekind, ekind, (size_t)3 * ne);
+    o->conn = xcalloc((size_t)o->nne * ne, sizeof(int));
+    memcpy(o->conn, conn, (size_t)o->nne * ne * sizeof(int));
+    o->ekind = xcalloc((size_t)o->nv * ne, 1);
+    memcpy(o->ekind, ekind, (size_t)o->nv * ne);
     o->Lx = Lx;
     o->Ly = Ly;
     o->mkind = mkind;
     memcpy(o->mp, mp, 16 * sizeof(double));
     kin_from(kin, &o->K);
-    for (int e = 0; e < 6 * ne; ++e)
+    for (int e = 0; e < o->nne * ne; ++e)
         if (conn[e] < 0 || conn[e] >= nn) {
             *status = ST_MESH;
             return o;
@@ -1315,8 +1516,8 @@ static int choose_element(const orc_t *o, int a, double chx, double chy, double 
     double dx = px - ax, dy = py - ay, L2 = dx * dx + dy * dy;
     for (int k = o->bnear_ptr[a]; k < o->bnear_ptr[a + 1]; ++k) {
         const bedge_t *b = &o->be[o->bnear_e[k]];
-        const double *v = &o->ev[12 * b->elem];
-        int k0 = b->k, k1 = (b->k + 1) % 3;
+        const double *v = &o->ev[EVS * b->elem];
+        int k0 = b->k, k1 = (b->k + 1) % o->nv;
         double ox = o->bnear_sx[k] * o->Lx, oy = o->bnear_sy[k] * o->Ly;
         double ux = v[2 * k0] + ox, uy = v[2 * k0 + 1] + oy;
         double wx = v[2 * k1] + ox, wy = v[2 * k1 + 1] + oy;
@@ -1382,19 +1583,24 @@ static int choose_element(const orc_t *o, int a, double chx, double chy, double 
 }
 
 /* FE derivative d/dX of nodal field K at node a in its owner element
-   (Eq. FE_Derivative with J^{-1} of the straight-sided triangle). */
+   (Eq. FE_Derivative with J^{-1} of the element at the node: constant on
+   the straight-sided triangle, that of the bilinear map at the node's
+   local position on the quadrilateral). */
 static void fe_grad_X(const orc_t *o, int a, const double *K, double *KX, double *KY)
 {
-    int e = o->owner[a], l = o->owner_loc[a];
-    const double *v = &o->ev[12 * e];
-    double x_xi = v[2] - v[0], x_eta = v[4] - v[0];
-    double y_xi = v[3] - v[1], y_eta = v[5] - v[1];
+    int e = o->owner[a], l = o->owner_loc[a], nne = o->nne;
+    double xl, yl, J[4];
+    node_local(o, l, &xl, &yl);
+    elem_jacobian(o, e, xl, yl, J);
+    double x_xi = J[0], x_eta = J[1];
+    double y_xi = J[2], y_eta = J[3];
     double detJ = x_xi * y_eta - y_xi * x_eta;
-    double Nxi[6], Neta[6];
-    shape_dxi(LOCAL_XI[l][0], LOCAL_XI[l][1], Nxi, Neta);
+    double Nxi[9], Neta[9];
+    if (o->etype == 1) shape_dxi_q2(xl, yl, Nxi, Neta);
+    else shape_dxi(xl, yl, Nxi, Neta);
     double sxi = 0, seta = 0;
-    for (int s = 0; s < 6; ++s) {
-        double Ks = K[o->conn[6 * e + s]];
+    for (int s = 0; s < nne; ++s) {
+        double Ks = K[o->conn[nne * e + s]];
         sxi += Ks * Nxi[s];
         seta += Ks * Neta[s];
     }
@@ -1404,19 +1610,36 @@ static void fe_grad_X(const orc_t *o, int a, const double *K, double *KX, double
 }
 
 /* First-order FE derivative d/dX of a nodal field at node a: the gradient
-   of the linear interpolant through the three vertices of the node's
-   wall-condition element (R8).  Used for the non-equilibrium part of the
-   wall condition, where a first-order gradient suffices (Sec. IV.A, last
-   paragraph). */
+   of the interpolant through the vertices alone of the node's
+   wall-condition element (R8) -- linear on the triangle, bilinear on the
+   quadrilateral, taken at the node.  Used for the non-equilibrium part of
+   the wall condition, where a first-order gradient suffices (Sec. IV.A,
+   last paragraph). */
 static void fe_grad_X_linear(const orc_t *o, int a, const double *K, double *KX, double *KY)
 {
-    int e = o->bcel[a];
-    const double *v = &o->ev[12 * e];
+    int e = o->bcel[a], nne = o->nne;
+    if (o->etype == 1) {
+        double xl, yl, J[4];
+        node_local(o, local_index(o, e, a), &xl, &yl);
+        elem_jacobian(o, e, xl, yl, J);
+        double nxi[4] = {-0.25 * (1.0 - yl), 0.25 * (1.0 - yl), 0.25 * (1.0 + yl), -0.25 * (1.0 + yl)};
+        double neta[4] = {-0.25 * (1.0 - xl), -0.25 * (1.0 + xl), 0.25 * (1.0 + xl), 0.25 * (1.0 - xl)};
+        double sxi = 0, seta = 0;
+        for (int k = 0; k < 4; ++k) {
+            sxi += nxi[k] * K[o->conn[nne * e + k]];
+            seta += neta[k] * K[o->conn[nne * e + k]];
+        }
+        double detJ = J[0] * J[3] - J[2] * J[1];
+        *KX = (J[3] * sxi - J[2] * seta) / detJ;
+        *KY = (-J[1] * sxi + J[0] * seta) / detJ;
+        return;
+    }
+    const double *v = &o->ev[EVS * e];
     double x_xi = v[2] - v[0], x_eta = v[4] - v[0];
     double y_xi = v[3] - v[1], y_eta = v[5] - v[1];
     double detJ = x_xi * y_eta - y_xi * x_eta;
-    double sxi = K[o->conn[6 * e + 1]] - K[o->conn[6 * e]];
-    double seta = K[o->conn[6 * e + 2]] - K[o->conn[6 * e]];
+    double sxi = K[o->conn[nne * e + 1]] - K[o->conn[nne * e]];
+    double seta = K[o->conn[nne * e + 2]] - K[o->conn[nne * e]];
     *KX = (y_eta * sxi - y_xi * seta) / detJ;
     *KY = (-x_eta * sxi + x_xi * seta) / detJ;
 }
@@ -1432,17 +1655,11 @@ static void phys_grad(const double *gi, double KX, double KY, double *Kx, double
 static double interp_field(const orc_t *o, int e, double sx, double sy, double px, double py,
                            const double *K)
 {
-    const double *v = &o->ev[12 * e];
-    double x0 = v[0] + sx, y0 = v[1] + sy;
-    double x_xi = v[2] - v[0], x_eta = v[4] - v[0];
-    double y_xi = v[3] - v[1], y_eta = v[5] - v[1];
-    double detJ = x_xi * y_eta - y_xi * x_eta;
-    double xi = (y_eta * (px - x0) - x_eta * (py - y0)) / detJ;
-    double eta = (-y_xi * (px - x0) + x_xi * (py - y0)) / detJ;
-    double N[6];
-    orc_shape(xi, eta, N);
+    double xi, eta, N[9];
+    elem_local(o, e, sx, sy, px, py, &xi, &eta);
+    elem_shape(o, xi, eta, N);
     double s = 0;
-    for (int k = 0; k < 6; ++k) s += N[k] * K[o->conn[6 * e + k]];
+    for (int k = 0; k < o->nne; ++k) s += N[k] * K[o->conn[o->nne * e + k]];
     return s;
 }
 
@@ -1485,18 +1702,15 @@ static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd, con
             continue;
         }
         if (e >= 0) {
-            const double *v = &o->ev[12 * e];
-            double x0 = v[0] + sx, y0 = v[1] + sy;
-            double x_xi = v[2] - v[0], x_eta = v[4] - v[0];
-            double y_xi = v[3] - v[1], y_eta = v[5] - v[1];
-            double detJ = x_xi * y_eta - y_xi * x_eta;
-            double xi = (y_eta * (px - x0) - x_eta * (py - y0)) / detJ;
-            double eta = (-y_xi * (px - x0) + x_xi * (py - y0)) / detJ;
-            double N[6];
-            orc_shape(xi, eta, N);
+            /* local coordinates of the departure point (closed form on the
+               triangle, Eq. NonLinear_Eq on the quadrilateral), then the
+               interpolation of Eq. Propagation */
+            double xi, eta, N[9];
+            if (elem_local(o, e, sx, sy, px, py, &xi, &eta)) return ST_LOCATE;
+            elem_shape(o, xi, eta, N);
             double sf = 0, sg = 0;
-            for (int k = 0; k < 6; ++k) {
-                int b = o->conn[6 * e + k];
+            for (int k = 0; k < o->nne; ++k) {
+                int b = o->conn[o->nne * e + k];
                 sf += N[k] * o->f[(size_t)i * nn + b];
                 sg += N[k] * o->g[(size_t)i * nn + b];
             }
@@ -1513,11 +1727,11 @@ static int stream_node(orc_t *o, int a, const mscal_t *S, const mscal_t *Sd, con
             if (!have_bc) {
                 if (o->is_wall[a]) {
                     int pe = o->probe_e[a];
-                    double N[6];
-                    orc_shape(o->probe_xi[2 * a], o->probe_xi[2 * a + 1], N);
+                    double N[9];
+                    elem_shape(o, o->probe_xi[2 * a], o->probe_xi[2 * a + 1], N);
                     double rB = 0, TB = 0, uB = 0, vB = 0;
-                    for (int k = 0; k < 6; ++k) {
-                        int b = o->conn[6 * pe + k];
+                    for (int k = 0; k < o->nne; ++k) {
+                        int b = o->conn[o->nne * pe + k];
                         rB += N[k] * o->rho[b];
                         TB += N[k] * o->T[b];
                         uB += N[k] * o->ux[b];
@@ -1852,8 +2066,8 @@ int orc_forces(void *h, double *out)
     }
     for (int b = 0; b < o->nbe; ++b) {
         if (o->be[b].kind != EK_WALL) continue;
-        int e = o->be[b].elem, k = o->be[b].k, k1 = (k + 1) % 3;
-        int nodes[3] = {o->conn[6 * e + k], o->conn[6 * e + 3 + k], o->conn[6 * e + k1]};
+        int e = o->be[b].elem, k = o->be[b].k, k1 = (k + 1) % o->nv;
+        int nodes[3] = {o->conn[o->nne * e + k], o->conn[o->nne * e + o->nv + k], o->conn[o->nne * e + k1]};
         double xa, ya, xb, yb;
         motion_position(o, nodes[0], &S, &xa, &ya);
         motion_position(o, nodes[2], &S, &xb, &yb);
@@ -1894,6 +2108,14 @@ int orc_forces(void *h, double *out)
 }
 
 int orc_status(void *h) { return ((orc_t *)h)->status; }
+
+/* Local coordinates of computational point p in element e (no periodic
+   shift): out = {xi, eta}; returns 0 or ST_LOCATE. */
+int orc_local(void *h, int e, double px, double py, double *out)
+{
+    orc_t *o = h;
+    return elem_local(o, e, 0.0, 0.0, px, py, &out[0], &out[1]);
+}
 
 /* Threads of the node loops of a step: n > 0 sets the count (OpenMP),
    n <= 0 leaves it; returns the count in use (1 without OpenMP). */

@@ -13,15 +13,19 @@ Conventions shared by every consumer of these arrays
   coordinates are quantised to multiples of 2**-20 so that periodic
   unwrapping (adding the period) and edge midpoints are exact in FP64.
 * ``conn``   int32 (n_elems, 6): ``v0 v1 v2 m01 m12 m20`` -- the three
-  vertices counter-clockwise, then the midside node of edge k (v_k, v_k+1).
-* ``edge_kind`` uint8 (n_elems, 3): kind of edge k: 0 interior or periodic,
-  1 wall, 2 far field.
+  vertices counter-clockwise, then the midside node of edge k (v_k, v_k+1);
+  for the 9-node quadrilaterals (``elem_type`` 1) int32 (n_elems, 9):
+  ``v0 v1 v2 v3 m01 m12 m23 m30 c`` -- four vertices counter-clockwise,
+  the midside nodes, then the centre (the mean of the four vertices).
+* ``edge_kind`` uint8 (n_elems, 3 or 4): kind of edge k: 0 interior or
+  periodic, 1 wall, 2 far field.
 * ``period`` (Lx, Ly): > 0 for a periodic direction, 0 otherwise.  Periodic
   coordinates lie in [0, L).
 
 The second-order finite-element mesh of the paper (Sec. III, Fig. 1) is a
-9-node quadrilateral mesh; the workloads here use the 6-node triangle
-variant (straight-sided P2) throughout.
+9-node quadrilateral mesh; every generator below makes either element: the
+6-node triangles split each cell along a diagonal, the 9-node
+quadrilaterals keep the cell.
 """
 from __future__ import annotations
 
@@ -44,6 +48,9 @@ EDGE_INTERIOR = 0
 EDGE_WALL = 1
 EDGE_FARFIELD = 2
 
+ELEM_P2TRI = 0
+ELEM_Q2QUAD = 1
+
 
 def quantize(x):
     return np.round(np.asarray(x, dtype=np.float64) / QUANTUM) * QUANTUM
@@ -57,6 +64,7 @@ class Mesh:
     period: tuple
     name: str = ""
     meta: dict = dataclasses.field(default_factory=dict)
+    elem_type: int = ELEM_P2TRI
 
     @property
     def n_nodes(self):
@@ -75,7 +83,7 @@ class Mesh:
         pe = rng.permutation(self.n_elems)
         conn = inv[self.conn[pe]].astype(np.int32)
         return Mesh(self.X[pn].copy(), conn, self.edge_kind[pe].copy(),
-                    self.period, self.name + f"/perm{seed}", dict(self.meta))
+                    self.period, self.name + f"/perm{seed}", dict(self.meta), self.elem_type)
 
 
 @dataclasses.dataclass
@@ -148,6 +156,60 @@ def p2_from_tris(vx, tris, period=(0.0, 0.0), tri_edge_kind=None):
     return X, conn, np.asarray(tri_edge_kind, dtype=np.uint8)
 
 
+def q2_from_quads(vx, quads, period=(0.0, 0.0), quad_edge_kind=None):
+    """Add one midside node per unique edge and a centre node per cell to a
+    counter-clockwise vertex quadrangulation (the paper's 9-node element).
+    The centre is the mean of the four vertices, the value of the bilinear
+    map at (0, 0), computed from vertices unwrapped about the first."""
+    vx = np.asarray(vx, dtype=np.float64)
+    quads = np.asarray(quads, dtype=np.int64)
+    nq = quads.shape[0]
+    nv = vx.shape[0]
+    a = quads[:, [0, 1, 2, 3]].reshape(-1)
+    b = quads[:, [1, 2, 3, 0]].reshape(-1)
+    key = np.minimum(a, b) * nv + np.maximum(a, b)
+    uniq, inv = np.unique(key, return_inverse=True)
+    ea = uniq // nv
+    eb = uniq % nv
+    d = vx[eb] - vx[ea]
+    d[:, 0] = _unwrap(d[:, 0], period[0])
+    d[:, 1] = _unwrap(d[:, 1], period[1])
+    mid = vx[ea] + 0.5 * d
+    v0 = vx[quads[:, 0]]
+    rel = [vx[quads[:, k]] - v0 for k in range(4)]
+    for r in rel:
+        r[:, 0] = _unwrap(r[:, 0], period[0])
+        r[:, 1] = _unwrap(r[:, 1], period[1])
+    u = [v0 + r for r in rel]
+    cen = 0.25 * (((u[0] + u[1]) + u[2]) + u[3])
+    for ax in range(2):
+        if period[ax] > 0:
+            mid[:, ax] = np.mod(mid[:, ax], period[ax])
+            cen[:, ax] = np.mod(cen[:, ax], period[ax])
+    X = np.concatenate([vx, mid, cen], axis=0)
+    conn = np.empty((nq, 9), dtype=np.int32)
+    conn[:, :4] = quads
+    conn[:, 4:8] = (nv + inv).reshape(nq, 4)
+    conn[:, 8] = nv + uniq.size + np.arange(nq)
+    if quad_edge_kind is None:
+        quad_edge_kind = np.zeros((nq, 4), dtype=np.uint8)
+    return X, conn, np.asarray(quad_edge_kind, dtype=np.uint8)
+
+
+def _check_convex(vx, quads, period):
+    """Every corner of every quadrilateral turns left (strictly convex)."""
+    p = [vx[quads[:, k]] for k in range(4)]
+    for k in range(4):
+        d1 = p[(k + 1) % 4] - p[k]
+        d2 = p[(k + 2) % 4] - p[(k + 1) % 4]
+        for d in (d1, d2):
+            for ax in range(2):
+                d[:, ax] = _unwrap(d[:, ax], period[ax])
+        cr = d1[:, 0] * d2[:, 1] - d1[:, 1] * d2[:, 0]
+        if not np.all(cr > 0):
+            raise ValueError(f"mesh generator produced {int(np.sum(cr <= 0))} non-convex quadrilaterals")
+
+
 def _check_ccw(vx, tris, period):
     p0 = vx[tris[:, 0]]
     d1 = vx[tris[:, 1]] - p0
@@ -165,10 +227,11 @@ def _check_ccw(vx, tris, period):
 # Periodic boxes
 # --------------------------------------------------------------------------
 
-def periodic_box(n: int, L: float, jitter: float = 0.2, seed: int = 0, name="box"):
+def periodic_box(n: int, L: float, jitter: float = 0.2, seed: int = 0, name="box", elem="p2"):
     """n x n vertices on the periodic square [0, L)^2, jittered by
-    U(-jitter*h, jitter*h) per coordinate (h = L/n), each quad cell split
-    along its SW-NE diagonal, then P2 midside nodes added."""
+    U(-jitter*h, jitter*h) per coordinate (h = L/n); each quad cell split
+    along its SW-NE diagonal with P2 midside nodes added (elem "p2"), or
+    kept as a 9-node quadrilateral (elem "q2")."""
     if n < 3:
         raise ValueError("need at least 3 vertices per side")
     h = L / n
@@ -184,18 +247,25 @@ def periodic_box(n: int, L: float, jitter: float = 0.2, seed: int = 0, name="box
     ii = ii.reshape(-1)
     jj = jj.reshape(-1)
     v00, v10, v11, v01 = vid(ii, jj), vid(ii + 1, jj), vid(ii + 1, jj + 1), vid(ii, jj + 1)
-    tris = np.concatenate([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], 0)
     period = (float(L), float(L))
+    meta = dict(n=n, L=L, h=h, jitter=jitter, seed=seed)
+    if elem == "q2":
+        quads = np.stack([v00, v10, v11, v01], 1)
+        _check_convex(vx, quads, period)
+        X, conn, ek = q2_from_quads(vx, quads, period)
+        return Mesh(X, conn, ek, period, name=f"{name}q{n}x{n}_L{L:g}_j{jitter:g}_s{seed}", meta=meta,
+                    elem_type=ELEM_Q2QUAD)
+    tris = np.concatenate([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], 0)
     _check_ccw(vx, tris, period)
     X, conn, ek = p2_from_tris(vx, tris, period)
-    return Mesh(X, conn, ek, period, name=f"{name}{n}x{n}_L{L:g}_j{jitter:g}_s{seed}",
-                meta=dict(n=n, L=L, h=h, jitter=jitter, seed=seed))
+    return Mesh(X, conn, ek, period, name=f"{name}{n}x{n}_L{L:g}_j{jitter:g}_s{seed}", meta=meta)
 
 
-def lattice_box(n: int):
-    """Unjittered periodic box with vertex spacing 2: every P2 node sits on
-    the integer lattice [0, 2n)^2, and every lattice point is a node."""
-    return periodic_box(n, 2.0 * n, jitter=0.0, seed=0, name="lattice")
+def lattice_box(n: int, elem="p2"):
+    """Unjittered periodic box with vertex spacing 2: every P2 (or Q2) node
+    sits on the integer lattice [0, 2n)^2, and every lattice point is a
+    node."""
+    return periodic_box(n, 2.0 * n, jitter=0.0, seed=0, name="lattice", elem=elem)
 
 
 # --------------------------------------------------------------------------
@@ -228,7 +298,7 @@ def _growth_ratio(first, total, n):
 
 
 def naca_omesh(ni: int, nj: int, chord: float = 200.0, thickness: float = 0.12,
-               R: float = 4000.0, first: float = 0.2, name="naca"):
+               R: float = 4000.0, first: float = 0.2, name="naca", elem="p2"):
     """O-mesh of P2 triangles around a NACA 00xx section (leading edge at the
     origin, chord along +x), outer far-field circle of radius R about
     mid-chord.  ni points around the section (even; spacing half
@@ -275,6 +345,16 @@ def naca_omesh(ni: int, nj: int, chord: float = 200.0, thickness: float = 0.12,
     ii = ii.reshape(-1)
     jr = jr.reshape(-1)
     a, b, c_, e = vid(ii, jr), vid(ii + 1, jr), vid(ii + 1, jr + 1), vid(ii, jr + 1)
+    meta = dict(ni=ni, nj=nj, chord=chord, thickness=thickness, R=R, first=first, growth=q)
+    if elem == "q2":
+        quads = np.stack([a, b, c_, e], 1)
+        kind = np.zeros((quads.shape[0], 4), dtype=np.uint8)
+        kind[jr == 0, 0] = EDGE_WALL                 # edge a-b on ring 0
+        kind[jr == nj - 2, 2] = EDGE_FARFIELD        # edge c-e on the last ring
+        _check_convex(vx, quads, (0.0, 0.0))
+        X, conn, ek = q2_from_quads(vx, quads, (0.0, 0.0), kind)
+        return Mesh(X, conn, ek, (0.0, 0.0), name=f"{name}{int(round(thickness * 100)):02d}_q{ni}x{nj}",
+                    meta=meta, elem_type=ELEM_Q2QUAD)
     tris = np.concatenate([np.stack([a, b, c_], 1), np.stack([a, c_, e], 1)], 0)
     nq = ii.size
     kind = np.zeros((2 * nq, 3), dtype=np.uint8)
@@ -289,7 +369,7 @@ def naca_omesh(ni: int, nj: int, chord: float = 200.0, thickness: float = 0.12,
 
 
 def wall_channel(nx: int = 12, hx: float = 8.0, first: float = 0.7, growth: float = 1.17,
-                 ny: int = 14, name="channel"):
+                 ny: int = 14, name="channel", elem="p2"):
     """Flat channel periodic in x: wall edges at y = 0 and at the top ring,
     nx cells of length hx along the wall, ny layers whose thickness starts
     at `first` and grows by `growth`, each cell split along its SW-NE
@@ -303,6 +383,17 @@ def wall_channel(nx: int = 12, hx: float = 8.0, first: float = 0.7, growth: floa
     ys = np.array(ys)
     V = quantize(np.array([[i * hx, y] for y in ys for i in range(nx)]))
     vid = lambda i, j: (i % nx) + nx * j
+    if elem == "q2":
+        quads, qk = [], []
+        for j in range(len(ys) - 1):
+            for i in range(nx):
+                quads.append((vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)))
+                qk.append((EDGE_WALL if j == 0 else 0, 0, EDGE_WALL if j == len(ys) - 2 else 0, 0))
+        quads = np.array(quads)
+        _check_convex(V, quads, (nx * hx, 0.0))
+        X, conn, ek = q2_from_quads(V, quads, (nx * hx, 0.0), np.array(qk, dtype=np.uint8))
+        return Mesh(X, conn, ek, (nx * hx, 0.0), name=f"{name}_q{nx}x{ny}",
+                    meta=dict(hx=hx, first=first, growth=growth, height=float(ys[-1])), elem_type=ELEM_Q2QUAD)
     tris, kinds = [], []
     for j in range(len(ys) - 1):
         for i in range(nx):
@@ -358,11 +449,11 @@ class Case:
 
 
 def uniform_flow_case(n=48, L=96.0, jitter=0.2, seed=0, amp_frac=0.05, period_steps=100.0,
-                      steps=200, Ma=0.3, angle_deg=15.0, T_inf=0.2, omega_inf=1.6):
+                      steps=200, Ma=0.3, angle_deg=15.0, T_inf=0.2, omega_inf=1.6, elem="p2"):
     """Uniform-flow preservation on a deforming periodic box: x += A sin(2 pi Y/L)
     sin(2 pi t/T), y += A sin(2 pi X/L) sin(2 pi t/T) with A = amp_frac*L.
     mu is chosen so that the free-stream relaxation rate is omega_inf."""
-    mesh = periodic_box(n, L, jitter, seed)
+    mesh = periodic_box(n, L, jitter, seed, elem=elem)
     motion = Motion.make(MOTION_SINE, amp_frac * L, L, period_steps, 0.0)
     mu = (1.0 / omega_inf - 0.5) * 1.0 * T_inf
     flow = flow_params(Ma, T_inf=T_inf, mu=mu, angle_deg=angle_deg, chord=L)
@@ -370,11 +461,11 @@ def uniform_flow_case(n=48, L=96.0, jitter=0.2, seed=0, amp_frac=0.05, period_st
 
 
 def plunge_case(ni=320, nj=118, Ma=0.2, T_inf=0.3, Re=1e4, k=1.0, h_frac=0.1, chord=1000.0,
-                thickness=0.12, R_frac=20.0, first_frac=1e-3, periods=5.0):
+                thickness=0.12, R_frac=20.0, first_frac=1e-3, periods=5.0, elem="p2"):
     """NACA00xx plunging y = Y - h sin(omega t), omega = 2 k U / c.  The
     chord is 1000 lattice units so that the first cell layer (1e-3 c) is one
     lattice unit."""
-    mesh = naca_omesh(ni, nj, chord, thickness, R_frac * chord, first_frac * chord)
+    mesh = naca_omesh(ni, nj, chord, thickness, R_frac * chord, first_frac * chord, elem=elem)
     flow = flow_params(Ma, T_inf=T_inf, Re=Re, chord=chord)
     U = flow.u_inf[0]
     om = 2.0 * k * U / chord
@@ -385,11 +476,11 @@ def plunge_case(ni=320, nj=118, Ma=0.2, T_inf=0.3, Re=1e4, k=1.0, h_frac=0.1, ch
 
 def pitch_case(ni=640, nj=235, Ma=0.75, T_inf=0.3, Re=1e4, k=0.08, alpha0_deg=0.1,
                amp_deg=2.5, chord=1000.0, thickness=0.12, R_frac=20.0, first_frac=1e-3,
-               blended=True, periods=3.0, plunge_frac=0.0):
+               blended=True, periods=3.0, plunge_frac=0.0, elem="p2"):
     """NACA00xx pitching about c/4 with alpha(t) = alpha0 + A sin(omega t)
     (nose-up positive, i.e. a clockwise rotation theta = -alpha), rigid or
     blended to zero between 2c and 10c from the pivot."""
-    mesh = naca_omesh(ni, nj, chord, thickness, R_frac * chord, first_frac * chord)
+    mesh = naca_omesh(ni, nj, chord, thickness, R_frac * chord, first_frac * chord, elem=elem)
     flow = flow_params(Ma, T_inf=T_inf, Re=Re, chord=chord)
     U = flow.u_inf[0]
     om = 2.0 * k * U / chord

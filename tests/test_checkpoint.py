@@ -11,9 +11,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _case():
-    mesh = I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0)
-    motion = I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.02, -0.04, 0.004, 250.0, 0.0, 30.0, 0.004)
-    flow = I.flow_params(0.3, T_inf=0.3, Re=1e4, chord=1000.0)
+    mesh = I.naca_omesh(64, 20, chord=200.0, thickness=0.15, R=4000.0, first=1.0)
+    motion = I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.05, 0.003, 50.0, 0.0, 20.0, 0.003)
+    flow = I.flow_params(0.15, T_inf=0.3, Re=800.0, chord=200.0, angle_deg=2.0)
     return mesh, motion, flow
 
 
@@ -58,9 +58,10 @@ def test_foreign_or_damaged_checkpoints_are_refused(tmp_path):
     f0, g0 = b.get_pops()
     # another precision, another mesh, another free stream: ALELB_ERR_STATE
     others = [alelb.Solver(m, flow, alelb.PREC_FP64),
-              alelb.Solver(alelb.Mesh(I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0, thickness=0.1),
+              alelb.Solver(alelb.Mesh(I.naca_omesh(64, 20, chord=200.0, thickness=0.12, R=4000.0, first=1.0),
                                       motion), flow, alelb.PREC_FP32_DEV),
-              alelb.Solver(m, I.flow_params(0.4, T_inf=0.3, Re=1e4, chord=1000.0), alelb.PREC_FP32_DEV)]
+              alelb.Solver(m, I.flow_params(0.2, T_inf=0.3, Re=800.0, chord=200.0, angle_deg=2.0),
+                           alelb.PREC_FP32_DEV)]
     for s in others:
         with pytest.raises(alelb.AlelbError) as e:
             s.load(path)
@@ -77,7 +78,7 @@ def test_foreign_or_damaged_checkpoints_are_refused(tmp_path):
     assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
     assert b.time() == (3.0, 3)
     # a good load after the refusals still works, and a viscosity change is allowed
-    c = alelb.Solver(m, I.flow_params(0.3, T_inf=0.3, Re=2e4, chord=1000.0), alelb.PREC_FP32_DEV)
+    c = alelb.Solver(m, I.flow_params(0.15, T_inf=0.3, Re=1600.0, chord=200.0, angle_deg=2.0), alelb.PREC_FP32_DEV)
     c.load(path)
     assert c.time() == (5.0, 5)
     c.lb_step(2)
