@@ -45,16 +45,23 @@ def _eq_state(rho, ux, uy, T):
     return f, g
 
 
+def _nv(mesh):
+    return 4 if mesh.elem_type == I.ELEM_Q2QUAD else 3
+
+
 def _wall_edges(mesh):
-    """(element, a, m, b, opposite vertex) of every wall edge: its end nodes a
-    and b, its midside node m, and the element's third vertex."""
-    out = []
+    """(element, a, m, b, other vertex) of every wall edge: its end nodes a
+    and b, its midside node m, and a vertex of the element off the edge."""
+    out, nv = [], _nv(mesh)
     for e in range(mesh.n_elems):
-        for k in range(3):
+        for k in range(nv):
             if mesh.edge_kind[e, k] == I.EDGE_WALL:
                 c = mesh.conn[e]
-                out.append((e, c[k], c[3 + k], c[(k + 1) % 3], c[(k + 2) % 3]))
+                out.append((e, c[k], c[nv + k], c[(k + 1) % nv], c[(k + 2) % nv]))
     return out
+
+
+ELEMS = ["p2", "q2"]
 
 
 def _rot(th):
@@ -85,15 +92,16 @@ def _body_integrals(mesh, x):
     return A, Mx, My
 
 
+@pytest.mark.parametrize("elem", ELEMS)
 @pytest.mark.parametrize("moving", [False, True], ids=["static", "pitched"])
-def test_wall_forces_of_quadratic_fields_match_closed_forms(moving):
+def test_wall_forces_of_quadratic_fields_match_closed_forms(moving, elem):
     """u_x = q1 y^2 + q2 x^2 + (linear), u_y = r1 y^2 + r2 x y + (linear),
     rho = 1 + a.x, T = T0 + b.x on a closed airfoil:
       F_visc = mu A (2 q1 + q2 (4 - 2/Cv) + r2 (1 - 1/Cv),  r1 (4 - 2/Cv)),
       F_pres = -int_body grad(rho T) dA.
     A factor 2 or a sign in S, the 1/Cv term, or a wrong Simpson weight
     changes these."""
-    mesh = I.naca_omesh(40, 8, chord=20.0, R=200.0, first=1.0)
+    mesh = I.naca_omesh(40, 8, chord=20.0, R=200.0, first=1.0, elem=elem)
     if moving:
         mot = I.Motion.make(I.MOTION_PITCH, 0.2, 0.3, 0.05, 5.0, 0.0)
         t = 9.0
@@ -145,10 +153,38 @@ def _wall_normals(mesh):
     return {v: n / np.linalg.norm(n) for v, n in acc.items()}
 
 
-def _p2_interp_brute(mesh, p, K):
-    """P2 interpolation of nodal field K at point p in an element that
-    contains it, found by testing every element (non-periodic mesh)."""
+def _q2_local(v, p):
+    """(xi, eta) of p under the bilinear map of the corners v, by a damped
+    least-squares iteration (the test's own solver, not the oracle's)."""
+    x = np.zeros(2)
+    for _ in range(60):
+        n = 0.25 * np.array([(1 - x[0]) * (1 - x[1]), (1 + x[0]) * (1 - x[1]), (1 + x[0]) * (1 + x[1]),
+                             (1 - x[0]) * (1 + x[1])])
+        dn = 0.25 * np.array([[-(1 - x[1]), -(1 - x[0])], [1 - x[1], -(1 + x[0])], [1 + x[1], 1 + x[0]],
+                              [-(1 + x[1]), 1 - x[0]]])
+        r = n @ v - p
+        J = v.T @ dn
+        x = x - np.linalg.lstsq(J, r, rcond=None)[0]
+    return x
+
+
+def _interp_brute(mesh, p, K):
+    """Interpolation of nodal field K at point p in an element that contains
+    it, found by testing every element (non-periodic mesh): P2 on
+    triangles, the products of 1-D quadratic Lagrange polynomials on
+    quadrilaterals."""
     for e in range(mesh.n_elems):
+        if mesh.elem_type == I.ELEM_Q2QUAD:
+            v = mesh.X[mesh.conn[e, :4]]
+            if not all((v[(k + 1) % 4, 0] - v[k, 0]) * (p[1] - v[k, 1])
+                       - (v[(k + 1) % 4, 1] - v[k, 1]) * (p[0] - v[k, 0]) >= -1e-12 for k in range(4)):
+                continue
+            xi, eta = _q2_local(v, p)
+            L = lambda s: [0.5 * s * (s - 1), (1 - s) * (1 + s), 0.5 * s * (s + 1)]
+            I9 = [0, 2, 2, 0, 1, 2, 1, 0, 1]
+            J9 = [0, 0, 2, 2, 0, 1, 2, 1, 1]
+            N = [L(xi)[I9[k]] * L(eta)[J9[k]] for k in range(9)]
+            return float(np.dot(N, K[mesh.conn[e]]))
         v = mesh.X[mesh.conn[e, :3]]
         J = np.stack([v[1] - v[0], v[2] - v[0]], 1)
         xi, eta = np.linalg.solve(J, p - v[0])
@@ -160,12 +196,13 @@ def _p2_interp_brute(mesh, p, K):
     raise AssertionError(f"probe point {p} outside the mesh")
 
 
+@pytest.mark.parametrize("elem", ELEMS)
 @pytest.mark.parametrize("field", ["linear", "random"])
-def test_wall_condition_reads_rho_and_T_at_the_probe_point(field):
+def test_wall_condition_reads_rho_and_T_at_the_probe_point(field, elem):
     """A probe at 2 dt, along the wrong normal, or interpolated in an element
     that does not contain B gives other values (the random field is not
     reproduced by any other element's extrapolation)."""
-    mesh = I.naca_omesh(32, 8, chord=20.0, R=200.0, first=1.0)
+    mesh = I.naca_omesh(32, 8, chord=20.0, R=200.0, first=1.0, elem=elem)
     fl = _flow(flags=O.FLAG_BC_EQUILIBRIUM | O.FLAG_COLLIDE_OFF)
     o = O.Oracle(mesh, I.Motion.make(0), fl)
     X, Y = mesh.X[:, 0], mesh.X[:, 1]
@@ -189,8 +226,8 @@ def test_wall_condition_reads_rho_and_T_at_the_probe_point(field):
             rB = 1.0 + 2e-4 * B[0] - 3e-4 * B[1]
             TB = 0.3 + 1e-4 * B[0] + 2e-4 * B[1]
         else:
-            rB = _p2_interp_brute(mesh, B, rho)
-            TB = _p2_interp_brute(mesh, B, T)
+            rB = _interp_brute(mesh, B, rho)
+            TB = _interp_brute(mesh, B, T)
         fe, ge = O.feq(rB, 0.0, 0.0, TB), O.geq(rB, 0.0, 0.0, TB, CV)
         miss = np.nonzero(kind[:, a] == 1)[0]
         assert miss.size > 0
@@ -205,6 +242,10 @@ def test_wall_condition_reads_rho_and_T_at_the_probe_point(field):
 # ---------------------------------------------------------------------------
 
 def _areas(mesh):
+    if mesh.elem_type == I.ELEM_Q2QUAD:  # twice the area: cross product of the diagonals
+        v = mesh.X[mesh.conn[:, :4]]
+        d1, d2 = v[:, 2] - v[:, 0], v[:, 3] - v[:, 1]
+        return d1[:, 0] * d2[:, 1] - d1[:, 1] * d2[:, 0]
     v = mesh.X[mesh.conn[:, :3]]
     d1, d2 = v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]
     return d1[:, 0] * d2[:, 1] - d1[:, 1] * d2[:, 0]
@@ -222,13 +263,21 @@ def _gradient_elements(mesh):
     for node in range(mesh.n_nodes):
         inc = np.nonzero((mesh.conn == node).any(1))[0]
         owner[node] = min(inc, key=lambda e: (-a2[e], e))
-        touch = [e for e in inc if any(v in wall for v in mesh.conn[e, :3])]
+        touch = [e for e in inc if any(v in wall for v in mesh.conn[e, :_nv(mesh)])]
         side[node] = min(touch, key=lambda e: (-a2[e], e)) if touch else owner[node]
     return owner, side, wall
 
 
-def _vertex_gradient(mesh, e, K):
-    """Gradient of the linear interpolant of K through the vertices of e."""
+def _vertex_gradient(mesh, e, K, node):
+    """Gradient at `node` of the interpolant of K through the vertices of e
+    alone: linear on a triangle, bilinear on a quadrilateral."""
+    if mesh.elem_type == I.ELEM_Q2QUAD:
+        v = mesh.X[mesh.conn[e, :4]]
+        xi, eta = _q2_local(v, mesh.X[node])
+        dn = 0.25 * np.array([[-(1 - eta), -(1 - xi)], [1 - eta, -(1 + xi)], [1 + eta, 1 + xi],
+                              [-(1 + eta), 1 - xi]])
+        J = v.T @ dn  # d x / d (xi, eta)
+        return np.linalg.solve(J.T, K[mesh.conn[e, :4]] @ dn)
     v = mesh.X[mesh.conn[e, :3]]
     J = np.stack([v[1] - v[0], v[2] - v[0]], 0)
     dK = K[mesh.conn[e, 1:3]] - K[mesh.conn[e, 0]]
@@ -239,14 +288,15 @@ def _lin(c, x):
     return c[0] + c[1] * x[..., 0] + c[2] * x[..., 1]
 
 
-def test_wall_condition_gradient_is_taken_in_the_wall_side_element():
+@pytest.mark.parametrize("elem", ELEMS)
+def test_wall_condition_gradient_is_taken_in_the_wall_side_element(elem):
     """Off-wall nodes one layer from the wall of a channel whose first layer
     (0.7) is thinner than a lattice unit have missing populations.  Fields
     linear inside the node's wall-side element and different linear fields
     at every other node: the reconstruction must carry the gradient of the
     inside fields.  The owner element (larger, one layer out) mixes the two
     and gives another value."""
-    mesh = I.wall_channel()
+    mesh = I.wall_channel(elem=elem)
     owner, side, wall = _gradient_elements(mesh)
     L = mesh.period[0]
     probe = I.Flow(gamma=1.4, Pr=0.71, mu=0.02, T_inf=0.3, flags=O.FLAG_COLLIDE_OFF)
@@ -258,12 +308,19 @@ def test_wall_condition_gradient_is_taken_in_the_wall_side_element():
     assert len(cand) >= 4
     L1, L2 = (0.05, 3e-3, -4e-3), (0.02, -6e-3, 8e-3)
     M1, M2 = (-0.01, 2e-3, 5e-3), (0.03, 1e-3, -7e-3)
-    du = np.array([L1[1], L1[2], M1[1], M1[2]])
+    # on the (rectangular) quadrilaterals the inside fields also carry a
+    # bilinear term about the cell centre, which the vertex interpolant
+    # reproduces: its gradient must be taken at the node, not the centre
+    q = 1e-3 if elem == "q2" else 0.0
     for a in cand[:: max(1, len(cand) // 4)][:4]:
         inside = np.zeros(mesh.n_nodes, bool)
         inside[mesh.conn[side[a]]] = True
-        ux = np.where(inside, _lin(L1, mesh.X), _lin(L2, mesh.X))
-        uy = np.where(inside, _lin(M1, mesh.X), _lin(M2, mesh.X))
+        xc = mesh.X[mesh.conn[side[a], :_nv(mesh)]].mean(0)
+        bil = q * (mesh.X[:, 0] - xc[0]) * (mesh.X[:, 1] - xc[1])
+        ux = np.where(inside, _lin(L1, mesh.X) + bil, _lin(L2, mesh.X))
+        uy = np.where(inside, _lin(M1, mesh.X) - bil, _lin(M2, mesh.X))
+        gb = q * np.array([mesh.X[a, 1] - xc[1], mesh.X[a, 0] - xc[0]])
+        du = np.array([L1[1] + gb[0], L1[2] + gb[1], M1[1] - gb[0], M1[2] - gb[1]])
         rho = np.ones(mesh.n_nodes)
         T = np.full(mesh.n_nodes, 0.3)
         f, g = _eq_state(rho, ux, uy, T)
@@ -277,7 +334,7 @@ def test_wall_condition_gradient_is_taken_in_the_wall_side_element():
         assert np.allclose(st["g"][miss, a], ge[miss], rtol=1e-12, atol=1e-16)
         # the owner element's vertex-linear gradient differs, and so does the
         # reconstruction it would give: the check above can fail
-        dow = np.concatenate([_vertex_gradient(mesh, owner[a], ux), _vertex_gradient(mesh, owner[a], uy)])
+        dow = np.concatenate([_vertex_gradient(mesh, owner[a], ux, a), _vertex_gradient(mesh, owner[a], uy, a)])
         assert np.abs(dow - du).max() > 1e-3
         fo, _ = O.grad_bc(probe, 1.0, ux[a], uy[a], 0.3, dow, np.zeros(2))
         assert np.abs(fe[miss] - fo[miss]).max() > 1e-6
@@ -287,8 +344,9 @@ def test_wall_condition_gradient_is_taken_in_the_wall_side_element():
 # off-wall target velocity (reading R8c, flag OFFWALL_VG)
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("elem", ELEMS)
 @pytest.mark.parametrize("offwall_vg", [True, False], ids=["R8c", "R8"])
-def test_offwall_target_velocity_next_to_a_receding_wall(offwall_vg):
+def test_offwall_target_velocity_next_to_a_receding_wall(offwall_vg, elem):
     """The channel plunges, y = Y - h sin(w t): the walls move with
     V_G = (0, -h w cos w t), away from the fluid above the lower wall.
     After one step without collision, each off-wall node's missing
@@ -296,7 +354,7 @@ def test_offwall_target_velocity_next_to_a_receding_wall(offwall_vg):
     with the gradients of the (linear) previous-step velocity, where
     u_tgt = V_G(t_{n+1}) under the flag and the node's own previous
     velocity without it (reading R8)."""
-    mesh = I.wall_channel()
+    mesh = I.wall_channel(elem=elem)
     h, w = 2.0, 0.02
     mot = I.Motion.make(I.MOTION_PLUNGE, h, w)
     flags = O.FLAG_COLLIDE_OFF | (O.FLAG_OFFWALL_VG if offwall_vg else 0)
