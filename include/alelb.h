@@ -65,6 +65,9 @@ enum {
 };
 
 enum { ALELB_EDGE_INTERIOR = 0, ALELB_EDGE_WALL = 1, ALELB_EDGE_FARFIELD = 2 };
+/* Element kinds (alelb_mesh_desc.elem_type): straight-sided 6-node
+   triangles, or the paper's 9-node quadrilaterals (Sec. III). */
+enum { ALELB_ELEM_P2TRI = 0, ALELB_ELEM_Q2QUAD = 1 };
 enum { ALELB_RENUMBER_NONE = 0, ALELB_RENUMBER_MORTON = 1 };
 /* Storage and arithmetic of a solver (Sec. IV's populations; the paper
    computes in FP64 and gives no reduced-precision form):
@@ -115,13 +118,25 @@ enum {
                                       plunging airfoils stay stable over whole runs */
 };
 
-/* Mesh description (computational domain, Sec. III).  Straight-sided
-   6-node triangles: conn[6*e .. 6*e+5] = v0 v1 v2 (counter-clockwise), then
-   the midside nodes of edges (v0,v1), (v1,v2), (v2,v0), which must be the
-   exact edge midpoints.  edge_kind[3*e + k] is the kind of edge k
-   (v_k, v_k+1).  period[d] > 0 makes direction d periodic with that period
-   (coordinates in [0, period)).  All pointers are host pointers, read
-   during alelb_mesh_create only. */
+/* Mesh description (computational domain, Sec. III).
+   ALELB_ELEM_P2TRI, straight-sided 6-node triangles: conn[6*e .. 6*e+5] =
+   v0 v1 v2 (counter-clockwise), then the midside nodes of edges (v0,v1),
+   (v1,v2), (v2,v0), which must be the exact edge midpoints;
+   edge_kind[3*e + k] is the kind of edge k (v_k, v_k+1).
+   ALELB_ELEM_Q2QUAD, the paper's 9-node quadrilaterals with straight edges
+   (the bilinear cells of Eq. NonLinear_Eq): conn[9*e .. 9*e+8] = v0 v1 v2
+   v3 (counter-clockwise, every corner turning left: strictly convex), the
+   midside nodes of edges (v0,v1), (v1,v2), (v2,v3), (v3,v0) (exact edge
+   midpoints), then the centre, exactly 0.25 (((v0 + v1) + v2) + v3);
+   edge_kind[4*e + k].  The local coordinates of a departure point solve
+   Eq. NonLinear_Eq by Newton's method from the cell centre (8 steps), and
+   every population of such a mesh takes the exact FP64 departure path in
+   every precision.  Quadrilateral meshes are not taken by the batched
+   step, the learned proposal, alelb_samples or alelb_lb_step_noalloc
+   (ALELB_ERR_ARG).
+   period[d] > 0 makes direction d periodic with that period (coordinates
+   in [0, period)).  All pointers are host pointers, read during
+   alelb_mesh_create only. */
 typedef struct {
     int32_t n_nodes;
     const double *X;          /* [2 * n_nodes], x0 y0 x1 y1 ... */
@@ -132,6 +147,7 @@ typedef struct {
     int32_t motion_kind;
     double motion[16];
     int32_t renumber;         /* ALELB_RENUMBER_* */
+    int32_t elem_type;        /* ALELB_ELEM_* (zero: 6-node triangles) */
 } alelb_mesh_desc;
 
 /* Fluid and run parameters (Sec. IV; R = 1, Cv = 1/(gamma - 1), Cp = Cv + 1,

@@ -24,6 +24,8 @@ PREC_BF16_DEV = 2
 PREC_FP16_DEV = 3
 RENUMBER_NONE = 0
 RENUMBER_MORTON = 1
+ELEM_P2TRI = 0
+ELEM_Q2QUAD = 1
 FLAG_PHI_OFF = 1
 FLAG_COLLIDE_OFF = 2
 FLAG_LITERAL_VG = 4
@@ -56,7 +58,8 @@ class AlelbError(RuntimeError):
 class MeshDesc(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("X", C.c_void_p), ("n_elems", C.c_int32),
                 ("conn", C.c_void_p), ("edge_kind", C.c_void_p), ("period", C.c_double * 2),
-                ("motion_kind", C.c_int32), ("motion", C.c_double * 16), ("renumber", C.c_int32)]
+                ("motion_kind", C.c_int32), ("motion", C.c_double * 16), ("renumber", C.c_int32),
+                ("elem_type", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -167,6 +170,7 @@ class Mesh:
         for k in range(16):
             d.motion[k] = float(motion.params[k])
         d.renumber = int(renumber)
+        d.elem_type = int(getattr(mesh, "elem_type", 0))
         h = C.c_void_p()
         st = L.alelb_mesh_create(C.byref(d), C.byref(h))
         if st != OK:

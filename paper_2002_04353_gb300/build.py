@@ -12,10 +12,11 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-UNITS = [os.path.join(CSRC, f) for f in ("alelb.cu", "batch.cu", "mlp.cu", "checkpoint.cu")]
+UNITS = [os.path.join(CSRC, f) for f in ("alelb.cu", "batch.cu", "mlp.cu", "checkpoint.cu", "quad.cu")]
 OUT = os.path.join(HERE, "_build", "libalelb.so")
 DEPS = UNITS + [os.path.join(CSRC, f) for f in ("geom.cuh", "kinetic.cuh", "kernels.cuh", "tables.h",
-                                                 "internal.h", "mlp.cuh")] + [os.path.join(ROOT, "include", "alelb.h")]
+                                                 "internal.h", "mlp.cuh", "quad.cuh", "quad_tables.h")] + [
+    os.path.join(ROOT, "include", "alelb.h")]
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 

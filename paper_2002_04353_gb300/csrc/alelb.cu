@@ -109,7 +109,14 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     alelb_mesh *m = new (std::nothrow) alelb_mesh();
     if (!m) return ALELB_ERR_OOM;
     HostTables &T = m->T;
-    alelb_status bs = build_tables(d, T, m->err);
+    if (d->elem_type != ALELB_ELEM_P2TRI && d->elem_type != ALELB_ELEM_Q2QUAD) {
+        *out = m;
+        m->err = "unknown element type";
+        return ALELB_ERR_ARG;
+    }
+    m->etype = d->elem_type;
+    alelb_status bs = m->etype == ALELB_ELEM_Q2QUAD ? build_quad_tables(d, T, m->QT, m->err)
+                                                    : build_tables(d, T, m->err);
     if (bs != ALELB_OK) {
         *out = m; // returned so that alelb_mesh_last_error can be read
         return bs;
@@ -123,9 +130,13 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
                 h *= 1099511628211ull;
             }
         };
+        const bool q = m->etype == ALELB_ELEM_Q2QUAD;
+        const std::vector<int> &cn = q ? m->QT.conn : T.conn;
+        const std::vector<uint32_t> &ei = q ? m->QT.einfo : T.einfo;
+        mix(&m->etype, sizeof(int));
         mix(T.X.data(), T.X.size() * sizeof(double2));
-        mix(T.conn.data(), T.conn.size() * sizeof(int));
-        mix(T.einfo.data(), T.einfo.size() * sizeof(uint32_t));
+        mix(cn.data(), cn.size() * sizeof(int));
+        mix(ei.data(), ei.size() * sizeof(uint32_t));
         mix(&T.Lx, sizeof(double));
         mix(&T.Ly, sizeof(double));
         mix(&T.mkind, sizeof(int));
@@ -135,6 +146,10 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     // upload
     cudaError_t st = cudaGetDevice(&m->device);
     if (st == cudaSuccess) forget_noalloc_scratch(m->device);
+    if (st == cudaSuccess && m->etype == ALELB_ELEM_Q2QUAD) {
+        *out = m;
+        return quad_mesh_upload(m);
+    }
     DevBuf &B = m->buf;
     MeshDev &D = m->dev;
     D.N = T.N;
@@ -392,6 +407,25 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                            : (s->flags & ALELB_FLAG_MIDPOINT) ? solver_map(s, map_scalars(m->T.mkind, m->T.mp, s->t + 0.5))
                                                               : sc;
     const MapScalarsF sfd = to_f32(scd, m->T);
+    if (m->etype == ALELB_ELEM_Q2QUAD) { // every population on the exact path, any precision
+        const int qseq[3] = {KT_STREAM, KT_DERIV1, KT_COLLIDE};
+        for (int q = 0; q < 3; ++q) {
+            if (qseq[q] == KT_DERIV1 && !phi) continue;
+            cudaEvent_t ea = nullptr, eb = nullptr;
+            if (s->prof) {
+                ea = get_event(s);
+                eb = get_event(s);
+                cudaEventRecord(ea, s->stream);
+            }
+            const cudaError_t qs = quad_launch(s, qseq[q], sc, scd);
+            if (qs != cudaSuccess) return qs;
+            if (s->prof) {
+                cudaEventRecord(eb, s->stream);
+                s->pending.push_back({qseq[q], ea, eb});
+            }
+        }
+        return cudaGetLastError();
+    }
     int seq[KT_N], ns = 0;
     if (fast) {
         seq[ns++] = KT_FAST;
@@ -747,7 +781,9 @@ extern "C" alelb_status alelb_forces(alelb_solver *s, double out[6])
     if (!s || !out) return ALELB_ERR_ARG;
     alelb_mesh *m = s->mesh;
     MapScalars sc = map_scalars(m->T.mkind, m->T.mp, s->t);
-    if (m->nw > 0) {
+    if (m->nw > 0 && m->etype == ALELB_ELEM_Q2QUAD) {
+        quad_forces(s, sc);
+    } else if (m->nw > 0) {
         with_state(s, [&](auto &sx, auto &) {
             k_forces<<<1, 256, 0, s->stream>>>(m->dev, m->mst, sc, sx, m->d_wedges, m->nw, s->mu, s->Cv,
                                                s->d_out);
@@ -789,8 +825,11 @@ extern "C" alelb_status alelb_locate(alelb_solver *s, double t, int32_t use_cach
     const MapScalars sc = solver_map(s, map_scalars(m->T.mkind, m->T.mp, t));
     int *de = (int *)s->d_scratch;
     int8_t *dk = (int8_t *)(s->d_scratch + (size_t)9 * N);
-    k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, cache,
-                                                     de, dk, s->d_err);
+    if (m->etype == ALELB_ELEM_Q2QUAD) // no fast path: the walk decides every population
+        quad_locate(s, sc, de, dk);
+    else
+        k_locate<<<(N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, cache,
+                                                         de, dk, s->d_err);
     std::vector<int> he((size_t)9 * N);
     std::vector<int8_t> hk((size_t)9 * N);
     cudaError_t st = cudaGetLastError();
@@ -907,6 +946,10 @@ extern "C" alelb_status alelb_lb_step_noalloc(alelb_mesh *m, const alelb_params 
     }
     if (!shift_ok(p->shift)) {
         m->err = "lb_step_noalloc: the lattice shift must be finite, at most 1 per component, and exact in FP32";
+        return ALELB_ERR_ARG;
+    }
+    if (m->etype != ALELB_ELEM_P2TRI) {
+        m->err = "lb_step_noalloc: 6-node triangle meshes only";
         return ALELB_ERR_ARG;
     }
     const int N = m->T.N;

@@ -503,6 +503,7 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         // and the arrival-time transformed velocities
         if (cases[c]->prec != ALELB_PREC_FP64 && cases[c]->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
         if (cases[c]->flags & (ALELB_FLAG_MIDPOINT | ALELB_FLAG_EXACT_CHAR)) return ALELB_ERR_ARG;
+        if (cases[c]->mesh->etype != ALELB_ELEM_P2TRI) return ALELB_ERR_ARG; // 6-node triangles only
         for (int d = 0; d < c; ++d)
             if (cases[d] == cases[c]) return ALELB_ERR_ARG;
     }

@@ -609,6 +609,13 @@ struct Pred64 {
     }
     // orient(X_a, p, w_k) of the loaded element
     ALELB_HD int avp(int k) { return orient(Xa, Ya, px, py, w[2 * k], w[2 * k + 1]); }
+    // p, known to lie on the line through w_l and w_k, lies on the ray from
+    // w_l through w_k (the two terms of a dot product of collinear vectors
+    // share one sign, so its sign is exact)
+    ALELB_HD bool fwd(int l, int k)
+    {
+        return (px - w[2 * l]) * (w[2 * k] - w[2 * l]) + (py - w[2 * l + 1]) * (w[2 * k + 1] - w[2 * l + 1]) > 0.0;
+    }
     ALELB_HD bool p_is_node() const { return px == Xa && py == Ya; }
 };
 
@@ -674,7 +681,14 @@ template <class P> ALELB_HD __forceinline__ Loc walk_t(const MeshDev &M, P &pr, 
         bool hit;
         if (ll < 3) {
             int k1 = (ll + 1) % 3, k2 = (ll + 2) % 3;
-            hit = pr.vvp(ll, k1) >= 0 && pr.vvp(ll, k2) < 0;
+            hit = pr.vvp(ll, k1) >= 0;
+            if (hit) {
+                // the sector ends before the ray ll -> k2, which the next fan
+                // element holds; when edge (k2, ll) is a boundary edge no
+                // element does, and a segment along it stays in the closed mesh
+                const int s2 = pr.vvp(ll, k2);
+                hit = s2 < 0 || (s2 == 0 && ((M.einfo[fe.x] >> (8 * k2)) & 3u) && pr.fwd(ll, k2));
+            }
         } else {
             int k0 = ll - 3, k1 = (k0 + 1) % 3;
             hit = pr.vvp(k0, k1) >= 0;
@@ -1274,6 +1288,13 @@ struct Pred32 {
         if (s) return s;
         ensure64();
         return orient(Xa, Ya, px, py, WX(k), WY(k));
+    }
+    // as Pred64::fwd, on the FP64 departure point (asked only after an
+    // exactly zero sign, which came from the FP64 stage)
+    ALELB_HD bool fwd(int l, int k)
+    {
+        ensure64();
+        return (px - WX(l)) * (WX(k) - WX(l)) + (py - WY(l)) * (WY(k) - WY(l)) > 0.0;
     }
     // the caller ensures |c^| > 4 F.eq(i): then the FP64 departure point is
     // not the node

@@ -9,6 +9,7 @@
 
 #include "alelb.h"
 #include "kernels.cuh"
+#include "quad_tables.h"
 #include "tables.h"
 
 namespace alelb {
@@ -72,6 +73,14 @@ cudaError_t batch_fe_tables();
 alelb_status check_sticky(alelb_solver *s);
 // Learned proposals for the solver's current work list (mlp.cu).
 cudaError_t mlp_propose(alelb_solver *s, const MapScalarsF &sf);
+// 9-node quadrilateral meshes (quad.cu): upload of the tables built by
+// build_quad_tables; one kernel of a step (KT_STREAM, KT_DERIV1 or
+// KT_COLLIDE) on the solver's stream; the element-choice report; the wall
+// forces into s->d_out.
+alelb_status quad_mesh_upload(alelb_mesh *m);
+cudaError_t quad_launch(alelb_solver *s, int kernel, const MapScalars &sc, const MapScalars &scd);
+cudaError_t quad_locate(alelb_solver *s, const MapScalars &sc, int *elem, int8_t *kind);
+cudaError_t quad_forces(alelb_solver *s, const MapScalars &sc);
 
 
 } // namespace alelb
@@ -81,7 +90,12 @@ using namespace alelb;
 
 struct alelb_mesh {
     std::string err;
-    HostTables T;   // host copies of every table (also used by the host-side walk check)
+    int etype = ALELB_ELEM_P2TRI; // element kind (alelb_mesh_desc.elem_type)
+    HostTables T;   // host copies of every table (also used by the host-side walk check);
+                    // for quadrilaterals only the generic fields (sizes, node order,
+                    // coordinates, map factors, wall edges)
+    QuadTables QT;  // quadrilateral meshes: their element tables
+    QuadDev qdev{}; // quadrilateral meshes: the device tables
     MeshDev dev{};
     MapStatic mst{};
     int2 *d_wedges = nullptr;

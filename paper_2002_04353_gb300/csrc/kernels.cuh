@@ -129,6 +129,7 @@ __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefe
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <class S> struct StateDev {
+    using Tag = S; // the storage form
     using P = pop_t<S>;
     using F = fld_t<S>;
     P *post;  // [18 N] post-collision populations (deviations), layout of fg_get

@@ -20,6 +20,7 @@
 namespace alelb {
 
 template <class A> struct KinParams {
+    using Arith = A; // the arithmetic type
     A Cv, Cp, mu, Pr;
     // moments of the reference populations: sum f_ref, sum c f_ref,
     // sum c c f_ref, sum g_ref

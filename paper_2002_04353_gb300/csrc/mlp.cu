@@ -677,6 +677,10 @@ extern "C" alelb_status alelb_samples(alelb_solver *s, double t, float *feat, in
 {
     if (!s || !s->mesh || !feat || !slot || !bary || !nring) return ALELB_ERR_ARG;
     alelb_mesh *m = s->mesh;
+    if (m->etype != ALELB_ELEM_P2TRI) {
+        s->err = "samples: the learned proposal serves 6-node triangle meshes";
+        return ALELB_ERR_ARG;
+    }
     const MapScalars sc = solver_map(s, map_scalars(m->T.mkind, m->T.mp, t));
     k_samples<<<(m->T.N + 127) / 128, 128, 0, s->stream>>>(m->dev, m->mst, sc, to_f32(sc, m->T), s->flags, feat,
                                                             slot, bary, nring, s->d_err);
@@ -694,6 +698,10 @@ extern "C" alelb_status alelb_solver_set_mlp(alelb_solver *s, alelb_mlp *m)
     if (!s) return ALELB_ERR_ARG;
     if (m && s->prec == ALELB_PREC_FP64) {
         s->err = "the learned proposal serves the deviation-form propagation only";
+        return ALELB_ERR_ARG;
+    }
+    if (m && s->mesh->etype != ALELB_ELEM_P2TRI) {
+        s->err = "the learned proposal serves 6-node triangle meshes";
         return ALELB_ERR_ARG;
     }
     if (m && !s->d_prop) {

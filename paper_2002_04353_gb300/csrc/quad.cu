@@ -1,0 +1,400 @@
+// quad.cu -- one time step on a mesh of the paper's 9-node quadrilaterals
+// (Sec. III), the element-choice report and the wall forces, plus the upload
+// of the mesh tables.  The kinetic model (equilibria, collision, Grad-type
+// missing populations) is the one the triangles use (kinetic.cuh); only the
+// geometry differs: the walk over quadrilaterals, Newton's method for the
+// local coordinates of Eq. NonLinear_Eq, the nine shape functions of
+// Eq. Propagation and the element gradients (quad.cuh).  Every population
+// takes the exact FP64 path in every storage precision.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "internal.h"
+
+namespace alelb {
+namespace {
+
+// Propagation of the nine population pairs of node a (Eq. Propagation over
+// the nine nodes of the departure element), the missing populations of
+// Sec. IV.A, then moments, Q'_aaa and mu/(rho T), as on triangles.
+template <class S, class A>
+__device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStatic &MS, const MapScalars &sc,
+                                                 const MapScalars &scd, const KinParams<A> &K,
+                                                 const StateDev<S> &st, int *err, unsigned long long *stats, int a)
+{
+    const int N = M.N;
+    const double2 Xa = M.X[a];
+    bool have64 = false;
+    double a11 = 0, a12 = 0, a21 = 0, a22 = 0, wx = 0, wy = 0, Vx = 0, Vy = 0;
+    int miss = 0, far = 0;
+    unsigned walks = 0;
+    A sfm = 0, jx = 0, jy = 0, sg = 0;
+#pragma unroll 1
+    for (int i = 0; i < NQ; ++i) {
+        A fi = 0, gi = 0;
+        int src = -1;
+        if (!have64 && !(K.flags & FLAG_EXACT_CHAR)) {
+            double xX, xY, yX, yY;
+            map_node(MS, scd, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+            mesh_velocity_term(a11, a12, a21, a22, ds(Vx, scd.Ux), ds(Vy, scd.Uy), (K.flags & FLAG_LITERAL_VG) != 0,
+                               wx, wy);
+            have64 = true;
+        }
+        double chx, chy, px, py;
+        if (K.flags & FLAG_EXACT_CHAR)
+            exact_departure(MS, sc, scd, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx, chy, px, py);
+        else
+            departure(a11, a12, a21, a22, wx, wy, (double)c_cx[i], (double)c_cy[i], Xa.x, Xa.y, chx, chy, px, py);
+        if (chx == 0.0 && chy == 0.0) {
+            src = a;
+        } else {
+            ++walks;
+            const Loc L = quad_walk(M, a, Xa.x, Xa.y, px, py, err);
+            if (L.e == -2) {
+                src = a;
+            } else if (L.e == -1) {
+                miss |= 1 << i;
+                if (L.kind == 2) far |= 1 << i;
+                continue;
+            } else if (L.vnode >= 0) {
+                src = L.vnode;
+            } else {
+                double xi, eta;
+                if (!quad_local(M, L.e, L.sx, L.sy, px, py, xi, eta)) set_err(err, ERR_LOCATE);
+                A Nw[9];
+                shape9<A>((A)xi, (A)eta, Nw);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int b = M.conn[9 * L.e + k];
+                    A fb, gb;
+                    fg_get(st.post, i, b, N, fb, gb);
+                    fi += Nw[k] * fb;
+                    gi += Nw[k] * gb;
+                }
+            }
+        }
+        if (src >= 0) fg_get(st.post, i, src, N, fi, gi);
+        fg_put(st.str, i, a, N, fi, gi);
+        sfm += fi;
+        jx += (A)c_cx[i] * fi;
+        jy += (A)c_cy[i] * fi;
+        sg += gi;
+    }
+    if (stats && walks) atomicAdd(stats, (unsigned long long)walks);
+    if (miss) {
+        if (!have64 || (K.flags & FLAG_MIDPOINT)) { // the wall condition's map: arrival time
+            double xX, xY, yX, yY;
+            map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        }
+        A fm[NQ], gm[NQ];
+        if (miss & ~far) {
+            A rt, uxt, uyt, Tt;
+            const int wi = M.wall_idx[a];
+            if (wi >= 0) { // wall node: u = V_G, rho and T at the probe B
+                const int pe = M.probe_e[wi];
+                const double2 pxi = M.probe_xi[wi];
+                A Nw[9];
+                shape9<A>((A)pxi.x, (A)pxi.y, Nw);
+                A r = 0, t = 0, ub = 0, vb = 0;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int b = M.conn[9 * pe + k];
+                    r += Nw[k] * (A)st.rho[b];
+                    t += Nw[k] * (A)st.T[b];
+                    if (K.flags & FLAG_SLIP) {
+                        ub += Nw[k] * (A)st.ux[b];
+                        vb += Nw[k] * (A)st.uy[b];
+                    }
+                }
+                rt = r;
+                Tt = t;
+                uxt = (A)Vx;
+                uyt = (A)Vy;
+                if (K.flags & FLAG_SLIP) {
+                    const double2 nw = M.wall_nrm[wi];
+                    slip_target<A>((A)a11, (A)a12, (A)a21, (A)a22, (A)nw.x, (A)nw.y, ub, vb, (A)Vx, (A)Vy, uxt, uyt);
+                }
+            } else { // off-wall node: its previous-step fields (mesh velocity under R8c)
+                const bool vg = (K.flags & FLAG_OFFWALL_VG) != 0;
+                rt = (A)st.rho[a];
+                uxt = vg ? (A)Vx : (A)st.ux[a];
+                uyt = vg ? (A)Vy : (A)st.uy[a];
+                Tt = (A)st.T[a];
+            }
+            A du[4] = {0, 0, 0, 0}, dT[2] = {0, 0};
+            if (!(K.flags & FLAG_BC_EQ) && !((K.flags & FLAG_SLIP) && wi >= 0)) {
+                const int2 bc = M.bcel[a];
+                double KX, KY;
+                quad_grad(M, bc, st.ux, false, KX, KY);
+                du[0] = (A)(a11 * KX + a21 * KY);
+                du[1] = (A)(a12 * KX + a22 * KY);
+                quad_grad(M, bc, st.uy, false, KX, KY);
+                du[2] = (A)(a11 * KX + a21 * KY);
+                du[3] = (A)(a12 * KX + a22 * KY);
+                quad_grad(M, bc, st.T, false, KX, KY);
+                dT[0] = (A)(a11 * KX + a21 * KY);
+                dT[1] = (A)(a12 * KX + a22 * KY);
+            }
+            grad_missing(K, rt, uxt, uyt, Tt, du, dT, fm, gm);
+        }
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            if (!(miss >> i & 1)) continue;
+            const A fi = (far >> i & 1) ? K.finf[i] : fm[i];
+            const A gi = (far >> i & 1) ? K.ginf[i] : gm[i];
+            fg_put(st.str, i, a, N, fi, gi);
+            sfm += fi;
+            jx += (A)c_cx[i] * fi;
+            jy += (A)c_cy[i] * fi;
+            sg += gi;
+        }
+    }
+    const A rho = K.rho_ref + sfm;
+    const A rwx = (K.jx_ref + jx) / rho, rwy = (K.jy_ref + jy) / rho;
+    const A ux = rwx + K.Ux, uy = rwy + K.Uy;
+    const A E = (K.E2_ref + sg) / (A(2) * rho);
+    const A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
+    if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
+    const A k3 = A(1) - A(3) * T;
+    st.Qx[a] = (fld_t<S>)(rho * rwx * k3 - rho * rwx * rwx * rwx);
+    st.Qy[a] = (fld_t<S>)(rho * rwy * k3 - rho * rwy * rwy * rwy);
+    st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(128) kq_stream(QuadDev M, MapStatic MS, MapScalars sc, MapScalars scd,
+                                                 KinParams<A> K, StateDev<S> st, int *err, unsigned long long *stats)
+{
+    wait_prior_grid();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < M.N) quad_stream_node(M, MS, sc, scd, K, st, err, stats, a);
+}
+
+// D_a = (mu / rho T) d_a Q'_aaa in the owner element (Eq. Xa).
+template <class S, class A>
+__global__ void __launch_bounds__(256) kq_deriv1(QuadDev M, MapStatic MS, MapScalars sc, StateDev<S> st)
+{
+    wait_prior_grid();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= M.N) return;
+    const double2 Xa = M.X[a];
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    double KX, KY;
+    quad_grad(M, M.owner[a], st.Qx, true, KX, KY);
+    const double dQx = a11 * KX + a21 * KY;
+    quad_grad(M, M.owner[a], st.Qy, true, KX, KY);
+    const double dQy = a12 * KX + a22 * KY;
+    const double m = (double)st.mrt[a];
+    st.Dx[a] = (fld_t<S>)(m * dQx);
+    st.Dy[a] = (fld_t<S>)(m * dQy);
+}
+
+// X_a = -d_a D_a in the owner element, then the collision (Eqs. feqn, geqn).
+template <class S, class A>
+__global__ void __launch_bounds__(128) kq_collide(QuadDev M, MapStatic MS, MapScalars sc, KinParams<A> K,
+                                                  StateDev<S> st, int *err)
+{
+    wait_prior_grid();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= M.N) return;
+    const int N = M.N;
+    A Xx = 0, Xy = 0;
+    if (!(K.flags & FLAG_PHI_OFF)) {
+        const double2 Xa = M.X[a];
+        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        double KX, KY;
+        quad_grad(M, M.owner[a], st.Dx, true, KX, KY);
+        Xx = (A)(-(a11 * KX + a21 * KY));
+        quad_grad(M, M.owner[a], st.Dy, true, KX, KY);
+        Xy = (A)(-(a12 * KX + a22 * KY));
+    }
+    A f[NQ], g[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) fg_get(st.str, i, a, N, f[i], g[i]);
+    A rho, ux, uy, T;
+    if (!collide_node(K, f, g, Xx, Xy, rho, ux, uy, T)) atomicOr(err, ERR_NONFINITE);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) fg_put(st.post, i, a, N, f[i], g[i]);
+    st.rho[a] = (fld_t<S>)rho;
+    st.ux[a] = (fld_t<S>)ux;
+    st.uy[a] = (fld_t<S>)uy;
+    st.T[a] = (fld_t<S>)T;
+}
+
+// Element choice of every population (parity report): original element id,
+// -2 (the node itself) or -1 with the boundary kind.
+static __global__ void kq_locate(QuadDev M, MapStatic MS, MapScalars sc, int literal, int *elem, int8_t *kind,
+                                 int *err)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = M.N;
+    if (a >= N) return;
+    const double2 Xa = M.X[a];
+    double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+    map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+    metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+    mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), literal != 0, wx, wy);
+    for (int i = 0; i < NQ; ++i) {
+        double chx, chy, px, py;
+        departure(a11, a12, a21, a22, wx, wy, (double)lat_cx(i), (double)lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
+        int e = -2, k = 0;
+        if (!(chx == 0.0 && chy == 0.0)) {
+            const Loc L = quad_walk(M, a, Xa.x, Xa.y, px, py, err);
+            if (L.e >= 0) {
+                e = M.orig_elem[L.vnode >= 0 ? quad_fan_best(M, L.vnode) : L.e];
+            } else if (L.e == -1) {
+                e = -1;
+                k = L.kind;
+            }
+        }
+        elem[i * N + a] = e;
+        kind[i * N + a] = (int8_t)k;
+    }
+}
+
+// Wall forces (reading R9): Simpson's rule on each straight 3-node wall edge
+// of the mapped geometry, owner-element gradients; one block, fixed-order
+// FP64 reduction.  out = {Fx_p, Fy_p, Fx_v, Fy_v}.
+template <class S>
+__global__ void __launch_bounds__(256) kq_forces(QuadDev M, MapStatic MS, MapScalars sc, StateDev<S> st,
+                                                 const int2 *wedges, int nw, double mu, double Cv, double *out)
+{
+    __shared__ double red[4][256];
+    double acc[4] = {0, 0, 0, 0};
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        const int e = wedges[w].x, k = wedges[w].y, k1 = (k + 1) & 3;
+        const int nodes[3] = {M.conn[9 * e + k], M.conn[9 * e + 4 + k], M.conn[9 * e + k1]};
+        const double2 A0 = M.X[nodes[0]], B0 = M.X[nodes[2]];
+        double xa, ya, xb, yb;
+        map_position(MS, sc, nodes[0], A0.x, A0.y, xa, ya);
+        map_position(MS, sc, nodes[2], B0.x, B0.y, xb, yb);
+        const double tx = xb - xa, ty = yb - ya, L = sqrt(tx * tx + ty * ty);
+        const double nx = -ty / L, ny = tx / L; // out of the body, into the fluid
+        const double wgt[3] = {L / 6.0, 4.0 * L / 6.0, L / 6.0};
+        for (int j = 0; j < 3; ++j) {
+            const int a = nodes[j];
+            const double2 Xa = M.X[a];
+            double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
+            map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+            metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+            double KX, KY, d[4];
+            quad_grad(M, M.owner[a], st.ux, true, KX, KY);
+            d[0] = a11 * KX + a21 * KY;
+            d[1] = a12 * KX + a22 * KY;
+            quad_grad(M, M.owner[a], st.uy, true, KX, KY);
+            d[2] = a11 * KX + a21 * KY;
+            d[3] = a12 * KX + a22 * KY;
+            const double div = d[0] + d[3];
+            const double p = (double)st.rho[a] * (double)st.T[a];
+            const double txx = mu * (2.0 * d[0] - div / Cv);
+            const double tyy = mu * (2.0 * d[3] - div / Cv);
+            const double txy = mu * (d[1] + d[2]);
+            acc[0] += wgt[j] * (-p * nx);
+            acc[1] += wgt[j] * (-p * ny);
+            acc[2] += wgt[j] * (txx * nx + txy * ny);
+            acc[3] += wgt[j] * (txy * nx + tyy * ny);
+        }
+    }
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+} // namespace
+
+alelb_status quad_mesh_upload(alelb_mesh *m)
+{
+    const QuadTables &Q = m->QT;
+    const HostTables &T = m->T;
+    cudaError_t st = cudaSuccess;
+    DevBuf &B = m->buf;
+    QuadDev &D = m->qdev;
+    D.N = T.N;
+    D.E = T.E;
+    D.Lx = T.Lx;
+    D.Ly = T.Ly;
+    D.X = B.put(T.X, st);
+    D.ev = B.put(Q.ev, st);
+    D.nbr = B.put(Q.nbr, st);
+    D.einfo = B.put(Q.einfo, st);
+    D.rank = B.put(Q.rank, st);
+    D.conn = B.put(Q.conn, st);
+    D.fan_ptr = B.put(Q.fan_ptr, st);
+    D.fan = B.put(Q.fan, st);
+    D.owner = B.put(Q.owner, st);
+    D.bcel = B.put(Q.bcel, st);
+    D.bkind = B.put(Q.bkind, st);
+    D.wall_idx = B.put(Q.wall_idx, st);
+    D.probe_e = B.put(Q.probe_e, st);
+    D.probe_xi = B.put(Q.probe_xi, st);
+    D.wall_nrm = B.put(Q.wall_nrm, st);
+    D.orig_elem = B.put(Q.orig, st);
+    m->d_wedges = B.put(Q.wedges, st);
+    m->d_n2o = B.put(T.node_new2old, st);
+    m->nw = (int)Q.wedges.size();
+    m->mst = T.host_map();
+    m->mst.ms = B.put(T.ms, st);
+    m->mst.msf = B.put(T.msf, st);
+    if (st == cudaSuccess) st = cudaDeviceSynchronize();
+    if (st != cudaSuccess) {
+        m->buf.release();
+        m->err = cudaGetErrorString(st);
+        return st == cudaErrorMemoryAllocation ? ALELB_ERR_OOM : ALELB_ERR_CUDA;
+    }
+    return ALELB_OK;
+}
+
+cudaError_t quad_launch(alelb_solver *s, int kernel, const MapScalars &sc, const MapScalars &scd)
+{
+    alelb_mesh *m = s->mesh;
+    const int N = m->T.N;
+    with_state(s, [&](auto &st, auto &K) {
+        using S = typename std::remove_reference<decltype(st)>::type::Tag;
+        using A = typename std::remove_reference<decltype(K)>::type::Arith;
+        switch (kernel) {
+        case KT_STREAM:
+            launch_pdl(kq_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc, scd, K, st,
+                       s->d_err, s->d_stats);
+            break;
+        case KT_DERIV1:
+            launch_pdl(kq_deriv1<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, m->qdev, m->mst, sc, st);
+            break;
+        default:
+            launch_pdl(kq_collide<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc, K, st,
+                       s->d_err);
+        }
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t quad_locate(alelb_solver *s, const MapScalars &sc, int *elem, int8_t *kind)
+{
+    alelb_mesh *m = s->mesh;
+    kq_locate<<<(m->T.N + 127) / 128, 128, 0, s->stream>>>(m->qdev, m->mst, sc, (s->flags & ALELB_FLAG_LITERAL_VG) != 0,
+                                                           elem, kind, s->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t quad_forces(alelb_solver *s, const MapScalars &sc)
+{
+    alelb_mesh *m = s->mesh;
+    with_state(s, [&](auto &st, auto &) {
+        using S = typename std::remove_reference<decltype(st)>::type::Tag;
+        kq_forces<S><<<1, 256, 0, s->stream>>>(m->qdev, m->mst, sc, st, m->d_wedges, m->nw, s->mu, s->Cv, s->d_out);
+    });
+    return cudaGetLastError();
+}
+
+} // namespace alelb

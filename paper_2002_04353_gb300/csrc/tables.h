@@ -210,6 +210,63 @@ inline void build_rings(HostTables &T, const std::vector<double> &area2)
     }
 }
 
+// Static per-node factors of the map (host libm, the same expressions for
+// every element kind): SINE {A sin(w Y), A sin(w X), ...} (6 per node),
+// BLENDED {b, db/dX, db/dY} (3 per node), none for the rigid maps.  X in the
+// library's node order.
+inline std::vector<double> static_map_factors(int mkind, const double *mp, const std::vector<double2> &X)
+{
+    const int N = (int)X.size();
+    std::vector<double> ms;
+    if (mkind == MK_SINE) {
+        ms.assign((size_t)6 * N, 0.0);
+        double A = mp[0], L = mp[1];
+        double w = 2.0 * M_PI / L;
+        for (int a = 0; a < N; ++a) {
+            double Xx = X[a].x, Yy = X[a].y;
+            double f[6];
+            if (mp[3] == 0.0) {
+                f[0] = A * std::sin(w * Yy);
+                f[1] = A * std::sin(w * Xx);
+                f[2] = 0.0;
+                f[3] = (A * w) * std::cos(w * Yy);
+                f[4] = (A * w) * std::cos(w * Xx);
+                f[5] = 0.0;
+            } else {
+                double S = std::sin(w * Xx) * std::sin(w * Yy);
+                f[0] = A * S;
+                f[1] = A * S;
+                f[2] = (A * w) * (std::cos(w * Xx) * std::sin(w * Yy));
+                f[3] = (A * w) * (std::sin(w * Xx) * std::cos(w * Yy));
+                f[4] = f[2];
+                f[5] = f[3];
+            }
+            for (int k = 0; k < 6; ++k) ms[(size_t)k * N + a] = f[k];
+        }
+    } else if (mkind == MK_BLENDED) {
+        ms.assign((size_t)3 * N, 0.0);
+        double Xc = mp[3], Yc = mp[4], r1 = mp[5], r2 = mp[6];
+        for (int a = 0; a < N; ++a) {
+            double dx = X[a].x - Xc, dy = X[a].y - Yc;
+            double r = std::sqrt(dx * dx + dy * dy);
+            double b = 1.0, bX = 0.0, bY = 0.0;
+            if (r >= r2) {
+                b = 0.0;
+            } else if (r > r1) {
+                double s = (r - r1) / (r2 - r1);
+                b = 1.0 - s * s * (3.0 - 2.0 * s);
+                double dbdr = -(6.0 * s * (1.0 - s)) / (r2 - r1);
+                bX = dbdr * (dx / r);
+                bY = dbdr * (dy / r);
+            }
+            ms[a] = b;
+            ms[(size_t)N + a] = bX;
+            ms[(size_t)2 * N + a] = bY;
+        }
+    }
+    return ms;
+}
+
 inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::string &err)
 {
     if (!d || d->n_nodes <= 0 || d->n_elems <= 0 || !d->X || !d->conn || !d->edge_kind) {
@@ -545,55 +602,7 @@ inline alelb_status build_tables(const alelb_mesh_desc *d, HostTables &T, std::s
         }
     }
     // static per-node map factors (host libm, same expressions everywhere)
-    auto &ms = T.ms;
-    ms.clear();
-    if (T.mkind == MK_SINE) {
-        ms.assign((size_t)6 * N, 0.0);
-        double A = T.mp[0], L = T.mp[1];
-        double w = 2.0 * M_PI / L;
-        for (int a = 0; a < N; ++a) {
-            double Xx = T.X[a].x, Yy = T.X[a].y;
-            double f[6];
-            if (T.mp[3] == 0.0) {
-                f[0] = A * std::sin(w * Yy);
-                f[1] = A * std::sin(w * Xx);
-                f[2] = 0.0;
-                f[3] = (A * w) * std::cos(w * Yy);
-                f[4] = (A * w) * std::cos(w * Xx);
-                f[5] = 0.0;
-            } else {
-                double S = std::sin(w * Xx) * std::sin(w * Yy);
-                f[0] = A * S;
-                f[1] = A * S;
-                f[2] = (A * w) * (std::cos(w * Xx) * std::sin(w * Yy));
-                f[3] = (A * w) * (std::sin(w * Xx) * std::cos(w * Yy));
-                f[4] = f[2];
-                f[5] = f[3];
-            }
-            for (int k = 0; k < 6; ++k) ms[(size_t)k * N + a] = f[k];
-        }
-    } else if (T.mkind == MK_BLENDED) {
-        ms.assign((size_t)3 * N, 0.0);
-        double Xc = T.mp[3], Yc = T.mp[4], r1 = T.mp[5], r2 = T.mp[6];
-        for (int a = 0; a < N; ++a) {
-            double dx = T.X[a].x - Xc, dy = T.X[a].y - Yc;
-            double r = std::sqrt(dx * dx + dy * dy);
-            double b = 1.0, bX = 0.0, bY = 0.0;
-            if (r >= r2) {
-                b = 0.0;
-            } else if (r > r1) {
-                double s = (r - r1) / (r2 - r1);
-                b = 1.0 - s * s * (3.0 - 2.0 * s);
-                double dbdr = -(6.0 * s * (1.0 - s)) / (r2 - r1);
-                bX = dbdr * (dx / r);
-                bY = dbdr * (dy / r);
-            }
-            ms[a] = b;
-            ms[(size_t)N + a] = bX;
-            ms[(size_t)2 * N + a] = bY;
-        }
-    }
-
+    T.ms = static_map_factors(T.mkind, T.mp, T.X);
     T.n_wall_nodes = (int)T.probe_e.size();
     // FP32 edge vectors and inverse Jacobians (interpolation weights and the
     // certified FP32 containment filter)

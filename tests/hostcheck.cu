@@ -5,9 +5,72 @@
 #include <cstring>
 #include <string>
 
+#include "quad_tables.h"
 #include "tables.h"
 
 using namespace alelb;
+
+// The quadrilateral walk (quad_walk, the routine kq_locate runs) on the
+// host, for meshes of 9-node quadrilaterals.
+extern "C" int alelb_hostcheck_locate_q2(const alelb_mesh_desc *d, double t, int literal, int32_t *elem,
+                                         int8_t *kind, char *errbuf, int errlen)
+{
+    HostTables T;
+    QuadTables Q;
+    std::string err;
+    alelb_status st = build_quad_tables(d, T, Q, err);
+    if (st != ALELB_OK) {
+        if (errbuf && errlen > 0) std::strncpy(errbuf, err.c_str(), errlen - 1);
+        return st;
+    }
+    QuadDev M{};
+    M.N = T.N;
+    M.E = T.E;
+    M.Lx = T.Lx;
+    M.Ly = T.Ly;
+    M.X = T.X.data();
+    M.ev = Q.ev.data();
+    M.nbr = Q.nbr.data();
+    M.einfo = Q.einfo.data();
+    M.rank = Q.rank.data();
+    M.conn = Q.conn.data();
+    M.fan_ptr = Q.fan_ptr.data();
+    M.fan = Q.fan.data();
+    M.owner = Q.owner.data();
+    M.bcel = Q.bcel.data();
+    M.bkind = Q.bkind.data();
+    M.orig_elem = Q.orig.data();
+    MapStatic MS = T.host_map();
+    MapScalars sc = map_scalars(T.mkind, T.mp, t);
+    int e = 0;
+    const int N = T.N;
+    for (int a = 0; a < N; ++a) {
+        const double2 Xa = M.X[a];
+        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), literal != 0, wx, wy);
+        const int o = T.node_new2old[a];
+        for (int i = 0; i < NQ; ++i) {
+            double chx, chy, px, py;
+            departure(a11, a12, a21, a22, wx, wy, (double)lat_cx(i), (double)lat_cy(i), Xa.x, Xa.y, chx, chy, px,
+                      py);
+            int el = -2, k = 0;
+            if (!(chx == 0.0 && chy == 0.0)) {
+                const Loc L = quad_walk(M, a, Xa.x, Xa.y, px, py, &e);
+                if (L.e >= 0) {
+                    el = M.orig_elem[L.vnode >= 0 ? quad_fan_best(M, L.vnode) : L.e];
+                } else if (L.e == -1) {
+                    el = -1;
+                    k = L.kind;
+                }
+            }
+            elem[(size_t)i * N + o] = el;
+            kind[(size_t)i * N + o] = (int8_t)k;
+        }
+    }
+    return e ? ALELB_ERR_LOCATE : ALELB_OK;
+}
 
 extern "C" int alelb_hostcheck_locate(const alelb_mesh_desc *d, double t, int literal,
                                       int32_t *elem, int8_t *kind, char *errbuf, int errlen)

@@ -31,6 +31,8 @@ def lib():
         _lib = C.CDLL(build_lib())
         _lib.alelb_hostcheck_locate.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                                 C.c_char_p, C.c_int]
+        _lib.alelb_hostcheck_locate_q2.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                                   C.c_char_p, C.c_int]
         _lib.alelb_hostcheck_inside.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                 C.c_void_p]
         _lib.alelb_hostcheck_fast.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -52,6 +54,7 @@ def _desc(mesh, motion):
     for k in range(16):
         d.motion[k] = float(motion.params[k])
     d.renumber = alelb.RENUMBER_MORTON
+    d.elem_type = int(getattr(mesh, "elem_type", 0))
     return d, (X, conn, ek)
 
 
@@ -70,22 +73,14 @@ def inside_f32(mesh, elem, px, py):
 
 
 def locate(mesh, motion, t, literal=False):
-    X = np.ascontiguousarray(mesh.X, dtype=np.float64).reshape(-1)
-    conn = np.ascontiguousarray(mesh.conn, dtype=np.int32).reshape(-1)
-    ek = np.ascontiguousarray(mesh.edge_kind, dtype=np.uint8).reshape(-1)
-    d = alelb.MeshDesc()
-    d.n_nodes, d.X, d.n_elems = mesh.n_nodes, X.ctypes.data, mesh.n_elems
-    d.conn, d.edge_kind = conn.ctypes.data, ek.ctypes.data
-    d.period[0], d.period[1] = float(mesh.period[0]), float(mesh.period[1])
-    d.motion_kind = int(motion.kind)
-    for k in range(16):
-        d.motion[k] = float(motion.params[k])
-    d.renumber = alelb.RENUMBER_MORTON
+    """Element choices of the library's walk on the host (triangles or
+    quadrilaterals, after the mesh's element type)."""
+    d, keep = _desc(mesh, motion)
     e = np.empty((9, mesh.n_nodes), dtype=np.int32)
     k = np.empty((9, mesh.n_nodes), dtype=np.int8)
     err = C.create_string_buffer(256)
-    st = lib().alelb_hostcheck_locate(C.byref(d), float(t), int(literal), e.ctypes.data, k.ctypes.data,
-                                       err, 256)
+    fn = lib().alelb_hostcheck_locate_q2 if getattr(mesh, "elem_type", 0) == 1 else lib().alelb_hostcheck_locate
+    st = fn(C.byref(d), float(t), int(literal), e.ctypes.data, k.ctypes.data, err, 256)
     return st, e, k
 
 

@@ -59,6 +59,8 @@ LOC_CASES = {
     "omesh_plunge": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PLUNGE, 20.0, 0.002)),
     "omesh_pitch": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.05, 0.05, 0.003, 50.0, 0.0, 20.0, 0.003)),
     "omesh_blended": lambda: (I.naca_omesh(64, 20, chord=200.0, R=4000.0, first=1.0), I.Motion.make(I.MOTION_BLENDED_PITCH, 0.05, 0.05, 0.002, 50.0, 0.0, 400.0, 2000.0)),
+    # flat walls along lattice directions: segments run along boundary edges
+    "channel_plunge": lambda: (I.wall_channel(), I.Motion.make(I.MOTION_PLUNGE, 2.0, 0.02)),
 }
 
 
@@ -121,7 +123,7 @@ def test_fp64_steps_lattice_reduction_mesh():
     _compare64(o, s, "lattice")
 
 
-@pytest.mark.parametrize("motion_name", ["omesh_plunge", "omesh_pitch", "omesh_blended"])
+@pytest.mark.parametrize("motion_name", ["omesh_plunge", "omesh_pitch", "omesh_blended", "channel_plunge"])
 def test_fp64_steps_airfoil_walls_farfield(motion_name):
     mesh, motion = LOC_CASES[motion_name]()
     flow = I.flow_params(0.1, T_inf=0.3, Re=500.0, chord=200.0)
@@ -244,7 +246,7 @@ def test_mixed_airfoil_matches_fp64_oracle():
     _compare_mixed(o, s, "mixed airfoil")
 
 
-@pytest.mark.parametrize("name", ["box_sine", "box_paper_map", "omesh_plunge", "omesh_pitch", "omesh_blended"])
+@pytest.mark.parametrize("name", ["box_sine", "box_paper_map", "omesh_plunge", "omesh_pitch", "omesh_blended", "channel_plunge"])
 def test_fast_path_element_choices_bitwise(name):
     """The FP32-deviation propagation settles most populations with the
     previous-step element, verified by certified FP32 arithmetic; its

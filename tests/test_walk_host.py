@@ -23,7 +23,31 @@ CASES = {
     "blended": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0),
                 lambda: I.Motion.make(I.MOTION_BLENDED_PITCH, -0.002, -0.0436, 7.8e-5, 250.0, 0.0, 2000.0, 10000.0),
                 [1, 10000, 20000]),
+    # flat walls along lattice directions: departure segments run along
+    # boundary edges (inside the closed mesh)
+    "channel_static": (lambda: I.wall_channel(first=1.0, growth=1.0), lambda: I.Motion.make(I.MOTION_NONE), [1]),
+    "channel_plunge": (lambda: I.wall_channel(), lambda: I.Motion.make(I.MOTION_PLUNGE, 2.0, 0.02), [1, 40]),
 }
+# the same on meshes of the paper's 9-node quadrilaterals
+CASES.update({
+    "q2_box_config_map": (lambda: I.uniform_flow_case(elem="q2").mesh,
+                          lambda: I.uniform_flow_case().motion, [1, 25, 50, 99, 175]),
+    "q2_box_paper_map": (lambda: I.periodic_box(20, 40.0, 0.2, seed=2, elem="q2"),
+                         lambda: I.Motion.make(I.MOTION_SINE, 2.5, 40.0, 60.0, 1.0), [1, 15, 30]),
+    "q2_lattice": (lambda: I.lattice_box(12, elem="q2"), lambda: I.Motion.make(I.MOTION_NONE), [1]),
+    "q2_plunge": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0, elem="q2"),
+                  lambda: I.Motion.make(I.MOTION_PLUNGE, 100.0, 2.6e-4), [1, 3000, 6000]),
+    "q2_pitch_plunge": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0, elem="q2"),
+                        lambda: I.Motion.make(I.MOTION_PITCH_PLUNGE, 0.0, -0.05, 1e-4, 250.0, 0.0, 100.0, 1e-4),
+                        [1, 5000, 12000]),
+    "q2_blended": (lambda: I.naca_omesh(96, 30, chord=1000.0, R=20000.0, first=1.0, elem="q2"),
+                   lambda: I.Motion.make(I.MOTION_BLENDED_PITCH, -0.002, -0.0436, 7.8e-5, 250.0, 0.0, 2000.0, 10000.0),
+                   [1, 10000, 20000]),
+    "q2_channel_static": (lambda: I.wall_channel(first=1.0, growth=1.0, elem="q2"),
+                          lambda: I.Motion.make(I.MOTION_NONE), [1]),
+    "q2_channel_plunge": (lambda: I.wall_channel(elem="q2"), lambda: I.Motion.make(I.MOTION_PLUNGE, 2.0, 0.02),
+                          [1, 40]),
+})
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -84,7 +108,7 @@ def test_fp32_filter_never_accepts_a_point_that_is_not_strictly_inside():
         assert got[easy].sum() >= 0.99 * easy.sum()  # and it does decide the clear-cut ones
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("name", sorted(k for k in CASES if not k.startswith("q2_")))
 def test_fast_path_decisions_match_oracle(name):
     """The FP32-deviation propagation's decisions (previous-step element
     verified in FP32 with certified bounds, exact walk otherwise), run on the
@@ -98,7 +122,9 @@ def test_fast_path_decisions_match_oracle(name):
         eo, ko = o.locate(float(t))
         assert np.array_equal(e, eo), f"{name} t={t}: {np.sum(e != eo)} differ"
         assert np.array_equal(k, ko)
-        if name != "lattice":  # on the lattice every departure point is a node
+        # on the lattice every departure point is a node; the small channel
+        # is mostly wall layers, where the exact path decides
+        if name != "lattice" and not name.startswith("channel"):
             assert fast.mean() > 0.8, f"{name}: only {fast.mean():.3f} settled by the fast path"
 
 
