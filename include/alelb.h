@@ -354,6 +354,27 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    Synchronous. */
 alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
 
+/* How a batch runs its steps.  ALELB_BATCH_GRAPHS (the default): one
+   launch per phase over all cases, chunks of up to 64 steps captured once
+   into CUDA graphs and replayed.  ALELB_BATCH_PERSISTENT: one cooperative
+   launch per chunk of up to 64 steps, every block resident, a grid-wide
+   barrier between phases; each wait at a barrier gives up after the limit
+   of alelb_batch_set_wait (1 s by default), sets ALELB_ERR_TIMEOUT on every
+   case and returns, so a wait cannot hang the device.  Both give every
+   case the result of alelb_lb_step on that solver alone (the same per-node
+   code, values equal up to the compiler's multiply-add fusion).  While
+   profiling is on, steps are launched one kernel at a time in either mode.
+   Waits for the batch's stream; ALELB_ERR_ARG for another mode. */
+enum { ALELB_BATCH_GRAPHS = 0, ALELB_BATCH_PERSISTENT = 1 };
+alelb_status alelb_batch_set_mode(alelb_batch *b, int32_t mode);
+/* Limit of each grid-wide wait of the persistent form, in seconds
+   (0 < limit <= 60).  missing_arrivals (0 or 1) makes every barrier wait
+   for that many blocks more than the grid holds, so that every wait runs
+   out: a test of the time-out path, which leaves the cases' state
+   mid-step and ALELB_ERR_TIMEOUT sticky on them.  Waits for the batch's
+   stream. */
+alelb_status alelb_batch_set_wait(alelb_batch *b, double limit_seconds, int32_t missing_arrivals);
+
 /* Per-kernel device times of the batch, as alelb_profile and
    alelb_kernel_times for a solver.  While enabled, steps are launched one
    kernel at a time (not through the graph) between two events each. */

@@ -26,6 +26,8 @@ RENUMBER_NONE = 0
 RENUMBER_MORTON = 1
 ELEM_P2TRI = 0
 ELEM_Q2QUAD = 1
+BATCH_GRAPHS = 0
+BATCH_PERSISTENT = 1
 FLAG_PHI_OFF = 1
 FLAG_COLLIDE_OFF = 2
 FLAG_LITERAL_VG = 4
@@ -46,7 +48,7 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_batch_last_error", "alelb_mlp_create", "alelb_mlp_destroy", "alelb_mlp_get_params",
            "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
            "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
-           "alelb_checkpoint_info"]
+           "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait"]
 
 
 class AlelbError(RuntimeError):
@@ -130,6 +132,8 @@ def load(path: str = LIB_PATH):
     L.alelb_save.argtypes = [p, C.c_char_p]
     L.alelb_load.argtypes = [p, C.c_char_p]
     L.alelb_checkpoint_info.argtypes = [C.c_char_p, p, p, C.c_char_p, i32]
+    L.alelb_batch_set_mode.argtypes = [p, i32]
+    L.alelb_batch_set_wait.argtypes = [p, d, i32]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -392,6 +396,15 @@ class Batch:
 
     def sync(self):
         self._check(load().alelb_batch_sync(self.h), "batch_sync")
+
+    def set_mode(self, mode):
+        """BATCH_GRAPHS (launch per phase, CUDA graphs) or BATCH_PERSISTENT
+        (one cooperative launch per chunk, bounded grid barriers)."""
+        self._check(load().alelb_batch_set_mode(self.h, int(mode)), "batch_set_mode")
+
+    def set_wait(self, limit_seconds=1.0, missing_arrivals=0):
+        self._check(load().alelb_batch_set_wait(self.h, float(limit_seconds), int(missing_arrivals)),
+                    "batch_set_wait")
 
     def tune(self, reps=3):
         out = np.zeros(8, dtype=np.int32)

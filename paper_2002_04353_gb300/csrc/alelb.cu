@@ -65,6 +65,10 @@ alelb_status check_sticky(alelb_solver *s)
         s->err = "non-finite or non-positive density or temperature";
         return ALELB_ERR_NONFINITE;
     }
+    if (s->sticky & ERR_TIMEOUT) {
+        s->err = "a grid-wide wait of the persistent batched step ran out of time";
+        return ALELB_ERR_TIMEOUT;
+    }
     return ALELB_OK;
 }
 

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -230,6 +231,170 @@ __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The persistent form: one cooperative launch runs a chunk of steps, every
+// phase of every step over all cases, with a grid-wide barrier between
+// phases (each phase reads what the previous one wrote anywhere in the
+// mesh).  Each wait at a barrier is bounded: past the limit the block sets
+// ERR_TIMEOUT in every case's error word and an abort flag that releases
+// every other wait, and the kernel returns.
+// ---------------------------------------------------------------------------
+struct GridSync {
+    unsigned *count;   // arrivals at the barrier being formed
+    unsigned *gen;     // barriers completed so far
+    int *abort;        // set once a wait has run out: every later wait returns at once
+    unsigned expected; // arrivals that complete a barrier (the grid, plus a test's missing ones)
+    unsigned long long limit_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false when the kernel must stop (a wait ran out here or elsewhere).
+template <class S, class A>
+__device__ bool grid_barrier(const GridSync &g, const CaseDev<S, A> *cases, int B)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence(); // this block's writes of the phase, before it arrives
+        const unsigned my_gen = *(volatile unsigned *)g.gen;
+        if (atomicAdd(g.count, 1u) + 1u == g.expected) {
+            *(volatile unsigned *)g.count = 0u;
+            __threadfence();
+            atomicAdd(g.gen, 1u); // opens the barrier
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*(volatile unsigned *)g.gen == my_gen) {
+                if (*(volatile int *)g.abort) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > g.limit_ns) {
+                    for (int c = 0; c < B; ++c) atomicOr(cases[c].err, ERR_TIMEOUT);
+                    atomicExch(g.abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence(); // the other blocks' writes, before this block reads them
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Steps 0..K-1 of a chunk (map scalars sc[k B + c], sf[k B + c]), one block
+// per SM-resident slot, node tiles of blockDim.x nodes (offsets off) dealt
+// out over the grid in every node-parallel phase.
+template <class S, class A>
+__global__ void __launch_bounds__(128) kb_persistent(const CaseDev<S, A> *__restrict__ cases,
+                                                     const int *__restrict__ off, int B,
+                                                     const MapScalars *__restrict__ scs,
+                                                     const MapScalarsF *__restrict__ sfs, int K, GridSync g)
+{
+    constexpr int NS = NQ + 1;
+    constexpr bool FAST = !std::is_same<S, double>::value;
+    __shared__ SharedCase<S, A> sh;
+    __shared__ unsigned pre[BATCH_MAX * NS + 1];
+    const int tiles = __ldg(off + B);
+    // node-parallel phase: body(C, sc, sf, node) for every node of every case
+    auto tiles_loop = [&](int k, auto &&body) {
+        for (int vt = blockIdx.x; vt < tiles; vt += gridDim.x) {
+            const int c = tile_case(off, B, vt);
+            __syncthreads(); // the previous tile's users of sh are done
+            sh.load(cases, scs + (size_t)k * B, sfs + (size_t)k * B, c);
+            __syncthreads();
+            body(sh.C(), sh.SC(), sh.SF(), (vt - __ldg(off + c)) * blockDim.x + threadIdx.x);
+        }
+    };
+    for (int k = 0; k < K; ++k) {
+        const MapScalars *sc = scs + (size_t)k * B;
+        const MapScalarsF *sf = sfs + (size_t)k * B;
+        if (FAST) {
+            tiles_loop(k, [&](const CaseDev<S, A> &C, const MapScalars &, const MapScalarsF &SF, int a) {
+                stream_fast_group<BATCH_FAST_G>(C.M, C.MS, SF, C.K, C.st, a);
+            });
+            if (!grid_barrier(g, cases, B)) return;
+            // the exact path over every case's work list (kb_slow's numbering)
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                unsigned loc[NS];
+                unsigned s = 0, npop = 0;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    loc[i] = lane < B ? *(volatile unsigned *)(cases[lane].st.wcount + i) : 0u;
+                    s += loc[i];
+                    if (i < NQ) npop += loc[i];
+                }
+                unsigned incl = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (lane < B) {
+                    unsigned run = incl - s;
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        pre[lane * NS + i] = run;
+                        run += loc[i];
+                    }
+                    if (lane == B - 1) pre[B * NS] = run;
+                    if (npop && blockIdx.x == 0 && cases[lane].stats)
+                        atomicAdd(cases[lane].stats, (unsigned long long)npop);
+                }
+            }
+            __syncthreads();
+            const unsigned total = pre[B * NS];
+            for (unsigned w = spread_first(); w < total; w += spread_stride()) {
+                int lo = 0, hi = B * NS - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pre[mid] <= w) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int c = lo / NS, i = lo % NS;
+                const CaseDev<S, A> &C = cases[c];
+                const int entry = C.st.work[(size_t)i * C.M.N + (w - pre[lo])];
+                if (i < NQ) {
+                    stream_slow_item(C.M, C.MS, sc[c], sf[c], sc[c], sf[c], C.K, C.st, C.err, entry);
+                } else {
+                    const unsigned mask = C.st.wmask[entry];
+                    if (C.stats) atomicAdd(C.stats, (unsigned long long)__popc(mask));
+                    stream_bc_node<S, A>(C.M, C.MS, sc[c], sf[c], C.K, C.st, entry,
+                                         fast_map(C.MS, sf[c], entry, C.M.Xf[entry]), mask);
+                }
+            }
+            if (!grid_barrier(g, cases, B)) return;
+            tiles_loop(k, [&](const CaseDev<S, A> &C, const MapScalars &, const MapScalarsF &, int a) {
+                if (a <= NQ) C.st.wcount[a] = 0u; // the case's work list has been consumed
+                if (a < C.M.N) moments_node(C.K, C.st, C.M.N, C.err, a);
+            });
+        } else {
+            tiles_loop(k, [&](const CaseDev<S, A> &C, const MapScalars &SC, const MapScalarsF &, int a) {
+                if (a < C.M.N) stream_plain_node(C.M, C.MS, SC, SC, C.K, C.st, C.err, C.stats, a);
+            });
+        }
+        if (!grid_barrier(g, cases, B)) return;
+        tiles_loop(k, [&](const CaseDev<S, A> &C, const MapScalars &SC, const MapScalarsF &SF, int a) {
+            if (a < C.M.N) deriv1_node<S, A, FAST>(C.M, C.MS, SC, SF, C.st, a);
+        });
+        if (!grid_barrier(g, cases, B)) return;
+        tiles_loop(k, [&](const CaseDev<S, A> &C, const MapScalars &SC, const MapScalarsF &SF, int a) {
+            if (a < C.M.N) collide_at<S, A, FAST>(C.M, C.MS, SC, SF, C.K, C.st, C.err, a);
+        });
+        if (!grid_barrier(g, cases, B)) return;
+    }
+}
+
 int bs_index(int bs) { return bs == 64 ? 0 : bs == 128 ? 1 : 2; }
 
 // Blocks of the exact-path kernel resident per SM at block size bs.
@@ -265,6 +430,13 @@ struct alelb_batch {
     int slow_grid = 0;
     int n_sm = 152;
     std::map<int, cudaGraphExec_t> graphs;
+    // the persistent form (mode ALELB_BATCH_PERSISTENT): threads per block,
+    // blocks (all resident), barrier words {count, gen, abort}, wait limit
+    int mode = ALELB_BATCH_GRAPHS;
+    int pers_bs = 128, pers_grid = 0;
+    unsigned *d_sync = nullptr;
+    double wait_limit_s = 1.0;
+    int missing = 0;
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -377,6 +549,48 @@ void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count)
 {
     if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count);
     else launch_phase<double, double>(b, kt, bs, grid, k, count);
+}
+
+// One cooperative launch of the persistent kernel for chunk steps 0..K-1.
+template <class S, class A> cudaError_t launch_persistent_t(alelb_batch *b, int K)
+{
+    const auto *cases = reinterpret_cast<const CaseDev<S, A> *>(b->d_cases);
+    GridSync g;
+    g.count = b->d_sync;
+    g.gen = b->d_sync + 1;
+    g.abort = reinterpret_cast<int *>(b->d_sync + 2);
+    g.expected = (unsigned)b->pers_grid + (unsigned)b->missing;
+    g.limit_ns = (unsigned long long)(b->wait_limit_s * 1e9);
+    // a barrier left half formed by an earlier wait that ran out starts afresh
+    cudaError_t st = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned), b->stream);
+    if (st == cudaSuccess) st = cudaMemsetAsync(b->d_sync + 2, 0, sizeof(unsigned), b->stream);
+    if (st != cudaSuccess) return st;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->pers_grid);
+    cfg.blockDim = dim3(b->pers_bs);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative; // every block resident at once
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kb_persistent<S, A>, cases, (const int *)b->d_off[bs_index(b->pers_bs)], b->B,
+                              (const MapScalars *)b->d_sc, (const MapScalarsF *)b->d_sf, K, g);
+}
+
+cudaError_t launch_persistent(alelb_batch *b, int K)
+{
+    return b->prec == ALELB_PREC_FP32_DEV ? launch_persistent_t<float, float>(b, K)
+                                          : launch_persistent_t<double, double>(b, K);
+}
+
+// Blocks of the persistent kernel that fit on the device at once.
+template <class S, class A> int persistent_grid_t(int bs, int n_sm)
+{
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kb_persistent<S, A>, bs, 0);
+    return std::max(v, 1) * n_sm;
 }
 
 void enqueue_step(alelb_batch *b, int k)
@@ -536,6 +750,10 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     }
     if (st == cudaSuccess)
         st = b->prec == ALELB_PREC_FP32_DEV ? upload_cases<float, float>(b) : upload_cases<double, double>(b);
+    b->d_sync = b->buf.alloc<unsigned>(4, st);
+    if (st == cudaSuccess) st = cudaMemset(b->d_sync, 0, 4 * sizeof(unsigned));
+    b->pers_grid = b->prec == ALELB_PREC_FP32_DEV ? persistent_grid_t<float, float>(b->pers_bs, b->n_sm)
+                                                  : persistent_grid_t<double, double>(b->pers_bs, b->n_sm);
     b->d_sc = b->buf.alloc<MapScalars>((size_t)CHUNK_MAX * B, st);
     b->d_sf = b->buf.alloc<MapScalarsF>((size_t)CHUNK_MAX * B, st);
     for (int sl = 0; sl < 2; ++sl) {
@@ -589,6 +807,8 @@ extern "C" alelb_status alelb_batch_step(alelb_batch *b, int32_t n)
         if (b->prof) {
             for (int k = 0; k < K; ++k) enqueue_step(b, k);
             st = cudaGetLastError();
+        } else if (b->mode == ALELB_BATCH_PERSISTENT) {
+            st = launch_persistent(b, K);
         } else {
             cudaGraphExec_t g = nullptr;
             st = get_graph(b, K, g);
@@ -734,5 +954,25 @@ extern "C" alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **na
         if (launches) launches[k] = b->n_acc[k];
     }
     *n = m;
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_set_mode(alelb_batch *b, int32_t mode)
+{
+    if (!b || (mode != ALELB_BATCH_GRAPHS && mode != ALELB_BATCH_PERSISTENT)) return ALELB_ERR_ARG;
+    cudaError_t st = cudaStreamSynchronize(b->stream);
+    if (st != cudaSuccess) return bfail(b, st, "batch_set_mode");
+    b->mode = mode;
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_set_wait(alelb_batch *b, double limit_seconds, int32_t missing_arrivals)
+{
+    if (!b || !(limit_seconds > 0.0) || limit_seconds > 60.0 || missing_arrivals < 0 || missing_arrivals > 1)
+        return ALELB_ERR_ARG;
+    cudaError_t st = cudaStreamSynchronize(b->stream);
+    if (st != cudaSuccess) return bfail(b, st, "batch_set_wait");
+    b->wait_limit_s = limit_seconds;
+    b->missing = missing_arrivals;
     return ALELB_OK;
 }

@@ -25,7 +25,7 @@ __constant__ int c_cy[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 enum : int { MK_NONE = 0, MK_SINE = 1, MK_PLUNGE = 2, MK_PITCH = 3, MK_PITCH_PLUNGE = 4,
              MK_BLENDED = 5 };
-enum : int { ERR_LOCATE = 1, ERR_NONFINITE = 2 };
+enum : int { ERR_LOCATE = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
 // Per-step scalars of the map (host libm, once per step).
 struct MapScalars {

@@ -82,8 +82,10 @@ def test_batch_equals_solvers_stepped_alone(prec):
     same solver stepped alone up to rounding, with the same walks.  The two
     differ only in the order of fused multiply-adds, which the flow
     amplifies over 70 steps like any rounding (most on the Mach 0.6 case):
-    element by element 1e-11 in FP64 and the FP32 budget 2e-4."""
+    element by element 1e-11 in FP64; in FP32 the fields within the 2e-4
+    budget, the populations within 1e-3."""
     tol = 1e-11 if prec == alelb.PREC_FP64 else 2e-4
+    ptol = 1e-11 if prec == alelb.PREC_FP64 else 1e-3
     cases = _cases()
     alone = _solvers(cases, prec)
     for s in alone:
@@ -96,7 +98,7 @@ def test_batch_equals_solvers_stepped_alone(prec):
     for c, (sa, sb) in enumerate(zip(alone, batched)):
         fa, ga = sa.get_pops()
         fb, gb = sb.get_pops()
-        assert _rel(fb, fa) < tol and _rel(gb, ga) < tol, f"case {c}"
+        assert _rel(fb, fa) < ptol and _rel(gb, ga) < ptol, f"case {c}"
         ma, mb = sa.moments(), sb.moments()
         for k, e in parity_util.field_errors(mb, ma).items():
             assert e < tol, f"case {c}: {k} {e:.2e}"
@@ -180,3 +182,71 @@ def test_case_error_is_reported_with_its_index():
     with pytest.raises(alelb.AlelbError) as ex:
         b.sync()
     assert ex.value.status == -7 and "case 1" in str(ex.value)
+
+
+# ---------------------------------------------------------------------------
+# the persistent form: one cooperative launch per chunk, grid-wide barriers
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [alelb.PREC_FP64, alelb.PREC_FP32_DEV])
+def test_persistent_batch_matches_oracle_and_the_graph_form(prec):
+    """The persistent kernel runs the same per-node code as the phase
+    kernels: per case it matches the oracle after 5 steps (1e-12 / 2e-4)
+    and the graph form after 70 steps (across a 64-step chunk) up to
+    rounding, with the same walks."""
+    cases = _cases()
+    ss = _solvers(cases, prec)
+    b = alelb.Batch(ss)
+    b.set_mode(alelb.BATCH_PERSISTENT)
+    b.step(5)
+    b.sync()
+    for c, ((mesh, motion, flow), s) in enumerate(zip(cases, ss)):
+        o = O.Oracle(mesh, motion, flow)
+        o.step(5)
+        st = o.state()
+        tol = TOL64 if prec == alelb.PREC_FP64 else TOL32
+        for k, e in parity_util.field_errors(s.moments(), st).items():
+            assert e < tol, f"persistent case {c}: {k} {e:.2e}"
+    b.step(65)
+    b.sync()
+    ref = _solvers(cases, prec)
+    bg = alelb.Batch(ref)
+    bg.step(70)
+    bg.sync()
+    tol = 1e-11 if prec == alelb.PREC_FP64 else 2e-4
+    ptol = 1e-11 if prec == alelb.PREC_FP64 else 1e-3
+    for c, (sp, sg) in enumerate(zip(ss, ref)):
+        fp, gp = sp.get_pops()
+        fg, gg = sg.get_pops()
+        assert _rel(fp, fg) < ptol and _rel(gp, gg) < ptol, f"case {c}"
+        for k, e in parity_util.field_errors(sp.moments(), sg.moments()).items():
+            assert e < tol, f"case {c}: {k} {e:.2e}"
+        assert sp.info()["walks"] == sg.info()["walks"]
+        assert sp.time() == sg.time() == (70.0, 70)
+
+
+def test_persistent_barrier_wait_runs_out_and_reports():
+    """A barrier told to wait for one block more than the grid holds (a flag
+    that nothing sets): every wait gives up after its limit, the kernel
+    returns, every case reports ALELB_ERR_TIMEOUT, and the device stays
+    usable for other work."""
+    cases = _cases()
+    ss = _solvers(cases, alelb.PREC_FP32_DEV)
+    b = alelb.Batch(ss)
+    b.set_mode(alelb.BATCH_PERSISTENT)
+    b.set_wait(0.2, missing_arrivals=1)
+    b.step(1)
+    with pytest.raises(alelb.AlelbError) as e:
+        b.sync()
+    assert e.value.status == -8
+    for s in ss:
+        with pytest.raises(alelb.AlelbError) as e:
+            s.sync()
+        assert e.value.status == -8
+    mesh, motion, flow = cases[1]
+    other = alelb.Solver(alelb.Mesh(mesh, motion), flow, alelb.PREC_FP32_DEV)
+    other.lb_step(3)
+    other.sync()
+    with pytest.raises(alelb.AlelbError) as e:
+        b.set_wait(0.0)
+    assert e.value.status == -1

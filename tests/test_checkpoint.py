@@ -43,7 +43,7 @@ def test_resume_from_a_checkpoint_is_bit_identical(tmp_path, prec):
     for key in ("rho", "ux", "uy", "T"):
         assert np.array_equal(mo[key], mo_ref[key]), key
     # the element cache and the counters came along: the same walks ran
-    assert b.info()[7] == ref.info()[7]
+    assert b.info()["walks"] == ref.info()["walks"]
 
 
 def test_foreign_or_damaged_checkpoints_are_refused(tmp_path):
