@@ -318,7 +318,7 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     batched kernels' rooflines and the end-to-end figure (host-resident
     state through the C-ABI)."""
     from paper_2002_04353_gb300 import shard
-    sweep = I.batched_sweep()
+    sweep = I.batched_sweep(scale=args.sweep_scale)
     mine = shard.assign_cases([c.mesh.n_nodes for c in sweep], world)[rank]
     cases = [sweep[k] for k in mine]
     meshes = [alelb.Mesh(c.mesh, c.motion) for c in cases]
@@ -361,6 +361,22 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     b.step(20)
     kt = b.kernel_times()
     b.profile(False)
+    # the persistent form (one cooperative launch per chunk of 64 steps,
+    # grid-wide barriers between phases) over the same number of steps
+    persistent = None
+    if not args.no_persistent:
+        b.set_mode(alelb.BATCH_PERSISTENT)
+        b.step(3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msp = shard.max_over_ranks(e0.elapsed_time(e1), torch, dev)
+        b.set_mode(alelb.BATCH_GRAPHS)
+        persistent = {"value": n_total * K / (msp * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": msp / K, "steps": K,
+                      "note": "same sweep and steps, one cooperative launch per 64-step chunk with grid-wide "
+                              "barriers between phases"}
     kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt.items() if v[1]}
     rl = {}  # the phase kernels carry the single-case names (kb_fast runs as k_stream_fast, ...)
     for k, v in kernels.items():
@@ -410,7 +426,7 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
             "exact_path_per_step": n_exact,
             "cases_on_shifted_lattice": sum(1 for fl in flows if any(fl.shift)), "tuned_launch_shapes": choice,
             "kernels": kernels, "kernel_rooflines": rl, "method_bytes_per_step": method_bytes(n_nodes, n_elems),
-            "e2e": e2e, "clocks": clocks, "gpu_launches": 5 * K}
+            "persistent_form": persistent, "e2e": e2e, "clocks": clocks, "gpu_launches": 5 * K}
 
 
 def run_learned(alelb, torch, dev, args):
@@ -852,6 +868,9 @@ def main():
     ap.add_argument("--prec-mach", type=float, default=0.75)
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-forces", action="store_true")
+    ap.add_argument("--no-persistent", action="store_true")
+    ap.add_argument("--sweep-scale", type=float, default=1.0,
+                    help="node counts of the sweep's cases times this (1: the workload; smaller for counter captures)")
     ap.add_argument("--only-batched", action="store_true",
                     help="the headline alone (no single case, e2e, network, precision, forces, CPU baseline)")
     args = ap.parse_args()

@@ -1086,16 +1086,19 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         // FP64 rounding of the canonical departure point), u/2 on each J
         // entry, the products, the sums and the additions to the node's
         // coordinates
-        const float xl[6] = {0.0f, 1.0f, 0.0f, 0.5f, 0.5f, 0.0f};
-        const float el[6] = {0.0f, 0.0f, 1.0f, 0.0f, 0.5f, 0.5f};
+        // local coordinates of node l, twice over, as 2-bit fields of one
+        // word ({0, 2, 0, 1, 1, 0} and {0, 0, 2, 0, 1, 1}): a run-time index
+        // into a constant array would put the array in local memory
+        const float xl = 0.5f * (float)((0x148u >> (2 * l)) & 3u);
+        const float el = 0.5f * (float)((0x520u >> (2 * l)) & 3u);
         const float rx = -chx, ry = -chy;
         const float t11 = J.x * rx, t12 = J.y * ry, t21 = J.z * rx, t22 = J.w * ry;
         const float T1 = t11 + t12, T2 = t21 + t22;
-        xi = xl[l] + T1;
-        eta = el[l] + T2;
+        xi = xl + T1;
+        eta = el + T2;
         // the third coordinate from its exact value at the node minus the
         // offsets (1 - xi - eta would cancel at nodes where it is zero)
-        const float l0 = (1.0f - xl[l] - el[l]) - (T1 + T2);
+        const float l0 = (1.0f - xl - el) - (T1 + T2);
         const float eq = F.eq(i);
         const float S1 = fabsf(J.x) + fabsf(J.y), S2 = fabsf(J.z) + fabsf(J.w);
         const float d1 = 2.0f * (S1 * eq + 3.0f * u * (fabsf(t11) + fabsf(t12)));
@@ -1106,22 +1109,10 @@ ALELB_HD __forceinline__ bool fast_decide(const MeshDev &M, const FastMap &F, fl
         return xi > m1 && eta > m2 && l0 > m0;
     }
     const float4 ed = M.ejf[2 * e];
-    float dx, dy; // node position relative to v0
-    if (l >= 0) {
-        const float wx[3] = {0.0f, ed.x, ed.z}, wy[3] = {0.0f, ed.y, ed.w};
-        if (l < 3) {
-            dx = wx[l];
-            dy = wy[l];
-        } else {
-            const int k0 = l - 3, k1 = (k0 + 1) % 3;
-            dx = 0.5f * (wx[k0] + wx[k1]);
-            dy = 0.5f * (wy[k0] + wy[k1]);
-        }
-    } else {
-        const float4 v0 = M.v0f[e];
-        dx = (Xf.x - v0.x) + (Xf.z - v0.z);
-        dy = (Xf.y - v0.y) + (Xf.w - v0.w);
-    }
+    // node position relative to v0 (the node is not one of e's: l < 0 here)
+    const float4 v0 = M.v0f[e];
+    const float dx = (Xf.x - v0.x) + (Xf.z - v0.z);
+    const float dy = (Xf.y - v0.y) + (Xf.w - v0.w);
     const float qx = dx - chx, qy = dy - chy;
     const float E = fmaxf(fmaxf(fabsf(ed.x), fabsf(ed.y)), fmaxf(fabsf(ed.z), fabsf(ed.w)));
     const float Q = fmaxf(fabsf(qx), fabsf(qy));

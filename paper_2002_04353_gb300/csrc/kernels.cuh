@@ -636,8 +636,14 @@ __device__ __forceinline__ void stream_fast_group(const MeshDev &M, const MapSta
 #pragma unroll
         for (int j = 0; j < G; ++j) code[j] = stream_fast_pop(M, K, st, a, i0 + j, F, Xf, bd, c[j]);
     }
+    // most warps list nothing: one vote spares them the appends' ballots
+    int any = 0;
 #pragma unroll
-    for (int j = 0; j < G; ++j) append_pop(st, a, M.N, i0 + j, code[j]);
+    for (int j = 0; j < G; ++j) any |= code[j];
+    if (__any_sync(0xffffffffu, any != 0)) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) append_pop(st, a, M.N, i0 + j, code[j]);
+    }
 }
 
 // Threads per block of the single-case propagation kernel.
