@@ -606,6 +606,55 @@ def run_precision(alelb, torch, dev, args, Ma, shift=(0.0, 0.0), flags=0):
             **out}
 
 
+def run_precision_growth(alelb, args):
+    """How the flow amplifies rounding: on the 150,400-node plunge (paper's
+    wall targets, and off-wall targets at the mesh velocity, R8c) and the
+    600,320-node blended pitch at Mach 0.3, three runs from the same start
+    -- FP64, FP64 with every f population changed in its last bit, and the
+    FP32-deviation form -- compared at several step counts: the largest of
+    the field errors (rho and T relative per node, u relative to the
+    largest speed) of FP32 against FP64 and of the perturbed FP64 run
+    against FP64.  When their ratio stays near the ratio of the formats'
+    unit roundoffs, the FP32 difference is rounding amplified by the flow."""
+    def field_err(mo, ref):
+        umax = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+        return max(float((np.abs(mo["rho"] - ref["rho"]) / ref["rho"]).max()),
+                   float(np.abs(mo["ux"] - ref["ux"]).max() / umax),
+                   float(np.abs(mo["uy"] - ref["uy"]).max() / umax),
+                   float((np.abs(mo["T"] - ref["T"]) / ref["T"]).max()))
+
+    out = {}
+    runs = (("plunge150k_paper", I.plunge_case(), 0, (20, 100, 200, 300, 500)),
+            ("plunge150k_R8c", I.plunge_case(), alelb.FLAG_OFFWALL_VG, (20, 200, 1000, 2000)),
+            ("pitch600k_ma03", I.pitch_case(Ma=0.3), 0, (20, 50, 100, 150, 220)))
+    for name, case, flags, marks in runs:
+        fl = dataclasses.replace(case.flow, flags=flags)
+        m = alelb.Mesh(case.mesh, case.motion)
+        sol = {k: alelb.Solver(m, fl, p) for k, p in (("fp64", alelb.PREC_FP64), ("fp64_perturbed", alelb.PREC_FP64),
+                                                        ("fp32_dev", alelb.PREC_FP32_DEV))}
+        for k, s in sol.items():
+            f, g = s.get_pops()
+            if k == "fp64_perturbed":
+                f = f * (1.0 + np.random.default_rng(0).choice([-1.0, 1.0], size=f.shape) * 2.0 ** -52)
+            s.set_pops(f, g, t=0.0)
+        rows, done = [], 0
+        for n in marks:
+            try:
+                for s in sol.values():
+                    s.lb_step(n - done)
+                mo = {k: s.moments() for k, s in sol.items()}
+            except alelb.AlelbError as e:
+                rows.append({"step": n, "diverged": str(e)})
+                break
+            done = n
+            a, b = field_err(mo["fp32_dev"], mo["fp64"]), field_err(mo["fp64_perturbed"], mo["fp64"])
+            rows.append({"step": n, "fp32_vs_fp64": a, "fp64_perturbed_vs_fp64": b, "ratio": a / max(b, 1e-300)})
+        for s in sol.values():
+            s.close()
+        out[name] = rows
+    return out
+
+
 def run_force_history(alelb, args):
     """Lift and drag histories over whole runs on the 150,400-node plunging
     and pitching NACA 0012 (Sec. V.B, V.C), FP32 populations, off-wall missing populations at
@@ -790,6 +839,7 @@ def run_ours(args):
     single = None if args.no_single else run_single(alelb, torch, dev, world, args)
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
     forces = None if (args.no_forces or world > 1) else run_force_history(alelb, args)
+    growth = None if (args.no_precision or world > 1) else run_precision_growth(alelb, args)
     precision = precision_low = None
     if not (args.no_precision or world > 1):
         # config 3 at its own Mach number: the shifted lattice of the transonic
@@ -838,6 +888,7 @@ def run_ours(args):
             "precision_study": precision,
             "force_history": forces,
             "precision_study_ma03": precision_low,
+            "precision_growth": growth,
             "e2e": bat["e2e"],
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,

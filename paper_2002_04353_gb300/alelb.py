@@ -412,6 +412,7 @@ class Batch:
         keys = ["k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide"]
         d = {k: int(out[i]) for i, k in enumerate(keys)}
         d["k_stream_slow_grid"] = int(out[6])
+        d["k_stream_fast_directions_per_thread"] = int(out[7])
         return d
 
     def profile(self, enable=True):

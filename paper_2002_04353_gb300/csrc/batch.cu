@@ -90,7 +90,9 @@ __global__ void __launch_bounds__(256) kb_stream(const CaseDev<S, A> *__restrict
     if (a < C.M.N) stream_plain_node(C.M, C.MS, sh.SC(), sh.SC(), C.K, C.st, C.err, count ? C.stats : nullptr, a);
 }
 
-template <class S, class A>
+// G directions per thread (grid y: 9 / G groups), chosen by the tuner:
+// one map evaluation per thread, fewer and longer load chains as G grows.
+template <class S, class A, int G>
 __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__ cases,
                                                const int *__restrict__ off, int B,
                                                const MapScalarsF *__restrict__ sf)
@@ -101,8 +103,7 @@ __global__ void __launch_bounds__(256) kb_fast(const CaseDev<S, A> *__restrict__
     sh.load(cases, nullptr, sf, c);
     __syncthreads();
     const CaseDev<S, A> &C = sh.C();
-    stream_fast_group<BATCH_FAST_G>(C.M, C.MS, sh.SF(), C.K, C.st,
-                                    (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x);
+    stream_fast_group<G>(C.M, C.MS, sh.SF(), C.K, C.st, (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x);
 }
 
 // The exact path over the work lists of all cases as one list, numbered
@@ -428,6 +429,7 @@ struct alelb_batch {
     // launch shapes (threads per block per kernel; blocks of k_stream_slow)
     int bs[KT_N] = {128, 128, 128, 256, 256, 128, 128};
     int slow_grid = 0;
+    int fast_g = BATCH_FAST_G; // directions per thread of k_stream_fast
     int n_sm = 152;
     std::map<int, cudaGraphExec_t> graphs;
     // the persistent form (mode ALELB_BATCH_PERSISTENT): threads per block,
@@ -512,7 +514,7 @@ int step_sequence(const alelb_batch *b, int seq[KT_N])
 // One phase kernel over all cases with the scalars of chunk step k.
 // bs: threads per block; grid: blocks (k_stream_slow only).
 template <class S, class A>
-void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count)
+void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g)
 {
     const auto *cases = reinterpret_cast<const CaseDev<S, A> *>(b->d_cases);
     const int q = bs_index(bs);
@@ -527,7 +529,12 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count)
         launch_pdl(kb_stream<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, count);
         break;
     case KT_FAST:
-        launch_pdl(kb_fast<S, A>, dim3(tiles, NQ / BATCH_FAST_G), dim3(bs), b->stream, cases, off, B, sf);
+        if (fast_g == 1)
+            launch_pdl(kb_fast<S, A, 1>, dim3(tiles, NQ), dim3(bs), b->stream, cases, off, B, sf);
+        else if (fast_g == 3)
+            launch_pdl(kb_fast<S, A, 3>, dim3(tiles, NQ / 3), dim3(bs), b->stream, cases, off, B, sf);
+        else
+            launch_pdl(kb_fast<S, A, 9>, dim3(tiles, 1), dim3(bs), b->stream, cases, off, B, sf);
         break;
     case KT_SLOW:
         launch_pdl(kb_slow<S, A>, dim3(grid), dim3(bs), b->stream, cases, B, sc, sf, count);
@@ -545,10 +552,10 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count)
     }
 }
 
-void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count)
+void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g)
 {
-    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count);
-    else launch_phase<double, double>(b, kt, bs, grid, k, count);
+    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count, fast_g);
+    else launch_phase<double, double>(b, kt, bs, grid, k, count, fast_g);
 }
 
 // One cooperative launch of the persistent kernel for chunk steps 0..K-1.
@@ -605,7 +612,7 @@ void enqueue_step(alelb_batch *b, int k)
             eb = bget_event(b);
             cudaEventRecord(ea, b->stream);
         }
-        launch_kernel(b, kt, b->bs[kt], b->slow_grid, k, 1);
+        launch_kernel(b, kt, b->bs[kt], b->slow_grid, k, 1, b->fast_g);
         if (b->prof) {
             cudaEventRecord(eb, b->stream);
             b->pending.push_back({kt, ea, eb});
@@ -869,25 +876,27 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     };
     for (int q = 0; q < ns && st == cudaSuccess; ++q) {
         const int kt = seq[q];
-        struct Cand { int bs, grid; };
+        struct Cand { int bs, grid, g; };
         std::vector<Cand> cands;
         for (int bsq = 0; bsq < N_BS; ++bsq) {
             const int bs = 64 << bsq;
             if (kt == KT_SLOW) {
-                for (int gm = 1; gm <= 16; gm *= 2) cands.push_back({bs, gm * b->n_sm});
-                cands.push_back({bs, slow_resident(b, bs) * b->n_sm}); // one wave
+                for (int gm = 1; gm <= 16; gm *= 2) cands.push_back({bs, gm * b->n_sm, b->fast_g});
+                cands.push_back({bs, slow_resident(b, bs) * b->n_sm, b->fast_g}); // one wave
+            } else if (kt == KT_FAST) {
+                for (int g : {1, 3, 9}) cands.push_back({bs, 0, g});
             } else {
-                cands.push_back({bs, 0});
+                cands.push_back({bs, 0, b->fast_g});
             }
         }
         float best = 1e30f;
-        Cand pick = {b->bs[kt], b->slow_grid};
+        Cand pick = {b->bs[kt], b->slow_grid, b->fast_g};
         for (const Cand &cd : cands) {
             float tmin = 1e30f;
             for (int r = 0; r < reps && st == cudaSuccess; ++r) {
                 if (kt == KT_FAST) clear();
                 st = cudaEventRecord(e0, b->stream);
-                launch_kernel(b, kt, cd.bs, cd.grid, 0, 0);
+                launch_kernel(b, kt, cd.bs, cd.grid, 0, 0, cd.g);
                 if (st == cudaSuccess) st = cudaGetLastError();
                 if (st == cudaSuccess) st = cudaEventRecord(e1, b->stream);
                 if (st == cudaSuccess) st = cudaEventSynchronize(e1);
@@ -903,9 +912,10 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
         if (st != cudaSuccess) break;
         b->bs[kt] = pick.bs;
         if (kt == KT_SLOW) b->slow_grid = pick.grid;
+        if (kt == KT_FAST) b->fast_g = pick.g;
         // the launch that counts (walk statistics) with the chosen shape
         if (kt == KT_FAST) clear();
-        launch_kernel(b, kt, pick.bs, pick.grid, 0, 1);
+        launch_kernel(b, kt, pick.bs, pick.grid, 0, 1, b->fast_g);
         st = cudaGetLastError();
     }
     cudaEventDestroy(e0);
@@ -922,7 +932,7 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     if (choice) {
         for (int k = 0; k < 6; ++k) choice[k] = b->bs[k];
         choice[6] = b->slow_grid;
-        choice[7] = 0;
+        choice[7] = b->fast_g;
     }
     return ALELB_OK;
 }

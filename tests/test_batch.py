@@ -117,6 +117,7 @@ def test_tuning_changes_no_value():
     assert all(choice[k] in (64, 128, 256) for k in ("k_stream_fast", "k_stream_slow", "k_moments",
                                                      "k_deriv1", "k_collide"))
     assert choice["k_stream_slow_grid"] > 0
+    assert choice["k_stream_fast_directions_per_thread"] in (1, 3, 9)
     bt.step(3)
     bp.sync()
     bt.sync()
