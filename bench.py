@@ -473,11 +473,30 @@ def run_learned(alelb, torch, dev, args):
     stream = torch.cuda.Stream(device=dev)
     res = {}
     pops = {}
+    def one_step(s):
+        """One step timed alone, with the proposal counters it moved."""
+        a0 = s.mlp_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            s.lb_step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        a1 = s.mlp_stats()
+        d = {k: a1[k] - a0[k] for k in a1}
+        return {"ms": e0.elapsed_time(e1), "exact_path": d["exact_path"], "proposed": d["proposed"],
+                "accepted": d["accepted"], "hit_rate": d["accepted"] / max(1, d["proposed"])}
+
     for label, use in (("without", False), ("with", True)):
         s = alelb.Solver(m5, c5.flow, alelb.PREC_FP32_DEV, stream=stream.cuda_stream)
         if use:
             s.set_mlp(net)
-        s.lb_step(max(3, args.warmup))
+        # the first step runs with an empty element cache: every population
+        # takes the exact path, where a proposal can save the walk
+        cold = one_step(s)
+        s.lb_step(max(3, args.warmup) - 1)
         s.sync()
         st0 = s.mlp_stats()
         K = args.mlp_steps
@@ -492,6 +511,11 @@ def run_learned(alelb, torch, dev, args):
         s.sync()
         ms = sum(a.elapsed_time(b) for a, b in evs)
         st1 = s.mlp_stats()
+        # a jump of the map time: the cached elements belong to another map
+        t_now = s.time()[0]
+        fj, gj = s.get_pops()
+        s.set_pops(fj, gj, t=t_now + 2000.0)
+        jump = one_step(s)
         s.profile(True)
         s.lb_step(3)
         kt = s.kernel_times()
@@ -500,7 +524,7 @@ def run_learned(alelb, torch, dev, args):
         prop = st1["proposed"] - st0["proposed"]
         acc = st1["accepted"] - st0["accepted"]
         res[label] = {"value": N * K / (ms * 1e-3) / 1e6, "ms_per_step": ms / K,
-                      "exact_path_per_step": exact / K,
+                      "exact_path_per_step": exact / K, "cold_cache_step": cold, "time_jump_step": jump,
                       "kernels": {k_: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]}
                                   for k_, v in kt.items() if v[1]}}
         if use:
@@ -805,6 +829,45 @@ def run_single(alelb, torch, dev, world, args):
     }
 
 
+def run_q2(alelb, torch, dev, args):
+    """The paper's own element: the 150,400-node plunging NACA 0012 O-mesh
+    of 9-node quadrilaterals (the same rings as the triangle mesh, each cell
+    kept whole), FP32-deviation and FP64 forms, L2 flushed before each
+    timed step.  Every population takes the exact path (FP64 departure
+    point, exact walk over quadrilaterals, Newton for Eq. NonLinear_Eq)."""
+    case = I.plunge_case(elem="q2")
+    mesh = alelb.Mesh(case.mesh, case.motion)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": case.name, "nodes": case.mesh.n_nodes, "elements": case.mesh.n_elems}
+    for label, prec in (("fp32_dev", alelb.PREC_FP32_DEV), ("fp64", alelb.PREC_FP64)):
+        s = alelb.Solver(mesh, case.flow, prec, stream=stream.cuda_stream)
+        s.lb_step(max(3, args.warmup))
+        s.sync()
+        K = args.q2_steps
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                s.lb_step(1)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        s.profile(True)
+        with torch.cuda.stream(stream):
+            s.lb_step(3)
+        torch.cuda.synchronize()
+        kt = s.kernel_times()
+        s.profile(False)
+        s.close()
+        out[label] = {"value": case.mesh.n_nodes * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K,
+                      "steps": K, "kernels": {k: {"ms_per_launch": v[0] / v[1]} for k, v in kt.items() if v[1]}}
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2002_04353_gb300 import alelb
@@ -837,6 +900,7 @@ def run_ours(args):
                "note": "the method's own bytes (populations once each way, derivative-pass fields, geometry)"}
 
     single = None if args.no_single else run_single(alelb, torch, dev, world, args)
+    q2 = None if (args.no_q2 or world > 1) else run_q2(alelb, torch, dev, args)
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
     forces = None if (args.no_forces or world > 1) else run_force_history(alelb, args)
     growth = None if (args.no_precision or world > 1) else run_precision_growth(alelb, args)
@@ -883,6 +947,7 @@ def run_ours(args):
             "fp64_plain": None if single is None else dict(single["fp64_plain"], workload=single["workload"]),
             "single_case": None if single is None else dict(single["fp32_dev"], workload=single["workload"],
                                                             e2e=single["e2e"]),
+            "q2_single_case": q2,
             "gpu_launches": bat["gpu_launches"],
             "learned_proposal": learned,
             "precision_study": precision,
@@ -920,13 +985,15 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-forces", action="store_true")
     ap.add_argument("--no-persistent", action="store_true")
+    ap.add_argument("--no-q2", action="store_true")
+    ap.add_argument("--q2-steps", type=int, default=10)
     ap.add_argument("--sweep-scale", type=float, default=1.0,
                     help="node counts of the sweep's cases times this (1: the workload; smaller for counter captures)")
     ap.add_argument("--only-batched", action="store_true",
                     help="the headline alone (no single case, e2e, network, precision, forces, CPU baseline)")
     args = ap.parse_args()
     if args.only_batched:
-        args.no_single = args.no_e2e = args.no_mlp = args.no_precision = args.no_forces = True
+        args.no_single = args.no_e2e = args.no_mlp = args.no_precision = args.no_forces = args.no_q2 = True
         args.no_cpu_baseline = True
     if args.impl == "reference":
         run_reference(args)

@@ -1312,7 +1312,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                                          const MapScalars &sc, const FastMap &F, float4 Xf, int a,
                                          int i, int literal, float &qx, float &qy, int &src,
                                          int *err, int hint = -1, int clear = -1,
-                                         const MapScalars *s1 = nullptr)
+                                         const MapScalars *s1 = nullptr, bool *hint_taken = nullptr)
 {
     const double2 Xa = M.X[a];
     src = -1;
@@ -1362,6 +1362,7 @@ ALELB_HD __forceinline__ Loc slow_decide(const MeshDev &M, const MapStatic &MS,
                             if (o2 >= 0) {
                                 L = finish_loc(M, ce, 0, 0, o0, o1, o2);
                                 have = true;
+                                if (hint_taken) *hint_taken = true;
                             }
                         }
                     }

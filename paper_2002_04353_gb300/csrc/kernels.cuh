@@ -735,8 +735,14 @@ __device__ __forceinline__ void stream_slow_item(const MeshDev &M, const MapStat
             src = -1;
             if (hits) atomicAdd(hits, 1ull);
         } else {
-            L = slow_decide(M, MS, scd, F, Xf, a, i, literal, qx, qy, src, err, hint, clear,
-                            exact_char ? &sc : nullptr);
+            // the exact check runs on the previous-step element, or, when
+            // there is none (a cold cache), on the proposal: the element it
+            // accepts is the one the walk would reach
+            bool taken = false;
+            const bool use_prop = hint < 0 && pc >= 0;
+            L = slow_decide(M, MS, scd, F, Xf, a, i, literal, qx, qy, src, err, use_prop ? pc : hint, clear,
+                            exact_char ? &sc : nullptr, use_prop ? &taken : nullptr);
+            if (taken && hits) atomicAdd(hits, 1ull);
         }
         A fi = 0, gi = 0;
         if (src >= 0) {

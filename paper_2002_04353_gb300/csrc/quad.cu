@@ -61,10 +61,10 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
             } else if (L.vnode >= 0) {
                 src = L.vnode;
             } else {
-                double xi, eta;
-                if (!quad_local(M, L.e, L.sx, L.sy, px, py, xi, eta)) set_err(err, ERR_LOCATE);
+                A xi, eta;
+                if (!quad_local<A>(M, L.e, L.sx, L.sy, px, py, xi, eta)) set_err(err, ERR_LOCATE);
                 A Nw[9];
-                shape9<A>((A)xi, (A)eta, Nw);
+                shape9<A>(xi, eta, Nw);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
                     const int b = M.conn[9 * L.e + k];

@@ -40,26 +40,43 @@ ALELB_HD __forceinline__ void quad_bilinear(const double w[8], double xi, double
 }
 
 // Newton's method on Eq. NonLinear_Eq for corners c taken relative to the
-// point (so the root is x(xi, eta) = 0): start at the centre, a fixed
-// number of steps (the paper names no method; a fixed count makes every
-// run take the same steps), converged when the last step is negligible.
+// point (so the root is x(xi, eta) = 0), in the arithmetic A of the values
+// it serves: start at the centre, at most QUAD_NEWTON_ITERS steps, stopping
+// once a step is below `done` (quadratic convergence: the next one would be
+// below the rounding); converged when the last step is below `tol`.  The
+// element choice never depends on it (exact signs decide), only the
+// interpolation weights.
 constexpr int QUAD_NEWTON_ITERS = 8;
-ALELB_HD __forceinline__ bool quad_newton(const double c[8], double &xi, double &eta)
+template <class A>
+ALELB_HD __forceinline__ bool quad_newton_t(const A c[8], A done, A tol, A &xi, A &eta)
 {
-    double a = 0.0, b = 0.0, da = 0.0, db = 0.0;
+    A a = A(0), b = A(0), da = A(0), db = A(0);
 #pragma unroll 1
     for (int it = 0; it < QUAD_NEWTON_ITERS; ++it) {
-        double rx, ry, J[4];
-        quad_bilinear(c, a, b, rx, ry, J);
-        const double det = J[0] * J[3] - J[1] * J[2];
-        da = (J[3] * rx - J[1] * ry) / det;
-        db = (-J[2] * rx + J[0] * ry) / det;
+        const A n0 = A(0.25) * (A(1) - a) * (A(1) - b), n1 = A(0.25) * (A(1) + a) * (A(1) - b);
+        const A n2 = A(0.25) * (A(1) + a) * (A(1) + b), n3 = A(0.25) * (A(1) - a) * (A(1) + b);
+        const A a0 = A(-0.25) * (A(1) - b), a1 = A(0.25) * (A(1) - b), a2 = A(0.25) * (A(1) + b), a3 = -a2;
+        const A b0 = A(-0.25) * (A(1) - a), b1 = A(-0.25) * (A(1) + a), b2 = -b1, b3 = -b0;
+        const A rx = n0 * c[0] + n1 * c[2] + n2 * c[4] + n3 * c[6];
+        const A ry = n0 * c[1] + n1 * c[3] + n2 * c[5] + n3 * c[7];
+        const A J0 = a0 * c[0] + a1 * c[2] + a2 * c[4] + a3 * c[6];
+        const A J1 = b0 * c[0] + b1 * c[2] + b2 * c[4] + b3 * c[6];
+        const A J2 = a0 * c[1] + a1 * c[3] + a2 * c[5] + a3 * c[7];
+        const A J3 = b0 * c[1] + b1 * c[3] + b2 * c[5] + b3 * c[7];
+        const A inv = A(1) / (J0 * J3 - J1 * J2);
+        da = (J3 * rx - J1 * ry) * inv;
+        db = (-J2 * rx + J0 * ry) * inv;
         a -= da;
         b -= db;
+        if (fabs(da) + fabs(db) < done) break;
     }
     xi = a;
     eta = b;
-    return fabs(da) <= 1e-9 && fabs(db) <= 1e-9;
+    return fabs(da) <= tol && fabs(db) <= tol;
+}
+ALELB_HD __forceinline__ bool quad_newton(const double c[8], double &xi, double &eta)
+{
+    return quad_newton_t<double>(c, 1e-12, 1e-9, xi, eta);
 }
 
 // One-dimensional quadratic Lagrange polynomials through -1, 0, 1 and
@@ -274,18 +291,23 @@ ALELB_HD inline Loc quad_walk(const QuadDev &M, int a, double Xa, double Ya, dou
     return r;
 }
 
-// Local coordinates of p in element e (frame shift sx, sy) by Newton.
-ALELB_HD __forceinline__ bool quad_local(const QuadDev &M, int e, int sx, int sy, double px, double py, double &xi,
-                                         double &eta)
+// Local coordinates of p in element e (frame shift sx, sy) by Newton, in
+// the arithmetic A of the interpolation (the corners relative to p are
+// formed in FP64, then rounded to A).
+template <class A>
+ALELB_HD __forceinline__ bool quad_local(const QuadDev &M, int e, int sx, int sy, double px, double py, A &xi,
+                                         A &eta)
 {
     double w[8];
     quad_frame(M, e, sx, sy, w);
+    A c[8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        w[2 * k] -= px;
-        w[2 * k + 1] -= py;
+        c[2 * k] = (A)(w[2 * k] - px);
+        c[2 * k + 1] = (A)(w[2 * k + 1] - py);
     }
-    return quad_newton(w, xi, eta);
+    if (sizeof(A) == 8) return quad_newton_t<A>(c, A(1e-12), A(1e-9), xi, eta);
+    return quad_newton_t<A>(c, A(1e-5), A(1e-4), xi, eta); // FP32: converged near 1e-7
 }
 
 // d K / d X at node a in element el = (elem, local): the nine-node
