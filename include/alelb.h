@@ -346,13 +346,16 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    shape and timed with CUDA events; the fastest shape per kernel is kept
    for later steps.  Candidates: 64, 128 or 256 threads per block (one
    node tile per block); for the propagation's fast part also 1, 3 or 9
-   directions per thread; for the exact part of the propagation also 1, 2,
-   4, 8 or 16 blocks per SM.  The step's values do not depend on the
+   directions per thread; for the two derivative passes of the FP32 form
+   also the staging of each tile's neighbour stencil in shared memory (the
+   two fields over the tile's node range widened by 256 on each side); for
+   the exact part of the propagation also 1, 2, 4, 8 or 16 blocks per SM.  The step's values do not depend on the
    shapes, and every phase kernel gives the same values when repeated
    within a step, so tuning changes no result.  choice (may be NULL, else 8
    values out): block size of {k_stream, k_stream_fast, k_stream_slow,
-   k_moments, k_deriv1, k_collide}, grid of k_stream_slow, directions per
-   thread of k_stream_fast.
+   k_moments, k_deriv1, k_collide}, grid of k_stream_slow, then directions
+   per thread of k_stream_fast + 16 (k_deriv1 staged) + 32 (k_collide
+   staged).
    Synchronous. */
 alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
 

@@ -412,7 +412,9 @@ class Batch:
         keys = ["k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide"]
         d = {k: int(out[i]) for i, k in enumerate(keys)}
         d["k_stream_slow_grid"] = int(out[6])
-        d["k_stream_fast_directions_per_thread"] = int(out[7])
+        d["k_stream_fast_directions_per_thread"] = int(out[7]) & 15
+        d["k_deriv1_staged"] = bool(out[7] & 16)
+        d["k_collide_staged"] = bool(out[7] & 32)
         return d
 
     def profile(self, enable=True):

@@ -219,6 +219,132 @@ __global__ void __launch_bounds__(256) kb_collide(const CaseDev<S, A> *__restric
     if (a < C.M.N) collide_at<S, A, FAST>(C.M, C.MS, sh.SC(), sh.SF(), C.K, C.st, C.err, a);
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory staging of a tile's neighbour stencil (a tuner candidate for
+// the FP32 derivative passes): the block copies the two node fields it
+// differentiates over the index window [first node - STAGE_HALO, last node +
+// STAGE_HALO] into shared memory (Morton numbering keeps most of a tile's
+// owner-element nodes in it) and reads its gradient stencils there, from
+// global memory outside it.  Same values as the unstaged kernels.
+// ---------------------------------------------------------------------------
+constexpr int STAGE_HALO = 256, STAGE_MAX = 256 + 2 * STAGE_HALO;
+
+struct StagedPair {
+    float *s0, *s1; // shared windows
+    int lo, n;      // window [lo, lo + n)
+    const float *g0, *g1;
+    __device__ __forceinline__ float v0(int b) const { return (unsigned)(b - lo) < (unsigned)n ? s0[b - lo] : g0[b]; }
+    __device__ __forceinline__ float v1(int b) const { return (unsigned)(b - lo) < (unsigned)n ? s1[b - lo] : g1[b]; }
+};
+
+__device__ __forceinline__ StagedPair stage_pair(float *s0, float *s1, const float *g0, const float *g1, int first,
+                                                 int N, int stage)
+{
+    StagedPair P;
+    P.lo = max(0, first - STAGE_HALO);
+    P.n = stage ? min(N, first + (int)blockDim.x + STAGE_HALO) - P.lo : 0; // 0: every read from global
+    P.s0 = s0;
+    P.s1 = s1;
+    P.g0 = g0;
+    P.g1 = g1;
+    for (int j = threadIdx.x; j < P.n; j += blockDim.x) {
+        s0[j] = g0[P.lo + j];
+        s1[j] = g1[P.lo + j];
+    }
+    return P;
+}
+
+// FP32 owner-element derivatives d/dX of both staged fields at node a.
+__device__ __forceinline__ void owner_grad2_staged(const MeshDev &M, int a, const StagedPair &P, float &K0X,
+                                                   float &K0Y, float &K1X, float &K1Y)
+{
+    const int2 ow = M.owner[a];
+    const int e = ow.x, l = ow.y;
+    const float4 J = M.ejf[2 * e + 1];
+    float s0x = 0.f, s0e = 0.f, s1x = 0.f, s1e = 0.f;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const int b = M.conn[6 * e + s];
+        const float v0 = P.v0(b), v1 = P.v1(b);
+        s0x += v0 * c_dNxif[l][s];
+        s0e += v0 * c_dNetaf[l][s];
+        s1x += v1 * c_dNxif[l][s];
+        s1e += v1 * c_dNetaf[l][s];
+    }
+    K0X = s0x * J.x + s0e * J.z;
+    K0Y = s0x * J.y + s0e * J.w;
+    K1X = s1x * J.x + s1e * J.z;
+    K1Y = s1x * J.y + s1e * J.w;
+}
+
+// kb_deriv1 / kb_collide of the FP32-deviation form, with (stage != 0) or
+// without staged stencils: one kernel either way, so that the choice cannot
+// change a single bit of the result.
+__global__ void __launch_bounds__(256) kb_deriv1_staged(const CaseDev<float, float> *__restrict__ cases,
+                                                        const int *__restrict__ off, int B,
+                                                        const MapScalarsF *__restrict__ sf, int stage)
+{
+    wait_prior_grid();
+    __shared__ SharedCase<float, float> sh;
+    __shared__ float w0[STAGE_MAX], w1[STAGE_MAX];
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, nullptr, sf, c);
+    __syncthreads();
+    const CaseDev<float, float> &C = sh.C();
+    const int first = (blockIdx.x - __ldg(off + c)) * blockDim.x;
+    const StagedPair P = stage_pair(w0, w1, C.st.Qx, C.st.Qy, first, C.M.N, stage);
+    __syncthreads();
+    const int a = first + threadIdx.x;
+    if (a >= C.M.N) return;
+    const FastMap F = fast_map(C.MS, sh.SF(), a, C.M.Xf[a]);
+    float QxX, QxY, QyX, QyY;
+    owner_grad2_staged(C.M, a, P, QxX, QxY, QyX, QyY);
+    const float dQx = F.A11 * QxX + F.A21 * QxY; // d_x Q'_xxx
+    const float dQy = F.A12 * QyX + F.A22 * QyY; // d_y Q'_yyy
+    const float m = C.st.mrt[a];
+    C.st.Dx[a] = m * dQx;
+    C.st.Dy[a] = m * dQy;
+}
+
+__global__ void __launch_bounds__(256) kb_collide_staged(const CaseDev<float, float> *__restrict__ cases,
+                                                         const int *__restrict__ off, int B,
+                                                         const MapScalarsF *__restrict__ sf, int stage)
+{
+    wait_prior_grid();
+    __shared__ SharedCase<float, float> sh;
+    __shared__ float w0[STAGE_MAX], w1[STAGE_MAX];
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, nullptr, sf, c);
+    __syncthreads();
+    const CaseDev<float, float> &C = sh.C();
+    const int first = (blockIdx.x - __ldg(off + c)) * blockDim.x;
+    const StagedPair P = stage_pair(w0, w1, C.st.Dx, C.st.Dy, first, C.M.N, stage);
+    __syncthreads();
+    const int a = first + threadIdx.x;
+    if (a >= C.M.N) return;
+    const int N = C.M.N;
+    const KinParams<float> &K = C.K;
+    float Xx = 0.f, Xy = 0.f;
+    if (!(K.flags & FLAG_PHI_OFF)) {
+        const FastMap F = fast_map(C.MS, sh.SF(), a, C.M.Xf[a]);
+        float DxX, DxY, DyX, DyY;
+        owner_grad2_staged(C.M, a, P, DxX, DxY, DyX, DyY);
+        Xx = -(F.A11 * DxX + F.A21 * DxY);
+        Xy = -(F.A12 * DyX + F.A22 * DyY);
+    }
+    float f[NQ], g[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) fg_get(C.st.str, i, a, N, f[i], g[i]);
+    float rho, ux, uy, T;
+    if (!collide_node(K, f, g, Xx, Xy, rho, ux, uy, T)) atomicOr(C.err, ERR_NONFINITE);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) fg_put(C.st.post, i, a, N, f[i], g[i]);
+    C.st.rho[a] = rho;
+    C.st.ux[a] = ux;
+    C.st.uy[a] = uy;
+    C.st.T[a] = T;
+}
+
 // Empties every case's work list (before a repeated launch of kb_fast while
 // tuning).
 template <class S, class A>
@@ -430,6 +556,7 @@ struct alelb_batch {
     int bs[KT_N] = {128, 128, 128, 256, 256, 128, 128};
     int slow_grid = 0;
     int fast_g = BATCH_FAST_G; // directions per thread of k_stream_fast
+    bool stage[KT_N] = {};     // shared-memory staging of the derivative stencils (FP32 form)
     int n_sm = 152;
     std::map<int, cudaGraphExec_t> graphs;
     // the persistent form (mode ALELB_BATCH_PERSISTENT): threads per block,
@@ -514,7 +641,7 @@ int step_sequence(const alelb_batch *b, int seq[KT_N])
 // One phase kernel over all cases with the scalars of chunk step k.
 // bs: threads per block; grid: blocks (k_stream_slow only).
 template <class S, class A>
-void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g)
+void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g, bool stage)
 {
     const auto *cases = reinterpret_cast<const CaseDev<S, A> *>(b->d_cases);
     const int q = bs_index(bs);
@@ -543,19 +670,23 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, in
         launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B);
         break;
     case KT_DERIV1:
-        if (fast) launch_pdl(kb_deriv1<S, A, true>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
+        if (fast)
+            launch_pdl(kb_deriv1_staged, dim3(tiles), dim3(bs), b->stream,
+                       reinterpret_cast<const CaseDev<float, float> *>(cases), off, B, sf, (int)stage);
         else launch_pdl(kb_deriv1<S, A, false>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
         break;
     default:
-        if (fast) launch_pdl(kb_collide<S, A, true>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
+        if (fast)
+            launch_pdl(kb_collide_staged, dim3(tiles), dim3(bs), b->stream,
+                       reinterpret_cast<const CaseDev<float, float> *>(cases), off, B, sf, (int)stage);
         else launch_pdl(kb_collide<S, A, false>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
     }
 }
 
-void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g)
+void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g, bool stage)
 {
-    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count, fast_g);
-    else launch_phase<double, double>(b, kt, bs, grid, k, count, fast_g);
+    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count, fast_g, stage);
+    else launch_phase<double, double>(b, kt, bs, grid, k, count, fast_g, stage);
 }
 
 // One cooperative launch of the persistent kernel for chunk steps 0..K-1.
@@ -612,7 +743,7 @@ void enqueue_step(alelb_batch *b, int k)
             eb = bget_event(b);
             cudaEventRecord(ea, b->stream);
         }
-        launch_kernel(b, kt, b->bs[kt], b->slow_grid, k, 1, b->fast_g);
+        launch_kernel(b, kt, b->bs[kt], b->slow_grid, k, 1, b->fast_g, b->stage[kt]);
         if (b->prof) {
             cudaEventRecord(eb, b->stream);
             b->pending.push_back({kt, ea, eb});
@@ -876,27 +1007,29 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     };
     for (int q = 0; q < ns && st == cudaSuccess; ++q) {
         const int kt = seq[q];
-        struct Cand { int bs, grid, g; };
+        struct Cand { int bs, grid, g; bool stage; };
         std::vector<Cand> cands;
+        const bool stageable = (kt == KT_DERIV1 || kt == KT_COLLIDE) && b->prec == ALELB_PREC_FP32_DEV;
         for (int bsq = 0; bsq < N_BS; ++bsq) {
             const int bs = 64 << bsq;
             if (kt == KT_SLOW) {
-                for (int gm = 1; gm <= 16; gm *= 2) cands.push_back({bs, gm * b->n_sm, b->fast_g});
-                cands.push_back({bs, slow_resident(b, bs) * b->n_sm, b->fast_g}); // one wave
+                for (int gm = 1; gm <= 16; gm *= 2) cands.push_back({bs, gm * b->n_sm, b->fast_g, false});
+                cands.push_back({bs, slow_resident(b, bs) * b->n_sm, b->fast_g, false}); // one wave
             } else if (kt == KT_FAST) {
-                for (int g : {1, 3, 9}) cands.push_back({bs, 0, g});
+                for (int g : {1, 3, 9}) cands.push_back({bs, 0, g, false});
             } else {
-                cands.push_back({bs, 0, b->fast_g});
+                cands.push_back({bs, 0, b->fast_g, false});
+                if (stageable) cands.push_back({bs, 0, b->fast_g, true});
             }
         }
         float best = 1e30f;
-        Cand pick = {b->bs[kt], b->slow_grid, b->fast_g};
+        Cand pick = {b->bs[kt], b->slow_grid, b->fast_g, b->stage[kt]};
         for (const Cand &cd : cands) {
             float tmin = 1e30f;
             for (int r = 0; r < reps && st == cudaSuccess; ++r) {
                 if (kt == KT_FAST) clear();
                 st = cudaEventRecord(e0, b->stream);
-                launch_kernel(b, kt, cd.bs, cd.grid, 0, 0, cd.g);
+                launch_kernel(b, kt, cd.bs, cd.grid, 0, 0, cd.g, cd.stage);
                 if (st == cudaSuccess) st = cudaGetLastError();
                 if (st == cudaSuccess) st = cudaEventRecord(e1, b->stream);
                 if (st == cudaSuccess) st = cudaEventSynchronize(e1);
@@ -913,9 +1046,10 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
         b->bs[kt] = pick.bs;
         if (kt == KT_SLOW) b->slow_grid = pick.grid;
         if (kt == KT_FAST) b->fast_g = pick.g;
+        b->stage[kt] = pick.stage;
         // the launch that counts (walk statistics) with the chosen shape
         if (kt == KT_FAST) clear();
-        launch_kernel(b, kt, pick.bs, pick.grid, 0, 1, b->fast_g);
+        launch_kernel(b, kt, pick.bs, pick.grid, 0, 1, b->fast_g, b->stage[kt]);
         st = cudaGetLastError();
     }
     cudaEventDestroy(e0);
@@ -932,7 +1066,7 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     if (choice) {
         for (int k = 0; k < 6; ++k) choice[k] = b->bs[k];
         choice[6] = b->slow_grid;
-        choice[7] = b->fast_g;
+        choice[7] = b->fast_g | (b->stage[KT_DERIV1] ? 16 : 0) | (b->stage[KT_COLLIDE] ? 32 : 0);
     }
     return ALELB_OK;
 }
