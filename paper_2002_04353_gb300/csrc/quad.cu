@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -20,9 +21,10 @@ namespace {
 // Sec. IV.A, then moments, Q'_aaa and mu/(rho T), as on triangles.
 template <class S, class A>
 __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStatic &MS, const MapScalars &sc,
-                                                 const MapScalars &scd, const KinParams<A> &K,
+                                                 const MapScalars &scd, const MapScalarsF &sfd, const KinParams<A> &K,
                                                  const StateDev<S> &st, int *err, unsigned long long *stats, int a)
 {
+    constexpr bool FAST = !std::is_same<S, double>::value; // the deviation forms: certified FP32 decisions
     const int N = M.N;
     const double2 Xa = M.X[a];
     bool have64 = false;
@@ -30,10 +32,43 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
     int miss = 0, far = 0;
     unsigned walks = 0;
     A sfm = 0, jx = 0, jy = 0, sg = 0;
+    float4 Xf = make_float4(0.f, 0.f, 0.f, 0.f);
+    FastMap F;
+    F.ok = false;
+    if (FAST) {
+        Xf = M.Xf[a];
+        F = fast_map(MS, sfd, a, Xf);
+        if (K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
+    }
 #pragma unroll 1
     for (int i = 0; i < NQ; ++i) {
         A fi = 0, gi = 0;
         int src = -1;
+        if (FAST && F.ok) {
+            // the previous-step element, verified in FP32 with certified bounds
+            const int c = st.cache[i * N + a];
+            int e;
+            float cw[8];
+            float xi, eta;
+            if (quad_fast_decide(M, F, Xf, a, i, c, e, cw) && quad_newton_t<float>(cw, 1e-5f, 1e-4f, xi, eta)) {
+                A Nw[9];
+                shape9<A>((A)xi, (A)eta, Nw);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int b = M.conn[9 * e + k];
+                    A fb, gb;
+                    fg_get(st.post, i, b, N, fb, gb);
+                    fi += Nw[k] * fb;
+                    gi += Nw[k] * gb;
+                }
+                fg_put(st.str, i, a, N, fi, gi);
+                sfm += fi;
+                jx += (A)c_cx[i] * fi;
+                jy += (A)c_cy[i] * fi;
+                sg += gi;
+                continue;
+            }
+        }
         if (!have64 && !(K.flags & FLAG_EXACT_CHAR)) {
             double xX, xY, yX, yY;
             map_node(MS, scd, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -52,6 +87,8 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
         } else {
             ++walks;
             const Loc L = quad_walk(M, a, Xa.x, Xa.y, px, py, err);
+            if (FAST) // the element for the next step's certified check
+                st.cache[i * N + a] = L.e >= 0 ? (L.e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30)) : -1;
             if (L.e == -2) {
                 src = a;
             } else if (L.e == -1) {
@@ -166,11 +203,12 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
 
 template <class S, class A>
 __global__ void __launch_bounds__(128) kq_stream(QuadDev M, MapStatic MS, MapScalars sc, MapScalars scd,
-                                                 KinParams<A> K, StateDev<S> st, int *err, unsigned long long *stats)
+                                                 MapScalarsF sfd, KinParams<A> K, StateDev<S> st, int *err,
+                                                 unsigned long long *stats)
 {
     wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < M.N) quad_stream_node(M, MS, sc, scd, K, st, err, stats, a);
+    if (a < M.N) quad_stream_node(M, MS, sc, scd, sfd, K, st, err, stats, a);
 }
 
 // D_a = (mu / rho T) d_a Q'_aaa in the owner element (Eq. Xa).
@@ -341,6 +379,9 @@ alelb_status quad_mesh_upload(alelb_mesh *m)
     D.probe_xi = B.put(Q.probe_xi, st);
     D.wall_nrm = B.put(Q.wall_nrm, st);
     D.orig_elem = B.put(Q.orig, st);
+    D.Xf = B.put(Q.Xf, st);
+    D.evf = B.put(Q.evf, st);
+    D.bdist = B.put(Q.bdist, st);
     m->d_wedges = B.put(Q.wedges, st);
     m->d_n2o = B.put(T.node_new2old, st);
     m->nw = (int)Q.wedges.size();
@@ -365,8 +406,8 @@ cudaError_t quad_launch(alelb_solver *s, int kernel, const MapScalars &sc, const
         using A = typename std::remove_reference<decltype(K)>::type::Arith;
         switch (kernel) {
         case KT_STREAM:
-            launch_pdl(kq_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc, scd, K, st,
-                       s->d_err, s->d_stats);
+            launch_pdl(kq_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc, scd,
+                       to_f32(scd, m->T), K, st, s->d_err, s->d_stats);
             break;
         case KT_DERIV1:
             launch_pdl(kq_deriv1<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, m->qdev, m->mst, sc, st);

@@ -120,6 +120,9 @@ struct QuadDev {
     const double2 *probe_xi; // [NW]
     const double2 *wall_nrm; // [NW]
     const int *orig_elem;  // [E]
+    const float4 *Xf;      // [N] node coordinates, FP32 hi + lo
+    const float4 *evf;     // [4E] corners, FP32 hi + lo
+    const float *bdist;    // [N] lower bound of the distance to the nearest boundary edge
 };
 
 // The four corners of element e shifted by (sx, sy) periods.
@@ -289,6 +292,60 @@ ALELB_HD inline Loc quad_walk(const QuadDev &M, int a, double Xa, double Ya, dou
     set_err(err, ERR_LOCATE);
     r.e = -2;
     return r;
+}
+
+// The certified FP32 decision of the deviation forms for population i of
+// node a: its previous-step element (cache code c, unshifted) holds the FP64
+// departure point strictly inside -- four orientation signs certified in
+// FP32 against their error bounds (the departure offset -c^ carries F.eq(i)
+// per component, the node-relative corners their hi/lo rounding) -- and the
+// segment from the node cannot leave the mesh: the cell is one of the
+// node's own (convex, it holds both ends) or the segment is shorter than
+// the node's distance to any boundary.  The oracle's exhaustive search
+// then picks the same cell: a point strictly inside one cell lies in no
+// other.  On success cw holds the corners relative to the departure point
+// (FP32) for Newton.
+ALELB_HD __forceinline__ bool quad_fast_decide(const QuadDev &M, const FastMap &F, float4 Xf, int a, int i, int c,
+                                               int &e, float cw[8])
+{
+    if (!F.ok || c < 0 || (c >> 28) != 5) return false;
+    const float u = 5.9604644775390625e-08f;
+    const float cx = (float)lat_cx(i), cy = (float)lat_cy(i);
+    const float chx = F.A11 * cx + F.A12 * cy - F.W1;
+    const float chy = F.A21 * cx + F.A22 * cy - F.W2;
+    const float eq = F.eq(i);
+    const float len2 = chx * chx + chy * chy;
+    const float q4 = 4.0f * eq;
+    if (!(len2 > q4 * q4)) return false;
+    e = c & CACHE_ELEM;
+    bool own = false;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) own = own || M.conn[9 * e + k] == a;
+    if (!own) {
+        const float room = M.bdist[a] - eq;
+        if (!(room > 0.0f && len2 < room * room)) return false;
+    }
+    const float px = -chx, py = -chy;
+    float rx[4], ry[4], er[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 v = M.evf[4 * e + k];
+        const float hx = v.x - Xf.x, hy = v.y - Xf.y;
+        rx[k] = hx + (v.z - Xf.z);
+        ry[k] = hy + (v.w - Xf.w);
+        er[k] = 4.0f * u * (fmaxf(fabsf(rx[k]), fabsf(ry[k])) + fmaxf(fabsf(hx), fabsf(hy))) + 9.313225746154785e-10f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int k1 = (k + 1) & 3;
+        if (orient3_f32(rx[k], ry[k], er[k], rx[k1], ry[k1], er[k1], px, py, eq) <= 0) return false;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cw[2 * k] = rx[k] - px;
+        cw[2 * k + 1] = ry[k] - py;
+    }
+    return true;
 }
 
 // Local coordinates of p in element e (frame shift sx, sy) by Newton, in

@@ -22,6 +22,10 @@ struct QuadTables {
     std::vector<int2> fan, owner, bcel, wedges;
     std::vector<uint8_t> bkind;
     std::vector<double2> probe_xi, wall_nrm;
+    // the certified FP32 decisions of the deviation forms
+    std::vector<float4> Xf;  // [N] node coordinates split hi + lo in FP32
+    std::vector<float4> evf; // [4E] corners split hi + lo in FP32
+    std::vector<float> bdist; // [N] lower bound of the distance to the nearest boundary edge
 };
 
 // Local coordinates of p in the quadrilateral with corners w (x, y pairs),
@@ -323,6 +327,57 @@ inline alelb_status build_quad_tables(const alelb_mesh_desc *d, HostTables &T, Q
             Q.wall_nrm.push_back(make_double2(nx, ny));
             Q.probe_e.push_back(best);
             Q.probe_xi.push_back(make_double2(xi, eta));
+        }
+    }
+    // FP32 hi + lo splits (hi = fl32(x), lo = fl32(x - hi)) of the node
+    // coordinates and the corners
+    auto split = [](double2 v) {
+        const float xh = (float)v.x, yh = (float)v.y;
+        return make_float4(xh, yh, (float)(v.x - (double)xh), (float)(v.y - (double)yh));
+    };
+    Q.Xf.resize(N);
+    for (int a = 0; a < N; ++a) Q.Xf[a] = split(T.X[a]);
+    Q.evf.resize((size_t)4 * E);
+    for (size_t k = 0; k < (size_t)4 * E; ++k) Q.evf[k] = split(Q.ev[k]);
+    // lower bound of every node's distance to the nearest boundary edge,
+    // capped at DCAP (zero on periodic meshes with boundaries: those always
+    // walk): a departure segment shorter than it cannot leave the mesh
+    {
+        const double DCAP = 16.0;
+        Q.bdist.assign(N, (float)DCAP);
+        std::vector<std::pair<double2, double2>> be;
+        for (int en = 0; en < E; ++en)
+            for (int k = 0; k < 4; ++k)
+                if ((Q.einfo[en] >> (8 * k)) & 3u) be.push_back({Q.ev[4 * en + k], Q.ev[4 * en + (k + 1) % 4]});
+        if (!be.empty() && (T.Lx > 0 || T.Ly > 0)) {
+            Q.bdist.assign(N, 0.0f);
+        } else if (!be.empty()) {
+            std::unordered_map<uint64_t, std::vector<int>> grid;
+            auto key = [](long ix, long iy) { return ((uint64_t)(uint32_t)ix << 32) | (uint32_t)iy; };
+            for (size_t b = 0; b < be.size(); ++b) {
+                const double x0 = std::min(be[b].first.x, be[b].second.x) - DCAP;
+                const double x1 = std::max(be[b].first.x, be[b].second.x) + DCAP;
+                const double y0 = std::min(be[b].first.y, be[b].second.y) - DCAP;
+                const double y1 = std::max(be[b].first.y, be[b].second.y) + DCAP;
+                for (long ix = (long)std::floor(x0 / DCAP); ix <= (long)std::floor(x1 / DCAP); ++ix)
+                    for (long iy = (long)std::floor(y0 / DCAP); iy <= (long)std::floor(y1 / DCAP); ++iy)
+                        grid[key(ix, iy)].push_back((int)b);
+            }
+            for (int a = 0; a < N; ++a) {
+                const double px = T.X[a].x, py = T.X[a].y;
+                auto it = grid.find(key((long)std::floor(px / DCAP), (long)std::floor(py / DCAP)));
+                if (it == grid.end()) continue;
+                double dmin = DCAP;
+                for (int b : it->second) {
+                    const double ax = be[b].first.x, ay = be[b].first.y, dx = be[b].second.x - ax,
+                                 dy = be[b].second.y - ay, L2 = dx * dx + dy * dy;
+                    double t = L2 > 0 ? ((px - ax) * dx + (py - ay) * dy) / L2 : 0.0;
+                    t = std::min(1.0, std::max(0.0, t));
+                    const double qx = ax + t * dx - px, qy = ay + t * dy - py;
+                    dmin = std::min(dmin, std::sqrt(qx * qx + qy * qy));
+                }
+                Q.bdist[a] = (float)(dmin * (1.0 - 1e-6));
+            }
         }
     }
     T.ms = static_map_factors(T.mkind, T.mp, T.X);

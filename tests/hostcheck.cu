@@ -10,19 +10,8 @@
 
 using namespace alelb;
 
-// The quadrilateral walk (quad_walk, the routine kq_locate runs) on the
-// host, for meshes of 9-node quadrilaterals.
-extern "C" int alelb_hostcheck_locate_q2(const alelb_mesh_desc *d, double t, int literal, int32_t *elem,
-                                         int8_t *kind, char *errbuf, int errlen)
+static QuadDev quad_host_view(const HostTables &T, const QuadTables &Q)
 {
-    HostTables T;
-    QuadTables Q;
-    std::string err;
-    alelb_status st = build_quad_tables(d, T, Q, err);
-    if (st != ALELB_OK) {
-        if (errbuf && errlen > 0) std::strncpy(errbuf, err.c_str(), errlen - 1);
-        return st;
-    }
     QuadDev M{};
     M.N = T.N;
     M.E = T.E;
@@ -40,6 +29,26 @@ extern "C" int alelb_hostcheck_locate_q2(const alelb_mesh_desc *d, double t, int
     M.bcel = Q.bcel.data();
     M.bkind = Q.bkind.data();
     M.orig_elem = Q.orig.data();
+    M.Xf = Q.Xf.data();
+    M.evf = Q.evf.data();
+    M.bdist = Q.bdist.data();
+    return M;
+}
+
+// The quadrilateral walk (quad_walk, the routine kq_locate runs) on the
+// host, for meshes of 9-node quadrilaterals.
+extern "C" int alelb_hostcheck_locate_q2(const alelb_mesh_desc *d, double t, int literal, int32_t *elem,
+                                         int8_t *kind, char *errbuf, int errlen)
+{
+    HostTables T;
+    QuadTables Q;
+    std::string err;
+    alelb_status st = build_quad_tables(d, T, Q, err);
+    if (st != ALELB_OK) {
+        if (errbuf && errlen > 0) std::strncpy(errbuf, err.c_str(), errlen - 1);
+        return st;
+    }
+    const QuadDev M = quad_host_view(T, Q);
     MapStatic MS = T.host_map();
     MapScalars sc = map_scalars(T.mkind, T.mp, t);
     int e = 0;
@@ -191,4 +200,81 @@ extern "C" void alelb_hostcheck_orient(const double *p, int n, int32_t *out, int
         out[k] = orient(q[0], q[1], q[2], q[3], q[4], q[5]);
         stage[k] = orient_int(q[0], q[1], q[2], q[3], q[4], q[5]);
     }
+}
+
+// The deviation forms' decisions on quadrilaterals at map time t with the
+// element cache an exact walk at t_prev leaves (quad_fast_decide, then the
+// walk), on the host: elem/kind as alelb_locate, fast = 1 where the
+// certified FP32 check settled the population.
+extern "C" int alelb_hostcheck_fast_q2(const alelb_mesh_desc *d, double t_prev, double t, int32_t *elem,
+                                       int8_t *kind, int8_t *fast)
+{
+    HostTables T;
+    QuadTables Q;
+    std::string err;
+    alelb_status st = build_quad_tables(d, T, Q, err);
+    if (st != ALELB_OK) return st;
+    const QuadDev M = quad_host_view(T, Q);
+    MapStatic MS = T.host_map();
+    const int N = T.N;
+    std::vector<int> cache((size_t)9 * N, -1);
+    int e = 0;
+    auto depart = [&](const MapScalars &sc, int a, int i, double &chx, double &chy, double &px, double &py) {
+        const double2 Xa = M.X[a];
+        double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22, wx, wy;
+        map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
+        metric_inverse_T(xX, xY, yX, yY, a11, a12, a21, a22);
+        mesh_velocity_term(a11, a12, a21, a22, ds(Vx, sc.Ux), ds(Vy, sc.Uy), false, wx, wy);
+        departure(a11, a12, a21, a22, wx, wy, (double)lat_cx(i), (double)lat_cy(i), Xa.x, Xa.y, chx, chy, px, py);
+    };
+    {
+        const MapScalars sc = map_scalars(T.mkind, T.mp, t_prev);
+        for (int a = 0; a < N; ++a)
+            for (int i = 0; i < NQ; ++i) {
+                double chx, chy, px, py;
+                depart(sc, a, i, chx, chy, px, py);
+                if (chx == 0.0 && chy == 0.0) continue;
+                const Loc L = quad_walk(M, a, M.X[a].x, M.X[a].y, px, py, &e);
+                if (L.e >= 0) cache[(size_t)i * N + a] = L.e | ((L.sx + 1) << 28) | ((L.sy + 1) << 30);
+            }
+    }
+    const MapScalars sc = map_scalars(T.mkind, T.mp, t);
+    MapScalarsF sf{};
+    sf.s = (float)sc.s;
+    sf.sd = (float)sc.sd;
+    sf.vy = (float)sc.vy;
+    sf.c = (float)sc.c;
+    sf.sn = (float)sc.sn;
+    sf.thd = (float)sc.thd;
+    sf.cm = (float)sc.cm;
+    sf.Xc = (float)T.mp[3];
+    sf.Yc = (float)T.mp[4];
+    sf.er0 = 2.0f;
+    for (int a = 0; a < N; ++a) {
+        const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
+        const int o = T.node_new2old[a];
+        for (int i = 0; i < NQ; ++i) {
+            int el = -2, k = 0, f = 0, ef;
+            float cw[8];
+            if (quad_fast_decide(M, F, M.Xf[a], a, i, cache[(size_t)i * N + a], ef, cw)) {
+                el = M.orig_elem[ef];
+                f = 1;
+            } else {
+                double chx, chy, px, py;
+                depart(sc, a, i, chx, chy, px, py);
+                if (!(chx == 0.0 && chy == 0.0)) {
+                    const Loc L = quad_walk(M, a, M.X[a].x, M.X[a].y, px, py, &e);
+                    if (L.e >= 0) el = M.orig_elem[L.vnode >= 0 ? quad_fan_best(M, L.vnode) : L.e];
+                    else if (L.e == -1) {
+                        el = -1;
+                        k = L.kind;
+                    }
+                }
+            }
+            elem[(size_t)i * N + o] = el;
+            kind[(size_t)i * N + o] = (int8_t)k;
+            fast[(size_t)i * N + o] = (int8_t)f;
+        }
+    }
+    return e ? ALELB_ERR_LOCATE : ALELB_OK;
 }

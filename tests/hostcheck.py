@@ -33,6 +33,8 @@ def lib():
                                                 C.c_char_p, C.c_int]
         _lib.alelb_hostcheck_locate_q2.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                                    C.c_char_p, C.c_int]
+        _lib.alelb_hostcheck_fast_q2.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                                 C.c_void_p]
         _lib.alelb_hostcheck_inside.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                 C.c_void_p]
         _lib.alelb_hostcheck_fast.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -91,8 +93,8 @@ def locate_fast(mesh, motion, t_prev, t):
     e = np.empty((9, mesh.n_nodes), dtype=np.int32)
     k = np.empty((9, mesh.n_nodes), dtype=np.int8)
     f = np.empty((9, mesh.n_nodes), dtype=np.int8)
-    st = lib().alelb_hostcheck_fast(C.byref(d), float(t_prev), float(t), e.ctypes.data, k.ctypes.data,
-                                    f.ctypes.data)
+    fn = lib().alelb_hostcheck_fast_q2 if getattr(mesh, "elem_type", 0) == 1 else lib().alelb_hostcheck_fast
+    st = fn(C.byref(d), float(t_prev), float(t), e.ctypes.data, k.ctypes.data, f.ctypes.data)
     return st, e, k, f.astype(bool)
 
 
