@@ -743,6 +743,42 @@ def run_force_history(alelb, args):
     return out
 
 
+def run_element_stability(alelb, args):
+    """How far the paper's airfoil runs get under its own wall targets (R8,
+    correction phi on) on triangles and on the same rings as 9-node
+    quadrilaterals (150,400 nodes each), FP32 populations, up to
+    args.stability_steps steps with the forces read every 100 steps (a
+    non-finite state stops the run): config 2's plunge, the paper's slow
+    plunge (also with R8c) and its pitch at k = 6.68."""
+    V = alelb.FLAG_OFFWALL_VG
+    runs = (("config2_plunge", dict(Re=1e4, k=1.0, h_frac=0.1), 0),
+            ("paper_slow_plunge", dict(Re=1850.0, k=0.46 / (2 * 0.08), h_frac=0.08), 0),
+            ("paper_slow_plunge_R8c", dict(Re=1850.0, k=0.46 / (2 * 0.08), h_frac=0.08), V),
+            ("paper_pitch_k6.68", dict(Re=12000.0, k=6.68, pitch=True), 0))
+    out = {}
+    for elem in ("p2", "q2"):
+        for name, kw, flags in runs:
+            if kw.get("pitch"):
+                case = I.pitch_case(ni=320, nj=118, Ma=0.2, Re=kw["Re"], k=kw["k"], alpha0_deg=0.0, amp_deg=2.0,
+                                    blended=False, elem=elem)
+            else:
+                case = I.plunge_case(ni=320, nj=118, Ma=0.2, elem=elem, **kw)
+            fl = dataclasses.replace(case.flow, flags=flags)
+            s = alelb.Solver(alelb.Mesh(case.mesh, case.motion), fl, alelb.PREC_FP32_DEV)
+            done, status = 0, "completed"
+            while done < args.stability_steps:
+                s.lb_step(100)
+                done += 100
+                try:
+                    s.forces()
+                except alelb.AlelbError:
+                    status = f"diverged by step {done}"
+                    break
+            s.close()
+            out[f"{elem}:{name}"] = {"status": status, "steps": done, "nodes": case.mesh.n_nodes}
+    return out
+
+
 def run_single(alelb, torch, dev, world, args):
     """The 150,400-node plunge (h = 0.1c, k = 1, Mach 0.2, Re 1e4): the
     FP32-deviation form and the plain FP64 form, one case.  Its working set
@@ -904,6 +940,7 @@ def run_ours(args):
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
     forces = None if (args.no_forces or world > 1) else run_force_history(alelb, args)
     growth = None if (args.no_precision or world > 1) else run_precision_growth(alelb, args)
+    stability = run_element_stability(alelb, args) if (args.stability and world == 1) else None
     precision = precision_low = None
     if not (args.no_precision or world > 1):
         # config 3 at its own Mach number: the shifted lattice of the transonic
@@ -954,6 +991,7 @@ def run_ours(args):
             "force_history": forces,
             "precision_study_ma03": precision_low,
             "precision_growth": growth,
+            "element_stability": stability,
             "e2e": bat["e2e"],
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
@@ -987,6 +1025,9 @@ def main():
     ap.add_argument("--no-persistent", action="store_true")
     ap.add_argument("--no-q2", action="store_true")
     ap.add_argument("--q2-steps", type=int, default=10)
+    ap.add_argument("--stability", action="store_true",
+                    help="also run the paper's airfoil cases on triangles and quadrilaterals until they diverge")
+    ap.add_argument("--stability-steps", type=int, default=3000)
     ap.add_argument("--sweep-scale", type=float, default=1.0,
                     help="node counts of the sweep's cases times this (1: the workload; smaller for counter captures)")
     ap.add_argument("--only-batched", action="store_true",

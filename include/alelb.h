@@ -129,9 +129,11 @@ enum {
    midside nodes of edges (v0,v1), (v1,v2), (v2,v3), (v3,v0) (exact edge
    midpoints), then the centre, exactly 0.25 (((v0 + v1) + v2) + v3);
    edge_kind[4*e + k].  The local coordinates of a departure point solve
-   Eq. NonLinear_Eq by Newton's method from the cell centre (8 steps), and
-   every population of such a mesh takes the exact FP64 departure path in
-   every precision.  Quadrilateral meshes are not taken by the batched
+   Eq. NonLinear_Eq by Newton's method from the cell centre (at most 8
+   steps, stopping once converged).  The element choices are those of the
+   exact FP64 departure path in every precision: the deviation forms accept
+   the previous-step element only under a certified FP32 test, and send
+   every other population down that path.  Quadrilateral meshes are not taken by the batched
    step, the learned proposal, alelb_samples or alelb_lb_step_noalloc
    (ALELB_ERR_ARG).
    period[d] > 0 makes direction d periodic with that period (coordinates
@@ -346,7 +348,9 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    shape and timed with CUDA events; the fastest shape per kernel is kept
    for later steps.  Candidates: 64, 128 or 256 threads per block (one
    node tile per block); for the propagation's fast part also 1, 3 or 9
-   directions per thread; for the two derivative passes of the FP32 form
+   directions per thread, and in the FP32 form 3 or 9 fused with the
+   moments; for
+   the two derivative passes of the FP32 form
    also the staging of each tile's neighbour stencil in shared memory (the
    two fields over the tile's node range widened by 256 on each side); for
    the exact part of the propagation also 1, 2, 4, 8 or 16 blocks per SM.  The step's values do not depend on the
@@ -355,9 +359,19 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    values out): block size of {k_stream, k_stream_fast, k_stream_slow,
    k_moments, k_deriv1, k_collide}, grid of k_stream_slow, then directions
    per thread of k_stream_fast + 16 (k_deriv1 staged) + 32 (k_collide
-   staged).
+   staged) + 256 (k_stream_fast fused with the moments: the
+   moments of the nodes whose populations all settle there are computed
+   in the same launch, and k_moments takes only the others).
    Synchronous. */
 alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
+
+/* Sets the launch shapes that alelb_batch_tune would choose, in its
+   encoding (for example a choice saved from an earlier tuning):
+   block sizes 64, 128 or 256; a k_stream_slow grid of 1 .. 64 x the SM
+   count; directions per thread 1, 3 or 9, optionally + 256 (fused with
+   the moments; 3 or 9 only); + 16, + 32 (staging).  Every flag needs the FP32 form.  Changes
+   no result; ALELB_ERR_ARG for a value outside these. */
+alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t choice[8]);
 
 /* How a batch runs its steps.  ALELB_BATCH_GRAPHS (the default): one
    launch per phase over all cases, chunks of up to 64 steps captured once

@@ -48,7 +48,7 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_batch_last_error", "alelb_mlp_create", "alelb_mlp_destroy", "alelb_mlp_get_params",
            "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
            "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
-           "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait"]
+           "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait", "alelb_batch_set_choice"]
 
 
 class AlelbError(RuntimeError):
@@ -134,6 +134,7 @@ def load(path: str = LIB_PATH):
     L.alelb_checkpoint_info.argtypes = [C.c_char_p, p, p, C.c_char_p, i32]
     L.alelb_batch_set_mode.argtypes = [p, i32]
     L.alelb_batch_set_wait.argtypes = [p, d, i32]
+    L.alelb_batch_set_choice.argtypes = [p, p]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -406,15 +407,27 @@ class Batch:
         self._check(load().alelb_batch_set_wait(self.h, float(limit_seconds), int(missing_arrivals)),
                     "batch_set_wait")
 
-    def tune(self, reps=3):
+    def set_choice(self, choice):
+        """Launch shapes in alelb_batch_tune's encoding (8 int32 values)."""
+        c = np.ascontiguousarray(choice, dtype=np.int32)
+        if c.shape != (8,):
+            raise ValueError("choice: 8 values")
+        self._check(load().alelb_batch_set_choice(self.h, _ptr(c)), "batch_set_choice")
+
+    def tune(self, reps=3, raw=False):
+        """Tunes the launch shapes; the chosen ones by name, or (raw) in the
+        8-value encoding that set_choice takes."""
         out = np.zeros(8, dtype=np.int32)
         self._check(load().alelb_batch_tune(self.h, int(reps), _ptr(out)), "batch_tune")
+        if raw:
+            return out
         keys = ["k_stream", "k_stream_fast", "k_stream_slow", "k_moments", "k_deriv1", "k_collide"]
         d = {k: int(out[i]) for i, k in enumerate(keys)}
         d["k_stream_slow_grid"] = int(out[6])
         d["k_stream_fast_directions_per_thread"] = int(out[7]) & 15
         d["k_deriv1_staged"] = bool(out[7] & 16)
         d["k_collide_staged"] = bool(out[7] & 32)
+        d["k_stream_fast_fused_moments"] = bool(out[7] & 256)
         return d
 
     def profile(self, enable=True):

@@ -411,9 +411,9 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                            : (s->flags & ALELB_FLAG_MIDPOINT) ? solver_map(s, map_scalars(m->T.mkind, m->T.mp, s->t + 0.5))
                                                               : sc;
     const MapScalarsF sfd = to_f32(scd, m->T);
-    if (m->etype == ALELB_ELEM_Q2QUAD) { // every population on the exact path, any precision
-        const int qseq[3] = {KT_STREAM, KT_DERIV1, KT_COLLIDE};
-        for (int q = 0; q < 3; ++q) {
+    if (m->etype == ALELB_ELEM_Q2QUAD) { // quad.cu: propagation, moments, the two derivative passes
+        const int qseq[4] = {KT_STREAM, KT_MOMENTS, KT_DERIV1, KT_COLLIDE};
+        for (int q = 0; q < 4; ++q) {
             if (qseq[q] == KT_DERIV1 && !phi) continue;
             cudaEvent_t ea = nullptr, eb = nullptr;
             if (s->prof) {

@@ -33,6 +33,8 @@ namespace {
 constexpr int BATCH_MAX = 32;
 constexpr int CHUNK_MAX = 64; // steps per captured graph
 constexpr int N_BS = 3;       // block sizes 64, 128, 256
+// flag of the directions-per-thread choice (FP32 form): kb_fast_fused
+constexpr int FAST_FUSED = 256;
 
 template <class S, class A> struct CaseDev {
     MeshDev M;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
         if (i < NQ) {
             stream_slow_item(C.M, C.MS, sc[c], sf[c], sc[c], sf[c], C.K, C.st, C.err, entry);
         } else {
-            const unsigned mask = C.st.wmask[entry];
+            const unsigned mask = C.st.wmask[entry] & WMASK_DIRS;
             if (count && C.stats) atomicAdd(C.stats, (unsigned long long)__popc(mask));
             stream_bc_node<S, A>(C.M, C.MS, sc[c], sf[c], C.K, C.st, entry,
                                  fast_map(C.MS, sf[c], entry, C.M.Xf[entry]), mask);
@@ -172,9 +174,11 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
     }
 }
 
+// pending: the fused propagation ran (kb_fast_fused) and computed the
+// moments of every node but those it marked WMASK_PENDING.
 template <class S, class A>
 __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restrict__ cases,
-                                                  const int *__restrict__ off, int B)
+                                                  const int *__restrict__ off, int B, int pending)
 {
     wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
@@ -184,7 +188,81 @@ __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restric
     const CaseDev<S, A> &C = sh.C();
     const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
     if (a <= NQ) C.st.wcount[a] = 0u; // the case's work list has been consumed
-    if (a < C.M.N) moments_node(C.K, C.st, C.M.N, C.err, a);
+    if (a < C.M.N && (!pending || (C.st.wmask[a] & WMASK_PENDING))) moments_node(C.K, C.st, C.M.N, C.err, a);
+}
+
+// The propagation of the FP32 form fused with the moments: a block holds
+// the NQ / G direction groups of a tile of T nodes (group-uniform warps),
+// each thread settles its G populations as kb_fast does and leaves the
+// settled pairs in shared memory; then one thread per node computes the
+// node's moments from them, exactly as the moments kernel would, unless a
+// population of the node went to the exact path or its wall condition:
+// then the node is marked WMASK_PENDING and the moments kernel takes it.
+// The nodes the exact path never touches are read once per step instead of
+// twice.
+template <int G, int T>
+__global__ void __launch_bounds__(T *NQ / G) kb_fast_fused(const CaseDev<float, float> *__restrict__ cases,
+                                                           const int *__restrict__ off, int B,
+                                                           const MapScalarsF *__restrict__ sf)
+{
+    static_assert(NQ % G == 0 && T % 32 == 0, "group-uniform warps");
+    constexpr int NG = NQ / G;
+    wait_prior_grid();
+    __shared__ SharedCase<float, float> sh;
+    __shared__ float fs[NQ][T], gs[NQ][T];
+    __shared__ int pend[NG][T];
+    const int c = tile_case(off, B, blockIdx.x);
+    sh.load(cases, nullptr, sf, c);
+    __syncthreads();
+    const CaseDev<float, float> &C = sh.C();
+    const MeshDev &M = C.M;
+    const StateDev<float> &st = C.st;
+    const int tx = threadIdx.x % T, grp = threadIdx.x / T, i0 = G * grp;
+    const int a = (blockIdx.x - __ldg(off + c)) * T + tx;
+    int code[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) code[j] = 0;
+    if (a < M.N) {
+        int cc[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) cc[j] = st.cache[(i0 + j) * M.N + a];
+        const float bd = M.bdist[a];
+        const float4 Xf = M.Xf[a];
+        FastMap F = fast_map(C.MS, sh.SF(), a, Xf);
+        if (C.K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            float fo = 0.f, go = 0.f;
+            code[j] = stream_fast_pop(M, C.K, st, a, i0 + j, F, Xf, bd, cc[j], fo, go);
+            fs[i0 + j][tx] = fo;
+            gs[i0 + j][tx] = go;
+        }
+    }
+    int any = 0;
+#pragma unroll
+    for (int j = 0; j < G; ++j) any |= code[j];
+    if (__any_sync(0xffffffffu, any != 0)) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) append_pop(st, a, M.N, i0 + j, code[j]);
+    }
+    pend[grp][tx] = any;
+    __syncthreads(); // every group's pairs and wall bits of the tile are in
+    if (grp == 0 && a < M.N) {
+        int p = 0;
+#pragma unroll
+        for (int q = 0; q < NG; ++q) p |= pend[q][tx];
+        if (p) {
+            atomicOr(st.wmask + a, WMASK_PENDING);
+        } else {
+            float f[NQ], g[NQ];
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                f[i] = fs[i][tx];
+                g[i] = gs[i][tx];
+            }
+            moments_store(C.K, st, C.err, a, f, g);
+        }
+    }
 }
 
 template <class S, class A, bool FAST>
@@ -345,17 +423,25 @@ __global__ void __launch_bounds__(256) kb_collide_staged(const CaseDev<float, fl
     C.st.T[a] = T;
 }
 
-// Empties every case's work list (before a repeated launch of kb_fast while
-// tuning).
+// Empties every case's work list and the wall masks and pending marks of
+// its nodes (before a repeated launch of kb_fast while tuning): one block
+// per case.
 template <class S, class A>
 __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
 {
-    const int c = threadIdx.x;
-    if (c < B) {
-        const StateDev<S> &st = cases[c].st;
-        for (unsigned k = 0; k < st.wcount[NQ]; ++k) st.wmask[st.work[(size_t)NQ * cases[c].M.N + k]] = 0u;
-        for (int i = 0; i <= NQ; ++i) st.wcount[i] = 0u;
+    const int c = blockIdx.x;
+    if (c >= B) return;
+    const StateDev<S> &st = cases[c].st;
+    const int N = cases[c].M.N;
+    for (int i = 0; i <= NQ; ++i) {
+        const unsigned n = st.wcount[i];
+        for (unsigned k = threadIdx.x; k < n; k += blockDim.x) {
+            const int e = st.work[(size_t)i * N + k];
+            st.wmask[i < NQ ? e / NQ : e] = 0u;
+        }
     }
+    __syncthreads();
+    if (threadIdx.x <= NQ) st.wcount[threadIdx.x] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -494,7 +580,7 @@ __global__ void __launch_bounds__(128) kb_persistent(const CaseDev<S, A> *__rest
                 if (i < NQ) {
                     stream_slow_item(C.M, C.MS, sc[c], sf[c], sc[c], sf[c], C.K, C.st, C.err, entry);
                 } else {
-                    const unsigned mask = C.st.wmask[entry];
+                    const unsigned mask = C.st.wmask[entry] & WMASK_DIRS;
                     if (C.stats) atomicAdd(C.stats, (unsigned long long)__popc(mask));
                     stream_bc_node<S, A>(C.M, C.MS, sc[c], sf[c], C.K, C.st, entry,
                                          fast_map(C.MS, sf[c], entry, C.M.Xf[entry]), mask);
@@ -656,7 +742,26 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, in
         launch_pdl(kb_stream<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, count);
         break;
     case KT_FAST:
-        if (fast_g == 1)
+        // fast_g: directions per thread, plus FAST_FUSED for the propagation
+        // fused with the moments
+        if (fast_g & FAST_FUSED) {
+            if constexpr (std::is_same<S, float>::value) {
+                const auto *cf = reinterpret_cast<const CaseDev<float, float> *>(cases);
+                const int G = fast_g & 15;
+                if (G == 3 && bs == 64)
+                    launch_pdl(kb_fast_fused<3, 64>, dim3(tiles), dim3(64 * 3), b->stream, cf, off, B, sf);
+                else if (G == 3 && bs == 128)
+                    launch_pdl(kb_fast_fused<3, 128>, dim3(tiles), dim3(128 * 3), b->stream, cf, off, B, sf);
+                else if (G == 3)
+                    launch_pdl(kb_fast_fused<3, 256>, dim3(tiles), dim3(256 * 3), b->stream, cf, off, B, sf);
+                else if (bs == 64)
+                    launch_pdl(kb_fast_fused<9, 64>, dim3(tiles), dim3(64), b->stream, cf, off, B, sf);
+                else if (bs == 128)
+                    launch_pdl(kb_fast_fused<9, 128>, dim3(tiles), dim3(128), b->stream, cf, off, B, sf);
+                else
+                    launch_pdl(kb_fast_fused<9, 256>, dim3(tiles), dim3(256), b->stream, cf, off, B, sf);
+            }
+        } else if (fast_g == 1)
             launch_pdl(kb_fast<S, A, 1>, dim3(tiles, NQ), dim3(bs), b->stream, cases, off, B, sf);
         else if (fast_g == 3)
             launch_pdl(kb_fast<S, A, 3>, dim3(tiles, NQ / 3), dim3(bs), b->stream, cases, off, B, sf);
@@ -667,7 +772,8 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, in
         launch_pdl(kb_slow<S, A>, dim3(grid), dim3(bs), b->stream, cases, B, sc, sf, count);
         break;
     case KT_MOMENTS:
-        launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B);
+        launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B,
+                   (int)((fast_g & FAST_FUSED) != 0));
         break;
     case KT_DERIV1:
         if (fast)
@@ -1000,10 +1106,10 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     const auto clear = [b]() {
         if (b->prec == ALELB_PREC_FP32_DEV)
             kb_clear_work<float, float>
-                <<<1, 32, 0, b->stream>>>(reinterpret_cast<const CaseDev<float, float> *>(b->d_cases), b->B);
+                <<<b->B, 256, 0, b->stream>>>(reinterpret_cast<const CaseDev<float, float> *>(b->d_cases), b->B);
         else
             kb_clear_work<double, double>
-                <<<1, 32, 0, b->stream>>>(reinterpret_cast<const CaseDev<double, double> *>(b->d_cases), b->B);
+                <<<b->B, 256, 0, b->stream>>>(reinterpret_cast<const CaseDev<double, double> *>(b->d_cases), b->B);
     };
     for (int q = 0; q < ns && st == cudaSuccess; ++q) {
         const int kt = seq[q];
@@ -1017,6 +1123,8 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
                 cands.push_back({bs, slow_resident(b, bs) * b->n_sm, b->fast_g, false}); // one wave
             } else if (kt == KT_FAST) {
                 for (int g : {1, 3, 9}) cands.push_back({bs, 0, g, false});
+                if (b->prec == ALELB_PREC_FP32_DEV)
+                    for (int g : {3 | FAST_FUSED, 9 | FAST_FUSED}) cands.push_back({bs, 0, g, false});
             } else {
                 cands.push_back({bs, 0, b->fast_g, false});
                 if (stageable) cands.push_back({bs, 0, b->fast_g, true});
@@ -1030,6 +1138,11 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
                 if (kt == KT_FAST) clear();
                 st = cudaEventRecord(e0, b->stream);
                 launch_kernel(b, kt, cd.bs, cd.grid, 0, 0, cd.g, cd.stage);
+                // a propagation candidate is timed with the moments launch it
+                // implies (the fused form leaves kb_moments only the nodes it
+                // marked pending)
+                if (kt == KT_FAST && b->prec == ALELB_PREC_FP32_DEV)
+                    launch_kernel(b, KT_MOMENTS, b->bs[KT_MOMENTS], 0, 0, 0, cd.g, false);
                 if (st == cudaSuccess) st = cudaGetLastError();
                 if (st == cudaSuccess) st = cudaEventRecord(e1, b->stream);
                 if (st == cudaSuccess) st = cudaEventSynchronize(e1);
@@ -1066,7 +1179,7 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     if (choice) {
         for (int k = 0; k < 6; ++k) choice[k] = b->bs[k];
         choice[6] = b->slow_grid;
-        choice[7] = b->fast_g | (b->stage[KT_DERIV1] ? 16 : 0) | (b->stage[KT_COLLIDE] ? 32 : 0);
+        choice[7] = b->fast_g | (b->stage[KT_DERIV1] ? 16 : 0) | (b->stage[KT_COLLIDE] ? 32 : 0); // FAST_FUSED = 256
     }
     return ALELB_OK;
 }
@@ -1098,6 +1211,30 @@ extern "C" alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **na
         if (launches) launches[k] = b->n_acc[k];
     }
     *n = m;
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t choice[8])
+{
+    if (!b || !choice) return ALELB_ERR_ARG;
+    for (int k = 0; k < 6; ++k)
+        if (choice[k] != 64 && choice[k] != 128 && choice[k] != 256) return ALELB_ERR_ARG;
+    if (choice[6] < 1 || choice[6] > 64 * b->n_sm) return ALELB_ERR_ARG;
+    const int c7 = choice[7], G = c7 & 15, fl = c7 & ~15;
+    const bool fp32 = b->prec == ALELB_PREC_FP32_DEV;
+    if (G != 1 && G != 3 && G != 9) return ALELB_ERR_ARG;
+    if (fl & ~(16 | 32 | FAST_FUSED)) return ALELB_ERR_ARG;
+    if (!fp32 && fl) return ALELB_ERR_ARG;
+    const int form = fl & FAST_FUSED;
+    if (form && G == 1) return ALELB_ERR_ARG;
+    cudaError_t st = cudaStreamSynchronize(b->stream);
+    if (st != cudaSuccess) return bfail(b, st, "batch_set_choice");
+    for (int k = 0; k < 6; ++k) b->bs[k] = choice[k];
+    b->slow_grid = choice[6];
+    b->fast_g = G | form;
+    b->stage[KT_DERIV1] = (c7 & 16) != 0;
+    b->stage[KT_COLLIDE] = (c7 & 32) != 0;
+    drop_graphs(b);
     return ALELB_OK;
 }
 

@@ -144,10 +144,12 @@ template <class S> struct StateDev {
                           // with populations certified missing at a wall, at work[9 N + k],
                           // k < wcount[9], their directions in wmask
     unsigned *wcount;     // [10] entries of each segment
-    unsigned *wmask;      // [N] directions certified missing at a wall; set by the
+    unsigned *wmask;      // [N] directions certified missing at a wall (bits 0-8); set by the
                           // propagation kernel, read by the exact path, cleared by the
-                          // moments kernel
+                          // moments kernel; WMASK_PENDING: the fused batched propagation
+                          // left the node's moments to the moments kernel
 };
+constexpr unsigned WMASK_DIRS = (1u << NQ) - 1u, WMASK_PENDING = 1u << 31;
 
 // The exact-path kernels number the work list direction by direction
 // (populations of one direction at neighbouring nodes take similar paths,
@@ -524,14 +526,17 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
 // field.  Returns 0 when settled, 1 when left to the exact path, 2 when
 // certified missing at a wall (the wall condition then runs once per node
 // in the exact-path kernel).
+// fo, go: the settled pair as stored (the moments of the fused batched
+// kernel read them; unused elsewhere).
 template <class S, class A>
 __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams<A> &K,
                                                const StateDev<S> &st, int a, int i,
-                                               const FastMap &F, float4 Xf, float bd, int c)
+                                               const FastMap &F, float4 Xf, float bd, int c, A &fo, A &go)
 {
     const int N = M.N;
     if (i == 0 && M.vzero[a] && !(K.flags & FLAG_SHIFT)) { // c^_0 exactly zero: the node's own value
         fg_copy(st.str, st.post, 0, a, N);
+        fg_get(st.post, 0, a, N, fo, go);
         return 0;
     }
     if (!F.ok) return 1;
@@ -560,14 +565,26 @@ __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams
             gi += Nw[k] * gb;
         }
         fg_put(st.str, i, a, N, fi, gi);
+        fo = fi;
+        go = gi;
         return 0;
     }
     const int ck = cone_missing(M, F, a, i);
     if (ck == 2) { // far field: free-stream equilibria
         fg_put(st.str, i, a, N, K.finf[i], K.ginf[i]);
+        fo = K.finf[i];
+        go = K.ginf[i];
         return 0;
     }
     return ck == 1 ? 2 : 1;
+}
+template <class S, class A>
+__device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams<A> &K,
+                                               const StateDev<S> &st, int a, int i,
+                                               const FastMap &F, float4 Xf, float bd, int c)
+{
+    A fo, go;
+    return stream_fast_pop(M, K, st, a, i, F, Xf, bd, c, fo, go);
 }
 
 // Work-list entries of the lanes of a warp (all lanes take part; direction
@@ -799,7 +816,7 @@ __device__ __forceinline__ void slow_entry(const MeshDev &M, const MapStatic &MS
                          prop ? prop[w] : -1, prop && stats ? stats + 1 : nullptr);
     } else {
         const int a = st.work[(size_t)NQ * M.N + (w - pre[NQ])];
-        const unsigned mask = st.wmask[a];
+        const unsigned mask = st.wmask[a] & WMASK_DIRS;
         if (stats) atomicAdd(stats, (unsigned long long)__popc(mask));
         stream_bc_node<S, A>(M, MS, sc, sf, K, st, a, fast_map(MS, sf, a, M.Xf[a]), mask);
     }
@@ -823,16 +840,12 @@ __global__ void __launch_bounds__(128) k_stream_slow(MeshDev M, MapStatic MS, Ma
 }
 
 
+// rho, u, E, T of the streamed pairs f, g of node a, then Q'_aaa and
+// mu / (rho T) (the fused batched propagation kernel shares this).
 template <class S, class A>
-__device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateDev<S> &st, int N,
-                                             int *err, int a)
+__device__ __forceinline__ void moments_store(const KinParams<A> &K, const StateDev<S> &st, int *err, int a,
+                                              const A f[NQ], const A g[NQ])
 {
-    st.wmask[a] = 0u; // used by the exact path of this step
-    A f[NQ], g[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-        fg_get(st.str, i, a, N, f[i], g[i]);
-    }
     const A sf = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
     const A jx = K.jx_ref + ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
     const A jy = K.jy_ref + ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
@@ -847,6 +860,19 @@ __device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateD
     st.Qx[a] = (fld_t<S>)(rho * wx * k3 - rho * wx * wx * wx);
     st.Qy[a] = (fld_t<S>)(rho * wy * k3 - rho * wy * wy * wy);
     st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
+}
+
+template <class S, class A>
+__device__ __forceinline__ void moments_node(const KinParams<A> &K, const StateDev<S> &st, int N,
+                                             int *err, int a)
+{
+    st.wmask[a] = 0u; // used by the exact path of this step
+    A f[NQ], g[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        fg_get(st.str, i, a, N, f[i], g[i]);
+    }
+    moments_store(K, st, err, a, f, g);
 }
 
 template <class S, class A>

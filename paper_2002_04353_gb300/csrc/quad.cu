@@ -4,8 +4,10 @@
 // missing populations) is the one the triangles use (kinetic.cuh); only the
 // geometry differs: the walk over quadrilaterals, Newton's method for the
 // local coordinates of Eq. NonLinear_Eq, the nine shape functions of
-// Eq. Propagation and the element gradients (quad.cuh).  Every population
-// takes the exact FP64 path in every storage precision.
+// Eq. Propagation and the element gradients (quad.cuh).  The deviation
+// forms first try the previous-step element under a certified FP32 test
+// (quad_fast_decide); every other population, and every population of the
+// FP64 form, takes the exact FP64 path.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -16,13 +18,15 @@
 namespace alelb {
 namespace {
 
-// Propagation of the nine population pairs of node a (Eq. Propagation over
-// the nine nodes of the departure element), the missing populations of
-// Sec. IV.A, then moments, Q'_aaa and mu/(rho T), as on triangles.
-template <class S, class A>
-__device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStatic &MS, const MapScalars &sc,
+// Propagation of population pairs i0 .. i0 + G - 1 of node a (Eq.
+// Propagation over the nine nodes of the departure element) and, for those
+// that are missing, the condition of Sec. IV.A.  The moments, Q'_aaa and
+// mu/(rho T) follow in k_moments, as on triangles.
+template <int G, class S, class A>
+__device__ __forceinline__ void quad_stream_pops(const QuadDev &M, const MapStatic &MS, const MapScalars &sc,
                                                  const MapScalars &scd, const MapScalarsF &sfd, const KinParams<A> &K,
-                                                 const StateDev<S> &st, int *err, unsigned long long *stats, int a)
+                                                 const StateDev<S> &st, int *err, unsigned long long *stats, int a,
+                                                 int i0)
 {
     constexpr bool FAST = !std::is_same<S, double>::value; // the deviation forms: certified FP32 decisions
     const int N = M.N;
@@ -31,7 +35,6 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
     double a11 = 0, a12 = 0, a21 = 0, a22 = 0, wx = 0, wy = 0, Vx = 0, Vy = 0;
     int miss = 0, far = 0;
     unsigned walks = 0;
-    A sfm = 0, jx = 0, jy = 0, sg = 0;
     float4 Xf = make_float4(0.f, 0.f, 0.f, 0.f);
     FastMap F;
     F.ok = false;
@@ -41,7 +44,7 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
         if (K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
     }
 #pragma unroll 1
-    for (int i = 0; i < NQ; ++i) {
+    for (int i = i0; i < i0 + G; ++i) {
         A fi = 0, gi = 0;
         int src = -1;
         if (FAST && F.ok) {
@@ -62,10 +65,6 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
                     gi += Nw[k] * gb;
                 }
                 fg_put(st.str, i, a, N, fi, gi);
-                sfm += fi;
-                jx += (A)c_cx[i] * fi;
-                jy += (A)c_cy[i] * fi;
-                sg += gi;
                 continue;
             }
         }
@@ -114,10 +113,6 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
         }
         if (src >= 0) fg_get(st.post, i, src, N, fi, gi);
         fg_put(st.str, i, a, N, fi, gi);
-        sfm += fi;
-        jx += (A)c_cx[i] * fi;
-        jy += (A)c_cy[i] * fi;
-        sg += gi;
     }
     if (stats && walks) atomicAdd(stats, (unsigned long long)walks);
     if (miss) {
@@ -183,41 +178,55 @@ __device__ __forceinline__ void quad_stream_node(const QuadDev &M, const MapStat
             const A fi = (far >> i & 1) ? K.finf[i] : fm[i];
             const A gi = (far >> i & 1) ? K.ginf[i] : gm[i];
             fg_put(st.str, i, a, N, fi, gi);
-            sfm += fi;
-            jx += (A)c_cx[i] * fi;
-            jy += (A)c_cy[i] * fi;
-            sg += gi;
         }
     }
-    const A rho = K.rho_ref + sfm;
-    const A rwx = (K.jx_ref + jx) / rho, rwy = (K.jy_ref + jy) / rho;
-    const A ux = rwx + K.Ux, uy = rwy + K.Uy;
-    const A E = (K.E2_ref + sg) / (A(2) * rho);
-    const A T = (E - A(0.5) * (ux * ux + uy * uy)) / K.Cv;
-    if (!(rho > A(0)) || !(T > A(0)) || !isfinite(rho) || !isfinite(T)) atomicOr(err, ERR_NONFINITE);
-    const A k3 = A(1) - A(3) * T;
-    st.Qx[a] = (fld_t<S>)(rho * rwx * k3 - rho * rwx * rwx * rwx);
-    st.Qy[a] = (fld_t<S>)(rho * rwy * k3 - rho * rwy * rwy * rwy);
-    st.mrt[a] = (fld_t<S>)(K.mu / (rho * T));
 }
 
-template <class S, class A>
+// Grid (node blocks, 9 / G direction groups): G directions per thread.
+template <class S, class A, int G>
 __global__ void __launch_bounds__(128) kq_stream(QuadDev M, MapStatic MS, MapScalars sc, MapScalars scd,
                                                  MapScalarsF sfd, KinParams<A> K, StateDev<S> st, int *err,
                                                  unsigned long long *stats)
 {
     wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < M.N) quad_stream_node(M, MS, sc, scd, sfd, K, st, err, stats, a);
+    if (a < M.N) quad_stream_pops<G>(M, MS, sc, scd, sfd, K, st, err, stats, a, G * blockIdx.y);
 }
 
-// D_a = (mu / rho T) d_a Q'_aaa in the owner element (Eq. Xa).
+// Directions per thread of kq_stream: one per population in both forms,
+// the most threads to hide the walks' dependent loads (measured at 150k
+// nodes, FP32 / FP64 per launch: 145 / 3,900 us at one, 184 / 4,000 at
+// three, 240 / 4,120 at nine).
+#ifndef ALELB_QUAD_G32
+#define ALELB_QUAD_G32 1
+#endif
+#ifndef ALELB_QUAD_G64
+#define ALELB_QUAD_G64 1
+#endif
+static_assert(NQ % ALELB_QUAD_G32 == 0 && NQ % ALELB_QUAD_G64 == 0, "directions per thread");
+
+// D_a = (mu / rho T) d_a Q'_aaa in the owner element (Eq. Xa); FP32 in the
+// deviation forms (the FP32 map and the node's FP32 owner-element J^{-1}),
+// FP64 otherwise.
 template <class S, class A>
-__global__ void __launch_bounds__(256) kq_deriv1(QuadDev M, MapStatic MS, MapScalars sc, StateDev<S> st)
+__global__ void __launch_bounds__(256) kq_deriv1(QuadDev M, MapStatic MS, MapScalars sc, MapScalarsF sf,
+                                                 StateDev<S> st)
 {
     wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= M.N) return;
+    if (!std::is_same<S, double>::value) {
+        const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
+        float KX, KY;
+        quad_grad_f32(M, a, st.Qx, KX, KY);
+        const float dQx = F.A11 * KX + F.A21 * KY; // d_x Q'_xxx
+        quad_grad_f32(M, a, st.Qy, KX, KY);
+        const float dQy = F.A12 * KX + F.A22 * KY; // d_y Q'_yyy
+        const float m = (float)st.mrt[a];
+        st.Dx[a] = (fld_t<S>)(m * dQx);
+        st.Dy[a] = (fld_t<S>)(m * dQy);
+        return;
+    }
     const double2 Xa = M.X[a];
     double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
     map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -234,15 +243,22 @@ __global__ void __launch_bounds__(256) kq_deriv1(QuadDev M, MapStatic MS, MapSca
 
 // X_a = -d_a D_a in the owner element, then the collision (Eqs. feqn, geqn).
 template <class S, class A>
-__global__ void __launch_bounds__(128) kq_collide(QuadDev M, MapStatic MS, MapScalars sc, KinParams<A> K,
-                                                  StateDev<S> st, int *err)
+__global__ void __launch_bounds__(128) kq_collide(QuadDev M, MapStatic MS, MapScalars sc, MapScalarsF sf,
+                                                  KinParams<A> K, StateDev<S> st, int *err)
 {
     wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= M.N) return;
     const int N = M.N;
     A Xx = 0, Xy = 0;
-    if (!(K.flags & FLAG_PHI_OFF)) {
+    if (!std::is_same<S, double>::value && !(K.flags & FLAG_PHI_OFF)) {
+        const FastMap F = fast_map(MS, sf, a, M.Xf[a]);
+        float KX, KY;
+        quad_grad_f32(M, a, st.Dx, KX, KY);
+        Xx = (A)(-(F.A11 * KX + F.A21 * KY));
+        quad_grad_f32(M, a, st.Dy, KX, KY);
+        Xy = (A)(-(F.A12 * KX + F.A22 * KY));
+    } else if (!(K.flags & FLAG_PHI_OFF)) {
         const double2 Xa = M.X[a];
         double xX, xY, yX, yY, Vx, Vy, a11, a12, a21, a22;
         map_node(MS, sc, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -382,6 +398,7 @@ alelb_status quad_mesh_upload(alelb_mesh *m)
     D.Xf = B.put(Q.Xf, st);
     D.evf = B.put(Q.evf, st);
     D.bdist = B.put(Q.bdist, st);
+    D.ownJf = B.put(Q.ownJf, st);
     m->d_wedges = B.put(Q.wedges, st);
     m->d_n2o = B.put(T.node_new2old, st);
     m->nw = (int)Q.wedges.size();
@@ -405,16 +422,22 @@ cudaError_t quad_launch(alelb_solver *s, int kernel, const MapScalars &sc, const
         using S = typename std::remove_reference<decltype(st)>::type::Tag;
         using A = typename std::remove_reference<decltype(K)>::type::Arith;
         switch (kernel) {
-        case KT_STREAM:
-            launch_pdl(kq_stream<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc, scd,
-                       to_f32(scd, m->T), K, st, s->d_err, s->d_stats);
+        case KT_STREAM: {
+            constexpr int G = std::is_same<S, double>::value ? ALELB_QUAD_G64 : ALELB_QUAD_G32;
+            launch_pdl(kq_stream<S, A, G>, dim3((N + 127) / 128, NQ / G), dim3(128), s->stream, m->qdev, m->mst, sc,
+                       scd, to_f32(scd, m->T), K, st, s->d_err, s->d_stats);
+            break;
+        }
+        case KT_MOMENTS:
+            launch_pdl(k_moments<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, K, st, N, s->d_err);
             break;
         case KT_DERIV1:
-            launch_pdl(kq_deriv1<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, m->qdev, m->mst, sc, st);
+            launch_pdl(kq_deriv1<S, A>, dim3((N + 255) / 256), dim3(256), s->stream, m->qdev, m->mst, sc,
+                       to_f32(sc, m->T), st);
             break;
         default:
-            launch_pdl(kq_collide<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc, K, st,
-                       s->d_err);
+            launch_pdl(kq_collide<S, A>, dim3((N + 127) / 128), dim3(128), s->stream, m->qdev, m->mst, sc,
+                       to_f32(sc, m->T), K, st, s->d_err);
         }
     });
     return cudaGetLastError();

@@ -9,9 +9,11 @@
 // v3 (-1,1) counter-clockwise, the midside nodes of edges (v0,v1), (v1,v2),
 // (v2,v3), (v3,v0), then the centre (0,0).  Edge k runs from v_k to v_k+1.
 //
-// Every population takes the exact path: the FP64 departure point, exact
-// orientation signs for the walk and the tie rules, Newton in FP64; the
-// populations are stored and interpolated in the solver's precision.
+// The exact path: the FP64 departure point, exact orientation signs for the
+// walk and the tie rules, Newton in the interpolation's arithmetic; the
+// populations are stored and interpolated in the solver's precision.  The
+// deviation forms settle most populations before it with a certified FP32
+// test of the previous-step element (quad_fast_decide).
 #pragma once
 #include "geom.cuh"
 
@@ -123,6 +125,7 @@ struct QuadDev {
     const float4 *Xf;      // [N] node coordinates, FP32 hi + lo
     const float4 *evf;     // [4E] corners, FP32 hi + lo
     const float *bdist;    // [N] lower bound of the distance to the nearest boundary edge
+    const float4 *ownJf;   // [N] owner element's J^{-1} at the node, FP32
 };
 
 // The four corners of element e shifted by (sx, sy) periods.
@@ -404,6 +407,41 @@ __device__ __forceinline__ void quad_grad(const QuadDev &M, int2 el, const S *K,
     const double det = J[0] * J[3] - J[2] * J[1];
     KX = (J[3] * sxi - J[2] * seta) / det;
     KY = (-J[1] * sxi + J[0] * seta) / det;
+}
+
+} // namespace alelb
+
+namespace alelb {
+
+// Local node at grid position (i, j) of the 3 x 3 node lattice of an
+// element (i along xi, j along eta; 0, 1, 2 for -1, 0, 1): 4-bit fields of
+// one word, row j = 0 first (a run-time index into a constant array would
+// put the array in local memory).
+ALELB_HD __forceinline__ int quad_node_at(int i, int j)
+{
+    return (int)((0x263587140ull >> (4 * (3 * j + i))) & 15ull);
+}
+
+// FP32 d K / d X at node a in its owner element (Eq. FE_Derivative): at a
+// node the nine shape functions' xi derivatives vanish off the node's eta
+// row and their eta derivatives off its xi column, so each derivative is a
+// three-term sum; dL_m at the node's coordinate t in {-1, 0, 1} is t - 1/2,
+// -2 t, t + 1/2 (exact in FP32).
+template <class S>
+__device__ __forceinline__ void quad_grad_f32(const QuadDev &M, int a, const S *K, float &KX, float &KY)
+{
+    const int2 ow = M.owner[a];
+    const int e = ow.x, l = ow.y;
+    const int li = quad_ix(l), lj = quad_iy(l);
+    const float tx = (float)(li - 1), ty = (float)(lj - 1);
+    const int *cn = M.conn + 9 * e;
+    const float sxi = (tx - 0.5f) * (float)K[cn[quad_node_at(0, lj)]] + (-2.0f * tx) * (float)K[cn[quad_node_at(1, lj)]] +
+                      (tx + 0.5f) * (float)K[cn[quad_node_at(2, lj)]];
+    const float seta = (ty - 0.5f) * (float)K[cn[quad_node_at(li, 0)]] + (-2.0f * ty) * (float)K[cn[quad_node_at(li, 1)]] +
+                       (ty + 0.5f) * (float)K[cn[quad_node_at(li, 2)]];
+    const float4 J = M.ownJf[a];
+    KX = sxi * J.x + seta * J.z;
+    KY = sxi * J.y + seta * J.w;
 }
 
 } // namespace alelb

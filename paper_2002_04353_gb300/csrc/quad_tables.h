@@ -26,6 +26,9 @@ struct QuadTables {
     std::vector<float4> Xf;  // [N] node coordinates split hi + lo in FP32
     std::vector<float4> evf; // [4E] corners split hi + lo in FP32
     std::vector<float> bdist; // [N] lower bound of the distance to the nearest boundary edge
+    // the FP32 derivative passes: J^{-1} of the owner element's bilinear map
+    // at the node, (d xi/dX, d xi/dY, d eta/dX, d eta/dY)
+    std::vector<float4> ownJf; // [N]
 };
 
 // Local coordinates of p in the quadrilateral with corners w (x, y pairs),
@@ -339,6 +342,18 @@ inline alelb_status build_quad_tables(const alelb_mesh_desc *d, HostTables &T, Q
     for (int a = 0; a < N; ++a) Q.Xf[a] = split(T.X[a]);
     Q.evf.resize((size_t)4 * E);
     for (size_t k = 0; k < (size_t)4 * E; ++k) Q.evf[k] = split(Q.ev[k]);
+    Q.ownJf.resize(N);
+    for (int a = 0; a < N; ++a) {
+        const int e = Q.owner[a].x, l = Q.owner[a].y;
+        double w[8], x, y, J[4];
+        for (int k = 0; k < 4; ++k) {
+            w[2 * k] = Q.ev[4 * e + k].x;
+            w[2 * k + 1] = Q.ev[4 * e + k].y;
+        }
+        quad_bilinear(w, quad_ix(l) - 1.0, quad_iy(l) - 1.0, x, y, J);
+        const double det = J[0] * J[3] - J[2] * J[1];
+        Q.ownJf[a] = make_float4((float)(J[3] / det), (float)(-J[1] / det), (float)(-J[2] / det), (float)(J[0] / det));
+    }
     // lower bound of every node's distance to the nearest boundary edge,
     // capped at DCAP (zero on periodic meshes with boundaries: those always
     // walk): a departure segment shorter than it cannot leave the mesh

@@ -32,6 +32,7 @@ static QuadDev quad_host_view(const HostTables &T, const QuadTables &Q)
     M.Xf = Q.Xf.data();
     M.evf = Q.evf.data();
     M.bdist = Q.bdist.data();
+    M.ownJf = Q.ownJf.data();
     return M;
 }
 

@@ -129,6 +129,66 @@ def test_tuning_changes_no_value():
         assert sa.info()["walks"] == sb.info()["walks"]
 
 
+# every launch form of the FP32 batch (alelb_batch_tune's encoding): block
+# sizes, directions per thread, the propagation fused with the moments
+# (+256), staged derivative stencils (+16, +32)
+FORMS = [[128, 128, 128, 256, 256, 128, 64, 9],
+         [128, 64, 128, 256, 256, 128, 64, 1],
+         [128, 256, 64, 128, 64, 256, 300, 3 | 16 | 32],
+         [128, 64, 128, 64, 256, 128, 64, 3 | 256],
+         [128, 128, 128, 256, 256, 128, 64, 3 | 256],
+         [128, 256, 128, 256, 128, 128, 64, 3 | 256 | 16],
+         [128, 64, 128, 256, 256, 128, 64, 9 | 256],
+         [128, 128, 128, 256, 256, 128, 64, 9 | 256 | 32],
+         [128, 256, 128, 256, 256, 128, 64, 9 | 256]]
+
+
+def test_every_launch_form_gives_the_same_bits():
+    """Each form of alelb_batch_set_choice, 6 steps (a wall node's missing
+    populations, far-field cones and listed populations included): the
+    same populations, fields and walk counts as the default form, bit for
+    bit."""
+    cases = _cases()
+    ref = _solvers(cases, alelb.PREC_FP32_DEV)
+    br = alelb.Batch(ref)
+    br.step(6)
+    br.sync()
+    want = [(s.get_pops(), s.moments(), s.info()["walks"]) for s in ref]
+    for choice in FORMS:
+        ss = _solvers(cases, alelb.PREC_FP32_DEV)
+        b = alelb.Batch(ss)
+        b.set_choice(choice)
+        b.step(6)
+        b.sync()
+        for c, s in enumerate(ss):
+            (fr, gr), mr, wr = want[c]
+            f, g = s.get_pops()
+            assert np.array_equal(f, fr) and np.array_equal(g, gr), f"{choice} case {c}"
+            mo = s.moments()
+            assert all(np.array_equal(mo[k], mr[k]) for k in mr), f"{choice} case {c}"
+            assert s.info()["walks"] == wr
+
+
+def test_set_choice_refuses_unknown_forms():
+    ss = _solvers(_cases()[:1], alelb.PREC_FP32_DEV)
+    b = alelb.Batch(ss)
+    good = [128, 128, 128, 256, 256, 128, 64, 3]
+    bad = [dict(i=0, v=96), dict(i=6, v=0), dict(i=7, v=2), dict(i=7, v=1 | 256), dict(i=7, v=3 | 128),
+           dict(i=7, v=3 | 512), dict(i=7, v=3 | 64)]
+    for d in bad:
+        c = list(good)
+        c[d["i"]] = d["v"]
+        with pytest.raises(alelb.AlelbError) as e:
+            b.set_choice(c)
+        assert e.value.status == -1
+    b.set_choice(good)
+    s64 = _solvers(_cases()[:1], alelb.PREC_FP64)
+    b64 = alelb.Batch(s64)
+    with pytest.raises(alelb.AlelbError):
+        b64.set_choice([128, 128, 128, 256, 256, 128, 64, 3 | 256])
+    b64.set_choice([128, 128, 128, 256, 256, 128, 64, 9])
+
+
 def test_batch_and_single_steps_interleave():
     cases = _cases()[:2]
     alone = _solvers(cases, alelb.PREC_FP64)
