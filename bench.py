@@ -916,6 +916,14 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     peak, peak_src = measured_peaks()
     W, K = max(3, args.warmup), args.steps
+    if args.only_part:
+        # one part alone (for counter captures of its kernels): no headline
+        part = {"single": lambda: run_single(alelb, torch, dev, world, args),
+                "q2": lambda: run_q2(alelb, torch, dev, args),
+                "learned": lambda: run_learned(alelb, torch, dev, args)}[args.only_part]()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "part": args.only_part, "result": part}), flush=True)
+        return
 
     # headline: the batched sweep, clocks sampled during its timed region
     sampler = ClockSampler(local)
@@ -1030,6 +1038,8 @@ def main():
     ap.add_argument("--stability-steps", type=int, default=3000)
     ap.add_argument("--sweep-scale", type=float, default=1.0,
                     help="node counts of the sweep's cases times this (1: the workload; smaller for counter captures)")
+    ap.add_argument("--only-part", choices=["single", "q2", "learned"],
+                    help="run one part alone, without the headline (for counter captures of its kernels)")
     ap.add_argument("--only-batched", action="store_true",
                     help="the headline alone (no single case, e2e, network, precision, forces, CPU baseline)")
     args = ap.parse_args()

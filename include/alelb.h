@@ -353,7 +353,14 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    the two derivative passes of the FP32 form
    also the staging of each tile's neighbour stencil in shared memory (the
    two fields over the tile's node range widened by 256 on each side); for
-   the exact part of the propagation also 1, 2, 4, 8 or 16 blocks per SM.  The step's values do not depend on the
+   the exact part of the propagation also 1, 2, 4, 8 or 16 blocks per SM.
+   Then, for the FP32 form in graph mode, the propagation's form is
+   refined on whole steps: the forms with 3 and 9 directions per thread,
+   plain and fused with the moments, at 128 and 256 threads, and the
+   per-kernel pick each run 8 steps twice from a saved copy of every case's
+   state, the second run timed; the fastest is kept and the state put back
+   (the cases advance by the one real step only; a device copy of each
+   case's populations, fields and element cache is held meanwhile).  The step's values do not depend on the
    shapes, and every phase kernel gives the same values when repeated
    within a step, so tuning changes no result.  choice (may be NULL, else 8
    values out): block size of {k_stream, k_stream_fast, k_stream_slow,

@@ -412,8 +412,11 @@ cudaError_t launch_step(alelb_solver *s, StateDev<S> &st, KinParams<A> &K, const
                                                               : sc;
     const MapScalarsF sfd = to_f32(scd, m->T);
     if (m->etype == ALELB_ELEM_Q2QUAD) { // quad.cu: propagation, moments, the two derivative passes
-        const int qseq[4] = {KT_STREAM, KT_MOMENTS, KT_DERIV1, KT_COLLIDE};
-        for (int q = 0; q < 4; ++q) {
+        const int qseq64[4] = {KT_STREAM, KT_MOMENTS, KT_DERIV1, KT_COLLIDE};
+        const int qseq32[5] = {KT_FAST, KT_SLOW, KT_MOMENTS, KT_DERIV1, KT_COLLIDE};
+        const int *qseq = fast ? qseq32 : qseq64;
+        const int nq = fast ? 5 : 4;
+        for (int q = 0; q < nq; ++q) {
             if (qseq[q] == KT_DERIV1 && !phi) continue;
             cudaEvent_t ea = nullptr, eb = nullptr;
             if (s->prof) {

@@ -18,17 +18,48 @@
 namespace alelb {
 namespace {
 
+// Population i of node a by the certified FP32 decision of the deviation
+// forms: its previous-step element, accepted by quad_fast_decide, Newton in
+// FP32, the nine-node interpolation.  False: left to the exact path.
+template <class S, class A>
+__device__ __forceinline__ bool quad_fast_pop(const QuadDev &M, const FastMap &F, float4 Xf, const StateDev<S> &st,
+                                              int a, int i)
+{
+    const int N = M.N;
+    const int c = st.cache[i * N + a];
+    int e;
+    float cw[8];
+    float xi, eta;
+    if (!(quad_fast_decide(M, F, Xf, a, i, c, e, cw) && quad_newton_t<float>(cw, 1e-5f, 1e-4f, xi, eta)))
+        return false;
+    A Nw[9];
+    shape9<A>((A)xi, (A)eta, Nw);
+    A fi = 0, gi = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int b = M.conn[9 * e + k];
+        A fb, gb;
+        fg_get(st.post, i, b, N, fb, gb);
+        fi += Nw[k] * fb;
+        gi += Nw[k] * gb;
+    }
+    fg_put(st.str, i, a, N, fi, gi);
+    return true;
+}
+
 // Propagation of population pairs i0 .. i0 + G - 1 of node a (Eq.
 // Propagation over the nine nodes of the departure element) and, for those
-// that are missing, the condition of Sec. IV.A.  The moments, Q'_aaa and
-// mu/(rho T) follow in k_moments, as on triangles.
-template <int G, class S, class A>
-__device__ __forceinline__ void quad_stream_pops(const QuadDev &M, const MapStatic &MS, const MapScalars &sc,
-                                                 const MapScalars &scd, const MapScalarsF &sfd, const KinParams<A> &K,
-                                                 const StateDev<S> &st, int *err, unsigned long long *stats, int a,
-                                                 int i0)
+// that are missing, the condition of Sec. IV.A.  TRY: first the certified
+// FP32 decision (deviation forms).  The moments, Q'_aaa and mu/(rho T)
+// follow in k_moments, as on triangles.
+// Returns the number of element walks taken.
+template <int G, bool TRY, class S, class A>
+__device__ __forceinline__ unsigned quad_stream_pops(const QuadDev &M, const MapStatic &MS, const MapScalars &sc,
+                                                     const MapScalars &scd, const MapScalarsF &sfd,
+                                                     const KinParams<A> &K, const StateDev<S> &st, int *err, int a,
+                                                     int i0)
 {
-    constexpr bool FAST = !std::is_same<S, double>::value; // the deviation forms: certified FP32 decisions
+    constexpr bool FAST = !std::is_same<S, double>::value; // the deviation forms keep the element cache
     const int N = M.N;
     const double2 Xa = M.X[a];
     bool have64 = false;
@@ -38,7 +69,7 @@ __device__ __forceinline__ void quad_stream_pops(const QuadDev &M, const MapStat
     float4 Xf = make_float4(0.f, 0.f, 0.f, 0.f);
     FastMap F;
     F.ok = false;
-    if (FAST) {
+    if (FAST && TRY) {
         Xf = M.Xf[a];
         F = fast_map(MS, sfd, a, Xf);
         if (K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
@@ -47,27 +78,7 @@ __device__ __forceinline__ void quad_stream_pops(const QuadDev &M, const MapStat
     for (int i = i0; i < i0 + G; ++i) {
         A fi = 0, gi = 0;
         int src = -1;
-        if (FAST && F.ok) {
-            // the previous-step element, verified in FP32 with certified bounds
-            const int c = st.cache[i * N + a];
-            int e;
-            float cw[8];
-            float xi, eta;
-            if (quad_fast_decide(M, F, Xf, a, i, c, e, cw) && quad_newton_t<float>(cw, 1e-5f, 1e-4f, xi, eta)) {
-                A Nw[9];
-                shape9<A>((A)xi, (A)eta, Nw);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const int b = M.conn[9 * e + k];
-                    A fb, gb;
-                    fg_get(st.post, i, b, N, fb, gb);
-                    fi += Nw[k] * fb;
-                    gi += Nw[k] * gb;
-                }
-                fg_put(st.str, i, a, N, fi, gi);
-                continue;
-            }
-        }
+        if (FAST && TRY && F.ok && quad_fast_pop<S, A>(M, F, Xf, st, a, i)) continue;
         if (!have64 && !(K.flags & FLAG_EXACT_CHAR)) {
             double xX, xY, yX, yY;
             map_node(MS, scd, a, Xa.x, Xa.y, xX, xY, yX, yY, Vx, Vy);
@@ -114,7 +125,7 @@ __device__ __forceinline__ void quad_stream_pops(const QuadDev &M, const MapStat
         if (src >= 0) fg_get(st.post, i, src, N, fi, gi);
         fg_put(st.str, i, a, N, fi, gi);
     }
-    if (stats && walks) atomicAdd(stats, (unsigned long long)walks);
+
     if (miss) {
         if (!have64 || (K.flags & FLAG_MIDPOINT)) { // the wall condition's map: arrival time
             double xX, xY, yX, yY;
@@ -180,6 +191,7 @@ __device__ __forceinline__ void quad_stream_pops(const QuadDev &M, const MapStat
             fg_put(st.str, i, a, N, fi, gi);
         }
     }
+    return walks;
 }
 
 // Grid (node blocks, 9 / G direction groups): G directions per thread.
@@ -190,20 +202,58 @@ __global__ void __launch_bounds__(128) kq_stream(QuadDev M, MapStatic MS, MapSca
 {
     wait_prior_grid();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < M.N) quad_stream_pops<G>(M, MS, sc, scd, sfd, K, st, err, stats, a, G * blockIdx.y);
+    unsigned walks = 0;
+    if (a < M.N) walks = quad_stream_pops<G, true>(M, MS, sc, scd, sfd, K, st, err, a, G * blockIdx.y);
+    // one atomic per warp (all lanes here: blocks of whole warps)
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, walks);
+    if (stats && (threadIdx.x & 31u) == 0u && wsum) atomicAdd(stats, (unsigned long long)wsum);
 }
 
-// Directions per thread of kq_stream: one per population in both forms,
-// the most threads to hide the walks' dependent loads (measured at 150k
-// nodes, FP32 / FP64 per launch: 145 / 3,900 us at one, 184 / 4,000 at
-// three, 240 / 4,120 at nine).
-#ifndef ALELB_QUAD_G32
-#define ALELB_QUAD_G32 1
+// The deviation forms in two passes, as on triangles: kq_fast settles the
+// populations whose previous-step element passes the certified FP32 test
+// (one thread per population, grid y = direction) and lists the others;
+// kq_slow runs the exact path over the list, spread over all blocks, so
+// that the walks do not hold up the warps of settled populations.
+template <class S, class A>
+__global__ void __launch_bounds__(128) kq_fast(QuadDev M, MapStatic MS, MapScalarsF sfd, KinParams<A> K,
+                                               StateDev<S> st)
+{
+    wait_prior_grid();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    int code = 0;
+    if (a < M.N) {
+        const float4 Xf = M.Xf[a];
+        FastMap F = fast_map(MS, sfd, a, Xf);
+        if (K.flags & (FLAG_LITERAL_VG | FLAG_EXACT_CHAR)) F.ok = false;
+        code = F.ok && quad_fast_pop<S, A>(M, F, Xf, st, a, i) ? 0 : 1;
+    }
+    if (__any_sync(0xffffffffu, code != 0)) append_pop(st, a, M.N, i, code);
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(128) kq_slow(QuadDev M, MapStatic MS, MapScalars sc, MapScalars scd,
+                                               MapScalarsF sfd, KinParams<A> K, StateDev<S> st, int *err,
+                                               unsigned long long *stats)
+{
+    wait_prior_grid();
+    __shared__ unsigned pre[NQ + 1];
+    if (threadIdx.x == 0) work_prefix(st.wcount, pre);
+    __syncthreads();
+    const unsigned n = pre[NQ];
+    if (stats && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(stats, (unsigned long long)n);
+    for (unsigned w = spread_first(); w < n; w += spread_stride()) {
+        const int code = work_at(st.work, M.N, pre, w);
+        quad_stream_pops<1, false>(M, MS, sc, scd, sfd, K, st, err, code / NQ, code % NQ);
+    }
+}
+
+// Directions per thread of kq_stream (the FP64 form): one per population,
+// the most threads to hide the walks' dependent loads (3.90 ms per launch
+// at 150k nodes, against 4.00 at three and 4.12 at nine).
+#ifndef ALELB_QUAD_G
+#define ALELB_QUAD_G 1
 #endif
-#ifndef ALELB_QUAD_G64
-#define ALELB_QUAD_G64 1
-#endif
-static_assert(NQ % ALELB_QUAD_G32 == 0 && NQ % ALELB_QUAD_G64 == 0, "directions per thread");
+static_assert(NQ % ALELB_QUAD_G == 0, "directions per thread");
 
 // D_a = (mu / rho T) d_a Q'_aaa in the owner element (Eq. Xa); FP32 in the
 // deviation forms (the FP32 map and the node's FP32 owner-element J^{-1}),
@@ -423,9 +473,24 @@ cudaError_t quad_launch(alelb_solver *s, int kernel, const MapScalars &sc, const
         using A = typename std::remove_reference<decltype(K)>::type::Arith;
         switch (kernel) {
         case KT_STREAM: {
-            constexpr int G = std::is_same<S, double>::value ? ALELB_QUAD_G64 : ALELB_QUAD_G32;
+            constexpr int G = ALELB_QUAD_G;
             launch_pdl(kq_stream<S, A, G>, dim3((N + 127) / 128, NQ / G), dim3(128), s->stream, m->qdev, m->mst, sc,
                        scd, to_f32(scd, m->T), K, st, s->d_err, s->d_stats);
+            break;
+        }
+        case KT_FAST:
+            launch_pdl(kq_fast<S, A>, dim3((N + 127) / 128, NQ), dim3(128), s->stream, m->qdev, m->mst,
+                       to_f32(scd, m->T), K, st);
+            break;
+        case KT_SLOW: {
+            // every block resident at once (the list spread over all of them)
+            static const int per_sm = [] {
+                int v = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kq_slow<S, A>, 128, 0);
+                return v > 0 ? v : 1;
+            }();
+            launch_pdl(kq_slow<S, A>, dim3(per_sm * s->n_sm), dim3(128), s->stream, m->qdev, m->mst, sc, scd,
+                       to_f32(scd, m->T), K, st, s->d_err, s->d_stats);
             break;
         }
         case KT_MOMENTS:
