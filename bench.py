@@ -65,7 +65,7 @@ def workload(name="plunge150k"):
     return WORKLOADS[name]()
 
 
-def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4):
+def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4, fused=False):
     """Algorithmic bytes of one launch: every value the kernel must read or
     write, each counted once (FP32-deviation form: pop_bytes = fld_bytes = 4;
     16-bit forms: pop_bytes = 2, node fields still 4).
@@ -94,10 +94,18 @@ def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4
                     Q', mu/(rho T) written, FP64 coordinates, fan entries;
                     per element frame, neighbours, edge info, rank,
                     connectivity (92 B)
+    fused           the batched propagation fused with the moments: the
+                    propagation also writes Q'_x, Q'_y, mu/(rho T) of its
+                    nodes (counted for all N); the moments kernel reads every
+                    node's wall-mask word and does the rest for the pending
+                    nodes only, counted as exact_items nodes (an upper bound:
+                    a pending node has at least one listed population)
     """
     N, E, W, p, f = n_nodes, n_elems, exact_items, pop_bytes, fld_bytes
     if kernel == "k_stream_fast":
-        return N * (36 * p + 36 + 16 + 5) + E * 56
+        return N * (36 * p + 36 + 16 + 5 + (3 * f if fused else 0)) + E * 56
+    if kernel == "k_moments" and fused:
+        return N * 4 + min(N, W) * (18 * p + 3 * f + 4)
     if kernel == "k_stream_slow":
         return W * (4 + 16 + 14 * p + 4 + 104)
     if kernel == "k_moments":
@@ -122,9 +130,15 @@ NCU_TRAFFIC_150K = {"k_stream_fast": 23.93e6, "k_stream_slow": 1.48e6, "k_moment
                     "k_deriv1": 7.21e6, "k_collide": 17.45e6}
 
 
-# DRAM bytes per launch of the batched phase kernels on the 32-case sweep,
-# from one ncu capture of the current kernels (filled in from profiles/).
-NCU_TRAFFIC_SWEEP = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# of 20 steady-state launches) of the batched phase kernels on the 32-case
+# sweep, from one ncu capture of the current kernels in the launch form
+# named here (profiles/launch_list_sweep32.md); a run whose tuner picks
+# another form reports no traffic.
+NCU_TRAFFIC_SWEEP_FORM = {"k_stream_fast_directions_per_thread": 9, "k_stream_fast_fused_moments": True,
+                          "k_stream_fast": 256}
+NCU_TRAFFIC_SWEEP = {"k_stream_fast": 963.27e6, "k_stream_slow": 42.93e6, "k_moments": 30.29e6,
+                     "k_deriv1": 213.71e6, "k_collide": 785.41e6}
 
 
 def measured_peaks():
@@ -327,6 +341,9 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     stream = torch.cuda.Stream(device=dev)
     b = alelb.Batch(solvers, stream=stream.cuda_stream)
     choice = b.tune(reps=3)
+    if args.choice:  # a fixed launch form (counter captures of one form)
+        b.set_choice([int(v) for v in args.choice.split(",")])
+        choice = dict(choice, forced=args.choice)
     b.step(max(3, args.warmup) - 1)
     b.sync()
     n_nodes = sum(c.mesh.n_nodes for c in cases)
@@ -379,10 +396,13 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
                               "barriers between phases"}
     kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in kt.items() if v[1]}
     rl = {}  # the phase kernels carry the single-case names (kb_fast runs as k_stream_fast, ...)
+    fused = bool(choice.get("k_stream_fast_fused_moments"))
+    same_form = all(choice.get(k) == v for k, v in NCU_TRAFFIC_SWEEP_FORM.items()) and args.sweep_scale == 1.0
     for k, v in kernels.items():
-        alg = kernel_bytes(k, n_nodes, n_elems, n_exact)
+        alg = kernel_bytes(k, n_nodes, n_elems, n_exact, fused=fused)
         if alg:
-            rl[k] = {"algorithmic_bytes": alg, "achieved_gbs": alg / (v["ms_per_launch"] * 1e-3) / 1e9}
+            rl[k] = {"algorithmic_bytes": alg, "achieved_gbs": alg / (v["ms_per_launch"] * 1e-3) / 1e9,
+                     "traffic": NCU_TRAFFIC_SWEEP.get(k) if same_form else None}
     b.close()
     for s in solvers:
         s.close()
@@ -933,7 +953,7 @@ def run_ours(args):
     top_rl = bat["kernel_rooflines"].get(top, {})
     roofline = {"bound": "hbm", "kernel": top, "achieved": top_rl.get("achieved_gbs"), "peak": peak,
                 "unit": "GB/s", "frac": (top_rl.get("achieved_gbs") or 0.0) / peak, "peak_source": peak_src,
-                "traffic": NCU_TRAFFIC_SWEEP.get(top), "algorithmic_bytes_per_launch": top_rl.get("algorithmic_bytes"),
+                "traffic": top_rl.get("traffic"), "algorithmic_bytes_per_launch": top_rl.get("algorithmic_bytes"),
                 "launch_ms": bat["kernels"][top]["ms_per_launch"],
                 "note": ("achieved = algorithmic bytes of one launch over the sweep / its CUDA-event duration "
                          "(launched one by one right after the timed region); traffic = ncu dram bytes of one "
@@ -1040,6 +1060,8 @@ def main():
                     help="node counts of the sweep's cases times this (1: the workload; smaller for counter captures)")
     ap.add_argument("--only-part", choices=["single", "q2", "learned"],
                     help="run one part alone, without the headline (for counter captures of its kernels)")
+    ap.add_argument("--choice", default="",
+                    help="after tuning, set the batch's launch shapes to these 8 values (alelb_batch_set_choice)")
     ap.add_argument("--only-batched", action="store_true",
                     help="the headline alone (no single case, e2e, network, precision, forces, CPU baseline)")
     args = ap.parse_args()
