@@ -1036,8 +1036,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000, help="timed steps of the batched sweep (the headline)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=8)
-    ap.add_argument("--cpu-steps-1core", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=64)
+    ap.add_argument("--cpu-steps-1core", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-steps", type=int, default=40)
     ap.add_argument("--no-single", action="store_true")
