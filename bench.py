@@ -422,21 +422,20 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
             s.get_pops(f, g)
             host.append((f, g))
         Ke = args.e2e_steps
-        t_now = [s.time()[0] for s in solvers]
+        t_now = np.array([s.time()[0] for s in solvers])
+        hf, hg = [f for f, _ in host], [g for _, g in host]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(Ke):
-            for s, (f, g), t in zip(solvers, host, t_now):
-                s.set_pops(f, g, t=t + k)
+            b.set_pops(hf, hg, t=t_now + k)
             b.step(1)
-            for s, (f, g) in zip(solvers, host):
-                s.get_pops(f, g)
+            b.get_pops(hf, hg)
         dt = time.perf_counter() - t0
         bytes_step = 18 * 8 * n_nodes
         e2e = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                "d2h_bytes_per_step": bytes_step, "steps": Ke,
-               "note": "host-resident state: per step alelb_set_pops of every case from pinned FP64 host "
-                       "arrays, alelb_batch_step(1), alelb_get_pops of every case (fresh batch, "
+               "note": "host-resident state: per step alelb_batch_set_pops (every case's populations from "
+                       "pinned FP64 host arrays), alelb_batch_step(1), alelb_batch_get_pops (fresh batch, "
                        "free-stream start)"}
         b.close()
     return {"value": n_total * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "steps": K,

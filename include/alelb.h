@@ -372,6 +372,21 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    Synchronous. */
 alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
 
+/* The host exchange of alelb_get_pops / alelb_set_pops for every case of
+   the batch in one call (the paper has no counterpart).  f[c], g[c]: host
+   arrays of case c, [9][n_nodes of case c] FP64 each, the caller's node
+   order (pinned memory lets the copies run at the link's rate).  Every
+   case's copies and kernels are queued before the call waits on any of
+   them, so the cases' copies overlap one another and the other cases'
+   kernels.  set: the populations become the cases' post-collision state,
+   with the fields they imply (as alelb_set_pops without fields), and, when
+   t is not NULL, case c's time becomes t[c].  Both return once the caller's
+   arrays may be reused; ALELB_ERR_ARG for a NULL array; get reports a
+   case's sticky error (and names the case) like alelb_batch_sync. */
+alelb_status alelb_batch_set_pops(alelb_batch *b, const double *const *f, const double *const *g,
+                                  const double *t);
+alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *const *g);
+
 /* Sets the launch shapes that alelb_batch_tune would choose, in its
    encoding (for example a choice saved from an earlier tuning):
    block sizes 64, 128 or 256; a k_stream_slow grid of 1 .. 64 x the SM

@@ -48,7 +48,8 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_batch_last_error", "alelb_mlp_create", "alelb_mlp_destroy", "alelb_mlp_get_params",
            "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
            "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
-           "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait", "alelb_batch_set_choice"]
+           "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait", "alelb_batch_set_choice",
+           "alelb_batch_set_pops", "alelb_batch_get_pops"]
 
 
 class AlelbError(RuntimeError):
@@ -135,6 +136,8 @@ def load(path: str = LIB_PATH):
     L.alelb_batch_set_mode.argtypes = [p, i32]
     L.alelb_batch_set_wait.argtypes = [p, d, i32]
     L.alelb_batch_set_choice.argtypes = [p, p]
+    L.alelb_batch_set_pops.argtypes = [p, p, p, p]
+    L.alelb_batch_get_pops.argtypes = [p, p, p]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -406,6 +409,32 @@ class Batch:
     def set_wait(self, limit_seconds=1.0, missing_arrivals=0):
         self._check(load().alelb_batch_set_wait(self.h, float(limit_seconds), int(missing_arrivals)),
                     "batch_set_wait")
+
+    def _planes(self, arrs, writable):
+        ptrs = (C.c_void_p * len(arrs))()
+        for c, (a, s) in enumerate(zip(arrs, self.solvers)):
+            a = np.asarray(a)
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != 9 * s.nn or \
+                    (writable and not a.flags.writeable):
+                raise ValueError(f"case {c}: a C-contiguous float64 array of 9 x {s.nn} values")
+            ptrs[c] = a.ctypes.data
+        return ptrs
+
+    def set_pops(self, f, g, t=None):
+        """Every case's populations from host arrays (caller's node order),
+        one call; t: the cases' times (or None to keep them)."""
+        if len(f) != len(self.solvers) or len(g) != len(self.solvers):
+            raise ValueError("one f and one g array per case")
+        tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
+        self._check(load().alelb_batch_set_pops(self.h, self._planes(f, False), self._planes(g, False),
+                                                None if tt is None else _ptr(tt)), "batch_set_pops")
+
+    def get_pops(self, f, g):
+        """Every case's post-collision populations into host arrays."""
+        if len(f) != len(self.solvers) or len(g) != len(self.solvers):
+            raise ValueError("one f and one g array per case")
+        self._check(load().alelb_batch_get_pops(self.h, self._planes(f, True), self._planes(g, True)),
+                    "batch_get_pops")
 
     def set_choice(self, choice):
         """Launch shapes in alelb_batch_tune's encoding (8 int32 values)."""

@@ -692,6 +692,16 @@ namespace {
 // are skipped.
 alelb_status export_to_host(alelb_solver *s, double *f, double *g, double *const fld[4])
 {
+    const cudaError_t st = export_enqueue(s, f, g, fld);
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    return alelb_sync(s);
+}
+} // namespace
+
+// The exchange's device side, queued without waiting (the batched exchange
+// queues every case before it waits once per case).
+cudaError_t alelb::export_enqueue(alelb_solver *s, double *f, double *g, double *const fld[4])
+{
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
     double *dfields = s->d_scratch + (size_t)18 * N;
@@ -724,10 +734,8 @@ alelb_status export_to_host(alelb_solver *s, double *f, double *g, double *const
             st = cudaMemcpyAsync(fld[c], dfields + (size_t)c * N, (size_t)N * sizeof(double),
                                  cudaMemcpyDeviceToHost, s->stream);
     if (st == cudaSuccess && f) st = cudaStreamWaitEvent(s->stream, s->ev_copy[1], 0); // the f copy too
-    if (st != cudaSuccess) return cuda_fail(s, st);
-    return alelb_sync(s);
+    return st;
 }
-} // namespace
 
 extern "C" alelb_status alelb_moments(alelb_solver *s, double *rho, double *ux, double *uy, double *T)
 {
@@ -747,6 +755,16 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
                                        const double *T, double t)
 {
     if (!s || !f || !g) return ALELB_ERR_ARG;
+    cudaError_t st = import_enqueue(s, f, g, rho, ux, uy, T);
+    if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the caller's arrays are free again
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    s->t = t;
+    return ALELB_OK;
+}
+
+cudaError_t alelb::import_enqueue(alelb_solver *s, const double *f, const double *g, const double *rho,
+                                  const double *ux, const double *uy, const double *T)
+{
     const int N = s->mesh->T.N;
     const bool have = rho && ux && uy && T;
     const size_t plane = (size_t)9 * N * sizeof(double);
@@ -763,7 +781,7 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
         st = cudaMemcpyAsync(dfields + (size_t)c * N, fl[c], (size_t)N * sizeof(double), cudaMemcpyHostToDevice,
                              s->copy_stream);
     if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
-    if (st != cudaSuccess) return cuda_fail(s, st);
+    if (st != cudaSuccess) return st;
     const dim3 grid((N + 255) / 256), block(256);
     with_state(s, [&](auto &sx, auto &) {
         k_import<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, s->d_scratch, dfields, have, s->Cv, s->U[0],
@@ -777,10 +795,7 @@ extern "C" alelb_status alelb_set_pops(alelb_solver *s, const double *f, const d
                                                     have, s->Cv, s->U[0], s->U[1], s->mesh->d_n2o, dfields, 1);
         });
     if (st == cudaSuccess) st = cudaGetLastError();
-    if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the caller's arrays are free again
-    if (st != cudaSuccess) return cuda_fail(s, st);
-    s->t = t;
-    return ALELB_OK;
+    return st;
 }
 
 extern "C" alelb_status alelb_forces(alelb_solver *s, double out[6])

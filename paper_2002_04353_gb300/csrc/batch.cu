@@ -639,6 +639,7 @@ struct alelb_batch {
     int slot = 0;
     std::vector<cudaEvent_t> ev_in;
     cudaEvent_t ev_done = nullptr;
+    int *h_err = nullptr; // pinned: every case's error word, read in one wait
     // launch shapes (threads per block per kernel; blocks of k_stream_slow)
     int bs[KT_N] = {128, 128, 128, 256, 256, 128, 128};
     int slow_grid = 0;
@@ -1010,6 +1011,7 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     for (int c = 0; c < B && st == cudaSuccess; ++c)
         st = cudaEventCreateWithFlags(&b->ev_in[c], cudaEventDisableTiming);
     if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    if (st == cudaSuccess) st = cudaHostAlloc((void **)&b->h_err, sizeof(int) * B, 0);
     // the table uploads above run on the legacy default stream, which the
     // batch's non-blocking stream does not wait for
     if (st == cudaSuccess) st = cudaDeviceSynchronize();
@@ -1027,6 +1029,7 @@ extern "C" void alelb_batch_destroy(alelb_batch *b)
     for (cudaEvent_t e : b->ev_in)
         if (e) cudaEventDestroy(e);
     if (b->ev_done) cudaEventDestroy(b->ev_done);
+    if (b->h_err) cudaFreeHost(b->h_err);
     for (int sl = 0; sl < 2; ++sl) {
         if (b->h_ev[sl]) cudaEventDestroy(b->h_ev[sl]);
         if (b->h_sc[sl]) cudaFreeHost(b->h_sc[sl]);
@@ -1329,6 +1332,62 @@ extern "C" alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **na
         if (launches) launches[k] = b->n_acc[k];
     }
     *n = m;
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_set_pops(alelb_batch *b, const double *const *f, const double *const *g,
+                                             const double *t)
+{
+    if (!b || !f || !g) return ALELB_ERR_ARG;
+    for (int c = 0; c < b->B; ++c)
+        if (!f[c] || !g[c]) return ALELB_ERR_ARG;
+    // every case's copies and kernels are queued first (on its own streams,
+    // so that the copies of different cases overlap), then the batch's
+    // stream joins all of them and one wait covers the lot
+    cudaError_t st = cudaSuccess;
+    for (int c = 0; c < b->B && st == cudaSuccess; ++c)
+        st = import_enqueue(b->cs[c], f[c], g[c], nullptr, nullptr, nullptr, nullptr);
+    if (st == cudaSuccess) st = join_cases(b);
+    const cudaError_t sw = cudaStreamSynchronize(b->stream);
+    if (st == cudaSuccess) st = sw;
+    if (st != cudaSuccess) {
+        for (int c = 0; c < b->B; ++c) cudaStreamSynchronize(b->cs[c]->stream);
+        return bfail(b, st, "batch_set_pops");
+    }
+    if (t)
+        for (int c = 0; c < b->B; ++c) b->cs[c]->t = t[c];
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *const *g)
+{
+    if (!b || !f || !g) return ALELB_ERR_ARG;
+    for (int c = 0; c < b->B; ++c)
+        if (!f[c] || !g[c]) return ALELB_ERR_ARG;
+    // every case's kernels, copies and error word queued, then one wait
+    cudaError_t st = cudaSuccess;
+    for (int c = 0; c < b->B && st == cudaSuccess; ++c) {
+        alelb_solver *s = b->cs[c];
+        st = export_enqueue(s, f[c], g[c], nullptr);
+        if (st == cudaSuccess)
+            st = cudaMemcpyAsync(b->h_err + c, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (st == cudaSuccess) st = join_cases(b);
+    const cudaError_t sw = cudaStreamSynchronize(b->stream);
+    if (st == cudaSuccess) st = sw;
+    if (st != cudaSuccess) {
+        for (int c = 0; c < b->B; ++c) cudaStreamSynchronize(b->cs[c]->stream);
+        return bfail(b, st, "batch_get_pops");
+    }
+    for (int c = 0; c < b->B; ++c) {
+        alelb_solver *s = b->cs[c];
+        s->sticky |= b->h_err[c];
+        const alelb_status r = check_sticky(s);
+        if (r != ALELB_OK) {
+            b->err = "case " + std::to_string(c) + ": " + s->err;
+            return r;
+        }
+    }
     return ALELB_OK;
 }
 

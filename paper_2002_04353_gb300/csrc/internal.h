@@ -67,6 +67,12 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
 
 // FP32 copies of the per-step map scalars.
 MapScalarsF to_f32(const MapScalars &S, const HostTables &T);
+// the host exchange's copies and kernels for one solver, queued on its
+// streams without waiting (alelb_set_pops / alelb_get_pops and their
+// batched forms wait afterwards)
+cudaError_t import_enqueue(alelb_solver *s, const double *f, const double *g, const double *rho,
+                           const double *ux, const double *uy, const double *T);
+cudaError_t export_enqueue(alelb_solver *s, double *f, double *g, double *const fld[4]);
 // Uploads the P2 derivative tables of batch.cu's module.
 cudaError_t batch_fe_tables();
 // Status of a solver's sticky device errors (message in s->err).

@@ -189,6 +189,42 @@ def test_set_choice_refuses_unknown_forms():
     b64.set_choice([128, 128, 128, 256, 256, 128, 64, 9])
 
 
+def test_batched_host_exchange_matches_the_per_case_calls():
+    """alelb_batch_set_pops / alelb_batch_get_pops move what the per-case
+    calls move, bit for bit, and set the cases' times."""
+    cases = _cases()
+    for prec in (alelb.PREC_FP64, alelb.PREC_FP32_DEV):
+        ss = _solvers(cases, prec)
+        b = alelb.Batch(ss)
+        b.step(4)
+        b.sync()
+        n = [s.nn for s in ss]
+        hf = [np.empty((9, k)) for k in n]
+        hg = [np.empty((9, k)) for k in n]
+        b.get_pops(hf, hg)
+        for s, f, g in zip(ss, hf, hg):
+            fa, ga = s.get_pops()
+            assert np.array_equal(f, fa) and np.array_equal(g, ga)
+        # set every case back from perturbed arrays at new times, then read again
+        rng = np.random.default_rng(3)
+        pf = [f * (1 + 1e-6 * rng.standard_normal(f.shape)) for f in hf]
+        pg = [g * (1 + 1e-6 * rng.standard_normal(g.shape)) for g in hg]
+        t = np.arange(len(ss), dtype=np.float64) + 10.0
+        b.set_pops(pf, pg, t=t)
+        alone = _solvers(cases, prec)
+        for s, f, g, tc in zip(alone, pf, pg, t):
+            s.set_pops(f, g, t=tc)
+        for sa, sb, tc in zip(alone, ss, t):
+            assert sb.time()[0] == tc
+            fa, ga = sa.get_pops()
+            fb, gb = sb.get_pops()
+            assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+        with pytest.raises(ValueError):
+            b.get_pops(hf[:-1], hg[:-1])
+        with pytest.raises(ValueError):
+            b.set_pops([f.astype(np.float32) for f in pf], pg)
+
+
 def test_batch_and_single_steps_interleave():
     cases = _cases()[:2]
     alone = _solvers(cases, alelb.PREC_FP64)
