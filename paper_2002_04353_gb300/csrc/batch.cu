@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256) kb_deriv1_staged(const CaseDev<float, flo
     C.st.Dy[a] = m * dQy;
 }
 
-__global__ void __launch_bounds__(256) kb_collide_staged(const CaseDev<float, float> *__restrict__ cases,
+__global__ void __launch_bounds__(256, 4) kb_collide_staged(const CaseDev<float, float> *__restrict__ cases,
                                                          const int *__restrict__ off, int B,
                                                          const MapScalarsF *__restrict__ sf, int stage)
 {
