@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restric
 // The propagation of the FP32 form fused with the moments: a block holds
 // the NQ / G direction groups of a tile of T nodes (group-uniform warps),
 // each thread settles its G populations as kb_fast does and leaves the
-// settled pairs in shared memory; then one thread per node computes the
+// settled pairs in shared memory; then (after a block barrier when G < 9)
+// one thread per node computes the
 // node's moments from them, exactly as the moments kernel would, unless a
 // population of the node went to the exact path or its wall condition:
 // then the node is marked WMASK_PENDING and the moments kernel takes it.
@@ -247,7 +248,9 @@ __global__ void __launch_bounds__(T *NQ / G) kb_fast_fused(const CaseDev<float, 
         for (int j = 0; j < G; ++j) append_pop(st, a, M.N, i0 + j, code[j]);
     }
     pend[grp][tx] = any;
-    __syncthreads(); // every group's pairs and wall bits of the tile are in
+    // every group's pairs and wall bits of the tile are in; with one thread
+    // per node (G = 9) a thread reads back only what it wrote itself
+    if (NG > 1) __syncthreads();
     if (grp == 0 && a < M.N) {
         int p = 0;
 #pragma unroll

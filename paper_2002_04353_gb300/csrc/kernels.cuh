@@ -520,10 +520,6 @@ __device__ __forceinline__ void stream_bc_node(const MeshDev &M, const MapStatic
         }
 }
 
-#ifndef ALELB_FAST_EARLY_CONN
-#define ALELB_FAST_EARLY_CONN 0
-#endif
-
 // Population i of node a (one thread each): interpolated when its
 // previous-step element is verified, the node's own value when c^_0 is
 // exactly zero, free-stream equilibria when certified missing at the far
@@ -546,32 +542,18 @@ __device__ __forceinline__ int stream_fast_pop(const MeshDev &M, const KinParams
     if (!F.ok) return 1;
     int e;
     float xi, eta;
-    // the element's six nodes in three 8-byte loads (conn is 8-byte aligned
-    // at every element: 24 bytes per element); with ALELB_FAST_EARLY_CONN
-    // they are requested together with the element's inverse Jacobian,
-    // before the test, so that an accepted population waits on two rounds
-    // of loads after its cache word instead of three
-    int nb[6];
-    if (ALELB_FAST_EARLY_CONN && c >= 0) {
-        const int2 *cp = reinterpret_cast<const int2 *>(M.conn + 6 * (c & CACHE_ELEM));
+    if (fast_decide(M, F, Xf, bd, a, i, c, e, xi, eta)) {
+        A Nw[6];
+        shape6<A>((A)xi, (A)eta, Nw);
+        // the element's six nodes in three 8-byte loads (conn is 8-byte
+        // aligned at every element: 24 bytes per element)
+        int nb[6];
+        const int2 *cp = reinterpret_cast<const int2 *>(M.conn + 6 * e);
 #pragma unroll
         for (int h = 0; h < 3; ++h) {
             const int2 v = cp[h];
             nb[2 * h] = v.x;
             nb[2 * h + 1] = v.y;
-        }
-    }
-    if (fast_decide(M, F, Xf, bd, a, i, c, e, xi, eta)) {
-        A Nw[6];
-        shape6<A>((A)xi, (A)eta, Nw);
-        if (!ALELB_FAST_EARLY_CONN) {
-            const int2 *cp = reinterpret_cast<const int2 *>(M.conn + 6 * e);
-#pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                const int2 v = cp[h];
-                nb[2 * h] = v.x;
-                nb[2 * h + 1] = v.y;
-            }
         }
         A fi = 0, gi = 0;
 #pragma unroll
