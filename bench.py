@@ -96,8 +96,8 @@ def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4
                     connectivity (92 B)
     fused           the batched propagation fused with the moments: the
                     propagation also writes Q'_x, Q'_y, mu/(rho T) of its
-                    nodes (counted for all N); the moments kernel reads every
-                    node's wall-mask word and does the rest for the pending
+                    nodes (counted for all N) and lists the pending nodes;
+                    the moments kernel reads the list and does the pending
                     nodes only, counted as exact_items nodes (an upper bound:
                     a pending node has at least one listed population)
     """
@@ -105,7 +105,7 @@ def kernel_bytes(kernel, n_nodes, n_elems, exact_items, pop_bytes=4, fld_bytes=4
     if kernel == "k_stream_fast":
         return N * (36 * p + 36 + 16 + 5 + (3 * f if fused else 0)) + E * 56
     if kernel == "k_moments" and fused:
-        return N * 4 + min(N, W) * (18 * p + 3 * f + 4)
+        return min(N, W) * (4 + 18 * p + 3 * f + 4)
     if kernel == "k_stream_slow":
         return W * (4 + 16 + 14 * p + 4 + 104)
     if kernel == "k_moments":

@@ -93,9 +93,9 @@ template <class S> void put_state(DevBuf &b, StateDev<S> &s, int N, cudaError_t 
     s.Dy = b.alloc<F>(N, st);
     s.cache = b.alloc<int>((size_t)9 * N, st);
     if (st == cudaSuccess) st = cudaMemset(s.cache, 0xff, (size_t)9 * N * sizeof(int)); // -1: empty
-    s.work = b.alloc<int>((size_t)10 * N, st);
-    s.wcount = b.alloc<unsigned>(NQ + 1, st);
-    if (st == cudaSuccess) st = cudaMemset(s.wcount, 0, (NQ + 1) * sizeof(unsigned));
+    s.work = b.alloc<int>((size_t)(SEG_PENDING + 1) * N, st);
+    s.wcount = b.alloc<unsigned>(SEG_PENDING + 1, st);
+    if (st == cudaSuccess) st = cudaMemset(s.wcount, 0, (SEG_PENDING + 1) * sizeof(unsigned));
     s.wmask = b.alloc<unsigned>(N, st);
     if (st == cudaSuccess) st = cudaMemset(s.wmask, 0, (size_t)N * sizeof(unsigned));
 }
@@ -169,6 +169,14 @@ extern "C" alelb_status alelb_mesh_create(const alelb_mesh_desc *d, alelb_mesh *
     D.fan_ptr = B.put(T.fan_ptr, st);
     D.fan = B.put(T.fan, st);
     D.owner = B.put(T.owner, st);
+    T.ostn.resize((size_t)2 * T.N);
+    for (int a = 0; a < T.N; ++a) {
+        const int e = T.owner[a].x;
+        const int *c = T.conn.data() + (size_t)6 * e;
+        T.ostn[2 * a] = make_int4(c[0], c[1], c[2], c[3]);
+        T.ostn[2 * a + 1] = make_int4(c[4], c[5], e, T.owner[a].y);
+    }
+    D.ostn = B.put(T.ostn, st);
     D.bcel = B.put(T.bcel, st);
     D.ring_ptr = B.put(T.ring_ptr, st);
     D.ring = B.put(T.ring, st);

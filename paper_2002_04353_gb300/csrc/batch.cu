@@ -175,11 +175,9 @@ __global__ void __launch_bounds__(256) kb_slow(const CaseDev<S, A> *__restrict__
     }
 }
 
-// pending: the fused propagation ran (kb_fast_fused) and computed the
-// moments of every node but those it marked WMASK_PENDING.
 template <class S, class A>
 __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restrict__ cases,
-                                                  const int *__restrict__ off, int B, int pending)
+                                                  const int *__restrict__ off, int B)
 {
     wait_prior_grid();
     __shared__ SharedCase<S, A> sh;
@@ -189,19 +187,59 @@ __global__ void __launch_bounds__(256) kb_moments(const CaseDev<S, A> *__restric
     const CaseDev<S, A> &C = sh.C();
     const int a = (blockIdx.x - __ldg(off + c)) * blockDim.x + threadIdx.x;
     if (a <= NQ) C.st.wcount[a] = 0u; // the case's work list has been consumed
-    if (a < C.M.N && (!pending || (C.st.wmask[a] & WMASK_PENDING))) moments_node(C.K, C.st, C.M.N, C.err, a);
+    if (a < C.M.N) moments_node(C.K, C.st, C.M.N, C.err, a);
+}
+
+// After the fused propagation (kb_fast_fused): the moments of the nodes it
+// listed as pending.  All cases' lists form one numbering (a warp scan of
+// the B counts into shared memory, the case of an entry by binary search),
+// dealt out over the whole grid; the case descriptors are read from global
+// memory.  The pending list itself is emptied by the collision kernel, once
+// every reader is done.
+template <class S, class A>
+__global__ void __launch_bounds__(256) kb_moments_pending(const CaseDev<S, A> *__restrict__ cases, int B)
+{
+    wait_prior_grid();
+    __shared__ unsigned pre[BATCH_MAX + 1];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned v = lane < B ? cases[lane].st.wcount[SEG_PENDING] : 0u;
+        unsigned incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane < B) pre[lane + 1] = incl;
+        if (lane == 0) pre[0] = 0u;
+    }
+    __syncthreads();
+    const unsigned total = pre[B];
+    const unsigned stride = gridDim.x * blockDim.x, first = blockIdx.x * blockDim.x + threadIdx.x;
+    for (unsigned w = first; w < total; w += stride) {
+        int lo = 0, hi = B - 1; // last case with pre <= w
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const CaseDev<S, A> &C = cases[lo];
+        const int N = C.M.N;
+        moments_node(C.K, C.st, N, C.err, C.st.work[(size_t)SEG_PENDING * N + (w - pre[lo])]);
+    }
+    if (first < (unsigned)(B * (NQ + 1))) // every case's exact-path list has been consumed
+        cases[first / (NQ + 1)].st.wcount[first % (NQ + 1)] = 0u;
 }
 
 // The propagation of the FP32 form fused with the moments: a block holds
 // the NQ / G direction groups of a tile of T nodes (group-uniform warps),
 // each thread settles its G populations as kb_fast does and leaves the
 // settled pairs in shared memory; then (after a block barrier when G < 9)
-// one thread per node computes the
-// node's moments from them, exactly as the moments kernel would, unless a
-// population of the node went to the exact path or its wall condition:
-// then the node is marked WMASK_PENDING and the moments kernel takes it.
-// The nodes the exact path never touches are read once per step instead of
-// twice.
+// one thread per node computes the node's moments from them, exactly as the
+// moments kernel would, unless a population of the node went to the exact
+// path or its wall condition: then the node goes to the pending list, which
+// kb_moments_pending works through.  The nodes the exact path never touches
+// are read once per step instead of twice.
 template <int G, int T>
 __global__ void __launch_bounds__(T *NQ / G) kb_fast_fused(const CaseDev<float, float> *__restrict__ cases,
                                                            const int *__restrict__ off, int B,
@@ -251,13 +289,23 @@ __global__ void __launch_bounds__(T *NQ / G) kb_fast_fused(const CaseDev<float, 
     // every group's pairs and wall bits of the tile are in; with one thread
     // per node (G = 9) a thread reads back only what it wrote itself
     if (NG > 1) __syncthreads();
+    int p = 0;
     if (grp == 0 && a < M.N) {
-        int p = 0;
 #pragma unroll
         for (int q = 0; q < NG; ++q) p |= pend[q][tx];
-        if (p) {
-            atomicOr(st.wmask + a, WMASK_PENDING);
-        } else {
+    }
+    // pending nodes to the moments kernel's list, one atomic per warp
+    const unsigned pm = __ballot_sync(0xffffffffu, p != 0);
+    if (pm) {
+        const unsigned lane = threadIdx.x & 31u;
+        const int leader = __ffs(pm) - 1;
+        unsigned base = 0;
+        if ((int)lane == leader) base = atomicAdd(st.wcount + SEG_PENDING, (unsigned)__popc(pm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (p) st.work[(size_t)SEG_PENDING * M.N + base + __popc(pm & ((1u << lane) - 1u))] = a;
+    }
+    if (grp == 0 && a < M.N) {
+        if (!p) {
             float f[NQ], g[NQ];
 #pragma unroll
             for (int i = 0; i < NQ; ++i) {
@@ -340,18 +388,21 @@ __device__ __forceinline__ StagedPair stage_pair(float *s0, float *s1, const flo
 __device__ __forceinline__ void owner_grad2_staged(const MeshDev &M, int a, const StagedPair &P, float &K0X,
                                                    float &K0Y, float &K1X, float &K1Y)
 {
-    const int2 ow = M.owner[a];
-    const int e = ow.x, l = ow.y;
+    const int4 p = M.ostn[2 * a], q = M.ostn[2 * a + 1];
+    const int e = q.z, l = q.w;
     const float4 J = M.ejf[2 * e + 1];
+    const int nb[6] = {p.x, p.y, p.z, p.w, q.x, q.y};
+    float nx[6], ne[6];
+    p2_dN_at_node(l, nx, ne);
     float s0x = 0.f, s0e = 0.f, s1x = 0.f, s1e = 0.f;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-        const int b = M.conn[6 * e + s];
+        const int b = nb[s];
         const float v0 = P.v0(b), v1 = P.v1(b);
-        s0x += v0 * c_dNxif[l][s];
-        s0e += v0 * c_dNetaf[l][s];
-        s1x += v1 * c_dNxif[l][s];
-        s1e += v1 * c_dNetaf[l][s];
+        s0x += v0 * nx[s];
+        s0e += v0 * ne[s];
+        s1x += v1 * nx[s];
+        s1e += v1 * ne[s];
     }
     K0X = s0x * J.x + s0e * J.z;
     K0Y = s0x * J.y + s0e * J.w;
@@ -400,6 +451,8 @@ __global__ void __launch_bounds__(256, 4) kb_collide_staged(const CaseDev<float,
     __syncthreads();
     const CaseDev<float, float> &C = sh.C();
     const int first = (blockIdx.x - __ldg(off + c)) * blockDim.x;
+    // the pending-moments list has been read (kb_moments_pending ran before)
+    if (first == 0 && threadIdx.x == 0) C.st.wcount[SEG_PENDING] = 0u;
     const StagedPair P = stage_pair(w0, w1, C.st.Dx, C.st.Dy, first, C.M.N, stage);
     __syncthreads();
     const int a = first + threadIdx.x;
@@ -437,7 +490,7 @@ __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
     if (c >= B) return;
     const StateDev<S> &st = cases[c].st;
     const int N = cases[c].M.N;
-    for (int i = 0; i <= NQ; ++i) {
+    for (int i = 0; i <= SEG_PENDING; ++i) {
         const unsigned n = st.wcount[i];
         for (unsigned k = threadIdx.x; k < n; k += blockDim.x) {
             const int e = st.work[(size_t)i * N + k];
@@ -445,7 +498,7 @@ __global__ void kb_clear_work(const CaseDev<S, A> *__restrict__ cases, int B)
         }
     }
     __syncthreads();
-    if (threadIdx.x <= NQ) st.wcount[threadIdx.x] = 0u;
+    if (threadIdx.x <= SEG_PENDING) st.wcount[threadIdx.x] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -777,8 +830,10 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, in
         launch_pdl(kb_slow<S, A>, dim3(grid), dim3(bs), b->stream, cases, B, sc, sf, count);
         break;
     case KT_MOMENTS:
-        launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B,
-                   (int)((fast_g & FAST_FUSED) != 0));
+        if (fast_g & FAST_FUSED) // the pending nodes only, over one wave of blocks
+            launch_pdl(kb_moments_pending<S, A>, dim3(b->n_sm * (2048 / bs)), dim3(bs), b->stream, cases, B);
+        else
+            launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B);
         break;
     case KT_DERIV1:
         if (fast)

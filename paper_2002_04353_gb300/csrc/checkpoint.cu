@@ -261,7 +261,7 @@ extern "C" alelb_status alelb_load(alelb_solver *s, const char *path)
     }
     // the exact-path work list is empty between steps
     with_state(s, [&](auto &sx, auto &) {
-        if (st == cudaSuccess) st = cudaMemsetAsync(sx.wcount, 0, (NQ + 1) * sizeof(unsigned), s->stream);
+        if (st == cudaSuccess) st = cudaMemsetAsync(sx.wcount, 0, (SEG_PENDING + 1) * sizeof(unsigned), s->stream);
         if (st == cudaSuccess) st = cudaMemsetAsync(sx.wmask, 0, (size_t)m->T.N * sizeof(unsigned), s->stream);
     });
     if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the host buffer is released below

@@ -505,6 +505,8 @@ struct MeshDev {
     const int *fan_ptr;    // [N+1]
     const int2 *fan;       // (elem, loc | (sx+1)<<4 | (sy+1)<<6)
     const int2 *owner;     // (elem, local index) of each node
+    const int4 *ostn;      // [2N] owner element's six node numbers, then (elem, local index):
+                           // {n0, n1, n2, n3}, {n4, n5, elem, local} (the derivative passes)
     const int *bcel;       // element of each node's wall-condition gradients
     const int *ring_ptr;   // [N + 1] neighbour ring of each node (learned proposal)
     const int *ring;       // ring elements, cache code of an unshifted element

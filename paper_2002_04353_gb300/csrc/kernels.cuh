@@ -139,17 +139,19 @@ template <class S> struct StateDev {
     F *Dx, *Dy;           // first-pass results
     int *cache;           // [9 N] element of each population's previous departure point
                           // (elem | (sx+1)<<28 | (sy+1)<<30), -1 when empty
-    int *work;            // [10 N] populations (9 node + direction) left to the exact path,
+    int *work;            // [11 N] populations (9 node + direction) left to the exact path,
                           // direction i's at work[i N + k], k < wcount[i]; then the nodes
                           // with populations certified missing at a wall, at work[9 N + k],
-                          // k < wcount[9], their directions in wmask
-    unsigned *wcount;     // [10] entries of each segment
+                          // k < wcount[9], their directions in wmask; then the nodes whose
+                          // moments the fused batched propagation left to the moments
+                          // kernel, at work[10 N + k], k < wcount[10]
+    unsigned *wcount;     // [11] entries of each segment
     unsigned *wmask;      // [N] directions certified missing at a wall (bits 0-8); set by the
                           // propagation kernel, read by the exact path, cleared by the
-                          // moments kernel; WMASK_PENDING: the fused batched propagation
-                          // left the node's moments to the moments kernel
+                          // moments kernel
 };
-constexpr unsigned WMASK_DIRS = (1u << NQ) - 1u, WMASK_PENDING = 1u << 31;
+constexpr unsigned WMASK_DIRS = (1u << NQ) - 1u;
+constexpr int SEG_PENDING = NQ + 1; // the pending-moments segment of the work list
 
 // The exact-path kernels number the work list direction by direction
 // (populations of one direction at neighbouring nodes take similar paths,
@@ -915,19 +917,49 @@ static inline cudaError_t upload_fe_tables()
     return st;
 }
 
+// d N_s / d xi and d N_s / d eta of the P2 shape functions at local node l,
+// from its local coordinates (0, 1/2 or 1, as 2-bit fields of one word):
+// the values of the c_dNxif / c_dNetaf tables, exact in FP32, without a
+// per-thread index into constant memory (which serialises when the lanes'
+// l differ).
+__device__ __forceinline__ void p2_dN_at_node(int l, float nx[6], float ne[6])
+{
+    const float xi = 0.5f * (float)((0x148u >> (2 * l)) & 3u);
+    const float eta = 0.5f * (float)((0x520u >> (2 * l)) & 3u);
+    const float l0 = (1.0f - xi) - eta;
+    nx[0] = -(4.0f * l0 - 1.0f);
+    nx[1] = 4.0f * xi - 1.0f;
+    nx[2] = 0.0f;
+    nx[3] = 4.0f * (l0 - xi);
+    nx[4] = 4.0f * eta;
+    nx[5] = -4.0f * eta;
+    ne[0] = -(4.0f * l0 - 1.0f);
+    ne[1] = 0.0f;
+    ne[2] = 4.0f * eta - 1.0f;
+    ne[3] = -4.0f * xi;
+    ne[4] = 4.0f * xi;
+    ne[5] = 4.0f * (l0 - eta);
+}
+
+// The FP32 derivative passes read each node's owner stencil from one
+// per-node record (MeshDev::ostn), so the node values they gather wait on
+// one load, not on the owner record and then the element's node numbers.
 template <class S>
 __device__ __forceinline__ void owner_grad_f32(const MeshDev &M, int a, const S *K, float &KX,
                                                float &KY)
 {
-    const int2 ow = M.owner[a];
-    const int e = ow.x, l = ow.y;
+    const int4 p = M.ostn[2 * a], q = M.ostn[2 * a + 1];
+    const int e = q.z, l = q.w;
     const float4 J = M.ejf[2 * e + 1];
+    const int nb[6] = {p.x, p.y, p.z, p.w, q.x, q.y};
+    float nx[6], ne[6];
+    p2_dN_at_node(l, nx, ne);
     float sxi = 0.f, seta = 0.f;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-        const float Ks = (float)K[M.conn[6 * e + s]];
-        sxi += Ks * c_dNxif[l][s];
-        seta += Ks * c_dNetaf[l][s];
+        const float Ks = (float)K[nb[s]];
+        sxi += Ks * nx[s];
+        seta += Ks * ne[s];
     }
     KX = sxi * J.x + seta * J.z;
     KY = sxi * J.y + seta * J.w;

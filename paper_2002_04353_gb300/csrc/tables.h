@@ -59,6 +59,7 @@ struct HostTables {
     std::vector<float2> nscale;
     std::vector<uint32_t> einfo;
     std::vector<int2> fan, owner, wedges;
+    std::vector<int4> ostn; // [2N] owner stencils (MeshDev::ostn)
     std::vector<uint8_t> bkind, vzero, conek;
     std::vector<float4> cone;
     std::vector<double> ms;
@@ -86,6 +87,7 @@ struct HostTables {
         D.fan_ptr = fan_ptr.data();
         D.fan = fan.data();
         D.owner = owner.data();
+        D.ostn = ostn.data();
         D.bcel = bcel.data();
         D.bkind = bkind.data();
         D.vzero = vzero.data();
