@@ -128,7 +128,7 @@ SWEEP_NAME = "batched_sweep_32_naca00xx_4.06M"
 # FP32-deviation kernels on the 150,400-node plunge workload, from one ncu
 # capture of the current kernels; writes stay in L2 during these launches.
 NCU_TRAFFIC_150K = {"k_stream_fast": 23.93e6, "k_stream_slow": 1.48e6, "k_moments": 10.84e6,
-                    "k_deriv1": 7.21e6, "k_collide": 17.45e6}
+                    "k_deriv1": 9.02e6, "k_collide": 19.26e6}
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
