@@ -169,6 +169,30 @@ def test_every_launch_form_gives_the_same_bits():
             assert s.info()["walks"] == wr
 
 
+@pytest.mark.parametrize("flags", [O.FLAG_PHI_OFF, O.FLAG_OFFWALL_VG | O.FLAG_SLIP_WALL])
+def test_fused_form_with_run_options_gives_the_same_bits(flags):
+    """The fused propagation with its pending-moments list under run options
+    that change the step's kernel sequence (no derivative passes) or the
+    wall condition: the same bits as the plain form over 6 steps."""
+    import dataclasses
+    cases = [(m, mo, dataclasses.replace(fl, flags=flags)) for m, mo, fl in _cases()]
+    plain = _solvers(cases, alelb.PREC_FP32_DEV)
+    bp = alelb.Batch(plain)
+    bp.set_choice([128, 128, 128, 256, 256, 128, 64, 9])
+    bp.step(6)
+    bp.sync()
+    fused = _solvers(cases, alelb.PREC_FP32_DEV)
+    bf = alelb.Batch(fused)
+    bf.set_choice([128, 256, 128, 256, 256, 128, 64, 9 | 256])
+    bf.step(6)
+    bf.sync()
+    for c, (sa, sb) in enumerate(zip(plain, fused)):
+        fa, ga = sa.get_pops()
+        fb, gb = sb.get_pops()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), f"case {c}"
+        assert sa.info()["walks"] == sb.info()["walks"]
+
+
 def test_set_choice_refuses_unknown_forms():
     ss = _solvers(_cases()[:1], alelb.PREC_FP32_DEV)
     b = alelb.Batch(ss)
