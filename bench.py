@@ -273,6 +273,50 @@ def cpu_baseline(sweep, steps, threads):
     return work / dt / 1e6, dt, used, work
 
 
+def oracle_rate(case, steps, threads, flow=None):
+    """The FP64 oracle on one case: `steps` steps after one untimed step, its
+    node loops on `threads` host threads, node-updates/s (a state that turns
+    non-finite restarts from the free stream, untimed)."""
+    import oracle as O
+    n0 = O.threads()
+    used = O.threads(threads)
+    fl = case.flow if flow is None else flow
+    work, dt = 0, 0.0
+    try:
+        o = O.Oracle(case.mesh, case.motion, fl)
+        o.step(1)
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            try:
+                o.step(1)
+                dt += time.perf_counter() - t0
+            except O.OracleError:
+                o = O.Oracle(case.mesh, case.motion, fl)
+                o.step(1)
+                continue
+            work += case.mesh.n_nodes
+        del o
+    finally:
+        O.threads(n0)
+    return work / dt / 1e6, dt, used
+
+
+def oracle_timing(threads):
+    """The oracle on the paper-form configurations, all host threads: the
+    deforming box (200 steps) and a 20-step window of the 150k plunge.  (Its
+    set-up grows faster than linearly with the mesh -- 2.7 s at 150k nodes,
+    21 s at 600k, 128 s at 2M on an 8-core host -- so the larger meshes are
+    left out of the default run; the sweep's largest case, 281k nodes, is in
+    the CPU baseline.)"""
+    cases = {"box_9216_200_steps": (I.uniform_flow_case(), 200),
+             "plunge_150400_20_steps": (I.plunge_case(ni=320, nj=118), 20)}
+    out = {}
+    for name, (case, steps) in cases.items():
+        v, dt, used = oracle_rate(case, steps, threads)
+        out[name] = {"value": v, "unit": UNIT, "seconds": dt, "threads": used}
+    return out
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -771,6 +815,36 @@ def run_force_history(alelb, args):
     return out
 
 
+def run_sweep_seeds(alelb, torch, dev, args, seeds=(1, 2), steps=300):
+    """The same sweep drawn with other seeds (case sizes, Mach numbers and
+    motions differ): tuned, then `steps` graph-replayed steps timed with CUDA
+    events, as the headline."""
+    out = {}
+    for seed in seeds:
+        sweep = I.batched_sweep(seed=seed)
+        solvers = [alelb.Solver(alelb.Mesh(c.mesh, c.motion), sweep_lattice(c.flow), alelb.PREC_FP32_DEV)
+                   for c in sweep]
+        stream = torch.cuda.Stream(device=dev)
+        b = alelb.Batch(solvers, stream=stream.cuda_stream)
+        choice = b.tune(reps=3)
+        b.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        n = sum(c.mesh.n_nodes for c in sweep)
+        out[f"seed{seed}"] = {"value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                              "nodes": n, "fused_form": bool(choice.get("k_stream_fast_fused_moments")),
+                              "directions_per_thread": choice.get("k_stream_fast_directions_per_thread")}
+        b.close()
+        for s_ in solvers:
+            s_.close()
+    return out
+
+
 def run_element_stability(alelb, args):
     """How far the paper's airfoil runs get under its own wall targets (R8,
     correction phi on) on triangles and on the same rings as 9-node
@@ -971,6 +1045,7 @@ def run_ours(args):
                "achieved_gbs": mb / (ms_step * 1e-3) / 1e9, "frac": mb / (ms_step * 1e-3) / 1e9 / peak,
                "note": "the method's own bytes (populations once each way, derivative-pass fields, geometry)"}
 
+    seeds = None if (args.only_batched or world > 1) else run_sweep_seeds(alelb, torch, dev, args)
     single = None if args.no_single else run_single(alelb, torch, dev, world, args)
     q2 = None if (args.no_q2 or world > 1) else run_q2(alelb, torch, dev, args)
     learned = None if (args.no_mlp or world > 1) else run_learned(alelb, torch, dev, args)
@@ -986,7 +1061,7 @@ def run_ours(args):
         # the paper's wall condition on the plain lattice, at a Mach number it holds
         precision_low = run_precision(alelb, torch, dev, args, 0.3)
 
-    cpu = cpu1 = None
+    cpu = cpu1 = oracle_cfg = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sweep = I.batched_sweep()
         model, ncpu = cpu_model()
@@ -1001,6 +1076,7 @@ def run_ours(args):
         v1, dt1, used1, _ = cpu_baseline(sweep, args.cpu_steps_1core, 1)
         cpu1 = {"value": v1, "unit": UNIT, "cores": used1, "kind": "oracle", "cpu_model": model,
                 "sample": f"{args.cpu_steps_1core} steps each of the same three cases, one thread ({dt1:.1f} s)"}
+        oracle_cfg = oracle_timing(ncpu or 1)
 
     if rank == 0:
         line = {
@@ -1018,6 +1094,7 @@ def run_ours(args):
             "roofline": roofline,
             "step_roofline": step_rl,
             "batched": {k: v for k, v in bat.items() if k not in ("e2e", "clocks")},
+            "batched_other_seeds": seeds,
             "fp64_plain": None if single is None else dict(single["fp64_plain"], workload=single["workload"]),
             "single_case": None if single is None else dict(single["fp32_dev"], workload=single["workload"],
                                                             e2e=single["e2e"]),
@@ -1032,6 +1109,7 @@ def run_ours(args):
             "e2e": bat["e2e"],
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
+            "oracle_timing": oracle_cfg,
             "clocks": bat["clocks"],
         }
         print(json.dumps(line), flush=True)
