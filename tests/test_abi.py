@@ -65,3 +65,31 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(struct, "size")] == ctypes.sizeof(cls), struct
         for n in names:
             assert got[(struct, n)] == getattr(cls, n).offset, f"{struct}.{n}"
+
+
+def test_empty_and_oversize_inputs_are_refused_on_the_host():
+    """An empty mesh and a batch of 0 or more than 32 cases are refused with
+    ALELB_ERR_ARG before anything reaches a device (no GPU needed)."""
+    import numpy as np
+    L = alelb.load(build.build())
+    d = alelb.MeshDesc()
+    X = np.zeros(2, dtype=np.float64)
+    conn = np.zeros(6, dtype=np.int32)
+    ek = np.zeros(3, dtype=np.uint8)
+    d.n_nodes, d.X, d.n_elems = 0, X.ctypes.data, 0
+    d.conn, d.edge_kind = conn.ctypes.data, ek.ctypes.data
+    for et in (alelb.ELEM_P2TRI, alelb.ELEM_Q2QUAD):
+        d.elem_type = et
+        h = ctypes.c_void_p()
+        assert L.alelb_mesh_create(ctypes.byref(d), ctypes.byref(h)) == -1
+        assert b"empty" in L.alelb_mesh_last_error(h)
+        L.alelb_mesh_destroy(h)
+    d.elem_type = 7
+    h = ctypes.c_void_p()
+    assert L.alelb_mesh_create(ctypes.byref(d), ctypes.byref(h)) == -1
+    L.alelb_mesh_destroy(h)
+    arr = (ctypes.c_void_p * 33)()
+    out = ctypes.c_void_p()
+    assert L.alelb_batch_create(arr, 0, None, ctypes.byref(out)) == -1
+    assert L.alelb_batch_create(arr, 33, None, ctypes.byref(out)) == -1
+    assert not out.value
