@@ -360,7 +360,16 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    per-kernel pick each run 8 steps twice from a saved copy of every case's
    state, the second run timed; the fastest is kept and the state put back
    (the cases advance by the one real step only; a device copy of each
-   case's populations, fields and element cache is held meanwhile).  The step's values do not depend on the
+   case's populations, fields and element cache is held meanwhile).  The
+   case groups are then refined the same way: all cases as one group, or
+   two or four groups of balanced node counts (cases dealt largest
+   first), each with its own stream in graph mode, captured as branches of
+   every chunk's graph and running side by side, so that one group's
+   kernels fill the SMs that another group's leave idle (its propagation,
+   bound by load latency, beside another's collision, bound by memory
+   bandwidth; one kernel's tail beside another's start); free, or with
+   each group's propagation (+ 4096: its first kernel; + 8192: its exact
+   part too) ordered after the previous group's latest one.  The step's values do not depend on the
    shapes, and every phase kernel gives the same values when repeated
    within a step, so tuning changes no result.  choice (may be NULL, else 8
    values out): block size of {k_stream, k_stream_fast, k_stream_slow,
@@ -368,7 +377,10 @@ alelb_status alelb_batch_sync(alelb_batch *b);
    per thread of k_stream_fast + 16 (k_deriv1 staged) + 32 (k_collide
    staged) + 256 (k_stream_fast fused with the moments: the
    moments of the nodes whose populations all settle there are computed
-   in the same launch, and k_moments takes only the others).
+   in the same launch, and k_moments takes only the others) + 512 or 1024
+   (two or four case groups) + 4096 or 8192 (propagations in turn).
+   Groups apply in graph mode; the persistent form and profiled steps run
+   all cases as one.
    Synchronous. */
 alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
 
@@ -391,8 +403,11 @@ alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *cons
    encoding (for example a choice saved from an earlier tuning):
    block sizes 64, 128 or 256; a k_stream_slow grid of 1 .. 64 x the SM
    count; directions per thread 1, 3 or 9, optionally + 256 (fused with
-   the moments; 3 or 9 only); + 16, + 32 (staging).  Every flag needs the FP32 form.  Changes
-   no result; ALELB_ERR_ARG for a value outside these. */
+   the moments; 3 or 9 only); + 16, + 32 (staging), which need the FP32
+   form; + 512 (two case groups) or + 1024 (four; only when every group
+   receives a case), optionally + 4096 or + 8192 (their propagations in
+   turn), in either form.  Changes no result; ALELB_ERR_ARG for a value
+   outside these. */
 alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t choice[8]);
 
 /* How a batch runs its steps.  ALELB_BATCH_GRAPHS (the default): one

@@ -457,6 +457,8 @@ class Batch:
         d["k_deriv1_staged"] = bool(out[7] & 16)
         d["k_collide_staged"] = bool(out[7] & 32)
         d["k_stream_fast_fused_moments"] = bool(out[7] & 256)
+        d["case_groups"] = 2 if out[7] & 512 else 4 if out[7] & 1024 else 1
+        d["groups_pipelined"] = (int(out[7]) >> 12) & 3
         return d
 
     def profile(self, enable=True):

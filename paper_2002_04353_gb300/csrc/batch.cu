@@ -13,6 +13,7 @@
 // chunk's launches are captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <climits>
 #include <cmath>
@@ -36,6 +37,14 @@ constexpr int CHUNK_MAX = 64; // steps per captured graph
 constexpr int N_BS = 3;       // block sizes 64, 128, 256
 // flag of the directions-per-thread choice (FP32 form): kb_fast_fused
 constexpr int FAST_FUSED = 256;
+// flags of the same choice word for the case groups of a graph-mode step:
+// the cases in two or four groups, each group's phase kernels on a stream
+// of its own (captured as branches of the chunk's graph); PIPELINED (x 1
+// or 2) also orders each group's propagation after the previous group's
+// latest one, so that one group's propagation runs beside the other
+// groups' later phases
+constexpr int TWO_GROUPS = 512, FOUR_GROUPS = 1024, PIPELINED = 4096;
+constexpr int GROUPS_MAX = 4;
 
 template <class S, class A> struct CaseDev {
     MeshDev M;
@@ -703,6 +712,22 @@ struct alelb_batch {
     bool stage[KT_N] = {};     // shared-memory staging of the derivative stencils (FP32 form)
     int n_sm = 152;
     std::map<int, cudaGraphExec_t> graphs;
+    // case groups (graph mode): the descriptor array, tile tables and staged
+    // scalars hold the cases in the order ord (positions of b->cs), which
+    // splits into four contiguous runs of balanced node counts; two groups
+    // join runs 0-1 and 2-3; groups = 1 runs all cases as one
+    std::vector<int> ord;
+    int groups = 1;
+    int pipe = 0; // 0: groups run free; 1, 2: alternating propagations (enqueue_groups)
+    struct Run {
+        int c0 = 0, n = 0;       // first descriptor, number of cases
+        int *d_off[N_BS] = {};   // tile tables of the run (device)
+        std::vector<int> h_off[N_BS];
+    };
+    Run run2[2], run4[4];
+    bool has2 = false, has4 = false; // every group of the split holds a case
+    cudaStream_t gstream[GROUPS_MAX] = {}; // [0] unused: group 0 runs on the batch's stream
+    cudaEvent_t gev_fork = nullptr, gev_join[GROUPS_MAX] = {}, gev_fast[GROUPS_MAX] = {};
     // the persistent form (mode ALELB_BATCH_PERSISTENT): threads per block,
     // blocks (all resident), barrier words {count, gen, abort}, wait limit
     int mode = ALELB_BATCH_GRAPHS;
@@ -782,22 +807,62 @@ int step_sequence(const alelb_batch *b, int seq[KT_N])
     return n;
 }
 
-// One phase kernel over all cases with the scalars of chunk step k.
+// The cases one launch covers: all of them, or one group.
+struct Part {
+    cudaStream_t stream;
+    int c0, B;            // first descriptor, number of cases
+    const int *off[N_BS]; // their tile tables (device), per block size
+    int tiles[N_BS];
+    bool pdl;             // programmatic serialization after the stream's previous kernel
+};
+
+Part whole(const alelb_batch *b)
+{
+    Part P{b->stream, 0, b->B, {}, {}, true};
+    for (int q = 0; q < N_BS; ++q) {
+        P.off[q] = b->d_off[q];
+        P.tiles[q] = b->h_off[q][b->B];
+    }
+    return P;
+}
+
+Part group(const alelb_batch *b, int g, bool pdl)
+{
+    const alelb_batch::Run &R = b->groups == 4 ? b->run4[g] : b->run2[g];
+    Part P{g ? b->gstream[g] : b->stream, R.c0, R.n, {}, {}, pdl};
+    for (int q = 0; q < N_BS; ++q) {
+        P.off[q] = R.d_off[q];
+        P.tiles[q] = R.h_off[q][R.n];
+    }
+    return P;
+}
+
+// A phase kernel on a part's stream: with programmatic serialization, or
+// (right after a wait on another stream's event) as a plain launch, whose
+// wait_prior_grid returns at once.
+template <class... KArgs, class... Args>
+void launch_after(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args... args)
+{
+    if (pdl) launch_pdl(kern, grid, block, stream, args...);
+    else kern<<<grid, block, 0, stream>>>(static_cast<KArgs>(args)...);
+}
+
+// One phase kernel over the part's cases with the scalars of chunk step k.
 // bs: threads per block; grid: blocks (k_stream_slow only).
 template <class S, class A>
-void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g, bool stage)
+void launch_phase(alelb_batch *b, const Part &P, int kt, int bs, int grid, int k, int count, int fast_g, bool stage)
 {
-    const auto *cases = reinterpret_cast<const CaseDev<S, A> *>(b->d_cases);
+    const auto *cases = reinterpret_cast<const CaseDev<S, A> *>(b->d_cases) + P.c0;
     const int q = bs_index(bs);
-    const int *off = b->d_off[q];
-    const int tiles = b->h_off[q][b->B];
-    const MapScalars *sc = b->d_sc + (size_t)k * b->B;
-    const MapScalarsF *sf = b->d_sf + (size_t)k * b->B;
-    const int B = b->B;
+    const int *off = P.off[q];
+    const int tiles = P.tiles[q];
+    const MapScalars *sc = b->d_sc + (size_t)k * b->B + P.c0;
+    const MapScalarsF *sf = b->d_sf + (size_t)k * b->B + P.c0;
+    const int B = P.B;
     const bool fast = b->prec == ALELB_PREC_FP32_DEV;
     switch (kt) {
     case KT_STREAM:
-        launch_pdl(kb_stream<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, count);
+        launch_after(P.pdl, kb_stream<S, A>, dim3(tiles), dim3(bs), P.stream, cases, off, B, sc, count);
         break;
     case KT_FAST:
         // fast_g: directions per thread, plus FAST_FUSED for the propagation
@@ -807,52 +872,56 @@ void launch_phase(alelb_batch *b, int kt, int bs, int grid, int k, int count, in
                 const auto *cf = reinterpret_cast<const CaseDev<float, float> *>(cases);
                 const int G = fast_g & 15;
                 if (G == 3 && bs == 64)
-                    launch_pdl(kb_fast_fused<3, 64>, dim3(tiles), dim3(64 * 3), b->stream, cf, off, B, sf);
+                    launch_after(P.pdl, kb_fast_fused<3, 64>, dim3(tiles), dim3(64 * 3), P.stream, cf, off, B, sf);
                 else if (G == 3 && bs == 128)
-                    launch_pdl(kb_fast_fused<3, 128>, dim3(tiles), dim3(128 * 3), b->stream, cf, off, B, sf);
+                    launch_after(P.pdl, kb_fast_fused<3, 128>, dim3(tiles), dim3(128 * 3), P.stream, cf, off, B, sf);
                 else if (G == 3)
-                    launch_pdl(kb_fast_fused<3, 256>, dim3(tiles), dim3(256 * 3), b->stream, cf, off, B, sf);
+                    launch_after(P.pdl, kb_fast_fused<3, 256>, dim3(tiles), dim3(256 * 3), P.stream, cf, off, B, sf);
                 else if (bs == 64)
-                    launch_pdl(kb_fast_fused<9, 64>, dim3(tiles), dim3(64), b->stream, cf, off, B, sf);
+                    launch_after(P.pdl, kb_fast_fused<9, 64>, dim3(tiles), dim3(64), P.stream, cf, off, B, sf);
                 else if (bs == 128)
-                    launch_pdl(kb_fast_fused<9, 128>, dim3(tiles), dim3(128), b->stream, cf, off, B, sf);
+                    launch_after(P.pdl, kb_fast_fused<9, 128>, dim3(tiles), dim3(128), P.stream, cf, off, B, sf);
                 else
-                    launch_pdl(kb_fast_fused<9, 256>, dim3(tiles), dim3(256), b->stream, cf, off, B, sf);
+                    launch_after(P.pdl, kb_fast_fused<9, 256>, dim3(tiles), dim3(256), P.stream, cf, off, B, sf);
             }
         } else if (fast_g == 1)
-            launch_pdl(kb_fast<S, A, 1>, dim3(tiles, NQ), dim3(bs), b->stream, cases, off, B, sf);
+            launch_after(P.pdl, kb_fast<S, A, 1>, dim3(tiles, NQ), dim3(bs), P.stream, cases, off, B, sf);
         else if (fast_g == 3)
-            launch_pdl(kb_fast<S, A, 3>, dim3(tiles, NQ / 3), dim3(bs), b->stream, cases, off, B, sf);
+            launch_after(P.pdl, kb_fast<S, A, 3>, dim3(tiles, NQ / 3), dim3(bs), P.stream, cases, off, B, sf);
         else
-            launch_pdl(kb_fast<S, A, 9>, dim3(tiles, 1), dim3(bs), b->stream, cases, off, B, sf);
+            launch_after(P.pdl, kb_fast<S, A, 9>, dim3(tiles, 1), dim3(bs), P.stream, cases, off, B, sf);
         break;
     case KT_SLOW:
-        launch_pdl(kb_slow<S, A>, dim3(grid), dim3(bs), b->stream, cases, B, sc, sf, count);
+        launch_after(P.pdl, kb_slow<S, A>, dim3(grid), dim3(bs), P.stream, cases, B, sc, sf, count);
         break;
     case KT_MOMENTS:
         if (fast_g & FAST_FUSED) // the pending nodes only, over one wave of blocks
-            launch_pdl(kb_moments_pending<S, A>, dim3(b->n_sm * (2048 / bs)), dim3(bs), b->stream, cases, B);
+            launch_after(P.pdl, kb_moments_pending<S, A>, dim3(b->n_sm * (2048 / bs)), dim3(bs), P.stream, cases, B);
         else
-            launch_pdl(kb_moments<S, A>, dim3(tiles), dim3(bs), b->stream, cases, off, B);
+            launch_after(P.pdl, kb_moments<S, A>, dim3(tiles), dim3(bs), P.stream, cases, off, B);
         break;
     case KT_DERIV1:
         if (fast)
-            launch_pdl(kb_deriv1_staged, dim3(tiles), dim3(bs), b->stream,
+            launch_after(P.pdl, kb_deriv1_staged, dim3(tiles), dim3(bs), P.stream,
                        reinterpret_cast<const CaseDev<float, float> *>(cases), off, B, sf, (int)stage);
-        else launch_pdl(kb_deriv1<S, A, false>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
+        else launch_after(P.pdl, kb_deriv1<S, A, false>, dim3(tiles), dim3(bs), P.stream, cases, off, B, sc, sf);
         break;
     default:
         if (fast)
-            launch_pdl(kb_collide_staged, dim3(tiles), dim3(bs), b->stream,
+            launch_after(P.pdl, kb_collide_staged, dim3(tiles), dim3(bs), P.stream,
                        reinterpret_cast<const CaseDev<float, float> *>(cases), off, B, sf, (int)stage);
-        else launch_pdl(kb_collide<S, A, false>, dim3(tiles), dim3(bs), b->stream, cases, off, B, sc, sf);
+        else launch_after(P.pdl, kb_collide<S, A, false>, dim3(tiles), dim3(bs), P.stream, cases, off, B, sc, sf);
     }
 }
 
+void launch_kernel(alelb_batch *b, const Part &P, int kt, int bs, int grid, int k, int count, int fast_g, bool stage)
+{
+    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, P, kt, bs, grid, k, count, fast_g, stage);
+    else launch_phase<double, double>(b, P, kt, bs, grid, k, count, fast_g, stage);
+}
 void launch_kernel(alelb_batch *b, int kt, int bs, int grid, int k, int count, int fast_g, bool stage)
 {
-    if (b->prec == ALELB_PREC_FP32_DEV) launch_phase<float, float>(b, kt, bs, grid, k, count, fast_g, stage);
-    else launch_phase<double, double>(b, kt, bs, grid, k, count, fast_g, stage);
+    launch_kernel(b, whole(b), kt, bs, grid, k, count, fast_g, stage);
 }
 
 // One cooperative launch of the persistent kernel for chunk steps 0..K-1.
@@ -917,6 +986,35 @@ void enqueue_step(alelb_batch *b, int k)
     }
 }
 
+// Step k of every case group, inside a capture: group g >= 1 on its own
+// stream (forked from the batch's stream at the chunk's start).  With
+// pipe = p > 0 the first p phase kernels of each group's step (the
+// propagation, and with p = 2 its exact part) follow those of the previous
+// group (of the previous step for group 0); a kernel after such a wait, or
+// first on its stream, is launched plainly.
+cudaError_t enqueue_groups(alelb_batch *b, int k)
+{
+    int seq[KT_N];
+    const int ns = step_sequence(b, seq);
+    const int lead = std::min(b->pipe ? (b->pipe == 2 ? 2 : 1) : 0, ns);
+    cudaError_t st = cudaSuccess;
+    for (int g = 0; g < b->groups && st == cudaSuccess; ++g) {
+        cudaStream_t sg = g ? b->gstream[g] : b->stream;
+        bool pdl = !(k == 0 && g > 0);
+        if (lead && (k > 0 || g > 0)) {
+            st = cudaStreamWaitEvent(sg, b->gev_fast[g > 0 ? g - 1 : b->groups - 1], 0);
+            pdl = false;
+        }
+        for (int q = 0; q < ns && st == cudaSuccess; ++q) {
+            const int kt = seq[q];
+            launch_kernel(b, group(b, g, pdl), kt, b->bs[kt], b->slow_grid, k, 1, b->fast_g, b->stage[kt]);
+            pdl = true;
+            if (q + 1 == lead) st = cudaEventRecord(b->gev_fast[g], sg);
+        }
+    }
+    return st;
+}
+
 cudaError_t get_graph(alelb_batch *b, int K, cudaGraphExec_t &exec)
 {
     auto it = b->graphs.find(K);
@@ -927,8 +1025,23 @@ cudaError_t get_graph(alelb_batch *b, int K, cudaGraphExec_t &exec)
     cudaGraph_t g = nullptr;
     cudaError_t st = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (st != cudaSuccess) return st;
-    for (int k = 0; k < K; ++k) enqueue_step(b, k);
+    cudaError_t st_q = cudaSuccess;
+    if (b->groups > 1) {
+        st_q = cudaEventRecord(b->gev_fork, b->stream);
+        for (int h = 1; h < b->groups && st_q == cudaSuccess; ++h) st_q = cudaStreamWaitEvent(b->gstream[h], b->gev_fork, 0);
+        for (int k = 0; k < K && st_q == cudaSuccess; ++k) st_q = enqueue_groups(b, k);
+        // every branch joins the batch's stream (also after a failure, so
+        // that the capture can end)
+        for (int h = 1; h < b->groups; ++h) {
+            cudaError_t sj = cudaEventRecord(b->gev_join[h], b->gstream[h]);
+            if (sj == cudaSuccess) sj = cudaStreamWaitEvent(b->stream, b->gev_join[h], 0);
+            if (st_q == cudaSuccess) st_q = sj;
+        }
+    } else {
+        for (int k = 0; k < K; ++k) enqueue_step(b, k);
+    }
     cudaError_t st_launch = cudaGetLastError();
+    if (st_launch == cudaSuccess) st_launch = st_q;
     st = cudaStreamEndCapture(b->stream, &g);
     if (st == cudaSuccess) st = st_launch;
     if (st == cudaSuccess) st = cudaGraphInstantiate(&exec, g, 0);
@@ -946,7 +1059,7 @@ cudaError_t stage_scalars(alelb_batch *b, int done, int K)
     if (st != cudaSuccess) return st;
     for (int k = 0; k < K; ++k)
         for (int c = 0; c < b->B; ++c) {
-            const alelb_solver *s = b->cs[c];
+            const alelb_solver *s = b->cs[b->ord[c]];
             const HostTables &T = s->mesh->T;
             const MapScalars sc = solver_map(s, map_scalars(T.mkind, T.mp, s->t + (double)(done + k + 1)));
             b->h_sc[sl][(size_t)k * b->B + c] = sc;
@@ -998,7 +1111,7 @@ template <> CaseDev<double, double> case_desc<double, double>(alelb_solver *s)
 template <class S, class A> cudaError_t upload_cases(alelb_batch *b)
 {
     std::vector<CaseDev<S, A>> h(b->B);
-    for (int c = 0; c < b->B; ++c) h[c] = case_desc<S, A>(b->cs[c]);
+    for (int c = 0; c < b->B; ++c) h[c] = case_desc<S, A>(b->cs[b->ord[c]]);
     cudaError_t st = cudaSuccess;
     auto *d = b->buf.alloc<CaseDev<S, A>>(b->B, st);
     b->d_cases = d;
@@ -1041,16 +1154,59 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         b->own_stream = st == cudaSuccess;
     }
     if (st != cudaSuccess) return bfail(b, st, "stream");
-    // tile offsets per block size
+    // descriptor order: the cases dealt, largest first, to the half (runs
+    // 0-1 or 2-3) with fewer nodes so far, within it to the run with fewer
+    // nodes, each run's cases then in the callers' order
+    int first4[5] = {};
+    {
+        std::vector<int> idx(B);
+        for (int c = 0; c < B; ++c) idx[c] = c;
+        std::stable_sort(idx.begin(), idx.end(),
+                         [b](int x, int y) { return b->cs[x]->mesh->T.N > b->cs[y]->mesh->T.N; });
+        std::vector<int> rof(B, 0);
+        long long load[4] = {};
+        for (int c : idx) {
+            const int h = load[2] + load[3] < load[0] + load[1] ? 2 : 0;
+            const int r = load[h + 1] < load[h] ? h + 1 : h;
+            rof[c] = r;
+            load[r] += b->cs[c]->mesh->T.N;
+        }
+        for (int r = 0; r < 4; ++r) {
+            for (int c = 0; c < B; ++c)
+                if (rof[c] == r) b->ord.push_back(c);
+            first4[r + 1] = (int)b->ord.size();
+        }
+    }
+    // tile offsets per block size, of all cases and of each run
+    const auto tiles_of = [b](int j, int bs) { return (b->cs[b->ord[j]]->mesh->T.N + bs - 1) / bs; };
+    const auto set_run = [&](alelb_batch::Run &R, int c0, int c1) {
+        R.c0 = c0;
+        R.n = c1 - c0;
+        for (int q = 0; q < N_BS; ++q) {
+            auto &o = R.h_off[q];
+            o.assign(R.n + 1, 0);
+            for (int c = 0; c < R.n; ++c) o[c + 1] = o[c] + tiles_of(c0 + c, 64 << q);
+            R.d_off[q] = b->buf.put(o, st);
+        }
+    };
     for (int q = 0; q < N_BS; ++q) {
         const int bs = 64 << q;
         auto &o = b->h_off[q];
         o.assign(B + 1, 0);
-        for (int c = 0; c < B; ++c) {
-            const int N = b->cs[c]->mesh->T.N;
-            o[c + 1] = o[c] + (N + bs - 1) / bs;
-        }
+        for (int c = 0; c < B; ++c) o[c + 1] = o[c] + tiles_of(c, bs);
         b->d_off[q] = b->buf.put(o, st);
+    }
+    for (int r = 0; r < 4; ++r) set_run(b->run4[r], first4[r], first4[r + 1]);
+    set_run(b->run2[0], first4[0], first4[2]);
+    set_run(b->run2[1], first4[2], first4[4]);
+    b->has2 = b->run2[0].n > 0 && b->run2[1].n > 0;
+    b->has4 = b->run4[0].n > 0 && b->run4[1].n > 0 && b->run4[2].n > 0 && b->run4[3].n > 0;
+    for (int g = 1; g < GROUPS_MAX && st == cudaSuccess; ++g)
+        st = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking);
+    if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->gev_fork, cudaEventDisableTiming);
+    for (int g = 0; g < GROUPS_MAX && st == cudaSuccess; ++g) {
+        st = cudaEventCreateWithFlags(&b->gev_join[g], cudaEventDisableTiming);
+        if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->gev_fast[g], cudaEventDisableTiming);
     }
     if (st == cudaSuccess)
         st = b->prec == ALELB_PREC_FP32_DEV ? upload_cases<float, float>(b) : upload_cases<double, double>(b);
@@ -1087,6 +1243,12 @@ extern "C" void alelb_batch_destroy(alelb_batch *b)
     for (cudaEvent_t e : b->ev_in)
         if (e) cudaEventDestroy(e);
     if (b->ev_done) cudaEventDestroy(b->ev_done);
+    if (b->gev_fork) cudaEventDestroy(b->gev_fork);
+    for (int g = 0; g < GROUPS_MAX; ++g) {
+        if (b->gev_join[g]) cudaEventDestroy(b->gev_join[g]);
+        if (b->gev_fast[g]) cudaEventDestroy(b->gev_fast[g]);
+        if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
+    }
     if (b->h_err) cudaFreeHost(b->h_err);
     for (int sl = 0; sl < 2; ++sl) {
         if (b->h_ev[sl]) cudaEventDestroy(b->h_ev[sl]);
@@ -1168,15 +1330,16 @@ struct Snapshot {
     }
 };
 
-// Whole-step refinement of the propagation's form (FP32, graph mode): the
-// per-kernel timing of alelb_batch_tune does not see how a form fares
-// inside a replayed step (its moments pass, its overlap with its
-// neighbours), so the forms G = 3 and 9, plain and fused with the moments,
-// at 128 and 256 threads, and the per-kernel pick each run REFINE_STEPS
-// steps twice from the same saved state (the second run timed); the
-// fastest is kept and the state put back, so no case advances.
+// Whole-step refinement (FP32, graph mode): the per-kernel timing of
+// alelb_batch_tune does not see how a launch form fares inside a replayed
+// step (its moments pass, its overlap with its neighbours, the other case
+// group's kernels beside it), so each candidate (apply(j), j = 0 .. n - 1,
+// candidate 0 the current form) runs REFINE_STEPS steps twice from the
+// same saved state, the second run timed; the fastest is applied and the
+// state put back, so no case advances.  A batch in which a case has
+// already failed keeps its form.
 constexpr int REFINE_STEPS = 8;
-cudaError_t refine_fast_form(alelb_batch *b)
+template <class Apply> cudaError_t refine_whole_steps(alelb_batch *b, int n, Apply apply)
 {
     int err0 = 0;
     for (alelb_solver *s : b->cs) {
@@ -1185,23 +1348,16 @@ cudaError_t refine_fast_form(alelb_batch *b)
         if (st != cudaSuccess) return st;
         err0 |= e;
     }
-    if (err0) return cudaSuccess; // a case already failed: keep the per-kernel pick
+    if (err0) return cudaSuccess;
     Snapshot snap;
     cudaError_t st = snap.take(b);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == cudaSuccess) st = cudaEventCreate(&e0);
     if (st == cudaSuccess) st = cudaEventCreate(&e1);
-    struct Form { int g, bs; };
-    std::vector<Form> forms = {{b->fast_g, b->bs[KT_FAST]}};
-    for (int g : {3, 9, 3 | FAST_FUSED, 9 | FAST_FUSED})
-        for (int bs : {128, 256})
-            if (!(g == b->fast_g && bs == b->bs[KT_FAST])) forms.push_back({g, bs});
     float best = 1e30f;
-    Form pick = forms[0];
-    for (const Form &f : forms) {
-        if (st != cudaSuccess) break;
-        b->fast_g = f.g;
-        b->bs[KT_FAST] = f.bs;
+    int pick = 0;
+    for (int j = 0; j < n && st == cudaSuccess; ++j) {
+        apply(j);
         drop_graphs(b);
         float ms = 0.f;
         for (int r = 0; r < 2 && st == cudaSuccess; ++r) {
@@ -1214,17 +1370,43 @@ cudaError_t refine_fast_form(alelb_batch *b)
         }
         if (st == cudaSuccess && ms < best) {
             best = ms;
-            pick = f;
+            pick = j;
         }
     }
-    b->fast_g = pick.g;
-    b->bs[KT_FAST] = pick.bs;
+    apply(pick);
     drop_graphs(b);
     if (st == cudaSuccess) st = cudaStreamSynchronize(b->stream);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     snap.buf.release();
     return st;
+}
+
+// The propagation's form: G = 3 and 9, plain and fused with the moments,
+// at 128 and 256 threads, and the per-kernel pick.
+cudaError_t refine_fast_form(alelb_batch *b)
+{
+    struct Form { int g, bs; };
+    std::vector<Form> forms = {{b->fast_g, b->bs[KT_FAST]}};
+    for (int g : {3, 9, 3 | FAST_FUSED, 9 | FAST_FUSED})
+        for (int bs : {128, 256})
+            if (!(g == b->fast_g && bs == b->bs[KT_FAST])) forms.push_back({g, bs});
+    return refine_whole_steps(b, (int)forms.size(), [&](int j) {
+        b->fast_g = forms[j].g;
+        b->bs[KT_FAST] = forms[j].bs;
+    });
+}
+
+// The case groups: all cases as one, two or four groups running free, or
+// with their propagations in turn (pipe 1 and 2).
+cudaError_t refine_groups(alelb_batch *b)
+{
+    if (!b->has2) return cudaSuccess;
+    const int cand[7][2] = {{1, 0}, {2, 0}, {2, 1}, {2, 2}, {4, 0}, {4, 1}, {4, 2}};
+    return refine_whole_steps(b, b->has4 ? 7 : 4, [&](int j) {
+        b->groups = cand[j][0];
+        b->pipe = cand[j][1];
+    });
 }
 } // namespace
 
@@ -1351,6 +1533,7 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     drop_graphs(b);
     if (b->prec == ALELB_PREC_FP32_DEV && b->mode == ALELB_BATCH_GRAPHS && !b->prof) {
         st = refine_fast_form(b);
+        if (st == cudaSuccess) st = refine_groups(b);
         if (st != cudaSuccess) return bfail(b, st, "batch_tune: refinement");
     }
     st = release_cases(b);
@@ -1358,7 +1541,9 @@ extern "C" alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t c
     if (choice) {
         for (int k = 0; k < 6; ++k) choice[k] = b->bs[k];
         choice[6] = b->slow_grid;
-        choice[7] = b->fast_g | (b->stage[KT_DERIV1] ? 16 : 0) | (b->stage[KT_COLLIDE] ? 32 : 0); // FAST_FUSED = 256
+        choice[7] = b->fast_g | (b->stage[KT_DERIV1] ? 16 : 0) | (b->stage[KT_COLLIDE] ? 32 : 0) |
+                    (b->groups == 2 ? TWO_GROUPS : b->groups == 4 ? FOUR_GROUPS : 0) |
+                    b->pipe * PIPELINED; // FAST_FUSED = 256
     }
     return ALELB_OK;
 }
@@ -1455,13 +1640,17 @@ extern "C" alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t cho
     for (int k = 0; k < 6; ++k)
         if (choice[k] != 64 && choice[k] != 128 && choice[k] != 256) return ALELB_ERR_ARG;
     if (choice[6] < 1 || choice[6] > 64 * b->n_sm) return ALELB_ERR_ARG;
-    const int c7 = choice[7], G = c7 & 15, fl = c7 & ~15;
+    const int c7 = choice[7], G = c7 & 15, fl = c7 & ~15 & ~(TWO_GROUPS | FOUR_GROUPS | 3 * PIPELINED);
     const bool fp32 = b->prec == ALELB_PREC_FP32_DEV;
     if (G != 1 && G != 3 && G != 9) return ALELB_ERR_ARG;
     if (fl & ~(16 | 32 | FAST_FUSED)) return ALELB_ERR_ARG;
     if (!fp32 && fl) return ALELB_ERR_ARG;
     const int form = fl & FAST_FUSED;
     if (form && G == 1) return ALELB_ERR_ARG;
+    if ((c7 & TWO_GROUPS) && (c7 & FOUR_GROUPS)) return ALELB_ERR_ARG;
+    const int groups = c7 & TWO_GROUPS ? 2 : c7 & FOUR_GROUPS ? 4 : 1, pipe = (c7 / PIPELINED) & 3;
+    if ((groups == 2 && !b->has2) || (groups == 4 && !b->has4) || pipe == 3 || (pipe && groups == 1))
+        return ALELB_ERR_ARG;
     cudaError_t st = cudaStreamSynchronize(b->stream);
     if (st != cudaSuccess) return bfail(b, st, "batch_set_choice");
     for (int k = 0; k < 6; ++k) b->bs[k] = choice[k];
@@ -1469,6 +1658,8 @@ extern "C" alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t cho
     b->fast_g = G | form;
     b->stage[KT_DERIV1] = (c7 & 16) != 0;
     b->stage[KT_COLLIDE] = (c7 & 32) != 0;
+    b->groups = groups;
+    b->pipe = pipe;
     drop_graphs(b);
     return ALELB_OK;
 }

@@ -131,7 +131,8 @@ def test_tuning_changes_no_value():
 
 # every launch form of the FP32 batch (alelb_batch_tune's encoding): block
 # sizes, directions per thread, the propagation fused with the moments
-# (+256), staged derivative stencils (+16, +32)
+# (+256), staged derivative stencils (+16, +32), two or four case groups
+# (+512, +1024), their propagations in turn (+4096, +8192)
 FORMS = [[128, 128, 128, 256, 256, 128, 64, 9],
          [128, 64, 128, 256, 256, 128, 64, 1],
          [128, 256, 64, 128, 64, 256, 300, 3 | 16 | 32],
@@ -140,7 +141,13 @@ FORMS = [[128, 128, 128, 256, 256, 128, 64, 9],
          [128, 256, 128, 256, 128, 128, 64, 3 | 256 | 16],
          [128, 64, 128, 256, 256, 128, 64, 9 | 256],
          [128, 128, 128, 256, 256, 128, 64, 9 | 256 | 32],
-         [128, 256, 128, 256, 256, 128, 64, 9 | 256]]
+         [128, 256, 128, 256, 256, 128, 64, 9 | 256],
+         [128, 256, 128, 256, 256, 128, 64, 9 | 256 | 512],
+         [128, 256, 128, 256, 256, 128, 64, 9 | 256 | 512 | 4096],
+         [128, 64, 128, 256, 256, 128, 64, 3 | 512 | 8192 | 32],
+         [128, 64, 128, 256, 256, 128, 64, 1 | 512 | 4096],
+         [128, 256, 128, 256, 256, 128, 64, 9 | 256 | 1024],
+         [128, 128, 128, 256, 256, 128, 300, 3 | 256 | 1024 | 8192 | 16]]
 
 
 def test_every_launch_form_gives_the_same_bits():
@@ -211,6 +218,45 @@ def test_set_choice_refuses_unknown_forms():
     with pytest.raises(alelb.AlelbError):
         b64.set_choice([128, 128, 128, 256, 256, 128, 64, 3 | 256])
     b64.set_choice([128, 128, 128, 256, 256, 128, 64, 9])
+    # case groups: the alternation needs two groups, and 3 x 4096 is no form
+    s2 = _solvers(_cases()[:2], alelb.PREC_FP32_DEV)
+    b2 = alelb.Batch(s2)
+    for v in (3 | 4096, 3 | 8192, 3 | 512 | 3 * 4096, 3 | 512 | 16384, 3 | 512 | 1024, 3 | 1024):
+        with pytest.raises(alelb.AlelbError):
+            b2.set_choice(good[:7] + [v])
+    b2.set_choice(good[:7] + [3 | 512 | 8192])
+
+
+@pytest.mark.parametrize("prec", [alelb.PREC_FP64, alelb.PREC_FP32_DEV])
+def test_case_groups_give_the_same_bits(prec):
+    """Two and four case groups on their own streams, free and with their
+    propagations in turn, over 40 + 30 steps (across the 64-step graph
+    chunk): the same populations, fields and walk counts as one group, bit
+    for bit."""
+    base = [128, 128, 128, 256, 256, 128, 64, 9]
+    cases = _cases()
+    ref = _solvers(cases, prec)
+    br = alelb.Batch(ref)
+    br.set_choice(base)
+    br.step(40)
+    br.step(30)
+    br.sync()
+    want = [(s.get_pops(), s.moments(), s.info()["walks"]) for s in ref]
+    for extra in (512, 512 | 4096, 512 | 8192, 1024, 1024 | 4096):
+        ss = _solvers(cases, prec)
+        b = alelb.Batch(ss)
+        b.set_choice(base[:7] + [base[7] | extra])
+        b.step(40)
+        b.step(30)
+        b.sync()
+        for c, s in enumerate(ss):
+            (fr, gr), mr, wr = want[c]
+            f, g = s.get_pops()
+            assert np.array_equal(f, fr) and np.array_equal(g, gr), f"{extra} case {c}"
+            mo = s.moments()
+            assert all(np.array_equal(mo[k], mr[k]) for k in mr), f"{extra} case {c}"
+            assert s.info()["walks"] == wr
+            assert s.time() == (70.0, 70)
 
 
 def test_batched_host_exchange_matches_the_per_case_calls():
