@@ -133,12 +133,13 @@ NCU_TRAFFIC_150K = {"k_stream_fast": 23.93e6, "k_stream_slow": 1.48e6, "k_moment
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # of 20 steady-state launches) of the batched phase kernels on the 32-case
-# sweep, from one ncu capture of the current kernels in the launch form
+# sweep, each launch over all cases as in the per-kernel pass that times
+# them, from one ncu capture of the current kernels in the launch form
 # named here (profiles/launch_list_sweep32.md); a run whose tuner picks
 # another form reports no traffic.
 NCU_TRAFFIC_SWEEP_FORM = {"k_stream_fast_directions_per_thread": 9, "k_stream_fast_fused_moments": True}
-NCU_TRAFFIC_SWEEP = {"k_stream_fast": 962.82e6, "k_stream_slow": 42.88e6, "k_moments": 14.29e6,
-                     "k_deriv1": 264.48e6, "k_collide": 836.54e6}
+NCU_TRAFFIC_SWEEP = {"k_stream_fast": 962.6e6, "k_stream_slow": 42.9e6, "k_moments": 14.3e6,
+                     "k_deriv1": 265.3e6, "k_collide": 838.0e6}
 
 
 def measured_peaks():
