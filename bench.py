@@ -466,37 +466,52 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     for s in solvers:
         s.close()
     # end to end with host buffers: every step uploads every case's
-    # populations from pinned host memory (alelb_set_pops), advances the
-    # batch one step and reads every case's populations back
-    # (alelb_get_pops); a fresh batch from the free-stream start
-    e2e = None
+    # populations from pinned host memory, advances the batch one step and
+    # reads every case's populations back; a fresh batch from the
+    # free-stream start.  The headline figure exchanges the FP32-deviation
+    # form's stored deviations (alelb_batch_set_pops_dev32 / _get_pops_dev32:
+    # exact, 72 B per node each way); the FP64 exchange (alelb_batch_set_pops
+    # / _get_pops: full FP64 values, 144 B) is timed beside it.
+    e2e = e2e_fp64 = None
     if not args.no_e2e:
-        solvers = [alelb.Solver(m, fl, alelb.PREC_FP32_DEV) for m, fl in zip(meshes, flows)]
-        b = alelb.Batch(solvers, stream=stream.cuda_stream)
-        b.tune(reps=1)
-        host = []
-        for s, c in zip(solvers, cases):
-            f = torch.empty((9, c.mesh.n_nodes), dtype=torch.float64).pin_memory().numpy()
-            g = torch.empty((9, c.mesh.n_nodes), dtype=torch.float64).pin_memory().numpy()
-            s.get_pops(f, g)
-            host.append((f, g))
         Ke = args.e2e_steps
-        t_now = np.array([s.time()[0] for s in solvers])
-        hf, hg = [f for f, _ in host], [g for _, g in host]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(Ke):
-            b.set_pops(hf, hg, t=t_now + k)
-            b.step(1)
-            b.get_pops(hf, hg)
-        dt = time.perf_counter() - t0
-        bytes_step = 18 * 8 * n_nodes
+
+        def exchange_loop(dtype, stored):
+            # a fresh batch per form, so that both run within the first steps
+            # from the impulsive start, where every case stays finite
+            solvers = [alelb.Solver(m, fl, alelb.PREC_FP32_DEV) for m, fl in zip(meshes, flows)]
+            b = alelb.Batch(solvers, stream=stream.cuda_stream)
+            b.tune(reps=1)
+            get, put = (b.get_pops_dev32, b.set_pops_dev32) if stored else (b.get_pops, b.set_pops)
+            hf = [torch.empty((9, c.mesh.n_nodes), dtype=dtype).pin_memory().numpy() for c in cases]
+            hg = [torch.empty((9, c.mesh.n_nodes), dtype=dtype).pin_memory().numpy() for c in cases]
+            get(hf, hg)
+            t_now = np.array([s.time()[0] for s in solvers])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(Ke):
+                put(hf, hg, t=t_now + k)
+                b.step(1)
+                get(hf, hg)
+            dt = time.perf_counter() - t0
+            b.close()
+            for s in solvers:
+                s.close()
+            return dt
+
+        dt = exchange_loop(torch.float32, True)
+        bytes_step = 18 * 4 * n_nodes
         e2e = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                "d2h_bytes_per_step": bytes_step, "steps": Ke,
-               "note": "host-resident state: per step alelb_batch_set_pops (every case's populations from "
-                       "pinned FP64 host arrays), alelb_batch_step(1), alelb_batch_get_pops (fresh batch, "
-                       "free-stream start)"}
-        b.close()
+               "note": "host-resident state: per step alelb_batch_set_pops_dev32 (every case's stored FP32 "
+                       "deviations from pinned host arrays), alelb_batch_step(1), alelb_batch_get_pops_dev32 "
+                       "(fresh batch, free-stream start)"}
+        dt = exchange_loop(torch.float64, False)
+        bytes_step = 18 * 8 * n_nodes
+        e2e_fp64 = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
+                    "d2h_bytes_per_step": bytes_step, "steps": Ke,
+                    "note": "the same with the FP64 exchange: alelb_batch_set_pops / alelb_batch_get_pops "
+                            "(full FP64 populations)"}
     return {"value": n_total * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "steps": K,
             "cases": len(sweep) if world == 1 else f"{len(cases)} of {len(sweep)} on rank {rank}",
             "nodes": n_total, "elements": n_elems, "cases_finite_after_timing": finite,
@@ -504,7 +519,7 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
             "exact_path_per_step": n_exact,
             "cases_on_shifted_lattice": sum(1 for fl in flows if any(fl.shift)), "tuned_launch_shapes": choice,
             "kernels": kernels, "kernel_rooflines": rl, "method_bytes_per_step": method_bytes(n_nodes, n_elems),
-            "persistent_form": persistent, "e2e": e2e, "clocks": clocks,
+            "persistent_form": persistent, "e2e": e2e, "e2e_fp64_exchange": e2e_fp64, "clocks": clocks,
             # five phase kernels per step (propagation, exact path, moments, first derivative pass,
             # collision) in every case group
             "gpu_launches": 5 * K * groups}
@@ -944,20 +959,27 @@ def run_single(alelb, torch, dev, world, args):
                   for k, v in kt32.items() if v[1]}
     e2e = None
     if not args.no_e2e:
+        # the stored FP32 deviations (exact, 72 B per node each way), then the
+        # FP64 exchange (144 B) from the same solver
         s = alelb.Solver(mesh, case.flow, alelb.PREC_FP32_DEV, stream=stream.cuda_stream)
-        f = torch.empty((9, N), dtype=torch.float64).pin_memory().numpy()
-        g = torch.empty((9, N), dtype=torch.float64).pin_memory().numpy()
-        s.get_pops(f, g)
         Ke = max(3, K // 4)
-        t0 = time.perf_counter()
-        for k in range(Ke):
-            s.set_pops(f, g, t=float(k))
-            s.lb_step(1)
-            s.get_pops(f, g)
-        dt = time.perf_counter() - t0
+        e2e = {}
+        for name, dtype, get, put in (("stored", torch.float32, s.get_pops_dev32, s.set_pops_dev32),
+                                      ("fp64", torch.float64, s.get_pops, s.set_pops)):
+            f = torch.empty((9, N), dtype=dtype).pin_memory().numpy()
+            g = torch.empty((9, N), dtype=dtype).pin_memory().numpy()
+            get(f, g)
+            t0 = time.perf_counter()
+            for k in range(Ke):
+                put(f, g, t=float(k))
+                s.lb_step(1)
+                get(f, g)
+            dt = time.perf_counter() - t0
+            nb = 18 * N * f.itemsize
+            e2e[name] = {"value": world * N * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": nb,
+                         "d2h_bytes_per_step": nb}
         s.close()
-        e2e = {"value": world * N * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 18 * N * 8,
-               "d2h_bytes_per_step": 18 * N * 8}
+        e2e = dict(e2e["stored"], fp64_exchange=e2e["fp64"])
     return {
         "workload": case.name, "nodes": N, "elements": E,
         "fp32_dev": {"value": world * N * K / (ms32 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms32 / K,
@@ -1138,7 +1160,7 @@ def main():
     ap.add_argument("--single-steps", type=int, default=40)
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=10)

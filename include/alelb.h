@@ -224,6 +224,21 @@ alelb_status alelb_set_pops(alelb_solver *s, const double *f, const double *g,
                             const double *rho, const double *ux, const double *uy,
                             const double *T, double t);
 
+/* The same exchange in the stored form of ALELB_PREC_FP32_DEV (the paper
+   has no counterpart): f, g are host arrays of [9][n_nodes] FP32 in the
+   caller's node order, holding the deviations f_i - f_i^eq(rho_inf, 0,
+   T_inf) and g_i - g_i^eq(rho_inf, 0, T_inf) (the equilibria at the free
+   stream's density and temperature at rest, on the solver's lattice
+   c_i + U) exactly as the solver stores them: half the bytes of the FP64
+   exchange, and no rounding either way (a get, then a set, restores the
+   state bit for bit).  set: the deviations become the post-collision
+   state and the time becomes t; the fields are computed from the full
+   populations d + f^eq in FP64, as alelb_set_pops without fields computes
+   them.  Both synchronous (set returns once the arrays may be reused);
+   ALELB_ERR_ARG for a NULL array or a solver of another precision. */
+alelb_status alelb_get_pops_dev32(alelb_solver *s, float *f, float *g);
+alelb_status alelb_set_pops_dev32(alelb_solver *s, const float *f, const float *g, double t);
+
 /* Wall forces at the current time: {Fx_p, Fy_p, Fx_v, Fy_v, c_D, c_L} with
    p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule per straight
    wall edge of the mapped geometry, c = F / (rho_inf |u_inf|^2 chord / 2)
@@ -398,6 +413,12 @@ alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
 alelb_status alelb_batch_set_pops(alelb_batch *b, const double *const *f, const double *const *g,
                                   const double *t);
 alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *const *g);
+/* The batched forms of alelb_get_pops_dev32 / alelb_set_pops_dev32 (FP32
+   planes of each case's stored deviations; ALELB_ERR_ARG also for a batch
+   of another precision). */
+alelb_status alelb_batch_set_pops_dev32(alelb_batch *b, const float *const *f, const float *const *g,
+                                        const double *t);
+alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const *f, float *const *g);
 
 /* Sets the launch shapes that alelb_batch_tune would choose, in its
    encoding (for example a choice saved from an earlier tuning):

@@ -49,7 +49,8 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
            "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
            "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait", "alelb_batch_set_choice",
-           "alelb_batch_set_pops", "alelb_batch_get_pops"]
+           "alelb_batch_set_pops", "alelb_batch_get_pops", "alelb_get_pops_dev32", "alelb_set_pops_dev32",
+           "alelb_batch_set_pops_dev32", "alelb_batch_get_pops_dev32"]
 
 
 class AlelbError(RuntimeError):
@@ -138,6 +139,10 @@ def load(path: str = LIB_PATH):
     L.alelb_batch_set_choice.argtypes = [p, p]
     L.alelb_batch_set_pops.argtypes = [p, p, p, p]
     L.alelb_batch_get_pops.argtypes = [p, p, p]
+    L.alelb_get_pops_dev32.argtypes = [p, p, p]
+    L.alelb_set_pops_dev32.argtypes = [p, p, p, d]
+    L.alelb_batch_set_pops_dev32.argtypes = [p, p, p, p]
+    L.alelb_batch_get_pops_dev32.argtypes = [p, p, p]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -157,6 +162,14 @@ def _dptr(t):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32_out(a, n):
+    """A caller's output array: C-contiguous, writable float32 of 9 x n values."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous
+            and a.flags.writeable and a.size == NQ * n):
+        raise ValueError(f"a C-contiguous writable float32 array of 9 x {n} values")
+    return a
 
 
 class Mesh:
@@ -304,6 +317,20 @@ class Solver:
         self._check(load().alelb_set_pops(self.h, _ptr(f), _ptr(g), *[_ptr(a) for a in fl], float(t)),
                     "set_pops")
 
+    def get_pops_dev32(self, f=None, g=None):
+        """The FP32-deviation form's stored deviations, [9, n] float32 each."""
+        f = np.empty((NQ, self.nn), dtype=np.float32) if f is None else _f32_out(f, self.nn)
+        g = np.empty((NQ, self.nn), dtype=np.float32) if g is None else _f32_out(g, self.nn)
+        self._check(load().alelb_get_pops_dev32(self.h, _ptr(f), _ptr(g)), "get_pops_dev32")
+        return f, g
+
+    def set_pops_dev32(self, f, g, t=0.0):
+        f = np.ascontiguousarray(f, dtype=np.float32)
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        if f.size != NQ * self.nn or g.size != NQ * self.nn:
+            raise ValueError(f"9 x {self.nn} values per array")
+        self._check(load().alelb_set_pops_dev32(self.h, _ptr(f), _ptr(g), float(t)), "set_pops_dev32")
+
     def save(self, path):
         self._check(load().alelb_save(self.h, os.fsencode(path)), "save")
 
@@ -410,13 +437,15 @@ class Batch:
         self._check(load().alelb_batch_set_wait(self.h, float(limit_seconds), int(missing_arrivals)),
                     "batch_set_wait")
 
-    def _planes(self, arrs, writable):
+    def _planes(self, arrs, writable, dtype=np.float64):
+        if len(arrs) != len(self.solvers):
+            raise ValueError("one f and one g array per case")
         ptrs = (C.c_void_p * len(arrs))()
         for c, (a, s) in enumerate(zip(arrs, self.solvers)):
             a = np.asarray(a)
-            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != 9 * s.nn or \
+            if a.dtype != dtype or not a.flags.c_contiguous or a.size != 9 * s.nn or \
                     (writable and not a.flags.writeable):
-                raise ValueError(f"case {c}: a C-contiguous float64 array of 9 x {s.nn} values")
+                raise ValueError(f"case {c}: a C-contiguous {np.dtype(dtype).name} array of 9 x {s.nn} values")
             ptrs[c] = a.ctypes.data
         return ptrs
 
@@ -435,6 +464,18 @@ class Batch:
             raise ValueError("one f and one g array per case")
         self._check(load().alelb_batch_get_pops(self.h, self._planes(f, True), self._planes(g, True)),
                     "batch_get_pops")
+
+    def set_pops_dev32(self, f, g, t=None):
+        """Every case's stored FP32 deviations from host arrays, one call."""
+        tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
+        self._check(load().alelb_batch_set_pops_dev32(self.h, self._planes(f, False, np.float32),
+                                                      self._planes(g, False, np.float32),
+                                                      None if tt is None else _ptr(tt)), "batch_set_pops_dev32")
+
+    def get_pops_dev32(self, f, g):
+        """Every case's stored FP32 deviations into host arrays."""
+        self._check(load().alelb_batch_get_pops_dev32(self.h, self._planes(f, True, np.float32),
+                                                      self._planes(g, True, np.float32)), "batch_get_pops_dev32")
 
     def set_choice(self, choice):
         """Launch shapes in alelb_batch_tune's encoding (8 int32 values)."""

@@ -1578,40 +1578,34 @@ extern "C" alelb_status alelb_batch_kernel_times(alelb_batch *b, const char **na
     return ALELB_OK;
 }
 
-extern "C" alelb_status alelb_batch_set_pops(alelb_batch *b, const double *const *f, const double *const *g,
-                                             const double *t)
+namespace {
+// The batched host exchange: every case's copies and kernels are queued
+// first (on its own streams, so that the copies of different cases
+// overlap), then the batch's stream joins all of them and one wait covers
+// the lot.  enqueue(c) queues case c's part.
+template <class Enqueue> alelb_status batch_set(alelb_batch *b, Enqueue enqueue, const double *t, const char *what)
 {
-    if (!b || !f || !g) return ALELB_ERR_ARG;
-    for (int c = 0; c < b->B; ++c)
-        if (!f[c] || !g[c]) return ALELB_ERR_ARG;
-    // every case's copies and kernels are queued first (on its own streams,
-    // so that the copies of different cases overlap), then the batch's
-    // stream joins all of them and one wait covers the lot
     cudaError_t st = cudaSuccess;
-    for (int c = 0; c < b->B && st == cudaSuccess; ++c)
-        st = import_enqueue(b->cs[c], f[c], g[c], nullptr, nullptr, nullptr, nullptr);
+    for (int c = 0; c < b->B && st == cudaSuccess; ++c) st = enqueue(c);
     if (st == cudaSuccess) st = join_cases(b);
     const cudaError_t sw = cudaStreamSynchronize(b->stream);
     if (st == cudaSuccess) st = sw;
     if (st != cudaSuccess) {
         for (int c = 0; c < b->B; ++c) cudaStreamSynchronize(b->cs[c]->stream);
-        return bfail(b, st, "batch_set_pops");
+        return bfail(b, st, what);
     }
     if (t)
         for (int c = 0; c < b->B; ++c) b->cs[c]->t = t[c];
     return ALELB_OK;
 }
 
-extern "C" alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *const *g)
+// The same for reading; each case's error word comes back with its arrays.
+template <class Enqueue> alelb_status batch_get(alelb_batch *b, Enqueue enqueue, const char *what)
 {
-    if (!b || !f || !g) return ALELB_ERR_ARG;
-    for (int c = 0; c < b->B; ++c)
-        if (!f[c] || !g[c]) return ALELB_ERR_ARG;
-    // every case's kernels, copies and error word queued, then one wait
     cudaError_t st = cudaSuccess;
     for (int c = 0; c < b->B && st == cudaSuccess; ++c) {
         alelb_solver *s = b->cs[c];
-        st = export_enqueue(s, f[c], g[c], nullptr);
+        st = enqueue(c);
         if (st == cudaSuccess)
             st = cudaMemcpyAsync(b->h_err + c, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
     }
@@ -1620,7 +1614,7 @@ extern "C" alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, d
     if (st == cudaSuccess) st = sw;
     if (st != cudaSuccess) {
         for (int c = 0; c < b->B; ++c) cudaStreamSynchronize(b->cs[c]->stream);
-        return bfail(b, st, "batch_get_pops");
+        return bfail(b, st, what);
     }
     for (int c = 0; c < b->B; ++c) {
         alelb_solver *s = b->cs[c];
@@ -1632,6 +1626,44 @@ extern "C" alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, d
         }
     }
     return ALELB_OK;
+}
+
+template <class P> bool all_set(const alelb_batch *b, P *const *f, P *const *g)
+{
+    if (!f || !g) return false;
+    for (int c = 0; c < b->B; ++c)
+        if (!f[c] || !g[c]) return false;
+    return true;
+}
+} // namespace
+
+extern "C" alelb_status alelb_batch_set_pops(alelb_batch *b, const double *const *f, const double *const *g,
+                                             const double *t)
+{
+    if (!b || !all_set(b, f, g)) return ALELB_ERR_ARG;
+    return batch_set(b, [&](int c) { return import_enqueue(b->cs[c], f[c], g[c], nullptr, nullptr, nullptr, nullptr); },
+                     t, "batch_set_pops");
+}
+
+extern "C" alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *const *g)
+{
+    if (!b || !all_set(b, f, g)) return ALELB_ERR_ARG;
+    return batch_get(b, [&](int c) { return export_enqueue(b->cs[c], f[c], g[c], nullptr); }, "batch_get_pops");
+}
+
+extern "C" alelb_status alelb_batch_set_pops_dev32(alelb_batch *b, const float *const *f, const float *const *g,
+                                                   const double *t)
+{
+    if (!b || !all_set(b, f, g) || b->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
+    return batch_set(b, [&](int c) { return import_dev32_enqueue(b->cs[c], f[c], g[c]); }, t,
+                     "batch_set_pops_dev32");
+}
+
+extern "C" alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const *f, float *const *g)
+{
+    if (!b || !all_set(b, f, g) || b->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
+    return batch_get(b, [&](int c) { return export_dev32_enqueue(b->cs[c], f[c], g[c]); },
+                     "batch_get_pops_dev32");
 }
 
 extern "C" alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t choice[8])

@@ -1,0 +1,96 @@
+"""The host exchange in the FP32-deviation form's stored form
+(alelb_get_pops_dev32 / alelb_set_pops_dev32 and their batched forms).
+
+What it must give: the deviations exactly as the device stores them (a get,
+then a set, restores the state bit for bit); the same fields as the FP64
+exchange of the same state (both compute them from the full populations
+d + f^eq in FP64); full FP64 populations that differ from the deviations by
+one constant per direction (the reference equilibria); and refusals for the
+FP64 form.
+"""
+import numpy as np
+import pytest
+
+from paper_2002_04353_gb300 import alelb
+from test_batch import _cases, _solvers
+
+pytestmark = pytest.mark.gpu
+
+
+def test_round_trip_restores_the_stored_state_bit_for_bit():
+    s = _solvers(_cases()[1:2], alelb.PREC_FP32_DEV)[0]
+    s.lb_step(5)
+    df, dg = s.get_pops_dev32()
+    s.lb_step(3)
+    s.set_pops_dev32(df, dg, t=5.0)
+    assert s.time()[0] == 5.0
+    ef, eg = s.get_pops_dev32()
+    assert np.array_equal(ef, df) and np.array_equal(eg, dg)
+    assert all(np.isfinite(v).all() for v in s.moments().values())
+
+
+def test_fields_equal_those_of_the_fp64_exchange():
+    cases = _cases()[2:3]
+    a, b = _solvers(cases, alelb.PREC_FP32_DEV), _solvers(cases, alelb.PREC_FP32_DEV)
+    for s in a + b:
+        s.lb_step(4)
+    f, g = a[0].get_pops()
+    df, dg = b[0].get_pops_dev32()
+    # full values minus stored deviations: the reference equilibria, one
+    # constant per direction (to the FP64 rounding of the sum)
+    for full, dev in ((f, df), (g, dg)):
+        ref = full - dev.astype(np.float64)
+        spread = ref.max(axis=1) - ref.min(axis=1)
+        assert np.all(spread <= 4e-16 * np.abs(full).max()), spread
+    a[0].set_pops(f, g, t=9.0)
+    b[0].set_pops_dev32(df, dg, t=9.0)
+    ma, mb = a[0].moments(), b[0].moments()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
+
+
+def test_batched_form_matches_the_per_case_calls():
+    cases = _cases()
+    ss = _solvers(cases, alelb.PREC_FP32_DEV)
+    b = alelb.Batch(ss)
+    b.step(4)
+    b.sync()
+    hf = [np.empty((9, s.nn), dtype=np.float32) for s in ss]
+    hg = [np.empty((9, s.nn), dtype=np.float32) for s in ss]
+    b.get_pops_dev32(hf, hg)
+    for s, f, g in zip(ss, hf, hg):
+        ef, eg = s.get_pops_dev32()
+        assert np.array_equal(f, ef) and np.array_equal(g, eg)
+    # perturbed deviations back in at new times, against the per-case call
+    rng = np.random.default_rng(5)
+    pf = [(f + 1e-6 * rng.standard_normal(f.shape)).astype(np.float32) for f in hf]
+    pg = [(g + 1e-6 * rng.standard_normal(g.shape)).astype(np.float32) for g in hg]
+    t = np.arange(len(ss), dtype=np.float64) + 20.0
+    b.set_pops_dev32(pf, pg, t=t)
+    alone = _solvers(cases, alelb.PREC_FP32_DEV)
+    for s, f, g, tc in zip(alone, pf, pg, t):
+        s.set_pops_dev32(f, g, t=tc)
+    for sa, sb, f, g in zip(alone, ss, pf, pg):
+        assert sa.time()[0] == sb.time()[0]
+        fa, ga = sb.get_pops_dev32()
+        assert np.array_equal(fa, f) and np.array_equal(ga, g)
+        ma, mb = sa.moments(), sb.moments()
+        assert all(np.array_equal(ma[k], mb[k]) for k in ma)
+
+
+def test_other_precisions_and_bad_arrays_are_refused():
+    s64 = _solvers(_cases()[:1], alelb.PREC_FP64)[0]
+    with pytest.raises(alelb.AlelbError) as e:
+        s64.get_pops_dev32()
+    assert e.value.status == -1
+    n = s64.nn
+    with pytest.raises(alelb.AlelbError):
+        s64.set_pops_dev32(np.zeros((9, n), np.float32), np.zeros((9, n), np.float32))
+    b64 = alelb.Batch([s64])
+    with pytest.raises(alelb.AlelbError):
+        b64.get_pops_dev32([np.empty((9, n), np.float32)], [np.empty((9, n), np.float32)])
+    s32 = _solvers(_cases()[:1], alelb.PREC_FP32_DEV)[0]
+    with pytest.raises(ValueError):
+        s32.get_pops_dev32(np.empty((9, s32.nn)), None)  # float64 out array
+    with pytest.raises(ValueError):
+        s32.set_pops_dev32(np.zeros((9, s32.nn - 1), np.float32), np.zeros((9, s32.nn), np.float32))
