@@ -468,21 +468,23 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     # end to end with host buffers: every step uploads every case's
     # populations from pinned host memory, advances the batch one step and
     # reads every case's populations back; a fresh batch from the
-    # free-stream start.  The headline figure exchanges the FP32-deviation
-    # form's stored deviations (alelb_batch_set_pops_dev32 / _get_pops_dev32:
-    # exact, 72 B per node each way); the FP64 exchange (alelb_batch_set_pops
-    # / _get_pops: full FP64 values, 144 B) is timed beside it.
-    e2e = e2e_fp64 = None
+    # free-stream start.  The headline figure is alelb_batch_step_host (the
+    # FP32-deviation form's stored deviations, exact, 72 B per node each way,
+    # uploads, step and read-back pipelined by case group); beside it the
+    # same exchange as three calls (alelb_batch_set_pops_dev32, _step,
+    # _get_pops_dev32) and the FP64 exchange (alelb_batch_set_pops /
+    # _get_pops: full FP64 values, 144 B).
+    e2e = e2e_calls = e2e_fp64 = None
     if not args.no_e2e:
         Ke = args.e2e_steps
 
-        def exchange_loop(dtype, stored):
+        def exchange_loop(dtype, mode):
             # a fresh batch per form, so that both run within the first steps
             # from the impulsive start, where every case stays finite
             solvers = [alelb.Solver(m, fl, alelb.PREC_FP32_DEV) for m, fl in zip(meshes, flows)]
             b = alelb.Batch(solvers, stream=stream.cuda_stream)
             b.tune(reps=1)
-            get, put = (b.get_pops_dev32, b.set_pops_dev32) if stored else (b.get_pops, b.set_pops)
+            get, put = (b.get_pops, b.set_pops) if mode == "fp64" else (b.get_pops_dev32, b.set_pops_dev32)
             hf = [torch.empty((9, c.mesh.n_nodes), dtype=dtype).pin_memory().numpy() for c in cases]
             hg = [torch.empty((9, c.mesh.n_nodes), dtype=dtype).pin_memory().numpy() for c in cases]
             get(hf, hg)
@@ -490,23 +492,31 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for k in range(Ke):
-                put(hf, hg, t=t_now + k)
-                b.step(1)
-                get(hf, hg)
+                if mode == "pipelined":
+                    b.step_host(hf, hg, hf, hg, t=t_now + k)
+                else:
+                    put(hf, hg, t=t_now + k)
+                    b.step(1)
+                    get(hf, hg)
             dt = time.perf_counter() - t0
             b.close()
             for s in solvers:
                 s.close()
             return dt
 
-        dt = exchange_loop(torch.float32, True)
+        dt = exchange_loop(torch.float32, "pipelined")
         bytes_step = 18 * 4 * n_nodes
         e2e = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                "d2h_bytes_per_step": bytes_step, "steps": Ke,
-               "note": "host-resident state: per step alelb_batch_set_pops_dev32 (every case's stored FP32 "
-                       "deviations from pinned host arrays), alelb_batch_step(1), alelb_batch_get_pops_dev32 "
-                       "(fresh batch, free-stream start)"}
-        dt = exchange_loop(torch.float64, False)
+               "note": "host-resident state: per step one alelb_batch_step_host (every case's stored FP32 "
+                       "deviations from and back to pinned host arrays, the copies and the step pipelined by "
+                       "case group; fresh batch, free-stream start)"}
+        dt = exchange_loop(torch.float32, "calls")
+        e2e_calls = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
+                     "d2h_bytes_per_step": bytes_step, "steps": Ke,
+                     "note": "the same as three calls: alelb_batch_set_pops_dev32, alelb_batch_step(1), "
+                             "alelb_batch_get_pops_dev32"}
+        dt = exchange_loop(torch.float64, "fp64")
         bytes_step = 18 * 8 * n_nodes
         e2e_fp64 = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                     "d2h_bytes_per_step": bytes_step, "steps": Ke,
@@ -519,7 +529,8 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
             "exact_path_per_step": n_exact,
             "cases_on_shifted_lattice": sum(1 for fl in flows if any(fl.shift)), "tuned_launch_shapes": choice,
             "kernels": kernels, "kernel_rooflines": rl, "method_bytes_per_step": method_bytes(n_nodes, n_elems),
-            "persistent_form": persistent, "e2e": e2e, "e2e_fp64_exchange": e2e_fp64, "clocks": clocks,
+            "persistent_form": persistent, "e2e": e2e, "e2e_three_calls": e2e_calls, "e2e_fp64_exchange": e2e_fp64,
+            "clocks": clocks,
             # five phase kernels per step (propagation, exact path, moments, first derivative pass,
             # collision) in every case group
             "gpu_launches": 5 * K * groups}

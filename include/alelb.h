@@ -419,6 +419,20 @@ alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *cons
 alelb_status alelb_batch_set_pops_dev32(alelb_batch *b, const float *const *f, const float *const *g,
                                         const double *t);
 alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const *f, float *const *g);
+/* One step of every case with its state in host memory, in the stored form
+   of ALELB_PREC_FP32_DEV (the paper has no counterpart): the same values as
+   alelb_batch_set_pops_dev32(f_in, g_in, t), alelb_batch_step(b, 1) and
+   alelb_batch_get_pops_dev32(f_out, g_out), bit for bit, but pipelined by
+   case group: each group steps as soon as its own cases are uploaded, and
+   its cases are read back while later groups still upload, so that the
+   host link carries both directions at once.  f_out[c] may be f_in[c]
+   (likewise g).  The step's kernels are launched directly on the groups'
+   streams (not from the captured graphs, not profiled) with the batch's
+   launch shapes.  t (may be NULL): the cases' times before the step; each
+   case advances by one step.  Synchronous; errors as
+   alelb_batch_get_pops_dev32. */
+alelb_status alelb_batch_step_host(alelb_batch *b, const float *const *f_in, const float *const *g_in,
+                                   float *const *f_out, float *const *g_out, const double *t);
 
 /* Sets the launch shapes that alelb_batch_tune would choose, in its
    encoding (for example a choice saved from an earlier tuning):

@@ -50,7 +50,7 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
            "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait", "alelb_batch_set_choice",
            "alelb_batch_set_pops", "alelb_batch_get_pops", "alelb_get_pops_dev32", "alelb_set_pops_dev32",
-           "alelb_batch_set_pops_dev32", "alelb_batch_get_pops_dev32"]
+           "alelb_batch_set_pops_dev32", "alelb_batch_get_pops_dev32", "alelb_batch_step_host"]
 
 
 class AlelbError(RuntimeError):
@@ -143,6 +143,7 @@ def load(path: str = LIB_PATH):
     L.alelb_set_pops_dev32.argtypes = [p, p, p, d]
     L.alelb_batch_set_pops_dev32.argtypes = [p, p, p, p]
     L.alelb_batch_get_pops_dev32.argtypes = [p, p, p]
+    L.alelb_batch_step_host.argtypes = [p, p, p, p, p, p]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -476,6 +477,17 @@ class Batch:
         """Every case's stored FP32 deviations into host arrays."""
         self._check(load().alelb_batch_get_pops_dev32(self.h, self._planes(f, True, np.float32),
                                                       self._planes(g, True, np.float32)), "batch_get_pops_dev32")
+
+    def step_host(self, f_in, g_in, f_out, g_out, t=None):
+        """One step with every case's stored FP32 deviations in host arrays:
+        uploads, the step and the read-back pipelined by case group (the
+        output arrays may be the input arrays)."""
+        tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
+        self._check(load().alelb_batch_step_host(self.h, self._planes(f_in, False, np.float32),
+                                                 self._planes(g_in, False, np.float32),
+                                                 self._planes(f_out, True, np.float32),
+                                                 self._planes(g_out, True, np.float32),
+                                                 None if tt is None else _ptr(tt)), "batch_step_host")
 
     def set_choice(self, choice):
         """Launch shapes in alelb_batch_tune's encoding (8 int32 values)."""

@@ -826,9 +826,10 @@ Part whole(const alelb_batch *b)
     return P;
 }
 
-Part group(const alelb_batch *b, int g, bool pdl)
+// Group g of the split into `groups` (2 or 4) groups.
+Part group(const alelb_batch *b, int groups, int g, bool pdl)
 {
-    const alelb_batch::Run &R = b->groups == 4 ? b->run4[g] : b->run2[g];
+    const alelb_batch::Run &R = groups == 4 ? b->run4[g] : b->run2[g];
     Part P{g ? b->gstream[g] : b->stream, R.c0, R.n, {}, {}, pdl};
     for (int q = 0; q < N_BS; ++q) {
         P.off[q] = R.d_off[q];
@@ -1007,7 +1008,7 @@ cudaError_t enqueue_groups(alelb_batch *b, int k)
         }
         for (int q = 0; q < ns && st == cudaSuccess; ++q) {
             const int kt = seq[q];
-            launch_kernel(b, group(b, g, pdl), kt, b->bs[kt], b->slow_grid, k, 1, b->fast_g, b->stage[kt]);
+            launch_kernel(b, group(b, b->groups, g, pdl), kt, b->bs[kt], b->slow_grid, k, 1, b->fast_g, b->stage[kt]);
             pdl = true;
             if (q + 1 == lead) st = cudaEventRecord(b->gev_fast[g], sg);
         }
@@ -1664,6 +1665,86 @@ extern "C" alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const 
     if (!b || !all_set(b, f, g) || b->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
     return batch_get(b, [&](int c) { return export_dev32_enqueue(b->cs[c], f[c], g[c]); },
                      "batch_get_pops_dev32");
+}
+
+// One step with the state in host memory, pipelined by case group: every
+// case's upload is queued first, group by group; each group's phase kernels
+// start as soon as its own cases are in (on the group's stream), and each
+// case's download as soon as its group's step is done, so that the uploads
+// of later groups, the steps and the downloads of earlier ones overlap (the
+// link carries both directions at once).  Per case the same kernels as
+// set_pops_dev32, one batch step and get_pops_dev32.
+extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const *f_in, const float *const *g_in,
+                                              float *const *f_out, float *const *g_out, const double *t)
+{
+    if (!b || !all_set(b, f_in, g_in) || !all_set(b, f_out, g_out) || b->prec != ALELB_PREC_FP32_DEV)
+        return ALELB_ERR_ARG;
+    if (t)
+        for (int c = 0; c < b->B; ++c) b->cs[c]->t = t[c];
+    const int P = b->has4 ? 4 : b->has2 ? 2 : 1;
+    const auto part = [&](int g) {
+        Part G = P > 1 ? group(b, P, g, false) : whole(b);
+        G.pdl = false; // its first kernel follows waits on other streams
+        return G;
+    };
+    cudaError_t st = cudaSuccess;
+    for (int g = 0; g < P && st == cudaSuccess; ++g) {
+        const Part G = part(g);
+        for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
+            const int u = b->ord[j];
+            st = import_dev32_enqueue(b->cs[u], f_in[u], g_in[u]);
+        }
+    }
+    if (st == cudaSuccess) st = stage_scalars(b, 0, 1); // the map scalars of time t_c + 1
+    if (st == cudaSuccess) st = cudaEventRecord(b->gev_fork, b->stream);
+    int seq[KT_N];
+    const int ns = step_sequence(b, seq);
+    for (int g = 0; g < P && st == cudaSuccess; ++g) {
+        Part G = part(g);
+        st = cudaStreamWaitEvent(G.stream, b->gev_fork, 0);
+        for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
+            const int u = b->ord[j];
+            st = cudaEventRecord(b->ev_in[u], b->cs[u]->stream);
+            if (st == cudaSuccess) st = cudaStreamWaitEvent(G.stream, b->ev_in[u], 0);
+        }
+        for (int q = 0; q < ns && st == cudaSuccess; ++q) {
+            const int kt = seq[q];
+            launch_kernel(b, G, kt, b->bs[kt], b->slow_grid, 0, 1, b->fast_g, b->stage[kt]);
+            G.pdl = true;
+            st = cudaGetLastError();
+        }
+        if (st == cudaSuccess) st = cudaEventRecord(b->gev_fast[g], G.stream);
+        for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
+            const int u = b->ord[j];
+            alelb_solver *s = b->cs[u];
+            st = cudaStreamWaitEvent(s->stream, b->gev_fast[g], 0);
+            if (st == cudaSuccess) st = export_dev32_enqueue(s, f_out[u], g_out[u]);
+            if (st == cudaSuccess)
+                st = cudaMemcpyAsync(b->h_err + u, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        }
+    }
+    // the batch's stream after every case (so later batch calls follow), one wait
+    if (st == cudaSuccess) st = join_cases(b);
+    const cudaError_t sw = cudaStreamSynchronize(b->stream);
+    if (st == cudaSuccess) st = sw;
+    if (st != cudaSuccess) {
+        for (int c = 0; c < b->B; ++c) cudaStreamSynchronize(b->cs[c]->stream);
+        return bfail(b, st, "batch_step_host");
+    }
+    for (alelb_solver *s : b->cs) {
+        s->t += 1.0;
+        s->nstep += 1;
+    }
+    for (int c = 0; c < b->B; ++c) {
+        alelb_solver *s = b->cs[c];
+        s->sticky |= b->h_err[c];
+        const alelb_status r = check_sticky(s);
+        if (r != ALELB_OK) {
+            b->err = "case " + std::to_string(c) + ": " + s->err;
+            return r;
+        }
+    }
+    return ALELB_OK;
 }
 
 extern "C" alelb_status alelb_batch_set_choice(alelb_batch *b, const int32_t choice[8])

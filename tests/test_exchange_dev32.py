@@ -94,3 +94,39 @@ def test_other_precisions_and_bad_arrays_are_refused():
         s32.get_pops_dev32(np.empty((9, s32.nn)), None)  # float64 out array
     with pytest.raises(ValueError):
         s32.set_pops_dev32(np.zeros((9, s32.nn - 1), np.float32), np.zeros((9, s32.nn), np.float32))
+
+
+@pytest.mark.parametrize("n_cases", [4, 1])
+def test_pipelined_host_step_equals_set_step_get(n_cases):
+    """alelb_batch_step_host (uploads, the step and the read-back pipelined
+    by case group) against the three calls it stands for, three steps in a
+    row: the same stored deviations, times, fields and walk counts, bit for
+    bit; in place (outputs = inputs) and into other arrays."""
+    cases = _cases()[:n_cases]
+    ref, pip = _solvers(cases, alelb.PREC_FP32_DEV), _solvers(cases, alelb.PREC_FP32_DEV)
+    br, bp = alelb.Batch(ref), alelb.Batch(pip)
+    br.step(3)
+    bp.step(3)
+    hf = [np.empty((9, s.nn), dtype=np.float32) for s in ref]
+    hg = [np.empty((9, s.nn), dtype=np.float32) for s in ref]
+    br.get_pops_dev32(hf, hg)
+    pf, pg = [a.copy() for a in hf], [a.copy() for a in hg]
+    of, og = [np.empty_like(a) for a in hf], [np.empty_like(a) for a in hg]
+    for k in range(3):
+        t = np.arange(len(cases), dtype=np.float64) + 3.0 + k
+        br.set_pops_dev32(hf, hg, t=t)
+        br.step(1)
+        br.get_pops_dev32(hf, hg)
+        if k == 1:  # into other arrays, then back
+            bp.step_host(pf, pg, of, og, t=t)
+            for a, b in zip(pf + pg, of + og):
+                a[...] = b
+        else:
+            bp.step_host(pf, pg, pf, pg, t=t)
+        for c in range(len(cases)):
+            assert np.array_equal(pf[c], hf[c]) and np.array_equal(pg[c], hg[c]), f"step {k} case {c}"
+            assert ref[c].time() == pip[c].time()
+    for sa, sb in zip(ref, pip):
+        ma, mb = sa.moments(), sb.moments()
+        assert all(np.array_equal(ma[k], mb[k]) for k in ma)
+        assert sa.info()["walks"] == sb.info()["walks"]
