@@ -728,6 +728,7 @@ struct alelb_batch {
     bool has2 = false, has4 = false; // every group of the split holds a case
     cudaStream_t gstream[GROUPS_MAX] = {}; // [0] unused: group 0 runs on the batch's stream
     cudaEvent_t gev_fork = nullptr, gev_join[GROUPS_MAX] = {}, gev_fast[GROUPS_MAX] = {};
+    cudaEvent_t gev_up[GROUPS_MAX] = {}; // alelb_batch_step_host: group g's uploads are in
     // the persistent form (mode ALELB_BATCH_PERSISTENT): threads per block,
     // blocks (all resident), barrier words {count, gen, abort}, wait limit
     int mode = ALELB_BATCH_GRAPHS;
@@ -1208,6 +1209,7 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     for (int g = 0; g < GROUPS_MAX && st == cudaSuccess; ++g) {
         st = cudaEventCreateWithFlags(&b->gev_join[g], cudaEventDisableTiming);
         if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->gev_fast[g], cudaEventDisableTiming);
+        if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->gev_up[g], cudaEventDisableTiming);
     }
     if (st == cudaSuccess)
         st = b->prec == ALELB_PREC_FP32_DEV ? upload_cases<float, float>(b) : upload_cases<double, double>(b);
@@ -1248,6 +1250,7 @@ extern "C" void alelb_batch_destroy(alelb_batch *b)
     for (int g = 0; g < GROUPS_MAX; ++g) {
         if (b->gev_join[g]) cudaEventDestroy(b->gev_join[g]);
         if (b->gev_fast[g]) cudaEventDestroy(b->gev_fast[g]);
+        if (b->gev_up[g]) cudaEventDestroy(b->gev_up[g]);
         if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
     }
     if (b->h_err) cudaFreeHost(b->h_err);
@@ -1667,13 +1670,16 @@ extern "C" alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const 
                      "batch_get_pops_dev32");
 }
 
-// One step with the state in host memory, pipelined by case group: every
-// case's upload is queued first, group by group; each group's phase kernels
-// start as soon as its own cases are in (on the group's stream), and each
-// case's download as soon as its group's step is done, so that the uploads
-// of later groups, the steps and the downloads of earlier ones overlap (the
-// link carries both directions at once).  Per case the same kernels as
-// set_pops_dev32, one batch step and get_pops_dev32.
+// One step with the state in host memory, pipelined by case group: the
+// groups' uploads run one group after another (a group's copies wait until
+// the previous group's are in: the copy engine would otherwise interleave
+// every case's copies, and no group would be ready before all of them);
+// each group's phase kernels start on the group's stream once its own
+// cases are in, and each case's read-back once its group's step is done,
+// so that the uploads of later groups, the steps and the read-back of
+// earlier ones overlap (the host link carries both directions at once).
+// Per case the same kernels as set_pops_dev32, one batch step and
+// get_pops_dev32.
 extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const *f_in, const float *const *g_in,
                                               float *const *f_out, float *const *g_out, const double *t)
 {
@@ -1687,26 +1693,26 @@ extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const
         G.pdl = false; // its first kernel follows waits on other streams
         return G;
     };
-    cudaError_t st = cudaSuccess;
-    for (int g = 0; g < P && st == cudaSuccess; ++g) {
-        const Part G = part(g);
-        for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
-            const int u = b->ord[j];
-            st = import_dev32_enqueue(b->cs[u], f_in[u], g_in[u]);
-        }
-    }
-    if (st == cudaSuccess) st = stage_scalars(b, 0, 1); // the map scalars of time t_c + 1
+    cudaError_t st = stage_scalars(b, 0, 1); // the map scalars of time t_c + 1
     if (st == cudaSuccess) st = cudaEventRecord(b->gev_fork, b->stream);
     int seq[KT_N];
     const int ns = step_sequence(b, seq);
     for (int g = 0; g < P && st == cudaSuccess; ++g) {
         Part G = part(g);
-        st = cudaStreamWaitEvent(G.stream, b->gev_fork, 0);
+        // the group's uploads, after the previous group's
+        for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
+            const int u = b->ord[j];
+            if (g > 0) st = cudaStreamWaitEvent(b->cs[u]->stream, b->gev_up[g - 1], 0);
+            if (st == cudaSuccess) st = import_dev32_enqueue(b->cs[u], f_in[u], g_in[u]);
+        }
+        // the group's stream waits for them (and the scalars)
+        if (st == cudaSuccess) st = cudaStreamWaitEvent(G.stream, b->gev_fork, 0);
         for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
             const int u = b->ord[j];
             st = cudaEventRecord(b->ev_in[u], b->cs[u]->stream);
             if (st == cudaSuccess) st = cudaStreamWaitEvent(G.stream, b->ev_in[u], 0);
         }
+        if (st == cudaSuccess) st = cudaEventRecord(b->gev_up[g], G.stream);
         for (int q = 0; q < ns && st == cudaSuccess; ++q) {
             const int kt = seq[q];
             launch_kernel(b, G, kt, b->bs[kt], b->slow_grid, 0, 1, b->fast_g, b->stage[kt]);
