@@ -344,40 +344,41 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
 
 // The FP32-deviation form's stored pairs <-> the caller's [9][N] FP32
 // planes of the same deviations, without conversion (the exchange is exact
-// both ways).  Import: both planes, and the fields from the full FP64
-// populations d + ref, computed as k_import computes them (f: rho and u;
-// then g: T).
-__global__ void k_import_dev32(StateDev<float> st, int N, const double *consts, const float *pf, const float *pg,
-                               double Cv, double Ux, double Uy, const int *n2o)
+// both ways).  Import, part 0: the f plane, and rho and u into tmp from the
+// full FP64 populations d + ref, as k_import computes them; part 1: the g
+// plane and the fields.
+__global__ void k_import_dev32(StateDev<float> st, int N, const double *consts, const float *plane, double Cv,
+                               double Ux, double Uy, const int *n2o, double *tmp, int part)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
     const int o = n2o[a];
     double sum = 0, jx = 0, jy = 0;
     for (int i = 0; i < NQ; ++i) {
-        const float d = pf[i * N + o];
-        pop_put1(st.post, i, a, N, 0, (double)d);
-        const double v = (double)d + consts[i];
+        const float d = plane[i * N + o];
+        pop_put1(st.post, i, a, N, part, (double)d);
+        const double v = (double)d + consts[part * NQ + i];
         sum += v;
-        jx += c_cx[i] * v;
-        jy += c_cy[i] * v;
+        if (part == 0) {
+            jx += c_cx[i] * v;
+            jy += c_cy[i] * v;
+        }
     }
-    const double r = sum, ux = jx / sum + Ux, uy = jy / sum + Uy;
-    double esum = 0;
-    for (int i = 0; i < NQ; ++i) {
-        const float d = pg[i * N + o];
-        pop_put1(st.post, i, a, N, 1, (double)d);
-        esum += (double)d + consts[NQ + i];
+    if (part == 0) {
+        tmp[a] = sum;
+        tmp[N + a] = jx / sum + Ux;
+        tmp[2 * N + a] = jy / sum + Uy;
+    } else {
+        const double r = tmp[a], ux = tmp[N + a], uy = tmp[2 * N + a], E = sum / (2 * r);
+        st.rho[a] = (float)r;
+        st.ux[a] = (float)ux;
+        st.uy[a] = (float)uy;
+        st.T[a] = (float)((E - 0.5 * (ux * ux + uy * uy)) / Cv);
     }
-    const double E = esum / (2 * r);
-    st.rho[a] = (float)r;
-    st.ux[a] = (float)ux;
-    st.uy[a] = (float)uy;
-    st.T[a] = (float)((E - 0.5 * (ux * ux + uy * uy)) / Cv);
 }
 
-// Export: both planes.
-__global__ void k_export_dev32(StateDev<float> st, int N, float *pf, float *pg, const int *n2o)
+// Export: part 0 the f deviations, part 1 the g deviations.
+__global__ void k_export_dev32(StateDev<float> st, int N, float *plane, const int *n2o, int part)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
@@ -385,8 +386,7 @@ __global__ void k_export_dev32(StateDev<float> st, int N, float *pf, float *pg, 
     for (int i = 0; i < NQ; ++i) {
         float f, g;
         fg_get(st.post, i, a, N, f, g);
-        pf[i * N + o] = f;
-        pg[i * N + o] = g;
+        plane[i * N + o] = part == 0 ? f : g;
     }
 }
 
@@ -856,19 +856,27 @@ cudaError_t alelb::import_enqueue(alelb_solver *s, const double *f, const double
 
 // The FP32-deviation form's exchange in its stored form: half the bytes of
 // the FP64 exchange, and exact.  The planes sit in the FP64 scratch as
-// floats ([0, 9N) f, [9N, 18N) g).  One kernel and two copies, all on the
-// solver's stream (each copy alone fills the host link), so that a batch
-// of many cases queues few calls.
+// floats ([0, 9N) f, [9N, 18N) g), clear of the fields area at 18N doubles.
 cudaError_t alelb::export_dev32_enqueue(alelb_solver *s, float *f, float *g)
 {
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
     float *pf = reinterpret_cast<float *>(s->d_scratch), *pg = pf + (size_t)9 * N;
     const size_t plane = (size_t)9 * N * sizeof(float);
-    k_export_dev32<<<(N + 255) / 256, 256, 0, s->stream>>>(s->sf, N, pf, pg, m->d_n2o);
+    const dim3 grid((N + 255) / 256), block(256);
+    // the f copy on the copy stream overlaps the g kernel (as export_enqueue)
+    k_export_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, pf, m->d_n2o, 0);
     cudaError_t st = cudaGetLastError();
-    if (st == cudaSuccess) st = cudaMemcpyAsync(f, pf, plane, cudaMemcpyDeviceToHost, s->stream);
+    if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[0], s->stream);
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(s->copy_stream, s->ev_copy[0], 0);
+    if (st == cudaSuccess) st = cudaMemcpyAsync(f, pf, plane, cudaMemcpyDeviceToHost, s->copy_stream);
+    if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
+    if (st == cudaSuccess) {
+        k_export_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, pg, m->d_n2o, 1);
+        st = cudaGetLastError();
+    }
     if (st == cudaSuccess) st = cudaMemcpyAsync(g, pg, plane, cudaMemcpyDeviceToHost, s->stream);
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(s->stream, s->ev_copy[1], 0);
     return st;
 }
 
@@ -876,13 +884,25 @@ cudaError_t alelb::import_dev32_enqueue(alelb_solver *s, const float *f, const f
 {
     const int N = s->mesh->T.N;
     float *pf = reinterpret_cast<float *>(s->d_scratch), *pg = pf + (size_t)9 * N;
+    double *tmp = s->d_scratch + (size_t)18 * N;
     const size_t plane = (size_t)9 * N * sizeof(float);
     cudaError_t st = cudaMemcpyAsync(pf, f, plane, cudaMemcpyHostToDevice, s->stream);
-    if (st == cudaSuccess) st = cudaMemcpyAsync(pg, g, plane, cudaMemcpyHostToDevice, s->stream);
+    if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[0], s->stream);
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(s->copy_stream, s->ev_copy[0], 0);
+    if (st == cudaSuccess) st = cudaMemcpyAsync(pg, g, plane, cudaMemcpyHostToDevice, s->copy_stream);
+    if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
     if (st != cudaSuccess) return st;
-    k_import_dev32<<<(N + 255) / 256, 256, 0, s->stream>>>(s->sf, N, s->d_consts, pf, pg, s->Cv, s->U[0], s->U[1],
-                                                           s->mesh->d_n2o);
-    return cudaGetLastError();
+    const dim3 grid((N + 255) / 256), block(256);
+    k_import_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, s->d_consts, pf, s->Cv, s->U[0], s->U[1],
+                                                  s->mesh->d_n2o, tmp, 0);
+    st = cudaGetLastError();
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(s->stream, s->ev_copy[1], 0);
+    if (st == cudaSuccess) {
+        k_import_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, s->d_consts, pg, s->Cv, s->U[0], s->U[1],
+                                                      s->mesh->d_n2o, tmp, 1);
+        st = cudaGetLastError();
+    }
+    return st;
 }
 
 extern "C" alelb_status alelb_get_pops_dev32(alelb_solver *s, float *f, float *g)
