@@ -1735,6 +1735,8 @@ extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const
     if (st == cudaSuccess) st = sw;
     if (st != cudaSuccess) {
         for (int c = 0; c < b->B; ++c) cudaStreamSynchronize(b->cs[c]->stream);
+        for (int g = 1; g < GROUPS_MAX; ++g)
+            if (b->gstream[g]) cudaStreamSynchronize(b->gstream[g]);
         return bfail(b, st, "batch_step_host");
     }
     for (alelb_solver *s : b->cs) {
