@@ -89,11 +89,19 @@ def test_other_precisions_and_bad_arrays_are_refused():
     b64 = alelb.Batch([s64])
     with pytest.raises(alelb.AlelbError):
         b64.get_pops_dev32([np.empty((9, n), np.float32)], [np.empty((9, n), np.float32)])
+    planes = [np.zeros((9, n), np.float32)]
+    with pytest.raises(alelb.AlelbError):
+        b64.step_host(planes, planes, planes, planes)
+    assert s64.time() == (0.0, 0)  # refused before anything ran
     s32 = _solvers(_cases()[:1], alelb.PREC_FP32_DEV)[0]
     with pytest.raises(ValueError):
         s32.get_pops_dev32(np.empty((9, s32.nn)), None)  # float64 out array
     with pytest.raises(ValueError):
         s32.set_pops_dev32(np.zeros((9, s32.nn - 1), np.float32), np.zeros((9, s32.nn), np.float32))
+    b32 = alelb.Batch([s32])
+    good = [np.zeros((9, s32.nn), np.float32)]
+    with pytest.raises(ValueError):
+        b32.step_host(good, good, [np.zeros((9, s32.nn))], good)  # float64 out array
 
 
 @pytest.mark.parametrize("n_cases", [4, 1])
