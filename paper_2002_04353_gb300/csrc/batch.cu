@@ -7,10 +7,13 @@
 // block b finds its case with one ballot over the B <= 32 offsets, copies
 // the case's descriptor (mesh tables, map statics, kinetic constants, state
 // pointers) into shared memory and runs the same per-node code as the
-// single-case kernels.  The exact part of the propagation walks every case's
-// work list in turn.  Map scalars of each (step, case) are computed on the
+// single-case kernels.  The exact part of the propagation takes every
+// case's work list as one numbered list dealt out over the grid.  Map scalars of each (step, case) are computed on the
 // host, exactly as for a single solver, and staged per chunk of steps; a
-// chunk's launches are captured once into a CUDA graph and replayed.
+// chunk's launches are captured once into a CUDA graph and replayed.  The
+// cases may also run as two or four groups, each group's launches on a
+// stream of its own (branches of the chunk's graph), so that the groups'
+// kernels share the SMs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
