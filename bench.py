@@ -471,8 +471,8 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
     # free-stream start.  The headline figure is alelb_batch_step_host (the
     # FP32-deviation form's stored deviations, exact, 72 B per node each way,
     # uploads, step and read-back pipelined by case group); beside it the
-    # same exchange as three calls (alelb_batch_set_pops_dev32, _step,
-    # _get_pops_dev32) and the FP64 exchange (alelb_batch_set_pops /
+    # same exchange as three calls (alelb_batch_set_pops_stored, _step,
+    # _get_pops_stored) and the FP64 exchange (alelb_batch_set_pops /
     # _get_pops: full FP64 values, 144 B).
     e2e = e2e_calls = e2e_fp64 = None
     if not args.no_e2e:
@@ -484,7 +484,7 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
             solvers = [alelb.Solver(m, fl, alelb.PREC_FP32_DEV) for m, fl in zip(meshes, flows)]
             b = alelb.Batch(solvers, stream=stream.cuda_stream)
             b.tune(reps=1)
-            get, put = (b.get_pops, b.set_pops) if mode == "fp64" else (b.get_pops_dev32, b.set_pops_dev32)
+            get, put = (b.get_pops, b.set_pops) if mode == "fp64" else (b.get_pops_stored, b.set_pops_stored)
             hf = [torch.empty((9, c.mesh.n_nodes), dtype=dtype).pin_memory().numpy() for c in cases]
             hg = [torch.empty((9, c.mesh.n_nodes), dtype=dtype).pin_memory().numpy() for c in cases]
             get(hf, hg)
@@ -514,8 +514,8 @@ def run_batched(alelb, torch, dev, world, rank, args, sampler=None):
         dt = exchange_loop(torch.float32, "calls")
         e2e_calls = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
                      "d2h_bytes_per_step": bytes_step, "steps": Ke,
-                     "note": "the same as three calls: alelb_batch_set_pops_dev32, alelb_batch_step(1), "
-                             "alelb_batch_get_pops_dev32"}
+                     "note": "the same as three calls: alelb_batch_set_pops_stored, alelb_batch_step(1), "
+                             "alelb_batch_get_pops_stored"}
         dt = exchange_loop(torch.float64, "fp64")
         bytes_step = 18 * 8 * n_nodes
         e2e_fp64 = {"value": world * n_nodes * Ke / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": bytes_step,
@@ -975,7 +975,7 @@ def run_single(alelb, torch, dev, world, args):
         s = alelb.Solver(mesh, case.flow, alelb.PREC_FP32_DEV, stream=stream.cuda_stream)
         Ke = max(3, K // 4)
         e2e = {}
-        for name, dtype, get, put in (("stored", torch.float32, s.get_pops_dev32, s.set_pops_dev32),
+        for name, dtype, get, put in (("stored", torch.float32, s.get_pops_stored, s.set_pops_stored),
                                       ("fp64", torch.float64, s.get_pops, s.set_pops)):
             f = torch.empty((9, N), dtype=dtype).pin_memory().numpy()
             g = torch.empty((9, N), dtype=dtype).pin_memory().numpy()

@@ -236,8 +236,22 @@ alelb_status alelb_set_pops(alelb_solver *s, const double *f, const double *g,
    populations d + f^eq in FP64, as alelb_set_pops without fields computes
    them.  Both synchronous (set returns once the arrays may be reused);
    ALELB_ERR_ARG for a NULL array or a solver of another precision. */
-alelb_status alelb_get_pops_dev32(alelb_solver *s, float *f, float *g);
-alelb_status alelb_set_pops_dev32(alelb_solver *s, const float *f, const float *g, double t);
+alelb_status alelb_get_pops_stored(alelb_solver *s, float *f, float *g);
+alelb_status alelb_set_pops_stored(alelb_solver *s, const float *f, const float *g, double t);
+
+/* Zero-copy forms of alelb_get_pops, alelb_set_pops (without fields) and
+   alelb_moments (the paper has no counterpart): the arrays are DEVICE
+   memory of the mesh's device (for example CUDA tensors), the same layouts
+   and values as the host forms, in the caller's node order, and nothing
+   crosses the host link.  The caller's arrays must hold their data (set)
+   or be free to write (get, moments) when the call is made: the calls run
+   on the solver's stream and wait for it before returning.  Any moments
+   pointer may be NULL.  ALELB_ERR_ARG for a NULL population array or for
+   an address that is not device (or managed) memory of the mesh's device;
+   errors as the host forms otherwise. */
+alelb_status alelb_get_pops_dev(alelb_solver *s, double *f, double *g);
+alelb_status alelb_set_pops_dev(alelb_solver *s, const double *f, const double *g, double t);
+alelb_status alelb_moments_dev(alelb_solver *s, double *rho, double *ux, double *uy, double *T);
 
 /* Wall forces at the current time: {Fx_p, Fy_p, Fx_v, Fy_v, c_D, c_L} with
    p = rho T, tau = mu (S - (1/Cv) div u I), Simpson's rule per straight
@@ -413,16 +427,16 @@ alelb_status alelb_batch_tune(alelb_batch *b, int32_t reps, int32_t choice[8]);
 alelb_status alelb_batch_set_pops(alelb_batch *b, const double *const *f, const double *const *g,
                                   const double *t);
 alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, double *const *g);
-/* The batched forms of alelb_get_pops_dev32 / alelb_set_pops_dev32 (FP32
+/* The batched forms of alelb_get_pops_stored / alelb_set_pops_stored (FP32
    planes of each case's stored deviations; ALELB_ERR_ARG also for a batch
    of another precision). */
-alelb_status alelb_batch_set_pops_dev32(alelb_batch *b, const float *const *f, const float *const *g,
+alelb_status alelb_batch_set_pops_stored(alelb_batch *b, const float *const *f, const float *const *g,
                                         const double *t);
-alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const *f, float *const *g);
+alelb_status alelb_batch_get_pops_stored(alelb_batch *b, float *const *f, float *const *g);
 /* One step of every case with its state in host memory, in the stored form
    of ALELB_PREC_FP32_DEV (the paper has no counterpart): the same values as
-   alelb_batch_set_pops_dev32(f_in, g_in, t), alelb_batch_step(b, 1) and
-   alelb_batch_get_pops_dev32(f_out, g_out), bit for bit, but pipelined by
+   alelb_batch_set_pops_stored(f_in, g_in, t), alelb_batch_step(b, 1) and
+   alelb_batch_get_pops_stored(f_out, g_out), bit for bit, but pipelined by
    case group: each group steps as soon as its own cases are uploaded, and
    its cases are read back while later groups still upload, so that the
    host link carries both directions at once.  f_out[c] may be f_in[c]
@@ -430,7 +444,7 @@ alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const *f, float *
    streams (not from the captured graphs, not profiled) with the batch's
    launch shapes.  t (may be NULL): the cases' times before the step; each
    case advances by one step.  Synchronous; errors as
-   alelb_batch_get_pops_dev32. */
+   alelb_batch_get_pops_stored. */
 alelb_status alelb_batch_step_host(alelb_batch *b, const float *const *f_in, const float *const *g_in,
                                    float *const *f_out, float *const *g_out, const double *t);
 

@@ -49,8 +49,9 @@ EXPORTS = ["alelb_mesh_create", "alelb_mesh_destroy", "alelb_mesh_move", "alelb_
            "alelb_samples", "alelb_mlp_loss_grad", "alelb_mlp_train", "alelb_mlp_predict",
            "alelb_solver_set_mlp", "alelb_mlp_stats", "alelb_mlp_last_error", "alelb_save", "alelb_load",
            "alelb_checkpoint_info", "alelb_batch_set_mode", "alelb_batch_set_wait", "alelb_batch_set_choice",
-           "alelb_batch_set_pops", "alelb_batch_get_pops", "alelb_get_pops_dev32", "alelb_set_pops_dev32",
-           "alelb_batch_set_pops_dev32", "alelb_batch_get_pops_dev32", "alelb_batch_step_host"]
+           "alelb_batch_set_pops", "alelb_batch_get_pops", "alelb_get_pops_stored", "alelb_set_pops_stored",
+           "alelb_batch_set_pops_stored", "alelb_batch_get_pops_stored", "alelb_batch_step_host",
+           "alelb_get_pops_dev", "alelb_set_pops_dev", "alelb_moments_dev"]
 
 
 class AlelbError(RuntimeError):
@@ -139,11 +140,14 @@ def load(path: str = LIB_PATH):
     L.alelb_batch_set_choice.argtypes = [p, p]
     L.alelb_batch_set_pops.argtypes = [p, p, p, p]
     L.alelb_batch_get_pops.argtypes = [p, p, p]
-    L.alelb_get_pops_dev32.argtypes = [p, p, p]
-    L.alelb_set_pops_dev32.argtypes = [p, p, p, d]
-    L.alelb_batch_set_pops_dev32.argtypes = [p, p, p, p]
-    L.alelb_batch_get_pops_dev32.argtypes = [p, p, p]
+    L.alelb_get_pops_stored.argtypes = [p, p, p]
+    L.alelb_set_pops_stored.argtypes = [p, p, p, d]
+    L.alelb_batch_set_pops_stored.argtypes = [p, p, p, p]
+    L.alelb_batch_get_pops_stored.argtypes = [p, p, p]
     L.alelb_batch_step_host.argtypes = [p, p, p, p, p, p]
+    L.alelb_get_pops_dev.argtypes = [p, p, p]
+    L.alelb_set_pops_dev.argtypes = [p, p, p, d]
+    L.alelb_moments_dev.argtypes = [p, p, p, p, p]
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int:  # default: alelb_status
@@ -318,19 +322,47 @@ class Solver:
         self._check(load().alelb_set_pops(self.h, _ptr(f), _ptr(g), *[_ptr(a) for a in fl], float(t)),
                     "set_pops")
 
-    def get_pops_dev32(self, f=None, g=None):
+    def get_pops_stored(self, f=None, g=None):
         """The FP32-deviation form's stored deviations, [9, n] float32 each."""
         f = np.empty((NQ, self.nn), dtype=np.float32) if f is None else _f32_out(f, self.nn)
         g = np.empty((NQ, self.nn), dtype=np.float32) if g is None else _f32_out(g, self.nn)
-        self._check(load().alelb_get_pops_dev32(self.h, _ptr(f), _ptr(g)), "get_pops_dev32")
+        self._check(load().alelb_get_pops_stored(self.h, _ptr(f), _ptr(g)), "get_pops_stored")
         return f, g
 
-    def set_pops_dev32(self, f, g, t=0.0):
+    def set_pops_stored(self, f, g, t=0.0):
         f = np.ascontiguousarray(f, dtype=np.float32)
         g = np.ascontiguousarray(g, dtype=np.float32)
         if f.size != NQ * self.nn or g.size != NQ * self.nn:
             raise ValueError(f"9 x {self.nn} values per array")
-        self._check(load().alelb_set_pops_dev32(self.h, _ptr(f), _ptr(g), float(t)), "set_pops_dev32")
+        self._check(load().alelb_set_pops_stored(self.h, _ptr(f), _ptr(g), float(t)), "set_pops_stored")
+
+    def _dev_planes(self, *ts):
+        """CUDA float64 tensors of 9 x n values (or n for fields); torch's
+        current stream is waited for, so that the caller's writes are in."""
+        import torch
+        for t in ts:
+            if t is not None and not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("contiguous float64 CUDA tensors")
+        torch.cuda.current_stream().synchronize()
+        return [_dptr(t) for t in ts]
+
+    def get_pops_dev(self, f, g):
+        """Post-collision populations into CUDA tensors [9, n] (zero-copy)."""
+        if f.numel() != NQ * self.nn or g.numel() != NQ * self.nn:
+            raise ValueError(f"9 x {self.nn} values per tensor")
+        self._check(load().alelb_get_pops_dev(self.h, *self._dev_planes(f, g)), "get_pops_dev")
+
+    def set_pops_dev(self, f, g, t=0.0):
+        if f.numel() != NQ * self.nn or g.numel() != NQ * self.nn:
+            raise ValueError(f"9 x {self.nn} values per tensor")
+        self._check(load().alelb_set_pops_dev(self.h, *self._dev_planes(f, g), float(t)), "set_pops_dev")
+
+    def moments_dev(self, rho=None, ux=None, uy=None, T=None):
+        """The fields into CUDA tensors of n values (any may be None)."""
+        for t in (rho, ux, uy, T):
+            if t is not None and t.numel() != self.nn:
+                raise ValueError(f"{self.nn} values per tensor")
+        self._check(load().alelb_moments_dev(self.h, *self._dev_planes(rho, ux, uy, T)), "moments_dev")
 
     def save(self, path):
         self._check(load().alelb_save(self.h, os.fsencode(path)), "save")
@@ -466,17 +498,17 @@ class Batch:
         self._check(load().alelb_batch_get_pops(self.h, self._planes(f, True), self._planes(g, True)),
                     "batch_get_pops")
 
-    def set_pops_dev32(self, f, g, t=None):
+    def set_pops_stored(self, f, g, t=None):
         """Every case's stored FP32 deviations from host arrays, one call."""
         tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
-        self._check(load().alelb_batch_set_pops_dev32(self.h, self._planes(f, False, np.float32),
+        self._check(load().alelb_batch_set_pops_stored(self.h, self._planes(f, False, np.float32),
                                                       self._planes(g, False, np.float32),
-                                                      None if tt is None else _ptr(tt)), "batch_set_pops_dev32")
+                                                      None if tt is None else _ptr(tt)), "batch_set_pops_stored")
 
-    def get_pops_dev32(self, f, g):
+    def get_pops_stored(self, f, g):
         """Every case's stored FP32 deviations into host arrays."""
-        self._check(load().alelb_batch_get_pops_dev32(self.h, self._planes(f, True, np.float32),
-                                                      self._planes(g, True, np.float32)), "batch_get_pops_dev32")
+        self._check(load().alelb_batch_get_pops_stored(self.h, self._planes(f, True, np.float32),
+                                                      self._planes(g, True, np.float32)), "batch_get_pops_stored")
 
     def step_host(self, f_in, g_in, f_out, g_out, t=None):
         """One step with every case's stored FP32 deviations in host arrays:

@@ -347,7 +347,7 @@ __global__ void k_import(StateDev<S> st, int N, const double *consts, const doub
 // both ways).  Import, part 0: the f plane, and rho and u into tmp from the
 // full FP64 populations d + ref, as k_import computes them; part 1: the g
 // plane and the fields.
-__global__ void k_import_dev32(StateDev<float> st, int N, const double *consts, const float *plane, double Cv,
+__global__ void k_import_stored(StateDev<float> st, int N, const double *consts, const float *plane, double Cv,
                                double Ux, double Uy, const int *n2o, double *tmp, int part)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -378,7 +378,7 @@ __global__ void k_import_dev32(StateDev<float> st, int N, const double *consts, 
 }
 
 // Export: part 0 the f deviations, part 1 the g deviations.
-__global__ void k_export_dev32(StateDev<float> st, int N, float *plane, const int *n2o, int part)
+__global__ void k_export_stored(StateDev<float> st, int N, float *plane, const int *n2o, int part)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
@@ -857,7 +857,7 @@ cudaError_t alelb::import_enqueue(alelb_solver *s, const double *f, const double
 // The FP32-deviation form's exchange in its stored form: half the bytes of
 // the FP64 exchange, and exact.  The planes sit in the FP64 scratch as
 // floats ([0, 9N) f, [9N, 18N) g), clear of the fields area at 18N doubles.
-cudaError_t alelb::export_dev32_enqueue(alelb_solver *s, float *f, float *g)
+cudaError_t alelb::export_stored_enqueue(alelb_solver *s, float *f, float *g)
 {
     alelb_mesh *m = s->mesh;
     const int N = m->T.N;
@@ -865,14 +865,14 @@ cudaError_t alelb::export_dev32_enqueue(alelb_solver *s, float *f, float *g)
     const size_t plane = (size_t)9 * N * sizeof(float);
     const dim3 grid((N + 255) / 256), block(256);
     // the f copy on the copy stream overlaps the g kernel (as export_enqueue)
-    k_export_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, pf, m->d_n2o, 0);
+    k_export_stored<<<grid, block, 0, s->stream>>>(s->sf, N, pf, m->d_n2o, 0);
     cudaError_t st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[0], s->stream);
     if (st == cudaSuccess) st = cudaStreamWaitEvent(s->copy_stream, s->ev_copy[0], 0);
     if (st == cudaSuccess) st = cudaMemcpyAsync(f, pf, plane, cudaMemcpyDeviceToHost, s->copy_stream);
     if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
     if (st == cudaSuccess) {
-        k_export_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, pg, m->d_n2o, 1);
+        k_export_stored<<<grid, block, 0, s->stream>>>(s->sf, N, pg, m->d_n2o, 1);
         st = cudaGetLastError();
     }
     if (st == cudaSuccess) st = cudaMemcpyAsync(g, pg, plane, cudaMemcpyDeviceToHost, s->stream);
@@ -880,7 +880,7 @@ cudaError_t alelb::export_dev32_enqueue(alelb_solver *s, float *f, float *g)
     return st;
 }
 
-cudaError_t alelb::import_dev32_enqueue(alelb_solver *s, const float *f, const float *g)
+cudaError_t alelb::import_stored_enqueue(alelb_solver *s, const float *f, const float *g)
 {
     const int N = s->mesh->T.N;
     float *pf = reinterpret_cast<float *>(s->d_scratch), *pg = pf + (size_t)9 * N;
@@ -893,42 +893,116 @@ cudaError_t alelb::import_dev32_enqueue(alelb_solver *s, const float *f, const f
     if (st == cudaSuccess) st = cudaEventRecord(s->ev_copy[1], s->copy_stream);
     if (st != cudaSuccess) return st;
     const dim3 grid((N + 255) / 256), block(256);
-    k_import_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, s->d_consts, pf, s->Cv, s->U[0], s->U[1],
+    k_import_stored<<<grid, block, 0, s->stream>>>(s->sf, N, s->d_consts, pf, s->Cv, s->U[0], s->U[1],
                                                   s->mesh->d_n2o, tmp, 0);
     st = cudaGetLastError();
     if (st == cudaSuccess) st = cudaStreamWaitEvent(s->stream, s->ev_copy[1], 0);
     if (st == cudaSuccess) {
-        k_import_dev32<<<grid, block, 0, s->stream>>>(s->sf, N, s->d_consts, pg, s->Cv, s->U[0], s->U[1],
+        k_import_stored<<<grid, block, 0, s->stream>>>(s->sf, N, s->d_consts, pg, s->Cv, s->U[0], s->U[1],
                                                       s->mesh->d_n2o, tmp, 1);
         st = cudaGetLastError();
     }
     return st;
 }
 
-extern "C" alelb_status alelb_get_pops_dev32(alelb_solver *s, float *f, float *g)
+extern "C" alelb_status alelb_get_pops_stored(alelb_solver *s, float *f, float *g)
 {
     if (!s || !f || !g) return ALELB_ERR_ARG;
     if (s->prec != ALELB_PREC_FP32_DEV) {
-        s->err = "get_pops_dev32: the solver is not of the FP32-deviation form";
+        s->err = "get_pops_stored: the solver is not of the FP32-deviation form";
         return ALELB_ERR_ARG;
     }
-    const cudaError_t st = export_dev32_enqueue(s, f, g);
+    const cudaError_t st = export_stored_enqueue(s, f, g);
     if (st != cudaSuccess) return cuda_fail(s, st);
     return alelb_sync(s);
 }
 
-extern "C" alelb_status alelb_set_pops_dev32(alelb_solver *s, const float *f, const float *g, double t)
+extern "C" alelb_status alelb_set_pops_stored(alelb_solver *s, const float *f, const float *g, double t)
 {
     if (!s || !f || !g) return ALELB_ERR_ARG;
     if (s->prec != ALELB_PREC_FP32_DEV) {
-        s->err = "set_pops_dev32: the solver is not of the FP32-deviation form";
+        s->err = "set_pops_stored: the solver is not of the FP32-deviation form";
         return ALELB_ERR_ARG;
     }
-    cudaError_t st = import_dev32_enqueue(s, f, g);
+    cudaError_t st = import_stored_enqueue(s, f, g);
     if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream); // the caller's arrays are free again
     if (st != cudaSuccess) return cuda_fail(s, st);
     s->t = t;
     return ALELB_OK;
+}
+
+namespace {
+// A caller's device array for the zero-copy exchange: device (or managed)
+// memory of the mesh's device, else an argument error (so that no kernel
+// is ever handed a host address).
+bool on_mesh_device(alelb_solver *s, const void *p, const char *what)
+{
+    cudaPointerAttributes at{};
+    const cudaError_t st = cudaPointerGetAttributes(&at, p);
+    if (st != cudaSuccess) cudaGetLastError(); // clears the error of an unknown pointer
+    const bool ok = st == cudaSuccess &&
+                    (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+                    at.device == s->mesh->device;
+    if (!ok) s->err = std::string(what) + ": not device memory of the mesh's device";
+    return ok;
+}
+} // namespace
+
+extern "C" alelb_status alelb_get_pops_dev(alelb_solver *s, double *f, double *g)
+{
+    if (!s || !f || !g) return ALELB_ERR_ARG;
+    if (!on_mesh_device(s, f, "get_pops_dev") || !on_mesh_device(s, g, "get_pops_dev")) return ALELB_ERR_ARG;
+    alelb_mesh *m = s->mesh;
+    const int N = m->T.N;
+    const dim3 grid((N + 255) / 256), block(256);
+    with_state(s, [&](auto &sx, auto &) {
+        k_export<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, f, nullptr, m->d_n2o, 0);
+        k_export<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, g, nullptr, m->d_n2o, 1);
+    });
+    const cudaError_t st = cudaGetLastError();
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    return alelb_sync(s);
+}
+
+extern "C" alelb_status alelb_set_pops_dev(alelb_solver *s, const double *f, const double *g, double t)
+{
+    if (!s || !f || !g) return ALELB_ERR_ARG;
+    if (!on_mesh_device(s, f, "set_pops_dev") || !on_mesh_device(s, g, "set_pops_dev")) return ALELB_ERR_ARG;
+    const int N = s->mesh->T.N;
+    double *tmp = s->d_scratch + (size_t)18 * N;
+    const dim3 grid((N + 255) / 256), block(256);
+    with_state(s, [&](auto &sx, auto &) {
+        k_import<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, f, nullptr, 0, s->Cv, s->U[0], s->U[1],
+                                                s->mesh->d_n2o, tmp, 0);
+        k_import<<<grid, block, 0, s->stream>>>(sx, N, s->d_consts, g, nullptr, 0, s->Cv, s->U[0], s->U[1],
+                                                s->mesh->d_n2o, tmp, 1);
+    });
+    cudaError_t st = cudaGetLastError();
+    if (st == cudaSuccess) st = cudaStreamSynchronize(s->stream);
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    s->t = t;
+    return ALELB_OK;
+}
+
+extern "C" alelb_status alelb_moments_dev(alelb_solver *s, double *rho, double *ux, double *uy, double *T)
+{
+    if (!s) return ALELB_ERR_ARG;
+    double *const out[4] = {rho, ux, uy, T};
+    for (double *p : out)
+        if (p && !on_mesh_device(s, p, "moments_dev")) return ALELB_ERR_ARG;
+    alelb_mesh *m = s->mesh;
+    const int N = m->T.N;
+    double *dfields = s->d_scratch + (size_t)18 * N;
+    with_state(s, [&](auto &sx, auto &) {
+        k_export<<<(N + 255) / 256, 256, 0, s->stream>>>(sx, N, s->d_consts, nullptr, dfields, m->d_n2o, 1);
+    });
+    cudaError_t st = cudaGetLastError();
+    for (int c = 0; c < 4 && st == cudaSuccess; ++c)
+        if (out[c])
+            st = cudaMemcpyAsync(out[c], dfields + (size_t)c * N, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 s->stream);
+    if (st != cudaSuccess) return cuda_fail(s, st);
+    return alelb_sync(s);
 }
 
 extern "C" alelb_status alelb_forces(alelb_solver *s, double out[6])

@@ -1658,19 +1658,19 @@ extern "C" alelb_status alelb_batch_get_pops(alelb_batch *b, double *const *f, d
     return batch_get(b, [&](int c) { return export_enqueue(b->cs[c], f[c], g[c], nullptr); }, "batch_get_pops");
 }
 
-extern "C" alelb_status alelb_batch_set_pops_dev32(alelb_batch *b, const float *const *f, const float *const *g,
+extern "C" alelb_status alelb_batch_set_pops_stored(alelb_batch *b, const float *const *f, const float *const *g,
                                                    const double *t)
 {
     if (!b || !all_set(b, f, g) || b->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
-    return batch_set(b, [&](int c) { return import_dev32_enqueue(b->cs[c], f[c], g[c]); }, t,
-                     "batch_set_pops_dev32");
+    return batch_set(b, [&](int c) { return import_stored_enqueue(b->cs[c], f[c], g[c]); }, t,
+                     "batch_set_pops_stored");
 }
 
-extern "C" alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const *f, float *const *g)
+extern "C" alelb_status alelb_batch_get_pops_stored(alelb_batch *b, float *const *f, float *const *g)
 {
     if (!b || !all_set(b, f, g) || b->prec != ALELB_PREC_FP32_DEV) return ALELB_ERR_ARG;
-    return batch_get(b, [&](int c) { return export_dev32_enqueue(b->cs[c], f[c], g[c]); },
-                     "batch_get_pops_dev32");
+    return batch_get(b, [&](int c) { return export_stored_enqueue(b->cs[c], f[c], g[c]); },
+                     "batch_get_pops_stored");
 }
 
 // One step with the state in host memory, pipelined by case group: the
@@ -1681,8 +1681,8 @@ extern "C" alelb_status alelb_batch_get_pops_dev32(alelb_batch *b, float *const 
 // cases are in, and each case's read-back once its group's step is done,
 // so that the uploads of later groups, the steps and the read-back of
 // earlier ones overlap (the host link carries both directions at once).
-// Per case the same kernels as set_pops_dev32, one batch step and
-// get_pops_dev32.
+// Per case the same kernels as set_pops_stored, one batch step and
+// get_pops_stored.
 extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const *f_in, const float *const *g_in,
                                               float *const *f_out, float *const *g_out, const double *t)
 {
@@ -1706,7 +1706,7 @@ extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const
         for (int j = G.c0; j < G.c0 + G.B && st == cudaSuccess; ++j) {
             const int u = b->ord[j];
             if (g > 0) st = cudaStreamWaitEvent(b->cs[u]->stream, b->gev_up[g - 1], 0);
-            if (st == cudaSuccess) st = import_dev32_enqueue(b->cs[u], f_in[u], g_in[u]);
+            if (st == cudaSuccess) st = import_stored_enqueue(b->cs[u], f_in[u], g_in[u]);
         }
         // the group's stream waits for them (and the scalars)
         if (st == cudaSuccess) st = cudaStreamWaitEvent(G.stream, b->gev_fork, 0);
@@ -1727,7 +1727,7 @@ extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const
             const int u = b->ord[j];
             alelb_solver *s = b->cs[u];
             st = cudaStreamWaitEvent(s->stream, b->gev_fast[g], 0);
-            if (st == cudaSuccess) st = export_dev32_enqueue(s, f_out[u], g_out[u]);
+            if (st == cudaSuccess) st = export_stored_enqueue(s, f_out[u], g_out[u]);
             if (st == cudaSuccess)
                 st = cudaMemcpyAsync(b->h_err + u, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
         }

@@ -74,8 +74,8 @@ cudaError_t import_enqueue(alelb_solver *s, const double *f, const double *g, co
                            const double *ux, const double *uy, const double *T);
 cudaError_t export_enqueue(alelb_solver *s, double *f, double *g, double *const fld[4]);
 // the same for the FP32-deviation form's stored deviations (FP32 planes)
-cudaError_t import_dev32_enqueue(alelb_solver *s, const float *f, const float *g);
-cudaError_t export_dev32_enqueue(alelb_solver *s, float *f, float *g);
+cudaError_t import_stored_enqueue(alelb_solver *s, const float *f, const float *g);
+cudaError_t export_stored_enqueue(alelb_solver *s, float *f, float *g);
 // Uploads the P2 derivative tables of batch.cu's module.
 cudaError_t batch_fe_tables();
 // Status of a solver's sticky device errors (message in s->err).
