@@ -106,12 +106,13 @@ def test_other_precisions_and_bad_arrays_are_refused():
         b32.step_host(good, good, [np.zeros((9, s32.nn))], good)  # float64 out array
 
 
-@pytest.mark.parametrize("n_cases", [4, 1])
+@pytest.mark.parametrize("n_cases", [4, 2, 1])
 def test_pipelined_host_step_equals_set_step_get(n_cases):
     """alelb_batch_step_host (uploads, the step and the read-back pipelined
     by case group) against the three calls it stands for, three steps in a
     row: the same stored deviations, times, fields and walk counts, bit for
-    bit; in place (outputs = inputs) and into other arrays."""
+    bit; in place (outputs = inputs) and into other arrays.  Four cases run
+    as four groups, two as two, one as one."""
     cases = _cases()[:n_cases]
     ref, pip = _solvers(cases, alelb.PREC_FP32_DEV), _solvers(cases, alelb.PREC_FP32_DEV)
     br, bp = alelb.Batch(ref), alelb.Batch(pip)
