@@ -47,7 +47,7 @@ constexpr int FAST_FUSED = 256;
 // latest one, so that one group's propagation runs beside the other
 // groups' later phases
 constexpr int TWO_GROUPS = 512, FOUR_GROUPS = 1024, PIPELINED = 4096;
-constexpr int GROUPS_MAX = 4;
+constexpr int GROUPS_MAX = 8; // 2 or 4 in graph mode; 8 for the pipelined host step
 
 template <class S, class A> struct CaseDev {
     MeshDev M;
@@ -727,8 +727,8 @@ struct alelb_batch {
         int *d_off[N_BS] = {};   // tile tables of the run (device)
         std::vector<int> h_off[N_BS];
     };
-    Run run2[2], run4[4];
-    bool has2 = false, has4 = false; // every group of the split holds a case
+    Run run2[2], run4[4], run8[8];
+    bool has2 = false, has4 = false, has8 = false; // every group of the split holds a case
     cudaStream_t gstream[GROUPS_MAX] = {}; // [0] unused: group 0 runs on the batch's stream
     cudaEvent_t gev_fork = nullptr, gev_join[GROUPS_MAX] = {}, gev_fast[GROUPS_MAX] = {};
     cudaEvent_t gev_up[GROUPS_MAX] = {}; // alelb_batch_step_host: group g's uploads are in
@@ -830,10 +830,10 @@ Part whole(const alelb_batch *b)
     return P;
 }
 
-// Group g of the split into `groups` (2 or 4) groups.
+// Group g of the split into `groups` (2, 4 or 8) groups.
 Part group(const alelb_batch *b, int groups, int g, bool pdl)
 {
-    const alelb_batch::Run &R = groups == 4 ? b->run4[g] : b->run2[g];
+    const alelb_batch::Run &R = groups == 8 ? b->run8[g] : groups == 4 ? b->run4[g] : b->run2[g];
     Part P{g ? b->gstream[g] : b->stream, R.c0, R.n, {}, {}, pdl};
     for (int q = 0; q < N_BS; ++q) {
         P.off[q] = R.d_off[q];
@@ -1160,26 +1160,34 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     }
     if (st != cudaSuccess) return bfail(b, st, "stream");
     // descriptor order: the cases dealt, largest first, to the half (runs
-    // 0-1 or 2-3) with fewer nodes so far, within it to the run with fewer
-    // nodes, each run's cases then in the callers' order
-    int first4[5] = {};
+    // 0-3 or 4-7) with fewer nodes so far, within it to the quarter (a pair
+    // of runs) with fewer, within that to the run with fewer, each run's
+    // cases then in the callers' order; two groups are the halves, four
+    // the quarters, eight the runs
+    int first8[9] = {};
     {
         std::vector<int> idx(B);
         for (int c = 0; c < B; ++c) idx[c] = c;
         std::stable_sort(idx.begin(), idx.end(),
                          [b](int x, int y) { return b->cs[x]->mesh->T.N > b->cs[y]->mesh->T.N; });
         std::vector<int> rof(B, 0);
-        long long load[4] = {};
+        long long load[8] = {};
+        const auto sum = [&](int r0, int n) {
+            long long v = 0;
+            for (int r = r0; r < r0 + n; ++r) v += load[r];
+            return v;
+        };
         for (int c : idx) {
-            const int h = load[2] + load[3] < load[0] + load[1] ? 2 : 0;
-            const int r = load[h + 1] < load[h] ? h + 1 : h;
+            const int h = sum(4, 4) < sum(0, 4) ? 4 : 0;
+            const int q = sum(h + 2, 2) < sum(h, 2) ? h + 2 : h;
+            const int r = load[q + 1] < load[q] ? q + 1 : q;
             rof[c] = r;
             load[r] += b->cs[c]->mesh->T.N;
         }
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < 8; ++r) {
             for (int c = 0; c < B; ++c)
                 if (rof[c] == r) b->ord.push_back(c);
-            first4[r + 1] = (int)b->ord.size();
+            first8[r + 1] = (int)b->ord.size();
         }
     }
     // tile offsets per block size, of all cases and of each run
@@ -1201,11 +1209,17 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         for (int c = 0; c < B; ++c) o[c + 1] = o[c] + tiles_of(c, bs);
         b->d_off[q] = b->buf.put(o, st);
     }
-    for (int r = 0; r < 4; ++r) set_run(b->run4[r], first4[r], first4[r + 1]);
-    set_run(b->run2[0], first4[0], first4[2]);
-    set_run(b->run2[1], first4[2], first4[4]);
-    b->has2 = b->run2[0].n > 0 && b->run2[1].n > 0;
-    b->has4 = b->run4[0].n > 0 && b->run4[1].n > 0 && b->run4[2].n > 0 && b->run4[3].n > 0;
+    for (int r = 0; r < 8; ++r) set_run(b->run8[r], first8[r], first8[r + 1]);
+    for (int q = 0; q < 4; ++q) set_run(b->run4[q], first8[2 * q], first8[2 * q + 2]);
+    for (int h = 0; h < 2; ++h) set_run(b->run2[h], first8[4 * h], first8[4 * h + 4]);
+    const auto all_held = [](const alelb_batch::Run *R, int n) {
+        for (int k = 0; k < n; ++k)
+            if (R[k].n == 0) return false;
+        return true;
+    };
+    b->has2 = all_held(b->run2, 2);
+    b->has4 = all_held(b->run4, 4);
+    b->has8 = all_held(b->run8, 8);
     for (int g = 1; g < GROUPS_MAX && st == cudaSuccess; ++g)
         st = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking);
     if (st == cudaSuccess) st = cudaEventCreateWithFlags(&b->gev_fork, cudaEventDisableTiming);
@@ -1690,7 +1704,7 @@ extern "C" alelb_status alelb_batch_step_host(alelb_batch *b, const float *const
         return ALELB_ERR_ARG;
     if (t)
         for (int c = 0; c < b->B; ++c) b->cs[c]->t = t[c];
-    const int P = b->has4 ? 4 : b->has2 ? 2 : 1;
+    const int P = b->has8 ? 8 : b->has4 ? 4 : b->has2 ? 2 : 1;
     const auto part = [&](int g) {
         Part G = P > 1 ? group(b, P, g, false) : whole(b);
         G.pdl = false; // its first kernel follows waits on other streams
