@@ -1160,35 +1160,48 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
     }
     if (st != cudaSuccess) return bfail(b, st, "stream");
     // descriptor order: the cases dealt, largest first, to the half (runs
-    // 0-3 or 4-7) with fewer nodes so far, within it to the quarter (a pair
-    // of runs) with fewer, within that to the run with fewer, each run's
-    // cases then in the callers' order; two groups are the halves, four
-    // the quarters, eight the runs
-    int first8[9] = {};
+    // 0-1 or 2-3) with fewer nodes so far, within it to the run with fewer
+    // nodes, each run's cases then in the callers' order; two groups are the
+    // halves, four the runs, eight each run split where its nodes are
+    // closest to halved (the pipelined host step)
+    int first4[5] = {}, first8[9] = {};
     {
         std::vector<int> idx(B);
         for (int c = 0; c < B; ++c) idx[c] = c;
         std::stable_sort(idx.begin(), idx.end(),
                          [b](int x, int y) { return b->cs[x]->mesh->T.N > b->cs[y]->mesh->T.N; });
         std::vector<int> rof(B, 0);
-        long long load[8] = {};
-        const auto sum = [&](int r0, int n) {
-            long long v = 0;
-            for (int r = r0; r < r0 + n; ++r) v += load[r];
-            return v;
-        };
+        long long load[4] = {};
         for (int c : idx) {
-            const int h = sum(4, 4) < sum(0, 4) ? 4 : 0;
-            const int q = sum(h + 2, 2) < sum(h, 2) ? h + 2 : h;
-            const int r = load[q + 1] < load[q] ? q + 1 : q;
+            const int h = load[2] + load[3] < load[0] + load[1] ? 2 : 0;
+            const int r = load[h + 1] < load[h] ? h + 1 : h;
             rof[c] = r;
             load[r] += b->cs[c]->mesh->T.N;
         }
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < 4; ++r) {
             for (int c = 0; c < B; ++c)
                 if (rof[c] == r) b->ord.push_back(c);
-            first8[r + 1] = (int)b->ord.size();
+            first4[r + 1] = (int)b->ord.size();
         }
+        for (int r = 0; r < 4; ++r) {
+            // the split point of run r: at least one case each side when it
+            // holds two, the two sides' node counts as close as possible
+            const int c0 = first4[r], c1 = first4[r + 1];
+            long long tot = 0, left = 0, best = -1;
+            for (int j = c0; j < c1; ++j) tot += b->cs[b->ord[j]]->mesh->T.N;
+            int cut = c1 - c0 >= 2 ? c0 + 1 : c1;
+            for (int j = c0; j + 1 < c1; ++j) {
+                left += b->cs[b->ord[j]]->mesh->T.N;
+                const long long d = left * 2 > tot ? left * 2 - tot : tot - left * 2;
+                if (best < 0 || d < best) {
+                    best = d;
+                    cut = j + 1;
+                }
+            }
+            first8[2 * r] = c0;
+            first8[2 * r + 1] = cut;
+        }
+        first8[8] = B;
     }
     // tile offsets per block size, of all cases and of each run
     const auto tiles_of = [b](int j, int bs) { return (b->cs[b->ord[j]]->mesh->T.N + bs - 1) / bs; };
@@ -1210,8 +1223,8 @@ extern "C" alelb_status alelb_batch_create(alelb_solver *const *cases, int32_t B
         b->d_off[q] = b->buf.put(o, st);
     }
     for (int r = 0; r < 8; ++r) set_run(b->run8[r], first8[r], first8[r + 1]);
-    for (int q = 0; q < 4; ++q) set_run(b->run4[q], first8[2 * q], first8[2 * q + 2]);
-    for (int h = 0; h < 2; ++h) set_run(b->run2[h], first8[4 * h], first8[4 * h + 4]);
+    for (int q = 0; q < 4; ++q) set_run(b->run4[q], first4[q], first4[q + 1]);
+    for (int h = 0; h < 2; ++h) set_run(b->run2[h], first4[2 * h], first4[2 * h + 2]);
     const auto all_held = [](const alelb_batch::Run *R, int n) {
         for (int k = 0; k < n; ++k)
             if (R[k].n == 0) return false;
