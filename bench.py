@@ -916,6 +916,49 @@ def run_element_stability(alelb, args):
     return out
 
 
+def run_bulk_stability(alelb, args):
+    """Where the scheme itself stops being stable: a periodic box of 48 x 48
+    cells with jittered P2 nodes and no walls, uniform flow at Ma 0.2 with
+    every population perturbed by 1% (seeded), FP32 populations, 3,000
+    steps per free-stream temperature and relaxation frequency omega (the
+    viscosity set from omega); then the still 150k NACA 0012 at Re 1e4 and
+    12000 (T 0.3, the paper's wall targets, phi on).  A non-finite state
+    stops a run."""
+    out = {}
+
+    def run(s, steps, check):
+        done = 0
+        while done < steps:
+            s.lb_step(100)
+            done += 100
+            try:
+                check()
+            except alelb.AlelbError:
+                return {"status": f"diverged by step {done}", "steps": done}
+        return {"status": "completed", "steps": done}
+
+    m = alelb.Mesh(I.periodic_box(48, 96.0, 0.2, seed=1), I.Motion.make(I.MOTION_NONE))
+    rng = np.random.default_rng(2)
+    for T in (0.25, 0.3):
+        for om in (1.8, 1.85, 1.9, 1.95):
+            s = alelb.Solver(m, I.flow_params(0.2, T_inf=T, mu=(1.0 / om - 0.5) * T), alelb.PREC_FP32_DEV)
+            f, g = s.get_pops()
+            s.set_pops(f * (1 + 0.01 * rng.standard_normal(f.shape)), g * (1 + 0.01 * rng.standard_normal(g.shape)))
+            out[f"box_T{T}_omega{om}"] = run(s, 3000, s.sync)
+            s.close()
+    m.close()
+    m = alelb.Mesh(I.naca_omesh(320, 118, chord=1000.0, R=20000.0, first=1.0), I.Motion.make(I.MOTION_NONE))
+    for Re in (1e4, 12000.0):
+        flow = I.flow_params(0.2, T_inf=0.3, Re=Re, chord=1000.0)
+        s = alelb.Solver(m, flow, alelb.PREC_FP32_DEV)
+        r = run(s, 3000, s.forces)
+        r["omega"] = round(1.0 / (flow.mu / (flow.rho_inf * flow.T_inf) + 0.5), 3)
+        out[f"still_airfoil_Re{int(Re)}"] = r
+        s.close()
+    m.close()
+    return out
+
+
 def run_single(alelb, torch, dev, world, args):
     """The 150,400-node plunge (h = 0.1c, k = 1, Mach 0.2, Re 1e4): the
     FP32-deviation form and the plain FP64 form, one case.  Its working set
@@ -1094,6 +1137,7 @@ def run_ours(args):
     forces = None if (args.no_forces or world > 1) else run_force_history(alelb, args)
     growth = None if (args.no_precision or world > 1) else run_precision_growth(alelb, args)
     stability = run_element_stability(alelb, args) if (args.stability and world == 1) else None
+    bulk = run_bulk_stability(alelb, args) if (args.stability and world == 1) else None
     precision = precision_low = None
     if not (args.no_precision or world > 1):
         # config 3 at its own Mach number: the shifted lattice of the transonic
@@ -1148,6 +1192,7 @@ def run_ours(args):
             "precision_study_ma03": precision_low,
             "precision_growth": growth,
             "element_stability": stability,
+            "bulk_stability": bulk,
             "e2e": bat["e2e"],
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
